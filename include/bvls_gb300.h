@@ -1,0 +1,154 @@
+/*
+ * bvls_gb300.h -- C ABI of a GB300 (sm_103a) solver for box-constrained least squares
+ * with dynamic Gap safe screening.
+ *
+ * Problem (Dantas, Soubies, Fevotte, "Accelerating Non-Negative and Bounded-Variable
+ * Linear Regression Algorithms with Safe Screening", Section 2, Eq. (LR) with the
+ * least-squares loss of Section 5):
+ *
+ *     x* in argmin_x 1/2 ||y - A x||_2^2   subject to  l <= x <= u,
+ *
+ * with l finite and u in R or +inf (NNLS: l = 0, u = +inf; BVLS: every u finite).
+ *
+ * The solver is an accelerated projected-gradient iteration (FISTA with gradient-based
+ * adaptive restart) into which the screening procedure of Algorithm 1 (Algorithm 2 for
+ * NNLS) is fused: the dual point of Section 4 (Eq. (BVLR_dual_up) for BVLS, the dual
+ * translation of Eq. (BVLR_dual_up2) when some u_j = +inf), the duality gap of
+ * Eq. (Dual_Gap), the Gap safe radius of Eq. (GAP_Safe_sph) and the sphere test of
+ * Eq. (safe_rule), which fixes coordinates at their bounds and removes their columns from
+ * every later product (Eq. (decmposition_fwd)).
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are column-major float32: column j of A starts at A + j*lda, lda >= m.
+ *   - Pointers documented as "any" may point to device memory, pinned host memory or
+ *     pageable host memory; the library copies through the CUDA runtime with unified
+ *     addressing.  Pointers documented as "host" must be host memory.
+ *   - The caller owns every pointer it passes; the library keeps no reference to a
+ *     caller pointer after the call returns.  The handle owns its device workspace,
+ *     including its own padded copy of A.
+ *   - All device work of a handle runs in order after the work already queued on the
+ *     stream given to bvls_setup (0 = the legacy default stream); bvls_solve returns when
+ *     its results are in the caller's buffers.
+ *   - Every call returns a bvls_status and never aborts the process.  On BVLS_EINVAL,
+ *     BVLS_ENONFINITE and BVLS_ENOTSUP nothing is written to the outputs.
+ *     bvls_last_error() describes the last failure on the calling thread.
+ *   - A handle may be used by one host thread at a time.
+ */
+#ifndef BVLS_GB300_H
+#define BVLS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bvls_handle bvls_handle;
+
+typedef enum {
+  BVLS_OK = 0,
+  BVLS_EINVAL = 1,      /* invalid argument (sizes, bounds with l > u or l not finite, ...) */
+  BVLS_ENOMEM = 2,      /* a device allocation failed */
+  BVLS_ECUDA = 3,       /* a CUDA runtime call failed */
+  BVLS_EMAXITER = 4,    /* max_iter reached with gap >= tol; outputs hold the last evaluated
+                           iterate, its gap and its screened set */
+  BVLS_ENONFINITE = 5,  /* NaN or Inf found in A, y or x0 */
+  BVLS_ENOTSUP = 6      /* sizes beyond what this build supports (see bvls_setup) */
+} bvls_status;
+
+/* Arithmetic of the two products over the preserved columns. */
+enum {
+  BVLS_PREC_FP32X2 = 0, /* float32 data, error-free products and double-float (about 48-bit)
+                           accumulation; default */
+  BVLS_PREC_FP32 = 1    /* float32 data and plain float32 accumulation; faster, and the
+                           rounding margins of the test are about 2^24 times wider */
+};
+
+/* Dual point used by the screening step (Section 4). */
+enum {
+  BVLS_DUAL_SCALING = 0,     /* every u_j finite: theta = y - A x (Eq. (BVLR_dual_up)) */
+  BVLS_DUAL_TRANSLATION = 1, /* some u_j = +inf: theta = Xi_t(y - A x) (Eq. (BVLR_dual_up2)) */
+  BVLS_DUAL_ZERO = 2         /* some u_j = +inf and no interior direction t was found:
+                                theta = 0, the gap is P(x) and nothing is screened */
+};
+
+typedef struct {
+  double tol;         /* stop when the gap bound < tol (absolute; Algorithm 1's until test) */
+  int screen_every;   /* K >= 1: the gap and the screening step run every K iterations */
+  int max_iter;       /* >= 1; rounded up to a multiple of screen_every */
+  int screening;      /* 1: Algorithm 1; 0: the same iteration and gap with nothing fixed */
+  int precision;      /* BVLS_PREC_* */
+  int restart;        /* 1: gradient-based adaptive restart of the momentum */
+  double lipschitz;   /* > 0: use this step constant L instead of the one from bvls_setup */
+  int profile;        /* 1: launch without CUDA graphs and time every product kernel with
+                         CUDA events (fills the *_ms fields of bvls_info) */
+} bvls_opts;
+
+typedef struct {
+  int iters;            /* iterations run (gradient evaluations) */
+  int converged;        /* 1 when gap < tol */
+  int n_preserved;      /* |preserved set| at the end */
+  int dual_mode;        /* BVLS_DUAL_* */
+  int gap_evals;        /* screening / gap evaluations */
+  double gap;           /* rigorous upper bound of the duality gap at the returned x */
+  double primal;        /* P(x) = 1/2 ||y - A x||^2 at the returned x (reduced-problem value) */
+  double radius;        /* Gap safe radius of the last evaluation */
+  double L;             /* step constant used */
+  double sum_preserved; /* sum over iterations of |preserved set| (one product pass each) */
+  double fwd_ms, tr_ms; /* profile mode: total time in the A_S x_S and A_S^T r kernels */
+  int fwd_launches, tr_launches;
+} bvls_info;
+
+/* Fill *opts with the defaults: tol 1e-6, screen_every 10, max_iter 100000, screening 1,
+   precision BVLS_PREC_FP32X2, restart 1, lipschitz 0 (use setup's), profile 0. */
+void bvls_default_opts(bvls_opts* opts);
+
+/*
+ * Prepare a solver for the matrix A and the box [l, u].
+ *   A       any; m x n column-major float32 with leading dimension lda >= m.  Copied into a
+ *           handle-owned layout padded to a multiple of 32 rows.
+ *   l, u    host; n doubles each, or NULL for l = 0 / u = +inf.  l must be finite, u may
+ *           be +INFINITY, l_j <= u_j.
+ *   t       host; m doubles: the translation direction of Section 4.2 for the columns
+ *           with u_j = +inf, or NULL to choose one (t = -1, then minus the mean column,
+ *           then minus the column most correlated with all others, per Proposition 2 and
+ *           the choices of Section 5).  A given t must satisfy a_j^T t < 0 on every
+ *           nonzero column with u_j = +inf, else BVLS_EINVAL.
+ *   stream  a cudaStream_t (0 = legacy default stream).
+ *   out     receives the handle.
+ * Setup computes the column norms ||a_j||_2 (used by Eq. (safe_rule)), w = A^T t and the
+ * step constant L (1.05 x a 100-step power-iteration estimate of ||A||_2^2).
+ * Limits: 1 <= m <= 24576 (the residual is staged in shared memory), 1 <= n < 2^31,
+ * lda*n*4 bytes addressable.  Errors: EINVAL, ENOTSUP, ENOMEM, ECUDA, ENONFINITE (A).
+ */
+bvls_status bvls_setup(const float* A, int m, int n, int lda, const double* l,
+                       const double* u, const double* t, void* stream, bvls_handle** out);
+
+/*
+ * Solve for one right-hand side y with the handle's A and box.
+ *   y             any; m float32.
+ *   x0            any; n doubles, the starting point (projected onto [l, u]), or NULL for
+ *                 the projection of 0 (Algorithm 1: initialise x in [l, u]).
+ *   opts          host; NULL for the defaults.
+ *   x_out         any; n doubles: the iterate at which the final gap was evaluated, with
+ *                 every screened coordinate at its bound.
+ *   screened_out  any; n bytes or NULL: 0 preserved, 1 fixed at l_j, 2 fixed at u_j.
+ *   info          host; or NULL.
+ * Returns BVLS_OK when the gap bound fell below tol, BVLS_EMAXITER otherwise (outputs
+ * valid), or an error (outputs untouched).
+ */
+bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const bvls_opts* opts,
+                       double* x_out, uint8_t* screened_out, bvls_info* info);
+
+/* Release the handle and its device memory (NULL is ignored). */
+void bvls_destroy(bvls_handle* h);
+
+/* Text of the last error recorded on the calling thread ("" if none). */
+const char* bvls_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BVLS_GB300_H */

@@ -1,0 +1,328 @@
+"""Pins of the FP64 oracle against mathematics that does not come from the oracle itself.
+
+Each check is chosen so that a plausible slip in the oracle (a dropped term, a sign, a
+transposed operand, a wrong radius) fails at least one of them; ``test_mutations`` plants
+such slips in the oracle and confirms that the pins catch them.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.optimize as so
+
+import oracle as O
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _f64(p):
+    return p.A.astype(np.float64), p.y.astype(np.float64).reshape(-1)
+
+
+def _sigma(g, l, u):
+    """sup_{x in [l,u]} x g, written out per coordinate (Appendix B)."""
+    out = np.empty_like(g)
+    for j in range(g.size):
+        if g[j] >= 0:
+            out[j] = 0.0 if g[j] == 0 else (u[j] * g[j] if np.isfinite(u[j]) else np.inf)
+        else:
+            out[j] = l[j] * g[j]
+    return out
+
+
+# ----------------------------------------------------------------------------- pin helpers
+def check_closed_form_1col(solve_kw):
+    rng = np.random.default_rng(11)
+    for _ in range(6):
+        m = int(rng.integers(2, 9))
+        a = rng.standard_normal((m, 1))
+        y = rng.standard_normal(m) * 3
+        lo = float(rng.uniform(-1, 0))
+        hi = float(rng.uniform(0, 1)) if rng.random() < 0.7 else np.inf
+        exact = np.clip((a[:, 0] @ y) / (a[:, 0] @ a[:, 0]), lo, hi)
+        r = O.solve(a, y, [lo], [hi], tol=1e-12, screen_every=1, max_iter=5000, **solve_kw)
+        assert abs(r.x[0] - exact) < 1e-9 * (1 + abs(exact)), (r.x, exact)
+
+
+def check_golden():
+    with open(os.path.join(GOLDEN, "hand_derived.json")) as f:
+        cases = json.load(f)["cases"]
+    for c in cases:
+        A = np.array(c["A"], float)
+        y = np.array(c["y"], float)
+        l = np.array(c["l"], float)
+        u = np.array([np.inf if v == "inf" else v for v in c["u"]], float)
+        xs = np.array(c["x_star"], float)
+        th = np.array(c["theta_star"], float)
+        xb, Pb = O.brute_force(A, y, l, u)
+        assert np.allclose(xb, xs, atol=1e-12), (c["name"], xb)
+        assert abs(Pb - c["P_star"]) < 1e-12
+        assert abs(O.primal_objective(A, y, xs) - c["P_star"]) < 1e-12
+        assert abs(O.dual_objective(A, y, th, l, u) - c["P_star"]) < 1e-12, c["name"]
+        assert np.allclose(O.theta_scaling(A, y, xs), th, atol=1e-12)
+        assert O.dual_feasible(A, th, u, tol=1e-12)
+        r = O.solve(A, y, l, u, tol=1e-12, screen_every=1, max_iter=20000)
+        assert np.allclose(r.x, xs, atol=1e-7), (c["name"], r.x)
+        S_l, S_u = O.safe_rule(A, th, 0.0, u)
+        sign = np.array(c["screen_sign"])
+        assert np.array_equal(S_l, sign == -1) and np.array_equal(S_u, sign == 1), c["name"]
+
+
+def check_strong_duality(kinds=("bvls", "mixed", "nnls_abs")):
+    for kind in kinds:
+        for seed in range(3):
+            p = W.random_tiny(7, 5, kind, seed)
+            A, y = _f64(p)
+            xb, Pb = O.brute_force(A, y, p.l, p.u)
+            th = O.theta_scaling(A, y, xb)       # theta* = -f'(A x*) (Eq. (optimality1))
+            assert O.dual_feasible(A, th, p.u, tol=1e-9)
+            D = O.dual_objective(A, y, th, p.l, p.u)
+            assert abs(Pb - D) < 1e-9 * (1 + abs(Pb)), (kind, seed, Pb, D)
+
+
+def check_weak_duality_and_identity():
+    rng = np.random.default_rng(5)
+    for kind in ("bvls", "mixed", "nnls_abs", "nnls_gauss"):
+        for seed in range(4):
+            p = W.random_tiny(9, 6, kind, seed)
+            A, y = _f64(p)
+            l, u = p.l, p.u
+            ub = np.where(np.isfinite(u), u, l + 3.0)
+            t = O.choose_translation(A, u) if not np.all(np.isfinite(u)) else None
+            for _ in range(10):
+                x = rng.uniform(l, ub)
+                r = y - A @ x
+                if t is None and not np.all(np.isfinite(u)):
+                    th = np.zeros_like(y)
+                elif t is None:
+                    th = r + 0.3 * rng.standard_normal(y.size)
+                else:
+                    th, _ = O.translate(A, r + 0.3 * rng.standard_normal(y.size), t,
+                                        O.translation_columns(A, u))
+                assert O.dual_feasible(A, th, u, tol=1e-10)
+                P = O.primal_objective(A, y, x)
+                D = O.dual_objective(A, y, th, l, u)
+                assert D <= P + 1e-10 * (1 + abs(P)), (kind, seed)
+                # Identity derived from |y|^2 = |Ax|^2 + 2<Ax, r> + |r|^2:
+                # P(x) - D(theta) = sum_j [sigma_j(a_j^T theta) - x_j a_j^T theta] + |theta - r|^2 / 2.
+                g = A.T @ th
+                inf_cols = ~np.isfinite(u)
+                assert np.all(g[inf_cols] <= 1e-10 * (1 + np.abs(g).max()))
+                g = np.where(inf_cols, np.minimum(g, 0.0), g)   # F_D up to rounding
+                rhs = float(np.sum(_sigma(g, l, u) - x * g) + 0.5 * (th - r) @ (th - r))
+                gap = O.duality_gap(A, y, x, th, l, u)
+                assert abs(gap - rhs) < 1e-9 * (1 + abs(P)), (kind, seed, gap, rhs)
+
+
+def check_sphere_contains_theta_star():
+    """Gap safe sphere (Eq. (GAP_Safe_sph), alpha = 1): ||theta - theta*|| <= sqrt(2 Gap)."""
+    rng = np.random.default_rng(9)
+    for kind in ("bvls", "nnls_abs", "mixed"):
+        for seed in range(3):
+            p = W.random_tiny(8, 6, kind, seed)
+            A, y = _f64(p)
+            xb, _ = O.brute_force(A, y, p.l, p.u)
+            th_star = y - A @ xb
+            ub = np.where(np.isfinite(p.u), p.u, p.l + 3.0)
+            t = O.choose_translation(A, p.u) if not np.all(np.isfinite(p.u)) else None
+            for _ in range(20):
+                x = rng.uniform(p.l, ub)
+                r = y - A @ x
+                if t is None:
+                    th = r
+                else:
+                    th, _ = O.translate(A, r, t, O.translation_columns(A, p.u))
+                rad = O.safe_radius(O.duality_gap(A, y, x, th, p.l, p.u))
+                assert np.linalg.norm(th - th_star) <= rad * (1 + 1e-9) + 1e-9, (kind, seed)
+
+
+def check_solver_vs_brute_force(**kw):
+    for kind in ("nnls_abs", "nnls_gauss", "bvls", "mixed"):
+        for seed in range(3):
+            p = W.random_tiny(9, 6, kind, seed)
+            A, y = _f64(p)
+            xb, Pb = O.brute_force(A, y, p.l, p.u)
+            r = O.solve(A, y, p.l, p.u, tol=1e-11, screen_every=5, max_iter=200000, **kw)
+            assert r.converged, (kind, seed, r.gap, r.dual_mode)
+            assert abs(r.primal - Pb) < 1e-10 * (1 + Pb), (kind, seed)
+            assert np.max(np.abs(r.x - xb)) < 1e-5, (kind, seed, r.x, xb)
+            th_star = y - A @ xb
+            g = A.T @ th_star
+            # Every screened coordinate sits at its bound in the optimum (Eq. (screen_cond)).
+            low, upp = r.screened == 1, r.screened == 2
+            assert np.all(np.abs(xb[low] - p.l[low]) < 1e-9), (kind, seed)
+            assert np.all(np.abs(xb[upp] - p.u[upp]) < 1e-9), (kind, seed)
+            assert np.all(g[low] < 1e-9) and np.all(g[upp] > -1e-9)
+
+
+def check_translation_validity():
+    rng = np.random.default_rng(3)
+    for seed in range(5):
+        p = W.random_tiny(10, 8, "nnls_abs", seed)
+        A, y = _f64(p)
+        t = O.choose_translation(A, p.u)
+        assert t is not None and np.all(A.T @ t < 0)
+        cols = O.translation_columns(A, p.u)
+        for _ in range(20):
+            z = rng.standard_normal(y.size) * 3
+            th, eps = O.translate(A, z, t, cols)
+            g = A.T @ th
+            assert np.all(g <= 1e-12 * (1 + np.abs(A.T @ z)))       # Proposition 1: in F_D
+            if np.any(A.T @ z > 0):
+                assert np.max(g) > -1e-9                               # eps is the smallest such step
+            else:
+                assert eps == 0.0 and np.array_equal(th, z)
+
+
+# ----------------------------------------------------------------------------- tests
+def test_golden_hand_derived():
+    check_golden()
+
+
+def test_closed_form_single_column():
+    check_closed_form_1col({})
+    check_closed_form_1col({"screening": False})
+
+
+def test_identity_and_orthonormal_closed_forms():
+    rng = np.random.default_rng(1)
+    for trial in range(4):
+        m, n = 12, 7
+        Q, _ = np.linalg.qr(rng.standard_normal((m, n)))
+        y = 2 * rng.standard_normal(m)
+        for l, u in [(np.zeros(n), np.full(n, np.inf)), (-0.5 * np.ones(n), 0.7 * np.ones(n))]:
+            exact = np.clip(Q.T @ y, l, u)            # separable after the change of basis
+            r = O.solve(Q, y, l, u, tol=1e-12, screen_every=1, max_iter=5000)
+            assert np.max(np.abs(r.x - exact)) < 1e-8
+            if trial == 0:
+                r = O.solve(np.eye(m), y, np.zeros(m), None, tol=1e-12, screen_every=1)
+                assert np.allclose(r.x, np.maximum(y, 0), atol=1e-12)
+                th = O.theta_scaling(np.eye(m), y, r.x)
+                assert np.allclose(th, np.minimum(y, 0), atol=1e-12)
+
+
+def test_brute_force_matches_scipy():
+    for seed in range(4):
+        p = W.random_tiny(10, 7, "nnls_abs", seed)
+        A, y = _f64(p)
+        xb, Pb = O.brute_force(A, y, p.l, p.u)
+        xs, rn = so.nnls(A, y)
+        assert abs(Pb - 0.5 * rn ** 2) < 1e-10 * (1 + Pb)
+        assert np.allclose(xb, xs, atol=1e-8)
+        p = W.random_tiny(10, 7, "bvls", seed)
+        A, y = _f64(p)
+        xb, Pb = O.brute_force(A, y, p.l, p.u)
+        res = so.lsq_linear(A, y, bounds=(p.l, p.u), method="bvls", tol=1e-14)
+        assert abs(Pb - O.primal_objective(A, y, res.x)) < 1e-9 * (1 + Pb)
+
+
+def test_strong_duality_at_optimum():
+    check_strong_duality()
+
+
+def test_weak_duality_and_gap_identity():
+    check_weak_duality_and_identity()
+
+
+def test_sphere_contains_dual_optimum():
+    check_sphere_contains_theta_star()
+
+
+def test_translation_validity():
+    check_translation_validity()
+
+
+@pytest.mark.parametrize("kw", [{}, {"screening": False}, {"eps_scope": "all"}, {"restart": False}])
+def test_solver_matches_brute_force(kw):
+    check_solver_vs_brute_force(**kw)
+
+
+def test_solver_matches_scipy_midsize():
+    p = W.nnls_abs_gaussian(60, 150, 0.1, 1.0, 2)
+    A, y = _f64(p)
+    xs, rn = so.nnls(A, y, maxiter=5000)
+    r = O.solve(A, y, p.l, p.u, tol=1e-10, screen_every=10)
+    assert r.converged and abs(r.primal - 0.5 * rn ** 2) < 1e-9 * (1 + r.primal)
+    assert np.max(np.abs(O.polish(A, y, r.x, p.l, p.u) - xs)) < 1e-7
+    assert O.kkt_residual(A, y, r.x, p.l, p.u) < 1e-5
+    th_star = y - A @ xs
+    g = A.T @ th_star
+    assert np.all(xs[r.screened == 1] == 0.0) and np.all(g[r.screened == 1] < 0)
+    p = W.bvls_table2(80, 50, 4)
+    A, y = _f64(p)
+    res = so.lsq_linear(A, y, bounds=(p.l, p.u), method="bvls", tol=1e-14)
+    r = O.solve(A, y, p.l, p.u, tol=1e-11, screen_every=10)
+    assert r.converged and abs(r.primal - O.primal_objective(A, y, res.x)) < 1e-9 * (1 + r.primal)
+    assert np.max(np.abs(r.x - res.x)) < 1e-5
+
+
+def test_screening_does_not_change_iterates_when_pins_sit_at_bounds():
+    p = W.nnls_abs_gaussian(40, 120, 0.1, 1.0, 7)
+    A, y = _f64(p)
+    a = O.solve(A, y, tol=1e-10, screen_every=10, record=True)
+    b = O.solve(A, y, tol=1e-10, screen_every=10, screening=False, record=True)
+    assert a.iters == b.iters and (a.screened > 0).sum() > 0
+    assert np.max(np.abs(a.x - b.x)) < 1e-10
+
+
+def test_degenerate_gaussian_family_has_no_interior_direction():
+    # n = 2m Gaussian columns: 0 is inside conv{a_j} with overwhelming probability (Wendel),
+    # so Int(F_D) is empty (remark after Proposition 1) and the NNLS optimum interpolates y.
+    p = W.nnls_gaussian(100, 200, 0.1, 0.01, 0)
+    A, y = _f64(p)
+    assert O.choose_translation(A, p.u) is None
+    xs, rn = so.nnls(A, y, maxiter=20000)
+    assert rn < 1e-6
+    r = O.solve(A, y, tol=1e-9, screen_every=10)
+    assert r.converged and r.dual_mode == "zero" and r.screened.sum() == 0
+    assert abs(r.gap - r.primal) < 1e-15
+
+
+def test_choose_translation_cases():
+    rng = np.random.default_rng(0)
+    A = np.abs(rng.standard_normal((6, 9)))           # Proposition 2, case 3
+    assert np.array_equal(O.choose_translation(A, np.full(9, np.inf)), -np.ones(6))
+    A = rng.standard_normal((12, 5))                  # case 1: rank n <= m
+    t = O.choose_translation(A, np.full(5, np.inf))
+    assert t is not None and np.all(A.T @ t < 0)
+    assert O.choose_translation(A, np.ones(5)) is None   # no column in J_inf
+
+
+def test_bad_bounds_rejected():
+    with pytest.raises(ValueError):
+        O.as_problem(np.eye(2), np.ones(2), [0, 1], [1, 0])
+    with pytest.raises(ValueError):
+        O.as_problem(np.eye(2), np.ones(2), [-np.inf, 0], None)
+
+
+# ----------------------------------------------------------------------------- planted slips
+MUTANTS = {
+    "dual_drops_upper_term": ("dual_objective",
+        lambda A, y, th, l, u: 0.5 * y @ y - 0.5 * (y - th) @ (y - th) - np.sum(l * np.minimum(A.T @ th, 0))),
+    "dual_sign_flip": ("dual_objective",
+        lambda A, y, th, l, u: 0.5 * y @ y - 0.5 * (y - th) @ (y - th) + np.sum(l * np.minimum(A.T @ th, 0))
+        + np.sum(np.where(np.isfinite(u), u, 0) * np.maximum(A.T @ th, 0))),
+    "theta_sign_slip": ("theta_scaling", lambda A, y, x: y + A @ x),
+    "primal_half_missing": ("primal_objective", lambda A, y, x: float((y - A @ x) @ (y - A @ x))),
+    "radius_without_two": ("safe_radius", lambda gap, alpha=1.0: float(np.sqrt(max(gap, 0.0) / alpha))),
+    "translation_wrong_sign": ("translate",
+        lambda A, z, t, cols, w=None, margin=None: (z - 0.5 * t, 0.5)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutations_are_caught(name, monkeypatch):
+    import oracle.bvls as B
+    attr, fn = MUTANTS[name]
+    monkeypatch.setattr(B, attr, fn)
+    monkeypatch.setattr(O, attr, fn)
+    caught = 0
+    for check in (check_golden, check_strong_duality, check_weak_duality_and_identity,
+                  check_sphere_contains_theta_star, check_translation_validity):
+        try:
+            check()
+        except (AssertionError, ValueError, RuntimeError, IndexError):
+            caught += 1
+    assert caught > 0, name
