@@ -40,6 +40,12 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#if defined(__GNUC__)
+#define BVLS_API __attribute__((visibility("default")))
+#else
+#define BVLS_API
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -92,17 +98,20 @@ typedef struct {
   int dual_mode;        /* BVLS_DUAL_* */
   int gap_evals;        /* screening / gap evaluations */
   double gap;           /* rigorous upper bound of the duality gap at the returned x */
-  double primal;        /* P(x) = 1/2 ||y - A x||^2 at the returned x (reduced-problem value) */
+  double primal;        /* 1/2 ||y - A x||^2 at the iterate of the last gap evaluation, before
+                           that evaluation set its screened coordinates to their bounds */
   double radius;        /* Gap safe radius of the last evaluation */
   double L;             /* step constant used */
-  double sum_preserved; /* sum over iterations of |preserved set| (one product pass each) */
+  double sum_preserved; /* sum over iterations of |preserved set|: columns read by A_S^T r */
+  double sum_nonzero;   /* sum over iterations of the preserved x_j != 0: columns read by
+                           A_S x_S (zero coordinates contribute nothing and are skipped) */
   double fwd_ms, tr_ms; /* profile mode: total time in the A_S x_S and A_S^T r kernels */
   int fwd_launches, tr_launches;
 } bvls_info;
 
 /* Fill *opts with the defaults: tol 1e-6, screen_every 10, max_iter 100000, screening 1,
    precision BVLS_PREC_FP32X2, restart 1, lipschitz 0 (use setup's), profile 0. */
-void bvls_default_opts(bvls_opts* opts);
+BVLS_API void bvls_default_opts(bvls_opts* opts);
 
 /*
  * Prepare a solver for the matrix A and the box [l, u].
@@ -122,7 +131,7 @@ void bvls_default_opts(bvls_opts* opts);
  * Limits: 1 <= m <= 24576 (the residual is staged in shared memory), 1 <= n < 2^31,
  * lda*n*4 bytes addressable.  Errors: EINVAL, ENOTSUP, ENOMEM, ECUDA, ENONFINITE (A).
  */
-bvls_status bvls_setup(const float* A, int m, int n, int lda, const double* l,
+BVLS_API bvls_status bvls_setup(const float* A, int m, int n, int lda, const double* l,
                        const double* u, const double* t, void* stream, bvls_handle** out);
 
 /*
@@ -138,14 +147,14 @@ bvls_status bvls_setup(const float* A, int m, int n, int lda, const double* l,
  * Returns BVLS_OK when the gap bound fell below tol, BVLS_EMAXITER otherwise (outputs
  * valid), or an error (outputs untouched).
  */
-bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const bvls_opts* opts,
+BVLS_API bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const bvls_opts* opts,
                        double* x_out, uint8_t* screened_out, bvls_info* info);
 
 /* Release the handle and its device memory (NULL is ignored). */
-void bvls_destroy(bvls_handle* h);
+BVLS_API void bvls_destroy(bvls_handle* h);
 
 /* Text of the last error recorded on the calling thread ("" if none). */
-const char* bvls_last_error(void);
+BVLS_API const char* bvls_last_error(void);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,136 @@
+"""GB300 (sm_103a) solver for box-constrained least squares with dynamic Gap safe screening.
+
+    x* in argmin 1/2 ||y - A x||^2  s.t.  l <= x <= u      (NNLS: l = 0, u = +inf; BVLS)
+
+Dantas, Soubies and Fevotte, "Accelerating Non-Negative and Bounded-Variable Linear
+Regression Algorithms with Safe Screening": accelerated projected gradient with the
+screening of Algorithm 1 fused into the CUDA kernels of the C ABI (include/bvls_gb300.h).
+
+``_capi`` holds the C entry points under their C names; ``Solver`` marshals numpy arrays
+or torch tensors into them.  Nothing here computes: every step runs in the CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _capi
+from ._capi import (BVLS_DUAL_SCALING, BVLS_DUAL_TRANSLATION, BVLS_DUAL_ZERO, BVLS_EINVAL,
+                    BVLS_EMAXITER, BVLS_ENONFINITE, BVLS_ENOTSUP, BVLS_OK, BVLS_PREC_FP32,
+                    BVLS_PREC_FP32X2, DUAL_NAMES, STATUS_NAMES, bvls_default_opts, bvls_destroy,
+                    bvls_info, bvls_last_error, bvls_opts, bvls_setup, bvls_solve)
+
+__all__ = ["Solver", "BVLSError", "bvls_setup", "bvls_solve", "bvls_destroy", "bvls_default_opts",
+           "bvls_last_error", "bvls_opts", "bvls_info", "make_opts"]
+
+
+class BVLSError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _is_torch(x) -> bool:
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        return False
+    return isinstance(x, torch.Tensor)
+
+
+def _host_f64(v, n):
+    if v is None:
+        return None
+    return np.ascontiguousarray(np.broadcast_to(np.asarray(v, dtype=np.float64), (n,)))
+
+
+def make_opts(tol=1e-6, screen_every=10, max_iter=100000, screening=True, precision="fp32x2",
+              restart=True, lipschitz=0.0, profile=False) -> bvls_opts:
+    o = bvls_default_opts()
+    o.tol = float(tol)
+    o.screen_every = int(screen_every)
+    o.max_iter = int(max_iter)
+    o.screening = 1 if screening else 0
+    o.precision = {"fp32x2": BVLS_PREC_FP32X2, "fp32": BVLS_PREC_FP32}[precision]
+    o.restart = 1 if restart else 0
+    o.lipschitz = float(lipschitz)
+    o.profile = 1 if profile else 0
+    return o
+
+
+class Solver:
+    """One handle of the C ABI: the matrix A, the box [l, u] and the device workspace.
+
+    A is (m, n): a torch tensor (any device) or a numpy array.  l, u are scalars or length-n
+    arrays (u may hold inf); t optionally gives the translation direction (length m).
+    """
+
+    def __init__(self, A, l=None, u=None, t=None, stream=None):
+        if _is_torch(A):
+            import torch
+            m, n = A.shape
+            At = A.detach().to(dtype=torch.float32).t().contiguous()   # column-major A
+            self._A_keep = At
+            a_ptr = At.data_ptr()
+            if stream is None and At.is_cuda:
+                stream = torch.cuda.current_stream(At.device).cuda_stream
+        else:
+            A = np.asarray(A)
+            m, n = A.shape
+            Af = np.asfortranarray(A, dtype=np.float32)
+            self._A_keep = Af
+            a_ptr = Af.ctypes.data
+        self.m, self.n = int(m), int(n)
+        l_h, u_h = _host_f64(l, self.n), _host_f64(u, self.n)
+        t_h = None if t is None else np.ascontiguousarray(np.asarray(t, dtype=np.float64).reshape(self.m))
+        st, h = bvls_setup(a_ptr, self.m, self.n, self.m,
+                           None if l_h is None else l_h.ctypes.data,
+                           None if u_h is None else u_h.ctypes.data,
+                           None if t_h is None else t_h.ctypes.data, stream)
+        self._A_keep = None
+        if st != BVLS_OK:
+            raise BVLSError(st, bvls_last_error())
+        self.handle = h
+
+    def close(self):
+        bvls_destroy(getattr(self, "handle", None))
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, y, x0=None, *, opts: bvls_opts | None = None, x_out=None, screened_out=None,
+              check: bool = True, **kw):
+        """Run bvls_solve.  Returns (x, screened, info_dict, status).
+
+        Outputs follow y: a CUDA tensor y gives CUDA tensors (float64 x, uint8 screened),
+        a numpy y gives numpy arrays.  ``kw`` builds the options (see ``make_opts``).
+        With check=True a status other than OK / EMAXITER raises BVLSError.
+        """
+        if opts is None:
+            opts = make_opts(**kw)
+        if _is_torch(y):
+            import torch
+            dev = y.device
+            yk = y.detach().to(dtype=torch.float32).contiguous()
+            x0k = None if x0 is None else x0.detach().to(device=dev, dtype=torch.float64).contiguous()
+            x = x_out if x_out is not None else torch.empty(self.n, dtype=torch.float64, device=dev)
+            s = screened_out if screened_out is not None else torch.empty(self.n, dtype=torch.uint8, device=dev)
+            ptrs = (yk.data_ptr(), None if x0k is None else x0k.data_ptr(), x.data_ptr(), s.data_ptr())
+        else:
+            yk = np.ascontiguousarray(np.asarray(y, dtype=np.float32).reshape(self.m))
+            x0k = None if x0 is None else np.ascontiguousarray(np.asarray(x0, dtype=np.float64).reshape(self.n))
+            x = x_out if x_out is not None else np.empty(self.n, dtype=np.float64)
+            s = screened_out if screened_out is not None else np.empty(self.n, dtype=np.uint8)
+            ptrs = (yk.ctypes.data, None if x0k is None else x0k.ctypes.data, x.ctypes.data, s.ctypes.data)
+        st, info = bvls_solve(self.handle, ptrs[0], ptrs[1], opts, ptrs[2], ptrs[3])
+        if check and st not in (BVLS_OK, BVLS_EMAXITER):
+            raise BVLSError(st, bvls_last_error())
+        d = info.as_dict()
+        d["status"] = STATUS_NAMES.get(st, st)
+        d["dual"] = DUAL_NAMES.get(info.dual_mode, info.dual_mode)
+        return x, s, d, st

@@ -1,0 +1,115 @@
+"""ctypes binding of the C ABI declared in include/bvls_gb300.h (argument marshalling only).
+
+The functions keep the C names.  Pointers are passed as integers (device pointers from
+torch tensors, or host addresses from numpy arrays); the CUDA path does all the work.
+Loading fails loudly when the extension is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbvls_gb300.so")
+
+BVLS_OK, BVLS_EINVAL, BVLS_ENOMEM, BVLS_ECUDA, BVLS_EMAXITER, BVLS_ENONFINITE, BVLS_ENOTSUP = range(7)
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EMAXITER", 5: "ENONFINITE", 6: "ENOTSUP"}
+BVLS_PREC_FP32X2, BVLS_PREC_FP32 = 0, 1
+BVLS_DUAL_SCALING, BVLS_DUAL_TRANSLATION, BVLS_DUAL_ZERO = 0, 1, 2
+DUAL_NAMES = {0: "scaling", 1: "translation", 2: "zero"}
+
+# Every symbol the header declares; tests check that the library exports all of them.
+EXPORTED = ("bvls_default_opts", "bvls_setup", "bvls_solve", "bvls_destroy", "bvls_last_error")
+
+
+class bvls_opts(ctypes.Structure):
+    _fields_ = [
+        ("tol", ctypes.c_double),
+        ("screen_every", ctypes.c_int),
+        ("max_iter", ctypes.c_int),
+        ("screening", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("restart", ctypes.c_int),
+        ("lipschitz", ctypes.c_double),
+        ("profile", ctypes.c_int),
+    ]
+
+
+class bvls_info(ctypes.Structure):
+    _fields_ = [
+        ("iters", ctypes.c_int),
+        ("converged", ctypes.c_int),
+        ("n_preserved", ctypes.c_int),
+        ("dual_mode", ctypes.c_int),
+        ("gap_evals", ctypes.c_int),
+        ("gap", ctypes.c_double),
+        ("primal", ctypes.c_double),
+        ("radius", ctypes.c_double),
+        ("L", ctypes.c_double),
+        ("sum_preserved", ctypes.c_double),
+        ("sum_nonzero", ctypes.c_double),
+        ("fwd_ms", ctypes.c_double),
+        ("tr_ms", ctypes.c_double),
+        ("fwd_launches", ctypes.c_int),
+        ("tr_launches", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the extension (once).  Raises ImportError if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA extension not built: {path} is missing "
+                          "(run `python -c 'import __graft_entry__ as g; g.build()'`)")
+    lib = ctypes.CDLL(path)
+    vp, ci, cd = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.bvls_default_opts.argtypes = [ctypes.POINTER(bvls_opts)]
+    lib.bvls_default_opts.restype = None
+    lib.bvls_setup.argtypes = [vp, ci, ci, ci, vp, vp, vp, vp, ctypes.POINTER(vp)]
+    lib.bvls_setup.restype = ci
+    lib.bvls_solve.argtypes = [vp, vp, vp, ctypes.POINTER(bvls_opts), vp, vp, ctypes.POINTER(bvls_info)]
+    lib.bvls_solve.restype = ci
+    lib.bvls_destroy.argtypes = [vp]
+    lib.bvls_destroy.restype = None
+    lib.bvls_last_error.argtypes = []
+    lib.bvls_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def bvls_default_opts() -> bvls_opts:
+    o = bvls_opts()
+    load().bvls_default_opts(ctypes.byref(o))
+    return o
+
+
+def bvls_last_error() -> str:
+    return load().bvls_last_error().decode()
+
+
+def bvls_setup(A_ptr: int, m: int, n: int, lda: int, l_ptr: int | None, u_ptr: int | None,
+               t_ptr: int | None, stream: int | None) -> tuple[int, int | None]:
+    h = ctypes.c_void_p()
+    st = load().bvls_setup(A_ptr, m, n, lda, l_ptr, u_ptr, t_ptr, stream or 0, ctypes.byref(h))
+    return st, h.value
+
+
+def bvls_solve(h: int, y_ptr: int, x0_ptr: int | None, opts: bvls_opts | None, x_out_ptr: int,
+               screened_ptr: int | None) -> tuple[int, bvls_info]:
+    info = bvls_info()
+    st = load().bvls_solve(h, y_ptr, x0_ptr, ctypes.byref(opts) if opts is not None else None,
+                           x_out_ptr, screened_ptr, ctypes.byref(info))
+    return st, info
+
+
+def bvls_destroy(h: int | None) -> None:
+    if h:
+        load().bvls_destroy(h)

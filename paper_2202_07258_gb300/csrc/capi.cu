@@ -1,0 +1,541 @@
+// C ABI: handle management, setup and the solve loop (CUDA-graph chunks of iterations).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "bvls_gb300.h"
+#include "common.cuh"
+
+using namespace bvls;
+
+namespace {
+
+thread_local std::string g_err;
+
+bvls_status set_err(bvls_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return set_err(e_ == cudaErrorMemoryAllocation ? BVLS_ENOMEM : BVLS_ECUDA,         \
+                     "%s failed: %s (line %d)", #call, cudaGetErrorString(e_), __LINE__); \
+  } while (0)
+
+constexpr double kU = 5.9604644775390625e-08;   // 2^-24, unit roundoff of float32
+constexpr double kU64 = 1.1102230246251565e-16; // 2^-53
+
+struct GraphKey {
+  int K, screening, precision, restart, max_iter;
+  double tol, invL;
+  bool operator==(const GraphKey& o) const {
+    return K == o.K && screening == o.screening && precision == o.precision &&
+           restart == o.restart && max_iter == o.max_iter && tol == o.tol && invL == o.invL;
+  }
+};
+
+}  // namespace
+
+struct bvls_handle {
+  int m = 0, n = 0, lda = 0, m4 = 0, num_sms = 0;
+  cudaStream_t user = nullptr, s = nullptr;
+  cudaEvent_t ev_in = nullptr, poll[2] = {nullptr, nullptr};
+  float* A = nullptr;
+  double *l = nullptr, *u = nullptr, *nrm = nullptr, *w = nullptr, *t = nullptr;
+  uint8_t* jinf = nullptr;
+  double t_norm = 0.0, gamma_w = 0.0, L = 0.0;
+  int dual_mode = kScaling;
+  Buffers b{};
+  float* y_dev = nullptr;
+  double* x0_dev = nullptr;
+  int* pinned = nullptr;
+  int fwd_tiles = 0, fwd_chunks = 0, tr_blocks = 0, red_blocks = 0;
+  double Cg[2] = {0, 0}, Cf[2] = {0, 0}, Csub = 0.0;
+  bool have_graph = false;
+  GraphKey key{};
+  cudaGraphExec_t exec = nullptr;
+  int chunk_len = 0;
+  std::vector<cudaEvent_t> prof;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+template <typename T>
+bvls_status dalloc(bvls_handle* h, T** p, size_t count) {
+  void* q = nullptr;
+  CK(cudaMalloc(&q, count * sizeof(T) + 16));
+  h->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return BVLS_OK;
+}
+
+#define TRY(expr)                      \
+  do {                                 \
+    bvls_status st_ = (expr);          \
+    if (st_ != BVLS_OK) return st_;    \
+  } while (0)
+
+void free_handle(bvls_handle* h) {
+  if (!h) return;
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  for (auto e : h->prof) cudaEventDestroy(e);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->pinned) cudaFreeHost(h->pinned);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  for (auto e : h->poll)
+    if (e) cudaEventDestroy(e);
+  if (h->s) cudaStreamDestroy(h->s);
+  delete h;
+}
+
+// w = A^T t for a host direction t; returns whether a_j^T t < 0 (with its rounding bound)
+// on every nonzero column with u_j = +inf.
+bvls_status try_direction(bvls_handle* h, const std::vector<double>& t,
+                          const std::vector<uint8_t>& jinf, const std::vector<double>& nrm,
+                          bool* ok) {
+  CK(cudaMemcpyAsync(h->t, t.data(), sizeof(double) * h->m, cudaMemcpyHostToDevice, h->s));
+  CK(launch_col_dots(h->A, h->lda, h->m, h->n, h->t, h->w, h->s));
+  std::vector<double> w(h->n);
+  CK(cudaMemcpyAsync(w.data(), h->w, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  double tn = 0.0;
+  for (double v : t) tn += v * v;
+  tn = std::sqrt(tn);
+  const double gamma = 1.01 * (h->m + 8) * kU64;
+  *ok = true;
+  for (int j = 0; j < h->n; ++j) {
+    if (!jinf[j] || !(nrm[j] > 0.0)) continue;
+    if (!(w[j] + gamma * nrm[j] * tn < 0.0)) {
+      *ok = false;
+      break;
+    }
+  }
+  if (*ok) {
+    h->t_norm = tn;
+    h->gamma_w = gamma;
+  }
+  return BVLS_OK;
+}
+
+Params make_params(const bvls_handle* h, const bvls_opts& o, int max_iter) {
+  Params p{};
+  p.A = h->A;
+  p.m = h->m;
+  p.n = h->n;
+  p.lda = h->lda;
+  p.m4 = h->m4;
+  p.l = h->l;
+  p.u = h->u;
+  p.nrm = h->nrm;
+  p.w = h->w;
+  p.jinf = h->jinf;
+  const double L = o.lipschitz > 0.0 ? o.lipschitz : h->L;
+  p.invL = 1.0 / L;
+  p.t_norm = h->t_norm;
+  p.gamma_w = h->gamma_w;
+  p.Cg = h->Cg[o.precision];
+  p.Cf = h->Cf[o.precision];
+  p.Csub = h->Csub;
+  p.tol = o.tol;
+  p.max_iter = max_iter;
+  p.dual_mode = h->dual_mode;
+  p.screening = o.screening;
+  p.restart = o.restart;
+  p.fwd_chunks = h->fwd_chunks;
+  p.fwd_tiles = h->fwd_tiles;
+  return p;
+}
+
+// Enqueue chunk_len iterations (the chunk starts at an even k, so slot = j & 1).
+// With ev != nullptr, records ev[3j], ev[3j+1], ev[3j+2] around the two products.
+cudaError_t enqueue_chunk(bvls_handle* h, const Params& p, const bvls_opts& o, int chunk_len,
+                          cudaEvent_t* ev) {
+  const bool scr = o.screening && h->dual_mode != kZero;
+  cudaError_t e = cudaSuccess;
+  for (int j = 0; j < chunk_len && e == cudaSuccess; ++j) {
+    const int slot = j & 1;
+    const bool gap_iter = ((j + 1) % o.screen_every) == 0;
+    if (ev) cudaEventRecord(ev[3 * j], h->s);
+    e = launch_fwd(p, h->b, slot, o.precision, false, h->s);
+    if (e != cudaSuccess) break;
+    if (ev) cudaEventRecord(ev[3 * j + 1], h->s);
+    e = launch_tr(p, h->b, slot, o.precision, gap_iter, h->tr_blocks, h->s);
+    if (e != cudaSuccess) break;
+    if (ev) cudaEventRecord(ev[3 * j + 2], h->s);
+    if (gap_iter) {
+      e = launch_gap(p, h->b, slot, !scr, h->red_blocks, h->s);
+      if (e == cudaSuccess && scr) {
+        e = launch_test(p, h->b, slot, h->red_blocks, h->s);
+        if (e == cudaSuccess) e = launch_compact(p, h->b, slot, h->s);
+        if (e == cudaSuccess) e = launch_fwd(p, h->b, slot, o.precision, true, h->s);
+      }
+    }
+  }
+  return e;
+}
+
+int chunk_length(int K) {
+  int c = 1;
+  while (K * c < 16 || (K * c) % 2) ++c;
+  return K * c;
+}
+
+bvls_status validate_opts(const bvls_opts& o) {
+  if (!(o.tol >= 0.0) || o.screen_every < 1 || o.max_iter < 1 ||
+      (o.precision != BVLS_PREC_FP32X2 && o.precision != BVLS_PREC_FP32) ||
+      !(o.lipschitz >= 0.0) || !std::isfinite(o.lipschitz))
+    return set_err(BVLS_EINVAL, "invalid options (tol >= 0, screen_every >= 1, max_iter >= 1, "
+                                "precision 0/1, lipschitz >= 0 finite)");
+  return BVLS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void bvls_default_opts(bvls_opts* o) {
+  if (!o) return;
+  o->tol = 1e-6;
+  o->screen_every = 10;
+  o->max_iter = 100000;
+  o->screening = 1;
+  o->precision = BVLS_PREC_FP32X2;
+  o->restart = 1;
+  o->lipschitz = 0.0;
+  o->profile = 0;
+}
+
+const char* bvls_last_error(void) { return g_err.c_str(); }
+
+void bvls_destroy(bvls_handle* h) { free_handle(h); }
+
+static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const double* l,
+                              const double* u, const double* t) {
+  const int m = h->m, n = h->n;
+  // Host-side validation of the box.
+  std::vector<double> lv(n, 0.0), uv(n, INFINITY);
+  if (l) std::memcpy(lv.data(), l, sizeof(double) * n);
+  if (u) std::memcpy(uv.data(), u, sizeof(double) * n);
+  std::vector<uint8_t> jinf(n);
+  bool any_inf = false;
+  for (int j = 0; j < n; ++j) {
+    if (!std::isfinite(lv[j]) || std::isnan(uv[j]) || uv[j] == -INFINITY || lv[j] > uv[j])
+      return set_err(BVLS_EINVAL, "bound %d: need finite l_j <= u_j (u_j may be +inf)", j);
+    jinf[j] = std::isinf(uv[j]) ? 1 : 0;
+    any_inf |= jinf[j] != 0;
+  }
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
+  CK(cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&h->poll[0], cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&h->poll[1], cudaEventDisableTiming));
+  CK(cudaHostAlloc(reinterpret_cast<void**>(&h->pinned), 4 * sizeof(int), cudaHostAllocDefault));
+  CK(cudaEventRecord(h->ev_in, h->user));
+  CK(cudaStreamWaitEvent(h->s, h->ev_in, 0));
+
+  TRY(dalloc(h, &h->A, (size_t)h->lda * n));
+  CK(cudaMemsetAsync(h->A, 0, sizeof(float) * (size_t)h->lda * n, h->s));
+  CK(cudaMemcpy2DAsync(h->A, sizeof(float) * h->lda, A, sizeof(float) * lda, sizeof(float) * m, n,
+                       cudaMemcpyDefault, h->s));
+  int* flag = nullptr;
+  TRY(dalloc(h, &flag, 4));
+  CK(cudaMemsetAsync(flag, 0, sizeof(int), h->s));
+  CK(launch_check_finite(h->A, h->lda, m, n, flag, h->s));
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  if (bad) return set_err(BVLS_ENONFINITE, "A contains NaN or Inf");
+
+  TRY(dalloc(h, &h->l, n));
+  TRY(dalloc(h, &h->u, n));
+  TRY(dalloc(h, &h->nrm, n));
+  TRY(dalloc(h, &h->w, n));
+  TRY(dalloc(h, &h->jinf, n));
+  TRY(dalloc(h, &h->t, m));
+  CK(cudaMemcpyAsync(h->l, lv.data(), sizeof(double) * n, cudaMemcpyHostToDevice, h->s));
+  CK(cudaMemcpyAsync(h->u, uv.data(), sizeof(double) * n, cudaMemcpyHostToDevice, h->s));
+  CK(cudaMemcpyAsync(h->jinf, jinf.data(), n, cudaMemcpyHostToDevice, h->s));
+  CK(cudaMemsetAsync(h->w, 0, sizeof(double) * n, h->s));
+  CK(launch_col_norms(h->A, h->lda, m, n, h->nrm, h->s));
+  std::vector<double> nrm(n);
+  CK(cudaMemcpyAsync(nrm.data(), h->nrm, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+
+  // Dual point of Section 4.
+  if (!any_inf) {
+    h->dual_mode = kScaling;
+  } else if (t) {
+    std::vector<double> tv(t, t + m);
+    for (double v : tv)
+      if (!std::isfinite(v)) return set_err(BVLS_EINVAL, "t must be finite");
+    bool ok = false;
+    TRY(try_direction(h, tv, jinf, nrm, &ok));
+    if (!ok) return set_err(BVLS_EINVAL, "the given t is not an interior direction (a_j^T t < 0)");
+    h->dual_mode = kTranslation;
+  } else {
+    bool ok = false;
+    std::vector<double> tv(m, -1.0);  // Proposition 2, case 3
+    TRY(try_direction(h, tv, jinf, nrm, &ok));
+    if (!ok) {
+      double* rs = nullptr;
+      TRY(dalloc(h, &rs, m));
+      CK(launch_row_sums(h->A, h->lda, m, n, rs, h->s));
+      std::vector<double> s(m);
+      CK(cudaMemcpyAsync(s.data(), rs, sizeof(double) * m, cudaMemcpyDeviceToHost, h->s));
+      CK(cudaStreamSynchronize(h->s));
+      for (int i = 0; i < m; ++i) tv[i] = -s[i] / n;  // minus the mean column
+      TRY(try_direction(h, tv, jinf, nrm, &ok));
+      if (!ok) {
+        // minus the column most correlated with all others: argmax_j a_j^T sum_k a_k
+        TRY(try_direction(h, s, std::vector<uint8_t>(n, 0), nrm, &ok));  // w = A^T s
+        std::vector<double> corr(n);
+        CK(cudaMemcpyAsync(corr.data(), h->w, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
+        CK(cudaStreamSynchronize(h->s));
+        int jb = 0;
+        for (int j = 1; j < n; ++j)
+          if (corr[j] > corr[jb]) jb = j;
+        std::vector<float> col(m);
+        CK(cudaMemcpyAsync(col.data(), h->A + (size_t)jb * h->lda, sizeof(float) * m,
+                           cudaMemcpyDeviceToHost, h->s));
+        CK(cudaStreamSynchronize(h->s));
+        for (int i = 0; i < m; ++i) tv[i] = -(double)col[i];
+        TRY(try_direction(h, tv, jinf, nrm, &ok));
+      }
+    }
+    h->dual_mode = ok ? kTranslation : kZero;
+    if (!ok) {
+      h->t_norm = 0.0;
+      h->gamma_w = 0.0;
+    }
+  }
+
+  // Step constant: power iteration on A^T A (one unnormalised warm-up step is discarded).
+  {
+    float *v = nullptr, *q = nullptr, *v2 = nullptr;
+    double* scal = nullptr;
+    TRY(dalloc(h, &v, n));
+    TRY(dalloc(h, &v2, n));
+    TRY(dalloc(h, &q, m));
+    TRY(dalloc(h, &scal, 2));
+    CK(cudaMemsetAsync(scal, 0, 2 * sizeof(double), h->s));
+    CK(launch_power_init(v, n, h->s));
+    CK(launch_power_step(h->A, h->lda, m, n, v, q, v2, scal, h->s));
+    CK(cudaMemsetAsync(scal, 0, sizeof(double), h->s));
+    for (int it = 0; it < 100; ++it) CK(launch_power_step(h->A, h->lda, m, n, v, q, v2, scal, h->s));
+    double lam = 0.0;
+    CK(cudaMemcpyAsync(&lam, scal, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    h->L = lam > 0.0 ? 1.05 * lam : 1.0;
+  }
+
+  // Workspace of the solve loop and launch shapes.
+  h->fwd_tiles = (h->lda + kFwdRows - 1) / kFwdRows;
+  {
+    int chunks = (4 * h->num_sms + h->fwd_tiles - 1) / h->fwd_tiles;
+    chunks = std::max(1, std::min(chunks, std::max(1, (n + 7) / 8)));
+    h->fwd_chunks = std::min(chunks, 1024);
+  }
+  int bps = 1;
+  CK(tr_configure(h->m4, &bps));
+  h->tr_blocks = h->num_sms * std::max(1, std::min(bps, 2));
+  h->red_blocks = std::max(1, std::min(2 * h->num_sms, (n + kRedThreads - 1) / kRedThreads));
+  const int max_blocks = std::max(std::max(h->tr_blocks, h->red_blocks), 64);
+
+  Buffers& b = h->b;
+  TRY(dalloc(h, &b.x[0], n));
+  TRY(dalloc(h, &b.x[1], n));
+  TRY(dalloc(h, &b.g[0], n));
+  TRY(dalloc(h, &b.g[1], n));
+  TRY(dalloc(h, &b.idx, n));
+  TRY(dalloc(h, &b.idx_tmp, n));
+  TRY(dalloc(h, &b.fold, n));
+  TRY(dalloc(h, &b.flags, n));
+  TRY(dalloc(h, &b.yh, h->m4));
+  TRY(dalloc(h, &b.yl, h->m4));
+  TRY(dalloc(h, &b.rh, h->m4));
+  TRY(dalloc(h, &b.rl, h->m4));
+  TRY(dalloc(h, &b.part, (size_t)h->fwd_chunks * h->lda));
+  TRY(dalloc(h, &b.tileP, h->fwd_tiles));
+  TRY(dalloc(h, &b.tile_cnt, h->fwd_tiles));
+  TRY(dalloc(h, &b.blk, 4 * (size_t)max_blocks));
+  TRY(dalloc(h, &b.st, 1));
+  TRY(dalloc(h, &h->y_dev, h->m4));
+  TRY(dalloc(h, &h->x0_dev, n));
+  CK(cudaMemsetAsync(b.tile_cnt, 0, sizeof(unsigned) * h->fwd_tiles, h->s));
+  CK(cudaMemsetAsync(b.st, 0, sizeof(DevState), h->s));
+  CK(cudaMemsetAsync(h->y_dev, 0, sizeof(float) * h->m4, h->s));
+  b.y_in = h->y_dev;
+  b.x0_in = nullptr;
+
+  // Rounding constants of the double-float products (see the header of common.cuh): a
+  // tree of depth d of TwoSum steps is exact up to 2 (d+2)^2 u^2 sum |terms|.
+  {
+    const int m4q = h->m4 / 4;
+    const int d_g = (m4q + 31) / 32 + 7;
+    h->Cg[kX2] = 2.0 * (d_g + 2.0) * (d_g + 2.0) * kU * kU + 4.0 * kU * kU + 2.0 * kU64;
+    h->Cg[kF32] = 1.01 * (d_g + 2.0) * kU + kU;
+    const int per = (n + h->fwd_chunks - 1) / h->fwd_chunks;
+    const int d_f = ((per + kFwdWarps - 1) / kFwdWarps + 1) / 2 + 4 + h->fwd_chunks + 1;
+    h->Cf[kX2] = 2.0 * (d_f + 2.0) * (d_f + 2.0) * kU * kU + 2.0 * kU * kU;
+    h->Cf[kF32] = 1.01 * (d_f + 2.0) * kU + kU;
+    h->Csub = 8.0 * kU * kU;
+  }
+  CK(cudaStreamSynchronize(h->s));
+  return BVLS_OK;
+}
+
+bvls_status bvls_setup(const float* A, int m, int n, int lda, const double* l, const double* u,
+                       const double* t, void* stream, bvls_handle** out) {
+  if (!out) return set_err(BVLS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!A || m < 1 || n < 1 || lda < m) return set_err(BVLS_EINVAL, "need A != NULL, m >= 1, n >= 1, lda >= m");
+  if (m > kMaxRows) return set_err(BVLS_ENOTSUP, "m = %d exceeds %d", m, kMaxRows);
+  bvls_handle* h = new (std::nothrow) bvls_handle();
+  if (!h) return set_err(BVLS_ENOMEM, "host allocation failed");
+  h->m = m;
+  h->n = n;
+  h->lda = (m + 31) / 32 * 32;
+  h->m4 = (m + 3) / 4 * 4;
+  h->user = static_cast<cudaStream_t>(stream);
+  bvls_status st = setup_impl(h, A, lda, l, u, t);
+  if (st != BVLS_OK) {
+    free_handle(h);
+    return st;
+  }
+  g_err.clear();
+  *out = h;
+  return BVLS_OK;
+}
+
+bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const bvls_opts* opts,
+                       double* x_out, uint8_t* screened_out, bvls_info* info) {
+  if (!h || !y || !x_out) return set_err(BVLS_EINVAL, "handle, y and x_out are required");
+  bvls_opts o;
+  bvls_default_opts(&o);
+  if (opts) o = *opts;
+  TRY(validate_opts(o));
+  const int K = o.screen_every;
+  const int max_iter = (int)std::min<long long>((long long)(o.max_iter + K - 1) / K * K, 0x7fffffff);
+  const int chunk = chunk_length(K);
+  const Params p = make_params(h, o, max_iter);
+
+  CK(cudaEventRecord(h->ev_in, h->user));
+  CK(cudaStreamWaitEvent(h->s, h->ev_in, 0));
+  CK(cudaMemcpyAsync(h->y_dev, y, sizeof(float) * h->m, cudaMemcpyDefault, h->s));
+  h->b.x0_in = nullptr;
+  if (x0) {
+    CK(cudaMemcpyAsync(h->x0_dev, x0, sizeof(double) * h->n, cudaMemcpyDefault, h->s));
+    h->b.x0_in = h->x0_dev;
+  }
+  CK(launch_init(p, h->b, h->s));
+
+  const long long max_chunks = (max_iter + chunk - 1) / chunk + 1;
+  double fwd_ms = 0.0, tr_ms = 0.0;
+  int fwd_launches = 0, tr_launches = 0;
+  if (o.profile) {
+    if ((int)h->prof.size() < 3 * chunk) {
+      while ((int)h->prof.size() < 3 * chunk) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        h->prof.push_back(e);
+      }
+    }
+    int k_before = 0;
+    for (long long c = 0; c < max_chunks; ++c) {
+      CK(enqueue_chunk(h, p, o, chunk, h->prof.data()));
+      DevState hs;
+      CK(cudaMemcpyAsync(&hs, h->b.st, sizeof(DevState), cudaMemcpyDeviceToHost, h->s));
+      CK(cudaStreamSynchronize(h->s));
+      const int ran = std::min(chunk, hs.k - k_before);
+      for (int j = 0; j < ran; ++j) {
+        float a = 0.f, b2 = 0.f;
+        CK(cudaEventElapsedTime(&a, h->prof[3 * j], h->prof[3 * j + 1]));
+        CK(cudaEventElapsedTime(&b2, h->prof[3 * j + 1], h->prof[3 * j + 2]));
+        fwd_ms += a;
+        tr_ms += b2;
+      }
+      fwd_launches += ran;
+      tr_launches += ran;
+      k_before = hs.k;
+      if (hs.done) break;
+    }
+  } else {
+    GraphKey key{K, o.screening, o.precision, o.restart, max_iter, o.tol, p.invL};
+    if (!h->have_graph || !(h->key == key) || h->chunk_len != chunk) {
+      if (h->exec) {
+        cudaGraphExecDestroy(h->exec);
+        h->exec = nullptr;
+      }
+      h->have_graph = false;
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = enqueue_chunk(h, p, o, chunk, nullptr);
+      cudaError_t e2 = cudaStreamEndCapture(h->s, &g);
+      CK(e);
+      CK(e2);
+      e = cudaGraphInstantiate(&h->exec, g, 0);
+      cudaGraphDestroy(g);
+      CK(e);
+      h->have_graph = true;
+      h->key = key;
+      h->chunk_len = chunk;
+    }
+    // Keep one chunk queued behind the one whose stop flag is being read.
+    for (long long c = 0; c < max_chunks; ++c) {
+      CK(cudaGraphLaunch(h->exec, h->s));
+      CK(cudaMemcpyAsync(&h->pinned[c & 1], &h->b.st->done, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+      CK(cudaEventRecord(h->poll[c & 1], h->s));
+      if (c >= 1) {
+        CK(cudaEventSynchronize(h->poll[(c - 1) & 1]));
+        if (h->pinned[(c - 1) & 1]) break;
+      }
+    }
+  }
+  CK(cudaStreamSynchronize(h->s));
+  DevState hs;
+  CK(cudaMemcpy(&hs, h->b.st, sizeof(DevState), cudaMemcpyDeviceToHost));
+  if (hs.nonfinite) return set_err(BVLS_ENONFINITE, "y or x0 contains NaN or Inf");
+  CK(cudaMemcpyAsync(x_out, h->b.x[hs.out_slot], sizeof(double) * h->n, cudaMemcpyDefault, h->s));
+  if (screened_out)
+    CK(cudaMemcpyAsync(screened_out, h->b.flags, h->n, cudaMemcpyDefault, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->iters = hs.k;
+    info->converged = hs.converged;
+    info->n_preserved = hs.n_active;
+    info->dual_mode = h->dual_mode;
+    info->gap_evals = hs.gap_evals;
+    info->gap = hs.gap;
+    info->primal = hs.P;
+    info->radius = hs.radius;
+    info->L = 1.0 / p.invL;
+    info->sum_preserved = hs.sum_active;
+    info->sum_nonzero = hs.sum_nnz;
+    info->fwd_ms = fwd_ms;
+    info->tr_ms = tr_ms;
+    info->fwd_launches = fwd_launches;
+    info->tr_launches = tr_launches;
+  }
+  if (!hs.done) return set_err(BVLS_EMAXITER, "stopped after %d chunks without the stop flag", (int)max_chunks);
+  if (!hs.converged) return set_err(BVLS_EMAXITER, "gap %.3e >= tol after %d iterations", hs.gap, hs.k);
+  g_err.clear();
+  return BVLS_OK;
+}
+
+}  // extern "C"

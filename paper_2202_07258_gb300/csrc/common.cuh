@@ -1,0 +1,183 @@
+// Internal declarations shared by the CUDA translation units of the solver.
+//
+// Arithmetic conventions
+//   * A is float32, column-major, padded to lda_pad = roundup(m, 32) rows (pad rows are 0).
+//   * The iterate x, the correlations g = A^T r and every scalar of the screening step are
+//     float64.  float64 runs at a small fraction of the float32 rate on this part, so the
+//     two O(m |A|) products never use it: in the FP32X2 mode they multiply with error-free
+//     float32 products (fmaf) and accumulate in double-float pairs (hi, lo) with the
+//     TwoSum transformation, which carries about 48 significant bits.
+//   * Vectors of length m that feed the products (the folded data y' and the residual r)
+//     are stored as two float32 arrays, hi and lo; their value is defined as hi + lo.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bvls {
+
+constexpr int kFwdRows = 128;     // rows per block of the A_S x_S kernel (32 lanes x float4)
+constexpr int kFwdWarps = 4;      // column groups per block of that kernel
+constexpr int kFwdThreads = kFwdRows / 4 * kFwdWarps;
+constexpr int kFwdStage = 256;    // columns staged in shared memory at a time
+constexpr int kTrWarps = 16;      // warps per block of the A_S^T r kernel
+constexpr int kTrThreads = kTrWarps * 32;
+constexpr int kRedThreads = 256;  // blocks of the O(|A|) epilogue kernels
+constexpr int kCompactThreads = 1024;
+constexpr int kMaxRows = 24576;   // r is staged in shared memory: 8 bytes per row
+
+enum DualMode { kScaling = 0, kTranslation = 1, kZero = 2 };
+enum Precision { kX2 = 0, kF32 = 1 };
+
+// Scalars of one solve, in device memory.  Written by the last block of a kernel (the
+// others signal completion through the counters) and read by the next kernel.
+struct DevState {
+  int k;              // iterations completed
+  int done;           // 1: stop; every kernel returns at entry
+  int stop;           // set by the gap kernel, turned into done after the screening step
+  int converged;
+  int n_active;       // |preserved set|
+  int n_pins;         // coordinates fixed by the current screening step
+  int n_fold;         // of which with a nonzero bound value (their columns are folded into y')
+  int restart_pin;    // a coordinate was fixed while off its bound: restart the momentum
+  int out_slot;       // which x buffer holds the returned iterate
+  int gap_evals;
+  int nonfinite;
+  int pad0;
+  double t;           // FISTA momentum parameter t_k
+  double P;           // 1/2 ||r||^2 of the last A_S x_S pass (r = rh + rl)
+  double eps;         // translation step of the last evaluation
+  double gap;         // gap upper bound of the last evaluation
+  double radius;      // sqrt(2 gap)
+  double eta;         // per-unit-norm rounding margin of a_j^T theta
+  double E_fold;      // bound on || y' (stored) - y' (exact) ||_2
+  double S_fold;      // sum over folded columns of |b_j| ||a_j||
+  double y_norm;      // ||y||_2
+  double sum_active;  // sum of |preserved set| over the A_S^T r passes
+  double sum_nnz;     // sum of nonzero preserved x_j over the A_S x_S passes
+  unsigned int cnt_tr, cnt_gap, cnt_fwd, cnt_fold;
+};
+
+// Per-solve constants passed by value to the kernels.
+struct Params {
+  const float* A;          // padded copy, column-major
+  int m, n, lda;           // lda = padded rows
+  int m4;                  // m rounded up to a multiple of 4
+  const double* l;         // lower bounds
+  const double* u;         // upper bounds (+inf allowed)
+  const double* nrm;       // ||a_j||_2
+  const double* w;         // a_j^T t (translation mode)
+  const uint8_t* jinf;     // 1 if u_j = +inf
+  double invL;             // 1 / L
+  double t_norm;           // ||t||_2
+  double gamma_w;          // |w_j (stored) - a_j^T t| <= gamma_w ||a_j|| ||t||
+  double Cg;               // |g (computed) - a_j^T r| <= Cg ||a_j|| ||r||
+  double Cf;               // |q (computed) - A_S x_S| <= Cf sum |x_j| ||a_j|| (per row, in 2-norm)
+  double Csub;             // rounding of y' - q and of a fold, relative
+  double tol;
+  int max_iter;
+  int dual_mode;
+  int screening;
+  int restart;
+  int fwd_chunks;          // grid.y of the A_S x_S kernel
+  int fwd_tiles;           // grid.x of the A_S x_S kernel
+};
+
+// ---------------------------------------------------------------- double-float helpers
+// Error-free transformations (Knuth's TwoSum, FMA-based TwoProd).  Kept as separate
+// statements; nvcc does not reassociate floating-point additions.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  // requires |a| >= |b| or a == 0
+  s = a + b;
+  e = b - (s - a);
+}
+
+// (s, c) += a * (xh + xl): exact product of a*xh, rounded a*xl, TwoSum into s, error into c.
+__device__ __forceinline__ void df_fma(float& s, float& c, float a, float xh, float xl) {
+  float p = a * xh;
+  float e = fmaf(a, xh, -p);
+  e = fmaf(a, xl, e);
+  float t, err;
+  two_sum(s, p, t, err);
+  s = t;
+  c += err + e;
+}
+
+// (s, c) += (s2, c2)
+__device__ __forceinline__ void df_add(float& s, float& c, float s2, float c2) {
+  float t, err;
+  two_sum(s, s2, t, err);
+  s = t;
+  c += err + c2;
+}
+
+__device__ __forceinline__ double df_to_double(float s, float c) {
+  return (double)s + (double)c;
+}
+
+__device__ __forceinline__ void split_double(double x, float& h, float& l) {
+  h = (float)x;
+  l = (float)(x - (double)h);
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_max_d(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// ---------------------------------------------------------------- launch wrappers
+// Iteration kernels (iter_kernels.cu).
+struct Buffers {
+  double* x[2];
+  double* g[2];
+  int* idx;
+  int* idx_tmp;
+  int* fold;
+  uint8_t* flags;
+  float* yh;
+  float* yl;
+  float* rh;
+  float* rl;
+  float2* part;
+  double* tileP;
+  unsigned int* tile_cnt;
+  double* blk;            // per-block partials of the epilogue kernels (4 doubles each)
+  DevState* st;
+  const float* y_in;      // device copy of y
+  const double* x0_in;    // device copy of x0 or null
+};
+
+cudaError_t launch_init(const Params& p, const Buffers& b, cudaStream_t s);
+cudaError_t launch_fwd(const Params& p, const Buffers& b, int slot, int precision, bool fold,
+                       cudaStream_t s);
+cudaError_t launch_tr(const Params& p, const Buffers& b, int slot, int precision, bool gap_iter,
+                      int tr_blocks, cudaStream_t s);
+cudaError_t launch_gap(const Params& p, const Buffers& b, int slot, bool finalize, int red_blocks,
+                       cudaStream_t s);
+cudaError_t launch_test(const Params& p, const Buffers& b, int slot, int red_blocks, cudaStream_t s);
+cudaError_t launch_compact(const Params& p, const Buffers& b, int slot, cudaStream_t s);
+size_t tr_smem_bytes(int m4);
+cudaError_t tr_configure(int m4, int* blocks_per_sm);
+
+// Setup kernels (setup_kernels.cu).
+cudaError_t launch_check_finite(const float* A, int lda, int m, int n, int* flag, cudaStream_t s);
+cudaError_t launch_col_norms(const float* A, int lda, int m, int n, double* nrm, cudaStream_t s);
+cudaError_t launch_col_dots(const float* A, int lda, int m, int n, const double* t, double* w,
+                            cudaStream_t s);
+cudaError_t launch_row_sums(const float* A, int lda, int m, int n, double* out, cudaStream_t s);
+cudaError_t launch_power_step(const float* A, int lda, int m, int n, float* v, float* q, float* v2,
+                              double* scal, cudaStream_t s);
+cudaError_t launch_power_init(float* v, int n, cudaStream_t s);
+
+}  // namespace bvls

@@ -1,0 +1,232 @@
+"""GPU parity of the single-instance solver against the FP64 oracle (through the C ABI).
+
+Two kinds of comparison:
+  * trajectory parity -- both sides run exactly N iterations (tol = 0) from the same point
+    with the same step constant; the iterates must agree element by element;
+  * result parity -- both converge to the gap tolerance; the GPU's certified gap, its
+    objective, its solution and its screened set are checked against the oracle and
+    against an FP64 optimum certified by the optimality conditions of Section 3.2.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2202_07258_gb300 as pkg
+    return pkg
+
+
+def _f64(p):
+    return p.A.astype(np.float64), p.y.astype(np.float64).reshape(-1)
+
+
+def _L(A64):
+    return 1.05 * float(np.linalg.norm(A64, 2) ** 2)
+
+
+def gpu_solve(P, p, t=None, x0=None, **kw):
+    dev = torch.device("cuda:0")
+    s = P.Solver(torch.from_numpy(np.ascontiguousarray(p.A)).to(dev), p.l, p.u, t=t)
+    y = torch.from_numpy(np.ascontiguousarray(p.y.reshape(-1))).to(dev)
+    x0t = None if x0 is None else torch.from_numpy(np.asarray(x0, np.float64)).to(dev)
+    x, scr, info, st = s.solve(y, x0t, **kw)
+    torch.cuda.synchronize()
+    s.close()
+    return x.cpu().numpy(), scr.cpu().numpy(), info, st
+
+
+def certified_optimum(A, y, l, u, x_guess):
+    """Polish x_guess in FP64 and verify the optimality conditions (Eq. (optimality2))."""
+    xs = O.polish(A, y, x_guess, l, u, tau=1e-7)
+    assert np.all(xs >= l - 1e-12) and np.all(xs <= u + 1e-12)
+    assert O.kkt_residual(A, y, xs, l, u) < 1e-9 * (1 + np.abs(A.T @ y).max())
+    return xs
+
+
+def mixed_problem(seed=3, m=180, n=140):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((m, n))
+    x = rng.uniform(-1.5, 1.5, n)
+    y = A @ x + 0.5 * rng.standard_normal(m)
+    h = n // 2
+    l = np.concatenate([np.zeros(h), np.full(n - h, -1.0)])
+    u = np.concatenate([np.full(h, np.inf), np.full(n - h, 1.0)])
+    return W.Problem("mixed", A.astype(np.float32), y.astype(np.float32), l, u, x, {})
+
+
+def mixed_direction(p):
+    """A_inf^T t = -1 by least squares (Proposition 2, case 1), computed here in numpy."""
+    A64 = p.A.astype(np.float64)
+    cols = ~np.isfinite(p.u)
+    return np.linalg.lstsq(A64[:, cols].T, -np.ones(cols.sum()), rcond=None)[0]
+
+
+CASES = {
+    "nnls_abs_300x700": lambda: (W.nnls_abs_gaussian(300, 700, 0.05, 1.0, 1), None),
+    "bvls_t2_200x500": lambda: (W.bvls_table2(200, 500, 2), None),
+    "mixed_180x140": lambda: (lambda p: (p, mixed_direction(p)))(mixed_problem()),
+    "nnls_gauss_100x200": lambda: (W.nnls_gaussian(100, 200, 0.1, 0.01, 0), None),
+    "bvls_dir_224x512": lambda: (W.bvls_dirichlet_shared(224, 512, 1, 8, 0.005, 0), None),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_trajectory_matches_oracle(P, name):
+    p, t = CASES[name]()
+    A, y = _f64(p)
+    L = _L(A)
+    N = 300
+    ref = O.solve(A, y, p.l, p.u, tol=0.0, screen_every=10, max_iter=N, L=L, t=t)
+    x, scr, info, st = gpu_solve(P, p, t=t, tol=0.0, screen_every=10, max_iter=N, lipschitz=L)
+    assert st == P.BVLS_EMAXITER and info["iters"] == N == ref.iters
+    assert info["dual"] == ref.dual_mode
+    scale = max(1.0, float(np.abs(ref.x).max()))
+    err = float(np.abs(x - ref.x).max())
+    assert err <= 1e-9 * scale, (name, err)
+    # The GPU test carries wider rounding margins, so it may fix slightly fewer coordinates.
+    gpu_fixed, ref_fixed = scr > 0, ref.screened > 0
+    assert np.all(ref_fixed[gpu_fixed] | (np.abs(x[gpu_fixed] - ref.x[gpu_fixed]) == 0))
+    assert gpu_fixed.sum() >= 0.97 * ref_fixed.sum() - 2, (gpu_fixed.sum(), ref_fixed.sum())
+
+
+@pytest.mark.parametrize("name", ["nnls_abs_300x700", "bvls_t2_200x500", "mixed_180x140", "bvls_dir_224x512"])
+def test_result_matches_oracle_and_screens_safely(P, name):
+    p, t = CASES[name]()
+    A, y = _f64(p)
+    L = _L(A)
+    tol = 1e-9
+    ref = O.solve(A, y, p.l, p.u, tol=tol, screen_every=10, L=L, t=t)
+    assert ref.converged
+    x, scr, info, st = gpu_solve(P, p, t=t, tol=tol, screen_every=10, lipschitz=L)
+    assert st == P.BVLS_OK and info["converged"] and info["gap"] < tol
+    assert abs(info["iters"] - ref.iters) <= 20, (info["iters"], ref.iters)
+    xs = certified_optimum(A, y, p.l, p.u, ref.x)
+    th = y - A @ xs
+    g = A.T @ th
+    low, upp = scr == 1, scr == 2
+    # zero false screens: fixed coordinates sit at their bound in the certified optimum and
+    # a_j^T theta* has the fixed sign (Eq. (screen_cond)).
+    assert np.all(np.abs(xs[low] - p.l[low]) <= 1e-12) and np.all(g[low] < 0), name
+    assert np.all(np.abs(xs[upp] - p.u[upp]) <= 1e-12) and np.all(g[upp] > 0), name
+    assert np.all(x[low] == p.l[low]) and np.all(x[upp] == p.u[upp])
+    Pg = O.primal_objective(A, y, x)
+    Ps = O.primal_objective(A, y, xs)
+    assert Ps - 1e-12 <= Pg <= Ps + tol * 1.0001 + 1e-12
+    assert float(np.abs(x - xs).max()) <= 1e-5 * max(1.0, float(np.abs(xs).max()))
+
+
+def test_screened_and_unscreened_follow_the_same_iterates(P):
+    p = W.nnls_abs_gaussian(400, 1500, 0.05, 1.0, 4)
+    A, y = _f64(p)
+    L = _L(A)
+    a = gpu_solve(P, p, tol=1e-8, lipschitz=L)
+    b = gpu_solve(P, p, tol=1e-8, lipschitz=L, screening=False)
+    assert a[2]["converged"] and b[2]["converged"]
+    assert abs(a[2]["iters"] - b[2]["iters"]) <= 10
+    assert (a[1] > 0).sum() > 0.5 * p.n and (b[1] > 0).sum() == 0
+    assert a[2]["sum_preserved"] < 0.8 * b[2]["sum_preserved"]
+    assert float(np.abs(a[0] - b[0]).max()) < 1e-6
+
+
+def test_fp32_precision_mode(P):
+    p = W.bvls_table2(200, 500, 5)
+    A, y = _f64(p)
+    L = _L(A)
+    ref = O.solve(A, y, p.l, p.u, tol=1e-9, screen_every=10, L=L)
+    xs = certified_optimum(A, y, p.l, p.u, ref.x)
+    x, scr, info, st = gpu_solve(P, p, tol=1e-4, lipschitz=L, precision="fp32")
+    assert info["converged"]
+    g = A.T @ (y - A @ xs)
+    assert np.all(g[scr == 1] < 0) and np.all(g[scr == 2] > 0)
+    assert O.primal_objective(A, y, x) <= O.primal_objective(A, y, xs) + 1e-4
+
+
+def test_single_column_closed_form(P):
+    rng = np.random.default_rng(0)
+    for lo, hi in [(0.0, np.inf), (-0.3, 0.4), (0.0, 1.0)]:
+        a = rng.standard_normal((37, 1))
+        yv = rng.standard_normal(37) * 2
+        p = W.Problem("one", a.astype(np.float32), yv.astype(np.float32), np.array([lo]), np.array([hi]), None)
+        A, y = _f64(p)
+        exact = np.clip(A[:, 0] @ y / (A[:, 0] @ A[:, 0]), lo, hi)
+        x, scr, info, st = gpu_solve(P, p, tol=1e-12, screen_every=1, max_iter=2000)
+        assert abs(x[0] - exact) <= 1e-7 * max(1.0, abs(exact)), (x, exact)
+
+
+def test_single_row_and_odd_screen_period(P):
+    p = W.bvls_gaussian_box(1, 9, 0.5, 0)
+    A, y = _f64(p)
+    xb, Pb = O.brute_force(A, y, p.l, p.u)
+    x, scr, info, st = gpu_solve(P, p, tol=1e-12, screen_every=3, max_iter=30000)
+    assert info["converged"] and abs(O.primal_objective(A, y, x) - Pb) < 1e-9
+
+
+def test_zero_column_is_never_screened(P):
+    p = W.nnls_abs_gaussian(64, 90, 0.1, 1.0, 6)
+    A = p.A.copy()
+    A[:, 5] = 0.0
+    p = W.Problem("zc", A, p.y, p.l, p.u, None)
+    x, scr, info, st = gpu_solve(P, p, tol=1e-8)
+    assert info["converged"] and scr[5] == 0 and x[5] == 0.0
+
+
+def test_warm_start_and_status_codes(P):
+    p = W.bvls_table2(120, 260, 8)
+    A, y = _f64(p)
+    ref = O.solve(A, y, p.l, p.u, tol=1e-10, screen_every=10)
+    x, scr, info, st = gpu_solve(P, p, x0=ref.x, tol=1e-8)
+    assert st == P.BVLS_OK and info["iters"] <= 20
+    x, scr, info, st = gpu_solve(P, p, tol=1e-30, max_iter=25)
+    assert st == P.BVLS_EMAXITER and info["iters"] == 30 and not info["converged"]
+    bad = W.Problem("nan", p.A, p.y.copy(), p.l, p.u, None)
+    bad.y[3] = np.nan
+    x, scr, info, st = gpu_solve(P, bad, check=False)
+    assert st == P.BVLS_ENONFINITE
+    with pytest.raises(P.BVLSError):
+        P.Solver(torch.zeros(4, 3, device="cuda"), l=[0, 0, 1], u=[1, 1, 0])
+
+
+def test_degenerate_single_instance_full_size(P):
+    """The 2000 x 10000 Gaussian NNLS workload: no interior dual direction, nothing screens."""
+    p = W.nnls_gaussian(2000, 10000, 0.05, 0.01, 0)
+    A, y = _f64(p)
+    assert O.choose_translation(A, p.u) is None
+    x, scr, info, st = gpu_solve(P, p, tol=1e-6)
+    assert st == P.BVLS_OK and info["dual"] == "zero" and (scr > 0).sum() == 0
+    assert np.all(x >= 0)
+    Pval = O.primal_objective(A, y, x)
+    assert Pval <= info["gap"] * (1 + 1e-9) and info["gap"] < 1e-6      # Gap(x, 0) = P(x)
+    b = gpu_solve(P, p, tol=1e-6, screening=False)
+    assert b[2]["iters"] == info["iters"]
+
+
+def test_screenable_single_instance_full_size(P):
+    """2000 x 10000 |N(0,1)| NNLS (Table 1 family): certified gap and safe screens at full size."""
+    p = W.nnls_abs_gaussian(2000, 10000, 0.05, 1.0, 0)
+    A, y = _f64(p)
+    x, scr, info, st = gpu_solve(P, p, tol=1e-6)
+    assert st == P.BVLS_OK and info["dual"] == "translation"
+    assert np.all(x >= 0) and np.all(x[scr == 1] == 0)
+    t = -np.ones(p.m)
+    cols = ~np.isfinite(p.u)
+    r = y - A @ x
+    th, eps = O.translate(A, r, t, cols)
+    gap = O.duality_gap(A, y, x, th, p.l, p.u)
+    assert gap <= 1e-6 * 1.01 + 1e-9, gap
+    g = A.T @ th
+    rad = O.safe_radius(gap)
+    # at the final dual point every fixed column is still strictly on its side of 0
+    assert np.all(g[scr == 1] < 0)
+    assert (scr > 0).sum() > 0.5 * p.n
+    assert np.sum(g[scr == 1] >= -rad * np.linalg.norm(A[:, scr == 1], axis=0)) < 0.05 * (scr > 0).sum()
