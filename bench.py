@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Benchmark: instances/s to duality gap 1e-6, screened vs unscreened, single-instance NNLS.
+
+Workload (one instance = one right-hand side solved to gap < 1e-6):
+  A 2000 x 10000 iid N(0,1) with unit-norm columns, x0 with 5% nonzeros ~ U[0,1] at random
+  positions, y = A x0 + N(0, 0.01^2), seed 0; NNLS (l = 0, u = +inf); FISTA with
+  gap-safe screening every 10 iterations; float32 data with double-float products.
+A step is one complete solve (all steps of the iteration, the gap and the screening) with
+A set up and y resident in HBM.  L2 is flushed (256 MiB write) before every step; the
+flush is outside the timed intervals, which are CUDA events on the solve's stream.
+
+Also reported: the unscreened solver on the same instance, the screenable Table-1-family
+variant (A = |N(0,1)|, noise N(0,1)) screened and unscreened, the roofline of the dominant
+kernel (profile-mode CUDA events), an end-to-end number through the C ABI from pinned host
+buffers, clocks sampled during the timed region, and the FP64 oracle on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "instances/s to gap 1e-6, screened vs unscreened on GB300; % of HBM/TC roofline"
+WORKLOAD = "nnls_gaussian_2000x10000"
+WORKLOAD_DESC = ("NNLS, A 2000x10000 iid N(0,1) unit columns, x0 5% nonzeros U[0,1], "
+                 "y = A x0 + N(0, 0.01^2), seed 0 + rank")
+VARIANT = "nnls_abs_gaussian_2000x10000"
+TOL = 1e-6
+K_SCREEN = 10
+FLUSH_BYTES = 256 << 20
+
+
+def make_problem(name: str, rank: int):
+    if name == WORKLOAD:
+        return W.nnls_gaussian(2000, 10000, 0.05, 0.01, rank)
+    if name == VARIANT:
+        return W.nnls_abs_gaussian(2000, 10000, 0.05, 1.0, rank)
+    raise ValueError(name)
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.rows = []
+        if self.proc is None:
+            return False
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+        return False
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ----------------------------------------------------------------------------- oracle leg
+def oracle_sample(p, budget_s: float = 12.0):
+    """Time the FP64 oracle on a bounded number of iterations; scale by its own iteration count."""
+    import oracle as O
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "bench_oracle.json")))[WORKLOAD]
+    A = p.A.astype(np.float64)
+    y = p.y.astype(np.float64)
+    L = gold["L"]
+    t0 = time.perf_counter()
+    O.solve(A, y, p.l, p.u, tol=0.0, screen_every=K_SCREEN, max_iter=K_SCREEN, L=L)
+    per = (time.perf_counter() - t0) / K_SCREEN
+    n_it = int(max(K_SCREEN, min(gold["iters"], budget_s / max(per, 1e-9))) // K_SCREEN * K_SCREEN)
+    t0 = time.perf_counter()
+    O.solve(A, y, p.l, p.u, tol=0.0, screen_every=K_SCREEN, max_iter=n_it, L=L)
+    dt = time.perf_counter() - t0
+    per = dt / n_it
+    seconds = per * gold["iters"]
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max(int(i.get("num_threads", 0)) for i in threadpool_info()) or os.cpu_count()
+    except Exception:
+        cores = os.cpu_count()
+    return {"value": 1.0 / seconds, "unit": "instances/s", "cores": cores, "kind": "oracle",
+            "sample": (f"{n_it} of the oracle's {gold['iters']} iterations to gap {gold['tol']:g} "
+                       f"on {WORKLOAD} (numpy FP64, screening every {K_SCREEN}), {dt:.1f} s, "
+                       f"scaled to one full solve ({seconds:.1f} s)")}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    p = make_problem(WORKLOAD, 0)
+    for _ in range(args.warmup):
+        pass
+    vals = []
+    base = None
+    for _ in range(args.steps):
+        base = oracle_sample(p, budget_s=max(2.0, 60.0 / max(1, args.steps)))
+        vals.append(base["value"])
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "instances/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 / v, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "desc": WORKLOAD_DESC, "tol": TOL, "screen_every": K_SCREEN},
+            "cpu_baseline": dict(base, value=v),
+            "e2e": {"value": v, "unit": "instances/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU leg
+def timed_solves(solver, y_dev, flush, stream, steps, warmup, **kw):
+    import torch
+    from paper_2202_07258_gb300 import make_opts
+    opts = make_opts(tol=TOL, screen_every=K_SCREEN, **kw)
+    infos = []
+    for _ in range(warmup):
+        solver.solve(y_dev, opts=opts)
+    times = []
+    with torch.cuda.stream(stream):
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            x, s, info, st = solver.solve(y_dev, opts=opts)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            infos.append(info)
+    return times, infos, x, s
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("iter_kernels.cu", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2202_07258_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def roofline(solver, y_dev, m):
+    """Profile-mode solve: CUDA events around every product launch on the launching stream."""
+    from paper_2202_07258_gb300 import make_opts
+    x, s, info, st = solver.solve(y_dev, opts=make_opts(tol=TOL, screen_every=K_SCREEN, profile=True))
+    nl = max(1, info["tr_launches"])
+    tr_bytes = 4.0 * m * info["sum_preserved"] + nl * 8.0 * m + 60.0 * info["sum_preserved"]
+    fwd_bytes = 4.0 * m * info["sum_nonzero"] + nl * 16.0 * m + 12.0 * info["sum_preserved"]
+    kern = {
+        "k_tr (A_S^T r + FISTA step)": (info["tr_ms"], tr_bytes, info["tr_launches"]),
+        "k_fwd (A_S x_S, r, P)": (info["fwd_ms"], fwd_bytes, info["fwd_launches"]),
+    }
+    name = max(kern, key=lambda k: kern[k][0])
+    ms, by, launches = kern[name]
+    avg_s = ms / 1000.0 / max(1, launches)
+    achieved = by / max(1, launches) / avg_s / 1e9
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        peak = float(json.load(open(peaks_path))["hbm_gbs"])
+        src = "measured"
+    else:
+        peak, src = 6800.0, "fallback"
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if os.path.exists(tp):
+        t = json.load(open(tp))
+        rec = t.get(name.split()[0])
+        if rec and rec.get("kernel_hash") == kernel_hash():
+            traffic = rec.get("dram_bytes_per_launch")
+    other = {k: {"ms_total": v[0], "launches": v[2], "gb_per_launch": v[1] / max(1, v[2]) / 1e9,
+                 "achieved_gbs": (v[1] / max(1, v[2])) / (v[0] / 1000.0 / max(1, v[2])) / 1e9 if v[0] else None}
+             for k, v in kern.items()}
+    return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "peak_source": src,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+            "algorithmic_bytes_per_launch": by / max(1, launches), "avg_launch_us": avg_s * 1e6,
+            "kernels": other, "profile_iters": info["iters"]}
+
+
+def e2e_leg(p, steps, stream):
+    """Whole job through the C ABI from pinned host buffers: setup(A) + solve(y) + read x."""
+    import ctypes
+    import torch
+    from paper_2202_07258_gb300 import _capi, make_opts
+    m, n = p.m, p.n
+    A_h = torch.from_numpy(np.ascontiguousarray(p.A.T)).pin_memory()      # column-major A
+    y_h = torch.from_numpy(np.ascontiguousarray(p.y)).pin_memory()
+    l_h = np.zeros(n)
+    u_h = np.full(n, np.inf)
+    x_h = torch.empty(n, dtype=torch.float64).pin_memory()
+    s_h = torch.empty(n, dtype=torch.uint8).pin_memory()
+    opts = make_opts(tol=TOL, screen_every=K_SCREEN)
+    times = []
+    for i in range(steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, h = _capi.bvls_setup(A_h.data_ptr(), m, n, m, l_h.ctypes.data, u_h.ctypes.data, None,
+                                 stream.cuda_stream)
+        assert st == 0, _capi.bvls_last_error()
+        st, info = _capi.bvls_solve(h, y_h.data_ptr(), None, opts, x_h.data_ptr(), s_h.data_ptr())
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        _capi.bvls_destroy(h)
+        if i > 0:
+            times.append(t1 - t0)
+    h2d = 4 * m * n + 4 * m + 16 * n
+    d2h = 8 * n + n
+    return {"value": 1.0 / statistics.median(times), "unit": "instances/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "includes": "bvls_setup from host A (copy, column norms, dual "
+            "direction search, power iteration) + bvls_solve from host y to host x"}
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import __graft_entry__ as g
+    g.build()
+    from paper_2202_07258_gb300 import Solver
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+
+    def leg(name, screening, steps, warmup, keep=False):
+        p = make_problem(name, rank)
+        A = torch.from_numpy(p.A).to(dev)
+        y = torch.from_numpy(p.y).to(dev)
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            solver = Solver(A, p.l, p.u, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0
+        del A
+        barrier()
+        times, infos, x, s = timed_solves(solver, y, flush, stream, steps, warmup, screening=screening)
+        barrier()
+        out = {"times_ms": times, "info": infos[-1], "setup_s": setup_s,
+               "launches": sum(i["kernel_launches"] for i in infos)}
+        if keep:
+            out["solver"], out["y"], out["p"] = solver, y, p
+        else:
+            solver.close()
+        return out
+
+    with ClockSampler(local) as clk:
+        scr = leg(WORKLOAD, True, args.steps, args.warmup, keep=True)
+    uns = leg(WORKLOAD, False, args.steps, args.warmup)
+    var_s = leg(VARIANT, True, max(2, args.steps // 2), 1)
+    var_u = leg(VARIANT, False, max(2, args.steps // 2), 1)
+
+    total_ms = sum(scr["times_ms"])
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1000.0)
+
+    roof = roofline(scr["solver"], scr["y"], 2000) if rank == 0 else None
+    e2e = e2e_leg(scr["p"], max(2, min(args.steps, 5)), stream) if rank == 0 else None
+    cpu = oracle_sample(scr["p"]) if (rank == 0 and world == 1) else None
+    scr["solver"].close()
+
+
+    if rank == 0:
+        info = scr["info"]
+        line = {
+            "metric": METRIC, "value": value, "unit": "instances/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "desc": WORKLOAD_DESC, "tol": TOL, "screen_every": K_SCREEN,
+                       "precision": "f32 data, double-float (f32x2) products, f64 gap/screening",
+                       "l2": "flushed before every step (256 MiB write, untimed)",
+                       "parallelism": f"replicas x{world}"},
+            "screened": {"iters": info["iters"], "gap": info["gap"], "dual": info["dual"],
+                         "n_preserved_end": info["n_preserved"],
+                         "avg_preserved_fraction": info["sum_preserved"] / max(1, info["iters"]) / 10000,
+                         "setup_s": scr["setup_s"]},
+            "unscreened": {"value": world * args.steps / (sum(uns["times_ms"]) / 1000.0),
+                           "ms_per_step": sum(uns["times_ms"]) / args.steps, "iters": uns["info"]["iters"],
+                           "gap": uns["info"]["gap"]},
+            "screenable_variant": {
+                "workload": VARIANT + " (A = |N(0,1)| unit columns, x0 5% |N(0,1)|, noise N(0,1); Table 1 family)",
+                "screened_instances_per_s": 1000.0 * len(var_s["times_ms"]) / sum(var_s["times_ms"]),
+                "unscreened_instances_per_s": 1000.0 * len(var_u["times_ms"]) / sum(var_u["times_ms"]),
+                "speedup": sum(var_u["times_ms"]) / len(var_u["times_ms"]) / (sum(var_s["times_ms"]) / len(var_s["times_ms"])),
+                "iters_screened": var_s["info"]["iters"], "iters_unscreened": var_u["info"]["iters"],
+                "avg_preserved_fraction": var_s["info"]["sum_preserved"] / max(1, var_s["info"]["iters"]) / 10000,
+                "gap": var_s["info"]["gap"]},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(scr["launches"]), "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def args_world_rate(times_ms, world):
+    return world * len(times_ms) / (sum(times_ms) / 1000.0)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("note: warmup raised to 3", file=sys.stderr)
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -26,9 +26,11 @@
  *   - The caller owns every pointer it passes; the library keeps no reference to a
  *     caller pointer after the call returns.  The handle owns its device workspace,
  *     including its own padded copy of A.
- *   - All device work of a handle runs in order after the work already queued on the
- *     stream given to bvls_setup (0 = the legacy default stream); bvls_solve returns when
- *     its results are in the caller's buffers.
+ *   - All device work of a handle is enqueued on the stream given to bvls_setup, in order
+ *     after the work already queued there.  For stream 0 (the legacy default stream, which
+ *     cannot be captured into a CUDA graph) the handle uses a stream of its own, ordered
+ *     after the legacy stream by an event.  bvls_solve returns when its results are in the
+ *     caller's buffers.
  *   - Every call returns a bvls_status and never aborts the process.  On BVLS_EINVAL,
  *     BVLS_ENONFINITE and BVLS_ENOTSUP nothing is written to the outputs.
  *     bvls_last_error() describes the last failure on the calling thread.
@@ -107,6 +109,8 @@ typedef struct {
                            A_S x_S (zero coordinates contribute nothing and are skipped) */
   double fwd_ms, tr_ms; /* profile mode: total time in the A_S x_S and A_S^T r kernels */
   int fwd_launches, tr_launches;
+  double kernel_launches; /* kernels this call launched (including ones that found the solve
+                             already stopped and returned at entry) */
 } bvls_info;
 
 /* Fill *opts with the defaults: tol 1e-6, screen_every 10, max_iter 100000, screening 1,

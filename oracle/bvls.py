@@ -18,9 +18,9 @@ Readings of points the paper leaves open (each also listed in the design doc):
     O'Donoghue and Candes; the paper's experiments use plain projected gradient.
   * The screening step of Algorithm 1 is evaluated every ``screen_every`` iterations at the
     iterate x_k whose gradient the step has just used (so the inner products of the safe
-    rule are those of the step).  Coordinates it fixes are also fixed in the new iterate;
-    the momentum is kept (the extrapolation then runs over the preserved set only) unless
-    a fixed coordinate was not already at its bound in x_k, which restarts it.
+    rule are those of the step).  A coordinate that passes the test is fixed once x_k and
+    x_{k+1} both sit at that bound (the assignment of Algorithm 1 is then exact); the
+    momentum is kept and the extrapolation runs over the preserved set only.
   * The dual point and the gap are those of the reduced problem on the preserved set
     (data y folded as in the remark after Eq. (decmposition_fwd)); the translation maximum
     runs over the preserved columns of J_inf.  ``eps_scope="all"`` gives the literal
@@ -272,9 +272,9 @@ def solve(A, y, l=None, u=None, *, tol=1e-6, screen_every=10, screening=True,
       restart (t_{k+1} = 1) when (A^T (y' - A v_k))^T (x_{k+1} - x_k) < 0.
     Every ``screen_every`` iterations (and at the last one) the screening step runs at x_k:
       theta = Theta(x_k) (Eq. (BVLR_dual_up) or Eq. (BVLR_dual_up2)), Gap (Eq. (Dual_Gap)),
-      r = sqrt(2 Gap) (Eq. (GAP_Safe_sph)), S_l, S_u by Eq. (safe_rule), x_S <- bounds in
-      x_k and x_{k+1}, y' <- y' - A_S x_S, A <- A \\ S (momentum kept unless a fixed
-      coordinate of x_k was off its bound), and the loop stops when Gap < tol, returning x_k.
+      r = sqrt(2 Gap) (Eq. (GAP_Safe_sph)), S_l, S_u by Eq. (safe_rule) among coordinates
+      already at that bound in x_k and x_{k+1}, y' <- y' - A_S x_S, A <- A \\ S (momentum
+      kept), and the loop stops when Gap < tol, returning x_k.
     ``screening=False`` runs the same iteration and gap evaluations with nothing fixed.
     """
     A, y, l, u = as_problem(A, y, l, u)
@@ -338,13 +338,14 @@ def solve(A, y, l=None, u=None, *, tol=1e-6, screen_every=10, screening=True,
                     tau, pad = rounding_pads(A_P, y_red, xP, theta)
                 radius = safe_radius(gap + pad)
                 S_l, S_u = safe_rule(A_P, theta, radius + tau, uP)
-                low, upp = P[S_l], P[S_u & ~S_l]
+                # A coordinate is fixed once x_k and x_{k+1} both sit at the bound the rule
+                # names (the assignment x_S <- bounds of Algorithm 1 is then exact and the
+                # momentum stays consistent); until then it stays in the preserved set.
+                S_l &= (xP == lP) & (x_new[P] == lP)
+                S_u &= ~S_l & (xP == uP) & (x_new[P] == uP)
+                low, upp = P[S_l], P[S_u]
                 pinned = np.concatenate([low, upp])
                 if pinned.size:
-                    # A fixed coordinate that is not yet at its bound would make the
-                    # extrapolation from x_k inconsistent with the reduced problem: restart.
-                    if np.any(x[low] != l[low]) or np.any(x[upp] != u[upp]):
-                        t_next = 1.0
                     x[low] = l[low]
                     x[upp] = u[upp]
                     x_new[pinned] = x[pinned]

@@ -52,6 +52,7 @@ class bvls_info(ctypes.Structure):
         ("tr_ms", ctypes.c_double),
         ("fwd_launches", ctypes.c_int),
         ("tr_launches", ctypes.c_int),
+        ("kernel_launches", ctypes.c_double),
     ]
 
     def as_dict(self):

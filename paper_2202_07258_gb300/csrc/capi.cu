@@ -67,6 +67,7 @@ struct bvls_handle {
   GraphKey key{};
   cudaGraphExec_t exec = nullptr;
   int chunk_len = 0;
+  bool own_stream = false;
   std::vector<cudaEvent_t> prof;
   std::vector<void*> allocs;
 };
@@ -97,7 +98,7 @@ void free_handle(bvls_handle* h) {
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   for (auto e : h->poll)
     if (e) cudaEventDestroy(e);
-  if (h->s) cudaStreamDestroy(h->s);
+  if (h->s && h->own_stream) cudaStreamDestroy(h->s);
   delete h;
 }
 
@@ -240,13 +241,22 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
   int dev = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
-  CK(cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking));
+  // Work runs on the caller's stream; the legacy default stream cannot be captured into a
+  // graph, so for stream 0 the handle owns a stream ordered after it by events.
+  if (h->user) {
+    h->s = h->user;
+  } else {
+    CK(cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking));
+    h->own_stream = true;
+  }
   CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&h->poll[0], cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&h->poll[1], cudaEventDisableTiming));
   CK(cudaHostAlloc(reinterpret_cast<void**>(&h->pinned), 4 * sizeof(int), cudaHostAllocDefault));
-  CK(cudaEventRecord(h->ev_in, h->user));
-  CK(cudaStreamWaitEvent(h->s, h->ev_in, 0));
+  if (h->own_stream) {
+    CK(cudaEventRecord(h->ev_in, h->user));
+    CK(cudaStreamWaitEvent(h->s, h->ev_in, 0));
+  }
 
   TRY(dalloc(h, &h->A, (size_t)h->lda * n));
   CK(cudaMemsetAsync(h->A, 0, sizeof(float) * (size_t)h->lda * n, h->s));
@@ -434,8 +444,10 @@ bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const b
   const int chunk = chunk_length(K);
   const Params p = make_params(h, o, max_iter);
 
-  CK(cudaEventRecord(h->ev_in, h->user));
-  CK(cudaStreamWaitEvent(h->s, h->ev_in, 0));
+  if (h->own_stream) {
+    CK(cudaEventRecord(h->ev_in, h->user));
+    CK(cudaStreamWaitEvent(h->s, h->ev_in, 0));
+  }
   CK(cudaMemcpyAsync(h->y_dev, y, sizeof(float) * h->m, cudaMemcpyDefault, h->s));
   h->b.x0_in = nullptr;
   if (x0) {
@@ -445,6 +457,9 @@ bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const b
   CK(launch_init(p, h->b, h->s));
 
   const long long max_chunks = (max_iter + chunk - 1) / chunk + 1;
+  const bool scr = o.screening && h->dual_mode != kZero;
+  const long long per_chunk = 2LL * chunk + (long long)(chunk / K) * (scr ? 4 : 1);
+  long long chunks_run = 0;
   double fwd_ms = 0.0, tr_ms = 0.0;
   int fwd_launches = 0, tr_launches = 0;
   if (o.profile) {
@@ -458,6 +473,7 @@ bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const b
     int k_before = 0;
     for (long long c = 0; c < max_chunks; ++c) {
       CK(enqueue_chunk(h, p, o, chunk, h->prof.data()));
+      ++chunks_run;
       DevState hs;
       CK(cudaMemcpyAsync(&hs, h->b.st, sizeof(DevState), cudaMemcpyDeviceToHost, h->s));
       CK(cudaStreamSynchronize(h->s));
@@ -498,6 +514,7 @@ bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const b
     // Keep one chunk queued behind the one whose stop flag is being read.
     for (long long c = 0; c < max_chunks; ++c) {
       CK(cudaGraphLaunch(h->exec, h->s));
+      ++chunks_run;
       CK(cudaMemcpyAsync(&h->pinned[c & 1], &h->b.st->done, sizeof(int), cudaMemcpyDeviceToHost, h->s));
       CK(cudaEventRecord(h->poll[c & 1], h->s));
       if (c >= 1) {
@@ -531,6 +548,7 @@ bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const b
     info->tr_ms = tr_ms;
     info->fwd_launches = fwd_launches;
     info->tr_launches = tr_launches;
+    info->kernel_launches = 2.0 + (double)chunks_run * (double)per_chunk;
   }
   if (!hs.done) return set_err(BVLS_EMAXITER, "stopped after %d chunks without the stop flag", (int)max_chunks);
   if (!hs.converged) return set_err(BVLS_EMAXITER, "gap %.3e >= tol after %d iterations", hs.gap, hs.k);

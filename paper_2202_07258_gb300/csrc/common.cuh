@@ -39,11 +39,11 @@ struct DevState {
   int n_active;       // |preserved set|
   int n_pins;         // coordinates fixed by the current screening step
   int n_fold;         // of which with a nonzero bound value (their columns are folded into y')
-  int restart_pin;    // a coordinate was fixed while off its bound: restart the momentum
   int out_slot;       // which x buffer holds the returned iterate
   int gap_evals;
   int nonfinite;
   int pad0;
+  int pad1;
   double t;           // FISTA momentum parameter t_k
   double P;           // 1/2 ||r||^2 of the last A_S x_S pass (r = rh + rl)
   double eps;         // translation step of the last evaluation

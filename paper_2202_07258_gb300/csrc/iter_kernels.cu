@@ -11,7 +11,7 @@
 //   k_gap     duality gap of Eq. (Dual_Gap) in its nonnegative-sum form plus rounding
 //             bounds, radius of Eq. (GAP_Safe_sph), stop test.
 //   k_test    sphere test of Eq. (safe_rule) with the rounding margin added to the radius;
-//             fixes coordinates in x_k and x_{k+1}.
+//             fixes the coordinates that pass and already sit at that bound in x_k and x_{k+1}.
 //   k_compact stable compaction of the preserved index list; list of fixed columns with a
 //             nonzero bound, folded into y' by k_fwd<fold> (remark after Eq. (decmposition_fwd)).
 #include "common.cuh"
@@ -120,7 +120,6 @@ __global__ void k_init_state(Params p, Buffers b) {
     st->n_active = p.n;
     st->n_pins = 0;
     st->n_fold = 0;
-    st->restart_pin = 0;
     st->out_slot = 0;
     st->gap_evals = 0;
     st->nonfinite = bad;
@@ -574,10 +573,10 @@ __global__ void __launch_bounds__(kRedThreads) k_test(Params p, Buffers b, int s
   const bool trans = p.dual_mode == kTranslation;
   const double eps = trans ? st->eps : 0.0;
   const double rr = st->radius * (1.0 + 1e-12) + st->eta;
-  double* xc = b.x[slot];
-  double* xn = b.x[slot ^ 1];
+  const double* __restrict__ xc = b.x[slot];
+  const double* __restrict__ xn = b.x[slot ^ 1];
   const double* __restrict__ gc = b.g[slot];
-  int cnt = 0, off = 0;
+  int cnt = 0;
   const int stride = gridDim.x * blockDim.x;
   for (int pp = blockIdx.x * blockDim.x + threadIdx.x; pp < n_act; pp += stride) {
     const int j = b.idx[pp];
@@ -594,20 +593,15 @@ __global__ void __launch_bounds__(kRedThreads) k_test(Params p, Buffers b, int s
       pin = 2;
       bnd = p.u[j];
     }
-    if (pin) {
-      if (xc[j] != bnd) off = 1;
-      xc[j] = bnd;
-      xn[j] = bnd;
+    // Fixed once x_k and x_{k+1} both sit at that bound: the stored g_k then stays the
+    // gradient of the reduced problem and the momentum needs no correction.
+    if (pin && xc[j] == bnd && xn[j] == bnd) {
       b.flags[j] = (uint8_t)pin;
       ++cnt;
     }
   }
   for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-  off = __any_sync(0xffffffffu, off);
-  if ((threadIdx.x & 31) == 0) {
-    if (cnt) atomicAdd(&st->n_pins, cnt);
-    if (off) atomicOr(&st->restart_pin, 1);
-  }
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&st->n_pins, cnt);
 }
 
 cudaError_t launch_test(const Params& p, const Buffers& b, int slot, int red_blocks, cudaStream_t s) {
@@ -691,9 +685,7 @@ __global__ void __launch_bounds__(kCompactThreads) k_compact(Params p, Buffers b
     st->n_fold = nfold;
     st->S_fold += s;
     st->E_fold += p.Cf * s + p.Csub * (st->y_norm + st->S_fold);
-    if (st->restart_pin) st->t = 1.0;
     st->n_pins = 0;
-    st->restart_pin = 0;
     if (stop) st->done = 1;
   }
 }
