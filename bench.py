@@ -191,12 +191,21 @@ def roofline(solver, y_dev, m):
     from paper_2202_07258_gb300 import make_opts
     x, s, info, st = solver.solve(y_dev, opts=make_opts(tol=TOL, screen_every=K_SCREEN, profile=True))
     nl = max(1, info["tr_launches"])
-    tr_bytes = 4.0 * m * info["sum_preserved"] + nl * 8.0 * m + 60.0 * info["sum_preserved"]
-    fwd_bytes = 4.0 * m * info["sum_nonzero"] + nl * 16.0 * m + 12.0 * info["sum_preserved"]
-    kern = {
-        "k_tr (A_S^T r + FISTA step)": (info["tr_ms"], tr_bytes, info["tr_launches"]),
-        "k_fwd (A_S x_S, r, P)": (info["fwd_ms"], fwd_bytes, info["fwd_launches"]),
-    }
+    if info["single_pass"]:
+        # one read of the preserved columns per iteration: A_S^T r_k, the step and A_S x_{k+1}
+        pass_bytes = 4.0 * m * info["sum_preserved"] + nl * 8.0 * m + 60.0 * info["sum_preserved"]
+        resid_bytes = nl * 32.0 * m        # q (f64) read + clear, y' and r (hi, lo)
+        kern = {
+            "k_pass (one read of A_S: A_S^T r, FISTA step, A_S x)": (info["tr_ms"], pass_bytes, info["tr_launches"]),
+            "k_resid (r = y' - q, P)": (info["fwd_ms"], resid_bytes, info["fwd_launches"]),
+        }
+    else:
+        tr_bytes = 4.0 * m * info["sum_preserved"] + nl * 8.0 * m + 60.0 * info["sum_preserved"]
+        fwd_bytes = 4.0 * m * info["sum_nonzero"] + nl * 16.0 * m + 12.0 * info["sum_preserved"]
+        kern = {
+            "k_tr (A_S^T r + FISTA step)": (info["tr_ms"], tr_bytes, info["tr_launches"]),
+            "k_fwd (A_S x_S, r, P)": (info["fwd_ms"], fwd_bytes, info["fwd_launches"]),
+        }
     name = max(kern, key=lambda k: kern[k][0])
     ms, by, launches = kern[name]
     avg_s = ms / 1000.0 / max(1, launches)

@@ -62,7 +62,8 @@ typedef enum {
   BVLS_EMAXITER = 4,    /* max_iter reached with gap >= tol; outputs hold the last evaluated
                            iterate, its gap and its screened set */
   BVLS_ENONFINITE = 5,  /* NaN or Inf found in A, y or x0 */
-  BVLS_ENOTSUP = 6      /* sizes beyond what this build supports (see bvls_setup) */
+  BVLS_ENOTSUP = 6,     /* sizes beyond what this build supports (see bvls_setup) */
+  BVLS_ETIMEOUT = 7     /* a bounded device-side wait gave up (about 2 s); outputs untouched */
 } bvls_status;
 
 /* Arithmetic of the two products over the preserved columns. */
@@ -91,6 +92,9 @@ typedef struct {
   double lipschitz;   /* > 0: use this step constant L instead of the one from bvls_setup */
   int profile;        /* 1: launch without CUDA graphs and time every product kernel with
                          CUDA events (fills the *_ms fields of bvls_info) */
+  int single_pass;    /* 1 (default): when m <= 8192, one streaming read of the preserved
+                         columns per iteration yields both products; 0: two passes
+                         (A_S x_S, then A_S^T r), the form used for larger m */
 } bvls_opts;
 
 typedef struct {
@@ -107,14 +111,19 @@ typedef struct {
   double sum_preserved; /* sum over iterations of |preserved set|: columns read by A_S^T r */
   double sum_nonzero;   /* sum over iterations of the preserved x_j != 0: columns read by
                            A_S x_S (zero coordinates contribute nothing and are skipped) */
-  double fwd_ms, tr_ms; /* profile mode: total time in the A_S x_S and A_S^T r kernels */
+  double fwd_ms, tr_ms; /* profile mode, total kernel time.  Fused single-pass iteration
+                           (m <= 8192): tr_ms = the pass that reads A_S once for both products,
+                           fwd_ms = the residual kernel r = y' - q.  Two-pass iteration:
+                           fwd_ms = A_S x_S, tr_ms = A_S^T r. */
   int fwd_launches, tr_launches;
   double kernel_launches; /* kernels this call launched (including ones that found the solve
                              already stopped and returned at entry) */
+  int single_pass;        /* 1 when the iterations read A_S once each (see bvls_opts) */
 } bvls_info;
 
 /* Fill *opts with the defaults: tol 1e-6, screen_every 10, max_iter 100000, screening 1,
-   precision BVLS_PREC_FP32X2, restart 1, lipschitz 0 (use setup's), profile 0. */
+   precision BVLS_PREC_FP32X2, restart 1, lipschitz 0 (use setup's), profile 0,
+   single_pass 1. */
 BVLS_API void bvls_default_opts(bvls_opts* opts);
 
 /*

@@ -353,13 +353,12 @@ def solve(A, y, l=None, u=None, *, tol=1e-6, screen_every=10, screening=True,
                     active[pinned] = False
                     screened[low] = 1
                     screened[upp] = 2
-            if gap < tol:
-                return SolveResult(x, gap, primal_objective(A, y, x), k + 1, screened, True,
-                                   mode, L, t_dir, history if record else [])
+            if gap < tol or k == max_iter - 1:
+                # x_k is the iterate the gap certifies (also when max_iter ends the loop)
+                return SolveResult(x, gap, primal_objective(A, y, x), k + 1, screened,
+                                   bool(gap < tol), mode, L, t_dir, history if record else [])
         x_prev, x, tk = x, x_new, t_next
-
-    return SolveResult(x, gap, primal_objective(A, y, x), max_iter, screened, False, mode, L,
-                       t_dir, history if record else [])
+    raise AssertionError("unreachable: the last iteration always evaluates the gap")
 
 
 def brute_force(A, y, l=None, u=None, tol=1e-9):

@@ -46,7 +46,7 @@ def _host_f64(v, n):
 
 
 def make_opts(tol=1e-6, screen_every=10, max_iter=100000, screening=True, precision="fp32x2",
-              restart=True, lipschitz=0.0, profile=False) -> bvls_opts:
+              restart=True, lipschitz=0.0, profile=False, single_pass=True) -> bvls_opts:
     o = bvls_default_opts()
     o.tol = float(tol)
     o.screen_every = int(screen_every)
@@ -56,6 +56,7 @@ def make_opts(tol=1e-6, screen_every=10, max_iter=100000, screening=True, precis
     o.restart = 1 if restart else 0
     o.lipschitz = float(lipschitz)
     o.profile = 1 if profile else 0
+    o.single_pass = 1 if single_pass else 0
     return o
 
 

@@ -12,8 +12,9 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libbvls_gb300.so")
 
-BVLS_OK, BVLS_EINVAL, BVLS_ENOMEM, BVLS_ECUDA, BVLS_EMAXITER, BVLS_ENONFINITE, BVLS_ENOTSUP = range(7)
-STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EMAXITER", 5: "ENONFINITE", 6: "ENOTSUP"}
+BVLS_OK, BVLS_EINVAL, BVLS_ENOMEM, BVLS_ECUDA, BVLS_EMAXITER, BVLS_ENONFINITE, BVLS_ENOTSUP, BVLS_ETIMEOUT = range(8)
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EMAXITER", 5: "ENONFINITE", 6: "ENOTSUP",
+                7: "ETIMEOUT"}
 BVLS_PREC_FP32X2, BVLS_PREC_FP32 = 0, 1
 BVLS_DUAL_SCALING, BVLS_DUAL_TRANSLATION, BVLS_DUAL_ZERO = 0, 1, 2
 DUAL_NAMES = {0: "scaling", 1: "translation", 2: "zero"}
@@ -32,6 +33,7 @@ class bvls_opts(ctypes.Structure):
         ("restart", ctypes.c_int),
         ("lipschitz", ctypes.c_double),
         ("profile", ctypes.c_int),
+        ("single_pass", ctypes.c_int),
     ]
 
 
@@ -53,6 +55,7 @@ class bvls_info(ctypes.Structure):
         ("fwd_launches", ctypes.c_int),
         ("tr_launches", ctypes.c_int),
         ("kernel_launches", ctypes.c_double),
+        ("single_pass", ctypes.c_int),
     ]
 
     def as_dict(self):

@@ -38,11 +38,12 @@ constexpr double kU = 5.9604644775390625e-08;   // 2^-24, unit roundoff of float
 constexpr double kU64 = 1.1102230246251565e-16; // 2^-53
 
 struct GraphKey {
-  int K, screening, precision, restart, max_iter;
+  int K, screening, precision, restart, max_iter, single_pass;
   double tol, invL;
   bool operator==(const GraphKey& o) const {
     return K == o.K && screening == o.screening && precision == o.precision &&
-           restart == o.restart && max_iter == o.max_iter && tol == o.tol && invL == o.invL;
+           restart == o.restart && max_iter == o.max_iter && single_pass == o.single_pass &&
+           tol == o.tol && invL == o.invL;
   }
 };
 
@@ -62,6 +63,7 @@ struct bvls_handle {
   double* x0_dev = nullptr;
   int* pinned = nullptr;
   int fwd_tiles = 0, fwd_chunks = 0, tr_blocks = 0, red_blocks = 0;
+  int pass_stages = 0, pass_qw = 0;  // fused single-pass iteration when pass_stages > 0
   double Cg[2] = {0, 0}, Cf[2] = {0, 0}, Csub = 0.0;
   bool have_graph = false;
   GraphKey key{};
@@ -170,10 +172,18 @@ cudaError_t enqueue_chunk(bvls_handle* h, const Params& p, const bvls_opts& o, i
     const int slot = j & 1;
     const bool gap_iter = ((j + 1) % o.screen_every) == 0;
     if (ev) cudaEventRecord(ev[3 * j], h->s);
-    e = launch_fwd(p, h->b, slot, o.precision, false, h->s);
-    if (e != cudaSuccess) break;
-    if (ev) cudaEventRecord(ev[3 * j + 1], h->s);
-    e = launch_tr(p, h->b, slot, o.precision, gap_iter, h->tr_blocks, h->s);
+    if (h->pass_stages > 0 && o.single_pass) {
+      // fused: one read of A_S gives g_k and q_{k+1}; then r_{k+1} = y' - q_{k+1}
+      e = launch_pass(p, h->b, slot, o.precision, gap_iter, h->num_sms, h->pass_stages, h->pass_qw, h->s);
+      if (e != cudaSuccess) break;
+      if (ev) cudaEventRecord(ev[3 * j + 1], h->s);
+      e = launch_resid(p, h->b, slot, h->s);
+    } else {
+      e = launch_fwd(p, h->b, slot, o.precision, false, h->s);
+      if (e != cudaSuccess) break;
+      if (ev) cudaEventRecord(ev[3 * j + 1], h->s);
+      e = launch_tr(p, h->b, slot, o.precision, gap_iter, h->tr_blocks, h->s);
+    }
     if (e != cudaSuccess) break;
     if (ev) cudaEventRecord(ev[3 * j + 2], h->s);
     if (gap_iter) {
@@ -217,6 +227,7 @@ void bvls_default_opts(bvls_opts* o) {
   o->restart = 1;
   o->lipschitz = 0.0;
   o->profile = 0;
+  o->single_pass = 1;
 }
 
 const char* bvls_last_error(void) { return g_err.c_str(); }
@@ -362,6 +373,12 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
   }
   int bps = 1;
   CK(tr_configure(h->m4, &bps));
+  {
+    int optin = 0;
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    h->pass_stages = pass_configure(h->lda, h->m4, optin, &h->pass_qw);
+    cudaGetLastError();
+  }
   h->tr_blocks = h->num_sms * std::max(1, std::min(bps, 2));
   h->red_blocks = std::max(1, std::min(2 * h->num_sms, (n + kRedThreads - 1) / kRedThreads));
   const int max_blocks = std::max(std::max(h->tr_blocks, h->red_blocks), 64);
@@ -384,6 +401,8 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
   TRY(dalloc(h, &b.tile_cnt, h->fwd_tiles));
   TRY(dalloc(h, &b.blk, 4 * (size_t)max_blocks));
   TRY(dalloc(h, &b.st, 1));
+  TRY(dalloc(h, &b.qacc, h->m4));
+  CK(cudaMemsetAsync(b.qacc, 0, sizeof(double) * h->m4, h->s));
   TRY(dalloc(h, &h->y_dev, h->m4));
   TRY(dalloc(h, &h->x0_dev, n));
   CK(cudaMemsetAsync(b.tile_cnt, 0, sizeof(unsigned) * h->fwd_tiles, h->s));
@@ -455,6 +474,8 @@ bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const b
     h->b.x0_in = h->x0_dev;
   }
   CK(launch_init(p, h->b, h->s));
+  const bool fused = h->pass_stages > 0 && o.single_pass;
+  if (fused) CK(launch_fwd(p, h->b, 0, o.precision, false, h->s));  // r_0, P_0
 
   const long long max_chunks = (max_iter + chunk - 1) / chunk + 1;
   const bool scr = o.screening && h->dual_mode != kZero;
@@ -491,7 +512,7 @@ bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const b
       if (hs.done) break;
     }
   } else {
-    GraphKey key{K, o.screening, o.precision, o.restart, max_iter, o.tol, p.invL};
+    GraphKey key{K, o.screening, o.precision, o.restart, max_iter, o.single_pass, o.tol, p.invL};
     if (!h->have_graph || !(h->key == key) || h->chunk_len != chunk) {
       if (h->exec) {
         cudaGraphExecDestroy(h->exec);
@@ -527,6 +548,7 @@ bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const b
   DevState hs;
   CK(cudaMemcpy(&hs, h->b.st, sizeof(DevState), cudaMemcpyDeviceToHost));
   if (hs.nonfinite) return set_err(BVLS_ENONFINITE, "y or x0 contains NaN or Inf");
+  if (hs.error) return set_err(BVLS_ETIMEOUT, "a device-side wait exceeded its bound; results discarded");
   CK(cudaMemcpyAsync(x_out, h->b.x[hs.out_slot], sizeof(double) * h->n, cudaMemcpyDefault, h->s));
   if (screened_out)
     CK(cudaMemcpyAsync(screened_out, h->b.flags, h->n, cudaMemcpyDefault, h->s));
@@ -539,7 +561,7 @@ bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const b
     info->dual_mode = h->dual_mode;
     info->gap_evals = hs.gap_evals;
     info->gap = hs.gap;
-    info->primal = hs.P;
+    info->primal = hs.P[hs.out_slot];
     info->radius = hs.radius;
     info->L = 1.0 / p.invL;
     info->sum_preserved = hs.sum_active;
@@ -548,7 +570,8 @@ bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const b
     info->tr_ms = tr_ms;
     info->fwd_launches = fwd_launches;
     info->tr_launches = tr_launches;
-    info->kernel_launches = 2.0 + (double)chunks_run * (double)per_chunk;
+    info->kernel_launches = (fused ? 3.0 : 2.0) + (double)chunks_run * (double)per_chunk;
+    info->single_pass = fused ? 1 : 0;
   }
   if (!hs.done) return set_err(BVLS_EMAXITER, "stopped after %d chunks without the stop flag", (int)max_chunks);
   if (!hs.converged) return set_err(BVLS_EMAXITER, "gap %.3e >= tol after %d iterations", hs.gap, hs.k);

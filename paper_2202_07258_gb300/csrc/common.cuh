@@ -25,6 +25,9 @@ constexpr int kTrThreads = kTrWarps * 32;
 constexpr int kRedThreads = 256;  // blocks of the O(|A|) epilogue kernels
 constexpr int kCompactThreads = 1024;
 constexpr int kMaxRows = 24576;   // r is staged in shared memory: 8 bytes per row
+constexpr int kPassDot = 8;       // dot warps of the fused pass
+constexpr int kPassTmax = 8;      // float4 row chunks owned by one lane of a q warp
+constexpr int kPassMaxStages = 32;
 
 enum DualMode { kScaling = 0, kTranslation = 1, kZero = 2 };
 enum Precision { kX2 = 0, kF32 = 1 };
@@ -42,10 +45,10 @@ struct DevState {
   int out_slot;       // which x buffer holds the returned iterate
   int gap_evals;
   int nonfinite;
-  int pad0;
+  int error;          // a bounded device wait gave up (nonzero: results invalid)
   int pad1;
   double t;           // FISTA momentum parameter t_k
-  double P;           // 1/2 ||r||^2 of the last A_S x_S pass (r = rh + rl)
+  double P[2];        // 1/2 ||r_k||^2 in slot k & 1 (r = rh + rl)
   double eps;         // translation step of the last evaluation
   double gap;         // gap upper bound of the last evaluation
   double radius;      // sqrt(2 gap)
@@ -55,7 +58,7 @@ struct DevState {
   double y_norm;      // ||y||_2
   double sum_active;  // sum of |preserved set| over the A_S^T r passes
   double sum_nnz;     // sum of nonzero preserved x_j over the A_S x_S passes
-  unsigned int cnt_tr, cnt_gap, cnt_fwd, cnt_fold;
+  unsigned int cnt_tr, cnt_gap, cnt_fwd, cnt_resid;
 };
 
 // Per-solve constants passed by value to the kernels.
@@ -131,6 +134,9 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
+// All lanes of a warp agree on the outcome of a bounded wait.
+__device__ __forceinline__ bool warp_all(bool ok) { return __all_sync(0xffffffffu, ok) != 0; }
+
 __device__ __forceinline__ double warp_max_d(double v) {
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
@@ -153,6 +159,7 @@ struct Buffers {
   double* tileP;
   unsigned int* tile_cnt;
   double* blk;            // per-block partials of the epilogue kernels (4 doubles each)
+  double* qacc;           // float64 accumulator of A_S x_S for the fused pass (m entries)
   DevState* st;
   const float* y_in;      // device copy of y
   const double* x0_in;    // device copy of x0 or null
@@ -168,6 +175,11 @@ cudaError_t launch_gap(const Params& p, const Buffers& b, int slot, bool finaliz
 cudaError_t launch_test(const Params& p, const Buffers& b, int slot, int red_blocks, cudaStream_t s);
 cudaError_t launch_compact(const Params& p, const Buffers& b, int slot, cudaStream_t s);
 size_t tr_smem_bytes(int m4);
+// Fused single-pass iteration (pass_kernel.cu).
+int pass_configure(int lda, int m4, int smem_optin, int* qwarps);
+cudaError_t launch_pass(const Params& p, const Buffers& b, int slot, int precision, bool gap_iter,
+                        int grid, int nstages, int qwarps, cudaStream_t s);
+cudaError_t launch_resid(const Params& p, const Buffers& b, int slot, cudaStream_t s);
 cudaError_t tr_configure(int m4, int* blocks_per_sm);
 
 // Setup kernels (setup_kernels.cu).

@@ -124,7 +124,9 @@ __global__ void k_init_state(Params p, Buffers b) {
     st->gap_evals = 0;
     st->nonfinite = bad;
     st->t = 1.0;
-    st->P = 0.0;
+    st->P[0] = 0.0;
+    st->P[1] = 0.0;
+    st->error = 0;
     st->eps = 0.0;
     st->gap = INFINITY;
     st->radius = INFINITY;
@@ -134,7 +136,7 @@ __global__ void k_init_state(Params p, Buffers b) {
     st->y_norm = sqrt(s);
     st->sum_active = 0.0;
     st->sum_nnz = 0.0;
-    st->cnt_tr = st->cnt_gap = st->cnt_fwd = st->cnt_fold = 0u;
+    st->cnt_tr = st->cnt_gap = st->cnt_fwd = st->cnt_resid = 0u;
   }
 }
 
@@ -324,7 +326,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd(Params p, Buffers b, int sl
     double a = 0.0;
     for (int t = threadIdx.x; t < (int)gridDim.x; t += 32) a += __ldcg(&b.tileP[t]);
     a = warp_sum_d(a);
-    if (threadIdx.x == 0) st->P = a;
+    if (threadIdx.x == 0) st->P[slot] = a;
   }
 }
 
@@ -362,7 +364,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_tr(Params p, Buffers b, int s
   const double tk = st->t;
   const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk * tk));
   const double beta = (tk - 1.0) / tn;
-  const double rnorm = sqrt(2.0 * st->P) * (1.0 + 1e-6);
+  const double rnorm = sqrt(2.0 * st->P[slot]) * (1.0 + 1e-6);
   const double eta_g = p.Cg * rnorm;
   const bool want_eps = gap_iter && p.dual_mode == kTranslation;
   const double* __restrict__ xc = b.x[slot];
@@ -530,7 +532,7 @@ __global__ void __launch_bounds__(kRedThreads) k_gap(Params p, Buffers b, int sl
     c = warp_sum_d(c);
     x = warp_sum_d(x);
     if (threadIdx.x == 0) {
-      const double rnorm = sqrt(2.0 * st->P) * (1.0 + 1e-6);
+      const double rnorm = sqrt(2.0 * st->P[slot]) * (1.0 + 1e-6);
       const double eta = p.Cg * rnorm + (trans ? eps * p.gamma_w * p.t_norm : 0.0);
       const double E_r = st->E_fold + p.Cf * x + p.Csub * (rnorm + st->y_norm + st->S_fold + x);
       double gap;

@@ -1,0 +1,377 @@
+// One streaming pass over the preserved columns per iteration (A read once from HBM).
+//
+// For iteration k the pass computes, column by column,
+//   g_k,j     = a_j^T r_k                       (correlation; -grad P(x_k), Eq. (grad))
+//   x_{k+1,j} = clip(v_j + g_v,j / L, l_j, u_j) (FISTA step; g_v = (1+b) g_k - b g_{k-1})
+// and, while column a_j is still in shared memory, accumulates q_{k+1} = A_S x_{k+1}
+// (Eq. (decmposition_fwd)), so the next residual r_{k+1} = y' - q_{k+1} needs no second
+// pass over A.  The per-column step depends on g_k,j alone, so both products of an
+// iteration share one read of the column.
+//
+// Warp roles in each CTA (one CTA per SM, columns split into contiguous ranges):
+//   producer  lane 0 streams columns into a ring of shared-memory stages with bulk copies
+//             (cp.async.bulk, completion on a `full` mbarrier per stage);
+//   dot       kPassDot warps, one column each: a_j^T r from shared memory in double-float,
+//             then the FP64 step; x_{k+1,j} is handed to the q warps through shared memory
+//             and an `xready` mbarrier;
+//   q         QW warps, each owning a fixed slice of rows: q_slice += a_j x_{k+1,j} in
+//             double-float registers over every column of the CTA; columns with
+//             x_{k+1,j} = 0 are skipped.  At the end each row partial is added to a float64
+//             accumulator in global memory (FP64 atomics).
+// A stage is released (`empty` mbarrier) when its dot warp and all q warps are done.
+// k_resid then forms r_{k+1} = y' - q and P_{k+1} = 1/2 ||r_{k+1}||^2 and clears q.
+#include "common.cuh"
+#include "tma.cuh"
+
+namespace bvls {
+
+namespace {
+
+template <int PREC>
+__device__ __forceinline__ void pacc4(float* s, float* c, const float4 a, float xh, float xl) {
+  if (PREC == kX2) {
+    df_fma(s[0], c[0], a.x, xh, xl);
+    df_fma(s[1], c[1], a.y, xh, xl);
+    df_fma(s[2], c[2], a.z, xh, xl);
+    df_fma(s[3], c[3], a.w, xh, xl);
+  } else {
+    s[0] = fmaf(a.x, xh, s[0]);
+    s[1] = fmaf(a.y, xh, s[1]);
+    s[2] = fmaf(a.z, xh, s[2]);
+    s[3] = fmaf(a.w, xh, s[3]);
+  }
+}
+
+template <int PREC>
+__device__ __forceinline__ void pacc4v(float* s, float* c, const float4 a, const float4 h, const float4 l) {
+  if (PREC == kX2) {
+    df_fma(s[0], c[0], a.x, h.x, l.x);
+    df_fma(s[1], c[1], a.y, h.y, l.y);
+    df_fma(s[2], c[2], a.z, h.z, l.z);
+    df_fma(s[3], c[3], a.w, h.w, l.w);
+  } else {
+    s[0] = fmaf(a.x, h.x, s[0]);
+    s[1] = fmaf(a.y, h.y, s[1]);
+    s[2] = fmaf(a.z, h.z, s[2]);
+    s[3] = fmaf(a.w, h.w, s[3]);
+  }
+}
+
+template <int PREC>
+__device__ __forceinline__ void pmerge(float& s, float& c, float s2, float c2) {
+  if (PREC == kX2) df_add(s, c, s2, c2);
+  else s += s2;
+}
+
+}  // namespace
+
+template <int PREC, int QW>
+__global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
+    k_pass(Params p, Buffers b, int slot, int gap_iter, int nstages) {
+  DevState* st = b.st;
+  if (st->done) return;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int m4q = p.m4 >> 2;
+  const uint32_t col_bytes = (uint32_t)p.lda * 4u;
+  float* stages = reinterpret_cast<float*>(smem);
+  float4* srh = reinterpret_cast<float4*>(smem + (size_t)nstages * col_bytes);
+  float4* srl = srh + m4q;
+  float2* sx = reinterpret_cast<float2*>(srl + m4q);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sx + nstages + (nstages & 1));
+  uint64_t* xready = full + nstages;
+  uint64_t* empty = xready + nstages;
+  __shared__ double s_red[2][kPassDot];
+  __shared__ int s_err;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_act = st->n_active;
+  const int per = (n_act + gridDim.x - 1) / gridDim.x;
+  const int p0 = min(n_act, (int)blockIdx.x * per);
+  const int nq = min(n_act, p0 + per) - p0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < nstages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&xready[s], 1);
+      mbar_init(&empty[s], 1 + QW);
+    }
+    fence_barrier_init();
+    s_err = 0;
+  }
+  if (threadIdx.x < 2 * kPassDot) (&s_red[0][0])[threadIdx.x] = 0.0;
+  for (int i = threadIdx.x; i < m4q; i += blockDim.x) {
+    srh[i] = __ldcg(reinterpret_cast<const float4*>(b.rh) + i);
+    srl[i] = __ldcg(reinterpret_cast<const float4*>(b.rl) + i);
+  }
+  __syncthreads();
+
+  const double tk = st->t;
+  const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk * tk));
+  const double beta = (tk - 1.0) / tn;
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- producer
+    if (lane == 0) {
+      int issued = 0;
+      for (int q = 0; q < nq; ++q) {
+        const int s = q % nstages;
+        const int u = q / nstages;
+        if (u > 0 && !mbar_wait(&empty[s], (u - 1) & 1)) {
+          s_err = 1;
+          break;
+        }
+        const int j = b.idx[p0 + q];
+        mbar_arrive_expect_tx(&full[s], col_bytes);
+        bulk_g2s(stages + (size_t)s * p.lda, p.A + (size_t)j * p.lda, col_bytes, &full[s]);
+        issued = q + 1;
+      }
+      // The most recent copy into each stage must land before the CTA may exit.
+      for (int q = max(0, issued - nstages); q < issued; ++q)
+        if (!mbar_wait(&full[q % nstages], (q / nstages) & 1)) s_err = 1;
+    }
+  } else if (warp <= kPassDot) {
+    // ---------------------------------------------------------------- dot warps
+    const int dw = warp - 1;
+    const double rnorm = sqrt(2.0 * st->P[slot]) * (1.0 + 1e-6);
+    const double eta_g = p.Cg * rnorm;
+    const bool want_eps = gap_iter && p.dual_mode == kTranslation;
+    const double* __restrict__ xc = b.x[slot];
+    double* xn = b.x[slot ^ 1];
+    const double* __restrict__ gp = b.g[slot ^ 1];
+    double* gc = b.g[slot];
+    double dot = 0.0, epsm = 0.0;
+    for (int q = dw; q < nq; q += kPassDot) {
+      const int s = q % nstages;
+      const int u = q / nstages;
+      const int j = b.idx[p0 + q];
+      double xk = 0.0, xp = 0.0, gpv = 0.0, lj = 0.0, uj = 0.0, nr = 0.0, wj = 0.0;
+      int inf_j = 0;
+      if (lane == 0) {  // independent of the column data: issue before waiting
+        xk = xc[j];
+        xp = xn[j];
+        gpv = gp[j];
+        lj = p.l[j];
+        uj = p.u[j];
+        if (want_eps) {
+          nr = p.nrm[j];
+          wj = p.w[j];
+          inf_j = p.jinf[j];
+        }
+      }
+      if (!warp_all(mbar_wait(&full[s], u & 1))) {
+        s_err = 1;
+        break;
+      }
+      const float4* col = reinterpret_cast<const float4*>(stages + (size_t)s * p.lda);
+      float sa[4] = {0.f, 0.f, 0.f, 0.f}, ca[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+      for (int i = lane; i < m4q; i += 32) pacc4v<PREC>(sa, ca, col[i], srh[i], srl[i]);
+      pmerge<PREC>(sa[0], ca[0], sa[1], ca[1]);
+      pmerge<PREC>(sa[2], ca[2], sa[3], ca[3]);
+      pmerge<PREC>(sa[0], ca[0], sa[2], ca[2]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float os = __shfl_xor_sync(0xffffffffu, sa[0], o);
+        const float oc = __shfl_xor_sync(0xffffffffu, ca[0], o);
+        pmerge<PREC>(sa[0], ca[0], os, oc);
+      }
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&empty[s]);  // this warp is done reading the stage
+        const double g = PREC == kX2 ? df_to_double(sa[0], ca[0]) : (double)sa[0];
+        const double gv = (1.0 + beta) * g - beta * gpv;   // a_j^T (y' - A v_k)
+        const double v = xk + beta * (xk - xp);
+        double xnew = fmin(fmax(v + gv * p.invL, lj), uj);
+        float xh, xl;
+        split_double(xnew, xh, xl);
+        sx[s] = make_float2(xh, PREC == kX2 ? xl : 0.0f);
+        mbar_arrive(&xready[s]);
+        xn[j] = xnew;
+        gc[j] = g;
+        dot += gv * (xnew - xk);
+        if (want_eps && inf_j && nr > 0.0) {
+          const double den = -wj - p.gamma_w * nr * p.t_norm;
+          epsm = fmax(epsm, fmax(g + eta_g * nr, 0.0) / den);
+        }
+      }
+    }
+    if (lane == 0) {
+      s_red[0][dw] = dot;
+      s_red[1][dw] = epsm;
+    }
+  } else {
+    // ---------------------------------------------------------------- q warps
+    const int qw = warp - 1 - kPassDot;
+    float qs[kPassTmax][4], qc[kPassTmax][4];
+#pragma unroll
+    for (int t = 0; t < kPassTmax; ++t)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) qs[t][c] = qc[t][c] = 0.f;
+    for (int q = 0; q < nq; ++q) {
+      const int s = q % nstages;
+      const int u = q / nstages;
+      if (!warp_all(mbar_wait(&xready[s], u & 1) && mbar_wait(&full[s], u & 1))) {
+        s_err = 1;
+        break;
+      }
+      const float2 xv = sx[s];
+      if (xv.x != 0.0f || xv.y != 0.0f) {
+        const float4* col = reinterpret_cast<const float4*>(stages + (size_t)s * p.lda);
+#pragma unroll
+        for (int t = 0; t < kPassTmax; ++t) {
+          const int c4 = qw * 32 + lane + t * 32 * QW;
+          if (c4 < m4q) pacc4<PREC>(qs[t], qc[t], col[c4], xv.x, xv.y);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
+    }
+    if (nq > 0) {
+#pragma unroll
+      for (int t = 0; t < kPassTmax; ++t) {
+        const int c4 = qw * 32 + lane + t * 32 * QW;
+        if (c4 < m4q) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int row = 4 * c4 + c;
+            const double v = PREC == kX2 ? df_to_double(qs[t][c], qc[t][c]) : (double)qs[t][c];
+            if (row < p.m && v != 0.0) atomicAdd(&b.qacc[row], v);
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double d = 0.0, e = 0.0;
+    for (int w = 0; w < kPassDot; ++w) {
+      d += s_red[0][w];
+      e = fmax(e, s_red[1][w]);
+    }
+    b.blk[4 * blockIdx.x + 0] = d;
+    b.blk[4 * blockIdx.x + 1] = e;
+    if (s_err) atomicOr(&st->error, 1);
+  }
+  // last CTA: restart test, momentum parameter, translation step, iteration count
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(&st->cnt_tr, 1u);
+    s_last = prev == gridDim.x - 1;
+    if (s_last) st->cnt_tr = 0u;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x < 32) {
+    double d = 0.0, e = 0.0;
+    for (int t = threadIdx.x; t < (int)gridDim.x; t += 32) {
+      d += __ldcg(&b.blk[4 * t + 0]);
+      e = fmax(e, __ldcg(&b.blk[4 * t + 1]));
+    }
+    d = warp_sum_d(d);
+    e = warp_max_d(e);
+    if (threadIdx.x == 0) {
+      st->t = (p.restart && d < 0.0) ? 1.0 : tn;
+      st->eps = e;
+      st->k += 1;
+      st->sum_active += (double)n_act;
+    }
+  }
+}
+
+// r_{k+1} = y' - q_{k+1}, P_{k+1}; clears the accumulator for the next pass.
+__global__ void __launch_bounds__(256) k_resid(Params p, Buffers b, int slot) {
+  DevState* st = b.st;
+  if (st->done) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double pv = 0.0;
+  if (i < p.m) {
+    const double q = b.qacc[i];
+    b.qacc[i] = 0.0;
+    const double r = ((double)b.yh[i] - q) + (double)b.yl[i];
+    float h, l;
+    split_double(r, h, l);
+    b.rh[i] = h;
+    b.rl[i] = l;
+    const double rv = (double)h + (double)l;
+    pv = 0.5 * rv * rv;
+  }
+  __shared__ double sh[8];
+  pv = warp_sum_d(pv);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = pv;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int w = 0; w < 8; ++w) a += sh[w];
+    b.tileP[blockIdx.x] = a;
+  }
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(&st->cnt_resid, 1u);
+    s_last = prev == gridDim.x - 1;
+    if (s_last) st->cnt_resid = 0u;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x < 32) {
+    double a = 0.0;
+    for (int t = threadIdx.x; t < (int)gridDim.x; t += 32) a += __ldcg(&b.tileP[t]);
+    a = warp_sum_d(a);
+    if (threadIdx.x == 0) st->P[slot ^ 1] = a;
+  }
+}
+
+size_t pass_smem_bytes(int lda, int m4, int nstages) {
+  const size_t st = (size_t)nstages;
+  return st * (size_t)lda * 4 + (size_t)m4 * 8 + (st + 1) * 8 + 3 * st * 8 + 64;
+}
+
+// Largest stage count that fits, or 0 when the fused pass cannot be used for this m.
+int pass_configure(int lda, int m4, int smem_optin, int* qwarps) {
+  const int m4q = m4 / 4;
+  int qw = 0;
+  if (m4q <= 32 * 4 * kPassTmax) qw = 4;
+  else if (m4q <= 32 * 8 * kPassTmax) qw = 8;
+  else return 0;
+  int ns = kPassMaxStages;
+  while (ns >= 4 && pass_smem_bytes(lda, m4, ns) + 1024 > (size_t)smem_optin) --ns;
+  if (ns < 4) return 0;
+  const int bytes = (int)pass_smem_bytes(lda, m4, ns);
+  cudaError_t e;
+  if (qw == 4) {
+    e = cudaFuncSetAttribute(k_pass<kX2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass<kF32, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  } else {
+    e = cudaFuncSetAttribute(k_pass<kX2, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass<kF32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  }
+  if (e != cudaSuccess) return 0;
+  *qwarps = qw;
+  return ns;
+}
+
+cudaError_t launch_pass(const Params& p, const Buffers& b, int slot, int precision, bool gap_iter,
+                        int grid, int nstages, int qwarps, cudaStream_t s) {
+  const size_t sm = pass_smem_bytes(p.lda, p.m4, nstages);
+  const int g = gap_iter ? 1 : 0;
+  if (qwarps == 4) {
+    if (precision == kX2) k_pass<kX2, 4><<<grid, 32 * (1 + kPassDot + 4), sm, s>>>(p, b, slot, g, nstages);
+    else k_pass<kF32, 4><<<grid, 32 * (1 + kPassDot + 4), sm, s>>>(p, b, slot, g, nstages);
+  } else {
+    if (precision == kX2) k_pass<kX2, 8><<<grid, 32 * (1 + kPassDot + 8), sm, s>>>(p, b, slot, g, nstages);
+    else k_pass<kF32, 8><<<grid, 32 * (1 + kPassDot + 8), sm, s>>>(p, b, slot, g, nstages);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_resid(const Params& p, const Buffers& b, int slot, cudaStream_t s) {
+  k_resid<<<(p.m + 255) / 256, 256, 0, s>>>(p, b, slot);
+  return cudaGetLastError();
+}
+
+}  // namespace bvls
