@@ -484,33 +484,50 @@ bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const b
   double fwd_ms = 0.0, tr_ms = 0.0;
   int fwd_launches = 0, tr_launches = 0;
   if (o.profile) {
-    if ((int)h->prof.size() < 3 * chunk) {
-      while ((int)h->prof.size() < 3 * chunk) {
-        cudaEvent_t e;
-        CK(cudaEventCreate(&e));
-        h->prof.push_back(e);
-      }
+    // The chunk, with event-record nodes around the product kernels, is captured into a
+    // graph so the events time the kernels without host launch gaps in between.
+    while ((int)h->prof.size() < 3 * chunk) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      h->prof.push_back(e);
     }
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t gx = nullptr;
+    CK(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e1 = enqueue_chunk(h, p, o, chunk, h->prof.data());
+    cudaError_t e2 = cudaStreamEndCapture(h->s, &g);
+    CK(e1);
+    CK(e2);
+    cudaError_t e3 = cudaGraphInstantiate(&gx, g, 0);
+    cudaGraphDestroy(g);
+    CK(e3);
     int k_before = 0;
-    for (long long c = 0; c < max_chunks; ++c) {
-      CK(enqueue_chunk(h, p, o, chunk, h->prof.data()));
+    bvls_status pst = BVLS_OK;
+    for (long long c = 0; c < max_chunks && pst == BVLS_OK; ++c) {
+      cudaError_t e = cudaGraphLaunch(gx, h->s);
       ++chunks_run;
       DevState hs;
-      CK(cudaMemcpyAsync(&hs, h->b.st, sizeof(DevState), cudaMemcpyDeviceToHost, h->s));
-      CK(cudaStreamSynchronize(h->s));
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, h->b.st, sizeof(DevState), cudaMemcpyDeviceToHost, h->s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
+      if (e != cudaSuccess) {
+        pst = set_err(BVLS_ECUDA, "profile chunk: %s", cudaGetErrorString(e));
+        break;
+      }
       const int ran = std::min(chunk, hs.k - k_before);
       for (int j = 0; j < ran; ++j) {
         float a = 0.f, b2 = 0.f;
-        CK(cudaEventElapsedTime(&a, h->prof[3 * j], h->prof[3 * j + 1]));
-        CK(cudaEventElapsedTime(&b2, h->prof[3 * j + 1], h->prof[3 * j + 2]));
-        fwd_ms += a;
-        tr_ms += b2;
+        cudaEventElapsedTime(&a, h->prof[3 * j], h->prof[3 * j + 1]);
+        cudaEventElapsedTime(&b2, h->prof[3 * j + 1], h->prof[3 * j + 2]);
+        tr_ms += fused ? a : b2;
+        fwd_ms += fused ? b2 : a;
       }
       fwd_launches += ran;
       tr_launches += ran;
       k_before = hs.k;
       if (hs.done) break;
     }
+    cudaGraphExecDestroy(gx);
+    if (pst != BVLS_OK) return pst;
   } else {
     GraphKey key{K, o.screening, o.precision, o.restart, max_iter, o.single_pass, o.tol, p.invL};
     if (!h->have_graph || !(h->key == key) || h->chunk_len != chunk) {

@@ -361,11 +361,18 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_tr(Params p, Buffers b, int s
   __syncthreads();
 
   const int n_act = st->n_active;
-  const double tk = st->t;
-  const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk * tk));
-  const double beta = (tk - 1.0) / tn;
-  const double rnorm = sqrt(2.0 * st->P[slot]) * (1.0 + 1e-6);
-  const double eta_g = p.Cg * rnorm;
+  __shared__ double s_scal[3];   // float64 is slow here: scalars once per block
+  if (threadIdx.x == 0) {
+    const double tk = st->t;
+    const double tn0 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk * tk));
+    s_scal[0] = (tk - 1.0) / tn0;
+    s_scal[1] = tn0;
+    s_scal[2] = p.Cg * sqrt(2.0 * st->P[slot]) * (1.0 + 1e-6);
+  }
+  __syncthreads();
+  const double beta = s_scal[0];
+  const double tn = s_scal[1];
+  const double eta_g = s_scal[2];
   const bool want_eps = gap_iter && p.dual_mode == kTranslation;
   const double* __restrict__ xc = b.x[slot];
   double* xn = b.x[slot ^ 1];

@@ -81,6 +81,7 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
   uint64_t* xready = full + nstages;
   uint64_t* empty = xready + nstages;
   __shared__ double s_red[2][kPassDot];
+  __shared__ double s_scal[3];   // beta, t_{k+1} (no restart), eta_g: computed once per CTA
   __shared__ int s_err;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -97,6 +98,12 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
     }
     fence_barrier_init();
     s_err = 0;
+    // float64 runs at a small fraction of the float32 rate: scalars once per CTA
+    const double tk = st->t;
+    const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk * tk));
+    s_scal[0] = (tk - 1.0) / tn;
+    s_scal[1] = tn;
+    s_scal[2] = p.Cg * sqrt(2.0 * st->P[slot]) * (1.0 + 1e-6);
   }
   if (threadIdx.x < 2 * kPassDot) (&s_red[0][0])[threadIdx.x] = 0.0;
   for (int i = threadIdx.x; i < m4q; i += blockDim.x) {
@@ -105,9 +112,8 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
   }
   __syncthreads();
 
-  const double tk = st->t;
-  const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk * tk));
-  const double beta = (tk - 1.0) / tn;
+  const double beta = s_scal[0];
+  const double tn = s_scal[1];
 
   if (warp == 0) {
     // ---------------------------------------------------------------- producer
@@ -132,8 +138,7 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
   } else if (warp <= kPassDot) {
     // ---------------------------------------------------------------- dot warps
     const int dw = warp - 1;
-    const double rnorm = sqrt(2.0 * st->P[slot]) * (1.0 + 1e-6);
-    const double eta_g = p.Cg * rnorm;
+    const double eta_g = s_scal[2];
     const bool want_eps = gap_iter && p.dual_mode == kTranslation;
     const double* __restrict__ xc = b.x[slot];
     double* xn = b.x[slot ^ 1];
@@ -281,31 +286,42 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
   }
 }
 
-// r_{k+1} = y' - q_{k+1}, P_{k+1}; clears the accumulator for the next pass.
+// r_{k+1} = y' - q_{k+1}, P_{k+1}; clears the accumulator for the next pass.  The float64
+// accumulator is split once into a double-float pair; the rest runs in float32 pairs.
 __global__ void __launch_bounds__(256) k_resid(Params p, Buffers b, int slot) {
   DevState* st = b.st;
   if (st->done) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double pv = 0.0;
+  float ps = 0.f, pc = 0.f;
   if (i < p.m) {
     const double q = b.qacc[i];
     b.qacc[i] = 0.0;
-    const double r = ((double)b.yh[i] - q) + (double)b.yl[i];
-    float h, l;
-    split_double(r, h, l);
-    b.rh[i] = h;
-    b.rl[i] = l;
-    const double rv = (double)h + (double)l;
-    pv = 0.5 * rv * rv;
+    float qh, ql;
+    split_double(q, qh, ql);
+    float dh, de;
+    two_sum(b.yh[i], -qh, dh, de);
+    de += b.yl[i] - ql;
+    float rh, rl;
+    two_sum(dh, de, rh, rl);
+    b.rh[i] = rh;
+    b.rl[i] = rl;
+    // 1/2 r^2 as a double-float: exact square of rh plus the cross term
+    const float sq = rh * rh;
+    ps = 0.5f * sq;
+    pc = 0.5f * (fmaf(rh, rh, -sq) + 2.0f * rh * rl);
   }
-  __shared__ double sh[8];
-  pv = warp_sum_d(pv);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = pv;
+  for (int o = 16; o > 0; o >>= 1) {
+    const float os = __shfl_xor_sync(0xffffffffu, ps, o);
+    const float oc = __shfl_xor_sync(0xffffffffu, pc, o);
+    df_add(ps, pc, os, oc);
+  }
+  __shared__ float2 sh[8];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = make_float2(ps, pc);
   __syncthreads();
   if (threadIdx.x == 0) {
-    double a = 0.0;
-    for (int w = 0; w < 8; ++w) a += sh[w];
-    b.tileP[blockIdx.x] = a;
+    float a = 0.f, c = 0.f;
+    for (int w = 0; w < 8; ++w) df_add(a, c, sh[w].x, sh[w].y);
+    b.tileP[blockIdx.x] = df_to_double(a, c);
   }
   __shared__ int s_last;
   __threadfence();
@@ -318,11 +334,10 @@ __global__ void __launch_bounds__(256) k_resid(Params p, Buffers b, int slot) {
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  if (threadIdx.x < 32) {
+  if (threadIdx.x == 0) {
     double a = 0.0;
-    for (int t = threadIdx.x; t < (int)gridDim.x; t += 32) a += __ldcg(&b.tileP[t]);
-    a = warp_sum_d(a);
-    if (threadIdx.x == 0) st->P[slot ^ 1] = a;
+    for (int t = 0; t < (int)gridDim.x; ++t) a += __ldcg(&b.tileP[t]);
+    st->P[slot ^ 1] = a;
   }
 }
 
