@@ -209,7 +209,7 @@ def roofline(solver, y_dev, m):
     name = max(kern, key=lambda k: kern[k][0])
     ms, by, launches = kern[name]
     avg_s = ms / 1000.0 / max(1, launches)
-    achieved = by / max(1, launches) / avg_s / 1e9
+    achieved = by / max(1, launches) / avg_s / 1e9 if avg_s > 0 else None
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(peaks_path):
         peak = float(json.load(open(peaks_path))["hbm_gbs"])
@@ -227,7 +227,7 @@ def roofline(solver, y_dev, m):
                  "achieved_gbs": (v[1] / max(1, v[2])) / (v[0] / 1000.0 / max(1, v[2])) / 1e9 if v[0] else None}
              for k, v in kern.items()}
     return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "peak_source": src,
-            "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+            "unit": "GB/s", "frac": achieved / peak if achieved else None, "traffic": traffic,
             "algorithmic_bytes_per_launch": by / max(1, launches), "avg_launch_us": avg_s * 1e6,
             "kernels": other, "profile_iters": info["iters"]}
 

@@ -171,21 +171,23 @@ cudaError_t enqueue_chunk(bvls_handle* h, const Params& p, const bvls_opts& o, i
   for (int j = 0; j < chunk_len && e == cudaSuccess; ++j) {
     const int slot = j & 1;
     const bool gap_iter = ((j + 1) % o.screen_every) == 0;
-    if (ev) cudaEventRecord(ev[3 * j], h->s);
+    // External records: inside a captured graph they become event-record nodes that time
+    // the kernels (a plain record would only become a dependency edge).
+    if (ev) cudaEventRecordWithFlags(ev[3 * j], h->s, cudaEventRecordExternal);
     if (h->pass_stages > 0 && o.single_pass) {
       // fused: one read of A_S gives g_k and q_{k+1}; then r_{k+1} = y' - q_{k+1}
       e = launch_pass(p, h->b, slot, o.precision, gap_iter, h->num_sms, h->pass_stages, h->pass_qw, h->s);
       if (e != cudaSuccess) break;
-      if (ev) cudaEventRecord(ev[3 * j + 1], h->s);
+      if (ev) cudaEventRecordWithFlags(ev[3 * j + 1], h->s, cudaEventRecordExternal);
       e = launch_resid(p, h->b, slot, h->s);
     } else {
       e = launch_fwd(p, h->b, slot, o.precision, false, h->s);
       if (e != cudaSuccess) break;
-      if (ev) cudaEventRecord(ev[3 * j + 1], h->s);
+      if (ev) cudaEventRecordWithFlags(ev[3 * j + 1], h->s, cudaEventRecordExternal);
       e = launch_tr(p, h->b, slot, o.precision, gap_iter, h->tr_blocks, h->s);
     }
     if (e != cudaSuccess) break;
-    if (ev) cudaEventRecord(ev[3 * j + 2], h->s);
+    if (ev) cudaEventRecordWithFlags(ev[3 * j + 2], h->s, cudaEventRecordExternal);
     if (gap_iter) {
       e = launch_gap(p, h->b, slot, !scr, h->red_blocks, h->s);
       if (e == cudaSuccess && scr) {
@@ -376,7 +378,7 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
   {
     int optin = 0;
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    h->pass_stages = pass_configure(h->lda, h->m4, optin, &h->pass_qw);
+    h->pass_stages = pass_configure(h->lda, h->m4, (n + h->num_sms - 1) / h->num_sms, optin, &h->pass_qw);
     cudaGetLastError();
   }
   h->tr_blocks = h->num_sms * std::max(1, std::min(bps, 2));
@@ -516,8 +518,8 @@ bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const b
       const int ran = std::min(chunk, hs.k - k_before);
       for (int j = 0; j < ran; ++j) {
         float a = 0.f, b2 = 0.f;
-        cudaEventElapsedTime(&a, h->prof[3 * j], h->prof[3 * j + 1]);
-        cudaEventElapsedTime(&b2, h->prof[3 * j + 1], h->prof[3 * j + 2]);
+        CK(cudaEventElapsedTime(&a, h->prof[3 * j], h->prof[3 * j + 1]));
+        CK(cudaEventElapsedTime(&b2, h->prof[3 * j + 1], h->prof[3 * j + 2]));
         tr_ms += fused ? a : b2;
         fwd_ms += fused ? b2 : a;
       }

@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
   uint64_t* full = reinterpret_cast<uint64_t*>(sx + nstages + (nstages & 1));
   uint64_t* xready = full + nstages;
   uint64_t* empty = xready + nstages;
+  int* sidx = reinterpret_cast<int*>(empty + nstages);   // this CTA's column indices
   __shared__ double s_red[2][kPassDot];
   __shared__ double s_scal[3];   // beta, t_{k+1} (no restart), eta_g: computed once per CTA
   __shared__ int s_err;
@@ -110,6 +111,8 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
     srh[i] = __ldcg(reinterpret_cast<const float4*>(b.rh) + i);
     srl[i] = __ldcg(reinterpret_cast<const float4*>(b.rl) + i);
   }
+  // one coalesced read of the index range instead of a dependent load per column
+  for (int q = threadIdx.x; q < nq; q += blockDim.x) sidx[q] = b.idx[p0 + q];
   __syncthreads();
 
   const double beta = s_scal[0];
@@ -126,7 +129,7 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
           s_err = 1;
           break;
         }
-        const int j = b.idx[p0 + q];
+        const int j = sidx[q];
         mbar_arrive_expect_tx(&full[s], col_bytes);
         bulk_g2s(stages + (size_t)s * p.lda, p.A + (size_t)j * p.lda, col_bytes, &full[s]);
         issued = q + 1;
@@ -148,7 +151,7 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
     for (int q = dw; q < nq; q += kPassDot) {
       const int s = q % nstages;
       const int u = q / nstages;
-      const int j = b.idx[p0 + q];
+      const int j = sidx[q];
       double xk = 0.0, xp = 0.0, gpv = 0.0, lj = 0.0, uj = 0.0, nr = 0.0, wj = 0.0;
       int inf_j = 0;
       if (lane == 0) {  // independent of the column data: issue before waiting
@@ -341,22 +344,21 @@ __global__ void __launch_bounds__(256) k_resid(Params p, Buffers b, int slot) {
   }
 }
 
-size_t pass_smem_bytes(int lda, int m4, int nstages) {
+size_t pass_smem_bytes(int lda, int m4, int nstages, int idx_cap) {
   const size_t st = (size_t)nstages;
-  return st * (size_t)lda * 4 + (size_t)m4 * 8 + (st + 1) * 8 + 3 * st * 8 + 64;
+  return st * (size_t)lda * 4 + (size_t)m4 * 8 + (st + 1) * 8 + 3 * st * 8 + (size_t)idx_cap * 4 + 64;
 }
 
 // Largest stage count that fits, or 0 when the fused pass cannot be used for this m.
-int pass_configure(int lda, int m4, int smem_optin, int* qwarps) {
+// idx_cap: columns per CTA at most (ceil(n / grid)).
+int pass_configure(int lda, int m4, int idx_cap, int smem_optin, int* qwarps) {
   const int m4q = m4 / 4;
-  int qw = 0;
-  if (m4q <= 32 * 4 * kPassTmax) qw = 4;
-  else if (m4q <= 32 * 8 * kPassTmax) qw = 8;
-  else return 0;
+  if (m4q > 32 * 8 * kPassTmax) return 0;
+  const int qw = 8;
   int ns = kPassMaxStages;
-  while (ns >= 4 && pass_smem_bytes(lda, m4, ns) + 1024 > (size_t)smem_optin) --ns;
+  while (ns >= 4 && pass_smem_bytes(lda, m4, ns, idx_cap) + 1024 > (size_t)smem_optin) --ns;
   if (ns < 4) return 0;
-  const int bytes = (int)pass_smem_bytes(lda, m4, ns);
+  const int bytes = (int)pass_smem_bytes(lda, m4, ns, idx_cap);
   cudaError_t e;
   if (qw == 4) {
     e = cudaFuncSetAttribute(k_pass<kX2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -372,7 +374,7 @@ int pass_configure(int lda, int m4, int smem_optin, int* qwarps) {
 
 cudaError_t launch_pass(const Params& p, const Buffers& b, int slot, int precision, bool gap_iter,
                         int grid, int nstages, int qwarps, cudaStream_t s) {
-  const size_t sm = pass_smem_bytes(p.lda, p.m4, nstages);
+  const size_t sm = pass_smem_bytes(p.lda, p.m4, nstages, (p.n + grid - 1) / grid);
   const int g = gap_iter ? 1 : 0;
   if (qwarps == 4) {
     if (precision == kX2) k_pass<kX2, 4><<<grid, 32 * (1 + kPassDot + 4), sm, s>>>(p, b, slot, g, nstages);
