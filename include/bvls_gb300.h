@@ -163,6 +163,38 @@ BVLS_API bvls_status bvls_setup(const float* A, int m, int n, int lda, const dou
 BVLS_API bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const bvls_opts* opts,
                        double* x_out, uint8_t* screened_out, bvls_info* info);
 
+/*
+ * One-call solve that allocates nothing.  The paper has no counterpart: this is a service
+ * for callers that cannot allocate device memory -- code that runs inside a memory pool or
+ * allocator it does not own, code inside a framework's CUDA stream capture (where
+ * cudaMalloc is not permitted), or a plug-in whose host application forbids allocations
+ * after start-up.  It runs the same kernels as bvls_setup + bvls_solve, but all scratch
+ * lives in one static device array of 4 MiB that every GPU loading this library holds
+ * until the process exits; no cudaMalloc, cudaFree, pinned host memory, CUDA graph or
+ * event is created.
+ *   A             device memory, column-major float32, read in place; lda a multiple of 32;
+ *                 rows m..lda-1 of each column are read and must be finite (zero them).
+ *   l, u          host; n doubles or NULL (0 / +inf), as in bvls_setup.
+ *   y             any; m float32.  x0: any; n doubles or NULL.
+ *   opts          host or NULL (defaults).  opts->profile is ignored.
+ *   stream        a cudaStream_t (0 allowed); the call returns when its outputs are written.
+ *   x_out, screened_out, info: as in bvls_solve.
+ * Limits: m <= 4096, n <= 16384 and a scratch layout that fits the 4 MiB array; larger
+ * problems get BVLS_ENOTSUP with the size in bvls_last_error() (use bvls_setup then).
+ * The translation direction for columns with u_j = +inf is t = -1 when it is interior,
+ * else theta = 0 (bvls_setup also tries further candidates).  The step constant comes from
+ * opts->lipschitz when > 0, else from the same power iteration as bvls_setup.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.  Every call
+ * reuses the same array, which keeps the previous call's contents (each call clears what
+ * must start at zero); calls whose GPU work overlaps -- from two threads or on two streams
+ * -- race on it and must be serialised by the caller.
+ */
+BVLS_API bvls_status bvls_solve_static(const float* A, int m, int n, int lda, const double* l,
+                                       const double* u, const float* y, const double* x0,
+                                       const bvls_opts* opts, void* stream, double* x_out,
+                                       uint8_t* screened_out, bvls_info* info);
+
 /* Release the handle and its device memory (NULL is ignored). */
 BVLS_API void bvls_destroy(bvls_handle* h);
 

@@ -20,7 +20,8 @@ BVLS_DUAL_SCALING, BVLS_DUAL_TRANSLATION, BVLS_DUAL_ZERO = 0, 1, 2
 DUAL_NAMES = {0: "scaling", 1: "translation", 2: "zero"}
 
 # Every symbol the header declares; tests check that the library exports all of them.
-EXPORTED = ("bvls_default_opts", "bvls_setup", "bvls_solve", "bvls_destroy", "bvls_last_error")
+EXPORTED = ("bvls_default_opts", "bvls_setup", "bvls_solve", "bvls_destroy", "bvls_last_error",
+            "bvls_solve_static")
 
 
 class bvls_opts(ctypes.Structure):
@@ -85,6 +86,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.bvls_destroy.restype = None
     lib.bvls_last_error.argtypes = []
     lib.bvls_last_error.restype = ctypes.c_char_p
+    lib.bvls_solve_static.argtypes = [vp, ci, ci, ci, vp, vp, vp, vp, ctypes.POINTER(bvls_opts), vp, vp, vp,
+                                      ctypes.POINTER(bvls_info)]
+    lib.bvls_solve_static.restype = ci
     _lib = lib
     return lib
 
@@ -111,6 +115,16 @@ def bvls_solve(h: int, y_ptr: int, x0_ptr: int | None, opts: bvls_opts | None, x
     info = bvls_info()
     st = load().bvls_solve(h, y_ptr, x0_ptr, ctypes.byref(opts) if opts is not None else None,
                            x_out_ptr, screened_ptr, ctypes.byref(info))
+    return st, info
+
+
+def bvls_solve_static(A_ptr: int, m: int, n: int, lda: int, l_ptr: int | None, u_ptr: int | None,
+                      y_ptr: int, x0_ptr: int | None, opts: bvls_opts | None, stream: int | None,
+                      x_out_ptr: int, screened_ptr: int | None) -> tuple[int, bvls_info]:
+    info = bvls_info()
+    st = load().bvls_solve_static(A_ptr, m, n, lda, l_ptr, u_ptr, y_ptr, x0_ptr,
+                                  ctypes.byref(opts) if opts is not None else None, stream or 0,
+                                  x_out_ptr, screened_ptr, ctypes.byref(info))
     return st, info
 
 

@@ -217,6 +217,8 @@ bvls_status validate_opts(const bvls_opts& o) {
 
 }  // namespace
 
+void bvls::record_error(const char* msg) { g_err = msg; }
+
 extern "C" {
 
 void bvls_default_opts(bvls_opts* o) {

@@ -182,6 +182,9 @@ cudaError_t launch_pass(const Params& p, const Buffers& b, int slot, int precisi
 cudaError_t launch_resid(const Params& p, const Buffers& b, int slot, cudaStream_t s);
 cudaError_t tr_configure(int m4, int* blocks_per_sm);
 
+// Record the text returned by bvls_last_error() on this thread (capi.cu).
+void record_error(const char* msg);
+
 // Setup kernels (setup_kernels.cu).
 cudaError_t launch_check_finite(const float* A, int lda, int m, int n, int* flag, cudaStream_t s);
 cudaError_t launch_col_norms(const float* A, int lda, int m, int n, double* nrm, cudaStream_t s);
