@@ -169,7 +169,7 @@ BVLS_API bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0
  * allocator it does not own, code inside a framework's CUDA stream capture (where
  * cudaMalloc is not permitted), or a plug-in whose host application forbids allocations
  * after start-up.  It runs the same kernels as bvls_setup + bvls_solve, but all scratch
- * lives in one static device array of 4 MiB that every GPU loading this library holds
+ * lives in one static device array of 8 MiB that every GPU loading this library holds
  * until the process exits; no cudaMalloc, cudaFree, pinned host memory, CUDA graph or
  * event is created.
  *   A             device memory, column-major float32, read in place; lda a multiple of 32;
@@ -179,7 +179,7 @@ BVLS_API bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0
  *   opts          host or NULL (defaults).  opts->profile is ignored.
  *   stream        a cudaStream_t (0 allowed); the call returns when its outputs are written.
  *   x_out, screened_out, info: as in bvls_solve.
- * Limits: m <= 4096, n <= 16384 and a scratch layout that fits the 4 MiB array; larger
+ * Limits: m <= 4096, n <= 16384 and a scratch layout that fits the 8 MiB array; larger
  * problems get BVLS_ENOTSUP with the size in bvls_last_error() (use bvls_setup then).
  * The translation direction for columns with u_j = +inf is t = -1 when it is interior,
  * else theta = 0 (bvls_setup also tries further candidates).  The step constant comes from

@@ -55,6 +55,7 @@ struct bvls_handle {
   cudaEvent_t ev_in = nullptr, poll[2] = {nullptr, nullptr};
   float* A = nullptr;
   double *l = nullptr, *u = nullptr, *nrm = nullptr, *w = nullptr, *t = nullptr;
+  float2 *l2 = nullptr, *u2 = nullptr;
   uint8_t* jinf = nullptr;
   double t_norm = 0.0, gamma_w = 0.0, L = 0.0;
   int dual_mode = kScaling;
@@ -145,8 +146,11 @@ Params make_params(const bvls_handle* h, const bvls_opts& o, int max_iter) {
   p.nrm = h->nrm;
   p.w = h->w;
   p.jinf = h->jinf;
+  p.l2 = h->l2;
+  p.u2 = h->u2;
   const double L = o.lipschitz > 0.0 ? o.lipschitz : h->L;
   p.invL = 1.0 / L;
+  p.invL2 = df2_from_double(p.invL);
   p.t_norm = h->t_norm;
   p.gamma_w = h->gamma_w;
   p.Cg = h->Cg[o.precision];
@@ -179,7 +183,7 @@ cudaError_t enqueue_chunk(bvls_handle* h, const Params& p, const bvls_opts& o, i
       e = launch_pass(p, h->b, slot, o.precision, gap_iter, h->num_sms, h->pass_stages, h->pass_qw, h->s);
       if (e != cudaSuccess) break;
       if (ev) cudaEventRecordWithFlags(ev[3 * j + 1], h->s, cudaEventRecordExternal);
-      e = launch_resid(p, h->b, slot, h->s);
+      e = launch_resid(p, h->b, slot, h->num_sms, h->s);
     } else {
       e = launch_fwd(p, h->b, slot, o.precision, false, h->s);
       if (e != cudaSuccess) break;
@@ -294,6 +298,18 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
   TRY(dalloc(h, &h->t, m));
   CK(cudaMemcpyAsync(h->l, lv.data(), sizeof(double) * n, cudaMemcpyHostToDevice, h->s));
   CK(cudaMemcpyAsync(h->u, uv.data(), sizeof(double) * n, cudaMemcpyHostToDevice, h->s));
+  {
+    std::vector<float2> l2(n), u2(n);
+    for (int j = 0; j < n; ++j) {
+      l2[j] = df2_from_double(lv[j]);
+      u2[j] = df2_from_double(uv[j]);
+    }
+    TRY(dalloc(h, &h->l2, n));
+    TRY(dalloc(h, &h->u2, n));
+    CK(cudaMemcpyAsync(h->l2, l2.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, h->s));
+    CK(cudaMemcpyAsync(h->u2, u2.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, h->s));
+    CK(cudaStreamSynchronize(h->s));
+  }
   CK(cudaMemcpyAsync(h->jinf, jinf.data(), n, cudaMemcpyHostToDevice, h->s));
   CK(cudaMemsetAsync(h->w, 0, sizeof(double) * n, h->s));
   CK(launch_col_norms(h->A, h->lda, m, n, h->nrm, h->s));
@@ -401,12 +417,12 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
   TRY(dalloc(h, &b.rh, h->m4));
   TRY(dalloc(h, &b.rl, h->m4));
   TRY(dalloc(h, &b.part, (size_t)h->fwd_chunks * h->lda));
-  TRY(dalloc(h, &b.tileP, h->fwd_tiles));
+  TRY(dalloc(h, &b.tileP, (h->lda + 31) / 32));   // >= fwd_tiles and >= the residual kernel's grid
   TRY(dalloc(h, &b.tile_cnt, h->fwd_tiles));
   TRY(dalloc(h, &b.blk, 4 * (size_t)max_blocks));
   TRY(dalloc(h, &b.st, 1));
-  TRY(dalloc(h, &b.qacc, h->m4));
-  CK(cudaMemsetAsync(b.qacc, 0, sizeof(double) * h->m4, h->s));
+  TRY(dalloc(h, &b.qpart, (size_t)h->num_sms * h->m4));
+  TRY(dalloc(h, &b.xout, n));
   TRY(dalloc(h, &h->y_dev, h->m4));
   TRY(dalloc(h, &h->x0_dev, n));
   CK(cudaMemsetAsync(b.tile_cnt, 0, sizeof(unsigned) * h->fwd_tiles, h->s));
@@ -424,8 +440,11 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
     h->Cg[kF32] = 1.01 * (d_g + 2.0) * kU + kU;
     const int per = (n + h->fwd_chunks - 1) / h->fwd_chunks;
     const int d_f = ((per + kFwdWarps - 1) / kFwdWarps + 1) / 2 + 4 + h->fwd_chunks + 1;
-    h->Cf[kX2] = 2.0 * (d_f + 2.0) * (d_f + 2.0) * kU * kU + 2.0 * kU * kU;
-    h->Cf[kF32] = 1.01 * (d_f + 2.0) * kU + kU;
+    // the fused pass: a q-warp lane sums its CTA's columns, then 8 warps x nparts/8 partials
+    const int d_p = (n + h->num_sms - 1) / h->num_sms + (h->num_sms + 7) / 8 + 8;
+    const int d = std::max(d_f, d_p);
+    h->Cf[kX2] = 2.0 * (d + 2.0) * (d + 2.0) * kU * kU + 2.0 * kU * kU;
+    h->Cf[kF32] = 1.01 * (d + 2.0) * kU + kU;
     h->Csub = 8.0 * kU * kU;
   }
   CK(cudaStreamSynchronize(h->s));
@@ -570,7 +589,8 @@ bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const b
   CK(cudaMemcpy(&hs, h->b.st, sizeof(DevState), cudaMemcpyDeviceToHost));
   if (hs.nonfinite) return set_err(BVLS_ENONFINITE, "y or x0 contains NaN or Inf");
   if (hs.error) return set_err(BVLS_ETIMEOUT, "a device-side wait exceeded its bound; results discarded");
-  CK(cudaMemcpyAsync(x_out, h->b.x[hs.out_slot], sizeof(double) * h->n, cudaMemcpyDefault, h->s));
+  CK(launch_export(p, h->b, hs.out_slot, h->s));
+  CK(cudaMemcpyAsync(x_out, h->b.xout, sizeof(double) * h->n, cudaMemcpyDefault, h->s));
   if (screened_out)
     CK(cudaMemcpyAsync(screened_out, h->b.flags, h->n, cudaMemcpyDefault, h->s));
   CK(cudaStreamSynchronize(h->s));

@@ -71,7 +71,10 @@ struct Params {
   const double* nrm;       // ||a_j||_2
   const double* w;         // a_j^T t (translation mode)
   const uint8_t* jinf;     // 1 if u_j = +inf
+  const float2* l2;        // l and u as double-float pairs (for the step's clip)
+  const float2* u2;
   double invL;             // 1 / L
+  float2 invL2;            // 1 / L as a double-float pair
   double t_norm;           // ||t||_2
   double gamma_w;          // |w_j (stored) - a_j^T t| <= gamma_w ||a_j|| ||t||
   double Cg;               // |g (computed) - a_j^T r| <= Cg ||a_j|| ||r||
@@ -129,6 +132,56 @@ __device__ __forceinline__ void split_double(double x, float& h, float& l) {
   l = (float)(x - (double)h);
 }
 
+// ---- double-float values as float2 (x = hi, y = lo), float32 arithmetic only ----------
+// The per-iteration path keeps x and g in this form: float64 runs at a small fraction of
+// the float32 rate on this part, and these pairs carry about 48 significant bits.
+__device__ __forceinline__ float2 df2_norm(float s, float c) {
+  float h, l;
+  two_sum(s, c, h, l);
+  return make_float2(h, l);
+}
+
+__device__ __forceinline__ float2 df2_add(float2 a, float2 b) {
+  float s, e;
+  two_sum(a.x, b.x, s, e);
+  e += a.y + b.y;
+  float h, l;
+  two_sum(s, e, h, l);
+  return make_float2(h, l);
+}
+
+__device__ __forceinline__ float2 df2_sub(float2 a, float2 b) {
+  return df2_add(a, make_float2(-b.x, -b.y));
+}
+
+__device__ __forceinline__ float2 df2_mul(float2 a, float2 b) {
+  const float p = a.x * b.x;
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  float h, l;
+  fast_two_sum(p, e, h, l);
+  return make_float2(h, l);
+}
+
+// a < b for normalised pairs (|lo| <= ulp(hi)/2); infinities carry lo = 0
+__device__ __forceinline__ bool df2_lt(float2 a, float2 b) {
+  return a.x < b.x || (a.x == b.x && a.y < b.y);
+}
+
+__device__ __forceinline__ bool df2_eq(float2 a, float2 b) { return a.x == b.x && a.y == b.y; }
+
+__device__ __forceinline__ bool df2_nonzero(float2 a) { return a.x != 0.0f || a.y != 0.0f; }
+
+__device__ __forceinline__ double df2_to_double(float2 a) { return (double)a.x + (double)a.y; }
+
+// float64 -> pair; +-inf map to (+-inf, 0)
+__host__ __device__ __forceinline__ float2 df2_from_double(double x) {
+  const float h = (float)x;
+  if (isinf(h) || isinf(x)) return make_float2(h, 0.0f);
+  return make_float2(h, (float)(x - (double)h));
+}
+
 __device__ __forceinline__ double warp_sum_d(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -145,8 +198,8 @@ __device__ __forceinline__ double warp_max_d(double v) {
 // ---------------------------------------------------------------- launch wrappers
 // Iteration kernels (iter_kernels.cu).
 struct Buffers {
-  double* x[2];
-  double* g[2];
+  float2* x[2];           // iterates x_k (slot k & 1), double-float
+  float2* g[2];           // correlations g_k = A_S^T r_k (slot k & 1), double-float
   int* idx;
   int* idx_tmp;
   int* fold;
@@ -159,7 +212,8 @@ struct Buffers {
   double* tileP;
   unsigned int* tile_cnt;
   double* blk;            // per-block partials of the epilogue kernels (4 doubles each)
-  double* qacc;           // float64 accumulator of A_S x_S for the fused pass (m entries)
+  float2* qpart;          // fused pass: per-CTA double-float partials of A_S x_S (grid x m4)
+  double* xout;           // float64 copy of the returned iterate (n)
   DevState* st;
   const float* y_in;      // device copy of y
   const double* x0_in;    // device copy of x0 or null
@@ -179,7 +233,8 @@ size_t tr_smem_bytes(int m4);
 int pass_configure(int lda, int m4, int idx_cap, int smem_optin, int* qwarps);
 cudaError_t launch_pass(const Params& p, const Buffers& b, int slot, int precision, bool gap_iter,
                         int grid, int nstages, int qwarps, cudaStream_t s);
-cudaError_t launch_resid(const Params& p, const Buffers& b, int slot, cudaStream_t s);
+cudaError_t launch_resid(const Params& p, const Buffers& b, int slot, int nparts, cudaStream_t s);
+cudaError_t launch_export(const Params& p, const Buffers& b, int slot, cudaStream_t s);
 cudaError_t tr_configure(int m4, int* blocks_per_sm);
 
 // Record the text returned by bvls_last_error() on this thread (capi.cu).

@@ -150,10 +150,13 @@ __global__ void k_init_arrays(Params p, Buffers b) {
       x = 0.0;
     }
     x = fmin(fmax(x, p.l[j]), p.u[j]);
-    b.x[0][j] = x;
-    b.x[1][j] = x;
-    b.g[0][j] = 0.0;
-    b.g[1][j] = 0.0;
+    float2 x2 = df2_from_double(x);
+    if (df2_lt(x2, p.l2[j])) x2 = p.l2[j];   // keep the pair inside the box exactly
+    if (df2_lt(p.u2[j], x2)) x2 = p.u2[j];
+    b.x[0][j] = x2;
+    b.x[1][j] = x2;
+    b.g[0][j] = make_float2(0.f, 0.f);
+    b.g[1][j] = make_float2(0.f, 0.f);
     b.idx[j] = j;
     b.flags[j] = 0;
   }
@@ -187,7 +190,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd(Params p, Buffers b, int sl
   const int cnt = FOLD ? st->n_fold : st->n_active;
   if (FOLD && cnt == 0) return;
   const int* list = FOLD ? b.fold : b.idx;
-  const double* __restrict__ xv = b.x[slot];
+  const float2* __restrict__ xv = b.x[slot];
   const int nch = gridDim.y;
   const int per = (cnt + nch - 1) / nch;
   const int cb = blockIdx.y * per;
@@ -213,7 +216,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd(Params p, Buffers b, int sl
     int pos[2];
     bool keep[2];
     int j_c[2];
-    double x_c[2];
+    float2 x_c[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int q = threadIdx.x + h * kFwdThreads;
@@ -221,7 +224,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd(Params p, Buffers b, int sl
       if (q < nb) {
         j_c[h] = list[base + q];
         x_c[h] = xv[j_c[h]];
-        keep[h] = x_c[h] != 0.0;
+        keep[h] = df2_nonzero(x_c[h]);
       }
     }
     int total = 0;
@@ -241,11 +244,9 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd(Params p, Buffers b, int sl
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       if (keep[h]) {
-        float xh, xl;
-        split_double(x_c[h], xh, xl);
         s_col[pos[h]] = j_c[h];
-        s_xh[pos[h]] = xh;
-        s_xl[pos[h]] = xl;
+        s_xh[pos[h]] = x_c[h].x;
+        s_xl[pos[h]] = PREC == kX2 ? x_c[h].y : 0.0f;
       }
     }
     __syncthreads();
@@ -370,19 +371,21 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_tr(Params p, Buffers b, int s
     s_scal[2] = p.Cg * sqrt(2.0 * st->P[slot]) * (1.0 + 1e-6);
   }
   __syncthreads();
-  const double beta = s_scal[0];
   const double tn = s_scal[1];
   const double eta_g = s_scal[2];
+  const float2 bb = df2_from_double(s_scal[0]);
+  const float2 onepb = df2_from_double(1.0 + s_scal[0]);
   const bool want_eps = gap_iter && p.dual_mode == kTranslation;
-  const double* __restrict__ xc = b.x[slot];
-  double* xn = b.x[slot ^ 1];
-  const double* __restrict__ gp = b.g[slot ^ 1];
-  double* gc = b.g[slot];
+  const float2* __restrict__ xc = b.x[slot];
+  float2* xn = b.x[slot ^ 1];
+  const float2* __restrict__ gp = b.g[slot ^ 1];
+  float2* gc = b.g[slot];
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int gw = blockIdx.x * kTrWarps + warp;
   const int nw = gridDim.x * kTrWarps;
-  double dot = 0.0, epsm = 0.0;
+  float2 dot = make_float2(0.f, 0.f);
+  double epsm = 0.0;
 
   for (int pp = 2 * gw; pp < n_act; pp += 2 * nw) {
     const int j0 = b.idx[pp];
@@ -418,23 +421,23 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_tr(Params p, Buffers b, int s
     if (lane < 2) {
       const int j = lane == 0 ? j0 : j1;
       if (j >= 0) {
-        const double g = lane == 0 ? (PREC == kX2 ? df_to_double(sA[0], cA[0]) : (double)sA[0])
-                                   : (PREC == kX2 ? df_to_double(sB[0], cB[0]) : (double)sB[0]);
-        const double xk = xc[j];
-        const double xp = xn[j];
-        const double gpv = gp[j];
-        const double gv = (1.0 + beta) * g - beta * gpv;      // = a_j^T (y' - A v_k)
-        const double v = xk + beta * (xk - xp);
-        double xnew = v + gv * p.invL;
-        xnew = fmin(fmax(xnew, p.l[j]), p.u[j]);
+        const float2 g = lane == 0 ? df2_norm(sA[0], PREC == kX2 ? cA[0] : 0.f)
+                                   : df2_norm(sB[0], PREC == kX2 ? cB[0] : 0.f);
+        const float2 xk = xc[j];
+        const float2 xp = xn[j];
+        const float2 gv = df2_sub(df2_mul(onepb, g), df2_mul(bb, gp[j]));   // a_j^T (y' - A v_k)
+        const float2 v = df2_add(xk, df2_mul(bb, df2_sub(xk, xp)));
+        float2 xnew = df2_add(v, df2_mul(gv, p.invL2));
+        if (df2_lt(xnew, p.l2[j])) xnew = p.l2[j];
+        if (df2_lt(p.u2[j], xnew)) xnew = p.u2[j];
         xn[j] = xnew;
         gc[j] = g;
-        dot += gv * (xnew - xk);
+        dot = df2_add(dot, df2_mul(gv, df2_sub(xnew, xk)));
         if (want_eps && p.jinf[j]) {
           const double nr = p.nrm[j];
           if (nr > 0.0) {
             const double den = -p.w[j] - p.gamma_w * nr * p.t_norm;
-            epsm = fmax(epsm, fmax(g + eta_g * nr, 0.0) / den);
+            epsm = fmax(epsm, fmax(df2_to_double(g) + eta_g * nr, 0.0) / den);
           }
         }
       }
@@ -442,21 +445,26 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_tr(Params p, Buffers b, int s
   }
 
   // block reduction of (dot, eps) and the grid-wide finish in the last block
-  __shared__ double sh[64];
-  dot = warp_sum_d(dot);
+  __shared__ float2 shd[32][2];
+  __shared__ double she[32];
+  {
+    const float2 o = make_float2(__shfl_down_sync(0xffffffffu, dot.x, 1), __shfl_down_sync(0xffffffffu, dot.y, 1));
+    if (lane == 0) dot = df2_add(dot, o);   // lanes 0 and 1 carry the values
+  }
   epsm = warp_max_d(epsm);
   if (lane == 0) {
-    sh[warp] = dot;
-    sh[32 + warp] = epsm;
+    shd[warp][0] = dot;
+    she[warp] = epsm;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double d = 0.0, e = 0.0;
+    float2 d = make_float2(0.f, 0.f);
+    double e = 0.0;
     for (int w = 0; w < kTrWarps; ++w) {
-      d += sh[w];
-      e = fmax(e, sh[32 + w]);
+      d = df2_add(d, shd[w][0]);
+      e = fmax(e, she[w]);
     }
-    b.blk[4 * blockIdx.x + 0] = d;
+    b.blk[4 * blockIdx.x + 0] = df2_to_double(d);
     b.blk[4 * blockIdx.x + 1] = e;
   }
   if (!last_block(&st->cnt_tr, gridDim.x)) return;
@@ -498,17 +506,17 @@ __global__ void __launch_bounds__(kRedThreads) k_gap(Params p, Buffers b, int sl
   const int n_act = st->n_active;
   const bool trans = p.dual_mode == kTranslation;
   const double eps = trans ? st->eps : 0.0;
-  const double* __restrict__ xc = b.x[slot];
-  const double* __restrict__ gc = b.g[slot];
+  const float2* __restrict__ xc = b.x[slot];
+  const float2* __restrict__ gc = b.g[slot];
   double v[3] = {0.0, 0.0, 0.0};  // sum h_j, sum c_j ||a_j||, sum |x_j| ||a_j||
   const int stride = gridDim.x * blockDim.x;
   for (int pp = blockIdx.x * blockDim.x + threadIdx.x; pp < n_act; pp += stride) {
     const int j = b.idx[pp];
-    const double x = xc[j];
+    const double x = df2_to_double(xc[j]);
     const double nr = p.nrm[j];
     v[2] += fabs(x) * nr;
     if (p.dual_mode != kZero) {
-      const double gt = gc[j] + (trans ? eps * p.w[j] : 0.0);
+      const double gt = df2_to_double(gc[j]) + (trans ? eps * p.w[j] : 0.0);
       const double lj = p.l[j];
       if (p.jinf[j]) {
         v[0] += (x - lj) * fmax(-gt, 0.0);
@@ -582,29 +590,29 @@ __global__ void __launch_bounds__(kRedThreads) k_test(Params p, Buffers b, int s
   const bool trans = p.dual_mode == kTranslation;
   const double eps = trans ? st->eps : 0.0;
   const double rr = st->radius * (1.0 + 1e-12) + st->eta;
-  const double* __restrict__ xc = b.x[slot];
-  const double* __restrict__ xn = b.x[slot ^ 1];
-  const double* __restrict__ gc = b.g[slot];
+  const float2* __restrict__ xc = b.x[slot];
+  const float2* __restrict__ xn = b.x[slot ^ 1];
+  const float2* __restrict__ gc = b.g[slot];
   int cnt = 0;
   const int stride = gridDim.x * blockDim.x;
   for (int pp = blockIdx.x * blockDim.x + threadIdx.x; pp < n_act; pp += stride) {
     const int j = b.idx[pp];
     const double nr = p.nrm[j];
     if (!(nr > 0.0)) continue;
-    const double gt = gc[j] + (trans ? eps * p.w[j] : 0.0);
+    const double gt = df2_to_double(gc[j]) + (trans ? eps * p.w[j] : 0.0);
     const double thr = rr * nr * (1.0 + 1e-12);
     int pin = 0;
-    double bnd = 0.0;
+    float2 bnd = make_float2(0.f, 0.f);
     if (gt < -thr) {
       pin = 1;
-      bnd = p.l[j];
+      bnd = p.l2[j];
     } else if (!p.jinf[j] && gt > thr) {
       pin = 2;
-      bnd = p.u[j];
+      bnd = p.u2[j];
     }
     // Fixed once x_k and x_{k+1} both sit at that bound: the stored g_k then stays the
     // gradient of the reduced problem and the momentum needs no correction.
-    if (pin && xc[j] == bnd && xn[j] == bnd) {
+    if (pin && df2_eq(xc[j], bnd) && df2_eq(xn[j], bnd)) {
       b.flags[j] = (uint8_t)pin;
       ++cnt;
     }
@@ -661,14 +669,14 @@ __global__ void __launch_bounds__(kCompactThreads) k_compact(Params p, Buffers b
     return;
   }
   const int n_act = st->n_active;
-  const double* xc = b.x[slot];
+  const float2* xc = b.x[slot];
   const int per = (n_act + kCompactThreads - 1) / kCompactThreads;
   const int q0 = min(n_act, threadIdx.x * per), q1 = min(n_act, q0 + per);
   int keep = 0, fold = 0;
   for (int q = q0; q < q1; ++q) {
     const int j = b.idx[q];
     if (!b.flags[j]) ++keep;
-    else if (xc[j] != 0.0) ++fold;
+    else if (df2_nonzero(xc[j])) ++fold;
   }
   int nkeep, nfold;
   int ok = block_excl_scan(keep, sh, nkeep);
@@ -678,9 +686,9 @@ __global__ void __launch_bounds__(kCompactThreads) k_compact(Params p, Buffers b
     const int j = b.idx[q];
     if (!b.flags[j]) {
       b.idx_tmp[ok++] = j;
-    } else if (xc[j] != 0.0) {
+    } else if (df2_nonzero(xc[j])) {
       b.fold[of++] = j;
-      sabs += fabs(xc[j]) * p.nrm[j];
+      sabs += fabs(df2_to_double(xc[j])) * p.nrm[j];
     }
   }
   sabs = warp_sum_d(sabs);

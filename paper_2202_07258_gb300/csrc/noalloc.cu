@@ -21,7 +21,7 @@ using namespace bvls;
 
 namespace {
 
-constexpr size_t kStaticBytes = size_t(4) << 20;  // 4 MiB
+constexpr size_t kStaticBytes = size_t(8) << 20;  // 8 MiB
 constexpr int kStaticMaxM = 4096;
 constexpr int kStaticMaxN = 16384;
 constexpr int kMaxDevices = 64;
@@ -47,11 +47,14 @@ struct Arena {
   }
 };
 
-__global__ void k_fill_bounds(double* l, double* u, uint8_t* jinf, int n, int have_l, int have_u) {
+__global__ void k_fill_bounds(double* l, double* u, float2* l2, float2* u2, uint8_t* jinf, int n,
+                              int have_l, int have_u) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     if (!have_l) l[j] = 0.0;
     if (!have_u) u[j] = INFINITY;
     jinf[j] = isinf(u[j]) ? 1 : 0;
+    l2[j] = df2_from_double(l[j]);
+    u2[j] = df2_from_double(u[j]);
   }
 }
 
@@ -71,6 +74,7 @@ __global__ void k_dir_check(const double* w, const double* nrm, const uint8_t* j
 struct Layout {
   Buffers b;
   double *l, *u, *nrm, *w, *t, *scal;
+  float2 *l2, *u2;
   uint8_t* jinf;
   float *y, *v, *v2, *q;
   double* x0;
@@ -79,13 +83,13 @@ struct Layout {
 };
 
 Layout carve(unsigned char* base, int m, int n, int m4, int lda, int fwd_tiles, int fwd_chunks,
-             int max_blocks) {
+             int max_blocks, int sms) {
   Arena a{base, 0};
   Layout L{};
-  L.b.x[0] = a.take<double>(n);
-  L.b.x[1] = a.take<double>(n);
-  L.b.g[0] = a.take<double>(n);
-  L.b.g[1] = a.take<double>(n);
+  L.b.x[0] = a.take<float2>(n);
+  L.b.x[1] = a.take<float2>(n);
+  L.b.g[0] = a.take<float2>(n);
+  L.b.g[1] = a.take<float2>(n);
   L.b.idx = a.take<int>(n);
   L.b.idx_tmp = a.take<int>(n);
   L.b.fold = a.take<int>(n);
@@ -95,13 +99,16 @@ Layout carve(unsigned char* base, int m, int n, int m4, int lda, int fwd_tiles, 
   L.b.rh = a.take<float>(m4);
   L.b.rl = a.take<float>(m4);
   L.b.part = a.take<float2>((size_t)fwd_chunks * lda);
-  L.b.tileP = a.take<double>(fwd_tiles);
+  L.b.tileP = a.take<double>((lda + 31) / 32);
   L.b.tile_cnt = a.take<unsigned int>(fwd_tiles);
   L.b.blk = a.take<double>(4 * (size_t)max_blocks);
   L.b.st = a.take<DevState>(1);
-  L.b.qacc = a.take<double>(m4);
+  L.b.qpart = a.take<float2>((size_t)sms * m4);
+  L.b.xout = a.take<double>(n);
   L.l = a.take<double>(n);
   L.u = a.take<double>(n);
+  L.l2 = a.take<float2>(n);
+  L.u2 = a.take<float2>(n);
   L.nrm = a.take<double>(n);
   L.w = a.take<double>(n);
   L.jinf = a.take<uint8_t>(n);
@@ -193,7 +200,7 @@ bvls_status bvls_solve_static(const float* A, int m, int n, int lda, const doubl
   const int pass_stages = pass_configure(lda, m4, (n + sms - 1) / sms, optin, &pass_qw);
   cudaGetLastError();
 
-  const Layout need = carve(nullptr, m, n, m4, lda, fwd_tiles, fwd_chunks, max_blocks);
+  const Layout need = carve(nullptr, m, n, m4, lda, fwd_tiles, fwd_chunks, max_blocks, sms);
   if (need.bytes > kStaticBytes) {
     char msg[160];
     snprintf(msg, sizeof(msg), "problem needs %zu bytes of scratch > %zu static bytes", need.bytes,
@@ -201,13 +208,12 @@ bvls_status bvls_solve_static(const float* A, int m, int n, int lda, const doubl
     return fail(BVLS_ENOTSUP, msg);
   }
   Layout W = carve(static_cast<unsigned char*>(g_scratch_dev[dev]), m, n, m4, lda, fwd_tiles, fwd_chunks,
-                   max_blocks);
+                   max_blocks, sms);
   Buffers& b = W.b;
 
   // Clear what must start at zero (the array keeps the previous call's contents).
   SCK(cudaMemsetAsync(b.tile_cnt, 0, sizeof(unsigned) * fwd_tiles, s));
   SCK(cudaMemsetAsync(b.st, 0, sizeof(DevState), s));
-  SCK(cudaMemsetAsync(b.qacc, 0, sizeof(double) * m4, s));
   SCK(cudaMemsetAsync(W.y, 0, sizeof(float) * m4, s));
   SCK(cudaMemsetAsync(W.w, 0, sizeof(double) * n, s));
   SCK(cudaMemsetAsync(W.flag, 0, 2 * sizeof(int), s));
@@ -216,7 +222,7 @@ bvls_status bvls_solve_static(const float* A, int m, int n, int lda, const doubl
   SCK(launch_check_finite(A, lda, lda, n, W.flag, s));
   if (l) SCK(cudaMemcpyAsync(W.l, l, sizeof(double) * n, cudaMemcpyHostToDevice, s));
   if (u) SCK(cudaMemcpyAsync(W.u, u, sizeof(double) * n, cudaMemcpyHostToDevice, s));
-  k_fill_bounds<<<64, 256, 0, s>>>(W.l, W.u, W.jinf, n, l != nullptr, u != nullptr);
+  k_fill_bounds<<<64, 256, 0, s>>>(W.l, W.u, W.l2, W.u2, W.jinf, n, l != nullptr, u != nullptr);
   SCK(cudaGetLastError());
   SCK(launch_col_norms(A, lda, m, n, W.nrm, s));
   int dual_mode = kScaling;
@@ -264,13 +270,17 @@ bvls_status bvls_solve_static(const float* A, int m, int n, int lda, const doubl
   p.nrm = W.nrm;
   p.w = W.w;
   p.jinf = W.jinf;
+  p.l2 = W.l2;
+  p.u2 = W.u2;
   p.invL = 1.0 / Lc;
+  p.invL2 = df2_from_double(p.invL);
   p.t_norm = t_norm;
   p.gamma_w = gamma_w;
   {
     const int d_g = (m4 / 4 + 31) / 32 + 7;
     const int per = (n + fwd_chunks - 1) / fwd_chunks;
-    const int d_f = ((per + kFwdWarps - 1) / kFwdWarps + 1) / 2 + 4 + fwd_chunks + 1;
+    const int d_f0 = ((per + kFwdWarps - 1) / kFwdWarps + 1) / 2 + 4 + fwd_chunks + 1;
+    const int d_f = std::max(d_f0, (n + sms - 1) / sms + (sms + 7) / 8 + 8);
     if (o.precision == BVLS_PREC_FP32X2) {
       p.Cg = 2.0 * (d_g + 2.0) * (d_g + 2.0) * kU * kU + 4.0 * kU * kU + 2.0 * kU64;
       p.Cf = 2.0 * (d_f + 2.0) * (d_f + 2.0) * kU * kU + 2.0 * kU * kU;
@@ -313,7 +323,7 @@ bvls_status bvls_solve_static(const float* A, int m, int n, int lda, const doubl
       const bool gap_iter = ((j + 1) % K) == 0;
       if (fused) {
         SCK(launch_pass(p, b, slot, o.precision, gap_iter, sms, pass_stages, pass_qw, s));
-        SCK(launch_resid(p, b, slot, s));
+        SCK(launch_resid(p, b, slot, sms, s));
       } else {
         SCK(launch_fwd(p, b, slot, o.precision, false, s));
         SCK(launch_tr(p, b, slot, o.precision, gap_iter, tr_blocks, s));
@@ -336,7 +346,8 @@ bvls_status bvls_solve_static(const float* A, int m, int n, int lda, const doubl
   }
   if (hs.nonfinite) return fail(BVLS_ENONFINITE, "y or x0 contains NaN or Inf");
   if (hs.error) return fail(BVLS_ETIMEOUT, "a device-side wait exceeded its bound; results discarded");
-  SCK(cudaMemcpyAsync(x_out, b.x[hs.out_slot], sizeof(double) * n, cudaMemcpyDefault, s));
+  SCK(launch_export(p, b, hs.out_slot, s));
+  SCK(cudaMemcpyAsync(x_out, b.xout, sizeof(double) * n, cudaMemcpyDefault, s));
   if (screened_out) SCK(cudaMemcpyAsync(screened_out, b.flags, n, cudaMemcpyDefault, s));
   SCK(cudaStreamSynchronize(s));
   if (info) {

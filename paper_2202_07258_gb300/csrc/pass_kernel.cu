@@ -16,10 +16,14 @@
 //             and an `xready` mbarrier;
 //   q         QW warps, each owning a fixed slice of rows: q_slice += a_j x_{k+1,j} in
 //             double-float registers over every column of the CTA; columns with
-//             x_{k+1,j} = 0 are skipped.  At the end each row partial is added to a float64
-//             accumulator in global memory (FP64 atomics).
+//             x_{k+1,j} = 0 are skipped.  At the end the CTA writes its row partials
+//             (double-float) to a per-CTA slice of a global buffer.
 // A stage is released (`empty` mbarrier) when its dot warp and all q warps are done.
-// k_resid then forms r_{k+1} = y' - q and P_{k+1} = 1/2 ||r_{k+1}||^2 and clears q.
+// k_resid then sums the partials and forms r_{k+1} = y' - q and P_{k+1} = 1/2 ||r_{k+1}||^2.
+// The per-column step runs in double-float float32 arithmetic: float64 instructions are
+// slow on this part and would sit on the path from a column's dot product to its x_{k+1,j}.
+#include <algorithm>
+
 #include "common.cuh"
 #include "tma.cuh"
 
@@ -81,8 +85,10 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
   uint64_t* xready = full + nstages;
   uint64_t* empty = xready + nstages;
   int* sidx = reinterpret_cast<int*>(empty + nstages);   // this CTA's column indices
-  __shared__ double s_red[2][kPassDot];
+  __shared__ float2 s_dot[kPassDot];
+  __shared__ double s_eps[kPassDot];
   __shared__ double s_scal[3];   // beta, t_{k+1} (no restart), eta_g: computed once per CTA
+  __shared__ float2 s_beta2[2];  // beta and 1 + beta as double-float pairs
   __shared__ int s_err;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -102,11 +108,17 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
     // float64 runs at a small fraction of the float32 rate: scalars once per CTA
     const double tk = st->t;
     const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk * tk));
-    s_scal[0] = (tk - 1.0) / tn;
+    const double beta = (tk - 1.0) / tn;
+    s_scal[0] = beta;
     s_scal[1] = tn;
     s_scal[2] = p.Cg * sqrt(2.0 * st->P[slot]) * (1.0 + 1e-6);
+    s_beta2[0] = df2_from_double(beta);
+    s_beta2[1] = df2_from_double(1.0 + beta);
   }
-  if (threadIdx.x < 2 * kPassDot) (&s_red[0][0])[threadIdx.x] = 0.0;
+  if (threadIdx.x < kPassDot) {
+    s_dot[threadIdx.x] = make_float2(0.f, 0.f);
+    s_eps[threadIdx.x] = 0.0;
+  }
   for (int i = threadIdx.x; i < m4q; i += blockDim.x) {
     srh[i] = __ldcg(reinterpret_cast<const float4*>(b.rh) + i);
     srl[i] = __ldcg(reinterpret_cast<const float4*>(b.rl) + i);
@@ -115,7 +127,6 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
   for (int q = threadIdx.x; q < nq; q += blockDim.x) sidx[q] = b.idx[p0 + q];
   __syncthreads();
 
-  const double beta = s_scal[0];
   const double tn = s_scal[1];
 
   if (warp == 0) {
@@ -142,24 +153,27 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
     // ---------------------------------------------------------------- dot warps
     const int dw = warp - 1;
     const double eta_g = s_scal[2];
+    const float2 bb = s_beta2[0], onepb = s_beta2[1];
     const bool want_eps = gap_iter && p.dual_mode == kTranslation;
-    const double* __restrict__ xc = b.x[slot];
-    double* xn = b.x[slot ^ 1];
-    const double* __restrict__ gp = b.g[slot ^ 1];
-    double* gc = b.g[slot];
-    double dot = 0.0, epsm = 0.0;
+    const float2* __restrict__ xc = b.x[slot];
+    float2* xn = b.x[slot ^ 1];
+    const float2* __restrict__ gp = b.g[slot ^ 1];
+    float2* gc = b.g[slot];
+    float2 dot = make_float2(0.f, 0.f);
+    double epsm = 0.0;
     for (int q = dw; q < nq; q += kPassDot) {
       const int s = q % nstages;
       const int u = q / nstages;
       const int j = sidx[q];
-      double xk = 0.0, xp = 0.0, gpv = 0.0, lj = 0.0, uj = 0.0, nr = 0.0, wj = 0.0;
+      float2 xk = make_float2(0.f, 0.f), xp = xk, gpv = xk, lj = xk, uj = xk;
+      double nr = 0.0, wj = 0.0;
       int inf_j = 0;
       if (lane == 0) {  // independent of the column data: issue before waiting
         xk = xc[j];
         xp = xn[j];
         gpv = gp[j];
-        lj = p.l[j];
-        uj = p.u[j];
+        lj = p.l2[j];
+        uj = p.u2[j];
         if (want_eps) {
           nr = p.nrm[j];
           wj = p.w[j];
@@ -186,26 +200,27 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
       __syncwarp();
       if (lane == 0) {
         mbar_arrive(&empty[s]);  // this warp is done reading the stage
-        const double g = PREC == kX2 ? df_to_double(sa[0], ca[0]) : (double)sa[0];
-        const double gv = (1.0 + beta) * g - beta * gpv;   // a_j^T (y' - A v_k)
-        const double v = xk + beta * (xk - xp);
-        double xnew = fmin(fmax(v + gv * p.invL, lj), uj);
-        float xh, xl;
-        split_double(xnew, xh, xl);
-        sx[s] = make_float2(xh, PREC == kX2 ? xl : 0.0f);
+        // FISTA step in double-float arithmetic (no float64 on this path)
+        const float2 g = df2_norm(sa[0], PREC == kX2 ? ca[0] : 0.0f);
+        const float2 gv = df2_sub(df2_mul(onepb, g), df2_mul(bb, gpv));   // a_j^T (y' - A v_k)
+        const float2 v = df2_add(xk, df2_mul(bb, df2_sub(xk, xp)));
+        float2 xnew = df2_add(v, df2_mul(gv, p.invL2));
+        if (df2_lt(xnew, lj)) xnew = lj;
+        if (df2_lt(uj, xnew)) xnew = uj;
+        sx[s] = PREC == kX2 ? xnew : make_float2(xnew.x, 0.0f);
         mbar_arrive(&xready[s]);
         xn[j] = xnew;
         gc[j] = g;
-        dot += gv * (xnew - xk);
+        dot = df2_add(dot, df2_mul(gv, df2_sub(xnew, xk)));
         if (want_eps && inf_j && nr > 0.0) {
           const double den = -wj - p.gamma_w * nr * p.t_norm;
-          epsm = fmax(epsm, fmax(g + eta_g * nr, 0.0) / den);
+          epsm = fmax(epsm, fmax(df2_to_double(g) + eta_g * nr, 0.0) / den);
         }
       }
     }
     if (lane == 0) {
-      s_red[0][dw] = dot;
-      s_red[1][dw] = epsm;
+      s_dot[dw] = dot;
+      s_eps[dw] = epsm;
     }
   } else {
     // ---------------------------------------------------------------- q warps
@@ -234,29 +249,27 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);
     }
-    if (nq > 0) {
+    // per-CTA partials of A_S x_{k+1} (every row written, zeros included)
+    float2* part = b.qpart + (size_t)blockIdx.x * p.m4;
 #pragma unroll
-      for (int t = 0; t < kPassTmax; ++t) {
-        const int c4 = qw * 32 + lane + t * 32 * QW;
-        if (c4 < m4q) {
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const int row = 4 * c4 + c;
-            const double v = PREC == kX2 ? df_to_double(qs[t][c], qc[t][c]) : (double)qs[t][c];
-            if (row < p.m && v != 0.0) atomicAdd(&b.qacc[row], v);
-          }
-        }
+    for (int t = 0; t < kPassTmax; ++t) {
+      const int c4 = qw * 32 + lane + t * 32 * QW;
+      if (c4 < m4q) {
+        float4* dst = reinterpret_cast<float4*>(part + 4 * c4);
+        dst[0] = make_float4(qs[t][0], PREC == kX2 ? qc[t][0] : 0.f, qs[t][1], PREC == kX2 ? qc[t][1] : 0.f);
+        dst[1] = make_float4(qs[t][2], PREC == kX2 ? qc[t][2] : 0.f, qs[t][3], PREC == kX2 ? qc[t][3] : 0.f);
       }
     }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double d = 0.0, e = 0.0;
+    float2 d = make_float2(0.f, 0.f);
+    double e = 0.0;
     for (int w = 0; w < kPassDot; ++w) {
-      d += s_red[0][w];
-      e = fmax(e, s_red[1][w]);
+      d = df2_add(d, s_dot[w]);
+      e = fmax(e, s_eps[w]);
     }
-    b.blk[4 * blockIdx.x + 0] = d;
+    b.blk[4 * blockIdx.x + 0] = df2_to_double(d);
     b.blk[4 * blockIdx.x + 1] = e;
     if (s_err) atomicOr(&st->error, 1);
   }
@@ -289,42 +302,45 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
   }
 }
 
-// r_{k+1} = y' - q_{k+1}, P_{k+1}; clears the accumulator for the next pass.  The float64
-// accumulator is split once into a double-float pair; the rest runs in float32 pairs.
-__global__ void __launch_bounds__(256) k_resid(Params p, Buffers b, int slot) {
+// r_{k+1} = y' - q_{k+1} and P_{k+1} = 1/2 ||r_{k+1}||^2 from the per-CTA partials of the
+// pass, in double-float arithmetic.  Block: 32 rows (one per lane) x 8 warps over the
+// partials; the summation order is fixed, so r is reproducible run to run.
+__global__ void __launch_bounds__(256) k_resid(Params p, Buffers b, int slot, int nparts) {
   DevState* st = b.st;
   if (st->done) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  float ps = 0.f, pc = 0.f;
-  if (i < p.m) {
-    const double q = b.qacc[i];
-    b.qacc[i] = 0.0;
-    float qh, ql;
-    split_double(q, qh, ql);
-    float dh, de;
-    two_sum(b.yh[i], -qh, dh, de);
-    de += b.yl[i] - ql;
-    float rh, rl;
-    two_sum(dh, de, rh, rl);
-    b.rh[i] = rh;
-    b.rl[i] = rl;
-    // 1/2 r^2 as a double-float: exact square of rh plus the cross term
-    const float sq = rh * rh;
-    ps = 0.5f * sq;
-    pc = 0.5f * (fmaf(rh, rh, -sq) + 2.0f * rh * rl);
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    const float os = __shfl_xor_sync(0xffffffffu, ps, o);
-    const float oc = __shfl_xor_sync(0xffffffffu, pc, o);
-    df_add(ps, pc, os, oc);
-  }
-  __shared__ float2 sh[8];
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = make_float2(ps, pc);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int row = blockIdx.x * 32 + lane;
+  float s = 0.f, c = 0.f;
+  if (row < p.m4)
+    for (int t = warp; t < nparts; t += 8) {
+      const float2 v = __ldcg(&b.qpart[(size_t)t * p.m4 + row]);
+      df_add(s, c, v.x, v.y);
+    }
+  __shared__ float2 sh[8][32];
+  __shared__ float2 sp[32];
+  sh[warp][lane] = make_float2(s, c);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    float a = 0.f, c = 0.f;
-    for (int w = 0; w < 8; ++w) df_add(a, c, sh[w].x, sh[w].y);
-    b.tileP[blockIdx.x] = df_to_double(a, c);
+  if (warp == 0) {
+    for (int w = 1; w < 8; ++w) df_add(s, c, sh[w][lane].x, sh[w][lane].y);
+    float ps = 0.f, pc = 0.f;
+    if (row < p.m) {
+      float dh, de;
+      two_sum(b.yh[row], -s, dh, de);
+      de += b.yl[row] - c;
+      float rh, rl;
+      two_sum(dh, de, rh, rl);
+      b.rh[row] = rh;
+      b.rl[row] = rl;
+      const float sq = rh * rh;           // 1/2 r^2 as a double-float
+      ps = 0.5f * sq;
+      pc = 0.5f * (fmaf(rh, rh, -sq) + 2.0f * rh * rl);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const float os = __shfl_xor_sync(0xffffffffu, ps, o);
+      const float oc = __shfl_xor_sync(0xffffffffu, pc, o);
+      df_add(ps, pc, os, oc);
+    }
+    if (lane == 0) b.tileP[blockIdx.x] = df_to_double(ps, pc);
   }
   __shared__ int s_last;
   __threadfence();
@@ -342,6 +358,12 @@ __global__ void __launch_bounds__(256) k_resid(Params p, Buffers b, int slot) {
     for (int t = 0; t < (int)gridDim.x; ++t) a += __ldcg(&b.tileP[t]);
     st->P[slot ^ 1] = a;
   }
+}
+
+// x_out (float64) from the double-float iterate of the given slot.
+__global__ void k_export(Params p, Buffers b, int slot) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < p.n; j += gridDim.x * blockDim.x)
+    b.xout[j] = df2_to_double(b.x[slot][j]);
 }
 
 size_t pass_smem_bytes(int lda, int m4, int nstages, int idx_cap) {
@@ -386,8 +408,13 @@ cudaError_t launch_pass(const Params& p, const Buffers& b, int slot, int precisi
   return cudaGetLastError();
 }
 
-cudaError_t launch_resid(const Params& p, const Buffers& b, int slot, cudaStream_t s) {
-  k_resid<<<(p.m + 255) / 256, 256, 0, s>>>(p, b, slot);
+cudaError_t launch_resid(const Params& p, const Buffers& b, int slot, int nparts, cudaStream_t s) {
+  k_resid<<<(p.m4 + 31) / 32, 256, 0, s>>>(p, b, slot, nparts);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_export(const Params& p, const Buffers& b, int slot, cudaStream_t s) {
+  k_export<<<std::min(1024, (p.n + 255) / 256), 256, 0, s>>>(p, b, slot);
   return cudaGetLastError();
 }
 
