@@ -84,7 +84,12 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
   uint64_t* full = reinterpret_cast<uint64_t*>(sx + nstages + (nstages & 1));
   uint64_t* xready = full + nstages;
   uint64_t* empty = xready + nstages;
-  int* sidx = reinterpret_cast<int*>(empty + nstages);   // this CTA's column indices
+  // Uses of each stage issued so far.  mbarrier waits only see the parity of a phase, so a
+  // dot warp (which takes every kPassDot-th column) first waits until the producer has
+  // issued the use it needs: by then the previous use of that stage has landed and been
+  // consumed, and the parity wait on `full` is exact.
+  volatile int* s_issued = reinterpret_cast<volatile int*>(empty + nstages);
+  int* sidx = const_cast<int*>(s_issued) + nstages;   // this CTA's column indices
   __shared__ float2 s_dot[kPassDot];
   __shared__ double s_eps[kPassDot];
   __shared__ double s_scal[3];   // beta, t_{k+1} (no restart), eta_g: computed once per CTA
@@ -102,6 +107,7 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
       mbar_init(&full[s], 1);
       mbar_init(&xready[s], 1);
       mbar_init(&empty[s], 1 + QW);
+      s_issued[s] = 0;
     }
     fence_barrier_init();
     s_err = 0;
@@ -143,6 +149,7 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
         const int j = sidx[q];
         mbar_arrive_expect_tx(&full[s], col_bytes);
         bulk_g2s(stages + (size_t)s * p.lda, p.A + (size_t)j * p.lda, col_bytes, &full[s]);
+        s_issued[s] = u + 1;
         issued = q + 1;
       }
       // The most recent copy into each stage must land before the CTA may exit.
@@ -180,7 +187,7 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
           inf_j = p.jinf[j];
         }
       }
-      if (!warp_all(mbar_wait(&full[s], u & 1))) {
+      if (!warp_all(smem_wait_geq(&s_issued[s], u + 1) && mbar_wait(&full[s], u & 1))) {
         s_err = 1;
         break;
       }
@@ -368,7 +375,8 @@ __global__ void k_export(Params p, Buffers b, int slot) {
 
 size_t pass_smem_bytes(int lda, int m4, int nstages, int idx_cap) {
   const size_t st = (size_t)nstages;
-  return st * (size_t)lda * 4 + (size_t)m4 * 8 + (st + 1) * 8 + 3 * st * 8 + (size_t)idx_cap * 4 + 64;
+  return st * (size_t)lda * 4 + (size_t)m4 * 8 + (st + 1) * 8 + 3 * st * 8 + st * 4 +
+         (size_t)idx_cap * 4 + 64;
 }
 
 // Largest stage count that fits, or 0 when the fused pass cannot be used for this m.
@@ -376,19 +384,13 @@ size_t pass_smem_bytes(int lda, int m4, int nstages, int idx_cap) {
 int pass_configure(int lda, int m4, int idx_cap, int smem_optin, int* qwarps) {
   const int m4q = m4 / 4;
   if (m4q > 32 * 8 * kPassTmax) return 0;
-  const int qw = 8;
+  const int qw = 8;   // q warps; a lane owns up to kPassTmax float4 row chunks
   int ns = kPassMaxStages;
   while (ns >= 4 && pass_smem_bytes(lda, m4, ns, idx_cap) + 1024 > (size_t)smem_optin) --ns;
   if (ns < 4) return 0;
   const int bytes = (int)pass_smem_bytes(lda, m4, ns, idx_cap);
-  cudaError_t e;
-  if (qw == 4) {
-    e = cudaFuncSetAttribute(k_pass<kX2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass<kF32, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  } else {
-    e = cudaFuncSetAttribute(k_pass<kX2, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass<kF32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  }
+  cudaError_t e = cudaFuncSetAttribute(k_pass<kX2, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass<kF32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return 0;
   *qwarps = qw;
   return ns;
@@ -398,13 +400,9 @@ cudaError_t launch_pass(const Params& p, const Buffers& b, int slot, int precisi
                         int grid, int nstages, int qwarps, cudaStream_t s) {
   const size_t sm = pass_smem_bytes(p.lda, p.m4, nstages, (p.n + grid - 1) / grid);
   const int g = gap_iter ? 1 : 0;
-  if (qwarps == 4) {
-    if (precision == kX2) k_pass<kX2, 4><<<grid, 32 * (1 + kPassDot + 4), sm, s>>>(p, b, slot, g, nstages);
-    else k_pass<kF32, 4><<<grid, 32 * (1 + kPassDot + 4), sm, s>>>(p, b, slot, g, nstages);
-  } else {
-    if (precision == kX2) k_pass<kX2, 8><<<grid, 32 * (1 + kPassDot + 8), sm, s>>>(p, b, slot, g, nstages);
-    else k_pass<kF32, 8><<<grid, 32 * (1 + kPassDot + 8), sm, s>>>(p, b, slot, g, nstages);
-  }
+  if (qwarps != 8) return cudaErrorInvalidValue;
+  if (precision == kX2) k_pass<kX2, 8><<<grid, 32 * (1 + kPassDot + 8), sm, s>>>(p, b, slot, g, nstages);
+  else k_pass<kF32, 8><<<grid, 32 * (1 + kPassDot + 8), sm, s>>>(p, b, slot, g, nstages);
   return cudaGetLastError();
 }
 

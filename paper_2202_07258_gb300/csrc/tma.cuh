@@ -55,6 +55,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return true;
 }
 
+// Wait (bounded) until *flag >= target; flag lives in shared memory and is written by
+// another warp of the CTA.
+__device__ __forceinline__ bool smem_wait_geq(const volatile int* flag, int target) {
+  if (*flag >= target) return true;
+  const long long t0 = clock64();
+  while (*flag < target) {
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+  return true;
+}
+
 // Bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) from global memory
 // into this CTA's shared memory; completion is signalled on `bar` as transaction bytes.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
