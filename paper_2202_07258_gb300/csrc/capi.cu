@@ -64,7 +64,7 @@ struct bvls_handle {
   double* x0_dev = nullptr;
   int* pinned = nullptr;
   int fwd_tiles = 0, fwd_chunks = 0, tr_blocks = 0, red_blocks = 0;
-  int pass_stages = 0, pass_qw = 0;  // fused single-pass iteration when pass_stages > 0
+  int pass_stages = 0, pass_qw = 0, pass_cps = 1;  // fused single-pass iteration when pass_stages > 0
   double Cg[2] = {0, 0}, Cf[2] = {0, 0}, Csub = 0.0;
   bool have_graph = false;
   GraphKey key{};
@@ -180,7 +180,8 @@ cudaError_t enqueue_chunk(bvls_handle* h, const Params& p, const bvls_opts& o, i
     if (ev) cudaEventRecordWithFlags(ev[3 * j], h->s, cudaEventRecordExternal);
     if (h->pass_stages > 0 && o.single_pass) {
       // fused: one read of A_S gives g_k and q_{k+1}; then r_{k+1} = y' - q_{k+1}
-      e = launch_pass(p, h->b, slot, o.precision, gap_iter, h->num_sms, h->pass_stages, h->pass_qw, h->s);
+      e = launch_pass(p, h->b, slot, o.precision, gap_iter, h->num_sms, h->pass_stages, h->pass_cps, h->pass_qw,
+                      h->s);
       if (e != cudaSuccess) break;
       if (ev) cudaEventRecordWithFlags(ev[3 * j + 1], h->s, cudaEventRecordExternal);
       e = launch_resid(p, h->b, slot, h->num_sms, h->s);
@@ -396,7 +397,8 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
   {
     int optin = 0;
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    h->pass_stages = pass_configure(h->lda, h->m4, (n + h->num_sms - 1) / h->num_sms, optin, &h->pass_qw);
+    h->pass_stages = pass_configure(h->lda, h->m4, (n + h->num_sms - 1) / h->num_sms, optin, &h->pass_qw,
+                                    &h->pass_cps);
     cudaGetLastError();
   }
   h->tr_blocks = h->num_sms * std::max(1, std::min(bps, 2));

@@ -230,9 +230,9 @@ cudaError_t launch_test(const Params& p, const Buffers& b, int slot, int red_blo
 cudaError_t launch_compact(const Params& p, const Buffers& b, int slot, cudaStream_t s);
 size_t tr_smem_bytes(int m4);
 // Fused single-pass iteration (pass_kernel.cu).
-int pass_configure(int lda, int m4, int idx_cap, int smem_optin, int* qwarps);
+int pass_configure(int lda, int m4, int idx_cap, int smem_optin, int* qwarps, int* cps);
 cudaError_t launch_pass(const Params& p, const Buffers& b, int slot, int precision, bool gap_iter,
-                        int grid, int nstages, int qwarps, cudaStream_t s);
+                        int grid, int nstages, int cps, int qwarps, cudaStream_t s);
 cudaError_t launch_resid(const Params& p, const Buffers& b, int slot, int nparts, cudaStream_t s);
 cudaError_t launch_export(const Params& p, const Buffers& b, int slot, cudaStream_t s);
 cudaError_t tr_configure(int m4, int* blocks_per_sm);

@@ -196,8 +196,8 @@ bvls_status bvls_solve_static(const float* A, int m, int n, int lda, const doubl
   const int tr_blocks = sms * std::max(1, std::min(bps, 2));
   const int red_blocks = std::max(1, std::min(2 * sms, (n + kRedThreads - 1) / kRedThreads));
   const int max_blocks = std::max(std::max(tr_blocks, red_blocks), std::max(64, sms));
-  int pass_qw = 0;
-  const int pass_stages = pass_configure(lda, m4, (n + sms - 1) / sms, optin, &pass_qw);
+  int pass_qw = 0, pass_cps = 1;
+  const int pass_stages = pass_configure(lda, m4, (n + sms - 1) / sms, optin, &pass_qw, &pass_cps);
   cudaGetLastError();
 
   const Layout need = carve(nullptr, m, n, m4, lda, fwd_tiles, fwd_chunks, max_blocks, sms);
@@ -322,7 +322,7 @@ bvls_status bvls_solve_static(const float* A, int m, int n, int lda, const doubl
       const int slot = j & 1;
       const bool gap_iter = ((j + 1) % K) == 0;
       if (fused) {
-        SCK(launch_pass(p, b, slot, o.precision, gap_iter, sms, pass_stages, pass_qw, s));
+        SCK(launch_pass(p, b, slot, o.precision, gap_iter, sms, pass_stages, pass_cps, pass_qw, s));
         SCK(launch_resid(p, b, slot, sms, s));
       } else {
         SCK(launch_fwd(p, b, slot, o.precision, false, s));

@@ -71,17 +71,18 @@ __device__ __forceinline__ void pmerge(float& s, float& c, float s2, float c2) {
 
 template <int PREC, int QW>
 __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
-    k_pass(Params p, Buffers b, int slot, int gap_iter, int nstages) {
+    k_pass(Params p, Buffers b, int slot, int gap_iter, int nstages, int cps) {
   DevState* st = b.st;
   if (st->done) return;
   extern __shared__ __align__(128) unsigned char smem[];
   const int m4q = p.m4 >> 2;
   const uint32_t col_bytes = (uint32_t)p.lda * 4u;
+  const size_t stage_floats = (size_t)cps * p.lda;           // a stage holds cps columns
   float* stages = reinterpret_cast<float*>(smem);
-  float4* srh = reinterpret_cast<float4*>(smem + (size_t)nstages * col_bytes);
+  float4* srh = reinterpret_cast<float4*>(smem + (size_t)nstages * stage_floats * 4);
   float4* srl = srh + m4q;
-  float2* sx = reinterpret_cast<float2*>(srl + m4q);
-  uint64_t* full = reinterpret_cast<uint64_t*>(sx + nstages + (nstages & 1));
+  float2* sx = reinterpret_cast<float2*>(srl + m4q);            // x_{k+1} per stage slot
+  uint64_t* full = reinterpret_cast<uint64_t*>(sx + (size_t)nstages * cps);
   uint64_t* xready = full + nstages;
   uint64_t* empty = xready + nstages;
   // Uses of each stage issued so far.  mbarrier waits only see the parity of a phase, so a
@@ -101,12 +102,13 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
   const int per = (n_act + gridDim.x - 1) / gridDim.x;
   const int p0 = min(n_act, (int)blockIdx.x * per);
   const int nq = min(n_act, p0 + per) - p0;
+  const int ngroups = (nq + cps - 1) / cps;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < nstages; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&xready[s], 1);
-      mbar_init(&empty[s], 1 + QW);
+      mbar_init(&xready[s], cps);        // one arrival per column of the stage
+      mbar_init(&empty[s], cps + QW);    // each column's dot warp and every q warp
       s_issued[s] = 0;
     }
     fence_barrier_init();
@@ -137,24 +139,40 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
 
   if (warp == 0) {
     // ---------------------------------------------------------------- producer
+    // Group g = columns [g*cps, min(nq, (g+1)*cps)) goes to stage g % nstages; columns that
+    // are adjacent in A (runs of the preserved list) travel in one bulk copy.
     if (lane == 0) {
       int issued = 0;
-      for (int q = 0; q < nq; ++q) {
-        const int s = q % nstages;
-        const int u = q / nstages;
+      for (int g = 0; g < ngroups; ++g) {
+        const int s = g % nstages;
+        const int u = g / nstages;
         if (u > 0 && !mbar_wait(&empty[s], (u - 1) & 1)) {
           s_err = 1;
           break;
         }
-        const int j = sidx[q];
-        mbar_arrive_expect_tx(&full[s], col_bytes);
-        bulk_g2s(stages + (size_t)s * p.lda, p.A + (size_t)j * p.lda, col_bytes, &full[s]);
+        const int q0 = g * cps;
+        const int nc = min(cps, nq - q0);
+        mbar_arrive_expect_tx(&full[s], (uint32_t)nc * col_bytes);
+        float* dst = stages + (size_t)s * stage_floats;
+        int c = 0;
+        while (c < nc) {
+          int len = 1;
+          while (c + len < nc && sidx[q0 + c + len] == sidx[q0 + c] + len) ++len;
+          bulk_g2s(dst + (size_t)c * p.lda, p.A + (size_t)sidx[q0 + c] * p.lda, (uint32_t)len * col_bytes,
+                   &full[s]);
+          c += len;
+        }
+        // a short last group: stand in for the missing columns' dot warps
+        for (int k = nc; k < cps; ++k) {
+          mbar_arrive(&xready[s]);
+          mbar_arrive(&empty[s]);
+        }
         s_issued[s] = u + 1;
-        issued = q + 1;
+        issued = g + 1;
       }
       // The most recent copy into each stage must land before the CTA may exit.
-      for (int q = max(0, issued - nstages); q < issued; ++q)
-        if (!mbar_wait(&full[q % nstages], (q / nstages) & 1)) s_err = 1;
+      for (int g = max(0, issued - nstages); g < issued; ++g)
+        if (!mbar_wait(&full[g % nstages], (g / nstages) & 1)) s_err = 1;
     }
   } else if (warp <= kPassDot) {
     // ---------------------------------------------------------------- dot warps
@@ -169,8 +187,10 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
     float2 dot = make_float2(0.f, 0.f);
     double epsm = 0.0;
     for (int q = dw; q < nq; q += kPassDot) {
-      const int s = q % nstages;
-      const int u = q / nstages;
+      const int g = q / cps;
+      const int s = g % nstages;
+      const int u = g / nstages;
+      const int c = q - g * cps;
       const int j = sidx[q];
       float2 xk = make_float2(0.f, 0.f), xp = xk, gpv = xk, lj = xk, uj = xk;
       double nr = 0.0, wj = 0.0;
@@ -191,7 +211,7 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
         s_err = 1;
         break;
       }
-      const float4* col = reinterpret_cast<const float4*>(stages + (size_t)s * p.lda);
+      const float4* col = reinterpret_cast<const float4*>(stages + (size_t)s * stage_floats + (size_t)c * p.lda);
       float sa[4] = {0.f, 0.f, 0.f, 0.f}, ca[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 4
       for (int i = lane; i < m4q; i += 32) pacc4v<PREC>(sa, ca, col[i], srh[i], srl[i]);
@@ -208,20 +228,20 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
       if (lane == 0) {
         mbar_arrive(&empty[s]);  // this warp is done reading the stage
         // FISTA step in double-float arithmetic (no float64 on this path)
-        const float2 g = df2_norm(sa[0], PREC == kX2 ? ca[0] : 0.0f);
-        const float2 gv = df2_sub(df2_mul(onepb, g), df2_mul(bb, gpv));   // a_j^T (y' - A v_k)
+        const float2 g2 = df2_norm(sa[0], PREC == kX2 ? ca[0] : 0.0f);
+        const float2 gv = df2_sub(df2_mul(onepb, g2), df2_mul(bb, gpv));   // a_j^T (y' - A v_k)
         const float2 v = df2_add(xk, df2_mul(bb, df2_sub(xk, xp)));
         float2 xnew = df2_add(v, df2_mul(gv, p.invL2));
         if (df2_lt(xnew, lj)) xnew = lj;
         if (df2_lt(uj, xnew)) xnew = uj;
-        sx[s] = PREC == kX2 ? xnew : make_float2(xnew.x, 0.0f);
+        sx[(size_t)s * cps + c] = PREC == kX2 ? xnew : make_float2(xnew.x, 0.0f);
         mbar_arrive(&xready[s]);
         xn[j] = xnew;
-        gc[j] = g;
+        gc[j] = g2;
         dot = df2_add(dot, df2_mul(gv, df2_sub(xnew, xk)));
         if (want_eps && inf_j && nr > 0.0) {
           const double den = -wj - p.gamma_w * nr * p.t_norm;
-          epsm = fmax(epsm, fmax(df2_to_double(g) + eta_g * nr, 0.0) / den);
+          epsm = fmax(epsm, fmax(df2_to_double(g2) + eta_g * nr, 0.0) / den);
         }
       }
     }
@@ -237,20 +257,23 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
     for (int t = 0; t < kPassTmax; ++t)
 #pragma unroll
       for (int c = 0; c < 4; ++c) qs[t][c] = qc[t][c] = 0.f;
-    for (int q = 0; q < nq; ++q) {
-      const int s = q % nstages;
-      const int u = q / nstages;
+    for (int g = 0; g < ngroups; ++g) {
+      const int s = g % nstages;
+      const int u = g / nstages;
       if (!warp_all(mbar_wait(&xready[s], u & 1) && mbar_wait(&full[s], u & 1))) {
         s_err = 1;
         break;
       }
-      const float2 xv = sx[s];
-      if (xv.x != 0.0f || xv.y != 0.0f) {
-        const float4* col = reinterpret_cast<const float4*>(stages + (size_t)s * p.lda);
+      const int nc = min(cps, nq - g * cps);
+      for (int c = 0; c < nc; ++c) {
+        const float2 xv = sx[(size_t)s * cps + c];
+        if (xv.x != 0.0f || xv.y != 0.0f) {
+          const float4* col = reinterpret_cast<const float4*>(stages + (size_t)s * stage_floats + (size_t)c * p.lda);
 #pragma unroll
-        for (int t = 0; t < kPassTmax; ++t) {
-          const int c4 = qw * 32 + lane + t * 32 * QW;
-          if (c4 < m4q) pacc4<PREC>(qs[t], qc[t], col[c4], xv.x, xv.y);
+          for (int t = 0; t < kPassTmax; ++t) {
+            const int c4 = qw * 32 + lane + t * 32 * QW;
+            if (c4 < m4q) pacc4<PREC>(qs[t], qc[t], col[c4], xv.x, xv.y);
+          }
         }
       }
       __syncwarp();
@@ -318,11 +341,19 @@ __global__ void __launch_bounds__(256) k_resid(Params p, Buffers b, int slot, in
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int row = blockIdx.x * 32 + lane;
   float s = 0.f, c = 0.f;
-  if (row < p.m4)
-    for (int t = warp; t < nparts; t += 8) {
-      const float2 v = __ldcg(&b.qpart[(size_t)t * p.m4 + row]);
-      df_add(s, c, v.x, v.y);
+  if (row < p.m4) {
+    // batches of loads in flight, then the (dependent) double-float additions
+    for (int t0 = warp; t0 < nparts; t0 += 8 * 8) {
+      float2 v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int t = t0 + 8 * k;
+        v[k] = t < nparts ? __ldcg(&b.qpart[(size_t)t * p.m4 + row]) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) df_add(s, c, v[k].x, v[k].y);
     }
+  }
   __shared__ float2 sh[8][32];
   __shared__ float2 sp[32];
   sh[warp][lane] = make_float2(s, c);
@@ -373,36 +404,42 @@ __global__ void k_export(Params p, Buffers b, int slot) {
     b.xout[j] = df2_to_double(b.x[slot][j]);
 }
 
-size_t pass_smem_bytes(int lda, int m4, int nstages, int idx_cap) {
+size_t pass_smem_bytes(int lda, int m4, int nstages, int cps, int idx_cap) {
   const size_t st = (size_t)nstages;
-  return st * (size_t)lda * 4 + (size_t)m4 * 8 + (st + 1) * 8 + 3 * st * 8 + st * 4 +
+  return st * (size_t)cps * lda * 4 + (size_t)m4 * 8 + st * cps * 8 + 3 * st * 8 + st * 4 +
          (size_t)idx_cap * 4 + 64;
 }
 
-// Largest stage count that fits, or 0 when the fused pass cannot be used for this m.
-// idx_cap: columns per CTA at most (ceil(n / grid)).
-int pass_configure(int lda, int m4, int idx_cap, int smem_optin, int* qwarps) {
+// Stage layout for the fused pass: about 32 KB of columns per stage (bulk copies much
+// smaller than that are dominated by their fixed cost) and as many stages as fit.
+// Returns the stage count (0 when the fused pass cannot be used) and the columns per stage.
+int pass_configure(int lda, int m4, int idx_cap, int smem_optin, int* qwarps, int* cps_out) {
   const int m4q = m4 / 4;
   if (m4q > 32 * 8 * kPassTmax) return 0;
   const int qw = 8;   // q warps; a lane owns up to kPassTmax float4 row chunks
-  int ns = kPassMaxStages;
-  while (ns >= 4 && pass_smem_bytes(lda, m4, ns, idx_cap) + 1024 > (size_t)smem_optin) --ns;
-  if (ns < 4) return 0;
-  const int bytes = (int)pass_smem_bytes(lda, m4, ns, idx_cap);
-  cudaError_t e = cudaFuncSetAttribute(k_pass<kX2, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass<kF32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e != cudaSuccess) return 0;
-  *qwarps = qw;
-  return ns;
+  const int col_bytes = lda * 4;
+  for (int cps = std::max(1, std::min(8, 32768 / col_bytes)); cps >= 1; --cps) {
+    int ns = kPassMaxStages;
+    while (ns >= 3 && pass_smem_bytes(lda, m4, ns, cps, idx_cap) + 1024 > (size_t)smem_optin) --ns;
+    if (ns < 3) continue;
+    const int bytes = (int)pass_smem_bytes(lda, m4, ns, cps, idx_cap);
+    cudaError_t e = cudaFuncSetAttribute(k_pass<kX2, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass<kF32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return 0;
+    *qwarps = qw;
+    *cps_out = cps;
+    return ns;
+  }
+  return 0;
 }
 
 cudaError_t launch_pass(const Params& p, const Buffers& b, int slot, int precision, bool gap_iter,
-                        int grid, int nstages, int qwarps, cudaStream_t s) {
-  const size_t sm = pass_smem_bytes(p.lda, p.m4, nstages, (p.n + grid - 1) / grid);
+                        int grid, int nstages, int cps, int qwarps, cudaStream_t s) {
+  const size_t sm = pass_smem_bytes(p.lda, p.m4, nstages, cps, (p.n + grid - 1) / grid);
   const int g = gap_iter ? 1 : 0;
   if (qwarps != 8) return cudaErrorInvalidValue;
-  if (precision == kX2) k_pass<kX2, 8><<<grid, 32 * (1 + kPassDot + 8), sm, s>>>(p, b, slot, g, nstages);
-  else k_pass<kF32, 8><<<grid, 32 * (1 + kPassDot + 8), sm, s>>>(p, b, slot, g, nstages);
+  if (precision == kX2) k_pass<kX2, 8><<<grid, 32 * (1 + kPassDot + 8), sm, s>>>(p, b, slot, g, nstages, cps);
+  else k_pass<kF32, 8><<<grid, 32 * (1 + kPassDot + 8), sm, s>>>(p, b, slot, g, nstages, cps);
   return cudaGetLastError();
 }
 
