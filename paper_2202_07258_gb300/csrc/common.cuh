@@ -190,6 +190,24 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 // All lanes of a warp agree on the outcome of a bounded wait.
 __device__ __forceinline__ bool warp_all(bool ok) { return __all_sync(0xffffffffu, ok) != 0; }
 
+// Sum of v[0..count) by one warp: each lane issues 8 loads before adding them, so every
+// 256 entries cost one round trip to L2.  Result in every lane.
+__device__ __forceinline__ double warp_load_sum(const double* v, int count) {
+  double a = 0.0;
+  for (int t0 = 0; t0 < count; t0 += 256) {
+    double part[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int t = t0 + (threadIdx.x & 31) + 32 * k;
+      part[k] = t < count ? __ldcg(v + t) : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a += part[k];
+  }
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  return a;
+}
+
 __device__ __forceinline__ double warp_max_d(double v) {
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;

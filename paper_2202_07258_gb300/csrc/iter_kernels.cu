@@ -324,9 +324,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd(Params p, Buffers b, int sl
   if (threadIdx.x == 0) b.tileP[blockIdx.x] = pv[0];
   if (!last_block(&st->cnt_fwd, gridDim.x)) return;
   if (threadIdx.x < 32) {
-    double a = 0.0;
-    for (int t = threadIdx.x; t < (int)gridDim.x; t += 32) a += __ldcg(&b.tileP[t]);
-    a = warp_sum_d(a);
+    const double a = warp_load_sum(b.tileP, gridDim.x);
     if (threadIdx.x == 0) st->P[slot] = a;
   }
 }
@@ -470,9 +468,19 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_tr(Params p, Buffers b, int s
   if (!last_block(&st->cnt_tr, gridDim.x)) return;
   if (threadIdx.x < 32) {
     double d = 0.0, e = 0.0;
-    for (int t = threadIdx.x; t < (int)gridDim.x; t += 32) {
-      d += __ldcg(&b.blk[4 * t + 0]);
-      e = fmax(e, __ldcg(&b.blk[4 * t + 1]));
+    for (int t0 = 0; t0 < (int)gridDim.x; t0 += 256) {
+      double dv[8], ev[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {   // loads first: one L2 round trip per 256 blocks
+        const int t = t0 + threadIdx.x + 32 * k;
+        dv[k] = t < (int)gridDim.x ? __ldcg(&b.blk[4 * t + 0]) : 0.0;
+        ev[k] = t < (int)gridDim.x ? __ldcg(&b.blk[4 * t + 1]) : 0.0;
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        d += dv[k];
+        e = fmax(e, ev[k]);
+      }
     }
     d = warp_sum_d(d);
     e = warp_max_d(e);
@@ -538,10 +546,22 @@ __global__ void __launch_bounds__(kRedThreads) k_gap(Params p, Buffers b, int sl
   if (!last_block(&st->cnt_gap, gridDim.x)) return;
   if (threadIdx.x < 32) {
     double a = 0.0, c = 0.0, x = 0.0;
-    for (int t = threadIdx.x; t < (int)gridDim.x; t += 32) {
-      a += __ldcg(&b.blk[4 * t + 0]);
-      c += __ldcg(&b.blk[4 * t + 1]);
-      x += __ldcg(&b.blk[4 * t + 2]);
+    for (int t0 = 0; t0 < (int)gridDim.x; t0 += 256) {
+      double av[8], cv[8], xv[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {   // loads first: one L2 round trip per 256 blocks
+        const int t = t0 + threadIdx.x + 32 * k;
+        const bool ok = t < (int)gridDim.x;
+        av[k] = ok ? __ldcg(&b.blk[4 * t + 0]) : 0.0;
+        cv[k] = ok ? __ldcg(&b.blk[4 * t + 1]) : 0.0;
+        xv[k] = ok ? __ldcg(&b.blk[4 * t + 2]) : 0.0;
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        a += av[k];
+        c += cv[k];
+        x += xv[k];
+      }
     }
     a = warp_sum_d(a);
     c = warp_sum_d(c);

@@ -69,7 +69,7 @@ __device__ __forceinline__ void pmerge(float& s, float& c, float s2, float c2) {
 
 }  // namespace
 
-template <int PREC, int QW>
+template <int PREC, int QW, int QT>
 __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
     k_pass(Params p, Buffers b, int slot, int gap_iter, int nstages, int cps) {
   DevState* st = b.st;
@@ -252,9 +252,9 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
   } else {
     // ---------------------------------------------------------------- q warps
     const int qw = warp - 1 - kPassDot;
-    float qs[kPassTmax][4], qc[kPassTmax][4];
+    float qs[QT][4], qc[QT][4];   // QT float4 row chunks per lane
 #pragma unroll
-    for (int t = 0; t < kPassTmax; ++t)
+    for (int t = 0; t < QT; ++t)
 #pragma unroll
       for (int c = 0; c < 4; ++c) qs[t][c] = qc[t][c] = 0.f;
     for (int g = 0; g < ngroups; ++g) {
@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
         if (xv.x != 0.0f || xv.y != 0.0f) {
           const float4* col = reinterpret_cast<const float4*>(stages + (size_t)s * stage_floats + (size_t)c * p.lda);
 #pragma unroll
-          for (int t = 0; t < kPassTmax; ++t) {
+          for (int t = 0; t < QT; ++t) {
             const int c4 = qw * 32 + lane + t * 32 * QW;
             if (c4 < m4q) pacc4<PREC>(qs[t], qc[t], col[c4], xv.x, xv.y);
           }
@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
     // per-CTA partials of A_S x_{k+1} (every row written, zeros included)
     float2* part = b.qpart + (size_t)blockIdx.x * p.m4;
 #pragma unroll
-    for (int t = 0; t < kPassTmax; ++t) {
+    for (int t = 0; t < QT; ++t) {
       const int c4 = qw * 32 + lane + t * 32 * QW;
       if (c4 < m4q) {
         float4* dst = reinterpret_cast<float4*>(part + 4 * c4);
@@ -317,9 +317,19 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
   __threadfence();
   if (threadIdx.x < 32) {
     double d = 0.0, e = 0.0;
-    for (int t = threadIdx.x; t < (int)gridDim.x; t += 32) {
-      d += __ldcg(&b.blk[4 * t + 0]);
-      e = fmax(e, __ldcg(&b.blk[4 * t + 1]));
+    for (int t0 = 0; t0 < (int)gridDim.x; t0 += 256) {
+      double dv[8], ev[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {   // loads first: one L2 round trip per 256 CTAs
+        const int t = t0 + threadIdx.x + 32 * k;
+        dv[k] = t < (int)gridDim.x ? __ldcg(&b.blk[4 * t + 0]) : 0.0;
+        ev[k] = t < (int)gridDim.x ? __ldcg(&b.blk[4 * t + 1]) : 0.0;
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        d += dv[k];
+        e = fmax(e, ev[k]);
+      }
     }
     d = warp_sum_d(d);
     e = warp_max_d(e);
@@ -391,10 +401,9 @@ __global__ void __launch_bounds__(256) k_resid(Params p, Buffers b, int slot, in
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  if (threadIdx.x == 0) {
-    double a = 0.0;
-    for (int t = 0; t < (int)gridDim.x; ++t) a += __ldcg(&b.tileP[t]);
-    st->P[slot ^ 1] = a;
+  if (threadIdx.x < 32) {
+    const double a = warp_load_sum(b.tileP, gridDim.x);
+    if (threadIdx.x == 0) st->P[slot ^ 1] = a;
   }
 }
 
@@ -413,33 +422,70 @@ size_t pass_smem_bytes(int lda, int m4, int nstages, int cps, int idx_cap) {
 // Stage layout for the fused pass: about 32 KB of columns per stage (bulk copies much
 // smaller than that are dominated by their fixed cost) and as many stages as fit.
 // Returns the stage count (0 when the fused pass cannot be used) and the columns per stage.
-int pass_configure(int lda, int m4, int idx_cap, int smem_optin, int* qwarps, int* cps_out) {
+// Float4 row chunks per q-warp lane for m4 rows (1, 2, 4 or 8; 0 if too many rows).
+static int pass_qt(int m4) {
   const int m4q = m4 / 4;
-  if (m4q > 32 * 8 * kPassTmax) return 0;
-  const int qw = 8;   // q warps; a lane owns up to kPassTmax float4 row chunks
+  for (int qt = 1; qt <= kPassTmax; qt *= 2)
+    if (m4q <= 32 * 8 * qt) return qt;
+  return 0;
+}
+
+template <int PREC>
+static cudaError_t pass_set_smem(int qt, int bytes) {
+  switch (qt) {
+    case 1: return cudaFuncSetAttribute(k_pass<PREC, 8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    case 2: return cudaFuncSetAttribute(k_pass<PREC, 8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    case 4: return cudaFuncSetAttribute(k_pass<PREC, 8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    default: return cudaFuncSetAttribute(k_pass<PREC, 8, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  }
+}
+
+int pass_configure(int lda, int m4, int idx_cap, int smem_optin, int* qwarps, int* cps_out) {
+  const int qt = pass_qt(m4);
+  if (qt == 0) return 0;
   const int col_bytes = lda * 4;
   for (int cps = std::max(1, std::min(8, 32768 / col_bytes)); cps >= 1; --cps) {
     int ns = kPassMaxStages;
     while (ns >= 3 && pass_smem_bytes(lda, m4, ns, cps, idx_cap) + 1024 > (size_t)smem_optin) --ns;
     if (ns < 3) continue;
     const int bytes = (int)pass_smem_bytes(lda, m4, ns, cps, idx_cap);
-    cudaError_t e = cudaFuncSetAttribute(k_pass<kX2, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass<kF32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e = pass_set_smem<kX2>(qt, bytes);
+    if (e == cudaSuccess) e = pass_set_smem<kF32>(qt, bytes);
     if (e != cudaSuccess) return 0;
-    *qwarps = qw;
+    *qwarps = 8;
     *cps_out = cps;
     return ns;
   }
   return 0;
 }
 
+template <int PREC, int QT>
+static void pass_launch_t(const Params& p, const Buffers& b, int slot, int g, int grid, int nstages, int cps,
+                          size_t sm, cudaStream_t s) {
+  k_pass<PREC, 8, QT><<<grid, 32 * (1 + kPassDot + 8), sm, s>>>(p, b, slot, g, nstages, cps);
+}
+
 cudaError_t launch_pass(const Params& p, const Buffers& b, int slot, int precision, bool gap_iter,
                         int grid, int nstages, int cps, int qwarps, cudaStream_t s) {
   const size_t sm = pass_smem_bytes(p.lda, p.m4, nstages, cps, (p.n + grid - 1) / grid);
   const int g = gap_iter ? 1 : 0;
-  if (qwarps != 8) return cudaErrorInvalidValue;
-  if (precision == kX2) k_pass<kX2, 8><<<grid, 32 * (1 + kPassDot + 8), sm, s>>>(p, b, slot, g, nstages, cps);
-  else k_pass<kF32, 8><<<grid, 32 * (1 + kPassDot + 8), sm, s>>>(p, b, slot, g, nstages, cps);
+  const int qt = pass_qt(p.m4);
+  if (qwarps != 8 || qt == 0) return cudaErrorInvalidValue;
+  if (precision == kX2) {
+    switch (qt) {
+      case 1: pass_launch_t<kX2, 1>(p, b, slot, g, grid, nstages, cps, sm, s); break;
+      case 2: pass_launch_t<kX2, 2>(p, b, slot, g, grid, nstages, cps, sm, s); break;
+      case 4: pass_launch_t<kX2, 4>(p, b, slot, g, grid, nstages, cps, sm, s); break;
+      default: pass_launch_t<kX2, 8>(p, b, slot, g, grid, nstages, cps, sm, s); break;
+    }
+  } else {
+    switch (qt) {
+      case 1: pass_launch_t<kF32, 1>(p, b, slot, g, grid, nstages, cps, sm, s); break;
+      case 2: pass_launch_t<kF32, 2>(p, b, slot, g, grid, nstages, cps, sm, s); break;
+      case 4: pass_launch_t<kF32, 4>(p, b, slot, g, grid, nstages, cps, sm, s); break;
+      default: pass_launch_t<kF32, 8>(p, b, slot, g, grid, nstages, cps, sm, s); break;
+    }
+  }
   return cudaGetLastError();
 }
 
