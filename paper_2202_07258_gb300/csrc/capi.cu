@@ -419,7 +419,8 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
   TRY(dalloc(h, &b.rh, h->m4));
   TRY(dalloc(h, &b.rl, h->m4));
   TRY(dalloc(h, &b.part, (size_t)h->fwd_chunks * h->lda));
-  TRY(dalloc(h, &b.tileP, (h->lda + 31) / 32));   // >= fwd_tiles and >= the residual kernel's grid
+  TRY(dalloc(h, &b.tileP, (h->lda + 31) / 32));   // >= fwd_tiles
+  TRY(dalloc(h, &b.tileR, (h->m4 + 31) / 32));    // the residual kernel's grid
   TRY(dalloc(h, &b.tile_cnt, h->fwd_tiles));
   TRY(dalloc(h, &b.blk, 4 * (size_t)max_blocks));
   TRY(dalloc(h, &b.st, 1));

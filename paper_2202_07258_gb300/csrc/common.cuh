@@ -228,6 +228,7 @@ struct Buffers {
   float* rl;
   float2* part;
   double* tileP;
+  double* tileR;          // fused pass: block partials of P from the residual kernel
   unsigned int* tile_cnt;
   double* blk;            // per-block partials of the epilogue kernels (4 doubles each)
   float2* qpart;          // fused pass: per-CTA double-float partials of A_S x_S (grid x m4)

@@ -100,6 +100,7 @@ Layout carve(unsigned char* base, int m, int n, int m4, int lda, int fwd_tiles, 
   L.b.rl = a.take<float>(m4);
   L.b.part = a.take<float2>((size_t)fwd_chunks * lda);
   L.b.tileP = a.take<double>((lda + 31) / 32);
+  L.b.tileR = a.take<double>((m4 + 31) / 32);
   L.b.tile_cnt = a.take<unsigned int>(fwd_tiles);
   L.b.blk = a.take<double>(4 * (size_t)max_blocks);
   L.b.st = a.take<DevState>(1);

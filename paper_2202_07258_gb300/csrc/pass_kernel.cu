@@ -104,6 +104,13 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
   const int nq = min(n_act, p0 + per) - p0;
   const int ngroups = (nq + cps - 1) / cps;
 
+  // P_k = 1/2 ||r_k||^2: from the residual kernel's block partials after the first
+  // iteration (one L2 round trip by warp 0); CTA 0 records it for the gap kernel.
+  double Pk = 0.0;
+  if (threadIdx.x < 32) {
+    Pk = st->k > 0 ? warp_load_sum(b.tileR, (p.m4 + 31) / 32) : st->P[slot];
+    if (threadIdx.x == 0 && blockIdx.x == 0) st->P[slot] = Pk;
+  }
   if (threadIdx.x == 0) {
     for (int s = 0; s < nstages; ++s) {
       mbar_init(&full[s], 1);
@@ -119,7 +126,7 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
     const double beta = (tk - 1.0) / tn;
     s_scal[0] = beta;
     s_scal[1] = tn;
-    s_scal[2] = p.Cg * sqrt(2.0 * st->P[slot]) * (1.0 + 1e-6);
+    s_scal[2] = p.Cg * sqrt(2.0 * Pk) * (1.0 + 1e-6);
     s_beta2[0] = df2_from_double(beta);
     s_beta2[1] = df2_from_double(1.0 + beta);
   }
@@ -186,16 +193,24 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
     float2* gc = b.g[slot];
     float2 dot = make_float2(0.f, 0.f);
     double epsm = 0.0;
-    for (int q = dw; q < nq; q += kPassDot) {
-      const int g = q / cps;
+    // Work unit: two adjacent columns of one stage (they share the loads of r and give 8
+    // independent accumulation chains); single columns when a stage holds an odd count.
+    const int U = (cps % 2 == 0) ? 2 : 1;
+    for (int w = dw; w * U < nq; w += kPassDot) {
+      const int q0 = w * U;
+      const int ncol = min(U, nq - q0);
+      const int g = q0 / cps;
       const int s = g % nstages;
       const int u = g / nstages;
-      const int c = q - g * cps;
-      const int j = sidx[q];
+      const int c0 = q0 - g * cps;
+      // lane e (< ncol) runs the step of column q0 + e: its data does not depend on the
+      // column values, so it is loaded before the wait
+      const int e = lane < ncol ? lane : 0;
+      const int j = sidx[q0 + e];
       float2 xk = make_float2(0.f, 0.f), xp = xk, gpv = xk, lj = xk, uj = xk;
       double nr = 0.0, wj = 0.0;
       int inf_j = 0;
-      if (lane == 0) {  // independent of the column data: issue before waiting
+      if (lane < ncol) {
         xk = xc[j];
         xp = xn[j];
         gpv = gp[j];
@@ -211,24 +226,39 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
         s_err = 1;
         break;
       }
-      const float4* col = reinterpret_cast<const float4*>(stages + (size_t)s * stage_floats + (size_t)c * p.lda);
+      const float* sbase = stages + (size_t)s * stage_floats + (size_t)c0 * p.lda;
+      const float4* colA = reinterpret_cast<const float4*>(sbase);
+      const float4* colB = reinterpret_cast<const float4*>(sbase + (ncol > 1 ? p.lda : 0));
       float sa[4] = {0.f, 0.f, 0.f, 0.f}, ca[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 4
-      for (int i = lane; i < m4q; i += 32) pacc4v<PREC>(sa, ca, col[i], srh[i], srl[i]);
+      float sb[4] = {0.f, 0.f, 0.f, 0.f}, cb[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 2
+      for (int i = lane; i < m4q; i += 32) {
+        const float4 h = srh[i], l = srl[i];
+        pacc4v<PREC>(sa, ca, colA[i], h, l);
+        pacc4v<PREC>(sb, cb, colB[i], h, l);
+      }
       pmerge<PREC>(sa[0], ca[0], sa[1], ca[1]);
       pmerge<PREC>(sa[2], ca[2], sa[3], ca[3]);
       pmerge<PREC>(sa[0], ca[0], sa[2], ca[2]);
+      pmerge<PREC>(sb[0], cb[0], sb[1], cb[1]);
+      pmerge<PREC>(sb[2], cb[2], sb[3], cb[3]);
+      pmerge<PREC>(sb[0], cb[0], sb[2], cb[2]);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         const float os = __shfl_xor_sync(0xffffffffu, sa[0], o);
         const float oc = __shfl_xor_sync(0xffffffffu, ca[0], o);
+        const float ps = __shfl_xor_sync(0xffffffffu, sb[0], o);
+        const float pc = __shfl_xor_sync(0xffffffffu, cb[0], o);
         pmerge<PREC>(sa[0], ca[0], os, oc);
+        pmerge<PREC>(sb[0], cb[0], ps, pc);
       }
       __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(&empty[s]);  // this warp is done reading the stage
+      if (lane < ncol) {
+        const int c = c0 + lane;
+        mbar_arrive(&empty[s]);  // this column's dot is done with the stage
         // FISTA step in double-float arithmetic (no float64 on this path)
-        const float2 g2 = df2_norm(sa[0], PREC == kX2 ? ca[0] : 0.0f);
+        const float2 g2 = lane == 0 ? df2_norm(sa[0], PREC == kX2 ? ca[0] : 0.0f)
+                                    : df2_norm(sb[0], PREC == kX2 ? cb[0] : 0.0f);
         const float2 gv = df2_sub(df2_mul(onepb, g2), df2_mul(bb, gpv));   // a_j^T (y' - A v_k)
         const float2 v = df2_add(xk, df2_mul(bb, df2_sub(xk, xp)));
         float2 xnew = df2_add(v, df2_mul(gv, p.invL2));
@@ -243,6 +273,15 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
           const double den = -wj - p.gamma_w * nr * p.t_norm;
           epsm = fmax(epsm, fmax(df2_to_double(g2) + eta_g * nr, 0.0) / den);
         }
+      }
+    }
+    // lanes 0 and 1 carry partial sums
+    {
+      const float2 o = make_float2(__shfl_down_sync(0xffffffffu, dot.x, 1), __shfl_down_sync(0xffffffffu, dot.y, 1));
+      const double oe = __shfl_down_sync(0xffffffffu, epsm, 1);
+      if (lane == 0) {
+        dot = df2_add(dot, o);
+        epsm = fmax(epsm, oe);
       }
     }
     if (lane == 0) {
@@ -388,22 +427,7 @@ __global__ void __launch_bounds__(256) k_resid(Params p, Buffers b, int slot, in
       const float oc = __shfl_xor_sync(0xffffffffu, pc, o);
       df_add(ps, pc, os, oc);
     }
-    if (lane == 0) b.tileP[blockIdx.x] = df_to_double(ps, pc);
-  }
-  __shared__ int s_last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned prev = atomicAdd(&st->cnt_resid, 1u);
-    s_last = prev == gridDim.x - 1;
-    if (s_last) st->cnt_resid = 0u;
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  if (threadIdx.x < 32) {
-    const double a = warp_load_sum(b.tileP, gridDim.x);
-    if (threadIdx.x == 0) st->P[slot ^ 1] = a;
+    if (lane == 0) b.tileR[blockIdx.x] = df_to_double(ps, pc);   // summed by the next pass
   }
 }
 
