@@ -163,6 +163,56 @@ BVLS_API bvls_status bvls_setup(const float* A, int m, int n, int lda, const dou
 BVLS_API bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const bvls_opts* opts,
                        double* x_out, uint8_t* screened_out, bvls_info* info);
 
+typedef struct {
+  int iters_max;          /* largest per-instance iteration count */
+  int n_converged;        /* instances with gap < tol */
+  int gap_evals;          /* evaluations run (each covers every instance still active) */
+  int dual_mode;          /* BVLS_DUAL_* */
+  double L;               /* step constant used */
+  double sum_step;        /* sum over tensor-core steps of the instances they advanced */
+  double sum_eval;        /* sum over evaluations of the instances they covered */
+  double sum_preserved;   /* sum over evaluations and instances of |preserved set| */
+  double step_ms, eval_ms;  /* profile mode: total time of the step / evaluation kernels */
+  int step_launches, eval_launches;
+  double kernel_launches; /* kernels this call launched (including ones that returned at
+                             entry because every instance had finished) */
+} bvls_batch_info;
+
+/*
+ * Solve B problems that share the handle's A and box: x_b* in argmin 1/2 ||y_b - A x||^2,
+ * l <= x <= u, each with its own screened set, gap and stop (Algorithm 1 per instance).
+ * The instances advance in lockstep; each leaves the active set at the first evaluation
+ * whose gap bound is below tol.
+ *   Y             any; B rows of m float32, row b at Y + b*ldy (ldy >= m).
+ *   X0            any; B x n doubles (row b = instance b) or NULL for the projection of 0.
+ *   opts          host or NULL.  screen_every = K: every K-th iteration (k = 0, K, 2K, ...)
+ *                 is an evaluation: exact correlations g = A^T (y - A x_k) with float32
+ *                 (BVLS_PREC_FP32) or double-float (BVLS_PREC_FP32X2) products, the gap,
+ *                 the sphere test and the stop test.  The other iterations are tensor-core
+ *                 steps: g_k = g_{k-1} - bf16(A^T A) bf16(x_k - x_{k-1}) for all active
+ *                 instances in one tcgen05 GEMM with float32 accumulation.  max_iter is
+ *                 rounded up to a multiple of K; single_pass is ignored.
+ *   X_out         any; B x n doubles: per instance, the iterate of its last evaluation with
+ *                 screened coordinates at their bounds.
+ *   screened_out  any; B x n bytes or NULL (0 preserved, 1 at l_j, 2 at u_j).
+ *   gaps_out      any; B doubles or NULL: the gap bound at X_out.
+ *   iters_out     any; B ints or NULL: the iteration index of that evaluation.
+ *   status_out    any; B ints or NULL: BVLS_OK or BVLS_EMAXITER per instance.
+ *   info          host or NULL.
+ * The iterates are float32 (the bounds are rounded inward to float32 for them); the gap,
+ * the radius and the test are float64 with the rounding of every evaluation product
+ * bounded, so no coordinate is fixed unless the safe rule holds for the exact problem.
+ * Limits: m <= 1024, n <= 4096, 1 <= B <= 2^20.  The first call computes and keeps
+ * bf16(A^T A) (n rounded up to 128, squared, 2 bytes each) and a workspace of about
+ * 30 * B * n bytes, reused by later calls with the same or smaller B.
+ * Returns BVLS_OK when every instance converged, BVLS_EMAXITER otherwise (all outputs
+ * valid), or an error (outputs untouched).
+ */
+BVLS_API bvls_status bvls_solve_batched(bvls_handle* h, int B, const float* Y, int ldy, const double* X0,
+                                        const bvls_opts* opts, double* X_out, uint8_t* screened_out,
+                                        double* gaps_out, int* iters_out, int* status_out,
+                                        bvls_batch_info* info);
+
 /*
  * One-call solve that allocates nothing.  The paper has no counterpart: this is a service
  * for callers that cannot allocate device memory -- code that runs inside a memory pool or

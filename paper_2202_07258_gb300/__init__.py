@@ -19,10 +19,11 @@ from . import _capi
 from ._capi import (BVLS_DUAL_SCALING, BVLS_DUAL_TRANSLATION, BVLS_DUAL_ZERO, BVLS_EINVAL,
                     BVLS_EMAXITER, BVLS_ENONFINITE, BVLS_ENOTSUP, BVLS_OK, BVLS_PREC_FP32,
                     BVLS_PREC_FP32X2, DUAL_NAMES, STATUS_NAMES, bvls_default_opts, bvls_destroy,
-                    bvls_info, bvls_last_error, bvls_opts, bvls_setup, bvls_solve)
+                    bvls_batch_info, bvls_info, bvls_last_error, bvls_opts, bvls_setup, bvls_solve,
+                    bvls_solve_batched)
 
 __all__ = ["Solver", "BVLSError", "bvls_setup", "bvls_solve", "bvls_destroy", "bvls_default_opts",
-           "bvls_last_error", "bvls_opts", "bvls_info", "make_opts"]
+           "bvls_last_error", "bvls_opts", "bvls_info", "bvls_batch_info", "bvls_solve_batched", "make_opts"]
 
 
 class BVLSError(RuntimeError):
@@ -135,3 +136,43 @@ class Solver:
         d["status"] = STATUS_NAMES.get(st, st)
         d["dual"] = DUAL_NAMES.get(info.dual_mode, info.dual_mode)
         return x, s, d, st
+
+    def solve_batched(self, Y, X0=None, *, opts: bvls_opts | None = None, check: bool = True, **kw):
+        """Run bvls_solve_batched on the rows of Y (B x m).
+
+        Returns (X, screened, gaps, iters, status, info_dict, st): X (B x n float64),
+        screened (B x n uint8), per-instance gap bounds, iteration indices and statuses.
+        Outputs follow Y (CUDA tensors for a CUDA tensor Y, numpy arrays otherwise).
+        """
+        if opts is None:
+            opts = make_opts(**kw)
+        if _is_torch(Y):
+            import torch
+            dev = Y.device
+            Yk = Y.detach().to(dtype=torch.float32).contiguous()
+            B = int(Yk.shape[0])
+            X0k = None if X0 is None else X0.detach().to(device=dev, dtype=torch.float64).contiguous()
+            X = torch.empty((B, self.n), dtype=torch.float64, device=dev)
+            S = torch.empty((B, self.n), dtype=torch.uint8, device=dev)
+            gaps = torch.empty(B, dtype=torch.float64, device=dev)
+            its = torch.empty(B, dtype=torch.int32, device=dev)
+            sts = torch.empty(B, dtype=torch.int32, device=dev)
+            ptr = lambda t: None if t is None else t.data_ptr()
+        else:
+            Yk = np.ascontiguousarray(np.asarray(Y, dtype=np.float32).reshape(-1, self.m))
+            B = int(Yk.shape[0])
+            X0k = None if X0 is None else np.ascontiguousarray(np.asarray(X0, dtype=np.float64).reshape(B, self.n))
+            X = np.empty((B, self.n), dtype=np.float64)
+            S = np.empty((B, self.n), dtype=np.uint8)
+            gaps = np.empty(B, dtype=np.float64)
+            its = np.empty(B, dtype=np.int32)
+            sts = np.empty(B, dtype=np.int32)
+            ptr = lambda t: None if t is None else t.ctypes.data
+        st, info = bvls_solve_batched(self.handle, B, ptr(Yk), self.m, ptr(X0k), opts, ptr(X), ptr(S), ptr(gaps),
+                                      ptr(its), ptr(sts))
+        if check and st not in (BVLS_OK, BVLS_EMAXITER):
+            raise BVLSError(st, bvls_last_error())
+        d = info.as_dict()
+        d["status"] = STATUS_NAMES.get(st, st)
+        d["dual"] = DUAL_NAMES.get(info.dual_mode, info.dual_mode)
+        return X, S, gaps, its, sts, d, st

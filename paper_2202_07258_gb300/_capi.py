@@ -21,7 +21,7 @@ DUAL_NAMES = {0: "scaling", 1: "translation", 2: "zero"}
 
 # Every symbol the header declares; tests check that the library exports all of them.
 EXPORTED = ("bvls_default_opts", "bvls_setup", "bvls_solve", "bvls_destroy", "bvls_last_error",
-            "bvls_solve_static")
+            "bvls_solve_static", "bvls_solve_batched")
 
 
 class bvls_opts(ctypes.Structure):
@@ -63,6 +63,27 @@ class bvls_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class bvls_batch_info(ctypes.Structure):
+    _fields_ = [
+        ("iters_max", ctypes.c_int),
+        ("n_converged", ctypes.c_int),
+        ("gap_evals", ctypes.c_int),
+        ("dual_mode", ctypes.c_int),
+        ("L", ctypes.c_double),
+        ("sum_step", ctypes.c_double),
+        ("sum_eval", ctypes.c_double),
+        ("sum_preserved", ctypes.c_double),
+        ("step_ms", ctypes.c_double),
+        ("eval_ms", ctypes.c_double),
+        ("step_launches", ctypes.c_int),
+        ("eval_launches", ctypes.c_int),
+        ("kernel_launches", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -89,6 +110,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.bvls_solve_static.argtypes = [vp, ci, ci, ci, vp, vp, vp, vp, ctypes.POINTER(bvls_opts), vp, vp, vp,
                                       ctypes.POINTER(bvls_info)]
     lib.bvls_solve_static.restype = ci
+    lib.bvls_solve_batched.argtypes = [vp, ci, vp, ci, vp, ctypes.POINTER(bvls_opts), vp, vp, vp, vp, vp,
+                                       ctypes.POINTER(bvls_batch_info)]
+    lib.bvls_solve_batched.restype = ci
     _lib = lib
     return lib
 
@@ -125,6 +149,15 @@ def bvls_solve_static(A_ptr: int, m: int, n: int, lda: int, l_ptr: int | None, u
     st = load().bvls_solve_static(A_ptr, m, n, lda, l_ptr, u_ptr, y_ptr, x0_ptr,
                                   ctypes.byref(opts) if opts is not None else None, stream or 0,
                                   x_out_ptr, screened_ptr, ctypes.byref(info))
+    return st, info
+
+
+def bvls_solve_batched(h: int, B: int, Y_ptr: int, ldy: int, X0_ptr: int | None, opts: bvls_opts | None,
+                       X_out_ptr: int, screened_ptr: int | None, gaps_ptr: int | None, iters_ptr: int | None,
+                       status_ptr: int | None) -> tuple[int, bvls_batch_info]:
+    info = bvls_batch_info()
+    st = load().bvls_solve_batched(h, B, Y_ptr, ldy, X0_ptr, ctypes.byref(opts) if opts is not None else None,
+                                   X_out_ptr, screened_ptr, gaps_ptr, iters_ptr, status_ptr, ctypes.byref(info))
     return st, info
 
 

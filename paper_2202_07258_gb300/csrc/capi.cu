@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include "batch.cuh"
 #include "bvls_gb300.h"
 #include "common.cuh"
 
@@ -73,6 +74,18 @@ struct bvls_handle {
   bool own_stream = false;
   std::vector<cudaEvent_t> prof;
   std::vector<void*> allocs;
+  // batched solve (shared A): bf16 Gram matrix, float32 bounds, workspace of capacity b_cap
+  int b_npad = 0;
+  __nv_bfloat16* bH = nullptr;
+  float *lf = nullptr, *uf = nullptr;
+  int b_cap = 0;
+  BBuffers bb{};
+  float* bY = nullptr;
+  double* bX0 = nullptr;
+  std::vector<void*> b_allocs;
+  bool b_have_graph = false;
+  double b_key[10] = {0};
+  cudaGraphExec_t b_exec = nullptr;
 };
 
 namespace {
@@ -95,6 +108,8 @@ bvls_status dalloc(bvls_handle* h, T** p, size_t count) {
 void free_handle(bvls_handle* h) {
   if (!h) return;
   if (h->exec) cudaGraphExecDestroy(h->exec);
+  if (h->b_exec) cudaGraphExecDestroy(h->b_exec);
+  for (void* p : h->b_allocs) cudaFree(p);
   for (auto e : h->prof) cudaEventDestroy(e);
   for (void* p : h->allocs) cudaFree(p);
   if (h->pinned) cudaFreeHost(h->pinned);
@@ -624,3 +639,302 @@ bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const b
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ batched solve
+namespace {
+
+template <typename T>
+bvls_status balloc(bvls_handle* h, T** p, size_t count) {
+  void* q = nullptr;
+  CK(cudaMalloc(&q, count * sizeof(T) + 256));
+  h->b_allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return BVLS_OK;
+}
+
+// Gram matrix, float32 bounds (rounded inward) and the workspace for B instances.
+bvls_status batch_prepare(bvls_handle* h, int B) {
+  const int n = h->n;
+  if (!h->bH) {
+    h->b_npad = (n + kBTile - 1) / kBTile * kBTile;
+    CK(batch_configure(h->m));
+    TRY(dalloc(h, &h->bH, (size_t)h->b_npad * h->b_npad));
+    CK(launch_bgram(h->A, h->lda, h->m, n, h->b_npad, h->bH, h->s));
+    std::vector<double> lv(n), uv(n);
+    CK(cudaMemcpyAsync(lv.data(), h->l, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
+    CK(cudaMemcpyAsync(uv.data(), h->u, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    std::vector<float> lf(n), uf(n);
+    for (int j = 0; j < n; ++j) {
+      float a = (float)lv[j];
+      if ((double)a < lv[j]) a = std::nextafter(a, INFINITY);
+      float b = (float)uv[j];
+      if ((double)b > uv[j]) b = std::nextafter(b, -INFINITY);
+      lf[j] = a;
+      uf[j] = b;
+    }
+    TRY(dalloc(h, &h->lf, n));
+    TRY(dalloc(h, &h->uf, n));
+    CK(cudaMemcpyAsync(h->lf, lf.data(), sizeof(float) * n, cudaMemcpyHostToDevice, h->s));
+    CK(cudaMemcpyAsync(h->uf, uf.data(), sizeof(float) * n, cudaMemcpyHostToDevice, h->s));
+    CK(cudaStreamSynchronize(h->s));
+  }
+  if (B <= h->b_cap) return BVLS_OK;
+  if (h->b_exec) {
+    cudaGraphExecDestroy(h->b_exec);
+    h->b_exec = nullptr;
+  }
+  h->b_have_graph = false;
+  CK(cudaStreamSynchronize(h->s));
+  for (void* q : h->b_allocs) cudaFree(q);
+  h->b_allocs.clear();
+  h->b_cap = 0;
+  const size_t np = (size_t)h->b_npad, MT = np / kBTile;
+  BBuffers& b = h->bb;
+  b = BBuffers{};
+  for (int q = 0; q < 2; ++q) {
+    TRY(balloc(h, &b.X[q], (size_t)B * np));
+    TRY(balloc(h, &b.G[q], (size_t)B * np));
+    TRY(balloc(h, &b.D[q], (size_t)(B + 1) * np));
+    TRY(balloc(h, &b.tval[q], (size_t)B));
+    TRY(balloc(h, &b.dotp[q], MT * B));
+  }
+  TRY(balloc(h, &b.Ge, (size_t)B * np));
+  TRY(balloc(h, &b.flags, (size_t)B * np));
+  TRY(balloc(h, &b.act, (size_t)B));
+  TRY(balloc(h, &b.act_tmp, (size_t)B));
+  TRY(balloc(h, &b.fin, (size_t)B));
+  TRY(balloc(h, &b.xout, (size_t)B * n));
+  TRY(balloc(h, &b.gap, (size_t)B));
+  TRY(balloc(h, &b.primal, (size_t)B));
+  TRY(balloc(h, &b.iters, (size_t)B));
+  TRY(balloc(h, &b.status, (size_t)B));
+  TRY(balloc(h, &b.npres, (size_t)B));
+  TRY(balloc(h, &b.st, 1));
+  TRY(balloc(h, &h->bY, (size_t)B * h->lda));
+  TRY(balloc(h, &h->bX0, (size_t)B * n));
+  h->b_cap = B;
+  return BVLS_OK;
+}
+
+BParams make_bparams(bvls_handle* h, const bvls_opts& o, int max_iter, int B) {
+  BParams p{};
+  p.A = h->A;
+  p.m = h->m;
+  p.n = h->n;
+  p.lda = h->lda;
+  p.npad = h->b_npad;
+  p.B = B;
+  p.H = h->bH;
+  p.l = h->l;
+  p.u = h->u;
+  p.nrm = h->nrm;
+  p.w = h->w;
+  p.jinf = h->jinf;
+  p.lf = h->lf;
+  p.uf = h->uf;
+  const double L = o.lipschitz > 0.0 ? o.lipschitz : h->L;
+  p.invL = 1.0 / L;
+  p.invLf = (float)p.invL;
+  p.t_norm = h->t_norm;
+  p.gamma_w = h->gamma_w;
+  // Rounding of the evaluation products (see common.cuh for the double-float bound):
+  // a lane sums ceil(m/32) products, then 5 shuffle levels; the residual sums up to n
+  // products per row in double-float.
+  const double dg = (h->m + 31) / 32 + 5;
+  p.Cg = o.precision == BVLS_PREC_FP32X2 ? 2.0 * (dg + 2.0) * (dg + 2.0) * kU * kU + 4.0 * kU * kU + 2.0 * kU64
+                                         : 1.01 * (dg + 2.0) * kU + kU;
+  const double df = h->n;
+  p.Cf = 2.0 * (df + 2.0) * (df + 2.0) * kU * kU + 2.0 * kU * kU;
+  p.Csub = 8.0 * kU * kU;
+  p.tol = o.tol;
+  p.max_iter = max_iter;
+  p.dual_mode = h->dual_mode;
+  p.screening = o.screening;
+  p.restart = o.restart;
+  p.K = o.screen_every;
+  return p;
+}
+
+// One chunk of iterations k = kbase + j (kbase a multiple of K and even): evaluations at
+// j % K == 0 (followed by the retirement of finished instances), tensor-core steps otherwise.
+cudaError_t enqueue_bchunk(bvls_handle* h, const BParams& p, const bvls_opts& o, int chunk, cudaEvent_t* ev) {
+  cudaError_t e = cudaSuccess;
+  for (int j = 0; j < chunk && e == cudaSuccess; ++j) {
+    if (ev) cudaEventRecordWithFlags(ev[2 * j], h->s, cudaEventRecordExternal);
+    if (j % o.screen_every == 0) {
+      e = launch_beval(p, h->bb, j, o.precision, h->s);
+      if (e == cudaSuccess) e = launch_bcompact(p, h->bb, h->s);
+    } else {
+      e = launch_bstep(p, h->bb, j, h->s);
+    }
+    if (ev) cudaEventRecordWithFlags(ev[2 * j + 1], h->s, cudaEventRecordExternal);
+  }
+  if (e == cudaSuccess) e = launch_bchunk_end(h->bb, chunk, h->s);
+  return e;
+}
+
+}  // namespace
+
+extern "C" bvls_status bvls_solve_batched(bvls_handle* h, int B, const float* Y, int ldy, const double* X0,
+                                          const bvls_opts* opts, double* X_out, uint8_t* screened_out,
+                                          double* gaps_out, int* iters_out, int* status_out,
+                                          bvls_batch_info* info) {
+  if (!h || !Y || !X_out) return set_err(BVLS_EINVAL, "handle, Y and X_out are required");
+  if (B < 1 || B > kBMaxBatch) return set_err(BVLS_EINVAL, "B = %d outside [1, %d]", B, kBMaxBatch);
+  if (ldy < h->m) return set_err(BVLS_EINVAL, "ldy = %d < m = %d", ldy, h->m);
+  if (h->m > kBMaxRows || h->n > kBMaxCols)
+    return set_err(BVLS_ENOTSUP, "batched solve supports m <= %d and n <= %d (got %d x %d)", kBMaxRows,
+                   kBMaxCols, h->m, h->n);
+  bvls_opts o;
+  bvls_default_opts(&o);
+  if (opts) o = *opts;
+  TRY(validate_opts(o));
+  const int K = o.screen_every;
+  const int max_iter = (int)std::min<long long>((long long)(o.max_iter + K - 1) / K * K, 0x3fffffff);
+  const int chunk = chunk_length(K);
+  TRY(batch_prepare(h, B));
+  const BParams p = make_bparams(h, o, max_iter, B);
+
+  if (h->own_stream) {
+    CK(cudaEventRecord(h->ev_in, h->user));
+    CK(cudaStreamWaitEvent(h->s, h->ev_in, 0));
+  }
+  CK(cudaMemcpy2DAsync(h->bY, sizeof(float) * h->lda, Y, sizeof(float) * ldy, sizeof(float) * h->m, B,
+                       cudaMemcpyDefault, h->s));
+  BBuffers& bb = h->bb;
+  bb.Y = h->bY;
+  bb.X0 = nullptr;
+  if (X0) {
+    CK(cudaMemcpyAsync(h->bX0, X0, sizeof(double) * (size_t)B * h->n, cudaMemcpyDefault, h->s));
+    bb.X0 = h->bX0;
+  }
+  CK(cudaMemsetAsync(bb.st, 0, sizeof(BState), h->s));
+  CK(launch_binit(p, bb, h->s));
+
+  const long long max_chunks = (max_iter + chunk - 1) / chunk + 2;
+  const long long per_chunk = (long long)chunk + chunk / K + 1;
+  long long chunks_run = 0;
+  double step_ms = 0.0, eval_ms = 0.0;
+  int step_launches = 0, eval_launches = 0;
+  if (o.profile) {
+    while ((int)h->prof.size() < 2 * chunk) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      h->prof.push_back(e);
+    }
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t gx = nullptr;
+    CK(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e1 = enqueue_bchunk(h, p, o, chunk, h->prof.data());
+    cudaError_t e2 = cudaStreamEndCapture(h->s, &g);
+    CK(e1);
+    CK(e2);
+    cudaError_t e3 = cudaGraphInstantiate(&gx, g, 0);
+    cudaGraphDestroy(g);
+    CK(e3);
+    bvls_status pst = BVLS_OK;
+    for (long long c = 0; c < max_chunks; ++c) {
+      BState before;
+      cudaError_t e = cudaMemcpyAsync(&before, bb.st, sizeof(BState), cudaMemcpyDeviceToHost, h->s);
+      if (e == cudaSuccess) e = cudaGraphLaunch(gx, h->s);
+      ++chunks_run;
+      BState hs;
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, bb.st, sizeof(BState), cudaMemcpyDeviceToHost, h->s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
+      if (e != cudaSuccess) {
+        pst = set_err(BVLS_ECUDA, "profile chunk: %s", cudaGetErrorString(e));
+        break;
+      }
+      // iterations that ran with instances still active: up to the evaluation that ended
+      // the solve (a finished solve leaves the rest of the chunk's kernels returning at entry)
+      int ran = chunk;
+      if (hs.done) ran = std::min(chunk, (hs.gap_evals - before.gap_evals - 1) * K + 1);
+      for (int j = 0; j < ran; ++j) {
+        float a = 0.f;
+        CK(cudaEventElapsedTime(&a, h->prof[2 * j], h->prof[2 * j + 1]));
+        if (j % K == 0) {
+          eval_ms += a;
+          ++eval_launches;
+        } else {
+          step_ms += a;
+          ++step_launches;
+        }
+      }
+      if (hs.done) break;
+    }
+    cudaGraphExecDestroy(gx);
+    if (pst != BVLS_OK) return pst;
+  } else {
+    const double key[10] = {(double)K,  (double)chunk, (double)o.precision, (double)o.screening, (double)o.restart,
+                            o.tol,      (double)max_iter, p.invL,          (double)B,           1.0};
+    if (!h->b_have_graph || std::memcmp(key, h->b_key, sizeof(key)) != 0) {
+      if (h->b_exec) {
+        cudaGraphExecDestroy(h->b_exec);
+        h->b_exec = nullptr;
+      }
+      h->b_have_graph = false;
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = enqueue_bchunk(h, p, o, chunk, nullptr);
+      cudaError_t e2 = cudaStreamEndCapture(h->s, &g);
+      CK(e);
+      CK(e2);
+      e = cudaGraphInstantiate(&h->b_exec, g, 0);
+      cudaGraphDestroy(g);
+      CK(e);
+      h->b_have_graph = true;
+      std::memcpy(h->b_key, key, sizeof(key));
+    }
+    for (long long c = 0; c < max_chunks; ++c) {
+      CK(cudaGraphLaunch(h->b_exec, h->s));
+      ++chunks_run;
+      CK(cudaMemcpyAsync(&h->pinned[2 + (c & 1)], &bb.st->done, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+      CK(cudaEventRecord(h->poll[c & 1], h->s));
+      if (c >= 1) {
+        CK(cudaEventSynchronize(h->poll[(c - 1) & 1]));
+        if (h->pinned[2 + ((c - 1) & 1)]) break;
+      }
+    }
+  }
+  CK(cudaStreamSynchronize(h->s));
+  BState hs;
+  CK(cudaMemcpy(&hs, bb.st, sizeof(BState), cudaMemcpyDeviceToHost));
+  if (hs.nonfinite) return set_err(BVLS_ENONFINITE, "Y or X0 contains NaN or Inf");
+  if (hs.error) return set_err(BVLS_ETIMEOUT, "a device-side wait exceeded its bound; results discarded");
+  if (!hs.done) return set_err(BVLS_ECUDA, "batched solve stopped after %lld chunks without finishing", chunks_run);
+  std::vector<int> st_h(B), it_h(B);
+  CK(cudaMemcpyAsync(X_out, bb.xout, sizeof(double) * (size_t)B * h->n, cudaMemcpyDefault, h->s));
+  if (screened_out)
+    CK(cudaMemcpy2DAsync(screened_out, h->n, bb.flags, h->b_npad, h->n, B, cudaMemcpyDefault, h->s));
+  if (gaps_out) CK(cudaMemcpyAsync(gaps_out, bb.gap, sizeof(double) * B, cudaMemcpyDefault, h->s));
+  if (iters_out) CK(cudaMemcpyAsync(iters_out, bb.iters, sizeof(int) * B, cudaMemcpyDefault, h->s));
+  if (status_out) CK(cudaMemcpyAsync(status_out, bb.status, sizeof(int) * B, cudaMemcpyDefault, h->s));
+  CK(cudaMemcpyAsync(st_h.data(), bb.status, sizeof(int) * B, cudaMemcpyDeviceToHost, h->s));
+  CK(cudaMemcpyAsync(it_h.data(), bb.iters, sizeof(int) * B, cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  int nconv = 0, itmax = 0;
+  for (int q = 0; q < B; ++q) {
+    nconv += st_h[q] == BVLS_OK;
+    itmax = std::max(itmax, it_h[q]);
+  }
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->iters_max = itmax;
+    info->n_converged = nconv;
+    info->gap_evals = hs.gap_evals;
+    info->dual_mode = h->dual_mode;
+    info->L = 1.0 / p.invL;
+    info->sum_step = hs.sum_step;
+    info->sum_eval = hs.sum_eval;
+    info->sum_preserved = hs.sum_pres;
+    info->step_ms = step_ms;
+    info->eval_ms = eval_ms;
+    info->step_launches = step_launches;
+    info->eval_launches = eval_launches;
+    info->kernel_launches = 1.0 + (double)chunks_run * (double)per_chunk;
+  }
+  if (nconv < B) return set_err(BVLS_EMAXITER, "%d of %d instances reached max_iter with gap >= tol", B - nconv, B);
+  g_err.clear();
+  return BVLS_OK;
+}

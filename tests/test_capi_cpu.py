@@ -56,18 +56,21 @@ def test_setup_rejects_bad_sizes_before_touching_the_device(lib):
     assert st == _capi.BVLS_ENOTSUP
     st, _ = _capi.bvls_solve(None, None, None, None, None, None)
     assert st == _capi.BVLS_EINVAL
+    st, _ = _capi.bvls_solve_batched(None, 4, None, 2, None, None, None, None, None, None, None)
+    assert st == _capi.BVLS_EINVAL
 
 
 def test_struct_layouts_match_header(tmp_path):
-    """ctypes mirrors of bvls_opts / bvls_info have the C compiler's sizes and offsets."""
+    """ctypes mirrors of bvls_opts / bvls_info / bvls_batch_info have the C compiler's sizes and offsets."""
     import shutil
     import subprocess
     from paper_2202_07258_gb300 import _capi
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
-    fields = {"bvls_opts": [f for f, _ in _capi.bvls_opts._fields_],
-              "bvls_info": [f for f, _ in _capi.bvls_info._fields_]}
+    classes = {"bvls_opts": _capi.bvls_opts, "bvls_info": _capi.bvls_info,
+               "bvls_batch_info": _capi.bvls_batch_info}
+    fields = {k: [f for f, _ in c._fields_] for k, c in classes.items()}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "bvls_gb300.h"', "int main(void){"]
     for st, fl in fields.items():
         lines.append(f'printf("{st} %zu\\n", sizeof({st}));')
@@ -80,7 +83,7 @@ def test_struct_layouts_match_header(tmp_path):
     subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
                                                  check=True).stdout.splitlines())
-    for st, cls in (("bvls_opts", _capi.bvls_opts), ("bvls_info", _capi.bvls_info)):
+    for st, cls in classes.items():
         assert int(out[st]) == ctypes.sizeof(cls), st
         for f in fields[st]:
             assert int(out[f"{st}.{f}"]) == getattr(cls, f).offset, (st, f)

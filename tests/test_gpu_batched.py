@@ -1,0 +1,177 @@
+"""GPU parity of the batched solver (one shared A, many right-hand sides) against the FP64 oracle.
+
+Each instance of a batch is compared with the oracle's own solve of that instance:
+  * the GPU's gap bound holds: P(x_gpu) - P(x*) <= gap_gpu < tol, with x* an FP64 optimum
+    certified by the optimality conditions of Section 3.2;
+  * zero false screens: every coordinate the GPU fixed sits at that bound in x*, and
+    a_j^T theta* has the sign Eq. (screen_cond) requires;
+  * the solution agrees with x* to 1e-4 relative (the bar of the reduced-precision forms:
+    the iterates are float32 and the non-evaluation steps use bf16 tensor-core products).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2202_07258_gb300 as pkg
+    return pkg
+
+
+def batched(P, p, Y=None, X0=None, **kw):
+    dev = torch.device("cuda:0")
+    s = P.Solver(torch.from_numpy(np.ascontiguousarray(p.A)).to(dev), p.l, p.u)
+    Yt = torch.from_numpy(np.ascontiguousarray(p.y if Y is None else Y)).to(dev)
+    X0t = None if X0 is None else torch.from_numpy(np.asarray(X0, np.float64)).to(dev)
+    X, S, gaps, its, sts, info, st = s.solve_batched(Yt, X0t, **kw)
+    torch.cuda.synchronize()
+    out = (X.cpu().numpy(), S.cpu().numpy(), gaps.cpu().numpy(), its.cpu().numpy(), sts.cpu().numpy(), info, st)
+    s.close()
+    return out
+
+
+def certified_optimum(A, y, l, u, tol):
+    ref = O.solve(A, y, l, u, tol=tol, screen_every=10)
+    xs = O.polish(A, y, ref.x, l, u, tau=1e-7)
+    assert np.all(xs >= l - 1e-12) and np.all(xs <= u + 1e-12)
+    assert O.kkt_residual(A, y, xs, l, u) < 1e-9 * (1 + np.abs(A.T @ y).max())
+    return xs
+
+
+def check_instance(A, y, l, u, x, scr, gap, status, xs, tol, name):
+    assert status == 0 and gap < tol, (name, status, gap)
+    assert np.all(x >= l) and np.all(x <= u), name
+    Pg, Ps = O.primal_objective(A, y, x), O.primal_objective(A, y, xs)
+    assert Ps - 1e-12 <= Pg <= Ps + gap * (1 + 1e-9) + 1e-12, (name, Pg - Ps, gap)
+    g = A.T @ (y - A @ xs)
+    low, upp = scr == 1, scr == 2
+    assert np.all(np.abs(xs[low] - l[low]) <= 1e-12) and np.all(g[low] < 0), name
+    assert np.all(np.abs(xs[upp] - u[upp]) <= 1e-12) and np.all(g[upp] > 0), name
+    assert np.all(x[low] == l[low]) and np.all(x[upp] == u[upp]), name
+    err = float(np.abs(x - xs).max())
+    assert err <= 1e-4 * max(1.0, float(np.abs(xs).max())), (name, err)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-6), ("fp32x2", 1e-8)])
+def test_dirichlet_shared_matches_oracle(P, precision, tol):
+    """The shape of the batched BVLS workload: A 224 x 512 U[0,1] unit columns, box [0,1]."""
+    p = W.bvls_dirichlet_shared(224, 512, 12, 8, 0.005, 1)
+    A = p.A.astype(np.float64)
+    X, S, gaps, its, sts, info, st = batched(P, p, tol=tol, precision=precision)
+    assert st == P.BVLS_OK and info["n_converged"] == 12
+    assert info["dual"] == "scaling"
+    for b in range(12):
+        y = p.y[b].astype(np.float64)
+        xs = certified_optimum(A, y, p.l, p.u, 1e-10)
+        check_instance(A, y, p.l, p.u, X[b], S[b], gaps[b], sts[b], xs, tol, f"inst{b}")
+    assert (S > 0).sum() > 0.5 * S.size   # most coordinates are fixed at 0 by the end
+
+
+def test_nnls_translation_ragged_tiles(P):
+    """NNLS (dual translation, Eq. (BVLR_dual_up2)) with n = 300 (three coordinate tiles,
+    the last ragged) and B = 150 instances (two instance tiles, the last ragged)."""
+    p = W.nnls_shared(96, 300, 150, 0.06, 1.0, 2)
+    A = p.A.astype(np.float64)
+    X, S, gaps, its, sts, info, st = batched(P, p, tol=1e-7, precision="fp32x2")
+    assert st == P.BVLS_OK and info["dual"] == "translation"
+    assert len(set(its.tolist())) > 1          # uneven convergence: instances retire apart
+    for b in list(range(0, 150, 13)) + [149]:
+        y = p.y[b].astype(np.float64)
+        xs = certified_optimum(A, y, p.l, p.u, 1e-9)
+        check_instance(A, y, p.l, p.u, X[b], S[b], gaps[b], sts[b], xs, 1e-7, f"inst{b}")
+
+
+def test_gaussian_box_both_bounds(P):
+    """BVLS with both bounds active (N(0,1) data, box [-1,1]): fixes at l and at u."""
+    p = W.bvls_box_shared(80, 150, 40, 1.0, 3)
+    A = p.A.astype(np.float64)
+    X, S, gaps, its, sts, info, st = batched(P, p, tol=1e-8, precision="fp32x2")
+    assert st == P.BVLS_OK
+    assert (S == 1).sum() > 0 and (S == 2).sum() > 0
+    for b in range(0, 40, 5):
+        y = p.y[b].astype(np.float64)
+        xs = certified_optimum(A, y, p.l, p.u, 1e-11)
+        check_instance(A, y, p.l, p.u, X[b], S[b], gaps[b], sts[b], xs, 1e-8, f"inst{b}")
+
+
+def test_screening_off_reaches_the_same_optimum(P):
+    p = W.bvls_dirichlet_shared(128, 256, 20, 6, 0.005, 4)
+    a = batched(P, p, tol=1e-7, precision="fp32x2")
+    b = batched(P, p, tol=1e-7, precision="fp32x2", screening=False)
+    assert a[6] == P.BVLS_OK and b[6] == P.BVLS_OK
+    assert (a[1] > 0).sum() > 0 and (b[1] > 0).sum() == 0
+    assert a[5]["sum_preserved"] < b[5]["sum_preserved"]
+    A = p.A.astype(np.float64)
+    for i in range(20):
+        y = p.y[i].astype(np.float64)
+        Pa, Pb = O.primal_objective(A, y, a[0][i]), O.primal_objective(A, y, b[0][i])
+        assert abs(Pa - Pb) <= a[2][i] + b[2][i]
+
+
+def test_batched_agrees_with_single_instance_solver(P):
+    p = W.bvls_dirichlet_shared(224, 512, 4, 8, 0.005, 5)
+    X, S, gaps, its, sts, info, st = batched(P, p, tol=1e-8, precision="fp32x2")
+    dev = torch.device("cuda:0")
+    s = P.Solver(torch.from_numpy(np.ascontiguousarray(p.A)).to(dev), p.l, p.u)
+    A = p.A.astype(np.float64)
+    for b in range(4):
+        x1, s1, i1, st1 = s.solve(torch.from_numpy(p.y[b]).to(dev), tol=1e-8)
+        x1 = x1.cpu().numpy()
+        y = p.y[b].astype(np.float64)
+        # both certify gap < 1e-8, so both residuals lie within sqrt(2 * 1e-8) of theta*
+        r_b, r_1 = y - A @ X[b], y - A @ x1
+        assert np.linalg.norm(r_b - r_1) <= 2 * np.sqrt(2e-8) + 1e-9
+    s.close()
+
+
+def test_max_iter_warm_start_zero_rhs_and_single_instance(P):
+    p = W.bvls_dirichlet_shared(64, 160, 6, 5, 0.005, 6)
+    A = p.A.astype(np.float64)
+    # max_iter: every instance stops at the evaluation k = max_iter with a valid bound
+    X, S, gaps, its, sts, info, st = batched(P, p, tol=1e-12, max_iter=20)
+    assert st == P.BVLS_EMAXITER and np.all(sts == P.BVLS_EMAXITER) and np.all(its == 20)
+    for b in range(6):
+        y = p.y[b].astype(np.float64)
+        xs = certified_optimum(A, y, p.l, p.u, 1e-11)
+        assert O.primal_objective(A, y, X[b]) - O.primal_objective(A, y, xs) <= gaps[b] * (1 + 1e-9) + 1e-12
+    # warm start at the optimum: the first evaluation already certifies it
+    XS = np.stack([certified_optimum(A, p.y[b].astype(np.float64), p.l, p.u, 1e-11) for b in range(6)])
+    X, S, gaps, its, sts, info, st = batched(P, p, X0=XS, tol=1e-6)
+    assert st == P.BVLS_OK and np.all(its <= 10)
+    # y = 0: x = 0 is optimal with gap 0 at k = 0
+    Y = p.y.copy()
+    Y[2] = 0.0
+    X, S, gaps, its, sts, info, st = batched(P, p, Y=Y, tol=1e-9)
+    assert its[2] == 0 and np.all(X[2] == 0.0) and gaps[2] < 1e-12
+    # B = 1
+    X, S, gaps, its, sts, info, st = batched(P, p, Y=p.y[:1], tol=1e-8, precision="fp32x2")
+    xs = certified_optimum(A, p.y[0].astype(np.float64), p.l, p.u, 1e-11)
+    check_instance(A, p.y[0].astype(np.float64), p.l, p.u, X[0], S[0], gaps[0], sts[0], xs, 1e-8, "B1")
+
+
+def test_repeat_calls_are_identical_and_nonfinite_is_rejected(P):
+    p = W.bvls_dirichlet_shared(64, 160, 9, 5, 0.005, 7)
+    dev = torch.device("cuda:0")
+    s = P.Solver(torch.from_numpy(np.ascontiguousarray(p.A)).to(dev), p.l, p.u)
+    Y = torch.from_numpy(p.y).to(dev)
+    a = s.solve_batched(Y, tol=1e-8)
+    b = s.solve_batched(Y, tol=1e-8)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) and torch.equal(a[3], b[3])
+    Yb = Y.clone()
+    Yb[3, 7] = float("nan")
+    with pytest.raises(P.BVLSError) as e:
+        s.solve_batched(Yb, tol=1e-8)
+    assert e.value.status == P.BVLS_ENONFINITE
+    c = s.solve_batched(Y, tol=1e-8)   # the handle stays usable
+    assert torch.equal(a[0], c[0])
+    s.close()

@@ -22,6 +22,8 @@ __all__ = [
     "nnls_abs_gaussian",
     "bvls_table2",
     "bvls_dirichlet_shared",
+    "nnls_shared",
+    "bvls_box_shared",
     "bvls_gaussian_box",
     "random_tiny",
 ]
@@ -161,6 +163,39 @@ def bvls_dirichlet_shared(m: int, n: int, B: int, k_support: int, noise: float, 
                    Y.astype(np.float32), np.zeros(n), np.ones(n), X,
                    dict(family="bvls_dirichlet_shared", m=m, n=n, B=B, k_support=k_support,
                         noise=noise, seed=seed))
+
+
+def nnls_shared(m: int, n: int, B: int, density: float, noise: float, seed: int, abs_matrix: bool = True,
+                x_low: float = 0.0, name: str | None = None) -> Problem:
+    """Batch of NNLS problems sharing one matrix with unit-norm columns.
+
+    A has entries |N(0,1)| (``abs_matrix``, the Table 1 family) or N(0,1).  Each x_b has
+    ``density*n`` nonzeros ~ U[x_low, 1] at random positions and y_b = A x_b + N(0, noise^2).
+    Returns y of shape (B, m) and x_true of shape (B, n).
+    """
+    rng = np.random.default_rng(seed)
+    G = rng.standard_normal((m, n))
+    A = _unit_columns(np.abs(G) if abs_matrix else G)
+    X = np.zeros((B, n))
+    for b in range(B):
+        supp = _sparse_support(rng, n, density)
+        X[b, supp] = rng.uniform(x_low, 1.0, size=supp.size)
+    Y = X @ A.T + noise * rng.standard_normal((B, m))
+    kind = "abs" if abs_matrix else "gauss"
+    return Problem(name or f"nnls_{kind}_shared_{m}x{n}_B{B}_s{seed}", A.astype(np.float32),
+                   Y.astype(np.float32), np.zeros(n), np.full(n, np.inf), X,
+                   dict(family="nnls_shared", m=m, n=n, B=B, density=density, noise=noise, seed=seed,
+                        abs_matrix=abs_matrix, x_low=x_low))
+
+
+def bvls_box_shared(m: int, n: int, B: int, box: float, seed: int, name: str | None = None) -> Problem:
+    """Batch of BVLS problems sharing an N(0,1) matrix, y_b ~ N(0,1), box [-box, box]."""
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((m, n))
+    Y = rng.standard_normal((B, m))
+    return Problem(name or f"bvls_box{box:g}_shared_{m}x{n}_B{B}_s{seed}", A.astype(np.float32),
+                   Y.astype(np.float32), np.full(n, -box), np.full(n, box), np.zeros((B, n)),
+                   dict(family="bvls_box_shared", m=m, n=n, B=B, box=box, seed=seed))
 
 
 def random_tiny(m: int, n: int, kind: str, seed: int) -> Problem:
