@@ -22,10 +22,22 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kStageBytes = 2 * kBTile * kBChunk * 2;  // A and B tiles of one K chunk (bf16)
+constexpr int kBEvalList = 256;  // columns per chunk of the evaluation's nonzero lists
+static_assert(kBEvalThreads / 32 == kBEvalInst, "one list-building warp per instance");
 
 __device__ __forceinline__ double warp_sum_dd(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
   return v;
+}
+
+// x_{k+1} = clip(x_k + b (x_k - x_{k-1}) + g_v / L, l, u) with double-float iterates.
+__device__ __forceinline__ float2 fista_step(float2 xk, float2 xp, float gv, float be, float2 invL2, float2 l2,
+                                             float2 u2) {
+  const float2 v = df2_add(xk, df2_mul(df2_sub(xk, xp), make_float2(be, 0.f)));
+  float2 xn = df2_add(v, df2_mul(make_float2(gv, 0.f), invL2));
+  if (df2_lt(xn, l2)) xn = l2;
+  if (df2_lt(u2, xn)) xn = u2;
+  return xn;
 }
 
 }  // namespace
@@ -78,7 +90,7 @@ __global__ void k_binit(BParams p, BBuffers b) {
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
     const int inst = (int)(idx / p.npad), j = (int)(idx % p.npad);
-    float xf = 0.f;
+    float2 xf = make_float2(0.f, 0.f);
     if (j < p.n) {
       double x = 0.0;
       if (b.X0) {
@@ -89,8 +101,9 @@ __global__ void k_binit(BParams p, BBuffers b) {
         }
       }
       x = fmin(fmax(x, p.l[j]), p.u[j]);   // x_0 = clip(x0, l, u)
-      xf = (float)x;
-      xf = fminf(fmaxf(xf, p.lf[j]), p.uf[j]);
+      xf = df2_from_double(x);
+      if (df2_lt(xf, p.l2[j])) xf = p.l2[j];
+      if (df2_lt(p.u2[j], xf)) xf = p.u2[j];
     }
     b.X[0][idx] = xf;
     b.X[1][idx] = xf;
@@ -134,7 +147,7 @@ cudaError_t launch_binit(const BParams& p, const BBuffers& b, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ tensor-core step
-// Grid (npad / 128 coordinate tiles, ceil(B / 128) instance tiles), 128 threads, one CTA per
+// Grid (npad / 128 coordinate tiles, ceil(B / 128) instance tiles), 512 threads, one CTA per
 // SM (128 KB of stages).  Operand K chunks of 64 stream through kBStages shared-memory
 // stages with 16-byte asynchronous copies; thread 0 issues four 128x128x16 MMAs per chunk and
 // commits them to the stage's mbarrier, which releases the stage for the chunk kBStages
@@ -150,14 +163,14 @@ __global__ void __launch_bounds__(kBStepThreads, 1) k_bstep(BParams p, BBuffers 
   __shared__ uint32_t s_tmem;
   __shared__ int s_inst[kBTile];
   __shared__ float s_beta[kBTile];
-  __shared__ float s_l[kBTile], s_u[kBTile];
-  __shared__ float s_dot[kBStepThreads / 32][kBTile];
+  __shared__ float2 s_l[kBTile], s_u[kBTile];
+  __shared__ float s_dot[4][kBTile];   // [TMEM lane quarter][instance column]
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int k = st->kbase + jrel;
   const int s = k & 1;
   const int MT = p.npad / kBTile;
-  {
+  if (tid < kBTile) {
     // momentum parameter of this iteration for instance column tid (Section 5, FISTA with
     // gradient restart): t_k from t_{k-1} and the restart test of iteration k-1
     const int q = nt * kBTile + tid;
@@ -175,8 +188,8 @@ __global__ void __launch_bounds__(kBStepThreads, 1) k_bstep(BParams p, BBuffers 
     }
     s_beta[tid] = beta;
     const int jj = mt * kBTile + tid;
-    s_l[tid] = jj < p.n ? p.lf[jj] : 0.f;
-    s_u[tid] = jj < p.n ? p.uf[jj] : 0.f;
+    s_l[tid] = jj < p.n ? p.l2[jj] : make_float2(0.f, 0.f);
+    s_u[tid] = jj < p.n ? p.u2[jj] : make_float2(0.f, 0.f);
   }
   if (warp == 0) tmem_alloc(&s_tmem, kBTile);
   if (tid == 0) {
@@ -240,32 +253,36 @@ __global__ void __launch_bounds__(kBStepThreads, 1) k_bstep(BParams p, BBuffers 
   }
   tc_fence_after();
 
-  // epilogue: thread = coordinate jg of this tile, 32 instance columns per TMEM load
-  const int i = warp * 32 + lane;
+  // epilogue: warp w reads TMEM lane quarter w % 4 (coordinates) and instance columns
+  // [32 (w / 4), 32 (w / 4) + 32); thread = coordinate jg
+  const int quarter = warp & 3;
+  const int i = quarter * 32 + lane;
   const int jg = mt * kBTile + i;
   const bool jv = jg < p.n;
-  const float lj = s_l[i], uj = s_u[i];
-  const float invL = p.invLf;
+  const float2 lj = s_l[i], uj = s_u[i];
+  const float2 invL2 = p.invL2;
   const float* __restrict__ Gp = b.G[s ^ 1];
   float* Gc = b.G[s];
-  const float* __restrict__ Xc = b.X[s];
-  float* Xn = b.X[s ^ 1];
+  const float2* __restrict__ Xc = b.X[s];
+  float2* Xn = b.X[s ^ 1];
   __nv_bfloat16* Dn = b.D[s ^ 1];
-  for (int c0 = 0; c0 < kBTile; c0 += 32) {
+  const int cbeg = (warp >> 2) * (kBTile / (kBStepThreads / 128));
+  for (int c0 = cbeg; c0 < cbeg + kBTile / (kBStepThreads / 128); c0 += 32) {
     if (s_inst[c0] < 0) break;  // active instances are packed at the front of the tile
     float acc[32];
-    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, acc);
+    tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, acc);
     float dv[32];
 #pragma unroll
     for (int c8 = 0; c8 < 32; c8 += 8) {
-      float gp[8], xk[8], xp[8];
+      float gp[8];
+      float2 xk[8], xp[8];
       uint8_t fl[8];
 #pragma unroll
       for (int cc = 0; cc < 8; ++cc) {  // loads first: eight instances in flight
         const int inst = s_inst[c0 + c8 + cc];
         gp[cc] = 0.f;
-        xk[cc] = 0.f;
-        xp[cc] = 0.f;
+        xk[cc] = make_float2(0.f, 0.f);
+        xp[cc] = xk[cc];
         fl[cc] = 1;
         if (inst >= 0 && jv) {
           const size_t o = (size_t)inst * p.npad + jg;
@@ -282,17 +299,19 @@ __global__ void __launch_bounds__(kBStepThreads, 1) k_bstep(BParams p, BBuffers 
         if (inst >= 0 && jv) {
           const size_t o = (size_t)inst * p.npad + jg;
           const float gk = gp[cc] - acc[c8 + cc];
-          float xn = xk[cc];
+          float2 xn = xk[cc];
+          float dx = 0.f;
           if (!fl[cc]) {
             const float be = s_beta[c0 + c8 + cc];
-            const float gv = fmaf(be, gk - gp[cc], gk);            // (1 + b) g_k - b g_{k-1}
-            const float v = fmaf(be, xk[cc] - xp[cc], xk[cc]);     // x_k + b (x_k - x_{k-1})
-            xn = fminf(fmaxf(fmaf(gv, invL, v), lj), uj);
-            dv[c8 + cc] = gv * (xn - xk[cc]);
+            const float gv = fmaf(be, gk - gp[cc], gk);  // (1 + b) g_k - b g_{k-1}
+            xn = fista_step(xk[cc], xp[cc], gv, be, invL2, lj, uj);
+            const float2 d = df2_sub(xn, xk[cc]);
+            dx = d.x + d.y;
+            dv[c8 + cc] = gv * dx;
           }
           Gc[o] = gk;
           Xn[o] = xn;
-          Dn[o] = __float2bfloat16_rn(xn - xk[cc]);
+          Dn[o] = __float2bfloat16_rn(dx);
         }
       }
     }
@@ -308,18 +327,13 @@ __global__ void __launch_bounds__(kBStepThreads, 1) k_bstep(BParams p, BBuffers 
         dv[t] = keep + __shfl_xor_sync(kFull, send, o);
       }
     }
-    s_dot[warp][c0 + lane] = dv[0];
+    s_dot[quarter][c0 + lane] = dv[0];
   }
   tc_fence_before();
   __syncthreads();
-  {
+  if (tid < kBTile) {
     const int inst = s_inst[tid];
-    if (inst >= 0) {
-      float d = 0.f;
-#pragma unroll
-      for (int w = 0; w < kBStepThreads / 32; ++w) d += s_dot[w][tid];
-      b.dotp[s][(size_t)mt * p.B + inst] = d;
-    }
+    if (inst >= 0) b.dotp[s][(size_t)mt * p.B + inst] = s_dot[0][tid] + s_dot[1][tid] + s_dot[2][tid] + s_dot[3][tid];
   }
   if (warp == 0) tmem_dealloc(tmem, kBTile);
   if (!ok && tid == 0) atomicOr(&st->error, 1);
@@ -341,18 +355,21 @@ cudaError_t launch_bstep(const BParams& p, const BBuffers& b, int j, cudaStream_
 //   phase 3  gap sums and the step (thread = coordinate);
 //   phase 4  sphere test; phase 5  outputs of the instances that stop.
 template <int PREC>
-__global__ void __launch_bounds__(kBEvalThreads) k_beval(BParams p, BBuffers b, int jrel) {
+__global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers b, int jrel) {
   BState* st = b.st;
   if (st->done) return;
   const int n_act = st->n_act;
   const int i0 = blockIdx.x * kBEvalInst;
   if (i0 >= n_act) return;
-  extern __shared__ float2 sr[];  // [m][kBEvalInst] residual (hi, lo)
+  extern __shared__ float2 sr[];  // [m][kBEvalInst] residual (hi, lo), then the flags
+  uint8_t* s_fl = reinterpret_cast<uint8_t*>(sr + (size_t)p.m * kBEvalInst);  // [kBEvalInst][npad]
   __shared__ int s_inst[kBEvalInst];
   __shared__ float s_beta[kBEvalInst];
-  __shared__ float sx[kBEvalInst][33];
-  __shared__ double s_red[kBEvalThreads / 32][kBEvalInst][5];
-  __shared__ double s_q[kBEvalInst][8];  // P, ||y||^2, eta_g, eps, rr, eta, gap, X1
+  __shared__ int s_lj[kBEvalInst][kBEvalList];
+  __shared__ float2 s_lx[kBEvalInst][kBEvalList];
+  __shared__ int s_cnt[kBEvalInst];
+  __shared__ double s_red[kBEvalThreads / 32][kBEvalInst][4];
+  __shared__ double s_q[kBEvalInst][8];  // P, ||y||^2, eta_g, eps, radius + eta, eta, gap, preserved
   __shared__ int s_stop[kBEvalInst];
   __shared__ int s_pins[kBEvalInst];
 
@@ -382,9 +399,17 @@ __global__ void __launch_bounds__(kBEvalThreads) k_beval(BParams p, BBuffers b, 
     s_pins[tid] = 0;
   }
   __syncthreads();
+  // the screened flags of the CTA's instances, one coalesced pass (1 = fixed, or no instance)
+  for (int q = tid; q < kBEvalInst * p.npad; q += kBEvalThreads) {
+    const int bb = q / p.npad, j = q - bb * p.npad;
+    const int inst = s_inst[bb];
+    s_fl[q] = inst >= 0 ? b.flags[(size_t)inst * p.npad + j] : (uint8_t)1;
+  }
 
-  // ---- phase 1: r = y - A x_k, one block of kBEvalThreads rows at a time
-  const float* __restrict__ Xc = b.X[s];
+  // ---- phase 1: r = y - A x_k, one block of kBEvalThreads rows at a time.  Warp bb lists
+  // the nonzero x_j of instance bb in a chunk of kBEvalList columns; every thread (one row)
+  // then runs over the lists with eight column loads in flight.
+  const float2* __restrict__ Xc = b.X[s];
   double pv[kBEvalInst], yv[kBEvalInst];
 #pragma unroll
   for (int bb = 0; bb < kBEvalInst; ++bb) {
@@ -399,27 +424,49 @@ __global__ void __launch_bounds__(kBEvalThreads) k_beval(BParams p, BBuffers b, 
       qs[bb] = 0.f;
       qc[bb] = 0.f;
     }
-    for (int jc = 0; jc < p.n; jc += 32) {
+    for (int jc = 0; jc < p.n; jc += kBEvalList) {
       {
-        const int bb = tid >> 5, jj = tid & 31;
+        const int bb = warp;  // kBEvalThreads / 32 == kBEvalInst
         const int inst = s_inst[bb];
-        sx[bb][jj] = (inst >= 0 && jc + jj < p.n) ? Xc[(size_t)inst * p.npad + jc + jj] : 0.f;
+        int cnt = 0;
+        float2 xs[kBEvalList / 32];
+#pragma unroll
+        for (int t = 0; t < kBEvalList / 32; ++t) {  // loads first
+          const int j = jc + t * 32 + lane;
+          xs[t] = (inst >= 0 && j < p.n) ? Xc[(size_t)inst * p.npad + j] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int t = 0; t < kBEvalList / 32; ++t) {
+          const bool nz = df2_nonzero(xs[t]);
+          const unsigned msk = __ballot_sync(kFull, nz);
+          if (nz) {
+            const int pos = cnt + __popc(msk & ((1u << lane) - 1u));
+            s_lj[bb][pos] = jc + t * 32 + lane;
+            s_lx[bb][pos] = xs[t];
+          }
+          cnt += __popc(msk);
+        }
+        if (lane == 0) s_cnt[bb] = cnt;
       }
       __syncthreads();
-      const int jn = min(32, p.n - jc);
-      for (int jj = 0; jj < jn; ++jj) {
-        float xv[kBEvalInst];
-        bool any = false;
+      if (i < p.m) {
 #pragma unroll
         for (int bb = 0; bb < kBEvalInst; ++bb) {
-          xv[bb] = sx[bb][jj];
-          any |= xv[bb] != 0.f;
-        }
-        if (!any || i >= p.m) continue;
-        const float a = p.A[(size_t)(jc + jj) * p.lda + i];
+          const int cnt = s_cnt[bb];
+          for (int e = 0; e < cnt; e += 8) {
+            float a[8];
 #pragma unroll
-        for (int bb = 0; bb < kBEvalInst; ++bb)
-          if (xv[bb] != 0.f) df_fma(qs[bb], qc[bb], a, xv[bb], 0.f);
+            for (int u = 0; u < 8; ++u)
+              a[u] = e + u < cnt ? __ldg(p.A + (size_t)s_lj[bb][e + u] * p.lda + i) : 0.f;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              if (e + u < cnt) {
+                const float2 x = s_lx[bb][e + u];
+                df_fma(qs[bb], qc[bb], a[u], x.x, x.y);
+              }
+            }
+          }
+        }
       }
       __syncthreads();
     }
@@ -467,163 +514,185 @@ __global__ void __launch_bounds__(kBEvalThreads) k_beval(BParams p, BBuffers b, 
   }
   __syncthreads();
 
-  // ---- phase 2: correlations of the preserved coordinates
+  // ---- phase 2: correlations of the preserved coordinates, two columns per warp step
+  // (the residual loads from shared memory serve both)
   double epsm = 0.0;  // lane bb < kBEvalInst: translation step candidate of instance bb
   {
     const double eta_g = lane < kBEvalInst ? s_q[lane][2] : 0.0;
     const int inst_l = lane < kBEvalInst ? s_inst[lane] : -1;
-    for (int j = warp; j < p.n; j += kBEvalThreads / 32) {
-      const bool need_l = inst_l >= 0 && b.flags[(size_t)inst_l * p.npad + j] == 0;
-      const unsigned need = __ballot_sync(kFull, need_l);
-      if (!need) continue;
-      const float* __restrict__ col = p.A + (size_t)j * p.lda;
-      float sa[kBEvalInst], ca[kBEvalInst];
+    constexpr int W = kBEvalThreads / 32;
+    for (int j0 = 2 * warp; j0 < p.n; j0 += 2 * W) {
+      const int j1 = j0 + 1;
+      const bool n0 = lane < kBEvalInst && s_fl[lane * p.npad + j0] == 0;
+      const bool n1 = lane < kBEvalInst && j1 < p.n && s_fl[lane * p.npad + j1] == 0;
+      const unsigned need0 = __ballot_sync(kFull, n0), need1 = __ballot_sync(kFull, n1);
+      if (!(need0 | need1)) continue;
+      const float* __restrict__ c0 = p.A + (size_t)j0 * p.lda;
+      const float* __restrict__ c1 = p.A + (size_t)(j1 < p.n ? j1 : j0) * p.lda;
+      float sa[2][kBEvalInst], ca[2][kBEvalInst];
 #pragma unroll
       for (int bb = 0; bb < kBEvalInst; ++bb) {
-        sa[bb] = 0.f;
-        ca[bb] = 0.f;
+        sa[0][bb] = sa[1][bb] = 0.f;
+        ca[0][bb] = ca[1][bb] = 0.f;
       }
+#pragma unroll 2
       for (int i = lane; i < p.m; i += 32) {
-        const float a = col[i];
+        const float a0 = __ldg(c0 + i), a1 = __ldg(c1 + i);
         const float4* rr = reinterpret_cast<const float4*>(sr + (size_t)i * kBEvalInst);
 #pragma unroll
         for (int h = 0; h < kBEvalInst / 2; ++h) {
           const float4 v = rr[h];
           if (PREC == kX2) {
-            df_fma(sa[2 * h], ca[2 * h], a, v.x, v.y);
-            df_fma(sa[2 * h + 1], ca[2 * h + 1], a, v.z, v.w);
+            df_fma(sa[0][2 * h], ca[0][2 * h], a0, v.x, v.y);
+            df_fma(sa[0][2 * h + 1], ca[0][2 * h + 1], a0, v.z, v.w);
+            df_fma(sa[1][2 * h], ca[1][2 * h], a1, v.x, v.y);
+            df_fma(sa[1][2 * h + 1], ca[1][2 * h + 1], a1, v.z, v.w);
           } else {
-            sa[2 * h] = fmaf(a, v.x, sa[2 * h]);
-            sa[2 * h + 1] = fmaf(a, v.z, sa[2 * h + 1]);
+            sa[0][2 * h] = fmaf(a0, v.x, sa[0][2 * h]);
+            sa[0][2 * h + 1] = fmaf(a0, v.z, sa[0][2 * h + 1]);
+            sa[1][2 * h] = fmaf(a1, v.x, sa[1][2 * h]);
+            sa[1][2 * h + 1] = fmaf(a1, v.z, sa[1][2 * h + 1]);
           }
         }
       }
-      float gs = 0.f, gc = 0.f;
 #pragma unroll
-      for (int bb = 0; bb < kBEvalInst; ++bb) {
-        float x = sa[bb], c = ca[bb];
+      for (int c = 0; c < 2; ++c) {
+        float gs = 0.f, gc = 0.f;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const float ox = __shfl_xor_sync(kFull, x, o);
-          if (PREC == kX2) {
-            const float oc = __shfl_xor_sync(kFull, c, o);
-            df_add(x, c, ox, oc);
-          } else {
-            x += ox;
+        for (int bb = 0; bb < kBEvalInst; ++bb) {
+          float x = sa[c][bb], cc = ca[c][bb];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            const float ox = __shfl_xor_sync(kFull, x, o);
+            if (PREC == kX2) {
+              const float oc = __shfl_xor_sync(kFull, cc, o);
+              df_add(x, cc, ox, oc);
+            } else {
+              x += ox;
+            }
+          }
+          if (lane == bb) {
+            gs = x;
+            gc = PREC == kX2 ? cc : 0.f;
           }
         }
-        if (lane == bb) {
-          gs = x;
-          gc = PREC == kX2 ? c : 0.f;
-        }
-      }
-      if (need_l) {
-        const float2 g2 = df2_norm(gs, gc);
-        b.Ge[(size_t)inst_l * p.npad + j] = g2;
-        if (trans && p.jinf[j]) {
-          const double nr = p.nrm[j];
-          if (nr > 0.0) {
-            const double den = -p.w[j] - p.gamma_w * nr * p.t_norm;
-            epsm = fmax(epsm, fmax(df2_to_double(g2) + eta_g * nr, 0.0) / den);
+        const int j = c == 0 ? j0 : j1;
+        if (c == 0 ? n0 : n1) {
+          const float2 g2 = df2_norm(gs, gc);
+          b.Ge[(size_t)inst_l * p.npad + j] = g2;
+          if (trans && p.jinf[j]) {
+            const double nr = p.nrm[j];
+            if (nr > 0.0) {
+              const double den = -p.w[j] - p.gamma_w * nr * p.t_norm;
+              epsm = fmax(epsm, fmax(df2_to_double(g2) + eta_g * nr, 0.0) / den);
+            }
           }
         }
       }
     }
   }
-  if (lane < kBEvalInst) s_red[warp][lane][4] = epsm;
+  if (lane < kBEvalInst) s_red[warp][lane][3] = epsm;
   __syncthreads();
   if (tid < kBEvalInst) {
     double e = 0.0;
-    for (int w = 0; w < kBEvalThreads / 32; ++w) e = fmax(e, s_red[w][tid][4]);
-    s_q[tid][3] = trans ? e : 0.0;
+    for (int w = 0; w < kBEvalThreads / 32; ++w) e = fmax(e, s_red[w][tid][3]);
+    const double eps = trans ? e : 0.0;
+    s_q[tid][3] = eps;
+    const double rnorm = sqrt(2.0 * s_q[tid][0]) * (1.0 + 1e-6);
+    s_q[tid][5] = p.Cg * rnorm + (trans ? eps * p.gamma_w * p.t_norm : 0.0);  // eta
   }
   __syncthreads();
 
-  // ---- phase 3: gap sums (nonnegative-sum form of P - D) and the step
+  // ---- phase 3: gap terms and the step.  Each term of the nonnegative-sum form of P - D is
+  // a convex piecewise-linear function of gt_j = a_j^T theta; with the computed gt_j within
+  // e_j = eta ||a_j|| of the exact one, the term is bounded by its larger value at the two
+  // ends of [gt_j - e_j, gt_j + e_j].
   {
     const float* __restrict__ Gp = b.G[s ^ 1];
     float* Gc = b.G[s];
-    float* Xn = b.X[s ^ 1];
+    float2* Xn = b.X[s ^ 1];
     __nv_bfloat16* Dn = b.D[s ^ 1];
-    const float invL = p.invLf;
+    const float2 invL2 = p.invL2;
     for (int bb = 0; bb < kBEvalInst; ++bb) {
       const int inst = s_inst[bb];
       if (inst < 0) break;  // active instances are packed at the front
       const float be = s_beta[bb];
-      const double eps = s_q[bb][3];
-      double va = 0.0, vc = 0.0, vx = 0.0, vd = 0.0, vp = 0.0;
+      const double eps = s_q[bb][3], eta = s_q[bb][5];
+      double va = 0.0, vx = 0.0, vd = 0.0, vp = 0.0;
+#pragma unroll 2
       for (int j = tid; j < p.n; j += kBEvalThreads) {
         const size_t o = (size_t)inst * p.npad + j;
+        const float2 xk = Xc[o];
+        const float2 xp = Xn[o];
+        const float2 g2 = b.Ge[o];
+        const float gp = Gp[o];
         const double nr = p.nrm[j];
-        const float xk = Xc[o];
-        vx += fabs((double)xk) * nr;
-        if (b.flags[o]) {
+        const double x = df2_to_double(xk);
+        vx += fabs(x) * nr;
+        if (s_fl[bb * p.npad + j]) {
           Xn[o] = xk;
           Dn[o] = __float2bfloat16_rn(0.f);
           continue;
         }
         vp += 1.0;
-        const float2 g2 = b.Ge[o];
         if (p.dual_mode != kZero) {
-          const double x = (double)xk, lj = p.l[j];
+          const double lj = p.l[j];
           const double gt = df2_to_double(g2) + (trans ? eps * p.w[j] : 0.0);
+          const double e = eta * nr;
           if (p.jinf[j]) {
-            va += (x - lj) * fmax(-gt, 0.0);
-            vc += (x - lj) * nr;
+            va += (x - lj) * fmax(e - gt, 0.0);
           } else {
             const double uj = p.u[j];
-            va += (uj - x) * fmax(gt, 0.0) + (x - lj) * fmax(-gt, 0.0);
-            vc += fmax(uj - x, x - lj) * nr;
+            const double lo = gt - e, hi = gt + e;
+            const double h_lo = (uj - x) * fmax(lo, 0.0) + (x - lj) * fmax(-lo, 0.0);
+            const double h_hi = (uj - x) * fmax(hi, 0.0) + (x - lj) * fmax(-hi, 0.0);
+            va += fmax(h_lo, h_hi);
           }
         }
         const float gk = g2.x;
-        const float gp = Gp[o], xp = Xn[o];
         const float gv = fmaf(be, gk - gp, gk);
-        const float v = fmaf(be, xk - xp, xk);
-        const float xn = fminf(fmaxf(fmaf(gv, invL, v), p.lf[j]), p.uf[j]);
+        const float2 xn = fista_step(xk, xp, gv, be, invL2, p.l2[j], p.u2[j]);
+        const float2 d = df2_sub(xn, xk);
+        const float dx = d.x + d.y;
         Gc[o] = gk;
         Xn[o] = xn;
-        Dn[o] = __float2bfloat16_rn(xn - xk);
-        vd += (double)gv * (double)(xn - xk);
+        Dn[o] = __float2bfloat16_rn(dx);
+        vd += (double)gv * (double)dx;
       }
       va = warp_sum_dd(va);
-      vc = warp_sum_dd(vc);
       vx = warp_sum_dd(vx);
       vd = warp_sum_dd(vd);
       vp = warp_sum_dd(vp);
       if (lane == 0) {
         s_red[warp][bb][0] = va;
-        s_red[warp][bb][1] = vc;
-        s_red[warp][bb][2] = vx;
-        s_red[warp][bb][3] = vd;
-        s_red[warp][bb][4] = vp;
+        s_red[warp][bb][1] = vx;
+        s_red[warp][bb][2] = vd;
+        s_red[warp][bb][3] = vp;
       }
     }
   }
   __syncthreads();
   if (tid < kBEvalInst) {
-    double a = 0.0, c = 0.0, x1 = 0.0, d = 0.0, np = 0.0;
+    double a = 0.0, x1 = 0.0, d = 0.0, np = 0.0;
     for (int w = 0; w < kBEvalThreads / 32; ++w) {
       a += s_red[w][tid][0];
-      c += s_red[w][tid][1];
-      x1 += s_red[w][tid][2];
-      d += s_red[w][tid][3];
-      np += s_red[w][tid][4];
+      x1 += s_red[w][tid][1];
+      d += s_red[w][tid][2];
+      np += s_red[w][tid][3];
     }
     const int inst = s_inst[tid];
     int stop = 0;
     if (inst >= 0) {
       const double P = s_q[tid][0];
-      const double eps = s_q[tid][3];
+      const double eps = s_q[tid][3], eta = s_q[tid][5];
       const double rnorm = sqrt(2.0 * P) * (1.0 + 1e-6);
-      const double eta = p.Cg * rnorm + (trans ? eps * p.gamma_w * p.t_norm : 0.0);
       const double E_r = p.Cf * x1 + p.Csub * (rnorm + sqrt(s_q[tid][1]) + x1);
       double gap;
       if (p.dual_mode == kZero) {
         gap = 0.5 * (rnorm + E_r) * (rnorm + E_r);
       } else {
         const double dd = E_r + eps * p.t_norm;
-        gap = a + eta * c + 0.5 * dd * dd;
+        gap = a + 0.5 * dd * dd;
       }
       gap *= (1.0 + 1e-12);
       s_q[tid][4] = sqrt(2.0 * gap) * (1.0 + 1e-12) + eta;  // radius + margin, per unit ||a_j||
@@ -641,48 +710,49 @@ __global__ void __launch_bounds__(kBEvalThreads) k_beval(BParams p, BBuffers b, 
   // ---- phase 4: sphere test (Eq. (safe_rule)); a coordinate is fixed once x_k and x_{k+1}
   // both sit at the bound the test gives
   if (p.screening && p.dual_mode != kZero) {
-    const float* __restrict__ Xn = b.X[s ^ 1];
-    for (int j = tid; j < p.n; j += kBEvalThreads) {
-      const double nr = p.nrm[j];
-      if (!(nr > 0.0)) continue;
-      const double wj = trans ? p.w[j] : 0.0;
-      const int ji = p.jinf[j];
-      const float ljf = p.lf[j], ujf = p.uf[j];
-#pragma unroll
-      for (int bb = 0; bb < kBEvalInst; ++bb) {
-        const int inst = s_inst[bb];
-        if (inst < 0) continue;
+    const float2* __restrict__ Xn = b.X[s ^ 1];
+    for (int bb = 0; bb < kBEvalInst; ++bb) {
+      const int inst = s_inst[bb];
+      if (inst < 0) break;
+      const double eps = s_q[bb][3], rr = s_q[bb][4];
+      int pins = 0;
+      for (int j = tid; j < p.n; j += kBEvalThreads) {
+        if (s_fl[bb * p.npad + j]) continue;
+        const double nr = p.nrm[j];
+        if (!(nr > 0.0)) continue;
         const size_t o = (size_t)inst * p.npad + j;
-        if (b.flags[o]) continue;
-        const double gt = df2_to_double(b.Ge[o]) + s_q[bb][3] * wj;
-        const double thr = s_q[bb][4] * nr * (1.0 + 1e-12);
+        const double gt = df2_to_double(b.Ge[o]) + (trans ? eps * p.w[j] : 0.0);
+        const double thr = rr * nr * (1.0 + 1e-12);
         int pin = 0;
-        float bnd = 0.f;
+        float2 bnd = make_float2(0.f, 0.f);
         if (gt < -thr) {
           pin = 1;
-          bnd = ljf;
-        } else if (!ji && gt > thr) {
+          bnd = p.l2[j];
+        } else if (!p.jinf[j] && gt > thr) {
           pin = 2;
-          bnd = ujf;
+          bnd = p.u2[j];
         }
-        if (pin && Xc[o] == bnd && Xn[o] == bnd) {
+        if (pin && df2_eq(Xc[o], bnd) && df2_eq(Xn[o], bnd)) {
           b.flags[o] = (uint8_t)pin;
-          atomicAdd(&s_pins[bb], 1);
+          s_fl[bb * p.npad + j] = (uint8_t)pin;
+          ++pins;
         }
       }
+      for (int o2 = 16; o2 > 0; o2 >>= 1) pins += __shfl_xor_sync(kFull, pins, o2);
+      if (lane == 0 && pins) atomicAdd(&s_pins[bb], pins);
     }
     __syncthreads();
   }
 
   // ---- phase 5: outputs of the instances that stop at this evaluation
-  for (int j = tid; j < p.n; j += kBEvalThreads) {
-#pragma unroll
-    for (int bb = 0; bb < kBEvalInst; ++bb) {
-      const int inst = s_inst[bb];
-      if (inst < 0 || !s_stop[bb]) continue;
+  for (int bb = 0; bb < kBEvalInst; ++bb) {
+    const int inst = s_inst[bb];
+    if (inst < 0) break;
+    if (!s_stop[bb]) continue;
+    for (int j = tid; j < p.n; j += kBEvalThreads) {
+      const uint8_t f = s_fl[bb * p.npad + j];
       const size_t o = (size_t)inst * p.npad + j;
-      const uint8_t f = b.flags[o];
-      double x = f == 1 ? p.l[j] : f == 2 ? p.u[j] : fmin(fmax((double)Xc[o], p.l[j]), p.u[j]);
+      const double x = f == 1 ? p.l[j] : f == 2 ? p.u[j] : fmin(fmax(df2_to_double(Xc[o]), p.l[j]), p.u[j]);
       b.xout[(size_t)inst * p.n + j] = x;
     }
   }
@@ -701,11 +771,14 @@ __global__ void __launch_bounds__(kBEvalThreads) k_beval(BParams p, BBuffers b, 
   if (blockIdx.x == 0 && tid == 0) st->sum_eval += (double)n_act;
 }
 
-size_t beval_smem_bytes(int m) { return (size_t)m * kBEvalInst * sizeof(float2); }
+size_t beval_smem_bytes(int m, int npad) {
+  return (size_t)m * kBEvalInst * sizeof(float2) + (size_t)kBEvalInst * npad;
+}
+
 
 cudaError_t launch_beval(const BParams& p, const BBuffers& b, int j, int precision, cudaStream_t s) {
   const int grid = (p.B + kBEvalInst - 1) / kBEvalInst;
-  const size_t sm = beval_smem_bytes(p.m);
+  const size_t sm = beval_smem_bytes(p.m, p.npad);
   if (precision == kX2) k_beval<kX2><<<grid, kBEvalThreads, sm, s>>>(p, b, j);
   else k_beval<kF32><<<grid, kBEvalThreads, sm, s>>>(p, b, j);
   return cudaGetLastError();
@@ -757,12 +830,13 @@ __global__ void __launch_bounds__(1024) k_bcompact(BParams p, BBuffers b) {
   }
 }
 
-cudaError_t batch_configure(int m) {
+cudaError_t batch_configure(int m, int npad) {
   cudaError_t e = cudaFuncSetAttribute(k_bstep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bstep_smem_bytes());
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_beval<kX2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)beval_smem_bytes(m));
+  e = cudaFuncSetAttribute(k_beval<kX2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)beval_smem_bytes(m, npad));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_beval<kF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)beval_smem_bytes(m));
+  return cudaFuncSetAttribute(k_beval<kF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)beval_smem_bytes(m, npad));
 }
 
 cudaError_t launch_bcompact(const BParams& p, const BBuffers& b, cudaStream_t s) {

@@ -11,6 +11,9 @@
 //   otherwise    tensor-core step: g_k = g_{k-1} - H~ d_k with H~ = bf16(A^T A) and
 //                d_k = bf16(x_k - x_{k-1}), one tcgen05 GEMM over all active instances
 //                with the step fused into its epilogue.
+// The iterates are double-float pairs: with float32 iterates a coordinate stops moving once
+// |g_j| / L falls below half an ulp of x_j, which floors the gap far above 1e-6 when L is
+// in the hundreds.  Correlations and momentum stay float32.
 // The Gram form gives A^T (y - A x_k) = A^T (y - A x_{k-1}) - A^T A (x_k - x_{k-1}) exactly;
 // with bf16 operands the error of a step is proportional to |x_k - x_{k-1}|, so it vanishes
 // as the iteration converges, and every evaluation restarts the recurrence from the exact
@@ -26,7 +29,7 @@ namespace bvls {
 constexpr int kBTile = 128;        // coordinates per M tile = instances per N tile
 constexpr int kBChunk = 64;        // K elements per shared-memory stage (128 bytes of bf16)
 constexpr int kBStages = 4;        // stages in flight
-constexpr int kBStepThreads = 128;
+constexpr int kBStepThreads = 512;  // 16 warps: 4 TMEM lane quarters x 4 column groups
 constexpr int kBEvalInst = 8;      // instances per CTA of the evaluation kernel
 constexpr int kBEvalThreads = 256;
 constexpr int kBMaxRows = 1024;    // m limit: the residuals of a CTA's instances sit in shared memory
@@ -57,10 +60,10 @@ struct BParams {
   const double* nrm;       // ||a_j||
   const double* w;         // a_j^T t (translation mode)
   const uint8_t* jinf;
-  const float* lf;         // bounds rounded to float32 (clip of the float32 iterates)
-  const float* uf;
+  const float2* l2;        // bounds as double-float pairs (clip of the iterates)
+  const float2* u2;
   double invL;
-  float invLf;
+  float2 invL2;            // 1 / L as a double-float pair
   double t_norm, gamma_w;
   double Cg;               // |computed a_j^T r - a_j^T r| <= Cg ||a_j|| ||r||
   double Cf;               // residual rounding: <= Cf sum_j |x_j| ||a_j|| (2-norm)
@@ -74,7 +77,7 @@ struct BParams {
 };
 
 struct BBuffers {
-  float* X[2];             // B x npad: x_k in slot k & 1 (x_{k-1} in the other)
+  float2* X[2];            // B x npad: x_k in slot k & 1 (x_{k-1} in the other), double-float
   float* G[2];             // B x npad: g_k in slot k & 1
   __nv_bfloat16* D[2];     // (B + 1) x npad: bf16(x_k - x_{k-1}) in slot k & 1; row B is zero
   float2* Ge;              // B x npad: correlations of the last evaluation (double-float)
@@ -102,7 +105,7 @@ cudaError_t launch_beval(const BParams& p, const BBuffers& b, int j, int precisi
 cudaError_t launch_bcompact(const BParams& p, const BBuffers& b, cudaStream_t s);
 cudaError_t launch_bchunk_end(const BBuffers& b, int chunk_len, cudaStream_t s);
 size_t bstep_smem_bytes();
-cudaError_t batch_configure(int m);  // shared-memory attributes of the step and evaluation kernels
-size_t beval_smem_bytes(int m);
+cudaError_t batch_configure(int m, int npad);  // shared-memory attributes of the step and evaluation kernels
+size_t beval_smem_bytes(int m, int npad);
 
 }  // namespace bvls

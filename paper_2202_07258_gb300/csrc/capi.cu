@@ -77,7 +77,6 @@ struct bvls_handle {
   // batched solve (shared A): bf16 Gram matrix, float32 bounds, workspace of capacity b_cap
   int b_npad = 0;
   __nv_bfloat16* bH = nullptr;
-  float *lf = nullptr, *uf = nullptr;
   int b_cap = 0;
   BBuffers bb{};
   float* bY = nullptr;
@@ -652,31 +651,14 @@ bvls_status balloc(bvls_handle* h, T** p, size_t count) {
   return BVLS_OK;
 }
 
-// Gram matrix, float32 bounds (rounded inward) and the workspace for B instances.
+// Gram matrix and the workspace for B instances.
 bvls_status batch_prepare(bvls_handle* h, int B) {
   const int n = h->n;
   if (!h->bH) {
     h->b_npad = (n + kBTile - 1) / kBTile * kBTile;
-    CK(batch_configure(h->m));
+    CK(batch_configure(h->m, h->b_npad));
     TRY(dalloc(h, &h->bH, (size_t)h->b_npad * h->b_npad));
     CK(launch_bgram(h->A, h->lda, h->m, n, h->b_npad, h->bH, h->s));
-    std::vector<double> lv(n), uv(n);
-    CK(cudaMemcpyAsync(lv.data(), h->l, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
-    CK(cudaMemcpyAsync(uv.data(), h->u, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
-    CK(cudaStreamSynchronize(h->s));
-    std::vector<float> lf(n), uf(n);
-    for (int j = 0; j < n; ++j) {
-      float a = (float)lv[j];
-      if ((double)a < lv[j]) a = std::nextafter(a, INFINITY);
-      float b = (float)uv[j];
-      if ((double)b > uv[j]) b = std::nextafter(b, -INFINITY);
-      lf[j] = a;
-      uf[j] = b;
-    }
-    TRY(dalloc(h, &h->lf, n));
-    TRY(dalloc(h, &h->uf, n));
-    CK(cudaMemcpyAsync(h->lf, lf.data(), sizeof(float) * n, cudaMemcpyHostToDevice, h->s));
-    CK(cudaMemcpyAsync(h->uf, uf.data(), sizeof(float) * n, cudaMemcpyHostToDevice, h->s));
     CK(cudaStreamSynchronize(h->s));
   }
   if (B <= h->b_cap) return BVLS_OK;
@@ -731,11 +713,11 @@ BParams make_bparams(bvls_handle* h, const bvls_opts& o, int max_iter, int B) {
   p.nrm = h->nrm;
   p.w = h->w;
   p.jinf = h->jinf;
-  p.lf = h->lf;
-  p.uf = h->uf;
+  p.l2 = h->l2;
+  p.u2 = h->u2;
   const double L = o.lipschitz > 0.0 ? o.lipschitz : h->L;
   p.invL = 1.0 / L;
-  p.invLf = (float)p.invL;
+  p.invL2 = df2_from_double(p.invL);
   p.t_norm = h->t_norm;
   p.gamma_w = h->gamma_w;
   // Rounding of the evaluation products (see common.cuh for the double-float bound):
