@@ -361,15 +361,20 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
   const int n_act = st->n_act;
   const int i0 = blockIdx.x * kBEvalInst;
   if (i0 >= n_act) return;
-  extern __shared__ float2 sr[];  // [m][kBEvalInst] residual (hi, lo), then the flags
-  uint8_t* s_fl = reinterpret_cast<uint8_t*>(sr + (size_t)p.m * kBEvalInst);  // [kBEvalInst][npad]
+  // dynamic shared memory: the residuals [m][kBEvalInst] (hi, lo), the screened flags
+  // [kBEvalInst][npad] (bit 2 marks a correlation recomputed in double-float) and the
+  // per-instance lists of coordinates to recompute [kBEvalInst][npad]
+  extern __shared__ float2 sr[];
+  uint8_t* s_fl = reinterpret_cast<uint8_t*>(sr + (size_t)p.m * kBEvalInst);
+  uint16_t* s_item = reinterpret_cast<uint16_t*>(s_fl + (size_t)kBEvalInst * p.npad);
   __shared__ int s_inst[kBEvalInst];
   __shared__ float s_beta[kBEvalInst];
   __shared__ int s_lj[kBEvalInst][kBEvalList];
   __shared__ float2 s_lx[kBEvalInst][kBEvalList];
   __shared__ int s_cnt[kBEvalInst];
   __shared__ double s_red[kBEvalThreads / 32][kBEvalInst][4];
-  __shared__ double s_q[kBEvalInst][8];  // P, ||y||^2, eta_g, eps, radius + eta, eta, gap, preserved
+  __shared__ double s_q[kBEvalInst][10];  // P, ||y||^2, eta_g, eps, radius + eta, eta, gap, preserved,
+                                          // eta of the recomputed correlations
   __shared__ int s_stop[kBEvalInst];
   __shared__ int s_pins[kBEvalInst];
 
@@ -599,9 +604,57 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
     const double eps = trans ? e : 0.0;
     s_q[tid][3] = eps;
     const double rnorm = sqrt(2.0 * s_q[tid][0]) * (1.0 + 1e-6);
-    s_q[tid][5] = p.Cg * rnorm + (trans ? eps * p.gamma_w * p.t_norm : 0.0);  // eta
+    const double et = trans ? eps * p.gamma_w * p.t_norm : 0.0;
+    s_q[tid][5] = p.Cg * rnorm + et;    // eta of the correlations of this precision
+    s_q[tid][8] = p.Cg2 * rnorm + et;   // eta of double-float correlations
   }
   __syncthreads();
+
+  if (PREC == kF32) {
+    // ---- phase 2b: a gap term depends on the rounding of its correlation only when the
+    // coordinate is free or its correlation is within the margin of zero; those
+    // correlations are recomputed in double-float (lane = coordinate, all m rows).
+    const int bb = warp;
+    const int inst = s_inst[bb];
+    int cnt = 0;
+    if (inst >= 0) {
+      const double eps = s_q[bb][3], eF = s_q[bb][5];
+      for (int jc = 0; jc < p.n; jc += 32) {
+        const int j = jc + lane;
+        bool ref = false;
+        if (j < p.n && (s_fl[bb * p.npad + j] & 3) == 0) {
+          const size_t o = (size_t)inst * p.npad + j;
+          const double nr = p.nrm[j];
+          if (nr > 0.0) {
+            const float2 xk = Xc[o];
+            const double gt = (double)b.Ge[o].x + (trans ? eps * p.w[j] : 0.0);
+            const double e = eF * nr;
+            const bool at_l = df2_eq(xk, p.l2[j]);
+            const bool at_u = !p.jinf[j] && df2_eq(xk, p.u2[j]);
+            // at l_j with u_j = +inf the term (x_j - l_j)(-gt)^+ is zero whatever gt is
+            ref = at_l ? (!p.jinf[j] && gt + e > 0.0) : at_u ? (gt - e < 0.0) : true;
+          }
+        }
+        const unsigned msk = __ballot_sync(kFull, ref);
+        if (ref) s_item[bb * p.npad + cnt + __popc(msk & ((1u << lane) - 1u))] = (uint16_t)j;
+        cnt += __popc(msk);
+      }
+      __syncwarp();
+      for (int t = lane; t < cnt; t += 32) {
+        const int j = s_item[bb * p.npad + t];
+        const float* __restrict__ col = p.A + (size_t)j * p.lda;
+        float sh = 0.f, sc = 0.f;
+#pragma unroll 4
+        for (int i = 0; i < p.m; ++i) {
+          const float2 r = sr[(size_t)i * kBEvalInst + bb];
+          df_fma(sh, sc, __ldg(col + i), r.x, r.y);
+        }
+        b.Ge[(size_t)inst * p.npad + j] = df2_norm(sh, sc);
+        s_fl[bb * p.npad + j] |= 4;
+      }
+    }
+    __syncthreads();
+  }
 
   // ---- phase 3: gap terms and the step.  Each term of the nonnegative-sum form of P - D is
   // a convex piecewise-linear function of gt_j = a_j^T theta; with the computed gt_j within
@@ -617,7 +670,7 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
       const int inst = s_inst[bb];
       if (inst < 0) break;  // active instances are packed at the front
       const float be = s_beta[bb];
-      const double eps = s_q[bb][3], eta = s_q[bb][5];
+      const double eps = s_q[bb][3], eta = s_q[bb][5], eta_ref = s_q[bb][8];
       double va = 0.0, vx = 0.0, vd = 0.0, vp = 0.0;
 #pragma unroll 2
       for (int j = tid; j < p.n; j += kBEvalThreads) {
@@ -629,7 +682,8 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
         const double nr = p.nrm[j];
         const double x = df2_to_double(xk);
         vx += fabs(x) * nr;
-        if (s_fl[bb * p.npad + j]) {
+        const uint8_t fl = s_fl[bb * p.npad + j];
+        if (fl & 3) {
           Xn[o] = xk;
           Dn[o] = __float2bfloat16_rn(0.f);
           continue;
@@ -638,7 +692,7 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
         if (p.dual_mode != kZero) {
           const double lj = p.l[j];
           const double gt = df2_to_double(g2) + (trans ? eps * p.w[j] : 0.0);
-          const double e = eta * nr;
+          const double e = ((fl & 4) ? eta_ref : eta) * nr;
           if (p.jinf[j]) {
             va += (x - lj) * fmax(e - gt, 0.0);
           } else {
@@ -717,7 +771,7 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
       const double eps = s_q[bb][3], rr = s_q[bb][4];
       int pins = 0;
       for (int j = tid; j < p.n; j += kBEvalThreads) {
-        if (s_fl[bb * p.npad + j]) continue;
+        if (s_fl[bb * p.npad + j] & 3) continue;
         const double nr = p.nrm[j];
         if (!(nr > 0.0)) continue;
         const size_t o = (size_t)inst * p.npad + j;
@@ -750,7 +804,7 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
     if (inst < 0) break;
     if (!s_stop[bb]) continue;
     for (int j = tid; j < p.n; j += kBEvalThreads) {
-      const uint8_t f = s_fl[bb * p.npad + j];
+      const uint8_t f = s_fl[bb * p.npad + j] & 3;
       const size_t o = (size_t)inst * p.npad + j;
       const double x = f == 1 ? p.l[j] : f == 2 ? p.u[j] : fmin(fmax(df2_to_double(Xc[o]), p.l[j]), p.u[j]);
       b.xout[(size_t)inst * p.n + j] = x;
@@ -772,7 +826,7 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
 }
 
 size_t beval_smem_bytes(int m, int npad) {
-  return (size_t)m * kBEvalInst * sizeof(float2) + (size_t)kBEvalInst * npad;
+  return (size_t)m * kBEvalInst * sizeof(float2) + (size_t)kBEvalInst * npad * (1 + sizeof(uint16_t));
 }
 
 

@@ -65,7 +65,8 @@ struct BParams {
   double invL;
   float2 invL2;            // 1 / L as a double-float pair
   double t_norm, gamma_w;
-  double Cg;               // |computed a_j^T r - a_j^T r| <= Cg ||a_j|| ||r||
+  double Cg;               // |computed a_j^T r - a_j^T r| <= Cg ||a_j|| ||r|| (evaluation precision)
+  double Cg2;              // the same for double-float correlations
   double Cf;               // residual rounding: <= Cf sum_j |x_j| ||a_j|| (2-norm)
   double Csub;
   double tol;

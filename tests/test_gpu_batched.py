@@ -92,8 +92,8 @@ def test_nnls_translation_ragged_tiles(P):
 
 
 def test_gaussian_box_both_bounds(P):
-    """BVLS with both bounds active (N(0,1) data, box [-1,1]): fixes at l and at u."""
-    p = W.bvls_box_shared(80, 150, 40, 1.0, 3)
+    """BVLS with both bounds active (N(0,1) data, box [-0.05, 0.05]): fixes at l and at u."""
+    p = W.bvls_box_shared(80, 150, 40, 0.05, 3)
     A = p.A.astype(np.float64)
     X, S, gaps, its, sts, info, st = batched(P, p, tol=1e-8, precision="fp32x2")
     assert st == P.BVLS_OK
