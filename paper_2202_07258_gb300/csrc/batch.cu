@@ -372,7 +372,8 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
   __shared__ int s_lj[kBEvalInst][kBEvalList];
   __shared__ float2 s_lx[kBEvalInst][kBEvalList];
   __shared__ int s_cnt[kBEvalInst];
-  __shared__ double s_red[kBEvalThreads / 32][kBEvalInst][4];
+  __shared__ double s_red[kBEvalThreads / 32][kBEvalInst][5];
+  __shared__ int s_ref[kBEvalInst];
   __shared__ double s_q[kBEvalInst][10];  // P, ||y||^2, eta_g, eps, radius + eta, eta, gap, preserved,
                                           // eta of the recomputed correlations
   __shared__ int s_stop[kBEvalInst];
@@ -610,12 +611,121 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
   }
   __syncthreads();
 
-  if (PREC == kF32) {
+  // ---- phase 3: gap terms and the step.  Each term of the nonnegative-sum form of P - D is
+  // a convex piecewise-linear function of gt_j = a_j^T theta; with the computed gt_j within
+  // e_j = eta ||a_j|| of the exact one, the term is bounded by its larger value at the two
+  // ends of [gt_j - e_j, gt_j + e_j].
+  {
+    const float* __restrict__ Gp = b.G[s ^ 1];
+    float* Gc = b.G[s];
+    float2* Xn = b.X[s ^ 1];
+    __nv_bfloat16* Dn = b.D[s ^ 1];
+    const float2 invL2 = p.invL2;
+    for (int bb = 0; bb < kBEvalInst; ++bb) {
+      const int inst = s_inst[bb];
+      if (inst < 0) break;  // active instances are packed at the front
+      const float be = s_beta[bb];
+      const double eps = s_q[bb][3], eta = s_q[bb][5], eta_ref = s_q[bb][8];
+      double va = 0.0, vx = 0.0, vd = 0.0, vp = 0.0, vs = 0.0;
+#pragma unroll 2
+      for (int j = tid; j < p.n; j += kBEvalThreads) {
+        const size_t o = (size_t)inst * p.npad + j;
+        const float2 xk = Xc[o];
+        const float2 xp = Xn[o];
+        const float2 g2 = b.Ge[o];
+        const float gp = Gp[o];
+        const double nr = p.nrm[j];
+        const double x = df2_to_double(xk);
+        vx += fabs(x) * nr;
+        const uint8_t fl = s_fl[bb * p.npad + j];
+        if (fl & 3) {
+          Xn[o] = xk;
+          Dn[o] = __float2bfloat16_rn(0.f);
+          continue;
+        }
+        vp += 1.0;
+        if (p.dual_mode != kZero) {
+          const double lj = p.l[j];
+          const double gt = df2_to_double(g2) + (trans ? eps * p.w[j] : 0.0);
+          const double e = ((fl & 4) ? eta_ref : eta) * nr;
+          double h_up, h_mid;
+          if (p.jinf[j]) {
+            h_up = (x - lj) * fmax(e - gt, 0.0);
+            h_mid = (x - lj) * fmax(-gt, 0.0);
+          } else {
+            const double uj = p.u[j];
+            const double lo = gt - e, hi = gt + e;
+            const double h_lo = (uj - x) * fmax(lo, 0.0) + (x - lj) * fmax(-lo, 0.0);
+            const double h_hi = (uj - x) * fmax(hi, 0.0) + (x - lj) * fmax(-hi, 0.0);
+            h_up = fmax(h_lo, h_hi);
+            h_mid = (uj - x) * fmax(gt, 0.0) + (x - lj) * fmax(-gt, 0.0);
+          }
+          va += h_up;
+          vs += h_up - h_mid;  // what exact correlations could remove from the bound
+        }
+        const float gk = g2.x;
+        const float gv = fmaf(be, gk - gp, gk);
+        const float2 xn = fista_step(xk, xp, gv, be, invL2, p.l2[j], p.u2[j]);
+        const float2 d = df2_sub(xn, xk);
+        const float dx = d.x + d.y;
+        Gc[o] = gk;
+        Xn[o] = xn;
+        Dn[o] = __float2bfloat16_rn(dx);
+        vd += (double)gv * (double)dx;
+      }
+      va = warp_sum_dd(va);
+      vx = warp_sum_dd(vx);
+      vd = warp_sum_dd(vd);
+      vp = warp_sum_dd(vp);
+      vs = warp_sum_dd(vs);
+      if (lane == 0) {
+        s_red[warp][bb][0] = va;
+        s_red[warp][bb][1] = vx;
+        s_red[warp][bb][2] = vd;
+        s_red[warp][bb][3] = vp;
+        s_red[warp][bb][4] = vs;
+      }
+    }
+  }
+  __syncthreads();
+  if (tid < kBEvalInst) {
+    double a = 0.0, x1 = 0.0, d = 0.0, np = 0.0, sl = 0.0;
+    for (int w = 0; w < kBEvalThreads / 32; ++w) {
+      a += s_red[w][tid][0];
+      x1 += s_red[w][tid][1];
+      d += s_red[w][tid][2];
+      np += s_red[w][tid][3];
+      sl += s_red[w][tid][4];
+    }
+    const int inst = s_inst[tid];
+    int ref = 0;
+    if (inst >= 0) {
+      const double P = s_q[tid][0];
+      const double eps = s_q[tid][3];
+      const double rnorm = sqrt(2.0 * P) * (1.0 + 1e-6);
+      const double E_r = p.Cf * x1 + p.Csub * (rnorm + sqrt(s_q[tid][1]) + x1);
+      // the part of the bound that does not depend on the correlations' rounding
+      const double dd = p.dual_mode == kZero ? rnorm + E_r : E_r + eps * p.t_norm;
+      s_q[tid][9] = 0.5 * dd * dd;
+      const double gap = (p.dual_mode == kZero ? s_q[tid][9] : a + s_q[tid][9]) * (1.0 + 1e-12);
+      s_q[tid][6] = gap;
+      // recompute the sensitive correlations in double-float when that could decide the stop
+      ref = PREC == kF32 && p.dual_mode != kZero && gap >= p.tol && (gap - sl < p.tol || k >= p.max_iter);
+      b.dotp[s][inst] = (float)d;
+      for (int t = 1; t < MT; ++t) b.dotp[s][(size_t)t * p.B + inst] = 0.f;
+      atomicAdd(&st->sum_pres, np);
+    }
+    s_ref[tid] = ref;
+    s_q[tid][7] = np;
+  }
+  __syncthreads();
+
+  if (PREC == kF32 && __syncthreads_or(tid < kBEvalInst && s_ref[tid])) {
     // ---- phase 2b: a gap term depends on the rounding of its correlation only when the
     // coordinate is free or its correlation is within the margin of zero; those
     // correlations are recomputed in double-float (lane = coordinate, all m rows).
     const int bb = warp;
-    const int inst = s_inst[bb];
+    const int inst = s_ref[bb] ? s_inst[bb] : -1;
     int cnt = 0;
     if (inst >= 0) {
       const double eps = s_q[bb][3], eF = s_q[bb][5];
@@ -654,110 +764,50 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
       }
     }
     __syncthreads();
-  }
-
-  // ---- phase 3: gap terms and the step.  Each term of the nonnegative-sum form of P - D is
-  // a convex piecewise-linear function of gt_j = a_j^T theta; with the computed gt_j within
-  // e_j = eta ||a_j|| of the exact one, the term is bounded by its larger value at the two
-  // ends of [gt_j - e_j, gt_j + e_j].
-  {
-    const float* __restrict__ Gp = b.G[s ^ 1];
-    float* Gc = b.G[s];
-    float2* Xn = b.X[s ^ 1];
-    __nv_bfloat16* Dn = b.D[s ^ 1];
-    const float2 invL2 = p.invL2;
-    for (int bb = 0; bb < kBEvalInst; ++bb) {
-      const int inst = s_inst[bb];
-      if (inst < 0) break;  // active instances are packed at the front
-      const float be = s_beta[bb];
-      const double eps = s_q[bb][3], eta = s_q[bb][5], eta_ref = s_q[bb][8];
-      double va = 0.0, vx = 0.0, vd = 0.0, vp = 0.0;
-#pragma unroll 2
+    // ---- phase 3b: the gap terms of the refined instances again
+    for (int bb2 = 0; bb2 < kBEvalInst; ++bb2) {
+      const int inst2 = s_inst[bb2];
+      if (inst2 < 0) break;
+      if (!s_ref[bb2]) continue;
+      const double eps = s_q[bb2][3], eta = s_q[bb2][5], eta_ref = s_q[bb2][8];
+      double va = 0.0;
       for (int j = tid; j < p.n; j += kBEvalThreads) {
-        const size_t o = (size_t)inst * p.npad + j;
-        const float2 xk = Xc[o];
-        const float2 xp = Xn[o];
-        const float2 g2 = b.Ge[o];
-        const float gp = Gp[o];
-        const double nr = p.nrm[j];
-        const double x = df2_to_double(xk);
-        vx += fabs(x) * nr;
-        const uint8_t fl = s_fl[bb * p.npad + j];
-        if (fl & 3) {
-          Xn[o] = xk;
-          Dn[o] = __float2bfloat16_rn(0.f);
-          continue;
+        const uint8_t fl = s_fl[bb2 * p.npad + j];
+        if (fl & 3) continue;
+        const size_t o = (size_t)inst2 * p.npad + j;
+        const double nr = p.nrm[j], lj = p.l[j];
+        const double x = df2_to_double(Xc[o]);
+        const double gt = df2_to_double(b.Ge[o]) + (trans ? eps * p.w[j] : 0.0);
+        const double e = ((fl & 4) ? eta_ref : eta) * nr;
+        if (p.jinf[j]) {
+          va += (x - lj) * fmax(e - gt, 0.0);
+        } else {
+          const double uj = p.u[j];
+          const double lo = gt - e, hi = gt + e;
+          va += fmax((uj - x) * fmax(lo, 0.0) + (x - lj) * fmax(-lo, 0.0),
+                     (uj - x) * fmax(hi, 0.0) + (x - lj) * fmax(-hi, 0.0));
         }
-        vp += 1.0;
-        if (p.dual_mode != kZero) {
-          const double lj = p.l[j];
-          const double gt = df2_to_double(g2) + (trans ? eps * p.w[j] : 0.0);
-          const double e = ((fl & 4) ? eta_ref : eta) * nr;
-          if (p.jinf[j]) {
-            va += (x - lj) * fmax(e - gt, 0.0);
-          } else {
-            const double uj = p.u[j];
-            const double lo = gt - e, hi = gt + e;
-            const double h_lo = (uj - x) * fmax(lo, 0.0) + (x - lj) * fmax(-lo, 0.0);
-            const double h_hi = (uj - x) * fmax(hi, 0.0) + (x - lj) * fmax(-hi, 0.0);
-            va += fmax(h_lo, h_hi);
-          }
-        }
-        const float gk = g2.x;
-        const float gv = fmaf(be, gk - gp, gk);
-        const float2 xn = fista_step(xk, xp, gv, be, invL2, p.l2[j], p.u2[j]);
-        const float2 d = df2_sub(xn, xk);
-        const float dx = d.x + d.y;
-        Gc[o] = gk;
-        Xn[o] = xn;
-        Dn[o] = __float2bfloat16_rn(dx);
-        vd += (double)gv * (double)dx;
       }
       va = warp_sum_dd(va);
-      vx = warp_sum_dd(vx);
-      vd = warp_sum_dd(vd);
-      vp = warp_sum_dd(vp);
-      if (lane == 0) {
-        s_red[warp][bb][0] = va;
-        s_red[warp][bb][1] = vx;
-        s_red[warp][bb][2] = vd;
-        s_red[warp][bb][3] = vp;
-      }
+      if (lane == 0) s_red[warp][bb2][0] = va;
     }
+    __syncthreads();
+    if (tid < kBEvalInst && s_ref[tid]) {
+      double a = 0.0;
+      for (int w = 0; w < kBEvalThreads / 32; ++w) a += s_red[w][tid][0];
+      s_q[tid][6] = fmin(s_q[tid][6], (a + s_q[tid][9]) * (1.0 + 1e-12));
+    }
+    __syncthreads();
   }
-  __syncthreads();
   if (tid < kBEvalInst) {
-    double a = 0.0, x1 = 0.0, d = 0.0, np = 0.0;
-    for (int w = 0; w < kBEvalThreads / 32; ++w) {
-      a += s_red[w][tid][0];
-      x1 += s_red[w][tid][1];
-      d += s_red[w][tid][2];
-      np += s_red[w][tid][3];
-    }
     const int inst = s_inst[tid];
     int stop = 0;
     if (inst >= 0) {
-      const double P = s_q[tid][0];
-      const double eps = s_q[tid][3], eta = s_q[tid][5];
-      const double rnorm = sqrt(2.0 * P) * (1.0 + 1e-6);
-      const double E_r = p.Cf * x1 + p.Csub * (rnorm + sqrt(s_q[tid][1]) + x1);
-      double gap;
-      if (p.dual_mode == kZero) {
-        gap = 0.5 * (rnorm + E_r) * (rnorm + E_r);
-      } else {
-        const double dd = E_r + eps * p.t_norm;
-        gap = a + 0.5 * dd * dd;
-      }
-      gap *= (1.0 + 1e-12);
-      s_q[tid][4] = sqrt(2.0 * gap) * (1.0 + 1e-12) + eta;  // radius + margin, per unit ||a_j||
-      s_q[tid][6] = gap;
+      const double gap = s_q[tid][6];
+      s_q[tid][4] = sqrt(2.0 * gap) * (1.0 + 1e-12) + s_q[tid][5];  // radius + margin, per unit ||a_j||
       stop = (gap < p.tol || k >= p.max_iter) ? 1 : 0;
-      b.dotp[s][inst] = (float)d;
-      for (int t = 1; t < MT; ++t) b.dotp[s][(size_t)t * p.B + inst] = 0.f;
-      atomicAdd(&st->sum_pres, np);
     }
     s_stop[tid] = stop;
-    s_q[tid][7] = np;
   }
   __syncthreads();
 
