@@ -23,6 +23,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kStageBytes = 2 * kBTile * kBChunk * 2;  // A and B tiles of one K chunk (bf16)
 constexpr int kBEvalList = 256;  // columns per chunk of the evaluation's nonzero lists
+constexpr int kBEvalRows = 8;    // rows per lane and pass (256 rows) in the evaluation's A x
 static_assert(kBEvalThreads / 32 == kBEvalInst, "one list-building warp per instance");
 
 __device__ __forceinline__ double warp_sum_dd(double v) {
@@ -350,7 +351,7 @@ cudaError_t launch_bstep(const BParams& p, const BBuffers& b, int j, cudaStream_
 
 // ------------------------------------------------------------------ evaluation
 // kBEvalInst instances per CTA (A is read once for all of them), 256 threads.
-//   phase 1  r = y - A x_k per row (thread = row), double-float, skipping zero x_j;
+//   phase 1  r = y - A x_k (warp = instance, lanes over rows), double-float, nonzero x_j only;
 //   phase 2  g_j = a_j^T r for preserved j (warp = column, lanes over rows), PREC products;
 //   phase 3  gap sums and the step (thread = coordinate);
 //   phase 4  sphere test; phase 5  outputs of the instances that stop.
@@ -412,157 +413,142 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
     s_fl[q] = inst >= 0 ? b.flags[(size_t)inst * p.npad + j] : (uint8_t)1;
   }
 
-  // ---- phase 1: r = y - A x_k, one block of kBEvalThreads rows at a time.  Warp bb lists
-  // the nonzero x_j of instance bb in a chunk of kBEvalList columns; every thread (one row)
-  // then runs over the lists with eight column loads in flight.
+  // ---- phase 1: r = y - A x_k.  Warp bb owns instance bb: for each block of 256 rows it
+  // lists the nonzero x_j of a chunk of kBEvalList columns, then its lanes (rows lane,
+  // lane + 32, ...) accumulate the listed columns four at a time, so each lane keeps 32
+  // loads in flight.
   const float2* __restrict__ Xc = b.X[s];
-  double pv[kBEvalInst], yv[kBEvalInst];
+  {
+    const int bb = warp;  // kBEvalThreads / 32 == kBEvalInst
+    const int inst = s_inst[bb];
+    double pv = 0.0, yv = 0.0;
+    for (int r0 = 0; r0 < p.m; r0 += 32 * kBEvalRows) {
+    float qs[kBEvalRows], qc[kBEvalRows];
 #pragma unroll
-  for (int bb = 0; bb < kBEvalInst; ++bb) {
-    pv[bb] = 0.0;
-    yv[bb] = 0.0;
-  }
-  for (int r0 = 0; r0 < p.m; r0 += kBEvalThreads) {
-    const int i = r0 + tid;
-    float qs[kBEvalInst], qc[kBEvalInst];
-#pragma unroll
-    for (int bb = 0; bb < kBEvalInst; ++bb) {
-      qs[bb] = 0.f;
-      qc[bb] = 0.f;
+    for (int r = 0; r < kBEvalRows; ++r) {
+      qs[r] = 0.f;
+      qc[r] = 0.f;
     }
-    for (int jc = 0; jc < p.n; jc += kBEvalList) {
-      {
-        const int bb = warp;  // kBEvalThreads / 32 == kBEvalInst
-        const int inst = s_inst[bb];
-        int cnt = 0;
-        float2 xs[kBEvalList / 32];
+    for (int jc = 0; jc < p.n && inst >= 0; jc += kBEvalList) {
+      int cnt = 0;
+      float2 xs[kBEvalList / 32];
 #pragma unroll
-        for (int t = 0; t < kBEvalList / 32; ++t) {  // loads first
-          const int j = jc + t * 32 + lane;
-          xs[t] = (inst >= 0 && j < p.n) ? Xc[(size_t)inst * p.npad + j] : make_float2(0.f, 0.f);
-        }
-#pragma unroll
-        for (int t = 0; t < kBEvalList / 32; ++t) {
-          const bool nz = df2_nonzero(xs[t]);
-          const unsigned msk = __ballot_sync(kFull, nz);
-          if (nz) {
-            const int pos = cnt + __popc(msk & ((1u << lane) - 1u));
-            s_lj[bb][pos] = jc + t * 32 + lane;
-            s_lx[bb][pos] = xs[t];
-          }
-          cnt += __popc(msk);
-        }
-        if (lane == 0) s_cnt[bb] = cnt;
+      for (int t = 0; t < kBEvalList / 32; ++t) {  // loads first
+        const int j = jc + t * 32 + lane;
+        xs[t] = j < p.n ? Xc[(size_t)inst * p.npad + j] : make_float2(0.f, 0.f);
       }
-      __syncthreads();
+#pragma unroll
+      for (int t = 0; t < kBEvalList / 32; ++t) {
+        const bool nz = df2_nonzero(xs[t]);
+        const unsigned msk = __ballot_sync(kFull, nz);
+        if (nz) {
+          const int pos = cnt + __popc(msk & ((1u << lane) - 1u));
+          s_lj[bb][pos] = jc + t * 32 + lane;
+          s_lx[bb][pos] = xs[t];
+        }
+        cnt += __popc(msk);
+      }
+      __syncwarp();
+      for (int e = 0; e < cnt; e += 4) {
+        float a[4][kBEvalRows];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float* col = p.A + (size_t)s_lj[bb][e + u < cnt ? e + u : e] * p.lda;
+#pragma unroll
+          for (int r = 0; r < kBEvalRows; ++r) {
+            const int i = r0 + lane + 32 * r;
+            a[u][r] = (e + u < cnt && i < p.m) ? __ldg(col + i) : 0.f;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float2 x = e + u < cnt ? s_lx[bb][e + u] : make_float2(0.f, 0.f);
+#pragma unroll
+          for (int r = 0; r < kBEvalRows; ++r) df_fma(qs[r], qc[r], a[u][r], x.x, x.y);
+        }
+      }
+      __syncwarp();
+    }
+#pragma unroll
+    for (int r = 0; r < kBEvalRows; ++r) {
+      const int i = r0 + lane + 32 * r;
       if (i < p.m) {
-#pragma unroll
-        for (int bb = 0; bb < kBEvalInst; ++bb) {
-          const int cnt = s_cnt[bb];
-          for (int e = 0; e < cnt; e += 8) {
-            float a[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-              a[u] = e + u < cnt ? __ldg(p.A + (size_t)s_lj[bb][e + u] * p.lda + i) : 0.f;
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              if (e + u < cnt) {
-                const float2 x = s_lx[bb][e + u];
-                df_fma(qs[bb], qc[bb], a[u], x.x, x.y);
-              }
-            }
-          }
-        }
-      }
-      __syncthreads();
-    }
-    if (i < p.m) {
-#pragma unroll
-      for (int bb = 0; bb < kBEvalInst; ++bb) {
-        const int inst = s_inst[bb];
         float rh = 0.f, rl = 0.f;
         if (inst >= 0) {
           const float y = b.Y[(size_t)inst * p.lda + i];
           float dh, de;
-          two_sum(y, -qs[bb], dh, de);
-          de -= qc[bb];
+          two_sum(y, -qs[r], dh, de);
+          de -= qc[r];
           two_sum(dh, de, rh, rl);
           const double rv = (double)rh + (double)rl;
-          pv[bb] += 0.5 * rv * rv;
-          yv[bb] += (double)y * (double)y;
+          pv += 0.5 * rv * rv;
+          yv += (double)y * (double)y;
         }
         sr[(size_t)i * kBEvalInst + bb] = make_float2(rh, rl);
       }
     }
-  }
-#pragma unroll
-  for (int bb = 0; bb < kBEvalInst; ++bb) {
-    pv[bb] = warp_sum_dd(pv[bb]);
-    yv[bb] = warp_sum_dd(yv[bb]);
-  }
-  if (lane == 0) {
-#pragma unroll
-    for (int bb = 0; bb < kBEvalInst; ++bb) {
-      s_red[warp][bb][0] = pv[bb];
-      s_red[warp][bb][1] = yv[bb];
     }
-  }
-  __syncthreads();
-  if (tid < kBEvalInst) {
-    double P = 0.0, Y2 = 0.0;
-    for (int w = 0; w < kBEvalThreads / 32; ++w) {
-      P += s_red[w][tid][0];
-      Y2 += s_red[w][tid][1];
+    pv = warp_sum_dd(pv);
+    yv = warp_sum_dd(yv);
+    if (lane == 0) {
+      s_q[bb][0] = pv;
+      s_q[bb][1] = yv;
+      s_q[bb][2] = p.Cg * sqrt(2.0 * pv) * (1.0 + 1e-6);  // eta_g: rounding of a_j^T r per unit norm
     }
-    s_q[tid][0] = P;
-    s_q[tid][1] = Y2;
-    s_q[tid][2] = p.Cg * sqrt(2.0 * P) * (1.0 + 1e-6);  // eta_g: rounding of a_j^T r per unit norm
   }
   __syncthreads();
 
-  // ---- phase 2: correlations of the preserved coordinates, two columns per warp step
-  // (the residual loads from shared memory serve both)
+  // ---- phase 2: correlations of the preserved coordinates, CP columns per warp step (the
+  // residual loads from shared memory serve all of them)
   double epsm = 0.0;  // lane bb < kBEvalInst: translation step candidate of instance bb
   {
+    constexpr int CP = PREC == kX2 ? 2 : 4;
     const double eta_g = lane < kBEvalInst ? s_q[lane][2] : 0.0;
     const int inst_l = lane < kBEvalInst ? s_inst[lane] : -1;
     constexpr int W = kBEvalThreads / 32;
-    for (int j0 = 2 * warp; j0 < p.n; j0 += 2 * W) {
-      const int j1 = j0 + 1;
-      const bool n0 = lane < kBEvalInst && s_fl[lane * p.npad + j0] == 0;
-      const bool n1 = lane < kBEvalInst && j1 < p.n && s_fl[lane * p.npad + j1] == 0;
-      const unsigned need0 = __ballot_sync(kFull, n0), need1 = __ballot_sync(kFull, n1);
-      if (!(need0 | need1)) continue;
-      const float* __restrict__ c0 = p.A + (size_t)j0 * p.lda;
-      const float* __restrict__ c1 = p.A + (size_t)(j1 < p.n ? j1 : j0) * p.lda;
-      float sa[2][kBEvalInst], ca[2][kBEvalInst];
+    for (int j0 = CP * warp; j0 < p.n; j0 += CP * W) {
+      bool nd[CP];
+      unsigned any = 0;
+      const float* col[CP];
 #pragma unroll
-      for (int bb = 0; bb < kBEvalInst; ++bb) {
-        sa[0][bb] = sa[1][bb] = 0.f;
-        ca[0][bb] = ca[1][bb] = 0.f;
+      for (int c = 0; c < CP; ++c) {
+        const int j = j0 + c;
+        nd[c] = lane < kBEvalInst && j < p.n && s_fl[lane * p.npad + j] == 0;
+        any |= __ballot_sync(kFull, nd[c]);
+        col[c] = p.A + (size_t)(j < p.n ? j : j0) * p.lda;
       }
+      if (!any) continue;
+      float sa[CP][kBEvalInst], ca[CP][kBEvalInst];
+#pragma unroll
+      for (int c = 0; c < CP; ++c)
+#pragma unroll
+        for (int bb = 0; bb < kBEvalInst; ++bb) {
+          sa[c][bb] = 0.f;
+          ca[c][bb] = 0.f;
+        }
 #pragma unroll 2
       for (int i = lane; i < p.m; i += 32) {
-        const float a0 = __ldg(c0 + i), a1 = __ldg(c1 + i);
+        float a[CP];
+#pragma unroll
+        for (int c = 0; c < CP; ++c) a[c] = __ldg(col[c] + i);
         const float4* rr = reinterpret_cast<const float4*>(sr + (size_t)i * kBEvalInst);
 #pragma unroll
         for (int h = 0; h < kBEvalInst / 2; ++h) {
           const float4 v = rr[h];
-          if (PREC == kX2) {
-            df_fma(sa[0][2 * h], ca[0][2 * h], a0, v.x, v.y);
-            df_fma(sa[0][2 * h + 1], ca[0][2 * h + 1], a0, v.z, v.w);
-            df_fma(sa[1][2 * h], ca[1][2 * h], a1, v.x, v.y);
-            df_fma(sa[1][2 * h + 1], ca[1][2 * h + 1], a1, v.z, v.w);
-          } else {
-            sa[0][2 * h] = fmaf(a0, v.x, sa[0][2 * h]);
-            sa[0][2 * h + 1] = fmaf(a0, v.z, sa[0][2 * h + 1]);
-            sa[1][2 * h] = fmaf(a1, v.x, sa[1][2 * h]);
-            sa[1][2 * h + 1] = fmaf(a1, v.z, sa[1][2 * h + 1]);
+#pragma unroll
+          for (int c = 0; c < CP; ++c) {
+            if (PREC == kX2) {
+              df_fma(sa[c][2 * h], ca[c][2 * h], a[c], v.x, v.y);
+              df_fma(sa[c][2 * h + 1], ca[c][2 * h + 1], a[c], v.z, v.w);
+            } else {
+              sa[c][2 * h] = fmaf(a[c], v.x, sa[c][2 * h]);
+              sa[c][2 * h + 1] = fmaf(a[c], v.z, sa[c][2 * h + 1]);
+            }
           }
         }
       }
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
+      for (int c = 0; c < CP; ++c) {
         float gs = 0.f, gc = 0.f;
 #pragma unroll
         for (int bb = 0; bb < kBEvalInst; ++bb) {
@@ -582,8 +568,8 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
             gc = PREC == kX2 ? cc : 0.f;
           }
         }
-        const int j = c == 0 ? j0 : j1;
-        if (c == 0 ? n0 : n1) {
+        const int j = j0 + c;
+        if (nd[c]) {
           const float2 g2 = df2_norm(gs, gc);
           b.Ge[(size_t)inst_l * p.npad + j] = g2;
           if (trans && p.jinf[j]) {
