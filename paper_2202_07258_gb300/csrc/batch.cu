@@ -31,6 +31,49 @@ __device__ __forceinline__ double warp_sum_dd(double v) {
   return v;
 }
 
+constexpr float kUf = 6.0e-8f;  // a little above 2^-24, the unit roundoff of float32
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// float32 value >= x
+__device__ __forceinline__ float f32_up(double x) {
+  float f = (float)x;
+  if ((double)f < x) f = nextafterf(f, INFINITY);
+  return f;
+}
+
+// Inputs of one gap term in float32: the distances to the bounds du = u_j - x_j (0 when
+// u_j = +inf) and dl = x_j - l_j rounded up, gt = a_j^T theta = g_j + eps w_j, and the
+// half-width E of an interval around gt that holds the exact value: the correlation's own
+// error bound e plus the rounding of forming gt.
+__device__ __forceinline__ void term_inputs(float2 xk, float2 g2, int j, const BParams& p, float eps, float e,
+                                            float& du, float& dl, float& gt, float& E) {
+  const float2 a = df2_sub(xk, p.l2[j]);
+  dl = fmaxf(a.x + a.y, 0.f) * (1.f + 2.f * kUf);
+  du = 0.f;
+  if (!p.jinf[j]) {
+    const float2 c = df2_sub(p.u2[j], xk);
+    du = fmaxf(c.x + c.y, 0.f) * (1.f + 2.f * kUf);
+  }
+  const float ew = p.dual_mode == kTranslation ? eps * p.wf[j] : 0.f;
+  gt = (g2.x + ew) + g2.y;
+  E = e * (1.f + 2.f * kUf) + 8.f * kUf * (fabsf(g2.x) + fabsf(ew)) + fabsf(g2.y);
+}
+
+// Upper bound of h(g') = du (g')^+ + dl (-g')^+ over |g' - gt| <= E, computed in float32:
+// E is widened so that the rounded ends still enclose the interval, and the result is
+// rounded up by the bound of the few operations that form it.
+__device__ __forceinline__ float gap_term_up(float du, float dl, float gt, float E) {
+  const float E2 = fmaf(4.f * kUf, fabsf(gt) + E, E) + 1e-30f;
+  const float hi = gt + E2, lo = gt - E2;
+  const float h_hi = du * fmaxf(hi, 0.f) + dl * fmaxf(-hi, 0.f);
+  const float h_lo = du * fmaxf(lo, 0.f) + dl * fmaxf(-lo, 0.f);
+  return fmaxf(h_hi, h_lo) * (1.f + 4.f * kUf) + 1e-30f;
+}
+
 // x_{k+1} = clip(x_k + b (x_k - x_{k-1}) + g_v / L, l, u) with double-float iterates.
 __device__ __forceinline__ float2 fista_step(float2 xk, float2 xp, float gv, float be, float2 invL2, float2 l2,
                                              float2 u2) {
@@ -375,6 +418,8 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
   __shared__ int s_cnt[kBEvalInst];
   __shared__ double s_red[kBEvalThreads / 32][kBEvalInst][5];
   __shared__ int s_ref[kBEvalInst];
+  __shared__ float s_qf[kBEvalInst][4];   // eps, eta, eta of refined correlations (rounded up)
+  __shared__ double s_sum_infl;           // bound of the relative rounding of the float32 sums
   __shared__ double s_q[kBEvalInst][10];  // P, ||y||^2, eta_g, eps, radius + eta, eta, gap, preserved,
                                           // eta of the recomputed correlations
   __shared__ int s_stop[kBEvalInst];
@@ -588,19 +633,26 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
   if (tid < kBEvalInst) {
     double e = 0.0;
     for (int w = 0; w < kBEvalThreads / 32; ++w) e = fmax(e, s_red[w][tid][3]);
-    const double eps = trans ? e : 0.0;
+    const double eps = trans ? (double)f32_up(e) : 0.0;  // theta = r + eps t with the float32 eps
     s_q[tid][3] = eps;
     const double rnorm = sqrt(2.0 * s_q[tid][0]) * (1.0 + 1e-6);
     const double et = trans ? eps * p.gamma_w * p.t_norm : 0.0;
     s_q[tid][5] = p.Cg * rnorm + et;    // eta of the correlations of this precision
     s_q[tid][8] = p.Cg2 * rnorm + et;   // eta of double-float correlations
+    s_qf[tid][0] = f32_up(eps);
+    s_qf[tid][1] = f32_up(s_q[tid][5]);
+    s_qf[tid][2] = f32_up(s_q[tid][8]);
+    if (tid == 0) {
+      const int T = (p.n + kBEvalThreads - 1) / kBEvalThreads;
+      s_sum_infl = 1.0 + 2.0 * (T + 8) * 6.0e-8;
+    }
   }
   __syncthreads();
 
-  // ---- phase 3: gap terms and the step.  Each term of the nonnegative-sum form of P - D is
-  // a convex piecewise-linear function of gt_j = a_j^T theta; with the computed gt_j within
-  // e_j = eta ||a_j|| of the exact one, the term is bounded by its larger value at the two
-  // ends of [gt_j - e_j, gt_j + e_j].
+  // ---- phase 3: gap terms and the step, in float32 with every rounding bounded.  Each term
+  // of the nonnegative-sum form of P - D is a convex piecewise-linear function of
+  // gt_j = a_j^T theta; with the computed gt_j within E_j of the exact one, the term is
+  // bounded by its larger value at the two ends of [gt_j - E_j, gt_j + E_j] (gap_term_up).
   {
     const float* __restrict__ Gp = b.G[s ^ 1];
     float* Gc = b.G[s];
@@ -611,8 +663,9 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
       const int inst = s_inst[bb];
       if (inst < 0) break;  // active instances are packed at the front
       const float be = s_beta[bb];
-      const double eps = s_q[bb][3], eta = s_q[bb][5], eta_ref = s_q[bb][8];
-      double va = 0.0, vx = 0.0, vd = 0.0, vp = 0.0, vs = 0.0;
+      const float eps = s_qf[bb][0], eta = s_qf[bb][1], eta_ref = s_qf[bb][2];
+      float va = 0.f, vx = 0.f, vd = 0.f, vs = 0.f;
+      int vp = 0;
 #pragma unroll 2
       for (int j = tid; j < p.n; j += kBEvalThreads) {
         const size_t o = (size_t)inst * p.npad + j;
@@ -620,34 +673,21 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
         const float2 xp = Xn[o];
         const float2 g2 = b.Ge[o];
         const float gp = Gp[o];
-        const double nr = p.nrm[j];
-        const double x = df2_to_double(xk);
-        vx += fabs(x) * nr;
+        const float nr = p.nrmf[j];
+        vx += fabsf(xk.x) * nr;
         const uint8_t fl = s_fl[bb * p.npad + j];
         if (fl & 3) {
           Xn[o] = xk;
           Dn[o] = __float2bfloat16_rn(0.f);
           continue;
         }
-        vp += 1.0;
+        ++vp;
         if (p.dual_mode != kZero) {
-          const double lj = p.l[j];
-          const double gt = df2_to_double(g2) + (trans ? eps * p.w[j] : 0.0);
-          const double e = ((fl & 4) ? eta_ref : eta) * nr;
-          double h_up, h_mid;
-          if (p.jinf[j]) {
-            h_up = (x - lj) * fmax(e - gt, 0.0);
-            h_mid = (x - lj) * fmax(-gt, 0.0);
-          } else {
-            const double uj = p.u[j];
-            const double lo = gt - e, hi = gt + e;
-            const double h_lo = (uj - x) * fmax(lo, 0.0) + (x - lj) * fmax(-lo, 0.0);
-            const double h_hi = (uj - x) * fmax(hi, 0.0) + (x - lj) * fmax(-hi, 0.0);
-            h_up = fmax(h_lo, h_hi);
-            h_mid = (uj - x) * fmax(gt, 0.0) + (x - lj) * fmax(-gt, 0.0);
-          }
-          va += h_up;
-          vs += h_up - h_mid;  // what exact correlations could remove from the bound
+          float du, dl, gt, E;
+          term_inputs(xk, g2, j, p, eps, ((fl & 4) ? eta_ref : eta) * nr, du, dl, gt, E);
+          const float hup = gap_term_up(du, dl, gt, E);
+          va += hup;
+          vs += hup - (du * fmaxf(gt, 0.f) + dl * fmaxf(-gt, 0.f));  // what exact correlations could remove
         }
         const float gk = g2.x;
         const float gv = fmaf(be, gk - gp, gk);
@@ -657,13 +697,13 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
         Gc[o] = gk;
         Xn[o] = xn;
         Dn[o] = __float2bfloat16_rn(dx);
-        vd += (double)gv * (double)dx;
+        vd = fmaf(gv, dx, vd);
       }
-      va = warp_sum_dd(va);
-      vx = warp_sum_dd(vx);
-      vd = warp_sum_dd(vd);
-      vp = warp_sum_dd(vp);
-      vs = warp_sum_dd(vs);
+      va = warp_sum_f(va);
+      vx = warp_sum_f(vx);
+      vd = warp_sum_f(vd);
+      vs = warp_sum_f(vs);
+      for (int o2 = 16; o2 > 0; o2 >>= 1) vp += __shfl_xor_sync(kFull, vp, o2);
       if (lane == 0) {
         s_red[warp][bb][0] = va;
         s_red[warp][bb][1] = vx;
@@ -683,6 +723,8 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
       np += s_red[w][tid][3];
       sl += s_red[w][tid][4];
     }
+    a *= s_sum_infl;   // float32 sums of nonnegative terms: per-thread runs and 5 shuffle levels
+    x1 *= s_sum_infl;
     const int inst = s_inst[tid];
     int ref = 0;
     if (inst >= 0) {
@@ -691,7 +733,7 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
       const double rnorm = sqrt(2.0 * P) * (1.0 + 1e-6);
       const double E_r = p.Cf * x1 + p.Csub * (rnorm + sqrt(s_q[tid][1]) + x1);
       // the part of the bound that does not depend on the correlations' rounding
-      const double dd = p.dual_mode == kZero ? rnorm + E_r : E_r + eps * p.t_norm;
+      const double dd = p.dual_mode == kZero ? rnorm + E_r : E_r + (double)s_qf[tid][0] * p.t_norm;
       s_q[tid][9] = 0.5 * dd * dd;
       const double gap = (p.dual_mode == kZero ? s_q[tid][9] : a + s_q[tid][9]) * (1.0 + 1e-12);
       s_q[tid][6] = gap;
@@ -755,33 +797,24 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
       const int inst2 = s_inst[bb2];
       if (inst2 < 0) break;
       if (!s_ref[bb2]) continue;
-      const double eps = s_q[bb2][3], eta = s_q[bb2][5], eta_ref = s_q[bb2][8];
-      double va = 0.0;
+      const float eps = s_qf[bb2][0], eta = s_qf[bb2][1], eta_ref = s_qf[bb2][2];
+      float va = 0.f;
       for (int j = tid; j < p.n; j += kBEvalThreads) {
         const uint8_t fl = s_fl[bb2 * p.npad + j];
         if (fl & 3) continue;
         const size_t o = (size_t)inst2 * p.npad + j;
-        const double nr = p.nrm[j], lj = p.l[j];
-        const double x = df2_to_double(Xc[o]);
-        const double gt = df2_to_double(b.Ge[o]) + (trans ? eps * p.w[j] : 0.0);
-        const double e = ((fl & 4) ? eta_ref : eta) * nr;
-        if (p.jinf[j]) {
-          va += (x - lj) * fmax(e - gt, 0.0);
-        } else {
-          const double uj = p.u[j];
-          const double lo = gt - e, hi = gt + e;
-          va += fmax((uj - x) * fmax(lo, 0.0) + (x - lj) * fmax(-lo, 0.0),
-                     (uj - x) * fmax(hi, 0.0) + (x - lj) * fmax(-hi, 0.0));
-        }
+        float du, dl, gt, E;
+        term_inputs(Xc[o], b.Ge[o], j, p, eps, ((fl & 4) ? eta_ref : eta) * p.nrmf[j], du, dl, gt, E);
+        va += gap_term_up(du, dl, gt, E);
       }
-      va = warp_sum_dd(va);
+      va = warp_sum_f(va);
       if (lane == 0) s_red[warp][bb2][0] = va;
     }
     __syncthreads();
     if (tid < kBEvalInst && s_ref[tid]) {
       double a = 0.0;
       for (int w = 0; w < kBEvalThreads / 32; ++w) a += s_red[w][tid][0];
-      s_q[tid][6] = fmin(s_q[tid][6], (a + s_q[tid][9]) * (1.0 + 1e-12));
+      s_q[tid][6] = fmin(s_q[tid][6], (a * s_sum_infl + s_q[tid][9]) * (1.0 + 1e-12));
     }
     __syncthreads();
   }
@@ -797,28 +830,33 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
   }
   __syncthreads();
 
-  // ---- phase 4: sphere test (Eq. (safe_rule)); a coordinate is fixed once x_k and x_{k+1}
-  // both sit at the bound the test gives
+  // ---- phase 4: sphere test (Eq. (safe_rule)) in float32: the computed gt_j, widened by its
+  // own rounding, must clear (radius + eta) ||a_j|| rounded up.  A coordinate is fixed once
+  // x_k and x_{k+1} both sit at the bound the test gives.
   if (p.screening && p.dual_mode != kZero) {
     const float2* __restrict__ Xn = b.X[s ^ 1];
     for (int bb = 0; bb < kBEvalInst; ++bb) {
       const int inst = s_inst[bb];
       if (inst < 0) break;
-      const double eps = s_q[bb][3], rr = s_q[bb][4];
+      const float eps = s_qf[bb][0];
+      const float rr = f32_up(s_q[bb][4]);
       int pins = 0;
       for (int j = tid; j < p.n; j += kBEvalThreads) {
         if (s_fl[bb * p.npad + j] & 3) continue;
-        const double nr = p.nrm[j];
-        if (!(nr > 0.0)) continue;
+        const float nr = p.nrmf[j];
+        if (!(nr > 0.f)) continue;
         const size_t o = (size_t)inst * p.npad + j;
-        const double gt = df2_to_double(b.Ge[o]) + (trans ? eps * p.w[j] : 0.0);
-        const double thr = rr * nr * (1.0 + 1e-12);
+        const float2 g2 = b.Ge[o];
+        const float ew = trans ? eps * p.wf[j] : 0.f;
+        const float gt = (g2.x + ew) + g2.y;
+        const float dl = 8.f * kUf * (fabsf(g2.x) + fabsf(ew)) + fabsf(g2.y);
+        const float thr = rr * nr * (1.f + 4.f * kUf);
         int pin = 0;
         float2 bnd = make_float2(0.f, 0.f);
-        if (gt < -thr) {
+        if (gt + dl < -thr) {
           pin = 1;
           bnd = p.l2[j];
-        } else if (!p.jinf[j] && gt > thr) {
+        } else if (!p.jinf[j] && gt - dl > thr) {
           pin = 2;
           bnd = p.u2[j];
         }

@@ -58,6 +58,8 @@ struct BParams {
   const double* l;
   const double* u;
   const double* nrm;       // ||a_j||
+  const float* nrmf;       // ||a_j|| rounded up to float32
+  const float* wf;         // a_j^T t rounded to float32
   const double* w;         // a_j^T t (translation mode)
   const uint8_t* jinf;
   const float2* l2;        // bounds as double-float pairs (clip of the iterates)

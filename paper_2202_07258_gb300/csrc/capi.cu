@@ -78,6 +78,7 @@ struct bvls_handle {
   int b_npad = 0;
   __nv_bfloat16* bH = nullptr;
   int b_cap = 0;
+  float *b_nrmf = nullptr, *b_wf = nullptr;
   BBuffers bb{};
   float* bY = nullptr;
   double* bX0 = nullptr;
@@ -659,6 +660,21 @@ bvls_status batch_prepare(bvls_handle* h, int B) {
     CK(batch_configure(h->m, h->b_npad));
     TRY(dalloc(h, &h->bH, (size_t)h->b_npad * h->b_npad));
     CK(launch_bgram(h->A, h->lda, h->m, n, h->b_npad, h->bH, h->s));
+    std::vector<double> nrm(n), w(n);
+    CK(cudaMemcpyAsync(nrm.data(), h->nrm, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
+    CK(cudaMemcpyAsync(w.data(), h->w, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    std::vector<float> nrmf(n), wf(n);
+    for (int j = 0; j < n; ++j) {
+      float f = (float)nrm[j];
+      if ((double)f < nrm[j]) f = std::nextafter(f, INFINITY);
+      nrmf[j] = f;
+      wf[j] = (float)w[j];
+    }
+    TRY(dalloc(h, &h->b_nrmf, n));
+    TRY(dalloc(h, &h->b_wf, n));
+    CK(cudaMemcpyAsync(h->b_nrmf, nrmf.data(), sizeof(float) * n, cudaMemcpyHostToDevice, h->s));
+    CK(cudaMemcpyAsync(h->b_wf, wf.data(), sizeof(float) * n, cudaMemcpyHostToDevice, h->s));
     CK(cudaStreamSynchronize(h->s));
   }
   if (B <= h->b_cap) return BVLS_OK;
@@ -712,6 +728,8 @@ BParams make_bparams(bvls_handle* h, const bvls_opts& o, int max_iter, int B) {
   p.u = h->u;
   p.nrm = h->nrm;
   p.w = h->w;
+  p.nrmf = h->b_nrmf;
+  p.wf = h->b_wf;
   p.jinf = h->jinf;
   p.l2 = h->l2;
   p.u2 = h->u2;
