@@ -180,9 +180,11 @@ def timed_solves(solver, y_dev, flush, stream, steps, warmup, **kw):
 
 
 def kernel_hash():
+    """Hash of every CUDA source: stored ncu counters apply only to the kernels they measured."""
     h = hashlib.sha256()
-    for f in ("iter_kernels.cu", "common.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2202_07258_gb300", "csrc", f), "rb").read())
+    csrc = os.path.join(ROOT, "paper_2202_07258_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -232,6 +234,65 @@ def roofline(solver, y_dev, m):
             "kernels": other, "profile_iters": info["iters"]}
 
 
+BATCH = dict(m=224, n=512, B=4096, k_support=8, noise=0.005, seed=0)
+
+
+def batched_leg(dev, stream, flush, steps, warmup=1):
+    """Shared-A batch (BVLS, A 224 x 512 U[0,1] unit columns, 4096 Dirichlet right-hand sides,
+    box [0,1]): instances/s to gap 1e-6 screened and unscreened, and the tensor-core roofline
+    of the step kernel (dense BF16 Gram GEMM, 2 n^2 flops per instance per step)."""
+    import torch
+    from paper_2202_07258_gb300 import Solver, make_opts
+    c = BATCH
+    p = W.bvls_dirichlet_shared(c["m"], c["n"], c["B"], c["k_support"], c["noise"], c["seed"])
+    with torch.cuda.stream(stream):
+        solver = Solver(torch.from_numpy(p.A).to(dev), p.l, p.u, stream=stream.cuda_stream)
+    Y = torch.from_numpy(p.y).to(dev)
+    out = {"workload": (f"BVLS shared A {c['m']}x{c['n']} U[0,1] unit columns, B={c['B']} y_b = A x_b + "
+                        f"N(0,{c['noise']}^2), x_b Dirichlet on {c['k_support']} columns, box [0,1]"),
+           "precision": "bf16 tensor-core steps, f32 evaluations with double-float recomputation, "
+                        "double-float iterates"}
+    for scr in (True, False):
+        opts = make_opts(tol=TOL, screen_every=K_SCREEN, precision="fp32", screening=scr)
+        for _ in range(warmup):
+            solver.solve_batched(Y, opts=opts)
+        times = []
+        with torch.cuda.stream(stream):
+            for _ in range(steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                X, S, gaps, its, sts, info, st = solver.solve_batched(Y, opts=opts)
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+        key = "screened" if scr else "unscreened"
+        out[key] = {"instances_per_s": c["B"] * len(times) / (sum(times) / 1000.0),
+                    "ms_per_batch": sum(times) / len(times), "n_converged": info["n_converged"],
+                    "iters_max": info["iters_max"], "iters_mean": float(its.double().mean()),
+                    "gap_max": float(gaps.max()), "preserved_fraction": info["sum_preserved"] /
+                    max(1.0, info["sum_eval"] * c["n"]), "kernel_launches": info["kernel_launches"]}
+    opts = make_opts(tol=TOL, screen_every=K_SCREEN, precision="fp32", profile=True)
+    X, S, gaps, its, sts, info, st = solver.solve_batched(Y, opts=opts)
+    solver.close()
+    flops = 2.0 * c["n"] * c["n"] * info["sum_step"]
+    step_s = info["step_ms"] / 1000.0
+    achieved = flops / step_s / 1e12 if step_s > 0 else None
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak, src = 1700.0, "fallback sustained"
+    if os.path.exists(peaks_path):
+        peak, src = float(json.load(open(peaks_path))["bf16_tflops_sustained"]), "measured sustained"
+    out["roofline"] = {"bound": "tensor", "kernel": "k_bstep (tcgen05 Gram GEMM + fused FISTA step)",
+                       "achieved": achieved, "peak": peak, "peak_source": src, "unit": "TFLOP/s",
+                       "frac": achieved / peak if achieved else None,
+                       "flops_per_launch": flops / max(1, info["step_launches"]),
+                       "avg_launch_us": 1e6 * step_s / max(1, info["step_launches"]),
+                       "eval_avg_launch_us": 1e3 * info["eval_ms"] / max(1, info["eval_launches"]),
+                       "step_share": info["step_ms"] / max(1e-9, info["step_ms"] + info["eval_ms"])}
+    return out
+
+
 def e2e_leg(p, steps, stream):
     """Whole job through the C ABI from pinned host buffers: setup(A) + solve(y) + read x."""
     import ctypes
@@ -263,6 +324,36 @@ def e2e_leg(p, steps, stream):
     return {"value": 1.0 / statistics.median(times), "unit": "instances/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "includes": "bvls_setup from host A (copy, column norms, dual "
             "direction search, power iteration) + bvls_solve from host y to host x"}
+
+
+def ncu_region(args):
+    """One warm solve of a leg inside a profiler region, for ncu --profile-from-start off."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_2202_07258_gb300 import Solver, make_opts
+    dev = torch.device("cuda", 0)
+    if args.ncu_region == "single":
+        p = make_problem(WORKLOAD, 0)
+        s = Solver(torch.from_numpy(p.A).to(dev), p.l, p.u)
+        y = torch.from_numpy(p.y).to(dev)
+        opts = make_opts(tol=TOL, screen_every=K_SCREEN)
+        run = lambda: s.solve(y, opts=opts)
+    else:
+        c = BATCH
+        p = W.bvls_dirichlet_shared(c["m"], c["n"], c["B"], c["k_support"], c["noise"], c["seed"])
+        s = Solver(torch.from_numpy(p.A).to(dev), p.l, p.u)
+        Y = torch.from_numpy(p.y).to(dev)
+        opts = make_opts(tol=TOL, screen_every=K_SCREEN, precision="fp32", max_iter=200)
+        run = lambda: s.solve_batched(Y, opts=opts)
+    for _ in range(max(1, args.warmup)):
+        run()
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStart()
+    run()
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStop()
+    s.close()
 
 
 def run_ours(args):
@@ -319,6 +410,7 @@ def run_ours(args):
     value = world * args.steps / (total_ms / 1000.0)
 
     roof = roofline(scr["solver"], scr["y"], 2000) if rank == 0 else None
+    batched = batched_leg(dev, stream, flush, max(2, min(args.steps, 5))) if (rank == 0 and not args.no_batched) else None
     e2e = e2e_leg(scr["p"], max(2, min(args.steps, 5)), stream) if rank == 0 else None
     cpu = oracle_sample(scr["p"]) if (rank == 0 and world == 1) else None
     scr["solver"].close()
@@ -350,7 +442,7 @@ def run_ours(args):
                 "iters_screened": var_s["info"]["iters"], "iters_unscreened": var_u["info"]["iters"],
                 "avg_preserved_fraction": var_s["info"]["sum_preserved"] / max(1, var_s["info"]["iters"]) / 10000,
                 "gap": var_s["info"]["gap"]},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "batched_shared_A": batched,
             "gpu_launches": int(scr["launches"]), "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)
@@ -368,12 +460,18 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-batched", action="store_true", help="skip the shared-A batched leg")
+    ap.add_argument("--ncu-region", choices=["single", "batched"], default=None,
+                    help="profiling aid: run one warm solve of that leg between cudaProfilerStart/Stop "
+                         "(for ncu --profile-from-start off) and exit without a bench line")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: warmup raised to 3", file=sys.stderr)
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.ncu_region:
+        ncu_region(args)
     else:
         run_ours(args)
 
