@@ -58,6 +58,8 @@ __all__ = [
     "brute_force",
     "kkt_residual",
     "polish",
+    "free_set",
+    "backward",
 ]
 
 
@@ -431,3 +433,43 @@ def polish(A, y, x, l=None, u=None, tau=1e-9):
         rhs = y - A[:, fixed] @ xp[fixed]
         xp[F] = np.linalg.lstsq(A[:, F], rhs, rcond=None)[0]
     return xp
+
+
+def free_set(x, l, u, tau=1e-9):
+    """Indices of the coordinates strictly inside the box, with a relative margin tau:
+    l_j + tau (1 + |l_j|) < x_j < u_j - tau (1 + |u_j|)."""
+    x = np.asarray(x, dtype=np.float64)
+    l = np.asarray(l, dtype=np.float64)
+    u = np.asarray(u, dtype=np.float64)
+    above = x > l + tau * (1 + np.abs(l))
+    uu = np.where(np.isfinite(u), u, 0.0)
+    below = ~np.isfinite(u) | (x < uu - tau * (1 + np.abs(uu)))
+    return np.flatnonzero(above & below)
+
+
+def backward(A, y, x, dLdx, l=None, u=None, tau=1e-9):
+    """Gradients of a loss L(x*) through the solution map (y, A) -> x*(y, A).
+
+    At a non-degenerate optimum (strict complementarity, A_F of full column rank on the free
+    set F of ``free_set``) the optimality conditions of Section 3.2 pin the other
+    coordinates at their bounds and make x_F the solution of the restricted normal
+    equations  A_F^T A_F x_F = A_F^T (y - A_B x_B).  Differentiating them gives, with
+    w = (A_F^T A_F)^{-1} (dL/dx)_F extended by zeros off F and r = y - A x:
+
+        dL/dy = A_F w_F,        dL/dA = r w^T - (A_F w_F) x^T.
+
+    Components of dL/dx on the fixed coordinates do not flow back (the solution does not
+    move with y or A there).  Returns (dL/dy, dL/dA, F, w).
+    """
+    A, y, l, u = as_problem(A, y, l, u)
+    x = np.asarray(x, dtype=np.float64)
+    v = np.asarray(dLdx, dtype=np.float64)
+    F = free_set(x, l, u, tau)
+    w = np.zeros(A.shape[1])
+    if F.size:
+        AF = A[:, F]
+        w[F] = np.linalg.solve(AF.T @ AF, v[F])
+    q = A[:, F] @ w[F] if F.size else np.zeros(A.shape[0])
+    r = y - A @ x
+    return q, np.outer(r, w) - np.outer(q, x), F, w
+
