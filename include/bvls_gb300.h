@@ -213,6 +213,51 @@ BVLS_API bvls_status bvls_solve_batched(bvls_handle* h, int B, const float* Y, i
                                         double* gaps_out, int* iters_out, int* status_out,
                                         bvls_batch_info* info);
 
+typedef struct {
+  double free_tol;      /* free set: l_j + free_tol (1 + |l_j|) < x_j < u_j - free_tol (1 + |u_j|);
+                           default 1e-9 */
+  double cg_tol;        /* CG stops when ||A_F^T A_F w - v_F|| <= cg_tol ||v_F||; default 1e-12 */
+  int cg_max_iter;      /* CG iteration limit per instance; default 4000 */
+} bvls_backward_opts;
+
+typedef struct {
+  int n_converged;      /* instances whose CG met cg_tol */
+  int n_iter_limit;     /* instances that stopped at cg_max_iter (gradients approximate) */
+  int n_too_large;      /* instances whose free set exceeds 1024 (zero gradients returned) */
+  int max_free;         /* largest free set */
+  int max_cg_iters;     /* most CG iterations of an instance */
+} bvls_backward_info;
+
+/* Fill *opts with the defaults above. */
+BVLS_API void bvls_backward_default_opts(bvls_backward_opts* opts);
+
+/*
+ * Gradients of a loss L(x*) through the solution map (y, A) -> x*(y, A) for B instances
+ * that share the handle's A and box.  The paper has no backward pass; this follows from
+ * the optimality conditions of Section 3.2: at a non-degenerate optimum (strict
+ * complementarity, A_F of full column rank on the free set F) the coordinates outside F
+ * sit at their bounds and x_F solves the restricted normal equations
+ * A_F^T A_F x_F = A_F^T (y - A_B x_B).  With v = dL/dx and w = (A_F^T A_F)^{-1} v_F (zero
+ * off F, found by conjugate gradients on the free set, float64):
+ *     dL/dy_b = A_F w_b,     dL/dA = sum_b  r_b w_b^T - (A_F w_b) x_b^T,   r_b = y_b - A x_b.
+ * Components of dL/dx on the fixed coordinates do not flow back.
+ *   X        any; B x n doubles: the solutions (e.g. X_out of bvls_solve_batched).
+ *   Y        any; B rows of m float32 at Y + b*ldy (ldy >= m): the right-hand sides.
+ *   dLdX     any; B x n doubles.
+ *   opts     host or NULL (defaults).
+ *   dLdY     any; B x m doubles, or NULL.
+ *   dLdA     any; m x n doubles, column-major (leading dimension m), summed over the batch,
+ *            or NULL.
+ *   status_out  any; B ints or NULL: 0 CG converged, 1 CG iteration limit, 2 free set
+ *            larger than 1024 (that instance contributes zero gradients).
+ *   info     host or NULL.
+ * Limits: m <= 24576 (the handle's limit); free sets up to 1024 coordinates.  Returns
+ * BVLS_OK, or an error (EINVAL, ENOMEM, ECUDA; outputs untouched).
+ */
+BVLS_API bvls_status bvls_backward(bvls_handle* h, int B, const double* X, const float* Y, int ldy,
+                                   const double* dLdX, const bvls_backward_opts* opts, double* dLdY,
+                                   double* dLdA, int* status_out, bvls_backward_info* info);
+
 /*
  * One-call solve that allocates nothing.  The paper has no counterpart: this is a service
  * for callers that cannot allocate device memory -- code that runs inside a memory pool or

@@ -19,11 +19,13 @@ from . import _capi
 from ._capi import (BVLS_DUAL_SCALING, BVLS_DUAL_TRANSLATION, BVLS_DUAL_ZERO, BVLS_EINVAL,
                     BVLS_EMAXITER, BVLS_ENONFINITE, BVLS_ENOTSUP, BVLS_OK, BVLS_PREC_FP32,
                     BVLS_PREC_FP32X2, DUAL_NAMES, STATUS_NAMES, bvls_default_opts, bvls_destroy,
+                    bvls_backward, bvls_backward_default_opts, bvls_backward_info, bvls_backward_opts,
                     bvls_batch_info, bvls_info, bvls_last_error, bvls_opts, bvls_setup, bvls_solve,
                     bvls_solve_batched)
 
 __all__ = ["Solver", "BVLSError", "bvls_setup", "bvls_solve", "bvls_destroy", "bvls_default_opts",
-           "bvls_last_error", "bvls_opts", "bvls_info", "bvls_batch_info", "bvls_solve_batched", "make_opts"]
+           "bvls_last_error", "bvls_opts", "bvls_info", "bvls_batch_info", "bvls_solve_batched", "make_opts",
+           "bvls_backward", "bvls_backward_opts", "bvls_backward_info", "solve_batched_autograd"]
 
 
 class BVLSError(RuntimeError):
@@ -176,3 +178,83 @@ class Solver:
         d["status"] = STATUS_NAMES.get(st, st)
         d["dual"] = DUAL_NAMES.get(info.dual_mode, info.dual_mode)
         return X, S, gaps, its, sts, d, st
+
+    def backward(self, X, Y, dLdX, *, want_dA: bool = True, free_tol: float = 1e-9, cg_tol: float = 1e-12,
+                 cg_max_iter: int = 4000, check: bool = True):
+        """Run bvls_backward: gradients of L(x*) through the solution map.
+
+        X (B x n solutions), Y (B x m right-hand sides) and dLdX (B x n) as CUDA tensors or
+        numpy arrays.  Returns (dLdY (B x m), dLdA (m x n, summed over the batch, or None),
+        status (B), info_dict), following the type of X.
+        """
+        o = bvls_backward_default_opts()
+        o.free_tol, o.cg_tol, o.cg_max_iter = float(free_tol), float(cg_tol), int(cg_max_iter)
+        if _is_torch(X):
+            import torch
+            dev = X.device
+            Xk = X.detach().to(dtype=torch.float64).contiguous()
+            B = int(Xk.shape[0])
+            Yk = Y.detach().to(device=dev, dtype=torch.float32).contiguous()
+            Vk = dLdX.detach().to(device=dev, dtype=torch.float64).contiguous()
+            dY = torch.empty((B, self.m), dtype=torch.float64, device=dev)
+            dA = torch.empty((self.n, self.m), dtype=torch.float64, device=dev) if want_dA else None
+            sts = torch.empty(B, dtype=torch.int32, device=dev)
+            ptr = lambda t: None if t is None else t.data_ptr()
+        else:
+            Xk = np.ascontiguousarray(np.asarray(X, dtype=np.float64).reshape(-1, self.n))
+            B = int(Xk.shape[0])
+            Yk = np.ascontiguousarray(np.asarray(Y, dtype=np.float32).reshape(B, self.m))
+            Vk = np.ascontiguousarray(np.asarray(dLdX, dtype=np.float64).reshape(B, self.n))
+            dY = np.empty((B, self.m), dtype=np.float64)
+            dA = np.empty((self.n, self.m), dtype=np.float64) if want_dA else None
+            sts = np.empty(B, dtype=np.int32)
+            ptr = lambda t: None if t is None else t.ctypes.data
+        st, info = bvls_backward(self.handle, B, ptr(Xk), ptr(Yk), self.m, ptr(Vk), o, ptr(dY), ptr(dA), ptr(sts))
+        if check and st != BVLS_OK:
+            raise BVLSError(st, bvls_last_error())
+        # the C ABI writes dL/dA column-major (m x n): as a row-major (n x m) array, transpose
+        return dY, (dA.T if dA is not None else None), sts, info.as_dict()
+
+
+def _autograd_function():
+    import torch
+
+    class _SolveBatched(torch.autograd.Function):
+        """x* = argmin_{l <= x <= u} 1/2 ||y_b - A x||^2 for every row y_b of Y, with gradients
+        to A and Y from the free-set normal equations (bvls_backward)."""
+
+        @staticmethod
+        def forward(ctx, A, Y, l, u, opts_kw):
+            solver = Solver(A.detach(), l, u)
+            X, S, gaps, its, sts, info, st = solver.solve_batched(Y.detach(), **opts_kw)
+            ctx.solver = solver
+            ctx.save_for_backward(X, Y.detach())
+            ctx.mark_non_differentiable(S)
+            return X, S
+
+        @staticmethod
+        def backward(ctx, dX, dS):
+            X, Y = ctx.saved_tensors
+            solver = ctx.solver
+            want_dA = ctx.needs_input_grad[0]
+            dY, dA, sts, info = solver.backward(X, Y, dX, want_dA=want_dA)
+            solver.close()
+            ctx.solver = None
+            gA = dA.to(dtype=torch.float32) if want_dA else None
+            gY = dY.to(dtype=Y.dtype) if ctx.needs_input_grad[1] else None
+            return gA, gY, None, None, None
+
+    return _SolveBatched
+
+
+_FN = None
+
+
+def solve_batched_autograd(A, Y, l=None, u=None, **opts_kw):
+    """Differentiable batched solve: returns (X, screened) with X (B x n, float64) carrying
+    gradients to A (m x n) and Y (B x m) through the solution map."""
+    global _FN
+    if _FN is None:
+        _FN = _autograd_function()
+    return _FN.apply(A, Y, l, u, opts_kw)
+

@@ -21,7 +21,7 @@ DUAL_NAMES = {0: "scaling", 1: "translation", 2: "zero"}
 
 # Every symbol the header declares; tests check that the library exports all of them.
 EXPORTED = ("bvls_default_opts", "bvls_setup", "bvls_solve", "bvls_destroy", "bvls_last_error",
-            "bvls_solve_static", "bvls_solve_batched")
+            "bvls_solve_static", "bvls_solve_batched", "bvls_backward_default_opts", "bvls_backward")
 
 
 class bvls_opts(ctypes.Structure):
@@ -84,6 +84,27 @@ class bvls_batch_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class bvls_backward_opts(ctypes.Structure):
+    _fields_ = [
+        ("free_tol", ctypes.c_double),
+        ("cg_tol", ctypes.c_double),
+        ("cg_max_iter", ctypes.c_int),
+    ]
+
+
+class bvls_backward_info(ctypes.Structure):
+    _fields_ = [
+        ("n_converged", ctypes.c_int),
+        ("n_iter_limit", ctypes.c_int),
+        ("n_too_large", ctypes.c_int),
+        ("max_free", ctypes.c_int),
+        ("max_cg_iters", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -113,6 +134,11 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.bvls_solve_batched.argtypes = [vp, ci, vp, ci, vp, ctypes.POINTER(bvls_opts), vp, vp, vp, vp, vp,
                                        ctypes.POINTER(bvls_batch_info)]
     lib.bvls_solve_batched.restype = ci
+    lib.bvls_backward_default_opts.argtypes = [ctypes.POINTER(bvls_backward_opts)]
+    lib.bvls_backward_default_opts.restype = None
+    lib.bvls_backward.argtypes = [vp, ci, vp, vp, ci, vp, ctypes.POINTER(bvls_backward_opts), vp, vp, vp,
+                                  ctypes.POINTER(bvls_backward_info)]
+    lib.bvls_backward.restype = ci
     _lib = lib
     return lib
 
@@ -158,6 +184,21 @@ def bvls_solve_batched(h: int, B: int, Y_ptr: int, ldy: int, X0_ptr: int | None,
     info = bvls_batch_info()
     st = load().bvls_solve_batched(h, B, Y_ptr, ldy, X0_ptr, ctypes.byref(opts) if opts is not None else None,
                                    X_out_ptr, screened_ptr, gaps_ptr, iters_ptr, status_ptr, ctypes.byref(info))
+    return st, info
+
+
+def bvls_backward_default_opts() -> bvls_backward_opts:
+    o = bvls_backward_opts()
+    load().bvls_backward_default_opts(ctypes.byref(o))
+    return o
+
+
+def bvls_backward(h: int, B: int, X_ptr: int, Y_ptr: int, ldy: int, dLdX_ptr: int,
+                  opts: bvls_backward_opts | None, dLdY_ptr: int | None, dLdA_ptr: int | None,
+                  status_ptr: int | None) -> tuple[int, bvls_backward_info]:
+    info = bvls_backward_info()
+    st = load().bvls_backward(h, B, X_ptr, Y_ptr, ldy, dLdX_ptr, ctypes.byref(opts) if opts is not None else None,
+                              dLdY_ptr, dLdA_ptr, status_ptr, ctypes.byref(info))
     return st, info
 
 

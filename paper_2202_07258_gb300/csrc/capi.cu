@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include "backward.cuh"
 #include "batch.cuh"
 #include "bvls_gb300.h"
 #include "common.cuh"
@@ -940,3 +941,115 @@ extern "C" bvls_status bvls_solve_batched(bvls_handle* h, int B, const float* Y,
   g_err.clear();
   return BVLS_OK;
 }
+
+// ------------------------------------------------------------------ backward
+extern "C" void bvls_backward_default_opts(bvls_backward_opts* o) {
+  if (!o) return;
+  o->free_tol = 1e-9;
+  o->cg_tol = 1e-12;
+  o->cg_max_iter = 4000;
+}
+
+extern "C" bvls_status bvls_backward(bvls_handle* h, int B, const double* X, const float* Y, int ldy,
+                                     const double* dLdX, const bvls_backward_opts* opts, double* dLdY,
+                                     double* dLdA, int* status_out, bvls_backward_info* info) {
+  if (!h || !X || !Y || !dLdX) return set_err(BVLS_EINVAL, "handle, X, Y and dLdX are required");
+  if (B < 1 || ldy < h->m) return set_err(BVLS_EINVAL, "need B >= 1 and ldy >= m");
+  bvls_backward_opts o;
+  bvls_backward_default_opts(&o);
+  if (opts) o = *opts;
+  if (!(o.free_tol >= 0.0) || !(o.cg_tol >= 0.0) || o.cg_max_iter < 1)
+    return set_err(BVLS_EINVAL, "invalid backward options");
+  const int m = h->m, n = h->n;
+  std::vector<void*> mem;
+  auto alloc = [&](void** ptr, size_t bytes) -> cudaError_t {
+    cudaError_t e = cudaMalloc(ptr, bytes + 16);
+    if (e == cudaSuccess) mem.push_back(*ptr);
+    return e;
+  };
+  auto release = [&]() {
+    cudaStreamSynchronize(h->s);
+    for (void* q : mem) cudaFree(q);
+    mem.clear();
+  };
+#define BCK(call)                                                                              \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) {                                                                   \
+      release();                                                                               \
+      return set_err(e_ == cudaErrorMemoryAllocation ? BVLS_ENOMEM : BVLS_ECUDA, "%s failed: %s", \
+                     #call, cudaGetErrorString(e_));                                           \
+    }                                                                                          \
+  } while (0)
+  BwdParams p{};
+  p.A = h->A;
+  p.m = m;
+  p.n = n;
+  p.lda = h->lda;
+  p.B = B;
+  p.l = h->l;
+  p.u = h->u;
+  p.ldy = h->lda;
+  p.free_tol = o.free_tol;
+  p.cg_tol = o.cg_tol;
+  p.cg_max_iter = o.cg_max_iter;
+  double *dX = nullptr, *dV = nullptr, *dDY = nullptr, *dW = nullptr, *dQ = nullptr, *dR = nullptr, *dDA = nullptr;
+  float* dY = nullptr;
+  int *dSt = nullptr, *dIt = nullptr, *dNf = nullptr;
+  BCK(alloc((void**)&dX, sizeof(double) * (size_t)B * n));
+  BCK(alloc((void**)&dV, sizeof(double) * (size_t)B * n));
+  BCK(alloc((void**)&dY, sizeof(float) * (size_t)B * h->lda));
+  BCK(alloc((void**)&dDY, sizeof(double) * (size_t)B * m));
+  BCK(alloc((void**)&dSt, sizeof(int) * (size_t)B));
+  BCK(alloc((void**)&dIt, sizeof(int) * (size_t)B));
+  BCK(alloc((void**)&dNf, sizeof(int) * (size_t)B));
+  if (dLdA) {
+    BCK(alloc((void**)&dW, sizeof(double) * (size_t)B * n));
+    BCK(alloc((void**)&dQ, sizeof(double) * (size_t)B * m));
+    BCK(alloc((void**)&dR, sizeof(double) * (size_t)B * m));
+    BCK(alloc((void**)&dDA, sizeof(double) * (size_t)m * n));
+  }
+  if (h->own_stream) {
+    BCK(cudaEventRecord(h->ev_in, h->user));
+    BCK(cudaStreamWaitEvent(h->s, h->ev_in, 0));
+  }
+  BCK(cudaMemcpyAsync(dX, X, sizeof(double) * (size_t)B * n, cudaMemcpyDefault, h->s));
+  BCK(cudaMemcpyAsync(dV, dLdX, sizeof(double) * (size_t)B * n, cudaMemcpyDefault, h->s));
+  BCK(cudaMemcpy2DAsync(dY, sizeof(float) * h->lda, Y, sizeof(float) * ldy, sizeof(float) * m, B,
+                        cudaMemcpyDefault, h->s));
+  p.X = dX;
+  p.dLdX = dV;
+  p.Y = dY;
+  p.dLdY = dDY;
+  p.W = dW;
+  p.Q = dQ;
+  p.R = dR;
+  p.status = dSt;
+  p.iters = dIt;
+  p.nfree = dNf;
+  BCK(launch_bwd(p, h->s));
+  if (dLdA) BCK(launch_bwd_da(p, dDA, h->s));
+  std::vector<int> st(B), it(B), nf(B);
+  BCK(cudaMemcpyAsync(st.data(), dSt, sizeof(int) * B, cudaMemcpyDeviceToHost, h->s));
+  BCK(cudaMemcpyAsync(it.data(), dIt, sizeof(int) * B, cudaMemcpyDeviceToHost, h->s));
+  BCK(cudaMemcpyAsync(nf.data(), dNf, sizeof(int) * B, cudaMemcpyDeviceToHost, h->s));
+  if (dLdY) BCK(cudaMemcpyAsync(dLdY, dDY, sizeof(double) * (size_t)B * m, cudaMemcpyDefault, h->s));
+  if (dLdA) BCK(cudaMemcpyAsync(dLdA, dDA, sizeof(double) * (size_t)m * n, cudaMemcpyDefault, h->s));
+  if (status_out) BCK(cudaMemcpyAsync(status_out, dSt, sizeof(int) * B, cudaMemcpyDefault, h->s));
+  BCK(cudaStreamSynchronize(h->s));
+  release();
+#undef BCK
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    for (int b = 0; b < B; ++b) {
+      info->n_converged += st[b] == 0;
+      info->n_iter_limit += st[b] == 1;
+      info->n_too_large += st[b] == 2;
+      info->max_free = std::max(info->max_free, nf[b]);
+      info->max_cg_iters = std::max(info->max_cg_iters, it[b]);
+    }
+  }
+  g_err.clear();
+  return BVLS_OK;
+}
+

@@ -58,6 +58,10 @@ def test_setup_rejects_bad_sizes_before_touching_the_device(lib):
     assert st == _capi.BVLS_EINVAL
     st, _ = _capi.bvls_solve_batched(None, 4, None, 2, None, None, None, None, None, None, None)
     assert st == _capi.BVLS_EINVAL
+    st, _ = _capi.bvls_backward(None, 4, None, None, 2, None, None, None, None, None)
+    assert st == _capi.BVLS_EINVAL
+    o = _capi.bvls_backward_default_opts()
+    assert o.free_tol == 1e-9 and o.cg_tol == 1e-12 and o.cg_max_iter == 4000
 
 
 def test_struct_layouts_match_header(tmp_path):
@@ -69,7 +73,8 @@ def test_struct_layouts_match_header(tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     classes = {"bvls_opts": _capi.bvls_opts, "bvls_info": _capi.bvls_info,
-               "bvls_batch_info": _capi.bvls_batch_info}
+               "bvls_batch_info": _capi.bvls_batch_info, "bvls_backward_opts": _capi.bvls_backward_opts,
+               "bvls_backward_info": _capi.bvls_backward_info}
     fields = {k: [f for f, _ in c._fields_] for k, c in classes.items()}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "bvls_gb300.h"', "int main(void){"]
     for st, fl in fields.items():
