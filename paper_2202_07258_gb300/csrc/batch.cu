@@ -751,7 +751,7 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
   if (PREC == kF32 && __syncthreads_or(tid < kBEvalInst && s_ref[tid])) {
     // ---- phase 2b: a gap term depends on the rounding of its correlation only when the
     // coordinate is free or its correlation is within the margin of zero; those
-    // correlations are recomputed in double-float (lane = coordinate, all m rows).
+    // correlations are recomputed in double-float.
     const int bb = warp;
     const int inst = s_ref[bb] ? s_inst[bb] : -1;
     int cnt = 0;
@@ -778,17 +778,44 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
         cnt += __popc(msk);
       }
       __syncwarp();
-      for (int t = lane; t < cnt; t += 32) {
-        const int j = s_item[bb * p.npad + t];
-        const float* __restrict__ col = p.A + (size_t)j * p.lda;
-        float sh = 0.f, sc = 0.f;
-#pragma unroll 4
-        for (int i = 0; i < p.m; ++i) {
-          const float2 r = sr[(size_t)i * kBEvalInst + bb];
-          df_fma(sh, sc, __ldg(col + i), r.x, r.y);
+      // four listed coordinates at a time; lanes over rows, then a shuffle reduction, so the
+      // double-float chains are as short as in the main correlation
+      for (int t0 = 0; t0 < cnt; t0 += 4) {
+        int jj[4];
+        const float* col[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          jj[c] = s_item[bb * p.npad + (t0 + c < cnt ? t0 + c : t0)];
+          col[c] = p.A + (size_t)jj[c] * p.lda;
         }
-        b.Ge[(size_t)inst * p.npad + j] = df2_norm(sh, sc);
-        s_fl[bb * p.npad + j] |= 4;
+        float sh[4] = {0.f, 0.f, 0.f, 0.f}, sc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 2
+        for (int i = lane; i < p.m; i += 32) {
+          const float2 r = sr[(size_t)i * kBEvalInst + bb];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) df_fma(sh[c], sc[c], __ldg(col[c] + i), r.x, r.y);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            const float ox = __shfl_xor_sync(kFull, sh[c], o);
+            const float oc = __shfl_xor_sync(kFull, sc[c], o);
+            df_add(sh[c], sc[c], ox, oc);
+          }
+        }
+        if (lane < 4 && t0 + lane < cnt) {
+          float h = sh[0], l = sc[0];
+#pragma unroll
+          for (int c = 1; c < 4; ++c)
+            if (lane == c) {
+              h = sh[c];
+              l = sc[c];
+            }
+          b.Ge[(size_t)inst * p.npad + jj[lane]] = df2_norm(h, l);
+          s_fl[bb * p.npad + jj[lane]] |= 4;
+        }
+        __syncwarp();
       }
     }
     __syncthreads();

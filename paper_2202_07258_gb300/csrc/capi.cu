@@ -744,8 +744,6 @@ BParams make_bparams(bvls_handle* h, const bvls_opts& o, int max_iter, int B) {
   // products per row in double-float.
   const double dg = (h->m + 31) / 32 + 5;
   p.Cg2 = 2.0 * (dg + 2.0) * (dg + 2.0) * kU * kU + 4.0 * kU * kU + 2.0 * kU64;
-  // the recomputation in double-float runs one lane over all m rows
-  p.Cg2 = std::max(p.Cg2, 2.0 * (h->m + 2.0) * (h->m + 2.0) * kU * kU + 4.0 * kU * kU + 2.0 * kU64);
   p.Cg = o.precision == BVLS_PREC_FP32X2 ? p.Cg2 : 1.01 * (dg + 2.0) * kU + kU;
   const double df = h->n;
   p.Cf = 2.0 * (df + 2.0) * (df + 2.0) * kU * kU + 2.0 * kU * kU;
