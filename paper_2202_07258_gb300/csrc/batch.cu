@@ -1003,6 +1003,18 @@ __global__ void k_bchunk_end(BBuffers b, int chunk_len) {
   if (threadIdx.x == 0 && blockIdx.x == 0) b.st->kbase += chunk_len;
 }
 
+__global__ void k_bloop_ctl(BState* st, cudaGraphConditionalHandle h, int max_chunks) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const int c = ++st->chunks;
+    if (st->done || st->error || c >= max_chunks) cudaGraphSetConditional(h, 0);
+  }
+}
+
+cudaError_t launch_bloop_ctl(const BBuffers& b, cudaGraphConditionalHandle h, int max_chunks, cudaStream_t s) {
+  k_bloop_ctl<<<1, 32, 0, s>>>(b.st, h, max_chunks);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_bchunk_end(const BBuffers& b, int chunk_len, cudaStream_t s) {
   k_bchunk_end<<<1, 32, 0, s>>>(b, chunk_len);
   return cudaGetLastError();

@@ -43,7 +43,8 @@ struct BState {
   int error;          // a bounded wait gave up
   int nonfinite;      // Y or X0 held NaN/Inf
   int gap_evals;      // evaluations run
-  int pad0, pad1;
+  int chunks;         // chunks run by the device-side loop of the solve graph
+  int pad0;
   double sum_step;    // sum over tensor-core steps of the active instance count
   double sum_eval;    // sum over evaluations of the active instance count
   double sum_pres;    // sum over evaluations and instances of the preserved coordinates
@@ -107,6 +108,8 @@ cudaError_t launch_bstep(const BParams& p, const BBuffers& b, int j, cudaStream_
 cudaError_t launch_beval(const BParams& p, const BBuffers& b, int j, int precision, cudaStream_t s);
 cudaError_t launch_bcompact(const BParams& p, const BBuffers& b, cudaStream_t s);
 cudaError_t launch_bchunk_end(const BBuffers& b, int chunk_len, cudaStream_t s);
+// Last node of a chunk inside the batched solve graph's while loop (see launch_loop_ctl).
+cudaError_t launch_bloop_ctl(const BBuffers& b, cudaGraphConditionalHandle h, int max_chunks, cudaStream_t s);
 size_t bstep_smem_bytes();
 cudaError_t batch_configure(int m, int npad);  // shared-memory attributes of the step and evaluation kernels
 size_t beval_smem_bytes(int m, int npad);

@@ -578,30 +578,37 @@ bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const b
         h->exec = nullptr;
       }
       h->have_graph = false;
+      // One graph for the whole solve: a while node whose body is one chunk of iterations
+      // followed by the loop-control kernel, which ends the loop on the device once the stop
+      // flag is set (no host polling, no chunk launched after the stop).
       cudaGraph_t g = nullptr;
-      CK(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
-      cudaError_t e = enqueue_chunk(h, p, o, chunk, nullptr);
-      cudaError_t e2 = cudaStreamEndCapture(h->s, &g);
-      CK(e);
-      CK(e2);
-      e = cudaGraphInstantiate(&h->exec, g, 0);
+      CK(cudaGraphCreate(&g, 0));
+      cudaGraphConditionalHandle hc;
+      cudaError_t e = cudaGraphConditionalHandleCreate(&hc, g, 1, cudaGraphCondAssignDefault);
+      cudaGraphNodeParams np = {};
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = hc;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      cudaGraphNode_t node;
+      if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+      cudaGraph_t body = e == cudaSuccess ? np.conditional.phGraph_out[0] : nullptr;
+      if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(h->s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        cudaError_t e1 = enqueue_chunk(h, p, o, chunk, nullptr);
+        if (e1 == cudaSuccess) e1 = launch_loop_ctl(h->b, hc, (int)std::min<long long>(max_chunks, 0x7fffffff), h->s);
+        cudaError_t e2 = cudaStreamEndCapture(h->s, &body);
+        e = e1 != cudaSuccess ? e1 : e2;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&h->exec, g, 0);
       cudaGraphDestroy(g);
       CK(e);
       h->have_graph = true;
       h->key = key;
       h->chunk_len = chunk;
     }
-    // Keep one chunk queued behind the one whose stop flag is being read.
-    for (long long c = 0; c < max_chunks; ++c) {
-      CK(cudaGraphLaunch(h->exec, h->s));
-      ++chunks_run;
-      CK(cudaMemcpyAsync(&h->pinned[c & 1], &h->b.st->done, sizeof(int), cudaMemcpyDeviceToHost, h->s));
-      CK(cudaEventRecord(h->poll[c & 1], h->s));
-      if (c >= 1) {
-        CK(cudaEventSynchronize(h->poll[(c - 1) & 1]));
-        if (h->pinned[(c - 1) & 1]) break;
-      }
-    }
+    CK(cudaGraphLaunch(h->exec, h->s));
+    chunks_run = -1;  // counted on the device
   }
   CK(cudaStreamSynchronize(h->s));
   DevState hs;
@@ -630,10 +637,11 @@ bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const b
     info->tr_ms = tr_ms;
     info->fwd_launches = fwd_launches;
     info->tr_launches = tr_launches;
-    info->kernel_launches = (fused ? 3.0 : 2.0) + (double)chunks_run * (double)per_chunk;
+    const double chunks_done = chunks_run >= 0 ? (double)chunks_run : (double)hs.chunks;
+    info->kernel_launches = (fused ? 3.0 : 2.0) + chunks_done * (double)(per_chunk + (chunks_run >= 0 ? 0 : 1));
     info->single_pass = fused ? 1 : 0;
   }
-  if (!hs.done) return set_err(BVLS_EMAXITER, "stopped after %d chunks without the stop flag", (int)max_chunks);
+  if (!hs.done) return set_err(BVLS_EMAXITER, "stopped after %lld chunks without the stop flag", max_chunks);
   if (!hs.converged) return set_err(BVLS_EMAXITER, "gap %.3e >= tol after %d iterations", hs.gap, hs.k);
   g_err.clear();
   return BVLS_OK;
@@ -868,42 +876,49 @@ extern "C" bvls_status bvls_solve_batched(bvls_handle* h, int B, const float* Y,
     if (pst != BVLS_OK) return pst;
   } else {
     const double key[10] = {(double)K,  (double)chunk, (double)o.precision, (double)o.screening, (double)o.restart,
-                            o.tol,      (double)max_iter, p.invL,          (double)B,           1.0};
+                            o.tol,      (double)max_iter, p.invL,          (double)B,           2.0};
     if (!h->b_have_graph || std::memcmp(key, h->b_key, sizeof(key)) != 0) {
       if (h->b_exec) {
         cudaGraphExecDestroy(h->b_exec);
         h->b_exec = nullptr;
       }
       h->b_have_graph = false;
+      // one graph for the whole batched solve: a while node around one chunk and the
+      // loop-control kernel (ends the loop on the device when every instance has finished)
       cudaGraph_t g = nullptr;
-      CK(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
-      cudaError_t e = enqueue_bchunk(h, p, o, chunk, nullptr);
-      cudaError_t e2 = cudaStreamEndCapture(h->s, &g);
-      CK(e);
-      CK(e2);
-      e = cudaGraphInstantiate(&h->b_exec, g, 0);
+      CK(cudaGraphCreate(&g, 0));
+      cudaGraphConditionalHandle hc;
+      cudaError_t e = cudaGraphConditionalHandleCreate(&hc, g, 1, cudaGraphCondAssignDefault);
+      cudaGraphNodeParams np = {};
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = hc;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      cudaGraphNode_t node;
+      if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+      cudaGraph_t body = e == cudaSuccess ? np.conditional.phGraph_out[0] : nullptr;
+      if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(h->s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        cudaError_t e1 = enqueue_bchunk(h, p, o, chunk, nullptr);
+        if (e1 == cudaSuccess) e1 = launch_bloop_ctl(bb, hc, (int)std::min<long long>(max_chunks, 0x7fffffff), h->s);
+        cudaError_t e2 = cudaStreamEndCapture(h->s, &body);
+        e = e1 != cudaSuccess ? e1 : e2;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&h->b_exec, g, 0);
       cudaGraphDestroy(g);
       CK(e);
       h->b_have_graph = true;
       std::memcpy(h->b_key, key, sizeof(key));
     }
-    for (long long c = 0; c < max_chunks; ++c) {
-      CK(cudaGraphLaunch(h->b_exec, h->s));
-      ++chunks_run;
-      CK(cudaMemcpyAsync(&h->pinned[2 + (c & 1)], &bb.st->done, sizeof(int), cudaMemcpyDeviceToHost, h->s));
-      CK(cudaEventRecord(h->poll[c & 1], h->s));
-      if (c >= 1) {
-        CK(cudaEventSynchronize(h->poll[(c - 1) & 1]));
-        if (h->pinned[2 + ((c - 1) & 1)]) break;
-      }
-    }
+    CK(cudaGraphLaunch(h->b_exec, h->s));
+    chunks_run = -1;  // counted on the device
   }
   CK(cudaStreamSynchronize(h->s));
   BState hs;
   CK(cudaMemcpy(&hs, bb.st, sizeof(BState), cudaMemcpyDeviceToHost));
   if (hs.nonfinite) return set_err(BVLS_ENONFINITE, "Y or X0 contains NaN or Inf");
   if (hs.error) return set_err(BVLS_ETIMEOUT, "a device-side wait exceeded its bound; results discarded");
-  if (!hs.done) return set_err(BVLS_ECUDA, "batched solve stopped after %lld chunks without finishing", chunks_run);
+  if (!hs.done) return set_err(BVLS_ECUDA, "batched solve stopped after %d chunks without finishing", hs.chunks);
   std::vector<int> st_h(B), it_h(B);
   CK(cudaMemcpyAsync(X_out, bb.xout, sizeof(double) * (size_t)B * h->n, cudaMemcpyDefault, h->s));
   if (screened_out)
@@ -933,7 +948,8 @@ extern "C" bvls_status bvls_solve_batched(bvls_handle* h, int B, const float* Y,
     info->eval_ms = eval_ms;
     info->step_launches = step_launches;
     info->eval_launches = eval_launches;
-    info->kernel_launches = 1.0 + (double)chunks_run * (double)per_chunk;
+    info->kernel_launches =
+        1.0 + (chunks_run >= 0 ? (double)chunks_run * (double)per_chunk : (double)hs.chunks * (double)(per_chunk + 1));
   }
   if (nconv < B) return set_err(BVLS_EMAXITER, "%d of %d instances reached max_iter with gap >= tol", B - nconv, B);
   g_err.clear();

@@ -46,7 +46,7 @@ struct DevState {
   int gap_evals;
   int nonfinite;
   int error;          // a bounded device wait gave up (nonzero: results invalid)
-  int pad1;
+  int chunks;         // chunks run by the device-side loop of the solve graph
   double t;           // FISTA momentum parameter t_k
   double P[2];        // 1/2 ||r_k||^2 in slot k & 1 (r = rh + rl)
   double eps;         // translation step of the last evaluation
@@ -239,6 +239,9 @@ struct Buffers {
 };
 
 cudaError_t launch_init(const Params& p, const Buffers& b, cudaStream_t s);
+// Last node of a chunk inside the solve graph's while loop: clears the loop condition once
+// the solve has stopped, a wait gave up, or max_chunks chunks have run.
+cudaError_t launch_loop_ctl(const Buffers& b, cudaGraphConditionalHandle h, int max_chunks, cudaStream_t s);
 cudaError_t launch_fwd(const Params& p, const Buffers& b, int slot, int precision, bool fold,
                        cudaStream_t s);
 cudaError_t launch_tr(const Params& p, const Buffers& b, int slot, int precision, bool gap_iter,

@@ -123,6 +123,7 @@ __global__ void k_init_state(Params p, Buffers b) {
     st->out_slot = 0;
     st->gap_evals = 0;
     st->nonfinite = bad;
+    st->chunks = 0;
     st->t = 1.0;
     st->P[0] = 0.0;
     st->P[1] = 0.0;
@@ -168,6 +169,18 @@ __global__ void k_init_arrays(Params p, Buffers b) {
     b.rh[i] = 0.0f;
     b.rl[i] = 0.0f;
   }
+}
+
+__global__ void k_loop_ctl(DevState* st, cudaGraphConditionalHandle h, int max_chunks) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const int c = ++st->chunks;
+    if (st->done || st->error || c >= max_chunks) cudaGraphSetConditional(h, 0);
+  }
+}
+
+cudaError_t launch_loop_ctl(const Buffers& b, cudaGraphConditionalHandle h, int max_chunks, cudaStream_t s) {
+  k_loop_ctl<<<1, 32, 0, s>>>(b.st, h, max_chunks);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_init(const Params& p, const Buffers& b, cudaStream_t s) {
