@@ -95,6 +95,13 @@ typedef struct {
   int single_pass;    /* 1 (default): when m <= 8192, one streaming read of the preserved
                          columns per iteration yields both products; 0: two passes
                          (A_S x_S, then A_S^T r), the form used for larger m */
+  const double* dual_point; /* any; m doubles or NULL (default).  A fixed dual point used by
+                         every screening step of bvls_solve in place of Theta(x_k): the
+                         oracle-dual-point experiment of Section 5, where theta* informs the
+                         test.  Translated into F_D along t when some a_j^T theta > 0 with
+                         u_j = +inf; any dual-feasible point keeps the test safe.  Needs the
+                         single-pass form and a dual mode other than BVLS_DUAL_ZERO
+                         (else BVLS_ENOTSUP / BVLS_EINVAL).  Ignored by the other entry points. */
 } bvls_opts;
 
 typedef struct {

@@ -262,9 +262,22 @@ def _dual_point(A, y, x, l, u, mode, t, w, cols):
     return np.zeros(A.shape[0])
 
 
+def _fixed_dual_point(A, y, x, theta0, mode, t, w, cols):
+    """A caller-given dual point, translated into F_D (Eq. (BVLR_dual_up2)) when some
+    a_j^T theta0 > 0 on J_inf; with no interior direction it is used only if feasible."""
+    theta0 = np.asarray(theta0, dtype=np.float64)
+    if mode == "translation":
+        tau, _ = rounding_pads(A, y, x, theta0)
+        theta, _ = translate(A, theta0, t, cols, w, margin=tau * np.linalg.norm(A, axis=0))
+        return theta
+    if mode == "zero" and cols.size and np.max(A[:, cols].T @ theta0) > 0.0:
+        return np.zeros(A.shape[0])
+    return theta0
+
+
 def solve(A, y, l=None, u=None, *, tol=1e-6, screen_every=10, screening=True,
           max_iter=100_000, x0=None, L=None, t=None, eps_scope="preserved",
-          restart=True, record=False):
+          restart=True, record=False, dual_point=None):
     """Algorithm 1 (Algorithm 2 for NNLS) with a FISTA primal update.
 
     Each iteration k computes, on the preserved set A:
@@ -278,6 +291,9 @@ def solve(A, y, l=None, u=None, *, tol=1e-6, screen_every=10, screening=True,
       already at that bound in x_k and x_{k+1}, y' <- y' - A_S x_S, A <- A \\ S (momentum
       kept), and the loop stops when Gap < tol, returning x_k.
     ``screening=False`` runs the same iteration and gap evaluations with nothing fixed.
+    ``dual_point`` (length m) replaces Theta(x_k) in every screening step by a fixed dual
+    point (translated into F_D when needed) -- the oracle-dual-point experiment of Section 5,
+    where theta* itself informs the test; any feasible point keeps the sphere safe.
     """
     A, y, l, u = as_problem(A, y, l, u)
     m, n = A.shape
@@ -325,12 +341,14 @@ def solve(A, y, l=None, u=None, *, tol=1e-6, screen_every=10, screening=True,
         if (k + 1) % K == 0 or k == max_iter - 1:
             # Dynamic safe screening at x_k.
             if eps_scope == "all":
-                theta = _dual_point(A, y, x, l, u, mode, t_dir, w_all, cols_all)
+                theta = _dual_point(A, y, x, l, u, mode, t_dir, w_all, cols_all) if dual_point is None \
+                    else _fixed_dual_point(A, y, x, dual_point, mode, t_dir, w_all, cols_all)
                 gap = duality_gap(A, y, x, theta, l, u)
             else:
                 cols_P = cols_all[P]
                 w_P = w_all[P] if w_all is not None else None
-                theta = _dual_point(A_P, y_red, xP, lP, uP, mode, t_dir, w_P, cols_P)
+                theta = _dual_point(A_P, y_red, xP, lP, uP, mode, t_dir, w_P, cols_P) if dual_point is None \
+                    else _fixed_dual_point(A_P, y_red, xP, dual_point, mode, t_dir, w_P, cols_P)
                 gap = duality_gap(A_P, y_red, xP, theta, lP, uP)
             history.append((k, gap, int(P.size)))
             if screening and mode != "zero":

@@ -115,8 +115,19 @@ class Solver:
         a numpy y gives numpy arrays.  ``kw`` builds the options (see ``make_opts``).
         With check=True a status other than OK / EMAXITER raises BVLSError.
         """
+        dual_point = kw.pop("dual_point", None)
         if opts is None:
             opts = make_opts(**kw)
+        keep = None
+        if dual_point is not None:
+            # a fixed dual point for every screening step (the oracle-dual-point experiment)
+            if _is_torch(dual_point):
+                import torch
+                keep = dual_point.detach().to(dtype=torch.float64).contiguous()
+                opts.dual_point = keep.data_ptr()
+            else:
+                keep = np.ascontiguousarray(np.asarray(dual_point, dtype=np.float64).reshape(self.m))
+                opts.dual_point = keep.ctypes.data
         if _is_torch(y):
             import torch
             dev = y.device
@@ -132,6 +143,7 @@ class Solver:
             s = screened_out if screened_out is not None else np.empty(self.n, dtype=np.uint8)
             ptrs = (yk.ctypes.data, None if x0k is None else x0k.ctypes.data, x.ctypes.data, s.ctypes.data)
         st, info = bvls_solve(self.handle, ptrs[0], ptrs[1], opts, ptrs[2], ptrs[3])
+        del keep
         if check and st not in (BVLS_OK, BVLS_EMAXITER):
             raise BVLSError(st, bvls_last_error())
         d = info.as_dict()

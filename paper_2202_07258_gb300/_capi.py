@@ -35,6 +35,7 @@ class bvls_opts(ctypes.Structure):
         ("lipschitz", ctypes.c_double),
         ("profile", ctypes.c_int),
         ("single_pass", ctypes.c_int),
+        ("dual_point", ctypes.c_void_p),
     ]
 
 

@@ -41,11 +41,13 @@ constexpr double kU64 = 1.1102230246251565e-16; // 2^-53
 
 struct GraphKey {
   int K, screening, precision, restart, max_iter, single_pass;
-  double tol, invL;
+  double tol, invL, eps_star, eta_star;
+  bool fixed_dual;
   bool operator==(const GraphKey& o) const {
     return K == o.K && screening == o.screening && precision == o.precision &&
            restart == o.restart && max_iter == o.max_iter && single_pass == o.single_pass &&
-           tol == o.tol && invL == o.invL;
+           tol == o.tol && invL == o.invL && eps_star == o.eps_star && eta_star == o.eta_star &&
+           fixed_dual == o.fixed_dual;
   }
 };
 
@@ -64,6 +66,7 @@ struct bvls_handle {
   Buffers b{};
   float* y_dev = nullptr;
   double* x0_dev = nullptr;
+  double *theta_dev = nullptr, *wstar_dev = nullptr;  // fixed dual point and A^T theta
   int* pinned = nullptr;
   int fwd_tiles = 0, fwd_chunks = 0, tr_blocks = 0, red_blocks = 0;
   int pass_stages = 0, pass_qw = 0, pass_cps = 1;  // fused single-pass iteration when pass_stages > 0
@@ -236,6 +239,51 @@ bvls_status validate_opts(const bvls_opts& o) {
   return BVLS_OK;
 }
 
+// The fixed dual point of the oracle-dual-point experiment: copies theta, forms
+// w* = A^T theta in float64 and the translation step that puts theta in F_D.
+bvls_status prepare_fixed_dual(bvls_handle* h, const double* theta, Params* p) {
+  if (!(h->pass_stages > 0)) return set_err(BVLS_ENOTSUP, "dual_point needs the single-pass form (m <= 8192)");
+  if (h->dual_mode == kZero)
+    return set_err(BVLS_EINVAL, "dual_point needs an interior translation direction (dual mode zero)");
+  const int m = h->m, n = h->n;
+  if (!h->theta_dev) {
+    TRY(dalloc(h, &h->theta_dev, m));
+    TRY(dalloc(h, &h->wstar_dev, n));
+  }
+  std::vector<double> th(m), ws(n), nr(n), w(n);
+  CK(cudaMemcpyAsync(h->theta_dev, theta, sizeof(double) * m, cudaMemcpyDefault, h->s));
+  CK(cudaMemcpyAsync(th.data(), h->theta_dev, sizeof(double) * m, cudaMemcpyDeviceToHost, h->s));
+  CK(launch_col_dots(h->A, h->lda, m, n, h->theta_dev, h->wstar_dev, h->s));
+  CK(cudaMemcpyAsync(ws.data(), h->wstar_dev, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
+  CK(cudaMemcpyAsync(nr.data(), h->nrm, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
+  CK(cudaMemcpyAsync(w.data(), h->w, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
+  std::vector<uint8_t> jinf(n);
+  CK(cudaMemcpyAsync(jinf.data(), h->jinf, n, cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  double tn = 0.0;
+  for (double v : th) {
+    if (!std::isfinite(v)) return set_err(BVLS_ENONFINITE, "dual_point contains NaN or Inf");
+    tn += v * v;
+  }
+  tn = std::sqrt(tn);
+  const double eta0 = 1.01 * (m + 8) * kU64 * tn;  // float64 dot a_j^T theta, per unit ||a_j||
+  double eps = 0.0;
+  if (h->dual_mode == kTranslation) {
+    for (int j = 0; j < n; ++j) {
+      if (!jinf[j] || !(nr[j] > 0.0)) continue;
+      const double den = -w[j] - h->gamma_w * nr[j] * h->t_norm;
+      eps = std::max(eps, std::max(ws[j] + eta0 * nr[j], 0.0) / den);
+    }
+    eps *= 1.0 + 1e-12;
+  }
+  p->wstar = h->wstar_dev;
+  p->theta = h->theta_dev;
+  p->tvec = h->t;
+  p->eps_star = eps;
+  p->eta_star = eta0 + eps * h->gamma_w * h->t_norm;
+  return BVLS_OK;
+}
+
 }  // namespace
 
 void bvls::record_error(const char* msg) { g_err = msg; }
@@ -253,6 +301,7 @@ void bvls_default_opts(bvls_opts* o) {
   o->lipschitz = 0.0;
   o->profile = 0;
   o->single_pass = 1;
+  o->dual_point = nullptr;
 }
 
 const char* bvls_last_error(void) { return g_err.c_str(); }
@@ -503,7 +552,11 @@ bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const b
   const int K = o.screen_every;
   const int max_iter = (int)std::min<long long>((long long)(o.max_iter + K - 1) / K * K, 0x7fffffff);
   const int chunk = chunk_length(K);
-  const Params p = make_params(h, o, max_iter);
+  Params p = make_params(h, o, max_iter);
+  if (o.dual_point) {
+    if (!o.single_pass) return set_err(BVLS_ENOTSUP, "dual_point needs the single-pass form (single_pass = 1)");
+    TRY(prepare_fixed_dual(h, o.dual_point, &p));
+  }
 
   if (h->own_stream) {
     CK(cudaEventRecord(h->ev_in, h->user));
@@ -571,7 +624,8 @@ bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const b
     cudaGraphExecDestroy(gx);
     if (pst != BVLS_OK) return pst;
   } else {
-    GraphKey key{K, o.screening, o.precision, o.restart, max_iter, o.single_pass, o.tol, p.invL};
+    GraphKey key{K, o.screening, o.precision, o.restart, max_iter, o.single_pass, o.tol, p.invL,
+                 p.eps_star, p.eta_star, p.wstar != nullptr};
     if (!h->have_graph || !(h->key == key) || h->chunk_len != chunk) {
       if (h->exec) {
         cudaGraphExecDestroy(h->exec);

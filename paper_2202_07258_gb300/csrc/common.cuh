@@ -58,6 +58,7 @@ struct DevState {
   double y_norm;      // ||y||_2
   double sum_active;  // sum of |preserved set| over the A_S^T r passes
   double sum_nnz;     // sum of nonzero preserved x_j over the A_S x_S passes
+  double theta_r2;    // ||theta - r_k||^2 for a fixed dual point (computed by the pass at gap iterations)
   unsigned int cnt_tr, cnt_gap, cnt_fwd, cnt_resid;
 };
 
@@ -85,6 +86,12 @@ struct Params {
   int dual_mode;
   int screening;
   int restart;
+  // fixed dual point (the oracle-dual-point experiment of Section 5); wstar == null: Theta(x_k)
+  const double* wstar;     // a_j^T theta_fixed (float64)
+  const double* theta;     // theta_fixed (m)
+  const double* tvec;      // the translation direction t (m), used with eps_star
+  double eps_star;         // translation step that puts theta_fixed + eps_star t in F_D
+  double eta_star;         // rounding bound of wstar_j + eps_star w_j per unit ||a_j||
   int fwd_chunks;          // grid.y of the A_S x_S kernel
   int fwd_tiles;           // grid.x of the A_S x_S kernel
 };

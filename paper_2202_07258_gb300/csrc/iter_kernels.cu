@@ -537,7 +537,8 @@ __global__ void __launch_bounds__(kRedThreads) k_gap(Params p, Buffers b, int sl
     const double nr = p.nrm[j];
     v[2] += fabs(x) * nr;
     if (p.dual_mode != kZero) {
-      const double gt = df2_to_double(gc[j]) + (trans ? eps * p.w[j] : 0.0);
+      const double gt = p.wstar ? p.wstar[j] + (trans ? p.eps_star * p.w[j] : 0.0)
+                                : df2_to_double(gc[j]) + (trans ? eps * p.w[j] : 0.0);
       const double lj = p.l[j];
       if (p.jinf[j]) {
         v[0] += (x - lj) * fmax(-gt, 0.0);
@@ -581,10 +582,14 @@ __global__ void __launch_bounds__(kRedThreads) k_gap(Params p, Buffers b, int sl
     x = warp_sum_d(x);
     if (threadIdx.x == 0) {
       const double rnorm = sqrt(2.0 * st->P[slot]) * (1.0 + 1e-6);
-      const double eta = p.Cg * rnorm + (trans ? eps * p.gamma_w * p.t_norm : 0.0);
+      const double eta = p.wstar ? p.eta_star : p.Cg * rnorm + (trans ? eps * p.gamma_w * p.t_norm : 0.0);
       const double E_r = st->E_fold + p.Cf * x + p.Csub * (rnorm + st->y_norm + st->S_fold + x);
       double gap;
-      if (p.dual_mode == kZero) {
+      if (p.wstar) {
+        // fixed dual point: 1/2 ||theta - r||^2 with the stored residual's own error
+        const double d = sqrt(st->theta_r2) * (1.0 + 1e-12) + E_r;
+        gap = a + eta * c + 0.5 * d * d;
+      } else if (p.dual_mode == kZero) {
         gap = 0.5 * (rnorm + E_r) * (rnorm + E_r);
       } else {
         const double d = E_r + eps * p.t_norm;
@@ -632,7 +637,8 @@ __global__ void __launch_bounds__(kRedThreads) k_test(Params p, Buffers b, int s
     const int j = b.idx[pp];
     const double nr = p.nrm[j];
     if (!(nr > 0.0)) continue;
-    const double gt = df2_to_double(gc[j]) + (trans ? eps * p.w[j] : 0.0);
+    const double gt = p.wstar ? p.wstar[j] + (trans ? p.eps_star * p.w[j] : 0.0)
+                              : df2_to_double(gc[j]) + (trans ? eps * p.w[j] : 0.0);
     const double thr = rr * nr * (1.0 + 1e-12);
     int pin = 0;
     float2 bnd = make_float2(0.f, 0.f);

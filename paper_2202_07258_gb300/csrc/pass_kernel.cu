@@ -96,6 +96,7 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
   __shared__ double s_scal[3];   // beta, t_{k+1} (no restart), eta_g: computed once per CTA
   __shared__ float2 s_beta2[2];  // beta and 1 + beta as double-float pairs
   __shared__ int s_err;
+  __shared__ double s_th[32];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_act = st->n_active;
@@ -141,6 +142,24 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
   // one coalesced read of the index range instead of a dependent load per column
   for (int q = threadIdx.x; q < nq; q += blockDim.x) sidx[q] = b.idx[p0 + q];
   __syncthreads();
+  if (gap_iter && p.wstar && blockIdx.x == 0) {
+    // fixed dual point theta = theta_fixed + eps_star t: ||theta - r_k||^2 for the gap
+    const float* rh = reinterpret_cast<const float*>(srh);
+    const float* rl = reinterpret_cast<const float*>(srl);
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < p.m; i += blockDim.x) {
+      const double d = p.theta[i] + p.eps_star * p.tvec[i] - ((double)rh[i] + (double)rl[i]);
+      acc += d * d;
+    }
+    acc = warp_sum_d(acc);
+    if ((threadIdx.x & 31) == 0) s_th[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t2 = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t2 += s_th[w];
+      st->theta_r2 = t2;
+    }
+  }
 
   const double tn = s_scal[1];
 
@@ -186,7 +205,7 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
     const int dw = warp - 1;
     const double eta_g = s_scal[2];
     const float2 bb = s_beta2[0], onepb = s_beta2[1];
-    const bool want_eps = gap_iter && p.dual_mode == kTranslation;
+    const bool want_eps = gap_iter && p.dual_mode == kTranslation && !p.wstar;
     const float2* __restrict__ xc = b.x[slot];
     float2* xn = b.x[slot ^ 1];
     const float2* __restrict__ gp = b.g[slot ^ 1];

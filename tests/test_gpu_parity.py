@@ -245,3 +245,28 @@ def test_screenable_single_instance_full_size(P):
     assert np.all(g[scr == 1] < 0)
     assert (scr > 0).sum() > 0.5 * p.n
     assert np.sum(g[scr == 1] >= -rad * np.linalg.norm(A[:, scr == 1], axis=0)) < 0.05 * (scr > 0).sum()
+
+
+@pytest.mark.parametrize("name", ["nnls_abs_300x700", "bvls_t2_200x500"])
+def test_fixed_dual_point_matches_oracle(P, name):
+    """The oracle-dual-point option: the same iterates as the oracle run with the same fixed
+    dual point, safe screening, and earlier fixing than with Theta(x_k)."""
+    p, t = CASES[name]()
+    A, y = _f64(p)
+    L = _L(A)
+    ref = O.solve(A, y, p.l, p.u, tol=1e-10, L=L)
+    xs = certified_optimum(A, y, p.l, p.u, ref.x)
+    th = y - A @ xs
+    N = 300
+    o = O.solve(A, y, p.l, p.u, tol=0.0, max_iter=N, L=L, dual_point=th)
+    x, scr, info, st = gpu_solve(P, p, tol=0.0, max_iter=N, lipschitz=L, dual_point=th)
+    scale = max(1.0, float(np.abs(o.x).max()))
+    assert float(np.abs(x - o.x).max()) <= 1e-9 * scale
+    g = A.T @ th
+    assert np.all(g[scr == 1] < 0) and np.all(xs[scr == 1] == p.l[scr == 1])
+    assert np.all(g[scr == 2] > 0) and np.all(xs[scr == 2] == p.u[scr == 2])
+    x2, scr2, info2, st2 = gpu_solve(P, p, tol=1e-8, lipschitz=L, dual_point=th)
+    x3, scr3, info3, st3 = gpu_solve(P, p, tol=1e-8, lipschitz=L)
+    assert info2["converged"] and info2["iters"] <= info3["iters"]
+    assert info2["sum_preserved"] <= info3["sum_preserved"]
+    assert O.primal_objective(A, y, x2) - O.primal_objective(A, y, xs) <= info2["gap"] * (1 + 1e-9) + 1e-12

@@ -326,3 +326,26 @@ def test_mutations_are_caught(name, monkeypatch):
         except (AssertionError, ValueError, RuntimeError, IndexError):
             caught += 1
     assert caught > 0, name
+
+
+def test_fixed_dual_point_screens_safely_and_earlier():
+    """Oracle-dual-point experiment (Section 5): with theta* itself as the dual point the
+    gap of every evaluation is P(x_k) - P* (up to the folding), so the sphere is as small as
+    Gap-safe screening allows; the solution and the screened set stay correct."""
+    p = W.nnls_abs_gaussian(120, 400, 0.05, 1.0, 2)
+    A, y = p.A.astype(np.float64), p.y.astype(np.float64)
+    ref = O.solve(A, y, p.l, p.u, tol=1e-10)
+    xs = O.polish(A, y, ref.x, p.l, p.u, tau=1e-7)
+    assert O.kkt_residual(A, y, xs, p.l, p.u) < 1e-10
+    th = y - A @ xs
+    a = O.solve(A, y, p.l, p.u, tol=1e-8, record=True)
+    b = O.solve(A, y, p.l, p.u, tol=1e-8, record=True, dual_point=th)
+    assert b.converged and b.iters <= a.iters
+    g = A.T @ th
+    low = b.screened == 1
+    assert np.all(xs[low] == 0.0) and np.all(g[low] < 0)
+    pa = [h[2] for h in a.history]
+    pb = [h[2] for h in b.history]
+    k = min(len(pa), len(pb))
+    assert all(pb[i] <= pa[i] for i in range(k)) and pb[k // 2] < pa[k // 2]
+    assert O.primal_objective(A, y, b.x) - O.primal_objective(A, y, xs) <= b.gap + 1e-12
