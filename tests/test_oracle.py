@@ -349,3 +349,28 @@ def test_fixed_dual_point_screens_safely_and_earlier():
     k = min(len(pa), len(pb))
     assert all(pb[i] <= pa[i] for i in range(k)) and pb[k // 2] < pa[k // 2]
     assert O.primal_objective(A, y, b.x) - O.primal_objective(A, y, xs) <= b.gap + 1e-12
+
+
+def test_chambolle_pock_matches_brute_force_and_fista():
+    """The primal-dual solver (Section 5's PD) reaches the brute-force optimum on tiny BVLS
+    problems, the FISTA solver's optimum on a Table-2 instance, and its dual iterate -z
+    converges to theta*; screening does not change its iterates."""
+    for seed in range(6):
+        p = W.random_tiny(9, 6, "bvls", seed)
+        A, y = p.A.astype(np.float64), p.y.astype(np.float64)
+        xb, Pb = O.brute_force(A, y, p.l, p.u)
+        r = O.solve_cp(A, y, p.l, p.u, tol=1e-12, screen_every=5)
+        assert r.converged and abs(O.primal_objective(A, y, r.x) - Pb) <= 1e-10 * max(1.0, Pb)
+    p = W.bvls_table2(100, 250, 3)
+    A, y = p.A.astype(np.float64), p.y.astype(np.float64)
+    a = O.solve(A, y, p.l, p.u, tol=1e-10)
+    b = O.solve_cp(A, y, p.l, p.u, tol=1e-10)
+    c = O.solve_cp(A, y, p.l, p.u, tol=1e-10, screening=False)
+    xs = O.polish(A, y, a.x, p.l, p.u, tau=1e-7)
+    assert O.kkt_residual(A, y, xs, p.l, p.u) < 1e-10
+    assert np.abs(b.x - xs).max() < 1e-6 and np.abs(b.x - c.x).max() < 1e-12 and b.iters == c.iters
+    g = A.T @ (y - A @ xs)
+    assert np.all(xs[b.screened == 1] == 0.0) and np.all(g[b.screened == 1] < 0)
+    assert np.all(xs[b.screened == 2] == 1.0) and np.all(g[b.screened == 2] > 0)
+    with pytest.raises(ValueError):
+        O.solve_cp(A, y, p.l, np.full(A.shape[1], np.inf))
