@@ -74,6 +74,15 @@ enum {
                            rounding margins of the test are about 2^24 times wider */
 };
 
+/* Primal solver of bvls_solve. */
+enum {
+  BVLS_ALG_FISTA = 0,          /* accelerated projected gradient with adaptive restart (default) */
+  BVLS_ALG_CHAMBOLLE_POCK = 1  /* the primal-dual iteration of Section 5's BVLS experiments
+                                  (sigma = tau = 0.99 / sqrt(L)); screening uses its own dual
+                                  iterate theta = -z.  BVLS only (every u_j finite), single-pass
+                                  form, no dual_point; else BVLS_ENOTSUP */
+};
+
 /* Dual point used by the screening step (Section 4). */
 enum {
   BVLS_DUAL_SCALING = 0,     /* every u_j finite: theta = y - A x (Eq. (BVLR_dual_up)) */
@@ -102,6 +111,7 @@ typedef struct {
                          u_j = +inf; any dual-feasible point keeps the test safe.  Needs the
                          single-pass form and a dual mode other than BVLS_DUAL_ZERO
                          (else BVLS_ENOTSUP / BVLS_EINVAL).  Ignored by the other entry points. */
+  int algorithm;      /* BVLS_ALG_*; bvls_solve only (the other entry points use FISTA) */
 } bvls_opts;
 
 typedef struct {

@@ -49,7 +49,7 @@ def _host_f64(v, n):
 
 
 def make_opts(tol=1e-6, screen_every=10, max_iter=100000, screening=True, precision="fp32x2",
-              restart=True, lipschitz=0.0, profile=False, single_pass=True) -> bvls_opts:
+              restart=True, lipschitz=0.0, profile=False, single_pass=True, algorithm="fista") -> bvls_opts:
     o = bvls_default_opts()
     o.tol = float(tol)
     o.screen_every = int(screen_every)
@@ -60,6 +60,8 @@ def make_opts(tol=1e-6, screen_every=10, max_iter=100000, screening=True, precis
     o.lipschitz = float(lipschitz)
     o.profile = 1 if profile else 0
     o.single_pass = 1 if single_pass else 0
+    o.algorithm = {"fista": _capi.BVLS_ALG_FISTA, "cp": _capi.BVLS_ALG_CHAMBOLLE_POCK,
+                   "chambolle_pock": _capi.BVLS_ALG_CHAMBOLLE_POCK}[algorithm]
     return o
 
 

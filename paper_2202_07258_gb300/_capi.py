@@ -16,6 +16,7 @@ BVLS_OK, BVLS_EINVAL, BVLS_ENOMEM, BVLS_ECUDA, BVLS_EMAXITER, BVLS_ENONFINITE, B
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EMAXITER", 5: "ENONFINITE", 6: "ENOTSUP",
                 7: "ETIMEOUT"}
 BVLS_PREC_FP32X2, BVLS_PREC_FP32 = 0, 1
+BVLS_ALG_FISTA, BVLS_ALG_CHAMBOLLE_POCK = 0, 1
 BVLS_DUAL_SCALING, BVLS_DUAL_TRANSLATION, BVLS_DUAL_ZERO = 0, 1, 2
 DUAL_NAMES = {0: "scaling", 1: "translation", 2: "zero"}
 
@@ -36,6 +37,7 @@ class bvls_opts(ctypes.Structure):
         ("profile", ctypes.c_int),
         ("single_pass", ctypes.c_int),
         ("dual_point", ctypes.c_void_p),
+        ("algorithm", ctypes.c_int),
     ]
 
 

@@ -40,12 +40,13 @@ constexpr double kU = 5.9604644775390625e-08;   // 2^-24, unit roundoff of float
 constexpr double kU64 = 1.1102230246251565e-16; // 2^-53
 
 struct GraphKey {
-  int K, screening, precision, restart, max_iter, single_pass;
+  int K, screening, precision, restart, max_iter, single_pass, algorithm;
   double tol, invL, eps_star, eta_star;
   bool fixed_dual;
   bool operator==(const GraphKey& o) const {
     return K == o.K && screening == o.screening && precision == o.precision &&
            restart == o.restart && max_iter == o.max_iter && single_pass == o.single_pass &&
+           algorithm == o.algorithm &&
            tol == o.tol && invL == o.invL && eps_star == o.eps_star && eta_star == o.eta_star &&
            fixed_dual == o.fixed_dual;
   }
@@ -62,6 +63,7 @@ struct bvls_handle {
   float2 *l2 = nullptr, *u2 = nullptr;
   uint8_t* jinf = nullptr;
   double t_norm = 0.0, gamma_w = 0.0, L = 0.0;
+  double xbox = -1.0;  // sum_j max(|l_j|, |u_j|) ||a_j|| (primal-dual error bound), once computed
   int dual_mode = kScaling;
   Buffers b{};
   float* y_dev = nullptr;
@@ -180,6 +182,16 @@ Params make_params(const bvls_handle* h, const bvls_opts& o, int max_iter) {
   p.dual_mode = h->dual_mode;
   p.screening = o.screening;
   p.restart = o.restart;
+  p.alg = o.algorithm == BVLS_ALG_CHAMBOLLE_POCK ? kChambollePock : kFista;
+  if (p.alg == kChambollePock) {
+    const double st = 0.99 / std::sqrt(L);
+    p.tau2 = df2_from_double(st);
+    p.sigma2 = df2_from_double(st);
+    p.inv1ps2 = df2_from_double(1.0 / (1.0 + st));
+    // the recurrence's error: each step adds the rounding of A xbar (|xbar_j| <= 3 max(|l_j|,|u_j|))
+    // and halves what came before, so it stays below one step's bound
+    p.E_cp = (p.Cf + 2.0 * p.Csub) * 3.0 * std::max(0.0, h->xbox);
+  }
   p.fwd_chunks = h->fwd_chunks;
   p.fwd_tiles = h->fwd_tiles;
   return p;
@@ -231,11 +243,26 @@ int chunk_length(int K) {
 }
 
 bvls_status validate_opts(const bvls_opts& o) {
+  if (o.algorithm != BVLS_ALG_FISTA && o.algorithm != BVLS_ALG_CHAMBOLLE_POCK)
+    return set_err(BVLS_EINVAL, "algorithm must be BVLS_ALG_FISTA or BVLS_ALG_CHAMBOLLE_POCK");
   if (!(o.tol >= 0.0) || o.screen_every < 1 || o.max_iter < 1 ||
       (o.precision != BVLS_PREC_FP32X2 && o.precision != BVLS_PREC_FP32) ||
       !(o.lipschitz >= 0.0) || !std::isfinite(o.lipschitz))
     return set_err(BVLS_EINVAL, "invalid options (tol >= 0, screen_every >= 1, max_iter >= 1, "
                                 "precision 0/1, lipschitz >= 0 finite)");
+  return BVLS_OK;
+}
+
+// sum_j max(|l_j|, |u_j|) ||a_j|| for the primal-dual error bound (host, once per handle).
+bvls_status compute_xbox(bvls_handle* h) {
+  std::vector<double> l(h->n), u(h->n), nr(h->n);
+  CK(cudaMemcpyAsync(l.data(), h->l, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->s));
+  CK(cudaMemcpyAsync(u.data(), h->u, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->s));
+  CK(cudaMemcpyAsync(nr.data(), h->nrm, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  double s = 0.0;
+  for (int j = 0; j < h->n; ++j) s += std::max(std::fabs(l[j]), std::fabs(u[j])) * nr[j];
+  h->xbox = s * (1.0 + 1e-12);
   return BVLS_OK;
 }
 
@@ -302,6 +329,7 @@ void bvls_default_opts(bvls_opts* o) {
   o->profile = 0;
   o->single_pass = 1;
   o->dual_point = nullptr;
+  o->algorithm = BVLS_ALG_FISTA;
 }
 
 const char* bvls_last_error(void) { return g_err.c_str(); }
@@ -486,6 +514,10 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
   TRY(dalloc(h, &b.part, (size_t)h->fwd_chunks * h->lda));
   TRY(dalloc(h, &b.tileP, (h->lda + 31) / 32));   // >= fwd_tiles
   TRY(dalloc(h, &b.tileR, (h->m4 + 31) / 32));    // the residual kernel's grid
+  TRY(dalloc(h, &b.tileD, (h->m4 + 31) / 32));
+  TRY(dalloc(h, &b.tileZ, (h->m4 + 31) / 32));
+  TRY(dalloc(h, &b.crh, h->m4));
+  TRY(dalloc(h, &b.crl, h->m4));
   TRY(dalloc(h, &b.tile_cnt, h->fwd_tiles));
   TRY(dalloc(h, &b.blk, 4 * (size_t)max_blocks));
   TRY(dalloc(h, &b.st, 1));
@@ -555,7 +587,12 @@ bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const b
   Params p = make_params(h, o, max_iter);
   if (o.dual_point) {
     if (!o.single_pass) return set_err(BVLS_ENOTSUP, "dual_point needs the single-pass form (single_pass = 1)");
+    if (o.algorithm != BVLS_ALG_FISTA) return set_err(BVLS_ENOTSUP, "dual_point is a FISTA option");
     TRY(prepare_fixed_dual(h, o.dual_point, &p));
+  }
+  if (o.algorithm == BVLS_ALG_CHAMBOLLE_POCK && h->xbox < 0.0) {
+    TRY(compute_xbox(h));
+    p = make_params(h, o, max_iter);
   }
 
   if (h->own_stream) {
@@ -568,9 +605,12 @@ bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const b
     CK(cudaMemcpyAsync(h->x0_dev, x0, sizeof(double) * h->n, cudaMemcpyDefault, h->s));
     h->b.x0_in = h->x0_dev;
   }
-  CK(launch_init(p, h->b, h->s));
   const bool fused = h->pass_stages > 0 && o.single_pass;
+  if (o.algorithm == BVLS_ALG_CHAMBOLLE_POCK && (!fused || h->dual_mode != kScaling))
+    return set_err(BVLS_ENOTSUP, "the primal-dual solver covers BVLS (every u_j finite) in the single-pass form");
+  CK(launch_init(p, h->b, h->s));
   if (fused) CK(launch_fwd(p, h->b, 0, o.precision, false, h->s));  // r_0, P_0
+  if (p.alg == kChambollePock) CK(launch_cp_init(p, h->b, h->s));  // z_1 = -r_0
 
   const long long max_chunks = (max_iter + chunk - 1) / chunk + 1;
   const bool scr = o.screening && h->dual_mode != kZero;
@@ -624,7 +664,7 @@ bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const b
     cudaGraphExecDestroy(gx);
     if (pst != BVLS_OK) return pst;
   } else {
-    GraphKey key{K, o.screening, o.precision, o.restart, max_iter, o.single_pass, o.tol, p.invL,
+    GraphKey key{K, o.screening, o.precision, o.restart, max_iter, o.single_pass, o.algorithm, o.tol, p.invL,
                  p.eps_star, p.eta_star, p.wstar != nullptr};
     if (!h->have_graph || !(h->key == key) || h->chunk_len != chunk) {
       if (h->exec) {

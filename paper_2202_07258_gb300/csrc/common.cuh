@@ -31,6 +31,7 @@ constexpr int kPassMaxStages = 32;
 
 enum DualMode { kScaling = 0, kTranslation = 1, kZero = 2 };
 enum Precision { kX2 = 0, kF32 = 1 };
+enum Algorithm { kFista = 0, kChambollePock = 1 };
 
 // Scalars of one solve, in device memory.  Written by the last block of a kernel (the
 // others signal completion through the counters) and read by the next kernel.
@@ -92,6 +93,12 @@ struct Params {
   const double* tvec;      // the translation direction t (m), used with eps_star
   double eps_star;         // translation step that puts theta_fixed + eps_star t in F_D
   double eta_star;         // rounding bound of wstar_j + eps_star w_j per unit ||a_j||
+  // primal-dual (Chambolle-Pock) iteration: steps and the bound of its residual recurrence
+  int alg;                 // kFista or kChambollePock
+  float2 tau2;             // primal step tau
+  float2 sigma2;           // dual step sigma
+  float2 inv1ps2;          // 1 / (1 + sigma)
+  double E_cp;             // |r (stored) - r (exact)| from the recurrence r_{k+1} = (r_k + y' - A xbar) / 2
   int fwd_chunks;          // grid.y of the A_S x_S kernel
   int fwd_tiles;           // grid.x of the A_S x_S kernel
 };
@@ -236,6 +243,10 @@ struct Buffers {
   float2* part;
   double* tileP;
   double* tileR;          // fused pass: block partials of P from the residual kernel
+  double* tileD;          // primal-dual: block partials of ||z + r||^2 (theta = -z)
+  double* tileZ;          // primal-dual: block partials of ||z||^2
+  float* crh;             // primal-dual: the residual r(x_k) = y' - A_S x_S (hi, lo), kept by
+  float* crl;             // the recurrence while rh / rl hold the dual iterate z
   unsigned int* tile_cnt;
   double* blk;            // per-block partials of the epilogue kernels (4 doubles each)
   float2* qpart;          // fused pass: per-CTA double-float partials of A_S x_S (grid x m4)
@@ -264,6 +275,9 @@ cudaError_t launch_pass(const Params& p, const Buffers& b, int slot, int precisi
                         int grid, int nstages, int cps, int qwarps, cudaStream_t s);
 cudaError_t launch_resid(const Params& p, const Buffers& b, int slot, int nparts, cudaStream_t s);
 cudaError_t launch_export(const Params& p, const Buffers& b, int slot, cudaStream_t s);
+// primal-dual start: r_0 (in rh / rl from the forward kernel) moves to crh / crl and
+// z_1 = A x_0 - y' = -r_0 takes its place
+cudaError_t launch_cp_init(const Params& p, const Buffers& b, cudaStream_t s);
 cudaError_t tr_configure(int m4, int* blocks_per_sm);
 
 // Record the text returned by bvls_last_error() on this thread (capi.cu).

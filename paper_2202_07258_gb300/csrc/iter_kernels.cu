@@ -527,8 +527,12 @@ __global__ void __launch_bounds__(kRedThreads) k_gap(Params p, Buffers b, int sl
   const int n_act = st->n_active;
   const bool trans = p.dual_mode == kTranslation;
   const double eps = trans ? st->eps : 0.0;
-  const float2* __restrict__ xc = b.x[slot];
+  // FISTA: the pair (x_k, Theta(x_k)); primal-dual: (x_{k+1}, theta = -z_{k+1}), whose
+  // correlations a_j^T z_{k+1} the pass stored with the opposite sign
+  const bool cp = p.alg == kChambollePock;
+  const float2* __restrict__ xc = b.x[cp ? slot ^ 1 : slot];
   const float2* __restrict__ gc = b.g[slot];
+  const double gsign = cp ? -1.0 : 1.0;
   double v[3] = {0.0, 0.0, 0.0};  // sum h_j, sum c_j ||a_j||, sum |x_j| ||a_j||
   const int stride = gridDim.x * blockDim.x;
   for (int pp = blockIdx.x * blockDim.x + threadIdx.x; pp < n_act; pp += stride) {
@@ -538,7 +542,7 @@ __global__ void __launch_bounds__(kRedThreads) k_gap(Params p, Buffers b, int sl
     v[2] += fabs(x) * nr;
     if (p.dual_mode != kZero) {
       const double gt = p.wstar ? p.wstar[j] + (trans ? p.eps_star * p.w[j] : 0.0)
-                                : df2_to_double(gc[j]) + (trans ? eps * p.w[j] : 0.0);
+                                : gsign * df2_to_double(gc[j]) + (trans ? eps * p.w[j] : 0.0);
       const double lj = p.l[j];
       if (p.jinf[j]) {
         v[0] += (x - lj) * fmax(-gt, 0.0);
@@ -580,12 +584,27 @@ __global__ void __launch_bounds__(kRedThreads) k_gap(Params p, Buffers b, int sl
     a = warp_sum_d(a);
     c = warp_sum_d(c);
     x = warp_sum_d(x);
+    double P_cp = 0.0, dist2 = 0.0, z2 = 0.0;
+    if (cp) {  // the residual kernel's block partials of 1/2||r||^2, ||z + r||^2, ||z||^2
+      const int nres = (p.m4 + 31) / 32;
+      P_cp = warp_load_sum(b.tileR, nres);
+      dist2 = warp_load_sum(b.tileD, nres);
+      z2 = warp_load_sum(b.tileZ, nres);
+    }
     if (threadIdx.x == 0) {
-      const double rnorm = sqrt(2.0 * st->P[slot]) * (1.0 + 1e-6);
-      const double eta = p.wstar ? p.eta_star : p.Cg * rnorm + (trans ? eps * p.gamma_w * p.t_norm : 0.0);
-      const double E_r = st->E_fold + p.Cf * x + p.Csub * (rnorm + st->y_norm + st->S_fold + x);
+      const double rnorm = sqrt(2.0 * (cp ? P_cp : st->P[slot])) * (1.0 + 1e-6);
+      // rounding of a_j^T theta per unit ||a_j||: the correlation is taken with r (FISTA) or z
+      const double eta = p.wstar ? p.eta_star
+                                 : p.Cg * (cp ? sqrt(z2) * (1.0 + 1e-6) : rnorm) + (trans ? eps * p.gamma_w * p.t_norm : 0.0);
+      const double E_r = cp ? st->E_fold + p.E_cp + p.Csub * (st->y_norm + st->S_fold)
+                            : st->E_fold + p.Cf * x + p.Csub * (rnorm + st->y_norm + st->S_fold + x);
       double gap;
-      if (p.wstar) {
+      if (cp) {
+        // theta = -z: 1/2 ||theta - r (exact)||^2 <= 1/2 (||z + r (stored)|| + E_r)^2
+        const double d = sqrt(dist2) * (1.0 + 1e-12) + E_r;
+        gap = a + eta * c + 0.5 * d * d;
+        st->P[slot ^ 1] = P_cp;
+      } else if (p.wstar) {
         // fixed dual point: 1/2 ||theta - r||^2 with the stored residual's own error
         const double d = sqrt(st->theta_r2) * (1.0 + 1e-12) + E_r;
         gap = a + eta * c + 0.5 * d * d;
@@ -603,7 +622,7 @@ __global__ void __launch_bounds__(kRedThreads) k_gap(Params p, Buffers b, int sl
       const bool conv = gap < p.tol;
       if (conv || st->k >= p.max_iter) {
         st->converged = conv ? 1 : 0;
-        st->out_slot = slot;
+        st->out_slot = cp ? slot ^ 1 : slot;
         if (finalize) st->done = 1;
         else st->stop = 1;
       }
@@ -638,7 +657,8 @@ __global__ void __launch_bounds__(kRedThreads) k_test(Params p, Buffers b, int s
     const double nr = p.nrm[j];
     if (!(nr > 0.0)) continue;
     const double gt = p.wstar ? p.wstar[j] + (trans ? p.eps_star * p.w[j] : 0.0)
-                              : df2_to_double(gc[j]) + (trans ? eps * p.w[j] : 0.0);
+                              : (p.alg == kChambollePock ? -1.0 : 1.0) * df2_to_double(gc[j]) +
+                                    (trans ? eps * p.w[j] : 0.0);
     const double thr = rr * nr * (1.0 + 1e-12);
     int pin = 0;
     float2 bnd = make_float2(0.f, 0.f);

@@ -275,9 +275,22 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
       if (lane < ncol) {
         const int c = c0 + lane;
         mbar_arrive(&empty[s]);  // this column's dot is done with the stage
-        // FISTA step in double-float arithmetic (no float64 on this path)
         const float2 g2 = lane == 0 ? df2_norm(sa[0], PREC == kX2 ? ca[0] : 0.0f)
                                     : df2_norm(sb[0], PREC == kX2 ? cb[0] : 0.0f);
+        if (p.alg == kChambollePock) {
+          // primal step of the primal-dual iteration: x_{k+1} = clip(x_k - tau a_j^T z),
+          // and xbar = 2 x_{k+1} - x_k feeds the forward product
+          float2 xnew = df2_sub(xk, df2_mul(g2, p.tau2));
+          if (df2_lt(xnew, lj)) xnew = lj;
+          if (df2_lt(uj, xnew)) xnew = uj;
+          const float2 xbar = df2_sub(df2_add(xnew, xnew), xk);
+          sx[(size_t)s * cps + c] = PREC == kX2 ? xbar : make_float2(xbar.x, 0.0f);
+          mbar_arrive(&xready[s]);
+          xn[j] = xnew;
+          gc[j] = g2;
+          continue;
+        }
+        // FISTA step in double-float arithmetic (no float64 on this path)
         const float2 gv = df2_sub(df2_mul(onepb, g2), df2_mul(bb, gpv));   // a_j^T (y' - A v_k)
         const float2 v = df2_add(xk, df2_mul(bb, df2_sub(xk, xp)));
         float2 xnew = df2_add(v, df2_mul(gv, p.invL2));
@@ -426,7 +439,38 @@ __global__ void __launch_bounds__(256) k_resid(Params p, Buffers b, int slot, in
   __shared__ float2 sp[32];
   sh[warp][lane] = make_float2(s, c);
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 0 && p.alg == kChambollePock) {
+    // primal-dual: z_{k+2} = (z_{k+1} + sigma (A xbar - y')) / (1 + sigma) and
+    // r(x_{k+1}) = (r(x_k) + y' - A xbar) / 2; partials of 1/2 ||r||^2, ||z_{k+1} + r||^2, ||z_{k+1}||^2
+    for (int w = 1; w < 8; ++w) df_add(s, c, sh[w][lane].x, sh[w][lane].y);
+    double pv = 0.0, dv = 0.0, zv = 0.0;
+    if (row < p.m) {
+      const float2 q = df2_norm(s, c);
+      const float2 yv = make_float2(b.yh[row], b.yl[row]);
+      const float2 z = make_float2(b.rh[row], b.rl[row]);
+      const float2 r = make_float2(b.crh[row], b.crl[row]);
+      const float2 zn = df2_mul(df2_add(z, df2_mul(df2_sub(q, yv), p.sigma2)), p.inv1ps2);
+      const float2 rn = df2_mul(df2_add(r, df2_sub(yv, q)), make_float2(0.5f, 0.f));
+      b.rh[row] = zn.x;
+      b.rl[row] = zn.y;
+      b.crh[row] = rn.x;
+      b.crl[row] = rn.y;
+      const double rd = df2_to_double(rn), zd = df2_to_double(z);
+      pv = 0.5 * rd * rd;
+      dv = (zd + rd) * (zd + rd);
+      zv = zd * zd;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      pv += __shfl_xor_sync(0xffffffffu, pv, o);
+      dv += __shfl_xor_sync(0xffffffffu, dv, o);
+      zv += __shfl_xor_sync(0xffffffffu, zv, o);
+    }
+    if (lane == 0) {
+      b.tileR[blockIdx.x] = pv;
+      b.tileD[blockIdx.x] = dv;
+      b.tileZ[blockIdx.x] = zv;
+    }
+  } else if (warp == 0) {
     for (int w = 1; w < 8; ++w) df_add(s, c, sh[w][lane].x, sh[w][lane].y);
     float ps = 0.f, pc = 0.f;
     if (row < p.m) {
@@ -448,6 +492,21 @@ __global__ void __launch_bounds__(256) k_resid(Params p, Buffers b, int slot, in
     }
     if (lane == 0) b.tileR[blockIdx.x] = df_to_double(ps, pc);   // summed by the next pass
   }
+}
+
+__global__ void k_cp_init(Params p, Buffers b) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.m4; i += gridDim.x * blockDim.x) {
+    const float rh = b.rh[i], rl = b.rl[i];
+    b.crh[i] = rh;
+    b.crl[i] = rl;
+    b.rh[i] = -rh;
+    b.rl[i] = -rl;
+  }
+}
+
+cudaError_t launch_cp_init(const Params& p, const Buffers& b, cudaStream_t s) {
+  k_cp_init<<<(p.m4 + 255) / 256, 256, 0, s>>>(p, b);
+  return cudaGetLastError();
 }
 
 // x_out (float64) from the double-float iterate of the given slot.

@@ -270,3 +270,35 @@ def test_fixed_dual_point_matches_oracle(P, name):
     assert info2["converged"] and info2["iters"] <= info3["iters"]
     assert info2["sum_preserved"] <= info3["sum_preserved"]
     assert O.primal_objective(A, y, x2) - O.primal_objective(A, y, xs) <= info2["gap"] * (1 + 1e-9) + 1e-12
+
+
+@pytest.mark.parametrize("name", ["bvls_t2_200x500", "bvls_dir_224x512"])
+def test_chambolle_pock_matches_oracle(P, name):
+    """Primal-dual solver: the same iterates as the oracle's Chambolle-Pock over 300
+    iterations, then the certified optimum with safe screening on its own dual iterate."""
+    p, t = CASES[name]()
+    A, y = _f64(p)
+    L = _L(A)
+    N = 300
+    o = O.solve_cp(A, y, p.l, p.u, tol=0.0, max_iter=N, L=L)
+    x, scr, info, st = gpu_solve(P, p, tol=0.0, max_iter=N, lipschitz=L, algorithm="cp")
+    assert info["iters"] == N == o.iters
+    assert float(np.abs(x - o.x).max()) <= 1e-9 * max(1.0, float(np.abs(o.x).max()))
+    ref = O.solve_cp(A, y, p.l, p.u, tol=1e-8, L=L)
+    x, scr, info, st = gpu_solve(P, p, tol=1e-8, lipschitz=L, algorithm="cp")
+    assert st == P.BVLS_OK and info["gap"] < 1e-8 and abs(info["iters"] - ref.iters) <= 20
+    xs = certified_optimum(A, y, p.l, p.u, ref.x)
+    g = A.T @ (y - A @ xs)
+    assert np.all(xs[scr == 1] == p.l[scr == 1]) and np.all(g[scr == 1] < 0)
+    assert np.all(xs[scr == 2] == p.u[scr == 2]) and np.all(g[scr == 2] > 0)
+    assert (scr > 0).sum() > 0
+    Pg, Ps = O.primal_objective(A, y, x), O.primal_objective(A, y, xs)
+    assert Ps - 1e-12 <= Pg <= Ps + info["gap"] * (1 + 1e-9) + 1e-12
+    u = gpu_solve(P, p, tol=1e-8, lipschitz=L, algorithm="cp", screening=False)
+    assert u[2]["iters"] == info["iters"] and float(np.abs(u[0] - x).max()) < 1e-7
+
+
+def test_chambolle_pock_rejects_nnls(P):
+    p = W.nnls_abs_gaussian(50, 80, 0.1, 1.0, 1)
+    x, scr, info, st = gpu_solve(P, p, tol=1e-6, algorithm="cp", check=False)
+    assert st == P.BVLS_ENOTSUP
