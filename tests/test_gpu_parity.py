@@ -294,8 +294,12 @@ def test_chambolle_pock_matches_oracle(P, name):
     assert (scr > 0).sum() > 0
     Pg, Ps = O.primal_objective(A, y, x), O.primal_objective(A, y, xs)
     assert Ps - 1e-12 <= Pg <= Ps + info["gap"] * (1 + 1e-9) + 1e-12
+    # Without screening the iterates are the same, but the gap keeps the terms of the
+    # coordinates the screened run has fixed; with theta = -z those can stay positive, so the
+    # screened run (which certifies the reduced problem, same optimum) may stop earlier.
     u = gpu_solve(P, p, tol=1e-8, lipschitz=L, algorithm="cp", screening=False)
-    assert u[2]["iters"] == info["iters"] and float(np.abs(u[0] - x).max()) < 1e-7
+    assert u[2]["iters"] >= info["iters"] and u[2]["gap"] < 1e-8
+    assert abs(O.primal_objective(A, y, u[0]) - Pg) <= info["gap"] + u[2]["gap"]
 
 
 def test_chambolle_pock_rejects_nnls(P):
