@@ -275,6 +275,49 @@ BVLS_API bvls_status bvls_backward(bvls_handle* h, int B, const double* X, const
                                    const double* dLdX, const bvls_backward_opts* opts, double* dLdY,
                                    double* dLdA, int* status_out, bvls_backward_info* info);
 
+/* One problem of a ragged batch (bvls_solve_ragged). */
+typedef struct {
+  const float* A;       /* any; m x n column-major float32, leading dimension lda >= m */
+  int m, n, lda;
+  const float* y;       /* any; m float32 */
+  const double* l;      /* host; n doubles or NULL (0) */
+  const double* u;      /* host; n doubles or NULL (+inf); u_j may be +INFINITY */
+} bvls_problem;
+
+typedef struct {
+  int iters_max;        /* largest per-instance iteration count */
+  int n_converged;      /* instances with gap < tol */
+  int n_translation;    /* instances screened with the dual translation (t = -1) */
+  int n_zero;           /* instances with u_j = +inf and no interior t = -1: theta = 0 */
+  int chunks;           /* chunks of iterations the device loop ran */
+  int tiles_max;        /* work-list capacity (sum over instances of ceil(n / 16)) */
+  double setup_ms;      /* copies, column norms, dual modes and 40 power iterations */
+  double solve_ms;      /* the solve graph (host wall clock around one graph launch) */
+} bvls_ragged_info;
+
+/*
+ * Solve B independent problems of uneven sizes, each with its own A_k, y_k and box, in one
+ * set of launches per iteration (Algorithm 1 per instance, lockstep iterations, retirement of
+ * finished instances): the mixed NNLS / BVLS batch.  Per instance: the step constant is
+ * 1.05 x a 40-step power-iteration estimate of ||A_k||_2^2; the dual point is the scaling
+ * (every u_j finite), the translation with t = -1 when it is interior (Proposition 2), else
+ * theta = 0.  Products are float32 data with double-float accumulation.
+ *   probs         host; B problem descriptors (1 <= m_k <= 1024, n_k >= 1).
+ *   opts          host or NULL: tol, screen_every, max_iter, screening, restart are used.
+ *   stream        a cudaStream_t (0 allowed); the call returns when its outputs are written.
+ *   x_out         host; B pointers (any memory) to n_k doubles each.
+ *   screened_out  host; B pointers (any memory) to n_k bytes, or NULL.
+ *   gaps_out, iters_out, status_out: host; B entries each, or NULL.
+ *   info          host or NULL.
+ * The call allocates its workspace (the A_k copies padded to a multiple of 4 rows, about 60
+ * bytes per column and 40 bytes per row) and frees it before returning.
+ * Returns BVLS_OK when every instance converged, BVLS_EMAXITER otherwise (outputs valid),
+ * or an error (EINVAL, ENOTSUP, ENONFINITE, ENOMEM, ECUDA; outputs untouched).
+ */
+BVLS_API bvls_status bvls_solve_ragged(int B, const bvls_problem* probs, const bvls_opts* opts, void* stream,
+                                       double* const* x_out, uint8_t* const* screened_out, double* gaps_out,
+                                       int* iters_out, int* status_out, bvls_ragged_info* info);
+
 /*
  * One-call solve that allocates nothing.  The paper has no counterpart: this is a service
  * for callers that cannot allocate device memory -- code that runs inside a memory pool or

@@ -25,7 +25,8 @@ from ._capi import (BVLS_DUAL_SCALING, BVLS_DUAL_TRANSLATION, BVLS_DUAL_ZERO, BV
 
 __all__ = ["Solver", "BVLSError", "bvls_setup", "bvls_solve", "bvls_destroy", "bvls_default_opts",
            "bvls_last_error", "bvls_opts", "bvls_info", "bvls_batch_info", "bvls_solve_batched", "make_opts",
-           "bvls_backward", "bvls_backward_opts", "bvls_backward_info", "solve_batched_autograd"]
+           "bvls_backward", "bvls_backward_opts", "bvls_backward_info", "solve_batched_autograd",
+           "solve_ragged"]
 
 
 class BVLSError(RuntimeError):
@@ -271,4 +272,48 @@ def solve_batched_autograd(A, Y, l=None, u=None, **opts_kw):
     if _FN is None:
         _FN = _autograd_function()
     return _FN.apply(A, Y, l, u, opts_kw)
+
+
+def solve_ragged(problems, *, opts: bvls_opts | None = None, stream=None, check: bool = True, **kw):
+    """bvls_solve_ragged on a list of (A, y, l, u) with A (m_k x n_k) and y (m_k) as numpy
+    arrays or CUDA tensors and l, u as None, scalars or length-n_k arrays (host).
+
+    Returns (xs, screened, gaps, iters, statuses, info_dict, status): per-instance numpy
+    arrays x (float64) and screened flags (uint8), and per-instance gaps, iteration counts
+    and statuses.
+    """
+    if opts is None:
+        opts = make_opts(**kw)
+    keep, descs, xs, ss = [], [], [], []
+    for A, y, l, u in problems:
+        if _is_torch(A):
+            import torch
+            At = A.detach().to(dtype=torch.float32).t().contiguous()   # column-major
+            yt = y.detach().to(device=A.device, dtype=torch.float32).contiguous()
+            a_ptr, y_ptr = At.data_ptr(), yt.data_ptr()
+            m, n = int(A.shape[0]), int(A.shape[1])
+        else:
+            At = np.asfortranarray(np.asarray(A, dtype=np.float32))
+            yt = np.ascontiguousarray(np.asarray(y, dtype=np.float32).reshape(-1))
+            a_ptr, y_ptr = At.ctypes.data, yt.ctypes.data
+            m, n = At.shape
+        lh, uh = _host_f64(l, n), _host_f64(u, n)
+        keep += [At, yt, lh, uh]
+        x = np.empty(n, dtype=np.float64)
+        sc = np.empty(n, dtype=np.uint8)
+        xs.append(x)
+        ss.append(sc)
+        descs.append(_capi.bvls_problem(a_ptr, m, n, m, y_ptr, None if lh is None else lh.ctypes.data,
+                                        None if uh is None else uh.ctypes.data))
+    B = len(descs)
+    gaps = np.empty(B, dtype=np.float64)
+    its = np.empty(B, dtype=np.int32)
+    sts = np.empty(B, dtype=np.int32)
+    st, info = _capi.bvls_solve_ragged(descs, opts, stream, [x.ctypes.data for x in xs],
+                                       [s.ctypes.data for s in ss], gaps.ctypes.data, its.ctypes.data,
+                                       sts.ctypes.data)
+    del keep
+    if check and st not in (BVLS_OK, BVLS_EMAXITER):
+        raise BVLSError(st, bvls_last_error())
+    return xs, ss, gaps, its, sts, info.as_dict(), st
 

@@ -22,7 +22,8 @@ DUAL_NAMES = {0: "scaling", 1: "translation", 2: "zero"}
 
 # Every symbol the header declares; tests check that the library exports all of them.
 EXPORTED = ("bvls_default_opts", "bvls_setup", "bvls_solve", "bvls_destroy", "bvls_last_error",
-            "bvls_solve_static", "bvls_solve_batched", "bvls_backward_default_opts", "bvls_backward")
+            "bvls_solve_static", "bvls_solve_batched", "bvls_backward_default_opts", "bvls_backward",
+            "bvls_solve_ragged")
 
 
 class bvls_opts(ctypes.Structure):
@@ -108,6 +109,34 @@ class bvls_backward_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class bvls_problem(ctypes.Structure):
+    _fields_ = [
+        ("A", ctypes.c_void_p),
+        ("m", ctypes.c_int),
+        ("n", ctypes.c_int),
+        ("lda", ctypes.c_int),
+        ("y", ctypes.c_void_p),
+        ("l", ctypes.c_void_p),
+        ("u", ctypes.c_void_p),
+    ]
+
+
+class bvls_ragged_info(ctypes.Structure):
+    _fields_ = [
+        ("iters_max", ctypes.c_int),
+        ("n_converged", ctypes.c_int),
+        ("n_translation", ctypes.c_int),
+        ("n_zero", ctypes.c_int),
+        ("chunks", ctypes.c_int),
+        ("tiles_max", ctypes.c_int),
+        ("setup_ms", ctypes.c_double),
+        ("solve_ms", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -142,6 +171,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.bvls_backward.argtypes = [vp, ci, vp, vp, ci, vp, ctypes.POINTER(bvls_backward_opts), vp, vp, vp,
                                   ctypes.POINTER(bvls_backward_info)]
     lib.bvls_backward.restype = ci
+    lib.bvls_solve_ragged.argtypes = [ci, ctypes.POINTER(bvls_problem), ctypes.POINTER(bvls_opts), vp,
+                                      ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), vp, vp, vp,
+                                      ctypes.POINTER(bvls_ragged_info)]
+    lib.bvls_solve_ragged.restype = ci
     _lib = lib
     return lib
 
@@ -202,6 +235,18 @@ def bvls_backward(h: int, B: int, X_ptr: int, Y_ptr: int, ldy: int, dLdX_ptr: in
     info = bvls_backward_info()
     st = load().bvls_backward(h, B, X_ptr, Y_ptr, ldy, dLdX_ptr, ctypes.byref(opts) if opts is not None else None,
                               dLdY_ptr, dLdA_ptr, status_ptr, ctypes.byref(info))
+    return st, info
+
+
+def bvls_solve_ragged(probs, opts: bvls_opts | None, stream: int | None, x_ptrs, screened_ptrs, gaps_ptr,
+                      iters_ptr, status_ptr) -> tuple[int, bvls_ragged_info]:
+    B = len(probs)
+    arr = (bvls_problem * B)(*probs)
+    xp = (ctypes.c_void_p * B)(*x_ptrs)
+    sp = (ctypes.c_void_p * B)(*screened_ptrs) if screened_ptrs is not None else None
+    info = bvls_ragged_info()
+    st = load().bvls_solve_ragged(B, arr, ctypes.byref(opts) if opts is not None else None, stream or 0, xp,
+                                  sp, gaps_ptr, iters_ptr, status_ptr, ctypes.byref(info))
     return st, info
 
 

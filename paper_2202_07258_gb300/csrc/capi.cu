@@ -1,5 +1,6 @@
 // C ABI: handle management, setup and the solve loop (CUDA-graph chunks of iterations).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -9,6 +10,7 @@
 
 #include "backward.cuh"
 #include "batch.cuh"
+#include "ragged.cuh"
 #include "bvls_gb300.h"
 #include "common.cuh"
 
@@ -1157,6 +1159,298 @@ extern "C" bvls_status bvls_backward(bvls_handle* h, int B, const double* X, con
       info->max_cg_iters = std::max(info->max_cg_iters, it[b]);
     }
   }
+  g_err.clear();
+  return BVLS_OK;
+}
+
+// ------------------------------------------------------------------ ragged batch
+extern "C" bvls_status bvls_solve_ragged(int B, const bvls_problem* probs, const bvls_opts* opts, void* stream,
+                                         double* const* x_out, uint8_t* const* screened_out, double* gaps_out,
+                                         int* iters_out, int* status_out, bvls_ragged_info* info) {
+  using clk = std::chrono::steady_clock;
+  const auto t_start = clk::now();
+  if (B < 1 || !probs || !x_out) return set_err(BVLS_EINVAL, "need B >= 1, probs and x_out");
+  bvls_opts o;
+  bvls_default_opts(&o);
+  if (opts) o = *opts;
+  TRY(validate_opts(o));
+  // ---- layout
+  std::vector<RInst> in(B);
+  long long a_tot = 0, c_tot = 0, r_tot = 0, p_tot = 0, t_tot = 0;
+  for (int k = 0; k < B; ++k) {
+    const bvls_problem& q = probs[k];
+    if (!q.A || !q.y || q.m < 1 || q.n < 1 || q.lda < q.m)
+      return set_err(BVLS_EINVAL, "problem %d: need A, y, m >= 1, n >= 1, lda >= m", k);
+    if (q.m > kRMaxRows) return set_err(BVLS_ENOTSUP, "problem %d: m = %d exceeds %d", k, q.m, kRMaxRows);
+    RInst& r = in[k];
+    std::memset(&r, 0, sizeof(r));
+    r.m = q.m;
+    r.n = q.n;
+    r.lda = (q.m + 3) / 4 * 4;
+    r.tiles_max = (q.n + kRTile - 1) / kRTile;
+    r.a_off = a_tot;
+    r.c_off = c_tot;
+    r.r_off = r_tot;
+    r.p_off = p_tot;
+    r.t_off = t_tot;
+    a_tot += (long long)r.lda * q.n;
+    c_tot += q.n;
+    r_tot += q.m;
+    p_tot += (long long)r.tiles_max * q.m;
+    t_tot += r.tiles_max;
+  }
+  std::vector<double> l(c_tot), u(c_tot);
+  std::vector<float2> l2(c_tot), u2(c_tot);
+  std::vector<uint8_t> jinf(c_tot);
+  for (int k = 0; k < B; ++k) {
+    for (int j = 0; j < in[k].n; ++j) {
+      const long long c = in[k].c_off + j;
+      const double lv = probs[k].l ? probs[k].l[j] : 0.0, uv = probs[k].u ? probs[k].u[j] : INFINITY;
+      if (!std::isfinite(lv) || std::isnan(uv) || uv == -INFINITY || lv > uv)
+        return set_err(BVLS_EINVAL, "problem %d, coordinate %d: need finite l <= u", k, j);
+      l[c] = lv;
+      u[c] = uv;
+      l2[c] = df2_from_double(lv);
+      u2[c] = df2_from_double(uv);
+      jinf[c] = std::isinf(uv) ? 1 : 0;
+    }
+  }
+  // ---- workspace
+  std::vector<void*> mem;
+  cudaStream_t s = nullptr;
+  cudaEvent_t ev = nullptr;
+  cudaGraphExec_t gx = nullptr;
+  auto release = [&]() {
+    if (s) cudaStreamSynchronize(s);
+    if (gx) cudaGraphExecDestroy(gx);
+    for (void* q : mem) cudaFree(q);
+    if (ev) cudaEventDestroy(ev);
+    if (s) cudaStreamDestroy(s);
+  };
+#define RCK(call)                                                                              \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) {                                                                   \
+      release();                                                                               \
+      return set_err(e_ == cudaErrorMemoryAllocation ? BVLS_ENOMEM : BVLS_ECUDA, "%s failed: %s", \
+                     #call, cudaGetErrorString(e_));                                           \
+    }                                                                                          \
+  } while (0)
+  auto alloc = [&](auto** ptr, size_t count) -> cudaError_t {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(**ptr) + 256);
+    if (e == cudaSuccess) {
+      mem.push_back(q);
+      *ptr = static_cast<std::remove_reference_t<decltype(*ptr)>>(q);
+    }
+    return e;
+  };
+  RCK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  RCK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  RCK(cudaEventRecord(ev, static_cast<cudaStream_t>(stream)));
+  RCK(cudaStreamWaitEvent(s, ev, 0));
+  RBuf b{};
+  float* A = nullptr;
+  RInst* d_in = nullptr;
+  float2 *d_l2 = nullptr, *d_u2 = nullptr;
+  double *d_l = nullptr, *d_u = nullptr;
+  uint8_t* d_jinf = nullptr;
+  RCK(alloc(&A, (size_t)a_tot));
+  RCK(alloc(&d_in, (size_t)B));
+  RCK(alloc(&b.st, (size_t)B));
+  for (int q = 0; q < 2; ++q) {
+    RCK(alloc(&b.x[q], (size_t)c_tot));
+    RCK(alloc(&b.g[q], (size_t)c_tot));
+  }
+  RCK(alloc(&d_l2, (size_t)c_tot));
+  RCK(alloc(&d_u2, (size_t)c_tot));
+  RCK(alloc(&d_l, (size_t)c_tot));
+  RCK(alloc(&d_u, (size_t)c_tot));
+  RCK(alloc(&b.nrm, (size_t)c_tot));
+  RCK(alloc(&b.w, (size_t)c_tot));
+  RCK(alloc(&d_jinf, (size_t)c_tot));
+  RCK(alloc(&b.flags, (size_t)c_tot));
+  RCK(alloc(&b.idx, (size_t)c_tot));
+  RCK(alloc(&b.idx_tmp, (size_t)c_tot));
+  RCK(alloc(&b.xout, (size_t)c_tot));
+  RCK(alloc(&b.yh, (size_t)r_tot));
+  RCK(alloc(&b.yl, (size_t)r_tot));
+  RCK(alloc(&b.rh, (size_t)r_tot));
+  RCK(alloc(&b.rl, (size_t)r_tot));
+  RCK(alloc(&b.part, (size_t)p_tot));
+  RCK(alloc(&b.tdot, (size_t)t_tot));
+  RCK(alloc(&b.teps, (size_t)t_tot));
+  RCK(alloc(&b.tiles, (size_t)t_tot));
+  RCK(alloc(&b.n_tiles, 1));
+  RCK(alloc(&b.n_act_inst, 1));
+  RCK(alloc(&b.chunks, 1));
+  RCK(alloc(&b.act, (size_t)B));
+  RCK(alloc(&b.err, 1));
+  b.A = A;
+  b.inst = d_in;
+  b.l2 = d_l2;
+  b.u2 = d_u2;
+  b.l = d_l;
+  b.u = d_u;
+  b.jinf = d_jinf;
+  b.B = B;
+  b.screening = o.screening;
+  b.restart = o.restart;
+  b.tol = o.tol;
+  const int K = o.screen_every;
+  b.K = K;
+  b.max_iter = (int)std::min<long long>((long long)(o.max_iter + K - 1) / K * K, 0x3fffffff);
+  // ---- copies
+  RCK(cudaMemsetAsync(A, 0, sizeof(float) * (size_t)a_tot, s));
+  RCK(cudaMemsetAsync(b.yl, 0, sizeof(float) * (size_t)r_tot, s));
+  RCK(cudaMemsetAsync(b.err, 0, sizeof(unsigned), s));
+  RCK(cudaMemsetAsync(b.chunks, 0, sizeof(int), s));
+  for (int k = 0; k < B; ++k) {
+    const bvls_problem& q = probs[k];
+    RCK(cudaMemcpy2DAsync(A + in[k].a_off, sizeof(float) * in[k].lda, q.A, sizeof(float) * q.lda,
+                          sizeof(float) * q.m, q.n, cudaMemcpyDefault, s));
+    RCK(cudaMemcpyAsync(b.yh + in[k].r_off, q.y, sizeof(float) * q.m, cudaMemcpyDefault, s));
+  }
+  RCK(cudaMemcpyAsync(d_l, l.data(), sizeof(double) * c_tot, cudaMemcpyHostToDevice, s));
+  RCK(cudaMemcpyAsync(d_u, u.data(), sizeof(double) * c_tot, cudaMemcpyHostToDevice, s));
+  RCK(cudaMemcpyAsync(d_l2, l2.data(), sizeof(float2) * c_tot, cudaMemcpyHostToDevice, s));
+  RCK(cudaMemcpyAsync(d_u2, u2.data(), sizeof(float2) * c_tot, cudaMemcpyHostToDevice, s));
+  RCK(cudaMemcpyAsync(d_jinf, jinf.data(), c_tot, cudaMemcpyHostToDevice, s));
+  RCK(cudaMemcpyAsync(d_in, in.data(), sizeof(RInst) * B, cudaMemcpyHostToDevice, s));
+  // ---- column norms, w = A^T (-1), dual modes
+  RCK(launch_rnorms(b, c_tot, s));
+  std::vector<double> nrm(c_tot), w(c_tot);
+  RCK(cudaMemcpyAsync(nrm.data(), b.nrm, sizeof(double) * c_tot, cudaMemcpyDeviceToHost, s));
+  RCK(cudaMemcpyAsync(w.data(), b.w, sizeof(double) * c_tot, cudaMemcpyDeviceToHost, s));
+  unsigned herr = 0;
+  RCK(cudaMemcpyAsync(&herr, b.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  RCK(cudaStreamSynchronize(s));
+  if (herr) {
+    release();
+    return set_err(BVLS_ENONFINITE, "an A_k contains NaN or Inf");
+  }
+  int n_trans = 0, n_zero = 0;
+  for (int k = 0; k < B; ++k) {
+    RInst& r = in[k];
+    bool any_inf = false, ok = true;
+    const double gamma = 1.01 * (r.m + 8) * kU64;
+    r.t_norm = std::sqrt((double)r.m);
+    for (int j = 0; j < r.n; ++j) {
+      const long long c = r.c_off + j;
+      if (!jinf[c]) continue;
+      any_inf = true;
+      if (nrm[c] > 0.0 && !(w[c] + gamma * nrm[c] * r.t_norm < 0.0)) ok = false;
+    }
+    r.dual_mode = !any_inf ? kScaling : ok ? kTranslation : kZero;
+    r.gamma_w = gamma;
+    n_trans += r.dual_mode == kTranslation;
+    n_zero += r.dual_mode == kZero;
+    const double dg = ((r.m + 3) / 4 + 31) / 32 + 7;
+    r.Cg = 2.0 * (dg + 2.0) * (dg + 2.0) * kU * kU + 4.0 * kU * kU + 2.0 * kU64;
+    const double df = kRTile + r.tiles_max + 2;
+    r.Cf = 2.0 * (df + 2.0) * (df + 2.0) * kU * kU + 2.0 * kU * kU;
+    r.Csub = 8.0 * kU * kU;
+    r.invL = 1.0;
+  }
+  RCK(cudaMemcpyAsync(d_in, in.data(), sizeof(RInst) * B, cudaMemcpyHostToDevice, s));
+  // ---- step constants: 40 power iterations on every instance at once
+  const int max_tiles = (int)t_tot;
+  b.power = 1;
+  RCK(launch_rinit(b, c_tot, 1, s));
+  RCK(launch_rfwd(b, s));
+  RCK(launch_rtiles(b, s));
+  for (int it = 0; it < 40; ++it) {
+    RCK(launch_rpass(b, max_tiles, it & 1, 0, s));
+    RCK(launch_rresid(b, it & 1, s));
+  }
+  std::vector<RState> hs(B);
+  RCK(cudaMemcpyAsync(hs.data(), b.st, sizeof(RState) * B, cudaMemcpyDeviceToHost, s));
+  RCK(cudaStreamSynchronize(s));
+  for (int k = 0; k < B; ++k) in[k].invL = hs[k].pw_lambda > 0.0 ? 1.0 / (1.05 * hs[k].pw_lambda) : 1.0;
+  RCK(cudaMemcpyAsync(d_in, in.data(), sizeof(RInst) * B, cudaMemcpyHostToDevice, s));
+  const auto t_setup = clk::now();
+  // ---- solve: one graph, a while node around one chunk
+  b.power = 0;
+  RCK(launch_rinit(b, c_tot, 0, s));
+  RCK(launch_rfwd(b, s));
+  RCK(launch_rtiles(b, s));
+  const int chunk = chunk_length(K);
+  const long long max_chunks = (b.max_iter + chunk - 1) / chunk + 2;
+  {
+    cudaGraph_t g = nullptr;
+    RCK(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle hc;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&hc, g, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = hc;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    cudaGraph_t body = e == cudaSuccess ? np.conditional.phGraph_out[0] : nullptr;
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e1 = cudaSuccess;
+      for (int j = 0; j < chunk && e1 == cudaSuccess; ++j) {
+        const bool gap_iter = ((j + 1) % K) == 0;
+        e1 = launch_rpass(b, max_tiles, j & 1, gap_iter ? 1 : 0, s);
+        if (e1 == cudaSuccess) e1 = launch_rresid(b, j & 1, s);
+        if (e1 == cudaSuccess && gap_iter) e1 = launch_rgap(b, j & 1, s);
+        if (e1 == cudaSuccess && gap_iter) e1 = launch_rtiles(b, s);
+      }
+      if (e1 == cudaSuccess) e1 = launch_rloop_ctl(b, hc, (int)std::min<long long>(max_chunks, 0x7fffffff), s);
+      cudaError_t e2 = cudaStreamEndCapture(s, &body);
+      e = e1 != cudaSuccess ? e1 : e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&gx, g, 0);
+    cudaGraphDestroy(g);
+    RCK(e);
+  }
+  RCK(cudaGraphLaunch(gx, s));
+  RCK(launch_rexport(b, s));
+  RCK(cudaMemcpyAsync(hs.data(), b.st, sizeof(RState) * B, cudaMemcpyDeviceToHost, s));
+  int hchunks = 0;
+  RCK(cudaMemcpyAsync(&hchunks, b.chunks, sizeof(int), cudaMemcpyDeviceToHost, s));
+  RCK(cudaMemcpyAsync(&herr, b.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  RCK(cudaStreamSynchronize(s));
+  const auto t_solve = clk::now();
+  if (herr) {
+    release();
+    return set_err(BVLS_ENONFINITE, "a y_k contains NaN or Inf");
+  }
+  int nconv = 0, itmax = 0;
+  for (int k = 0; k < B; ++k) {
+    if (!hs[k].done) {
+      release();
+      return set_err(BVLS_ECUDA, "instance %d did not finish after %d chunks", k, hchunks);
+    }
+    nconv += hs[k].converged;
+    itmax = std::max(itmax, hs[k].k);
+  }
+  for (int k = 0; k < B; ++k) {
+    RCK(cudaMemcpyAsync(x_out[k], b.xout + in[k].c_off, sizeof(double) * in[k].n, cudaMemcpyDefault, s));
+    if (screened_out && screened_out[k])
+      RCK(cudaMemcpyAsync(screened_out[k], b.flags + in[k].c_off, in[k].n, cudaMemcpyDefault, s));
+    if (gaps_out) gaps_out[k] = hs[k].gap;
+    if (iters_out) iters_out[k] = hs[k].k;
+    if (status_out) status_out[k] = hs[k].converged ? BVLS_OK : BVLS_EMAXITER;
+  }
+  RCK(cudaStreamSynchronize(s));
+  release();
+#undef RCK
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->iters_max = itmax;
+    info->n_converged = nconv;
+    info->n_translation = n_trans;
+    info->n_zero = n_zero;
+    info->chunks = hchunks;
+    info->tiles_max = max_tiles;
+    info->setup_ms = std::chrono::duration<double, std::milli>(t_setup - t_start).count();
+    info->solve_ms = std::chrono::duration<double, std::milli>(t_solve - t_setup).count();
+  }
+  if (nconv < B) return set_err(BVLS_EMAXITER, "%d of %d instances reached max_iter with gap >= tol", B - nconv, B);
   g_err.clear();
   return BVLS_OK;
 }

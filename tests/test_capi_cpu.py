@@ -62,6 +62,11 @@ def test_setup_rejects_bad_sizes_before_touching_the_device(lib):
     assert st == _capi.BVLS_EINVAL
     o = _capi.bvls_backward_default_opts()
     assert o.free_tol == 1e-9 and o.cg_tol == 1e-12 and o.cg_max_iter == 4000
+    st, _ = _capi.bvls_solve_ragged([], None, 0, [], None, None, None, None)
+    assert st == _capi.BVLS_EINVAL
+    bad = _capi.bvls_problem(ctypes.addressof(buf), 2000, 2, 2000, ctypes.addressof(buf), None, None)
+    st, _ = _capi.bvls_solve_ragged([bad], None, 0, [ctypes.addressof(buf)], None, None, None, None)
+    assert st == _capi.BVLS_ENOTSUP     # m above the ragged path's limit, rejected before any device work
 
 
 def test_struct_layouts_match_header(tmp_path):
@@ -74,7 +79,8 @@ def test_struct_layouts_match_header(tmp_path):
         pytest.skip("no C compiler")
     classes = {"bvls_opts": _capi.bvls_opts, "bvls_info": _capi.bvls_info,
                "bvls_batch_info": _capi.bvls_batch_info, "bvls_backward_opts": _capi.bvls_backward_opts,
-               "bvls_backward_info": _capi.bvls_backward_info}
+               "bvls_backward_info": _capi.bvls_backward_info, "bvls_problem": _capi.bvls_problem,
+               "bvls_ragged_info": _capi.bvls_ragged_info}
     fields = {k: [f for f, _ in c._fields_] for k, c in classes.items()}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "bvls_gb300.h"', "int main(void){"]
     for st, fl in fields.items():

@@ -24,6 +24,7 @@ __all__ = [
     "bvls_dirichlet_shared",
     "nnls_shared",
     "bvls_box_shared",
+    "mixed_uneven",
     "bvls_gaussian_box",
     "random_tiny",
 ]
@@ -196,6 +197,39 @@ def bvls_box_shared(m: int, n: int, B: int, box: float, seed: int, name: str | N
     return Problem(name or f"bvls_box{box:g}_shared_{m}x{n}_B{B}_s{seed}", A.astype(np.float32),
                    Y.astype(np.float32), np.full(n, -box), np.full(n, box), np.zeros((B, n)),
                    dict(family="bvls_box_shared", m=m, n=n, B=B, box=box, seed=seed))
+
+
+def mixed_uneven(B: int, seed: int, m_lo: int = 64, m_hi: int = 1024, abs_matrix: bool = False,
+                 noise: float = 0.01, density: float = 0.10) -> list[Problem]:
+    """Batch of independent problems of uneven sizes (each with its own matrix).
+
+    m_k ~ U{m_lo..m_hi}, n_k ~ U{2 m_k..8 m_k}; A_k iid N(0,1) (|N(0,1)| with ``abs_matrix``)
+    with unit-norm columns; x_k has ``density * n_k`` nonzeros.  Even k: NNLS (l = 0,
+    u = +inf), nonzeros ~ U[0,1].  Odd k: BVLS on [-1, 1], nonzeros ~ U[-1,1] of which 20%
+    are set to +-1.  y_k = A_k x_k + N(0, noise^2).
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(B):
+        m = int(rng.integers(m_lo, m_hi + 1))
+        n = int(rng.integers(2 * m, 8 * m + 1))
+        G = rng.standard_normal((m, n))
+        A = _unit_columns(np.abs(G) if abs_matrix else G)
+        x = np.zeros(n)
+        supp = _sparse_support(rng, n, density)
+        if k % 2 == 0:
+            x[supp] = rng.uniform(0.0, 1.0, supp.size)
+            l, u = np.zeros(n), np.full(n, np.inf)
+        else:
+            x[supp] = rng.uniform(-1.0, 1.0, supp.size)
+            sat = supp[rng.random(supp.size) < 0.2]
+            x[sat] = rng.choice([-1.0, 1.0], sat.size)
+            l, u = np.full(n, -1.0), np.full(n, 1.0)
+        y = A @ x + noise * rng.standard_normal(m)
+        out.append(Problem(f"mixed_{k}_{m}x{n}", A.astype(np.float32), y.astype(np.float32), l, u, x,
+                           dict(family="mixed_uneven", m=m, n=n, k=k, seed=seed, abs_matrix=abs_matrix,
+                                noise=noise)))
+    return out
 
 
 def random_tiny(m: int, n: int, kind: str, seed: int) -> Problem:
