@@ -1245,6 +1245,7 @@ extern "C" bvls_status bvls_solve_ragged(int B, const bvls_problem* probs, const
     }
     return e;
   };
+  RCK(ragged_configure());
   RCK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
   RCK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
   RCK(cudaEventRecord(ev, static_cast<cudaStream_t>(stream)));

@@ -385,6 +385,10 @@ __global__ void __launch_bounds__(kRThreads) k_rpass(RBuf b, int slot, int gap_i
   }
 }
 
+cudaError_t ragged_configure() {
+  return cudaFuncSetAttribute(k_rpass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rpass_smem_bytes());
+}
+
 cudaError_t launch_rpass(const RBuf& b, int max_tiles, int slot, int gap_iter, cudaStream_t s) {
   k_rpass<<<max_tiles, kRThreads, rpass_smem_bytes(), s>>>(b, slot, gap_iter);
   return cudaGetLastError();

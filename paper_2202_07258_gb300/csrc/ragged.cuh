@@ -102,6 +102,7 @@ cudaError_t launch_rresid(const RBuf& b, int slot, cudaStream_t s);
 cudaError_t launch_rgap(const RBuf& b, int slot, cudaStream_t s);
 cudaError_t launch_rexport(const RBuf& b, cudaStream_t s);
 size_t rpass_smem_bytes();
+cudaError_t ragged_configure();  // shared-memory attribute of the tile kernel (before any launch)
 // Last node of a chunk in the ragged solve graph's while loop: ends the loop once no instance
 // is active or max_chunks chunks have run.
 cudaError_t launch_rloop_ctl(const RBuf& b, cudaGraphConditionalHandle h, int max_chunks, cudaStream_t s);
