@@ -239,6 +239,41 @@ def roofline(solver, y_dev, m):
 BATCH = dict(m=224, n=512, B=4096, k_support=8, noise=0.005, seed=0)
 
 
+def ragged_leg(dev, stream, B=512):
+    """Mixed NNLS/BVLS batch of uneven sizes (each instance its own A_k iid N(0,1), m_k ~
+    U{64..1024}, n_k ~ U{2m_k..8m_k}, x0 10% nonzeros, even k NNLS, odd k BVLS [-1,1] with
+    20% of x0 at +-1, noise 0.01; seed 0), one bvls_solve_ragged call with A_k resident in
+    HBM, screened and unscreened; plus the |N(0,1)| / unit-noise variant (screenable) on 64
+    instances with max_iter 20000."""
+    import torch
+    from paper_2202_07258_gb300 import solve_ragged
+    out = {}
+    for name, b, absm, noise, mx in (("gaussian_B%d" % B, B, False, 0.01, 100000),
+                                     ("abs_B64_maxiter20000", 64, True, 1.0, 20000)):
+        probs = W.mixed_uneven(b, 0, abs_matrix=absm, noise=noise)
+        items = [(torch.from_numpy(p.A).to(dev), torch.from_numpy(p.y).to(dev), p.l, p.u) for p in probs]
+        nbytes = sum(p.A.nbytes for p in probs)
+        del probs
+        torch.cuda.synchronize()
+        res = {"instances": b, "bytes_A": nbytes}
+        for scr in (True, False):
+            t0 = time.perf_counter()
+            xs, ss, gaps, its, sts, info, st = solve_ragged(items, tol=TOL, screen_every=K_SCREEN, screening=scr,
+                                                            max_iter=mx, stream=stream.cuda_stream)
+            wall = time.perf_counter() - t0
+            res["screened" if scr else "unscreened"] = {
+                "instances_per_s_solve": b / (info["solve_ms"] / 1000.0),
+                "instances_per_s_call": b / wall, "solve_ms": info["solve_ms"], "setup_ms": info["setup_ms"],
+                "n_converged": info["n_converged"], "iters_max": int(its.max()), "iters_mean": float(its.mean()),
+                "screened_fraction_end": float(sum(int((s > 0).sum()) for s in ss) / max(1, sum(len(s) for s in ss))),
+                "dual_modes": {"translation": info["n_translation"], "zero": info["n_zero"]}}
+        res["speedup"] = res["unscreened"]["solve_ms"] / res["screened"]["solve_ms"]
+        out[name] = res
+        del items
+        torch.cuda.empty_cache()
+    return out
+
+
 def table2_leg(dev, stream, flush, steps):
     """Table-2 family (BVLS, A = |N(0,1)| unit columns 1000 x 2000, x0 5% U(0,1), noise N(0,1),
     box [0,1]): FISTA and the Chambolle-Pock primal-dual solver, screened and unscreened, to
@@ -447,6 +482,7 @@ def run_ours(args):
     roof = roofline(scr["solver"], scr["y"], 2000) if rank == 0 else None
     batched = batched_leg(dev, stream, flush, max(2, min(args.steps, 5))) if (rank == 0 and not args.no_batched) else None
     table2 = table2_leg(dev, stream, flush, max(2, min(args.steps, 3))) if rank == 0 else None
+    ragged = ragged_leg(dev, stream) if (rank == 0 and not args.no_batched) else None
     e2e = e2e_leg(scr["p"], max(2, min(args.steps, 5)), stream) if rank == 0 else None
     cpu = oracle_sample(scr["p"]) if (rank == 0 and world == 1) else None
     scr["solver"].close()
@@ -486,7 +522,7 @@ def run_ours(args):
                     "iters": var_o["info"]["iters"],
                     "avg_preserved_fraction": var_o["info"]["sum_preserved"] / max(1, var_o["info"]["iters"]) / 10000}},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "batched_shared_A": batched,
-            "table2_bvls": table2,
+            "table2_bvls": table2, "ragged_uneven": ragged,
             "gpu_launches": int(scr["launches"]), "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)
