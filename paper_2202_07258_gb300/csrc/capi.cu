@@ -217,8 +217,7 @@ cudaError_t enqueue_chunk(bvls_handle* h, const Params& p, const bvls_opts& o, i
                       h->s);
       if (e != cudaSuccess) break;
       if (ev) cudaEventRecordWithFlags(ev[3 * j + 1], h->s, cudaEventRecordExternal);
-      // the FISTA pass accumulates A_S x_{k+1} with atomics; the next pass forms r itself
-      if (p.alg == kChambollePock) e = launch_resid(p, h->b, slot, h->num_sms, h->s);
+      e = launch_resid(p, h->b, slot, h->num_sms, h->s);
     } else {
       e = launch_fwd(p, h->b, slot, o.precision, false, h->s);
       if (e != cudaSuccess) break;
@@ -519,7 +518,6 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
   TRY(dalloc(h, &b.tileR, (h->m4 + 31) / 32));    // the residual kernel's grid
   TRY(dalloc(h, &b.tileD, (h->m4 + 31) / 32));
   TRY(dalloc(h, &b.tileZ, (h->m4 + 31) / 32));
-  TRY(dalloc(h, &b.q3, 3 * (size_t)h->m4));
   TRY(dalloc(h, &b.crh, h->m4));
   TRY(dalloc(h, &b.crl, h->m4));
   TRY(dalloc(h, &b.tile_cnt, h->fwd_tiles));
@@ -547,9 +545,8 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
     // the fused pass: a q-warp lane sums its CTA's columns, then 8 warps x nparts/8 partials
     const int d_p = (n + h->num_sms - 1) / h->num_sms + (h->num_sms + 7) / 8 + 8;
     const int d = std::max(d_f, d_p);
-    // + the float64 atomic sum of the per-CTA partials (any order)
-    h->Cf[kX2] = 2.0 * (d + 2.0) * (d + 2.0) * kU * kU + 2.0 * kU * kU + (h->num_sms + 2) * kU64;
-    h->Cf[kF32] = 1.01 * (d + 2.0) * kU + kU + (h->num_sms + 2) * kU64;
+    h->Cf[kX2] = 2.0 * (d + 2.0) * (d + 2.0) * kU * kU + 2.0 * kU * kU;
+    h->Cf[kF32] = 1.01 * (d + 2.0) * kU + kU;
     h->Csub = 8.0 * kU * kU;
   }
   CK(cudaStreamSynchronize(h->s));
@@ -616,11 +613,10 @@ bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const b
   CK(launch_init(p, h->b, h->s));
   if (fused) CK(launch_fwd(p, h->b, 0, o.precision, false, h->s));  // r_0, P_0
   if (p.alg == kChambollePock) CK(launch_cp_init(p, h->b, h->s));  // z_1 = -r_0
-  else if (fused) CK(launch_q3_init(p, h->b, h->s));                 // q_0 = y' - r_0
 
   const long long max_chunks = (max_iter + chunk - 1) / chunk + 1;
   const bool scr = o.screening && h->dual_mode != kZero;
-  const long long per_chunk = ((fused && p.alg == kFista) ? 1LL : 2LL) * chunk + (long long)(chunk / K) * (scr ? 4 : 1);
+  const long long per_chunk = 2LL * chunk + (long long)(chunk / K) * (scr ? 4 : 1);
   long long chunks_run = 0;
   double fwd_ms = 0.0, tr_ms = 0.0;
   int fwd_launches = 0, tr_launches = 0;

@@ -250,9 +250,6 @@ struct Buffers {
   unsigned int* tile_cnt;
   double* blk;            // per-block partials of the epilogue kernels (4 doubles each)
   float2* qpart;          // fused pass: per-CTA double-float partials of A_S x_S (grid x m4)
-  double* q3;             // fused FISTA pass: A_S x_S accumulated with float64 atomics, three
-                          // buffers of m4 (read k % 3, add into (k+1) % 3, clear (k+2) % 3);
-                          // null: the per-CTA partials and the residual kernel are used
   double* xout;           // float64 copy of the returned iterate (n)
   DevState* st;
   const float* y_in;      // device copy of y
@@ -281,8 +278,6 @@ cudaError_t launch_export(const Params& p, const Buffers& b, int slot, cudaStrea
 // primal-dual start: r_0 (in rh / rl from the forward kernel) moves to crh / crl and
 // z_1 = A x_0 - y' = -r_0 takes its place
 cudaError_t launch_cp_init(const Params& p, const Buffers& b, cudaStream_t s);
-// q3 start: q_0 = y' - r_0 in buffer 0 (r_0 from the forward kernel), buffers 1 and 2 cleared
-cudaError_t launch_q3_init(const Params& p, const Buffers& b, cudaStream_t s);
 cudaError_t tr_configure(int m4, int* blocks_per_sm);
 
 // Record the text returned by bvls_last_error() on this thread (capi.cu).

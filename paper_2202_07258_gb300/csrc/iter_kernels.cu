@@ -324,8 +324,6 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd(Params p, Buffers b, int sl
     if (FOLD) {
       b.yh[r_] = rh;
       b.yl[r_] = rl;
-      // with the atomic accumulation the pending A_S x_S still holds the folded columns
-      if (b.q3) b.q3[(size_t)(st->k % 3) * p.m4 + r_] -= (double)s + (double)c;
     } else {
       b.rh[r_] = rh;
       b.rl[r_] = rl;

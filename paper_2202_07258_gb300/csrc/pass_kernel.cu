@@ -105,44 +105,11 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
   const int nq = min(n_act, p0 + per) - p0;
   const int ngroups = (nq + cps - 1) / cps;
 
-  const bool q3mode = b.q3 != nullptr && p.alg == kFista;
-  const int kit = st->k;
+  // P_k = 1/2 ||r_k||^2: from the residual kernel's block partials after the first
+  // iteration (one L2 round trip by warp 0); CTA 0 records it for the gap kernel.
   double Pk = 0.0;
-  if (q3mode) {
-    // r_k = y' - q_k from the float64 accumulator of the previous pass; clear the buffer the
-    // next pass will accumulate into (its readers finished with the previous launch)
-    const double* q = b.q3 + (size_t)(kit % 3) * p.m4;
-    double* qz = b.q3 + (size_t)((kit + 2) % 3) * p.m4;
-    const int rows = (p.m4 + gridDim.x - 1) / gridDim.x;
-    for (int i = blockIdx.x * rows + threadIdx.x; i < min(p.m4, (int)(blockIdx.x + 1) * rows); i += blockDim.x)
-      qz[i] = 0.0;
-    float* rh = reinterpret_cast<float*>(srh);
-    float* rl = reinterpret_cast<float*>(srl);
-    double pk = 0.0;
-    for (int i = threadIdx.x; i < p.m4; i += blockDim.x) {
-      const double rd = ((double)b.yh[i] + (double)b.yl[i]) - __ldcg(q + i);
-      const float h = (float)rd;
-      rh[i] = h;
-      rl[i] = (float)(rd - (double)h);
-      if (gap_iter) pk += 0.5 * rd * rd;
-    }
-    if (gap_iter) {
-      // P_k for the translation step's margin and (CTA 0) for the gap kernel
-      pk = warp_sum_d(pk);
-      if ((threadIdx.x & 31) == 0) s_th[threadIdx.x >> 5] = pk;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        double t2 = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t2 += s_th[w];
-        Pk = t2;
-        if (blockIdx.x == 0) st->P[slot] = t2;
-      }
-      __syncthreads();
-    }
-  } else if (threadIdx.x < 32) {
-    // P_k = 1/2 ||r_k||^2 from the residual kernel's block partials after the first
-    // iteration (one L2 round trip by warp 0); CTA 0 records it for the gap kernel.
-    Pk = kit > 0 ? warp_load_sum(b.tileR, (p.m4 + 31) / 32) : st->P[slot];
+  if (threadIdx.x < 32) {
+    Pk = st->k > 0 ? warp_load_sum(b.tileR, (p.m4 + 31) / 32) : st->P[slot];
     if (threadIdx.x == 0 && blockIdx.x == 0) st->P[slot] = Pk;
   }
   if (threadIdx.x == 0) {
@@ -168,11 +135,9 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
     s_dot[threadIdx.x] = make_float2(0.f, 0.f);
     s_eps[threadIdx.x] = 0.0;
   }
-  if (!q3mode) {
-    for (int i = threadIdx.x; i < m4q; i += blockDim.x) {
-      srh[i] = __ldcg(reinterpret_cast<const float4*>(b.rh) + i);
-      srl[i] = __ldcg(reinterpret_cast<const float4*>(b.rl) + i);
-    }
+  for (int i = threadIdx.x; i < m4q; i += blockDim.x) {
+    srh[i] = __ldcg(reinterpret_cast<const float4*>(b.rh) + i);
+    srl[i] = __ldcg(reinterpret_cast<const float4*>(b.rl) + i);
   }
   // one coalesced read of the index range instead of a dependent load per column
   for (int q = threadIdx.x; q < nq; q += blockDim.x) sidx[q] = b.idx[p0 + q];
@@ -385,25 +350,10 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);
     }
-    if (q3mode) {
-      // float64 atomics into q_{k+1}: the double-float partial of a row converts exactly
-      double* qn = b.q3 + (size_t)((kit + 1) % 3) * p.m4;
-#pragma unroll
-      for (int t = 0; t < QT; ++t) {
-        const int c4 = qw * 32 + lane + t * 32 * QW;
-        if (c4 < m4q) {
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const double v = (double)qs[t][e] + (PREC == kX2 ? (double)qc[t][e] : 0.0);
-            if (v != 0.0) atomicAdd(qn + 4 * c4 + e, v);
-          }
-        }
-      }
-    }
     // per-CTA partials of A_S x_{k+1} (every row written, zeros included)
     float2* part = b.qpart + (size_t)blockIdx.x * p.m4;
 #pragma unroll
-    for (int t = 0; t < QT && !q3mode; ++t) {
+    for (int t = 0; t < QT; ++t) {
       const int c4 = qw * 32 + lane + t * 32 * QW;
       if (c4 < m4q) {
         float4* dst = reinterpret_cast<float4*>(part + 4 * c4);
@@ -542,19 +492,6 @@ __global__ void __launch_bounds__(256) k_resid(Params p, Buffers b, int slot, in
     }
     if (lane == 0) b.tileR[blockIdx.x] = df_to_double(ps, pc);   // summed by the next pass
   }
-}
-
-__global__ void k_q3_init(Params p, Buffers b) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.m4; i += gridDim.x * blockDim.x) {
-    b.q3[i] = ((double)b.yh[i] + (double)b.yl[i]) - ((double)b.rh[i] + (double)b.rl[i]);
-    b.q3[p.m4 + i] = 0.0;
-    b.q3[2 * (size_t)p.m4 + i] = 0.0;
-  }
-}
-
-cudaError_t launch_q3_init(const Params& p, const Buffers& b, cudaStream_t s) {
-  k_q3_init<<<(p.m4 + 255) / 256, 256, 0, s>>>(p, b);
-  return cudaGetLastError();
 }
 
 __global__ void k_cp_init(Params p, Buffers b) {
