@@ -70,8 +70,13 @@ typedef enum {
 enum {
   BVLS_PREC_FP32X2 = 0, /* float32 data, error-free products and double-float (about 48-bit)
                            accumulation; default */
-  BVLS_PREC_FP32 = 1    /* float32 data and plain float32 accumulation; faster, and the
+  BVLS_PREC_FP32 = 1,   /* float32 data and plain float32 accumulation; faster, and the
                            rounding margins of the test are about 2^24 times wider */
+  BVLS_PREC_MIXED = 2   /* float32 correlations a_j^T r, double-float forward product A x
+                           (bvls_solve, bvls_solve_static): the residual, P(x) and the
+                           certificate of the zero dual point keep the FP32X2 accuracy; the
+                           correlations and the screening margins are those of FP32.
+                           bvls_solve_batched treats it as FP32 */
 };
 
 /* Primal solver of bvls_solve. */

@@ -17,7 +17,7 @@ import numpy as np
 
 from . import _capi
 from ._capi import (BVLS_DUAL_SCALING, BVLS_DUAL_TRANSLATION, BVLS_DUAL_ZERO, BVLS_EINVAL,
-                    BVLS_EMAXITER, BVLS_ENONFINITE, BVLS_ENOTSUP, BVLS_OK, BVLS_PREC_FP32,
+                    BVLS_EMAXITER, BVLS_ENONFINITE, BVLS_ENOTSUP, BVLS_OK, BVLS_PREC_FP32, BVLS_PREC_MIXED,
                     BVLS_PREC_FP32X2, DUAL_NAMES, STATUS_NAMES, bvls_default_opts, bvls_destroy,
                     bvls_backward, bvls_backward_default_opts, bvls_backward_info, bvls_backward_opts,
                     bvls_batch_info, bvls_info, bvls_last_error, bvls_opts, bvls_setup, bvls_solve,
@@ -56,7 +56,7 @@ def make_opts(tol=1e-6, screen_every=10, max_iter=100000, screening=True, precis
     o.screen_every = int(screen_every)
     o.max_iter = int(max_iter)
     o.screening = 1 if screening else 0
-    o.precision = {"fp32x2": BVLS_PREC_FP32X2, "fp32": BVLS_PREC_FP32}[precision]
+    o.precision = {"fp32x2": BVLS_PREC_FP32X2, "fp32": BVLS_PREC_FP32, "mixed": BVLS_PREC_MIXED}[precision]
     o.restart = 1 if restart else 0
     o.lipschitz = float(lipschitz)
     o.profile = 1 if profile else 0

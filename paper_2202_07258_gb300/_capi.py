@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "libbvls_gb300.so")
 BVLS_OK, BVLS_EINVAL, BVLS_ENOMEM, BVLS_ECUDA, BVLS_EMAXITER, BVLS_ENONFINITE, BVLS_ENOTSUP, BVLS_ETIMEOUT = range(8)
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EMAXITER", 5: "ENONFINITE", 6: "ENOTSUP",
                 7: "ETIMEOUT"}
-BVLS_PREC_FP32X2, BVLS_PREC_FP32 = 0, 1
+BVLS_PREC_FP32X2, BVLS_PREC_FP32, BVLS_PREC_MIXED = 0, 1, 2
 BVLS_ALG_FISTA, BVLS_ALG_CHAMBOLLE_POCK = 0, 1
 BVLS_DUAL_SCALING, BVLS_DUAL_TRANSLATION, BVLS_DUAL_ZERO = 0, 1, 2
 DUAL_NAMES = {0: "scaling", 1: "translation", 2: "zero"}

@@ -74,7 +74,7 @@ struct bvls_handle {
   int* pinned = nullptr;
   int fwd_tiles = 0, fwd_chunks = 0, tr_blocks = 0, red_blocks = 0;
   int pass_stages = 0, pass_qw = 0, pass_cps = 1;  // fused single-pass iteration when pass_stages > 0
-  double Cg[2] = {0, 0}, Cf[2] = {0, 0}, Csub = 0.0;
+  double Cg[3] = {0, 0, 0}, Cf[3] = {0, 0, 0}, Csub = 0.0;
   bool have_graph = false;
   GraphKey key{};
   cudaGraphExec_t exec = nullptr;
@@ -248,10 +248,10 @@ bvls_status validate_opts(const bvls_opts& o) {
   if (o.algorithm != BVLS_ALG_FISTA && o.algorithm != BVLS_ALG_CHAMBOLLE_POCK)
     return set_err(BVLS_EINVAL, "algorithm must be BVLS_ALG_FISTA or BVLS_ALG_CHAMBOLLE_POCK");
   if (!(o.tol >= 0.0) || o.screen_every < 1 || o.max_iter < 1 ||
-      (o.precision != BVLS_PREC_FP32X2 && o.precision != BVLS_PREC_FP32) ||
+      (o.precision != BVLS_PREC_FP32X2 && o.precision != BVLS_PREC_FP32 && o.precision != BVLS_PREC_MIXED) ||
       !(o.lipschitz >= 0.0) || !std::isfinite(o.lipschitz))
     return set_err(BVLS_EINVAL, "invalid options (tol >= 0, screen_every >= 1, max_iter >= 1, "
-                                "precision 0/1, lipschitz >= 0 finite)");
+                                "precision 0/1/2, lipschitz >= 0 finite)");
   return BVLS_OK;
 }
 
@@ -547,6 +547,8 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
     const int d = std::max(d_f, d_p);
     h->Cf[kX2] = 2.0 * (d + 2.0) * (d + 2.0) * kU * kU + 2.0 * kU * kU;
     h->Cf[kF32] = 1.01 * (d + 2.0) * kU + kU;
+    h->Cg[kMix] = h->Cg[kF32];
+    h->Cf[kMix] = h->Cf[kX2];
     h->Csub = 8.0 * kU * kU;
   }
   CK(cudaStreamSynchronize(h->s));

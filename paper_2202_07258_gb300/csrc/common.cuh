@@ -30,7 +30,9 @@ constexpr int kPassTmax = 8;      // float4 row chunks owned by one lane of a q 
 constexpr int kPassMaxStages = 32;
 
 enum DualMode { kScaling = 0, kTranslation = 1, kZero = 2 };
-enum Precision { kX2 = 0, kF32 = 1 };
+// kMix: float32 correlations a_j^T r, double-float forward product A_S x (the values of the
+// public BVLS_PREC_* constants)
+enum Precision { kX2 = 0, kF32 = 1, kMix = 2 };
 enum Algorithm { kFista = 0, kChambollePock = 1 };
 
 // Scalars of one solve, in device memory.  Written by the last block of a kernel (the

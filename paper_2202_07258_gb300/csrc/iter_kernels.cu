@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd(Params p, Buffers b, int sl
 cudaError_t launch_fwd(const Params& p, const Buffers& b, int slot, int precision, bool fold,
                        cudaStream_t s) {
   dim3 grid(p.fwd_tiles, p.fwd_chunks);
-  if (precision == kX2) {
+  if (precision != kF32) {   // kX2 and kMix: double-float forward product
     if (fold) k_fwd<kX2, true><<<grid, kFwdThreads, 0, s>>>(p, b, slot);
     else k_fwd<kX2, false><<<grid, kFwdThreads, 0, s>>>(p, b, slot);
   } else {

@@ -159,7 +159,8 @@ bvls_status bvls_solve_static(const float* A, int m, int n, int lda, const doubl
   bvls_default_opts(&o);
   if (opts) o = *opts;
   if (!(o.tol >= 0.0) || o.screen_every < 1 || o.max_iter < 1 ||
-      (o.precision != BVLS_PREC_FP32X2 && o.precision != BVLS_PREC_FP32) || !(o.lipschitz >= 0.0) ||
+      (o.precision != BVLS_PREC_FP32X2 && o.precision != BVLS_PREC_FP32 && o.precision != BVLS_PREC_MIXED) ||
+      !(o.lipschitz >= 0.0) ||
       !std::isfinite(o.lipschitz))
     return fail(BVLS_EINVAL, "invalid options");
   bool any_inf = false;
@@ -282,13 +283,10 @@ bvls_status bvls_solve_static(const float* A, int m, int n, int lda, const doubl
     const int per = (n + fwd_chunks - 1) / fwd_chunks;
     const int d_f0 = ((per + kFwdWarps - 1) / kFwdWarps + 1) / 2 + 4 + fwd_chunks + 1;
     const int d_f = std::max(d_f0, (n + sms - 1) / sms + (sms + 7) / 8 + 8);
-    if (o.precision == BVLS_PREC_FP32X2) {
-      p.Cg = 2.0 * (d_g + 2.0) * (d_g + 2.0) * kU * kU + 4.0 * kU * kU + 2.0 * kU64;
-      p.Cf = 2.0 * (d_f + 2.0) * (d_f + 2.0) * kU * kU + 2.0 * kU * kU;
-    } else {
-      p.Cg = 1.01 * (d_g + 2.0) * kU + kU;
-      p.Cf = 1.01 * (d_f + 2.0) * kU + kU;
-    }
+    p.Cg = o.precision == BVLS_PREC_FP32X2 ? 2.0 * (d_g + 2.0) * (d_g + 2.0) * kU * kU + 4.0 * kU * kU + 2.0 * kU64
+                                           : 1.01 * (d_g + 2.0) * kU + kU;
+    p.Cf = o.precision != BVLS_PREC_FP32 ? 2.0 * (d_f + 2.0) * (d_f + 2.0) * kU * kU + 2.0 * kU * kU
+                                         : 1.01 * (d_f + 2.0) * kU + kU;
     p.Csub = 8.0 * kU * kU;
   }
   const int K = o.screen_every;

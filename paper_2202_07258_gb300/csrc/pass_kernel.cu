@@ -72,6 +72,9 @@ __device__ __forceinline__ void pmerge(float& s, float& c, float s2, float c2) {
 template <int PREC, int QW, int QT>
 __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
     k_pass(Params p, Buffers b, int slot, int gap_iter, int nstages, int cps) {
+  // arithmetic of the two products: correlations a_j^T r_k (DP) and A_S x_{k+1} (QP)
+  constexpr int DP = PREC == kX2 ? kX2 : kF32;
+  constexpr int QP = PREC == kF32 ? kF32 : kX2;
   DevState* st = b.st;
   if (st->done) return;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -253,30 +256,30 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
 #pragma unroll 2
       for (int i = lane; i < m4q; i += 32) {
         const float4 h = srh[i], l = srl[i];
-        pacc4v<PREC>(sa, ca, colA[i], h, l);
-        pacc4v<PREC>(sb, cb, colB[i], h, l);
+        pacc4v<DP>(sa, ca, colA[i], h, l);
+        pacc4v<DP>(sb, cb, colB[i], h, l);
       }
-      pmerge<PREC>(sa[0], ca[0], sa[1], ca[1]);
-      pmerge<PREC>(sa[2], ca[2], sa[3], ca[3]);
-      pmerge<PREC>(sa[0], ca[0], sa[2], ca[2]);
-      pmerge<PREC>(sb[0], cb[0], sb[1], cb[1]);
-      pmerge<PREC>(sb[2], cb[2], sb[3], cb[3]);
-      pmerge<PREC>(sb[0], cb[0], sb[2], cb[2]);
+      pmerge<DP>(sa[0], ca[0], sa[1], ca[1]);
+      pmerge<DP>(sa[2], ca[2], sa[3], ca[3]);
+      pmerge<DP>(sa[0], ca[0], sa[2], ca[2]);
+      pmerge<DP>(sb[0], cb[0], sb[1], cb[1]);
+      pmerge<DP>(sb[2], cb[2], sb[3], cb[3]);
+      pmerge<DP>(sb[0], cb[0], sb[2], cb[2]);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         const float os = __shfl_xor_sync(0xffffffffu, sa[0], o);
         const float oc = __shfl_xor_sync(0xffffffffu, ca[0], o);
         const float ps = __shfl_xor_sync(0xffffffffu, sb[0], o);
         const float pc = __shfl_xor_sync(0xffffffffu, cb[0], o);
-        pmerge<PREC>(sa[0], ca[0], os, oc);
-        pmerge<PREC>(sb[0], cb[0], ps, pc);
+        pmerge<DP>(sa[0], ca[0], os, oc);
+        pmerge<DP>(sb[0], cb[0], ps, pc);
       }
       __syncwarp();
       if (lane < ncol) {
         const int c = c0 + lane;
         mbar_arrive(&empty[s]);  // this column's dot is done with the stage
-        const float2 g2 = lane == 0 ? df2_norm(sa[0], PREC == kX2 ? ca[0] : 0.0f)
-                                    : df2_norm(sb[0], PREC == kX2 ? cb[0] : 0.0f);
+        const float2 g2 = lane == 0 ? df2_norm(sa[0], DP == kX2 ? ca[0] : 0.0f)
+                                    : df2_norm(sb[0], DP == kX2 ? cb[0] : 0.0f);
         if (p.alg == kChambollePock) {
           // primal step of the primal-dual iteration: x_{k+1} = clip(x_k - tau a_j^T z),
           // and xbar = 2 x_{k+1} - x_k feeds the forward product
@@ -284,7 +287,7 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
           if (df2_lt(xnew, lj)) xnew = lj;
           if (df2_lt(uj, xnew)) xnew = uj;
           const float2 xbar = df2_sub(df2_add(xnew, xnew), xk);
-          sx[(size_t)s * cps + c] = PREC == kX2 ? xbar : make_float2(xbar.x, 0.0f);
+          sx[(size_t)s * cps + c] = QP == kX2 ? xbar : make_float2(xbar.x, 0.0f);
           mbar_arrive(&xready[s]);
           xn[j] = xnew;
           gc[j] = g2;
@@ -296,7 +299,7 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
         float2 xnew = df2_add(v, df2_mul(gv, p.invL2));
         if (df2_lt(xnew, lj)) xnew = lj;
         if (df2_lt(uj, xnew)) xnew = uj;
-        sx[(size_t)s * cps + c] = PREC == kX2 ? xnew : make_float2(xnew.x, 0.0f);
+        sx[(size_t)s * cps + c] = QP == kX2 ? xnew : make_float2(xnew.x, 0.0f);
         mbar_arrive(&xready[s]);
         xn[j] = xnew;
         gc[j] = g2;
@@ -343,7 +346,7 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
 #pragma unroll
           for (int t = 0; t < QT; ++t) {
             const int c4 = qw * 32 + lane + t * 32 * QW;
-            if (c4 < m4q) pacc4<PREC>(qs[t], qc[t], col[c4], xv.x, xv.y);
+            if (c4 < m4q) pacc4<QP>(qs[t], qc[t], col[c4], xv.x, xv.y);
           }
         }
       }
@@ -357,8 +360,8 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
       const int c4 = qw * 32 + lane + t * 32 * QW;
       if (c4 < m4q) {
         float4* dst = reinterpret_cast<float4*>(part + 4 * c4);
-        dst[0] = make_float4(qs[t][0], PREC == kX2 ? qc[t][0] : 0.f, qs[t][1], PREC == kX2 ? qc[t][1] : 0.f);
-        dst[1] = make_float4(qs[t][2], PREC == kX2 ? qc[t][2] : 0.f, qs[t][3], PREC == kX2 ? qc[t][3] : 0.f);
+        dst[0] = make_float4(qs[t][0], QP == kX2 ? qc[t][0] : 0.f, qs[t][1], QP == kX2 ? qc[t][1] : 0.f);
+        dst[1] = make_float4(qs[t][2], QP == kX2 ? qc[t][2] : 0.f, qs[t][3], QP == kX2 ? qc[t][3] : 0.f);
       }
     }
   }
@@ -521,8 +524,9 @@ size_t pass_smem_bytes(int lda, int m4, int nstages, int cps, int idx_cap) {
          (size_t)idx_cap * 4 + 64;
 }
 
-// Stage layout for the fused pass: about 32 KB of columns per stage (bulk copies much
-// smaller than that are dominated by their fixed cost) and as many stages as fit.
+// Stage layout for the fused pass: up to 64 KB and 8 columns per stage (bulk copies much
+// smaller than that are dominated by their fixed cost; measured on 2000-row columns, 8
+// columns per stage beat 4, 2 and 1) and as many stages as fit.
 // Returns the stage count (0 when the fused pass cannot be used) and the columns per stage.
 // Float4 row chunks per q-warp lane for m4 rows (1, 2, 4 or 8; 0 if too many rows).
 static int pass_qt(int m4) {
@@ -546,13 +550,14 @@ int pass_configure(int lda, int m4, int idx_cap, int smem_optin, int* qwarps, in
   const int qt = pass_qt(m4);
   if (qt == 0) return 0;
   const int col_bytes = lda * 4;
-  for (int cps = std::max(1, std::min(8, 32768 / col_bytes)); cps >= 1; --cps) {
+  for (int cps = std::max(1, std::min(8, 65536 / col_bytes)); cps >= 1; --cps) {
     int ns = kPassMaxStages;
     while (ns >= 3 && pass_smem_bytes(lda, m4, ns, cps, idx_cap) + 1024 > (size_t)smem_optin) --ns;
     if (ns < 3) continue;
     const int bytes = (int)pass_smem_bytes(lda, m4, ns, cps, idx_cap);
     cudaError_t e = pass_set_smem<kX2>(qt, bytes);
     if (e == cudaSuccess) e = pass_set_smem<kF32>(qt, bytes);
+    if (e == cudaSuccess) e = pass_set_smem<kMix>(qt, bytes);
     if (e != cudaSuccess) return 0;
     *qwarps = 8;
     *cps_out = cps;
@@ -567,26 +572,28 @@ static void pass_launch_t(const Params& p, const Buffers& b, int slot, int g, in
   k_pass<PREC, 8, QT><<<grid, 32 * (1 + kPassDot + 8), sm, s>>>(p, b, slot, g, nstages, cps);
 }
 
+template <int PREC>
+static void pass_launch_p(int qt, const Params& p, const Buffers& b, int slot, int g, int grid, int nstages, int cps,
+                          size_t sm, cudaStream_t s) {
+  switch (qt) {
+    case 1: pass_launch_t<PREC, 1>(p, b, slot, g, grid, nstages, cps, sm, s); break;
+    case 2: pass_launch_t<PREC, 2>(p, b, slot, g, grid, nstages, cps, sm, s); break;
+    case 4: pass_launch_t<PREC, 4>(p, b, slot, g, grid, nstages, cps, sm, s); break;
+    default: pass_launch_t<PREC, 8>(p, b, slot, g, grid, nstages, cps, sm, s); break;
+  }
+}
+
 cudaError_t launch_pass(const Params& p, const Buffers& b, int slot, int precision, bool gap_iter,
                         int grid, int nstages, int cps, int qwarps, cudaStream_t s) {
   const size_t sm = pass_smem_bytes(p.lda, p.m4, nstages, cps, (p.n + grid - 1) / grid);
   const int g = gap_iter ? 1 : 0;
   const int qt = pass_qt(p.m4);
   if (qwarps != 8 || qt == 0) return cudaErrorInvalidValue;
-  if (precision == kX2) {
-    switch (qt) {
-      case 1: pass_launch_t<kX2, 1>(p, b, slot, g, grid, nstages, cps, sm, s); break;
-      case 2: pass_launch_t<kX2, 2>(p, b, slot, g, grid, nstages, cps, sm, s); break;
-      case 4: pass_launch_t<kX2, 4>(p, b, slot, g, grid, nstages, cps, sm, s); break;
-      default: pass_launch_t<kX2, 8>(p, b, slot, g, grid, nstages, cps, sm, s); break;
-    }
-  } else {
-    switch (qt) {
-      case 1: pass_launch_t<kF32, 1>(p, b, slot, g, grid, nstages, cps, sm, s); break;
-      case 2: pass_launch_t<kF32, 2>(p, b, slot, g, grid, nstages, cps, sm, s); break;
-      case 4: pass_launch_t<kF32, 4>(p, b, slot, g, grid, nstages, cps, sm, s); break;
-      default: pass_launch_t<kF32, 8>(p, b, slot, g, grid, nstages, cps, sm, s); break;
-    }
+  switch (precision) {
+    case kX2: pass_launch_p<kX2>(qt, p, b, slot, g, grid, nstages, cps, sm, s); break;
+    case kF32: pass_launch_p<kF32>(qt, p, b, slot, g, grid, nstages, cps, sm, s); break;
+    case kMix: pass_launch_p<kMix>(qt, p, b, slot, g, grid, nstages, cps, sm, s); break;
+    default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }

@@ -44,6 +44,20 @@ def test_default_opts_host_only(lib):
     assert o.precision == _capi.BVLS_PREC_FP32X2 and o.restart == 1 and o.profile == 0
 
 
+def test_enum_constants_match_header():
+    """Every BVLS_* enumerator of the header has the same value in the Python binding."""
+    from paper_2202_07258_gb300 import _capi
+    txt = "".join(open(os.path.join(ROOT, "include", f)).read()
+                  for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h"))
+    consts = dict((k, int(v)) for k, v in re.findall(r"\b(BVLS_[A-Z0-9_]+)\s*=\s*(-?\d+)", txt))
+    for k in ("BVLS_PREC_FP32X2", "BVLS_PREC_FP32", "BVLS_PREC_MIXED", "BVLS_ALG_FISTA",
+              "BVLS_ALG_CHAMBOLLE_POCK", "BVLS_OK", "BVLS_EINVAL"):
+        assert k in consts and getattr(_capi, k) == consts[k], k
+    for k, v in consts.items():
+        if hasattr(_capi, k):
+            assert getattr(_capi, k) == v, k
+
+
 def test_setup_rejects_bad_sizes_before_touching_the_device(lib):
     from paper_2202_07258_gb300 import _capi
     buf = (ctypes.c_float * 4)()

@@ -167,6 +167,33 @@ def test_fp32_precision_mode(P):
     assert O.primal_objective(A, y, x) <= O.primal_objective(A, y, xs) + 3e-3
 
 
+def test_mixed_precision_mode(P):
+    """Float32 correlations with the double-float forward product.  With the zero dual point
+    (no interior direction) the certificate 1/2 (||r|| + E_r)^2 needs only the residual, so
+    the gap reaches the fp32x2 tolerance; with a scaled dual point the screens stay safe
+    under the float32 margins of the correlations."""
+    p = W.nnls_gaussian(400, 1200, 0.05, 0.01, 1)
+    A, y = _f64(p)
+    assert O.choose_translation(A, p.u) is None
+    for single_pass in (True, False):
+        x, scr, info, st = gpu_solve(P, p, tol=1e-7, precision="mixed", single_pass=single_pass)
+        assert st == P.BVLS_OK and info["dual"] == "zero" and info["gap"] < 1e-7
+        assert np.all(x >= 0) and O.primal_objective(A, y, x) <= info["gap"] * (1 + 1e-9)
+    q = W.bvls_table2(200, 500, 5)
+    A, y = _f64(q)
+    L = _L(A)
+    ref = O.solve(A, y, q.l, q.u, tol=1e-9, screen_every=10, L=L)
+    xs = certified_optimum(A, y, q.l, q.u, ref.x)
+    x, scr, info, st = gpu_solve(P, q, tol=3e-3, lipschitz=L, precision="mixed")
+    assert info["converged"] and info["gap"] < 3e-3
+    g = A.T @ (y - A @ xs)
+    assert np.all(g[scr == 1] < 0) and np.all(g[scr == 2] > 0)
+    assert np.all(np.abs(xs[scr == 1] - q.l[scr == 1]) <= 1e-12)
+    assert np.all(np.abs(xs[scr == 2] - q.u[scr == 2]) <= 1e-12)
+    Pg, Ps = O.primal_objective(A, y, x), O.primal_objective(A, y, xs)
+    assert Ps - 1e-12 <= Pg <= Ps + info["gap"] * (1 + 1e-9) + 1e-12
+
+
 def test_single_column_closed_form(P):
     rng = np.random.default_rng(0)
     for lo, hi in [(0.0, np.inf), (-0.3, 0.4), (0.0, 1.0)]:
