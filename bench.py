@@ -195,7 +195,16 @@ def roofline(solver, y_dev, m):
     from paper_2202_07258_gb300 import make_opts
     x, s, info, st = solver.solve(y_dev, opts=make_opts(tol=TOL, screen_every=K_SCREEN, profile=True))
     nl = max(1, info["tr_launches"])
-    if info["single_pass"]:
+    if info["single_pass"] == 2:
+        # persistent form: each launch runs K iterations (one read of A_S each) and their
+        # residuals r = y' - q
+        iters = nl * K_SCREEN
+        by = 4.0 * m * info["sum_preserved"] + iters * 8.0 * m + 60.0 * info["sum_preserved"] + iters * 32.0 * m
+        kern = {
+            "k_iters (K iterations per launch: A_S^T r, FISTA step, A_S x, r = y' - q)":
+                (info["tr_ms"], by, info["tr_launches"]),
+        }
+    elif info["single_pass"]:
         # one read of the preserved columns per iteration: A_S^T r_k, the step and A_S x_{k+1}
         pass_bytes = 4.0 * m * info["sum_preserved"] + nl * 8.0 * m + 60.0 * info["sum_preserved"]
         resid_bytes = nl * 32.0 * m        # q (f64) read + clear, y' and r (hi, lo)

@@ -107,7 +107,10 @@ typedef struct {
   int profile;        /* 1: launch without CUDA graphs and time every product kernel with
                          CUDA events (fills the *_ms fields of bvls_info) */
   int single_pass;    /* 1 (default): when m <= 8192, one streaming read of the preserved
-                         columns per iteration yields both products; 0: two passes
+                         columns per iteration yields both products, and the K iterations
+                         between two gap evaluations run in one persistent (cooperative)
+                         launch when its shape fits one CTA per SM; 2: the same single pass
+                         with two launches per iteration (pass, residual); 0: two passes
                          (A_S x_S, then A_S^T r), the form used for larger m */
   const double* dual_point; /* any; m doubles or NULL (default).  A fixed dual point used by
                          every screening step of bvls_solve in place of Theta(x_k): the
@@ -133,14 +136,17 @@ typedef struct {
   double sum_preserved; /* sum over iterations of |preserved set|: columns read by A_S^T r */
   double sum_nonzero;   /* sum over iterations of the preserved x_j != 0: columns read by
                            A_S x_S (zero coordinates contribute nothing and are skipped) */
-  double fwd_ms, tr_ms; /* profile mode, total kernel time.  Fused single-pass iteration
-                           (m <= 8192): tr_ms = the pass that reads A_S once for both products,
-                           fwd_ms = the residual kernel r = y' - q.  Two-pass iteration:
-                           fwd_ms = A_S x_S, tr_ms = A_S^T r. */
+  double fwd_ms, tr_ms; /* profile mode, total kernel time.  Persistent single pass: tr_ms =
+                           the launches that run K iterations each (tr_launches of them),
+                           fwd_ms = 0.  Single pass with two launches per iteration: tr_ms =
+                           the pass that reads A_S once for both products, fwd_ms = the
+                           residual kernel r = y' - q.  Two-pass iteration: fwd_ms = A_S x_S,
+                           tr_ms = A_S^T r. */
   int fwd_launches, tr_launches;
   double kernel_launches; /* kernels this call launched (including ones that found the solve
                              already stopped and returned at entry) */
-  int single_pass;        /* 1 when the iterations read A_S once each (see bvls_opts) */
+  int single_pass;        /* form of the iterations (see bvls_opts): 0 two passes, 1 single pass
+                             with two launches per iteration, 2 single pass, persistent */
 } bvls_info;
 
 /* Fill *opts with the defaults: tol 1e-6, screen_every 10, max_iter 100000, screening 1,

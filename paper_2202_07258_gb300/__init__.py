@@ -60,7 +60,7 @@ def make_opts(tol=1e-6, screen_every=10, max_iter=100000, screening=True, precis
     o.restart = 1 if restart else 0
     o.lipschitz = float(lipschitz)
     o.profile = 1 if profile else 0
-    o.single_pass = 1 if single_pass else 0
+    o.single_pass = int(single_pass)   # 0 two passes, 1 single pass (persistent), 2 single pass, two launches
     o.algorithm = {"fista": _capi.BVLS_ALG_FISTA, "cp": _capi.BVLS_ALG_CHAMBOLLE_POCK,
                    "chambolle_pock": _capi.BVLS_ALG_CHAMBOLLE_POCK}[algorithm]
     return o

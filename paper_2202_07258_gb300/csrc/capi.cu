@@ -74,6 +74,7 @@ struct bvls_handle {
   int* pinned = nullptr;
   int fwd_tiles = 0, fwd_chunks = 0, tr_blocks = 0, red_blocks = 0;
   int pass_stages = 0, pass_qw = 0, pass_cps = 1;  // fused single-pass iteration when pass_stages > 0
+  bool pass_coop = false;                           // its persistent (cooperative) launch fits
   double Cg[3] = {0, 0, 0}, Cf[3] = {0, 0, 0}, Csub = 0.0;
   bool have_graph = false;
   GraphKey key{};
@@ -199,12 +200,38 @@ Params make_params(const bvls_handle* h, const bvls_opts& o, int max_iter) {
   return p;
 }
 
+// The single-pass iterations run as persistent launches (K iterations each).
+bool persistent_form(const bvls_handle* h, const bvls_opts& o) {
+  return h->pass_stages > 0 && h->pass_coop && o.single_pass == 1;
+}
+
 // Enqueue chunk_len iterations (the chunk starts at an even k, so slot = j & 1).
 // With ev != nullptr, records ev[3j], ev[3j+1], ev[3j+2] around the two products.
 cudaError_t enqueue_chunk(bvls_handle* h, const Params& p, const bvls_opts& o, int chunk_len,
                           cudaEvent_t* ev) {
   const bool scr = o.screening && h->dual_mode != kZero;
   cudaError_t e = cudaSuccess;
+  if (persistent_form(h, o)) {
+    // one cooperative launch per K iterations (ending at a gap iteration), then the gap
+    // evaluation and the screening step; with ev: ev[3 b] and ev[3 b + 1] around launch b
+    const int K = o.screen_every;
+    for (int j0 = 0, blk = 0; j0 < chunk_len && e == cudaSuccess; j0 += K, ++blk) {
+      const int slot = j0 & 1;
+      const int last = (j0 + K - 1) & 1;
+      if (ev) cudaEventRecordWithFlags(ev[3 * blk], h->s, cudaEventRecordExternal);
+      e = launch_iters(p, h->b, slot, K, true, o.precision, h->num_sms, h->pass_stages, h->pass_cps, h->pass_qw,
+                       h->s);
+      if (e != cudaSuccess) break;
+      if (ev) cudaEventRecordWithFlags(ev[3 * blk + 1], h->s, cudaEventRecordExternal);
+      e = launch_gap(p, h->b, last, !scr, h->red_blocks, h->s);
+      if (e == cudaSuccess && scr) {
+        e = launch_test(p, h->b, last, h->red_blocks, h->s);
+        if (e == cudaSuccess) e = launch_compact(p, h->b, last, h->s);
+        if (e == cudaSuccess) e = launch_fwd(p, h->b, last, o.precision, true, h->s);
+      }
+    }
+    return e;
+  }
   for (int j = 0; j < chunk_len && e == cudaSuccess; ++j) {
     const int slot = j & 1;
     const bool gap_iter = ((j + 1) % o.screen_every) == 0;
@@ -252,6 +279,7 @@ bvls_status validate_opts(const bvls_opts& o) {
       !(o.lipschitz >= 0.0) || !std::isfinite(o.lipschitz))
     return set_err(BVLS_EINVAL, "invalid options (tol >= 0, screen_every >= 1, max_iter >= 1, "
                                 "precision 0/1/2, lipschitz >= 0 finite)");
+  if (o.single_pass < 0 || o.single_pass > 2) return set_err(BVLS_EINVAL, "single_pass must be 0, 1 or 2");
   return BVLS_OK;
 }
 
@@ -494,6 +522,9 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     h->pass_stages = pass_configure(h->lda, h->m4, (n + h->num_sms - 1) / h->num_sms, optin, &h->pass_qw,
                                     &h->pass_cps);
+    h->pass_coop = h->pass_stages > 0 &&
+                   iters_configure(h->lda, h->m4, h->pass_stages, h->pass_cps, (n + h->num_sms - 1) / h->num_sms,
+                                   h->num_sms);
     cudaGetLastError();
   }
   h->tr_blocks = h->num_sms * std::max(1, std::min(bps, 2));
@@ -524,10 +555,12 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
   TRY(dalloc(h, &b.blk, 4 * (size_t)max_blocks));
   TRY(dalloc(h, &b.st, 1));
   TRY(dalloc(h, &b.qpart, (size_t)h->num_sms * h->m4));
+  TRY(dalloc(h, &b.gbar, 2));
   TRY(dalloc(h, &b.xout, n));
   TRY(dalloc(h, &h->y_dev, h->m4));
   TRY(dalloc(h, &h->x0_dev, n));
   CK(cudaMemsetAsync(b.tile_cnt, 0, sizeof(unsigned) * h->fwd_tiles, h->s));
+  CK(cudaMemsetAsync(b.gbar, 0, 2 * sizeof(unsigned), h->s));
   CK(cudaMemsetAsync(b.st, 0, sizeof(DevState), h->s));
   CK(cudaMemsetAsync(h->y_dev, 0, sizeof(float) * h->m4, h->s));
   b.y_in = h->y_dev;
@@ -618,7 +651,8 @@ bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const b
 
   const long long max_chunks = (max_iter + chunk - 1) / chunk + 1;
   const bool scr = o.screening && h->dual_mode != kZero;
-  const long long per_chunk = 2LL * chunk + (long long)(chunk / K) * (scr ? 4 : 1);
+  const bool pers = persistent_form(h, o);
+  const long long per_chunk = (pers ? 0LL : 2LL * chunk) + (long long)(chunk / K) * ((scr ? 4 : 1) + (pers ? 1 : 0));
   long long chunks_run = 0;
   double fwd_ms = 0.0, tr_ms = 0.0;
   int fwd_launches = 0, tr_launches = 0;
@@ -653,15 +687,24 @@ bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const b
         break;
       }
       const int ran = std::min(chunk, hs.k - k_before);
-      for (int j = 0; j < ran; ++j) {
-        float a = 0.f, b2 = 0.f;
-        CK(cudaEventElapsedTime(&a, h->prof[3 * j], h->prof[3 * j + 1]));
-        CK(cudaEventElapsedTime(&b2, h->prof[3 * j + 1], h->prof[3 * j + 2]));
-        tr_ms += fused ? a : b2;
-        fwd_ms += fused ? b2 : a;
+      if (pers) {
+        for (int blk = 0; blk < ran / K; ++blk) {   // launches that ran their K iterations
+          float a = 0.f;
+          CK(cudaEventElapsedTime(&a, h->prof[3 * blk], h->prof[3 * blk + 1]));
+          tr_ms += a;
+          ++tr_launches;
+        }
+      } else {
+        for (int j = 0; j < ran; ++j) {
+          float a = 0.f, b2 = 0.f;
+          CK(cudaEventElapsedTime(&a, h->prof[3 * j], h->prof[3 * j + 1]));
+          CK(cudaEventElapsedTime(&b2, h->prof[3 * j + 1], h->prof[3 * j + 2]));
+          tr_ms += fused ? a : b2;
+          fwd_ms += fused ? b2 : a;
+        }
+        fwd_launches += ran;
+        tr_launches += ran;
       }
-      fwd_launches += ran;
-      tr_launches += ran;
       k_before = hs.k;
       if (hs.done) break;
     }
@@ -737,7 +780,7 @@ bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const b
     info->tr_launches = tr_launches;
     const double chunks_done = chunks_run >= 0 ? (double)chunks_run : (double)hs.chunks;
     info->kernel_launches = (fused ? 3.0 : 2.0) + chunks_done * (double)(per_chunk + (chunks_run >= 0 ? 0 : 1));
-    info->single_pass = fused ? 1 : 0;
+    info->single_pass = fused ? (pers ? 2 : 1) : 0;
   }
   if (!hs.done) return set_err(BVLS_EMAXITER, "stopped after %lld chunks without the stop flag", max_chunks);
   if (!hs.converged) return set_err(BVLS_EMAXITER, "gap %.3e >= tol after %d iterations", hs.gap, hs.k);

@@ -252,6 +252,7 @@ struct Buffers {
   unsigned int* tile_cnt;
   double* blk;            // per-block partials of the epilogue kernels (4 doubles each)
   float2* qpart;          // fused pass: per-CTA double-float partials of A_S x_S (grid x m4)
+  unsigned int* gbar;     // persistent pass: grid barrier (arrival count, generation)
   double* xout;           // float64 copy of the returned iterate (n)
   DevState* st;
   const float* y_in;      // device copy of y
@@ -276,6 +277,12 @@ int pass_configure(int lda, int m4, int idx_cap, int smem_optin, int* qwarps, in
 cudaError_t launch_pass(const Params& p, const Buffers& b, int slot, int precision, bool gap_iter,
                         int grid, int nstages, int cps, int qwarps, cudaStream_t s);
 cudaError_t launch_resid(const Params& p, const Buffers& b, int slot, int nparts, cudaStream_t s);
+// Persistent form: niter iterations (the last one a gap iteration when gap_last) in one
+// cooperative launch of grid CTAs; same outputs as niter x (launch_pass + launch_resid).
+// iters_configure returns true when the launch shape fits one CTA per SM.
+bool iters_configure(int lda, int m4, int nstages, int cps, int idx_cap, int grid);
+cudaError_t launch_iters(const Params& p, const Buffers& b, int slot0, int niter, bool gap_last, int precision,
+                         int grid, int nstages, int cps, int qwarps, cudaStream_t s);
 cudaError_t launch_export(const Params& p, const Buffers& b, int slot, cudaStream_t s);
 // primal-dual start: r_0 (in rh / rl from the forward kernel) moves to crh / crl and
 // z_1 = A x_0 - y' = -r_0 takes its place

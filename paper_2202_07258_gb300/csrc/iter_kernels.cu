@@ -138,6 +138,7 @@ __global__ void k_init_state(Params p, Buffers b) {
     st->sum_active = 0.0;
     st->sum_nnz = 0.0;
     st->cnt_tr = st->cnt_gap = st->cnt_fwd = st->cnt_resid = 0u;
+    if (b.gbar) b.gbar[0] = 0u;   // arrivals; the generation only ever advances
   }
 }
 

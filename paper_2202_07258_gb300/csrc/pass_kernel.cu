@@ -67,6 +67,67 @@ __device__ __forceinline__ void pmerge(float& s, float& c, float s2, float c2) {
   else s += s2;
 }
 
+// a_j^T r for the two columns of a work unit (colB == colA when the unit holds one column),
+// r staged in shared memory as (hi, lo) float4 rows; double-float (DP == kX2) or float32
+// accumulation.  Every lane returns both sums.
+template <int DP>
+__device__ __forceinline__ void dot_pair(const float4* colA, const float4* colB, const float4* srh,
+                                         const float4* srl, int m4q, int lane, float2& ga, float2& gb) {
+  float sa[4] = {0.f, 0.f, 0.f, 0.f}, ca[4] = {0.f, 0.f, 0.f, 0.f};
+  float sb[4] = {0.f, 0.f, 0.f, 0.f}, cb[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 2
+  for (int i = lane; i < m4q; i += 32) {
+    const float4 h = srh[i], l = srl[i];
+    pacc4v<DP>(sa, ca, colA[i], h, l);
+    pacc4v<DP>(sb, cb, colB[i], h, l);
+  }
+  pmerge<DP>(sa[0], ca[0], sa[1], ca[1]);
+  pmerge<DP>(sa[2], ca[2], sa[3], ca[3]);
+  pmerge<DP>(sa[0], ca[0], sa[2], ca[2]);
+  pmerge<DP>(sb[0], cb[0], sb[1], cb[1]);
+  pmerge<DP>(sb[2], cb[2], sb[3], cb[3]);
+  pmerge<DP>(sb[0], cb[0], sb[2], cb[2]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float os = __shfl_xor_sync(0xffffffffu, sa[0], o);
+    const float oc = __shfl_xor_sync(0xffffffffu, ca[0], o);
+    const float ps = __shfl_xor_sync(0xffffffffu, sb[0], o);
+    const float pc = __shfl_xor_sync(0xffffffffu, cb[0], o);
+    pmerge<DP>(sa[0], ca[0], os, oc);
+    pmerge<DP>(sb[0], cb[0], ps, pc);
+  }
+  ga = df2_norm(sa[0], DP == kX2 ? ca[0] : 0.0f);
+  gb = df2_norm(sb[0], DP == kX2 ? cb[0] : 0.0f);
+}
+
+__device__ __forceinline__ float2 clip2(float2 x, float2 lj, float2 uj) {
+  if (df2_lt(x, lj)) x = lj;
+  if (df2_lt(uj, x)) x = uj;
+  return x;
+}
+
+// One coordinate's step from g2 = a_j^T r_k, in double-float arithmetic (no float64 on this
+// path).  FISTA: x_{k+1} = clip(v + g_v / L), v = x_k + beta (x_k - x_{k-1}),
+// g_v = (1 + beta) g_k - beta g_{k-1} = a_j^T (y' - A v_k); the forward product takes x_{k+1}
+// and *dotc is the restart-test term g_v (x_{k+1} - x_k).  Primal-dual: x_{k+1} =
+// clip(x_k - tau a_j^T z) and the forward product takes xbar = 2 x_{k+1} - x_k.
+__device__ __forceinline__ float2 coord_step(const Params& p, float2 g2, float2 xk, float2 xp, float2 gpv,
+                                             float2 lj, float2 uj, float2 bb, float2 onepb, float2& xfwd,
+                                             float2& dotc) {
+  if (p.alg == kChambollePock) {
+    const float2 xnew = clip2(df2_sub(xk, df2_mul(g2, p.tau2)), lj, uj);
+    xfwd = df2_sub(df2_add(xnew, xnew), xk);
+    dotc = make_float2(0.f, 0.f);
+    return xnew;
+  }
+  const float2 gv = df2_sub(df2_mul(onepb, g2), df2_mul(bb, gpv));
+  const float2 v = df2_add(xk, df2_mul(bb, df2_sub(xk, xp)));
+  const float2 xnew = clip2(df2_add(v, df2_mul(gv, p.invL2)), lj, uj);
+  xfwd = xnew;
+  dotc = df2_mul(gv, df2_sub(xnew, xk));
+  return xnew;
+}
+
 }  // namespace
 
 template <int PREC, int QW, int QT>
@@ -251,59 +312,21 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
       const float* sbase = stages + (size_t)s * stage_floats + (size_t)c0 * p.lda;
       const float4* colA = reinterpret_cast<const float4*>(sbase);
       const float4* colB = reinterpret_cast<const float4*>(sbase + (ncol > 1 ? p.lda : 0));
-      float sa[4] = {0.f, 0.f, 0.f, 0.f}, ca[4] = {0.f, 0.f, 0.f, 0.f};
-      float sb[4] = {0.f, 0.f, 0.f, 0.f}, cb[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 2
-      for (int i = lane; i < m4q; i += 32) {
-        const float4 h = srh[i], l = srl[i];
-        pacc4v<DP>(sa, ca, colA[i], h, l);
-        pacc4v<DP>(sb, cb, colB[i], h, l);
-      }
-      pmerge<DP>(sa[0], ca[0], sa[1], ca[1]);
-      pmerge<DP>(sa[2], ca[2], sa[3], ca[3]);
-      pmerge<DP>(sa[0], ca[0], sa[2], ca[2]);
-      pmerge<DP>(sb[0], cb[0], sb[1], cb[1]);
-      pmerge<DP>(sb[2], cb[2], sb[3], cb[3]);
-      pmerge<DP>(sb[0], cb[0], sb[2], cb[2]);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float os = __shfl_xor_sync(0xffffffffu, sa[0], o);
-        const float oc = __shfl_xor_sync(0xffffffffu, ca[0], o);
-        const float ps = __shfl_xor_sync(0xffffffffu, sb[0], o);
-        const float pc = __shfl_xor_sync(0xffffffffu, cb[0], o);
-        pmerge<DP>(sa[0], ca[0], os, oc);
-        pmerge<DP>(sb[0], cb[0], ps, pc);
-      }
+      float2 ga, gb;
+      dot_pair<DP>(colA, colB, srh, srl, m4q, lane, ga, gb);
       __syncwarp();
       if (lane < ncol) {
         const int c = c0 + lane;
         mbar_arrive(&empty[s]);  // this column's dot is done with the stage
-        const float2 g2 = lane == 0 ? df2_norm(sa[0], DP == kX2 ? ca[0] : 0.0f)
-                                    : df2_norm(sb[0], DP == kX2 ? cb[0] : 0.0f);
-        if (p.alg == kChambollePock) {
-          // primal step of the primal-dual iteration: x_{k+1} = clip(x_k - tau a_j^T z),
-          // and xbar = 2 x_{k+1} - x_k feeds the forward product
-          float2 xnew = df2_sub(xk, df2_mul(g2, p.tau2));
-          if (df2_lt(xnew, lj)) xnew = lj;
-          if (df2_lt(uj, xnew)) xnew = uj;
-          const float2 xbar = df2_sub(df2_add(xnew, xnew), xk);
-          sx[(size_t)s * cps + c] = QP == kX2 ? xbar : make_float2(xbar.x, 0.0f);
-          mbar_arrive(&xready[s]);
-          xn[j] = xnew;
-          gc[j] = g2;
-          continue;
-        }
-        // FISTA step in double-float arithmetic (no float64 on this path)
-        const float2 gv = df2_sub(df2_mul(onepb, g2), df2_mul(bb, gpv));   // a_j^T (y' - A v_k)
-        const float2 v = df2_add(xk, df2_mul(bb, df2_sub(xk, xp)));
-        float2 xnew = df2_add(v, df2_mul(gv, p.invL2));
-        if (df2_lt(xnew, lj)) xnew = lj;
-        if (df2_lt(uj, xnew)) xnew = uj;
-        sx[(size_t)s * cps + c] = QP == kX2 ? xnew : make_float2(xnew.x, 0.0f);
+        const float2 g2 = lane == 0 ? ga : gb;
+        float2 xf, dc;
+        const float2 xnew = coord_step(p, g2, xk, xp, gpv, lj, uj, bb, onepb, xf, dc);
+        sx[(size_t)s * cps + c] = QP == kX2 ? xf : make_float2(xf.x, 0.0f);
         mbar_arrive(&xready[s]);
         xn[j] = xnew;
         gc[j] = g2;
-        dot = df2_add(dot, df2_mul(gv, df2_sub(xnew, xk)));
+        if (p.alg == kChambollePock) continue;
+        dot = df2_add(dot, dc);
         if (want_eps && inf_j && nr > 0.0) {
           const double den = -wj - p.gamma_w * nr * p.t_norm;
           epsm = fmax(epsm, fmax(df2_to_double(g2) + eta_g * nr, 0.0) / den);
@@ -497,6 +520,458 @@ __global__ void __launch_bounds__(256) k_resid(Params p, Buffers b, int slot, in
   }
 }
 
+// ------------------------------------------------------------------ persistent form
+// k_iters runs `niter` consecutive iterations (those between two gap evaluations) in one
+// cooperative launch: one CTA per SM, every CTA co-resident.  Each iteration is
+//   pass       as k_pass: the CTA's preserved columns stream through the stage ring once,
+//              giving a_j^T r_k, the step, and the CTA's partial of A_S x_{k+1};
+//   barrier    grid-wide;
+//   residual   as k_resid, the rows split into 32-row slices over the CTAs: r_{k+1} and
+//              the slice partials of P_{k+1}; every CTA also reduces the per-CTA restart
+//              terms itself (same order everywhere, so all CTAs hold the same t_{k+1});
+//   barrier    grid-wide.
+// The producer warp takes no part in the barriers: it walks the column groups of all
+// `niter` iterations, so the first stages of iteration k+1 load while the grid finishes
+// iteration k.  The outputs after the last iteration are those of k_pass + k_resid.
+
+namespace {
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Named barrier 1 over the CTA's consumer warps (all warps but the producer).
+template <int NCONS>
+__device__ __forceinline__ void consumer_sync() {
+  asm volatile("bar.sync 1, %0;" ::"r"(NCONS) : "memory");
+}
+
+// One arrival of this CTA at the grid barrier (gb[0] arrivals, gb[1] generation) and a
+// bounded wait for the others; called by one thread after the CTA's consumers synchronised.
+// The last arrival resets the count and then publishes the next generation.
+__device__ bool grid_arrive_wait(unsigned* gb, unsigned nblocks, unsigned gen) {
+  __threadfence();
+  const unsigned prev = atomicAdd(&gb[0], 1u);
+  if (prev == nblocks - 1) {
+    atomicExch(&gb[0], 0u);
+    __threadfence();
+    atomicAdd(&gb[1], 1u);
+    return true;
+  }
+  if (ld_acquire_u32(&gb[1]) != gen) return true;
+  const long long t0 = clock64();
+  while (ld_acquire_u32(&gb[1]) == gen) {
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+  __threadfence();
+  return true;
+}
+
+}  // namespace
+
+template <int PREC, int QW, int QT>
+__global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
+    k_iters(Params p, Buffers b, int slot0, int niter, int gap_last, int nstages, int cps) {
+  constexpr int DP = PREC == kX2 ? kX2 : kF32;
+  constexpr int QP = PREC == kF32 ? kF32 : kX2;
+  constexpr int NW = kPassDot + QW;          // consumer warps
+  constexpr int NCONS = 32 * NW;
+  DevState* st = b.st;
+  if (st->done) return;                      // fixed for the whole launch
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int m4q = p.m4 >> 2;
+  const uint32_t col_bytes = (uint32_t)p.lda * 4u;
+  const size_t stage_floats = (size_t)cps * p.lda;
+  float* stages = reinterpret_cast<float*>(smem);
+  float4* srh = reinterpret_cast<float4*>(smem + (size_t)nstages * stage_floats * 4);
+  float4* srl = srh + m4q;
+  float2* sx = reinterpret_cast<float2*>(srl + m4q);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sx + (size_t)nstages * cps);
+  uint64_t* xready = full + nstages;
+  uint64_t* empty = xready + nstages;
+  volatile int* s_issued = reinterpret_cast<volatile int*>(empty + nstages);
+  int* sidx = const_cast<int*>(s_issued) + nstages;
+  __shared__ float2 s_dot[kPassDot];
+  __shared__ double s_eps[kPassDot];
+  __shared__ double s_scal[3];
+  __shared__ float2 s_beta2[2];
+  __shared__ double s_t;
+  __shared__ int s_err, s_ok;
+  __shared__ double s_th[NW];
+  __shared__ float2 s_red[NW][32];
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_act = st->n_active;
+  const int k0 = st->k;
+  const int per = (n_act + gridDim.x - 1) / gridDim.x;
+  const int p0 = min(n_act, (int)blockIdx.x * per);
+  const int nq = min(n_act, p0 + per) - p0;
+  const int ngroups = (nq + cps - 1) / cps;
+  const int nslices = (p.m4 + 31) / 32;
+  const int nparts = gridDim.x;
+
+  unsigned gen = 0;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < nstages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&xready[s], cps);
+      mbar_init(&empty[s], cps + QW);
+      s_issued[s] = 0;
+    }
+    fence_barrier_init();
+    s_err = 0;
+    s_ok = 1;
+    s_t = st->t;
+  }
+  if (threadIdx.x == 32) gen = ld_acquire_u32(&b.gbar[1]);   // before this CTA's first arrival
+  for (int q = threadIdx.x; q < nq; q += blockDim.x) sidx[q] = b.idx[p0 + q];
+  __syncthreads();
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- producer
+    // Global group gg = it * ngroups + g goes to stage gg % nstages (use gg / nstages).
+    if (lane == 0) {
+      const int total = niter * ngroups;
+      int issued = 0;
+      for (int gg = 0; gg < total; ++gg) {
+        const int g = gg - (gg / ngroups) * ngroups;
+        const int s = gg % nstages;
+        const int u = gg / nstages;
+        if (u > 0 && !mbar_wait(&empty[s], (u - 1) & 1)) {
+          s_err = 1;
+          break;
+        }
+        const int q0 = g * cps;
+        const int nc = min(cps, nq - q0);
+        mbar_arrive_expect_tx(&full[s], (uint32_t)nc * col_bytes);
+        float* dst = stages + (size_t)s * stage_floats;
+        int c = 0;
+        while (c < nc) {
+          int len = 1;
+          while (c + len < nc && sidx[q0 + c + len] == sidx[q0 + c] + len) ++len;
+          bulk_g2s(dst + (size_t)c * p.lda, p.A + (size_t)sidx[q0 + c] * p.lda, (uint32_t)len * col_bytes,
+                   &full[s]);
+          c += len;
+        }
+        for (int k = nc; k < cps; ++k) {
+          mbar_arrive(&xready[s]);
+          mbar_arrive(&empty[s]);
+        }
+        s_issued[s] = u + 1;
+        issued = gg + 1;
+      }
+      for (int gg = max(0, issued - nstages); gg < issued; ++gg)
+        if (!mbar_wait(&full[gg % nstages], (gg / nstages) & 1)) s_err = 1;
+      if (s_err) atomicOr(&st->error, 1);
+    }
+    return;
+  }
+
+  // -------------------------------------------------------------------- consumers
+  const int wi = warp - 1;
+  const int ct = threadIdx.x - 32;
+  for (int it = 0; it < niter; ++it) {
+    const int slot = (slot0 + it) & 1;
+    const int gap_iter = gap_last && it == niter - 1;
+    const int k = k0 + it;
+    // prologue: P_k, the momentum scalars and r_k in shared memory
+    if (warp == 1) {
+      const double Pk = k > 0 ? warp_load_sum(b.tileR, nslices) : st->P[slot];
+      if (lane == 0) {
+        if (blockIdx.x == 0) st->P[slot] = Pk;
+        const double tk = s_t;
+        const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk * tk));
+        const double beta = (tk - 1.0) / tn;
+        s_scal[0] = beta;
+        s_scal[1] = tn;
+        s_scal[2] = p.Cg * sqrt(2.0 * Pk) * (1.0 + 1e-6);
+        s_beta2[0] = df2_from_double(beta);
+        s_beta2[1] = df2_from_double(1.0 + beta);
+      }
+    }
+    for (int i = ct; i < m4q; i += NCONS) {
+      srh[i] = __ldcg(reinterpret_cast<const float4*>(b.rh) + i);
+      srl[i] = __ldcg(reinterpret_cast<const float4*>(b.rl) + i);
+    }
+    if (gap_iter && p.wstar && blockIdx.x == 0) {
+      double acc = 0.0;
+      for (int i = ct; i < p.m; i += NCONS) {
+        const double d = p.theta[i] + p.eps_star * p.tvec[i] - ((double)__ldcg(b.rh + i) + (double)__ldcg(b.rl + i));
+        acc += d * d;
+      }
+      acc = warp_sum_d(acc);
+      if (lane == 0) s_th[wi] = acc;
+      consumer_sync<NCONS>();
+      if (ct == 0) {
+        double t2 = 0.0;
+        for (int w = 0; w < NW; ++w) t2 += s_th[w];
+        st->theta_r2 = t2;
+      }
+    }
+    consumer_sync<NCONS>();
+    const double tn = s_scal[1];
+
+    if (warp <= kPassDot) {
+      // ------------------------------------------------------------ dot warps
+      const int dw = warp - 1;
+      const double eta_g = s_scal[2];
+      const float2 bb = s_beta2[0], onepb = s_beta2[1];
+      const bool want_eps = gap_iter && p.dual_mode == kTranslation && !p.wstar;
+      const float2* xc = b.x[slot];
+      float2* xn = b.x[slot ^ 1];
+      const float2* gp = b.g[slot ^ 1];
+      float2* gc = b.g[slot];
+      float2 dot = make_float2(0.f, 0.f);
+      double epsm = 0.0;
+      const int U = (cps % 2 == 0) ? 2 : 1;
+      for (int w = dw; w * U < nq; w += kPassDot) {
+        const int q0 = w * U;
+        const int ncol = min(U, nq - q0);
+        const int g = q0 / cps;
+        const int gg = it * ngroups + g;
+        const int s = gg % nstages;
+        const int u = gg / nstages;
+        const int c0 = q0 - g * cps;
+        const int e = lane < ncol ? lane : 0;
+        const int j = sidx[q0 + e];
+        float2 xk = make_float2(0.f, 0.f), xp = xk, gpv = xk, lj = xk, uj = xk;
+        double nr = 0.0, wj = 0.0;
+        int inf_j = 0;
+        if (lane < ncol) {
+          // written by this CTA in the previous iteration: read through L2, not L1
+          xk = __ldcg(xc + j);
+          xp = __ldcg(xn + j);
+          gpv = __ldcg(gp + j);
+          lj = p.l2[j];
+          uj = p.u2[j];
+          if (want_eps) {
+            nr = p.nrm[j];
+            wj = p.w[j];
+            inf_j = p.jinf[j];
+          }
+        }
+        if (!warp_all(smem_wait_geq(&s_issued[s], u + 1) && mbar_wait(&full[s], u & 1))) {
+          s_err = 1;
+          break;
+        }
+        const float* sbase = stages + (size_t)s * stage_floats + (size_t)c0 * p.lda;
+        const float4* colA = reinterpret_cast<const float4*>(sbase);
+        const float4* colB = reinterpret_cast<const float4*>(sbase + (ncol > 1 ? p.lda : 0));
+        float2 ga, gb2;
+        dot_pair<DP>(colA, colB, srh, srl, m4q, lane, ga, gb2);
+        __syncwarp();
+        if (lane < ncol) {
+          const int c = c0 + lane;
+          mbar_arrive(&empty[s]);
+          const float2 g2 = lane == 0 ? ga : gb2;
+          float2 xf, dc;
+          const float2 xnew = coord_step(p, g2, xk, xp, gpv, lj, uj, bb, onepb, xf, dc);
+          sx[(size_t)s * cps + c] = QP == kX2 ? xf : make_float2(xf.x, 0.0f);
+          mbar_arrive(&xready[s]);
+          __stcg(xn + j, xnew);
+          __stcg(gc + j, g2);
+          if (p.alg == kChambollePock) continue;
+          dot = df2_add(dot, dc);
+          if (want_eps && inf_j && nr > 0.0) {
+            const double den = -wj - p.gamma_w * nr * p.t_norm;
+            epsm = fmax(epsm, fmax(df2_to_double(g2) + eta_g * nr, 0.0) / den);
+          }
+        }
+      }
+      {
+        const float2 o = make_float2(__shfl_down_sync(0xffffffffu, dot.x, 1), __shfl_down_sync(0xffffffffu, dot.y, 1));
+        const double oe = __shfl_down_sync(0xffffffffu, epsm, 1);
+        if (lane == 0) {
+          dot = df2_add(dot, o);
+          epsm = fmax(epsm, oe);
+        }
+      }
+      if (lane == 0) {
+        s_dot[dw] = dot;
+        s_eps[dw] = epsm;
+      }
+    } else {
+      // ------------------------------------------------------------ q warps
+      const int qw = warp - 1 - kPassDot;
+      float qs[QT][4], qc[QT][4];
+#pragma unroll
+      for (int t = 0; t < QT; ++t)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) qs[t][c] = qc[t][c] = 0.f;
+      for (int g = 0; g < ngroups; ++g) {
+        const int gg = it * ngroups + g;
+        const int s = gg % nstages;
+        const int u = gg / nstages;
+        if (!warp_all(mbar_wait(&xready[s], u & 1) && mbar_wait(&full[s], u & 1))) {
+          s_err = 1;
+          break;
+        }
+        const int nc = min(cps, nq - g * cps);
+        for (int c = 0; c < nc; ++c) {
+          const float2 xv = sx[(size_t)s * cps + c];
+          if (xv.x != 0.0f || xv.y != 0.0f) {
+            const float4* col = reinterpret_cast<const float4*>(stages + (size_t)s * stage_floats + (size_t)c * p.lda);
+#pragma unroll
+            for (int t = 0; t < QT; ++t) {
+              const int c4 = qw * 32 + lane + t * 32 * QW;
+              if (c4 < m4q) pacc4<QP>(qs[t], qc[t], col[c4], xv.x, xv.y);
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+      }
+      float2* part = b.qpart + (size_t)blockIdx.x * p.m4;
+#pragma unroll
+      for (int t = 0; t < QT; ++t) {
+        const int c4 = qw * 32 + lane + t * 32 * QW;
+        if (c4 < m4q) {
+          float4* dst = reinterpret_cast<float4*>(part + 4 * c4);
+          dst[0] = make_float4(qs[t][0], QP == kX2 ? qc[t][0] : 0.f, qs[t][1], QP == kX2 ? qc[t][1] : 0.f);
+          dst[1] = make_float4(qs[t][2], QP == kX2 ? qc[t][2] : 0.f, qs[t][3], QP == kX2 ? qc[t][3] : 0.f);
+        }
+      }
+    }
+
+    // ---- grid barrier 1: every CTA's q partials and restart terms are written
+    consumer_sync<NCONS>();
+    if (ct == 0) {
+      float2 d = make_float2(0.f, 0.f);
+      double e = 0.0;
+      for (int w = 0; w < kPassDot; ++w) {
+        d = df2_add(d, s_dot[w]);
+        e = fmax(e, s_eps[w]);
+      }
+      b.blk[4 * blockIdx.x + 0] = df2_to_double(d);
+      b.blk[4 * blockIdx.x + 1] = e;
+      if (s_err) atomicOr(&st->error, 1);
+      bool ok = grid_arrive_wait(b.gbar, gridDim.x, gen);
+      ++gen;
+      if (ok && *(volatile int*)&st->error) ok = false;
+      s_ok = ok ? 1 : 0;
+      if (!ok) atomicOr(&st->error, 1);
+    }
+    consumer_sync<NCONS>();
+    if (!s_ok) break;
+
+    // ---- scalars of the step: every CTA reduces the restart terms in the same order
+    if (warp == 1) {
+      double d = 0.0, e = 0.0;
+      for (int t0 = 0; t0 < nparts; t0 += 256) {
+        double dv[8], ev[8];
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+          const int t = t0 + lane + 32 * kk;
+          dv[kk] = t < nparts ? __ldcg(&b.blk[4 * t + 0]) : 0.0;
+          ev[kk] = t < nparts ? __ldcg(&b.blk[4 * t + 1]) : 0.0;
+        }
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+          d += dv[kk];
+          e = fmax(e, ev[kk]);
+        }
+      }
+      d = warp_sum_d(d);
+      e = warp_max_d(e);
+      if (lane == 0) {
+        const double tnext = (p.restart && d < 0.0) ? 1.0 : tn;
+        s_t = tnext;
+        if (blockIdx.x == 0) {
+          st->t = tnext;
+          st->eps = e;
+          st->k = k + 1;
+          st->sum_active += (double)n_act;
+        }
+      }
+    }
+
+    // ---- residual slices: r_{k+1} = y' - sum of the CTAs' partials (as k_resid)
+    for (int sl = blockIdx.x; sl < nslices; sl += gridDim.x) {
+      const int row = sl * 32 + lane;
+      float s = 0.f, c = 0.f;
+      if (row < p.m4) {
+        for (int t0 = wi; t0 < nparts; t0 += NW * 8) {
+          float2 v[8];
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) {
+            const int t = t0 + NW * kk;
+            v[kk] = t < nparts ? __ldcg(&b.qpart[(size_t)t * p.m4 + row]) : make_float2(0.f, 0.f);
+          }
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) df_add(s, c, v[kk].x, v[kk].y);
+        }
+      }
+      s_red[wi][lane] = make_float2(s, c);
+      consumer_sync<NCONS>();
+      if (wi == 0) {
+        for (int w = 1; w < NW; ++w) df_add(s, c, s_red[w][lane].x, s_red[w][lane].y);
+        if (p.alg == kChambollePock) {
+          double pv = 0.0, dv = 0.0, zv = 0.0;
+          if (row < p.m) {
+            const float2 q = df2_norm(s, c);
+            const float2 yv = make_float2(b.yh[row], b.yl[row]);
+            const float2 z = make_float2(__ldcg(b.rh + row), __ldcg(b.rl + row));
+            const float2 r = make_float2(__ldcg(b.crh + row), __ldcg(b.crl + row));
+            const float2 zn = df2_mul(df2_add(z, df2_mul(df2_sub(q, yv), p.sigma2)), p.inv1ps2);
+            const float2 rn = df2_mul(df2_add(r, df2_sub(yv, q)), make_float2(0.5f, 0.f));
+            b.rh[row] = zn.x;
+            b.rl[row] = zn.y;
+            b.crh[row] = rn.x;
+            b.crl[row] = rn.y;
+            const double rd = df2_to_double(rn), zd = df2_to_double(z);
+            pv = 0.5 * rd * rd;
+            dv = (zd + rd) * (zd + rd);
+            zv = zd * zd;
+          }
+          pv = warp_sum_d(pv);
+          dv = warp_sum_d(dv);
+          zv = warp_sum_d(zv);
+          if (lane == 0) {
+            b.tileR[sl] = pv;
+            b.tileD[sl] = dv;
+            b.tileZ[sl] = zv;
+          }
+        } else {
+          float ps = 0.f, pc = 0.f;
+          if (row < p.m) {
+            float dh, de;
+            two_sum(b.yh[row], -s, dh, de);
+            de += b.yl[row] - c;
+            float rh, rl;
+            two_sum(dh, de, rh, rl);
+            b.rh[row] = rh;
+            b.rl[row] = rl;
+            const float sq = rh * rh;
+            ps = 0.5f * sq;
+            pc = 0.5f * (fmaf(rh, rh, -sq) + 2.0f * rh * rl);
+          }
+          for (int o = 16; o > 0; o >>= 1) {
+            const float os = __shfl_xor_sync(0xffffffffu, ps, o);
+            const float oc = __shfl_xor_sync(0xffffffffu, pc, o);
+            df_add(ps, pc, os, oc);
+          }
+          if (lane == 0) b.tileR[sl] = df_to_double(ps, pc);
+        }
+      }
+      consumer_sync<NCONS>();
+    }
+
+    // ---- grid barrier 2: r_{k+1} and the P partials are written
+    consumer_sync<NCONS>();
+    if (ct == 0) {
+      bool ok = grid_arrive_wait(b.gbar, gridDim.x, gen);
+      ++gen;
+      if (ok && *(volatile int*)&st->error) ok = false;
+      s_ok = ok ? 1 : 0;
+      if (!ok) atomicOr(&st->error, 1);
+    }
+    consumer_sync<NCONS>();
+    if (!s_ok) break;
+  }
+}
+
 __global__ void k_cp_init(Params p, Buffers b) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.m4; i += gridDim.x * blockDim.x) {
     const float rh = b.rh[i], rl = b.rl[i];
@@ -552,7 +1027,8 @@ int pass_configure(int lda, int m4, int idx_cap, int smem_optin, int* qwarps, in
   const int col_bytes = lda * 4;
   for (int cps = std::max(1, std::min(8, 65536 / col_bytes)); cps >= 1; --cps) {
     int ns = kPassMaxStages;
-    while (ns >= 3 && pass_smem_bytes(lda, m4, ns, cps, idx_cap) + 1024 > (size_t)smem_optin) --ns;
+    // room for the kernels' static shared memory (the persistent form's is about 5 KB)
+    while (ns >= 3 && pass_smem_bytes(lda, m4, ns, cps, idx_cap) + 8192 > (size_t)smem_optin) --ns;
     if (ns < 3) continue;
     const int bytes = (int)pass_smem_bytes(lda, m4, ns, cps, idx_cap);
     cudaError_t e = pass_set_smem<kX2>(qt, bytes);
@@ -596,6 +1072,76 @@ cudaError_t launch_pass(const Params& p, const Buffers& b, int slot, int precisi
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+template <int PREC, int QT>
+static cudaError_t iters_launch_t(const Params& p, const Buffers& b, int slot0, int niter, int gap_last, int grid,
+                                  int nstages, int cps, size_t sm, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(32 * (1 + kPassDot + 8));
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;   // all CTAs co-resident (grid barriers)
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_iters<PREC, 8, QT>, p, b, slot0, niter, gap_last, nstages, cps);
+}
+
+template <int PREC>
+static cudaError_t iters_launch_p(int qt, const Params& p, const Buffers& b, int slot0, int niter, int gap_last,
+                                  int grid, int nstages, int cps, size_t sm, cudaStream_t s) {
+  switch (qt) {
+    case 1: return iters_launch_t<PREC, 1>(p, b, slot0, niter, gap_last, grid, nstages, cps, sm, s);
+    case 2: return iters_launch_t<PREC, 2>(p, b, slot0, niter, gap_last, grid, nstages, cps, sm, s);
+    case 4: return iters_launch_t<PREC, 4>(p, b, slot0, niter, gap_last, grid, nstages, cps, sm, s);
+    default: return iters_launch_t<PREC, 8>(p, b, slot0, niter, gap_last, grid, nstages, cps, sm, s);
+  }
+}
+
+cudaError_t launch_iters(const Params& p, const Buffers& b, int slot0, int niter, bool gap_last, int precision,
+                         int grid, int nstages, int cps, int qwarps, cudaStream_t s) {
+  const size_t sm = pass_smem_bytes(p.lda, p.m4, nstages, cps, (p.n + grid - 1) / grid);
+  const int qt = pass_qt(p.m4);
+  if (qwarps != 8 || qt == 0 || niter < 1 || b.gbar == nullptr) return cudaErrorInvalidValue;
+  const int g = gap_last ? 1 : 0;
+  switch (precision) {
+    case kX2: return iters_launch_p<kX2>(qt, p, b, slot0, niter, g, grid, nstages, cps, sm, s);
+    case kF32: return iters_launch_p<kF32>(qt, p, b, slot0, niter, g, grid, nstages, cps, sm, s);
+    case kMix: return iters_launch_p<kMix>(qt, p, b, slot0, niter, g, grid, nstages, cps, sm, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int PREC, int QT>
+static bool iters_fits(int bytes, int grid) {
+  const void* fn = reinterpret_cast<const void*>(k_iters<PREC, 8, QT>);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) return false;
+  int per_sm = 0, dev = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * (1 + kPassDot + 8), bytes) != cudaSuccess)
+    return false;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
+  return per_sm >= 1 && grid <= per_sm * sms;
+}
+
+template <int QT>
+static bool iters_fits_all(int bytes, int grid) {
+  return iters_fits<kX2, QT>(bytes, grid) && iters_fits<kF32, QT>(bytes, grid) && iters_fits<kMix, QT>(bytes, grid);
+}
+
+bool iters_configure(int lda, int m4, int nstages, int cps, int idx_cap, int grid) {
+  if (nstages < 3) return false;
+  const int bytes = (int)pass_smem_bytes(lda, m4, nstages, cps, idx_cap);
+  switch (pass_qt(m4)) {
+    case 1: return iters_fits_all<1>(bytes, grid);
+    case 2: return iters_fits_all<2>(bytes, grid);
+    case 4: return iters_fits_all<4>(bytes, grid);
+    case 8: return iters_fits_all<8>(bytes, grid);
+    default: return false;
+  }
 }
 
 cudaError_t launch_resid(const Params& p, const Buffers& b, int slot, int nparts, cudaStream_t s) {

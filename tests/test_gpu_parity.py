@@ -140,6 +140,25 @@ def test_single_pass_matches_two_pass(P, name):
     assert np.array_equal(a[1] > 0, b[1] > 0) or abs(int((a[1] > 0).sum()) - int((b[1] > 0).sum())) <= 2
 
 
+@pytest.mark.parametrize("name,K", [("nnls_abs_300x700", 10), ("bvls_t2_200x500", 3), ("mixed_180x140", 1)])
+def test_persistent_launch_matches_per_iteration_launches(P, name, K):
+    """The persistent form (K iterations per cooperative launch, grid barriers in place of
+    kernel boundaries) follows the iterates of the form with two launches per iteration,
+    for even, odd and unit screening periods (the slot parity crosses launches)."""
+    p, t = CASES[name]()
+    A, y = _f64(p)
+    L = _L(A)
+    a = gpu_solve(P, p, t=t, tol=0.0, max_iter=120, screen_every=K, lipschitz=L, single_pass=1)
+    b = gpu_solve(P, p, t=t, tol=0.0, max_iter=120, screen_every=K, lipschitz=L, single_pass=2)
+    assert a[2]["single_pass"] == 2 and b[2]["single_pass"] == 1
+    assert a[2]["iters"] == b[2]["iters"] == 120
+    assert float(np.abs(a[0] - b[0]).max()) <= 1e-10 * max(1.0, float(np.abs(b[0]).max()))
+    assert abs(int((a[1] > 0).sum()) - int((b[1] > 0).sum())) <= 2
+    c = gpu_solve(P, p, t=t, tol=0.0, max_iter=120, screen_every=K, lipschitz=L, profile=True)
+    assert c[2]["tr_launches"] == 120 // K and c[2]["tr_ms"] > 0 and c[2]["fwd_launches"] == 0
+    assert float(np.abs(c[0] - a[0]).max()) <= 1e-10 * max(1.0, float(np.abs(b[0]).max()))
+
+
 def test_screened_and_unscreened_follow_the_same_iterates(P):
     p = W.nnls_abs_gaussian(400, 1500, 0.05, 1.0, 4)
     A, y = _f64(p)
