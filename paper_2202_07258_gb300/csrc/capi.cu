@@ -555,12 +555,12 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
   TRY(dalloc(h, &b.blk, 4 * (size_t)max_blocks));
   TRY(dalloc(h, &b.st, 1));
   TRY(dalloc(h, &b.qpart, (size_t)h->num_sms * h->m4));
-  TRY(dalloc(h, &b.gbar, 2));
+  TRY(dalloc(h, &b.gbar, kMaxGridFlags));
   TRY(dalloc(h, &b.xout, n));
   TRY(dalloc(h, &h->y_dev, h->m4));
   TRY(dalloc(h, &h->x0_dev, n));
   CK(cudaMemsetAsync(b.tile_cnt, 0, sizeof(unsigned) * h->fwd_tiles, h->s));
-  CK(cudaMemsetAsync(b.gbar, 0, 2 * sizeof(unsigned), h->s));
+  CK(cudaMemsetAsync(b.gbar, 0, kMaxGridFlags * sizeof(unsigned), h->s));
   CK(cudaMemsetAsync(b.st, 0, sizeof(DevState), h->s));
   CK(cudaMemsetAsync(h->y_dev, 0, sizeof(float) * h->m4, h->s));
   b.y_in = h->y_dev;

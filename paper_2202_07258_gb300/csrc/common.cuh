@@ -28,6 +28,7 @@ constexpr int kMaxRows = 24576;   // r is staged in shared memory: 8 bytes per r
 constexpr int kPassDot = 8;       // dot warps of the fused pass
 constexpr int kPassTmax = 8;      // float4 row chunks owned by one lane of a q warp
 constexpr int kPassMaxStages = 32;
+constexpr int kMaxGridFlags = 1024;  // grid barrier flags of the persistent pass (one per CTA)
 
 enum DualMode { kScaling = 0, kTranslation = 1, kZero = 2 };
 // kMix: float32 correlations a_j^T r, double-float forward product A_S x (the values of the
@@ -252,7 +253,7 @@ struct Buffers {
   unsigned int* tile_cnt;
   double* blk;            // per-block partials of the epilogue kernels (4 doubles each)
   float2* qpart;          // fused pass: per-CTA double-float partials of A_S x_S (grid x m4)
-  unsigned int* gbar;     // persistent pass: grid barrier (arrival count, generation)
+  unsigned int* gbar;     // persistent pass: grid-barrier flags, one per CTA (kMaxGridFlags)
   double* xout;           // float64 copy of the returned iterate (n)
   DevState* st;
   const float* y_in;      // device copy of y

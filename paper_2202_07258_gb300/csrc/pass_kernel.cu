@@ -29,6 +29,20 @@
 
 namespace bvls {
 
+// Dynamic shared memory of the pass: the stages, r (hi, lo), x per stage slot, the
+// full / xready / empty barriers, the issue counters and the CTA's column indices.
+__host__ __device__ inline size_t pass_smem_bytes(int lda, int m4, int nstages, int cps, int idx_cap) {
+  const size_t st = (size_t)nstages;
+  return st * (size_t)cps * lda * 4 + (size_t)m4 * 8 + st * cps * 8 + 3 * st * 8 + st * 4 +
+         (size_t)idx_cap * 4 + 64;
+}
+
+// The persistent form adds, 16-byte aligned, x (two slots), g (two slots), l and u of the
+// CTA's columns.
+__host__ __device__ inline size_t iters_smem_bytes(int lda, int m4, int nstages, int cps, int idx_cap) {
+  return pass_smem_bytes(lda, m4, nstages, cps, idx_cap) + 16 + (size_t)idx_cap * 6 * sizeof(float2);
+}
+
 namespace {
 
 template <int PREC>
@@ -527,12 +541,16 @@ __global__ void __launch_bounds__(256) k_resid(Params p, Buffers b, int slot, in
 //              giving a_j^T r_k, the step, and the CTA's partial of A_S x_{k+1};
 //   barrier    grid-wide;
 //   residual   as k_resid, the rows split into 32-row slices over the CTAs: r_{k+1} and
-//              the slice partials of P_{k+1}; every CTA also reduces the per-CTA restart
-//              terms itself (same order everywhere, so all CTAs hold the same t_{k+1});
+//              the slice partials of P_{k+1}; one warp per CTA also reduces the per-CTA
+//              restart terms (same order everywhere, so all CTAs hold the same t_{k+1})
+//              and prepares the next momentum scalars;
 //   barrier    grid-wide.
-// The producer warp takes no part in the barriers: it walks the column groups of all
-// `niter` iterations, so the first stages of iteration k+1 load while the grid finishes
-// iteration k.  The outputs after the last iteration are those of k_pass + k_resid.
+// The CTA's columns keep their x, g and bounds in shared memory for the whole launch
+// (written back at the end).  The producer warp takes no part in the barriers: it walks
+// the column groups of all `niter` iterations, so the first stages of iteration k+1 load
+// while the grid finishes iteration k.  P_k and the margin eta_g are formed only at the
+// gap iteration, the one whose values the gap kernel reads.  The outputs after the last
+// iteration are those of k_pass + k_resid.
 
 namespace {
 
@@ -542,38 +560,57 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   return v;
 }
 
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // Named barrier 1 over the CTA's consumer warps (all warps but the producer).
 template <int NCONS>
 __device__ __forceinline__ void consumer_sync() {
   asm volatile("bar.sync 1, %0;" ::"r"(NCONS) : "memory");
 }
 
-// One arrival of this CTA at the grid barrier (gb[0] arrivals, gb[1] generation) and a
-// bounded wait for the others; called by one thread after the CTA's consumers synchronised.
-// The last arrival resets the count and then publishes the next generation.
-__device__ bool grid_arrive_wait(unsigned* gb, unsigned nblocks, unsigned gen) {
-  __threadfence();
-  const unsigned prev = atomicAdd(&gb[0], 1u);
-  if (prev == nblocks - 1) {
-    atomicExch(&gb[0], 0u);
+// Grid barrier on per-CTA flags: after the CTA's consumers synchronised, lane 0 of the
+// calling warp publishes `epoch` in this CTA's flag; the warp then waits (bounded) until
+// every CTA's flag has reached it.  Returns false after kWaitCycles.
+__device__ bool grid_flag_sync(unsigned* flags, int nblocks, unsigned epoch) {
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) {
     __threadfence();
-    atomicAdd(&gb[1], 1u);
-    return true;
+    st_release_u32(&flags[blockIdx.x], epoch);
   }
-  if (ld_acquire_u32(&gb[1]) != gen) return true;
+  __syncwarp();
   const long long t0 = clock64();
-  while (ld_acquire_u32(&gb[1]) == gen) {
-    if (clock64() - t0 > kWaitCycles) return false;
+  bool ok = true;
+  for (;;) {
+    bool mine = true;
+    for (int t = lane; t < nblocks; t += 32) mine &= (int)(ld_acquire_u32(&flags[t]) - epoch) >= 0;
+    if (__all_sync(0xffffffffu, mine)) break;
+    if (clock64() - t0 > kWaitCycles) {
+      ok = false;
+      break;
+    }
   }
   __threadfence();
-  return true;
+  return __all_sync(0xffffffffu, ok);
+}
+
+// Momentum scalars of the step that starts from t_k: t_{k+1} (no restart) and beta.
+__device__ __forceinline__ void momentum(double tk, double* s_scal, float2* s_beta2) {
+  const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk * tk));
+  const double beta = (tk - 1.0) / tn;
+  s_scal[0] = beta;
+  s_scal[1] = tn;
+  s_beta2[0] = df2_from_double(beta);
+  s_beta2[1] = df2_from_double(1.0 + beta);
 }
 
 }  // namespace
 
+
 template <int PREC, int QW, int QT>
 __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
-    k_iters(Params p, Buffers b, int slot0, int niter, int gap_last, int nstages, int cps) {
+    k_iters(Params p, Buffers b, int slot0, int niter, int gap_last, int nstages, int cps, int idx_cap) {
   constexpr int DP = PREC == kX2 ? kX2 : kF32;
   constexpr int QP = PREC == kF32 ? kF32 : kX2;
   constexpr int NW = kPassDot + QW;          // consumer warps
@@ -593,11 +630,17 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
   uint64_t* empty = xready + nstages;
   volatile int* s_issued = reinterpret_cast<volatile int*>(empty + nstages);
   int* sidx = const_cast<int*>(s_issued) + nstages;
+  float2* sv = reinterpret_cast<float2*>(smem + ((pass_smem_bytes(p.lda, p.m4, nstages, cps, idx_cap) + 15) & ~(size_t)15));
+  float2* sX0 = sv;                    // x by slot (0, 1), this CTA's columns
+  float2* sX1 = sv + idx_cap;
+  float2* sG0 = sv + 2 * idx_cap;      // g by slot
+  float2* sG1 = sv + 3 * idx_cap;
+  float2* sL = sv + 4 * idx_cap;
+  float2* sU = sv + 5 * idx_cap;
   __shared__ float2 s_dot[kPassDot];
   __shared__ double s_eps[kPassDot];
   __shared__ double s_scal[3];
   __shared__ float2 s_beta2[2];
-  __shared__ double s_t;
   __shared__ int s_err, s_ok;
   __shared__ double s_th[NW];
   __shared__ float2 s_red[NW][32];
@@ -611,8 +654,9 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
   const int ngroups = (nq + cps - 1) / cps;
   const int nslices = (p.m4 + 31) / 32;
   const int nparts = gridDim.x;
+  unsigned* flags = b.gbar;
+  const unsigned epoch0 = __ldcg(flags + blockIdx.x);   // barriers passed so far (the same in every CTA)
 
-  unsigned gen = 0;
   if (threadIdx.x == 0) {
     for (int s = 0; s < nstages; ++s) {
       mbar_init(&full[s], 1);
@@ -623,10 +667,18 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
     fence_barrier_init();
     s_err = 0;
     s_ok = 1;
-    s_t = st->t;
+    momentum(st->t, s_scal, s_beta2);
   }
-  if (threadIdx.x == 32) gen = ld_acquire_u32(&b.gbar[1]);   // before this CTA's first arrival
-  for (int q = threadIdx.x; q < nq; q += blockDim.x) sidx[q] = b.idx[p0 + q];
+  for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+    const int j = b.idx[p0 + q];
+    sidx[q] = j;
+    sX0[q] = b.x[0][j];
+    sX1[q] = b.x[1][j];
+    sG0[q] = b.g[0][j];
+    sG1[q] = b.g[1][j];
+    sL[q] = p.l2[j];
+    sU[q] = p.u2[j];
+  }
   __syncthreads();
 
   if (warp == 0) {
@@ -672,23 +724,17 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
   // -------------------------------------------------------------------- consumers
   const int wi = warp - 1;
   const int ct = threadIdx.x - 32;
+  unsigned epoch = epoch0;
   for (int it = 0; it < niter; ++it) {
     const int slot = (slot0 + it) & 1;
     const int gap_iter = gap_last && it == niter - 1;
     const int k = k0 + it;
-    // prologue: P_k, the momentum scalars and r_k in shared memory
-    if (warp == 1) {
+    // prologue: r_k in shared memory; at the gap iteration also P_k and the margin eta_g
+    if (gap_iter && warp == 1) {
       const double Pk = k > 0 ? warp_load_sum(b.tileR, nslices) : st->P[slot];
       if (lane == 0) {
         if (blockIdx.x == 0) st->P[slot] = Pk;
-        const double tk = s_t;
-        const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk * tk));
-        const double beta = (tk - 1.0) / tn;
-        s_scal[0] = beta;
-        s_scal[1] = tn;
         s_scal[2] = p.Cg * sqrt(2.0 * Pk) * (1.0 + 1e-6);
-        s_beta2[0] = df2_from_double(beta);
-        s_beta2[1] = df2_from_double(1.0 + beta);
       }
     }
     for (int i = ct; i < m4q; i += NCONS) {
@@ -716,13 +762,13 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
     if (warp <= kPassDot) {
       // ------------------------------------------------------------ dot warps
       const int dw = warp - 1;
-      const double eta_g = s_scal[2];
+      const double eta_g = gap_iter ? s_scal[2] : 0.0;
       const float2 bb = s_beta2[0], onepb = s_beta2[1];
       const bool want_eps = gap_iter && p.dual_mode == kTranslation && !p.wstar;
-      const float2* xc = b.x[slot];
-      float2* xn = b.x[slot ^ 1];
-      const float2* gp = b.g[slot ^ 1];
-      float2* gc = b.g[slot];
+      const float2* xc = slot ? sX1 : sX0;
+      float2* xn = slot ? sX0 : sX1;
+      const float2* gp = slot ? sG0 : sG1;
+      float2* gc = slot ? sG1 : sG0;
       float2 dot = make_float2(0.f, 0.f);
       double epsm = 0.0;
       const int U = (cps % 2 == 0) ? 2 : 1;
@@ -735,18 +781,18 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
         const int u = gg / nstages;
         const int c0 = q0 - g * cps;
         const int e = lane < ncol ? lane : 0;
-        const int j = sidx[q0 + e];
+        const int qj = q0 + e;                 // the lane's column, local index
         float2 xk = make_float2(0.f, 0.f), xp = xk, gpv = xk, lj = xk, uj = xk;
         double nr = 0.0, wj = 0.0;
         int inf_j = 0;
         if (lane < ncol) {
-          // written by this CTA in the previous iteration: read through L2, not L1
-          xk = __ldcg(xc + j);
-          xp = __ldcg(xn + j);
-          gpv = __ldcg(gp + j);
-          lj = p.l2[j];
-          uj = p.u2[j];
+          xk = xc[qj];
+          xp = xn[qj];
+          gpv = gp[qj];
+          lj = sL[qj];
+          uj = sU[qj];
           if (want_eps) {
+            const int j = sidx[qj];
             nr = p.nrm[j];
             wj = p.w[j];
             inf_j = p.jinf[j];
@@ -770,8 +816,8 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
           const float2 xnew = coord_step(p, g2, xk, xp, gpv, lj, uj, bb, onepb, xf, dc);
           sx[(size_t)s * cps + c] = QP == kX2 ? xf : make_float2(xf.x, 0.0f);
           mbar_arrive(&xready[s]);
-          __stcg(xn + j, xnew);
-          __stcg(gc + j, g2);
+          xn[qj] = xnew;
+          gc[qj] = g2;
           if (p.alg == kChambollePock) continue;
           dot = df2_add(dot, dc);
           if (want_eps && inf_j && nr > 0.0) {
@@ -847,17 +893,23 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
       b.blk[4 * blockIdx.x + 0] = df2_to_double(d);
       b.blk[4 * blockIdx.x + 1] = e;
       if (s_err) atomicOr(&st->error, 1);
-      bool ok = grid_arrive_wait(b.gbar, gridDim.x, gen);
-      ++gen;
+    }
+    ++epoch;
+    if (warp == 1) {
+      bool ok = grid_flag_sync(flags, nparts, epoch);
       if (ok && *(volatile int*)&st->error) ok = false;
-      s_ok = ok ? 1 : 0;
-      if (!ok) atomicOr(&st->error, 1);
+      if (lane == 0) {
+        s_ok = ok ? 1 : 0;
+        if (!ok) atomicOr(&st->error, 1);
+      }
     }
     consumer_sync<NCONS>();
     if (!s_ok) break;
 
-    // ---- scalars of the step: every CTA reduces the restart terms in the same order
-    if (warp == 1) {
+    // ---- residual slices r_{k+1} = y' - sum of the CTAs' partials (as k_resid); the last
+    // warp meanwhile reduces the restart terms and prepares the next step's scalars
+    bool scalars_done = false;
+    auto scalars = [&]() {
       double d = 0.0, e = 0.0;
       for (int t0 = 0; t0 < nparts; t0 += 256) {
         double dv[8], ev[8];
@@ -877,30 +929,29 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
       e = warp_max_d(e);
       if (lane == 0) {
         const double tnext = (p.restart && d < 0.0) ? 1.0 : tn;
-        s_t = tnext;
         if (blockIdx.x == 0) {
           st->t = tnext;
           st->eps = e;
           st->k = k + 1;
           st->sum_active += (double)n_act;
         }
+        momentum(tnext, s_scal, s_beta2);
       }
-    }
-
-    // ---- residual slices: r_{k+1} = y' - sum of the CTAs' partials (as k_resid)
+      scalars_done = true;
+    };
     for (int sl = blockIdx.x; sl < nslices; sl += gridDim.x) {
       const int row = sl * 32 + lane;
       float s = 0.f, c = 0.f;
       if (row < p.m4) {
-        for (int t0 = wi; t0 < nparts; t0 += NW * 8) {
-          float2 v[8];
+        for (int t0 = wi; t0 < nparts; t0 += NW * 10) {
+          float2 v[10];
 #pragma unroll
-          for (int kk = 0; kk < 8; ++kk) {
+          for (int kk = 0; kk < 10; ++kk) {
             const int t = t0 + NW * kk;
             v[kk] = t < nparts ? __ldcg(&b.qpart[(size_t)t * p.m4 + row]) : make_float2(0.f, 0.f);
           }
 #pragma unroll
-          for (int kk = 0; kk < 8; ++kk) df_add(s, c, v[kk].x, v[kk].y);
+          for (int kk = 0; kk < 10; ++kk) df_add(s, c, v[kk].x, v[kk].y);
         }
       }
       s_red[wi][lane] = make_float2(s, c);
@@ -954,21 +1005,35 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
           }
           if (lane == 0) b.tileR[sl] = df_to_double(ps, pc);
         }
+      } else if (wi == NW - 1 && !scalars_done) {
+        scalars();
       }
       consumer_sync<NCONS>();
     }
+    if (wi == NW - 1 && !scalars_done) scalars();
 
     // ---- grid barrier 2: r_{k+1} and the P partials are written
     consumer_sync<NCONS>();
-    if (ct == 0) {
-      bool ok = grid_arrive_wait(b.gbar, gridDim.x, gen);
-      ++gen;
+    ++epoch;
+    if (warp == 1) {
+      bool ok = grid_flag_sync(flags, nparts, epoch);
       if (ok && *(volatile int*)&st->error) ok = false;
-      s_ok = ok ? 1 : 0;
-      if (!ok) atomicOr(&st->error, 1);
+      if (lane == 0) {
+        s_ok = ok ? 1 : 0;
+        if (!ok) atomicOr(&st->error, 1);
+      }
     }
     consumer_sync<NCONS>();
     if (!s_ok) break;
+  }
+
+  // the CTA's columns back to global memory (both slots of x and g)
+  for (int q = ct; q < nq; q += NCONS) {
+    const int j = sidx[q];
+    b.x[0][j] = sX0[q];
+    b.x[1][j] = sX1[q];
+    b.g[0][j] = sG0[q];
+    b.g[1][j] = sG1[q];
   }
 }
 
@@ -991,12 +1056,6 @@ cudaError_t launch_cp_init(const Params& p, const Buffers& b, cudaStream_t s) {
 __global__ void k_export(Params p, Buffers b, int slot) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < p.n; j += gridDim.x * blockDim.x)
     b.xout[j] = df2_to_double(b.x[slot][j]);
-}
-
-size_t pass_smem_bytes(int lda, int m4, int nstages, int cps, int idx_cap) {
-  const size_t st = (size_t)nstages;
-  return st * (size_t)cps * lda * 4 + (size_t)m4 * 8 + st * cps * 8 + 3 * st * 8 + st * 4 +
-         (size_t)idx_cap * 4 + 64;
 }
 
 // Stage layout for the fused pass: up to 64 KB and 8 columns per stage (bulk copies much
@@ -1087,7 +1146,8 @@ static cudaError_t iters_launch_t(const Params& p, const Buffers& b, int slot0, 
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_iters<PREC, 8, QT>, p, b, slot0, niter, gap_last, nstages, cps);
+  return cudaLaunchKernelEx(&cfg, k_iters<PREC, 8, QT>, p, b, slot0, niter, gap_last, nstages, cps,
+                            (p.n + grid - 1) / grid);
 }
 
 template <int PREC>
@@ -1103,9 +1163,9 @@ static cudaError_t iters_launch_p(int qt, const Params& p, const Buffers& b, int
 
 cudaError_t launch_iters(const Params& p, const Buffers& b, int slot0, int niter, bool gap_last, int precision,
                          int grid, int nstages, int cps, int qwarps, cudaStream_t s) {
-  const size_t sm = pass_smem_bytes(p.lda, p.m4, nstages, cps, (p.n + grid - 1) / grid);
+  const size_t sm = iters_smem_bytes(p.lda, p.m4, nstages, cps, (p.n + grid - 1) / grid);
   const int qt = pass_qt(p.m4);
-  if (qwarps != 8 || qt == 0 || niter < 1 || b.gbar == nullptr) return cudaErrorInvalidValue;
+  if (qwarps != 8 || qt == 0 || niter < 1 || b.gbar == nullptr || grid > kMaxGridFlags) return cudaErrorInvalidValue;
   const int g = gap_last ? 1 : 0;
   switch (precision) {
     case kX2: return iters_launch_p<kX2>(qt, p, b, slot0, niter, g, grid, nstages, cps, sm, s);
@@ -1133,8 +1193,8 @@ static bool iters_fits_all(int bytes, int grid) {
 }
 
 bool iters_configure(int lda, int m4, int nstages, int cps, int idx_cap, int grid) {
-  if (nstages < 3) return false;
-  const int bytes = (int)pass_smem_bytes(lda, m4, nstages, cps, idx_cap);
+  if (nstages < 3 || grid > kMaxGridFlags) return false;
+  const int bytes = (int)iters_smem_bytes(lda, m4, nstages, cps, idx_cap);
   switch (pass_qt(m4)) {
     case 1: return iters_fits_all<1>(bytes, grid);
     case 2: return iters_fits_all<2>(bytes, grid);
