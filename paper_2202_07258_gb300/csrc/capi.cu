@@ -74,7 +74,8 @@ struct bvls_handle {
   int* pinned = nullptr;
   int fwd_tiles = 0, fwd_chunks = 0, tr_blocks = 0, red_blocks = 0;
   int pass_stages = 0, pass_qw = 0, pass_cps = 1;  // fused single-pass iteration when pass_stages > 0
-  bool pass_coop = false;                           // its persistent (cooperative) launch fits
+  bool pass_coop = false;
+  MomEntry* mom = nullptr;                          // momentum table of the persistent pass                           // its persistent (cooperative) launch fits
   double Cg[3] = {0, 0, 0}, Cf[3] = {0, 0, 0}, Csub = 0.0;
   bool have_graph = false;
   GraphKey key{};
@@ -197,6 +198,7 @@ Params make_params(const bvls_handle* h, const bvls_opts& o, int max_iter) {
   }
   p.fwd_chunks = h->fwd_chunks;
   p.fwd_tiles = h->fwd_tiles;
+  p.mom = h->mom;
   return p;
 }
 
@@ -556,6 +558,21 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
   TRY(dalloc(h, &b.st, 1));
   TRY(dalloc(h, &b.qpart, (size_t)h->num_sms * h->m4));
   TRY(dalloc(h, &b.gbar, kMaxGridFlags));
+  TRY(dalloc(h, &h->mom, kMomTable));
+  {
+    std::vector<MomEntry> tab(kMomTable);
+    double t = 1.0;
+    for (int i = 0; i < kMomTable; ++i) {
+      const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
+      const double beta = (t - 1.0) / tn;
+      tab[i].t = t;
+      tab[i].tn = tn;
+      tab[i].beta2 = df2_from_double(beta);
+      tab[i].onepb2 = df2_from_double(1.0 + beta);
+      t = tn;
+    }
+    CK(cudaMemcpy(h->mom, tab.data(), sizeof(MomEntry) * kMomTable, cudaMemcpyHostToDevice));
+  }
   TRY(dalloc(h, &b.xout, n));
   TRY(dalloc(h, &h->y_dev, h->m4));
   TRY(dalloc(h, &h->x0_dev, n));

@@ -52,6 +52,8 @@ struct DevState {
   int error;          // a bounded device wait gave up (nonzero: results invalid)
   int chunks;         // chunks run by the device-side loop of the solve graph
   double t;           // FISTA momentum parameter t_k
+  int ti;             // steps since the last restart (t_k = T[ti] of the momentum table)
+  int pad_ti;
   double P[2];        // 1/2 ||r_k||^2 in slot k & 1 (r = rh + rl)
   double eps;         // translation step of the last evaluation
   double gap;         // gap upper bound of the last evaluation
@@ -65,6 +67,15 @@ struct DevState {
   double theta_r2;    // ||theta - r_k||^2 for a fixed dual point (computed by the pass at gap iterations)
   unsigned int cnt_tr, cnt_gap, cnt_fwd, cnt_resid;
 };
+
+// Momentum table of the persistent pass: with T[0] = 1 and T[i+1] = (1 + sqrt(1 + 4 T[i]^2)) / 2
+// (the t_k recursion restarted at t = 1), entry i holds T[i], T[i+1] and beta = (T[i] - 1) /
+// T[i+1] as double-float pairs, computed on the host in float64 so the step needs no float64.
+struct MomEntry {
+  double t, tn;
+  float2 beta2, onepb2;   // beta and 1 + beta
+};
+constexpr int kMomTable = 1 << 16;
 
 // Per-solve constants passed by value to the kernels.
 struct Params {
@@ -102,6 +113,7 @@ struct Params {
   float2 sigma2;           // dual step sigma
   float2 inv1ps2;          // 1 / (1 + sigma)
   double E_cp;             // |r (stored) - r (exact)| from the recurrence r_{k+1} = (r_k + y' - A xbar) / 2
+  const MomEntry* mom;     // momentum table (kMomTable entries)
   int fwd_chunks;          // grid.y of the A_S x_S kernel
   int fwd_tiles;           // grid.x of the A_S x_S kernel
 };

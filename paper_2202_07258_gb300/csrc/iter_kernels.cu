@@ -125,6 +125,7 @@ __global__ void k_init_state(Params p, Buffers b) {
     st->nonfinite = bad;
     st->chunks = 0;
     st->t = 1.0;
+    st->ti = 0;
     st->P[0] = 0.0;
     st->P[1] = 0.0;
     st->error = 0;

@@ -560,47 +560,46 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   return v;
 }
 
-__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
 // Named barrier 1 over the CTA's consumer warps (all warps but the producer).
 template <int NCONS>
 __device__ __forceinline__ void consumer_sync() {
   asm volatile("bar.sync 1, %0;" ::"r"(NCONS) : "memory");
 }
 
-// Grid barrier on per-CTA flags: after the CTA's consumers synchronised, lane 0 of the
-// calling warp publishes `epoch` in this CTA's flag; the warp then waits (bounded) until
-// every CTA's flag has reached it.  Returns false after kWaitCycles.
-__device__ bool grid_flag_sync(unsigned* flags, int nblocks, unsigned epoch) {
-  const int lane = threadIdx.x & 31;
-  if (lane == 0) {
+// One arrival of this CTA at the grid barrier (gb[0] arrivals, gb[1] generation) and a
+// bounded wait for the others; called by one thread after the CTA's consumers synchronised.
+// The last arrival resets the count and then publishes the next generation.
+__device__ bool grid_arrive_wait(unsigned* gb, unsigned nblocks, unsigned gen) {
+  __threadfence();
+  const unsigned prev = atomicAdd(&gb[0], 1u);
+  if (prev == nblocks - 1) {
+    atomicExch(&gb[0], 0u);
     __threadfence();
-    st_release_u32(&flags[blockIdx.x], epoch);
+    atomicAdd(&gb[1], 1u);
+    return true;
   }
-  __syncwarp();
+  if (ld_acquire_u32(&gb[1]) != gen) return true;
   const long long t0 = clock64();
-  bool ok = true;
-  for (;;) {
-    bool mine = true;
-    for (int t = lane; t < nblocks; t += 32) mine &= (int)(ld_acquire_u32(&flags[t]) - epoch) >= 0;
-    if (__all_sync(0xffffffffu, mine)) break;
-    if (clock64() - t0 > kWaitCycles) {
-      ok = false;
-      break;
-    }
+  while (ld_acquire_u32(&gb[1]) == gen) {
+    if (clock64() - t0 > kWaitCycles) return false;
   }
   __threadfence();
-  return __all_sync(0xffffffffu, ok);
+  return true;
 }
 
-// Momentum scalars of the step that starts from t_k: t_{k+1} (no restart) and beta.
-__device__ __forceinline__ void momentum(double tk, double* s_scal, float2* s_beta2) {
+// Scalars of the step that starts from t_k = T[ti]: t_{k+1} without restart and beta as
+// double-float pairs (float64 arithmetic only past the table's end).
+__device__ __forceinline__ void momentum(const MomEntry* mom, int ti, double tk, double* s_tn, float2* s_beta2) {
+  if (ti < kMomTable) {
+    const MomEntry e = mom[ti];
+    *s_tn = e.tn;
+    s_beta2[0] = e.beta2;
+    s_beta2[1] = e.onepb2;
+    return;
+  }
   const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk * tk));
   const double beta = (tk - 1.0) / tn;
-  s_scal[0] = beta;
-  s_scal[1] = tn;
+  *s_tn = tn;
   s_beta2[0] = df2_from_double(beta);
   s_beta2[1] = df2_from_double(1.0 + beta);
 }
@@ -639,9 +638,9 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
   float2* sU = sv + 5 * idx_cap;
   __shared__ float2 s_dot[kPassDot];
   __shared__ double s_eps[kPassDot];
-  __shared__ double s_scal[3];
+  __shared__ double s_tn, s_tk, s_etag;   // t_{k+1} without restart, t_k, margin eta_g
   __shared__ float2 s_beta2[2];
-  __shared__ int s_err, s_ok;
+  __shared__ int s_ti, s_err, s_ok;
   __shared__ double s_th[NW];
   __shared__ float2 s_red[NW][32];
 
@@ -654,8 +653,8 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
   const int ngroups = (nq + cps - 1) / cps;
   const int nslices = (p.m4 + 31) / 32;
   const int nparts = gridDim.x;
-  unsigned* flags = b.gbar;
-  const unsigned epoch0 = __ldcg(flags + blockIdx.x);   // barriers passed so far (the same in every CTA)
+  unsigned gen = 0;
+  if (threadIdx.x == 32) gen = ld_acquire_u32(&b.gbar[1]);   // before this CTA's first arrival
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < nstages; ++s) {
@@ -667,7 +666,9 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
     fence_barrier_init();
     s_err = 0;
     s_ok = 1;
-    momentum(st->t, s_scal, s_beta2);
+    s_ti = st->ti;
+    s_tk = st->t;
+    momentum(p.mom, s_ti, s_tk, &s_tn, s_beta2);
   }
   for (int q = threadIdx.x; q < nq; q += blockDim.x) {
     const int j = b.idx[p0 + q];
@@ -724,7 +725,6 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
   // -------------------------------------------------------------------- consumers
   const int wi = warp - 1;
   const int ct = threadIdx.x - 32;
-  unsigned epoch = epoch0;
   for (int it = 0; it < niter; ++it) {
     const int slot = (slot0 + it) & 1;
     const int gap_iter = gap_last && it == niter - 1;
@@ -734,7 +734,7 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
       const double Pk = k > 0 ? warp_load_sum(b.tileR, nslices) : st->P[slot];
       if (lane == 0) {
         if (blockIdx.x == 0) st->P[slot] = Pk;
-        s_scal[2] = p.Cg * sqrt(2.0 * Pk) * (1.0 + 1e-6);
+        s_etag = p.Cg * sqrt(2.0 * Pk) * (1.0 + 1e-6);
       }
     }
     for (int i = ct; i < m4q; i += NCONS) {
@@ -757,12 +757,12 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
       }
     }
     consumer_sync<NCONS>();
-    const double tn = s_scal[1];
+    const double tn = s_tn;
 
     if (warp <= kPassDot) {
       // ------------------------------------------------------------ dot warps
       const int dw = warp - 1;
-      const double eta_g = gap_iter ? s_scal[2] : 0.0;
+      const double eta_g = gap_iter ? s_etag : 0.0;
       const float2 bb = s_beta2[0], onepb = s_beta2[1];
       const bool want_eps = gap_iter && p.dual_mode == kTranslation && !p.wstar;
       const float2* xc = slot ? sX1 : sX0;
@@ -888,20 +888,16 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
       double e = 0.0;
       for (int w = 0; w < kPassDot; ++w) {
         d = df2_add(d, s_dot[w]);
-        e = fmax(e, s_eps[w]);
+        if (gap_iter) e = fmax(e, s_eps[w]);
       }
-      b.blk[4 * blockIdx.x + 0] = df2_to_double(d);
-      b.blk[4 * blockIdx.x + 1] = e;
+      *reinterpret_cast<float2*>(&b.blk[4 * blockIdx.x + 0]) = d;   // restart term (double-float)
+      b.blk[4 * blockIdx.x + 1] = e;                                 // translation step candidate
       if (s_err) atomicOr(&st->error, 1);
-    }
-    ++epoch;
-    if (warp == 1) {
-      bool ok = grid_flag_sync(flags, nparts, epoch);
+      bool ok = grid_arrive_wait(b.gbar, gridDim.x, gen);
+      ++gen;
       if (ok && *(volatile int*)&st->error) ok = false;
-      if (lane == 0) {
-        s_ok = ok ? 1 : 0;
-        if (!ok) atomicOr(&st->error, 1);
-      }
+      s_ok = ok ? 1 : 0;
+      if (!ok) atomicOr(&st->error, 1);
     }
     consumer_sync<NCONS>();
     if (!s_ok) break;
@@ -910,32 +906,41 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
     // warp meanwhile reduces the restart terms and prepares the next step's scalars
     bool scalars_done = false;
     auto scalars = [&]() {
-      double d = 0.0, e = 0.0;
+      // restart test: sign of sum_j g_v,j (x_{k+1,j} - x_{k,j}) over all CTAs, double-float
+      float2 d = make_float2(0.f, 0.f);
+      double e = 0.0;
       for (int t0 = 0; t0 < nparts; t0 += 256) {
-        double dv[8], ev[8];
+        float2 dv[8];
+        double ev[8];
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk) {
           const int t = t0 + lane + 32 * kk;
-          dv[kk] = t < nparts ? __ldcg(&b.blk[4 * t + 0]) : 0.0;
-          ev[kk] = t < nparts ? __ldcg(&b.blk[4 * t + 1]) : 0.0;
+          dv[kk] = t < nparts ? __ldcg(reinterpret_cast<const float2*>(&b.blk[4 * t + 0])) : make_float2(0.f, 0.f);
+          ev[kk] = (gap_iter && t < nparts) ? __ldcg(&b.blk[4 * t + 1]) : 0.0;
         }
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
-          d += dv[kk];
-          e = fmax(e, ev[kk]);
-        }
+        for (int kk = 0; kk < 8; ++kk) d = df2_add(d, dv[kk]);
+        if (gap_iter)
+          for (int kk = 0; kk < 8; ++kk) e = fmax(e, ev[kk]);
       }
-      d = warp_sum_d(d);
-      e = warp_max_d(e);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+        d = df2_add(d, make_float2(__shfl_xor_sync(0xffffffffu, d.x, o), __shfl_xor_sync(0xffffffffu, d.y, o)));
+      if (gap_iter) e = warp_max_d(e);
       if (lane == 0) {
-        const double tnext = (p.restart && d < 0.0) ? 1.0 : tn;
+        const bool restart = p.restart && (d.x < 0.f || (d.x == 0.f && d.y < 0.f));
+        const int ti = restart ? 0 : s_ti + 1;
+        const double tnext = restart ? 1.0 : tn;
+        s_ti = ti;
+        s_tk = tnext;
+        momentum(p.mom, ti, tnext, &s_tn, s_beta2);
         if (blockIdx.x == 0) {
           st->t = tnext;
-          st->eps = e;
+          st->ti = ti;
+          if (gap_iter) st->eps = e;
           st->k = k + 1;
           st->sum_active += (double)n_act;
         }
-        momentum(tnext, s_scal, s_beta2);
       }
       scalars_done = true;
     };
@@ -1014,14 +1019,12 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
 
     // ---- grid barrier 2: r_{k+1} and the P partials are written
     consumer_sync<NCONS>();
-    ++epoch;
-    if (warp == 1) {
-      bool ok = grid_flag_sync(flags, nparts, epoch);
+    if (ct == 0) {
+      bool ok = grid_arrive_wait(b.gbar, gridDim.x, gen);
+      ++gen;
       if (ok && *(volatile int*)&st->error) ok = false;
-      if (lane == 0) {
-        s_ok = ok ? 1 : 0;
-        if (!ok) atomicOr(&st->error, 1);
-      }
+      s_ok = ok ? 1 : 0;
+      if (!ok) atomicOr(&st->error, 1);
     }
     consumer_sync<NCONS>();
     if (!s_ok) break;
