@@ -114,6 +114,29 @@ __device__ __forceinline__ void dot_pair(const float4* colA, const float4* colB,
   gb = df2_norm(sb[0], DP == kX2 ? cb[0] : 0.0f);
 }
 
+// q_slice += sum over one stage's columns of a_j x_j on the lane's rows (QT float4 chunks),
+// columns with x_j = 0 skipped (the test is uniform across the warp).  A stage holds at most
+// 8 columns: their x values are read together and the column loop is unrolled, so the
+// loads of several columns are in flight at once.
+template <int QP, int QT, int QW>
+__device__ __forceinline__ void q_stage(float (&qs)[QT][4], float (&qc)[QT][4], const float* sbase,
+                                        const float2* sxs, int nc, int lda, int qw, int lane, int m4q) {
+  float2 xs[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) xs[c] = c < nc ? sxs[c] : make_float2(0.f, 0.f);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    if (xs[c].x != 0.0f || xs[c].y != 0.0f) {
+      const float4* col = reinterpret_cast<const float4*>(sbase + (size_t)c * lda);
+#pragma unroll
+      for (int t = 0; t < QT; ++t) {
+        const int c4 = qw * 32 + lane + t * 32 * QW;
+        if (c4 < m4q) pacc4<QP>(qs[t], qc[t], col[c4], xs[c].x, xs[c].y);
+      }
+    }
+  }
+}
+
 __device__ __forceinline__ float2 clip2(float2 x, float2 lj, float2 uj) {
   if (df2_lt(x, lj)) x = lj;
   if (df2_lt(uj, x)) x = uj;
@@ -375,18 +398,8 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
         s_err = 1;
         break;
       }
-      const int nc = min(cps, nq - g * cps);
-      for (int c = 0; c < nc; ++c) {
-        const float2 xv = sx[(size_t)s * cps + c];
-        if (xv.x != 0.0f || xv.y != 0.0f) {
-          const float4* col = reinterpret_cast<const float4*>(stages + (size_t)s * stage_floats + (size_t)c * p.lda);
-#pragma unroll
-          for (int t = 0; t < QT; ++t) {
-            const int c4 = qw * 32 + lane + t * 32 * QW;
-            if (c4 < m4q) pacc4<QP>(qs[t], qc[t], col[c4], xv.x, xv.y);
-          }
-        }
-      }
+      q_stage<QP, QT, QW>(qs, qc, stages + (size_t)s * stage_floats, sx + (size_t)s * cps, min(cps, nq - g * cps),
+                          p.lda, qw, lane, m4q);
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);
     }
@@ -854,18 +867,8 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
           s_err = 1;
           break;
         }
-        const int nc = min(cps, nq - g * cps);
-        for (int c = 0; c < nc; ++c) {
-          const float2 xv = sx[(size_t)s * cps + c];
-          if (xv.x != 0.0f || xv.y != 0.0f) {
-            const float4* col = reinterpret_cast<const float4*>(stages + (size_t)s * stage_floats + (size_t)c * p.lda);
-#pragma unroll
-            for (int t = 0; t < QT; ++t) {
-              const int c4 = qw * 32 + lane + t * 32 * QW;
-              if (c4 < m4q) pacc4<QP>(qs[t], qc[t], col[c4], xv.x, xv.y);
-            }
-          }
-        }
+        q_stage<QP, QT, QW>(qs, qc, stages + (size_t)s * stage_floats, sx + (size_t)s * cps,
+                            min(cps, nq - g * cps), p.lda, qw, lane, m4q);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
       }

@@ -56,11 +56,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Wait (bounded) until *flag >= target; flag lives in shared memory and is written by
-// another warp of the CTA.
+// another warp of the CTA.  The poll backs off, so a waiting warp leaves the issue slots
+// and shared-memory bandwidth to the warps that are computing.
 __device__ __forceinline__ bool smem_wait_geq(const volatile int* flag, int target) {
   if (*flag >= target) return true;
   const long long t0 = clock64();
   while (*flag < target) {
+    __nanosleep(64);
     if (clock64() - t0 > kWaitCycles) return false;
   }
   return true;
