@@ -45,33 +45,63 @@ __host__ __device__ inline size_t iters_smem_bytes(int lda, int m4, int nstages,
 
 namespace {
 
-template <int PREC>
-__device__ __forceinline__ void pacc4(float* s, float* c, const float4 a, float xh, float xl) {
-  if (PREC == kX2) {
-    df_fma(s[0], c[0], a.x, xh, xl);
-    df_fma(s[1], c[1], a.y, xh, xl);
-    df_fma(s[2], c[2], a.z, xh, xl);
-    df_fma(s[3], c[3], a.w, xh, xl);
-  } else {
-    s[0] = fmaf(a.x, xh, s[0]);
-    s[1] = fmaf(a.y, xh, s[1]);
-    s[2] = fmaf(a.z, xh, s[2]);
-    s[3] = fmaf(a.w, xh, s[3]);
-  }
+// ---- two float32 lanes in one 64-bit register: add / sub / mul / fma .f32x2 round each
+// lane exactly as the scalar instruction does, at one instruction for both lanes.
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 x2_add(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 x2_sub(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 x2_mul(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 x2_fma(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f32x2 x2_pack(float lo, float hi) {
+  f32x2 d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+  return d;
+}
+__device__ __forceinline__ void x2_unpack(f32x2 v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
 }
 
+// (s, c) += a (h + l) lane by lane, as df_fma: FMA TwoProd of a h, rounded a l, TwoSum of
+// the product into s, both errors into c.
+__device__ __forceinline__ void df_fma_x2(f32x2& s, f32x2& c, f32x2 a, f32x2 h, f32x2 l) {
+  const f32x2 p = x2_mul(a, h);
+  f32x2 e = x2_fma(a, h, x2_sub(0ull, p));
+  e = x2_fma(a, l, e);
+  const f32x2 t = x2_add(s, p);
+  const f32x2 bb = x2_sub(t, s);
+  const f32x2 err = x2_add(x2_sub(s, x2_sub(t, bb)), x2_sub(p, bb));
+  c = x2_add(c, x2_add(err, e));
+  s = t;
+}
+
+// Four rows (one float4 as two packed pairs) of one product term: double-float (kX2) or
+// float32 accumulation.
 template <int PREC>
-__device__ __forceinline__ void pacc4v(float* s, float* c, const float4 a, const float4 h, const float4 l) {
+__device__ __forceinline__ void pacc4x2(f32x2 (&s)[2], f32x2 (&c)[2], const ulonglong2 a, f32x2 h0, f32x2 h1,
+                                        f32x2 l0, f32x2 l1) {
   if (PREC == kX2) {
-    df_fma(s[0], c[0], a.x, h.x, l.x);
-    df_fma(s[1], c[1], a.y, h.y, l.y);
-    df_fma(s[2], c[2], a.z, h.z, l.z);
-    df_fma(s[3], c[3], a.w, h.w, l.w);
+    df_fma_x2(s[0], c[0], a.x, h0, l0);
+    df_fma_x2(s[1], c[1], a.y, h1, l1);
   } else {
-    s[0] = fmaf(a.x, h.x, s[0]);
-    s[1] = fmaf(a.y, h.y, s[1]);
-    s[2] = fmaf(a.z, h.z, s[2]);
-    s[3] = fmaf(a.w, h.w, s[3]);
+    s[0] = x2_fma(a.x, h0, s[0]);
+    s[1] = x2_fma(a.y, h1, s[1]);
   }
 }
 
@@ -87,14 +117,27 @@ __device__ __forceinline__ void pmerge(float& s, float& c, float s2, float c2) {
 template <int DP>
 __device__ __forceinline__ void dot_pair(const float4* colA, const float4* colB, const float4* srh,
                                          const float4* srl, int m4q, int lane, float2& ga, float2& gb) {
-  float sa[4] = {0.f, 0.f, 0.f, 0.f}, ca[4] = {0.f, 0.f, 0.f, 0.f};
-  float sb[4] = {0.f, 0.f, 0.f, 0.f}, cb[4] = {0.f, 0.f, 0.f, 0.f};
+  const ulonglong2* A2 = reinterpret_cast<const ulonglong2*>(colA);
+  const ulonglong2* B2 = reinterpret_cast<const ulonglong2*>(colB);
+  const ulonglong2* H2 = reinterpret_cast<const ulonglong2*>(srh);
+  const ulonglong2* L2 = reinterpret_cast<const ulonglong2*>(srl);
+  f32x2 sa2[2] = {0ull, 0ull}, ca2[2] = {0ull, 0ull}, sb2[2] = {0ull, 0ull}, cb2[2] = {0ull, 0ull};
 #pragma unroll 2
   for (int i = lane; i < m4q; i += 32) {
-    const float4 h = srh[i], l = srl[i];
-    pacc4v<DP>(sa, ca, colA[i], h, l);
-    pacc4v<DP>(sb, cb, colB[i], h, l);
+    const ulonglong2 h = H2[i];
+    const ulonglong2 l = DP == kX2 ? L2[i] : make_ulonglong2(0ull, 0ull);
+    pacc4x2<DP>(sa2, ca2, A2[i], h.x, h.y, l.x, l.y);
+    pacc4x2<DP>(sb2, cb2, B2[i], h.x, h.y, l.x, l.y);
   }
+  float sa[4], ca[4], sb[4], cb[4];
+  x2_unpack(sa2[0], sa[0], sa[1]);
+  x2_unpack(sa2[1], sa[2], sa[3]);
+  x2_unpack(ca2[0], ca[0], ca[1]);
+  x2_unpack(ca2[1], ca[2], ca[3]);
+  x2_unpack(sb2[0], sb[0], sb[1]);
+  x2_unpack(sb2[1], sb[2], sb[3]);
+  x2_unpack(cb2[0], cb[0], cb[1]);
+  x2_unpack(cb2[1], cb[2], cb[3]);
   pmerge<DP>(sa[0], ca[0], sa[1], ca[1]);
   pmerge<DP>(sa[2], ca[2], sa[3], ca[3]);
   pmerge<DP>(sa[0], ca[0], sa[2], ca[2]);
@@ -114,12 +157,12 @@ __device__ __forceinline__ void dot_pair(const float4* colA, const float4* colB,
   gb = df2_norm(sb[0], DP == kX2 ? cb[0] : 0.0f);
 }
 
-// q_slice += sum over one stage's columns of a_j x_j on the lane's rows (QT float4 chunks),
-// columns with x_j = 0 skipped (the test is uniform across the warp).  A stage holds at most
-// 8 columns: their x values are read together and the column loop is unrolled, so the
-// loads of several columns are in flight at once.
+// q_slice += sum over one stage's columns of a_j x_j on the lane's rows (QT float4 chunks,
+// as packed pairs), columns with x_j = 0 skipped (the test is uniform across the warp).  A
+// stage holds at most 8 columns: their x values are read together and the column loop is
+// unrolled, so the loads of several columns are in flight at once.
 template <int QP, int QT, int QW>
-__device__ __forceinline__ void q_stage(float (&qs)[QT][4], float (&qc)[QT][4], const float* sbase,
+__device__ __forceinline__ void q_stage(f32x2 (&qs)[QT][2], f32x2 (&qc)[QT][2], const float* sbase,
                                         const float2* sxs, int nc, int lda, int qw, int lane, int m4q) {
   float2 xs[8];
 #pragma unroll
@@ -127,14 +170,30 @@ __device__ __forceinline__ void q_stage(float (&qs)[QT][4], float (&qc)[QT][4], 
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     if (xs[c].x != 0.0f || xs[c].y != 0.0f) {
-      const float4* col = reinterpret_cast<const float4*>(sbase + (size_t)c * lda);
+      const ulonglong2* col = reinterpret_cast<const ulonglong2*>(sbase + (size_t)c * lda);
+      const f32x2 xh = x2_pack(xs[c].x, xs[c].x), xl = x2_pack(xs[c].y, xs[c].y);
 #pragma unroll
       for (int t = 0; t < QT; ++t) {
         const int c4 = qw * 32 + lane + t * 32 * QW;
-        if (c4 < m4q) pacc4<QP>(qs[t], qc[t], col[c4], xs[c].x, xs[c].y);
+        if (c4 < m4q) pacc4x2<QP>(qs[t], qc[t], col[c4], xh, xh, xl, xl);
       }
     }
   }
+}
+
+// The lane's q partials (row chunk c4 of t) as float4 pairs (hi, lo) of four rows.
+template <int QP>
+__device__ __forceinline__ void q_store(float2* part, int c4, const f32x2 (&s)[2], const f32x2 (&c)[2]) {
+  float s0, s1, s2, s3, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+  x2_unpack(s[0], s0, s1);
+  x2_unpack(s[1], s2, s3);
+  if (QP == kX2) {
+    x2_unpack(c[0], c0, c1);
+    x2_unpack(c[1], c2, c3);
+  }
+  float4* dst = reinterpret_cast<float4*>(part + 4 * c4);
+  dst[0] = make_float4(s0, c0, s1, c1);
+  dst[1] = make_float4(s2, c2, s3, c3);
 }
 
 __device__ __forceinline__ float2 clip2(float2 x, float2 lj, float2 uj) {
@@ -386,11 +445,11 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
   } else {
     // ---------------------------------------------------------------- q warps
     const int qw = warp - 1 - kPassDot;
-    float qs[QT][4], qc[QT][4];   // QT float4 row chunks per lane
+    f32x2 qs[QT][2], qc[QT][2];   // QT float4 row chunks per lane
 #pragma unroll
     for (int t = 0; t < QT; ++t)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) qs[t][c] = qc[t][c] = 0.f;
+      for (int c = 0; c < 2; ++c) qs[t][c] = qc[t][c] = 0ull;
     for (int g = 0; g < ngroups; ++g) {
       const int s = g % nstages;
       const int u = g / nstages;
@@ -408,11 +467,7 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
 #pragma unroll
     for (int t = 0; t < QT; ++t) {
       const int c4 = qw * 32 + lane + t * 32 * QW;
-      if (c4 < m4q) {
-        float4* dst = reinterpret_cast<float4*>(part + 4 * c4);
-        dst[0] = make_float4(qs[t][0], QP == kX2 ? qc[t][0] : 0.f, qs[t][1], QP == kX2 ? qc[t][1] : 0.f);
-        dst[1] = make_float4(qs[t][2], QP == kX2 ? qc[t][2] : 0.f, qs[t][3], QP == kX2 ? qc[t][3] : 0.f);
-      }
+      if (c4 < m4q) q_store<QP>(part, c4, qs[t], qc[t]);
     }
   }
   __syncthreads();
@@ -854,11 +909,11 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
     } else {
       // ------------------------------------------------------------ q warps
       const int qw = warp - 1 - kPassDot;
-      float qs[QT][4], qc[QT][4];
+      f32x2 qs[QT][2], qc[QT][2];
 #pragma unroll
       for (int t = 0; t < QT; ++t)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) qs[t][c] = qc[t][c] = 0.f;
+        for (int c = 0; c < 2; ++c) qs[t][c] = qc[t][c] = 0ull;
       for (int g = 0; g < ngroups; ++g) {
         const int gg = it * ngroups + g;
         const int s = gg % nstages;
@@ -876,11 +931,7 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
 #pragma unroll
       for (int t = 0; t < QT; ++t) {
         const int c4 = qw * 32 + lane + t * 32 * QW;
-        if (c4 < m4q) {
-          float4* dst = reinterpret_cast<float4*>(part + 4 * c4);
-          dst[0] = make_float4(qs[t][0], QP == kX2 ? qc[t][0] : 0.f, qs[t][1], QP == kX2 ? qc[t][1] : 0.f);
-          dst[1] = make_float4(qs[t][2], QP == kX2 ? qc[t][2] : 0.f, qs[t][3], QP == kX2 ? qc[t][3] : 0.f);
-        }
+        if (c4 < m4q) q_store<QP>(part, c4, qs[t], qc[t]);
       }
     }
 
