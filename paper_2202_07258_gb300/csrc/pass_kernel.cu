@@ -45,8 +45,8 @@ __host__ __device__ inline size_t iters_smem_bytes(int lda, int m4, int nstages,
 
 namespace {
 
-// ---- two float32 lanes in one 64-bit register: add / sub / mul / fma .f32x2 round each
-// lane exactly as the scalar instruction does, at one instruction for both lanes.
+// ---- two float32 lanes in one 64-bit register: add / sub / fma .f32x2 round each lane
+// exactly as the scalar instruction does, at one instruction for both lanes.
 typedef unsigned long long f32x2;
 
 __device__ __forceinline__ f32x2 x2_add(f32x2 a, f32x2 b) {
@@ -57,11 +57,6 @@ __device__ __forceinline__ f32x2 x2_add(f32x2 a, f32x2 b) {
 __device__ __forceinline__ f32x2 x2_sub(f32x2 a, f32x2 b) {
   f32x2 d;
   asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f32x2 x2_mul(f32x2 a, f32x2 b) {
-  f32x2 d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
   return d;
 }
 __device__ __forceinline__ f32x2 x2_fma(f32x2 a, f32x2 b, f32x2 c) {
@@ -79,9 +74,12 @@ __device__ __forceinline__ void x2_unpack(f32x2 v, float& lo, float& hi) {
 }
 
 // (s, c) += a (h + l) lane by lane, as df_fma: FMA TwoProd of a h, rounded a l, TwoSum of
-// the product into s, both errors into c.
+// the product into s, both errors into c.  The rounded product is formed as fma(a, h, +0):
+// a packed mul.rn whose result feeds a packed add.rn was found fused into one multiply-add
+// by the code generator (with or without volatile, with -fmad=false too), which leaves
+// TwoSum's error term wrong; the fma form is bit-identical to the scalar sequence.
 __device__ __forceinline__ void df_fma_x2(f32x2& s, f32x2& c, f32x2 a, f32x2 h, f32x2 l) {
-  const f32x2 p = x2_mul(a, h);
+  const f32x2 p = x2_fma(a, h, 0ull);
   f32x2 e = x2_fma(a, h, x2_sub(0ull, p));
   e = x2_fma(a, l, e);
   const f32x2 t = x2_add(s, p);
