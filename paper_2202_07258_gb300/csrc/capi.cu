@@ -459,9 +459,10 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
     std::vector<double> tv(m, -1.0);  // Proposition 2, case 3
     TRY(try_direction(h, tv, jinf, nrm, &ok));
     if (!ok) {
-      double* rs = nullptr;
+      double *rs = nullptr, *rs_part = nullptr;
       TRY(dalloc(h, &rs, m));
-      CK(launch_row_sums(h->A, h->lda, m, n, rs, h->s));
+      TRY(dalloc(h, &rs_part, row_sums_scratch(m, n)));
+      CK(launch_row_sums(h->A, h->lda, m, n, rs_part, rs, h->s));
       std::vector<double> s(m);
       CK(cudaMemcpyAsync(s.data(), rs, sizeof(double) * m, cudaMemcpyDeviceToHost, h->s));
       CK(cudaStreamSynchronize(h->s));
@@ -501,13 +502,45 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
     TRY(dalloc(h, &scal, 2));
     CK(cudaMemsetAsync(scal, 0, 2 * sizeof(double), h->s));
     CK(launch_power_init(v, n, h->s));
-    CK(launch_power_step(h->A, h->lda, m, n, v, q, v2, scal, h->s));
-    CK(cudaMemsetAsync(scal, 0, sizeof(double), h->s));
-    for (int it = 0; it < 100; ++it) CK(launch_power_step(h->A, h->lda, m, n, v, q, v2, scal, h->s));
-    double lam = 0.0;
-    CK(cudaMemcpyAsync(&lam, scal, sizeof(double), cudaMemcpyDeviceToHost, h->s));
-    CK(cudaStreamSynchronize(h->s));
-    h->L = lam > 0.0 ? 1.05 * lam : 1.0;
+    // one cooperative launch for all 101 steps when it fits, else one launch per product
+    bool done = false;
+    {
+      float *part = nullptr, *qc = nullptr;
+      double *wn2 = nullptr, *qn2 = nullptr;
+      unsigned* gb = nullptr;
+      TRY(dalloc(h, &part, (size_t)h->num_sms * h->lda));
+      TRY(dalloc(h, &qc, h->lda));
+      TRY(dalloc(h, &wn2, h->num_sms));
+      TRY(dalloc(h, &qn2, h->lda / 32));
+      TRY(dalloc(h, &gb, 2));
+      CK(cudaMemsetAsync(gb, 0, 2 * sizeof(unsigned), h->s));
+      const cudaError_t e = launch_power_coop(h->A, h->lda, m, n, v, part, qc, wn2, qn2, scal, gb, 101,
+                                              h->num_sms, h->s);
+      if (e == cudaSuccess) {
+        double sc[2] = {0.0, 0.0};
+        CK(cudaMemcpyAsync(sc, scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+        CK(cudaStreamSynchronize(h->s));
+        if (sc[1] >= 0.0) {
+          h->L = sc[0] > 0.0 ? 1.05 * sc[0] : 1.0;
+          done = true;
+        } else {
+          return set_err(BVLS_ETIMEOUT, "a device-side wait of the power iteration exceeded its bound");
+        }
+      } else if (e != cudaErrorNotSupported) {
+        CK(e);
+      } else {
+        cudaGetLastError();
+      }
+    }
+    if (!done) {
+      CK(launch_power_step(h->A, h->lda, m, n, v, q, v2, scal, h->s));
+      CK(cudaMemsetAsync(scal, 0, sizeof(double), h->s));
+      for (int it = 0; it < 100; ++it) CK(launch_power_step(h->A, h->lda, m, n, v, q, v2, scal, h->s));
+      double lam = 0.0;
+      CK(cudaMemcpyAsync(&lam, scal, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+      CK(cudaStreamSynchronize(h->s));
+      h->L = lam > 0.0 ? 1.05 * lam : 1.0;
+    }
   }
 
   // Workspace of the solve loop and launch shapes.

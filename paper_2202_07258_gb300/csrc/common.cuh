@@ -28,7 +28,8 @@ constexpr int kMaxRows = 24576;   // r is staged in shared memory: 8 bytes per r
 constexpr int kPassDot = 8;       // dot warps of the fused pass
 constexpr int kPassTmax = 8;      // float4 row chunks owned by one lane of a q warp
 constexpr int kPassMaxStages = 32;
-constexpr int kMaxGridFlags = 1024;  // grid barrier flags of the persistent pass (one per CTA)
+constexpr int kMaxGridFlags = 1024;  // grid barrier words of the persistent pass
+constexpr long long kGridWaitCycles = 4000000000LL;  // bounded grid-barrier wait (about 2 s)
 
 enum DualMode { kScaling = 0, kTranslation = 1, kZero = 2 };
 // kMix: float32 correlations a_j^T r, double-float forward product A_S x (the values of the
@@ -216,6 +217,34 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// One arrival of this CTA at the grid barrier (gb[0] arrivals, gb[1] generation) and a
+// bounded wait for the others; called by one thread once the CTA's participating threads
+// have synchronised.
+// The last arrival resets the count and then publishes the next generation.
+__device__ inline bool grid_arrive_wait(unsigned* gb, unsigned nblocks, unsigned gen) {
+  __threadfence();
+  const unsigned prev = atomicAdd(&gb[0], 1u);
+  if (prev == nblocks - 1) {
+    atomicExch(&gb[0], 0u);
+    __threadfence();
+    atomicAdd(&gb[1], 1u);
+    return true;
+  }
+  if (ld_acquire_u32(&gb[1]) != gen) return true;
+  const long long t0 = clock64();
+  while (ld_acquire_u32(&gb[1]) == gen) {
+    if (clock64() - t0 > kGridWaitCycles) return false;
+  }
+  __threadfence();
+  return true;
+}
+
 // All lanes of a warp agree on the outcome of a bounded wait.
 __device__ __forceinline__ bool warp_all(bool ok) { return __all_sync(0xffffffffu, ok) != 0; }
 
@@ -310,9 +339,19 @@ cudaError_t launch_check_finite(const float* A, int lda, int m, int n, int* flag
 cudaError_t launch_col_norms(const float* A, int lda, int m, int n, double* nrm, cudaStream_t s);
 cudaError_t launch_col_dots(const float* A, int lda, int m, int n, const double* t, double* w,
                             cudaStream_t s);
-cudaError_t launch_row_sums(const float* A, int lda, int m, int n, double* out, cudaStream_t s);
+// out_i = sum_j a_ij (deterministic); part: row_sums_scratch(m, n) doubles.
+size_t row_sums_scratch(int m, int n);
+cudaError_t launch_row_sums(const float* A, int lda, int m, int n, double* part, double* out, cudaStream_t s);
 cudaError_t launch_power_step(const float* A, int lda, int m, int n, float* v, float* q, float* v2,
                               double* scal, cudaStream_t s);
 cudaError_t launch_power_init(float* v, int n, cudaStream_t s);
+// All power steps in one cooperative launch (one CTA per SM, lda <= 8192): `steps` steps
+// v <- A^T A v / ||A^T A v|| from v (unit or not); scal[0] = the largest ||A v||^2 over the
+// steps after the first.  gb: two zeroed words (grid barrier); part: grid x lda floats;
+// q: lda floats; wn2: grid doubles; qn2: lda / 32 doubles.  Returns cudaErrorNotSupported
+// when the launch shape does not fit.
+cudaError_t launch_power_coop(const float* A, int lda, int m, int n, float* v, float* part, float* q,
+                              double* wn2, double* qn2, double* scal, unsigned* gb, int steps, int grid,
+                              cudaStream_t s);
 
 }  // namespace bvls

@@ -620,37 +620,10 @@ __global__ void __launch_bounds__(256) k_resid(Params p, Buffers b, int slot, in
 
 namespace {
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
 // Named barrier 1 over the CTA's consumer warps (all warps but the producer).
 template <int NCONS>
 __device__ __forceinline__ void consumer_sync() {
   asm volatile("bar.sync 1, %0;" ::"r"(NCONS) : "memory");
-}
-
-// One arrival of this CTA at the grid barrier (gb[0] arrivals, gb[1] generation) and a
-// bounded wait for the others; called by one thread after the CTA's consumers synchronised.
-// The last arrival resets the count and then publishes the next generation.
-__device__ bool grid_arrive_wait(unsigned* gb, unsigned nblocks, unsigned gen) {
-  __threadfence();
-  const unsigned prev = atomicAdd(&gb[0], 1u);
-  if (prev == nblocks - 1) {
-    atomicExch(&gb[0], 0u);
-    __threadfence();
-    atomicAdd(&gb[1], 1u);
-    return true;
-  }
-  if (ld_acquire_u32(&gb[1]) != gen) return true;
-  const long long t0 = clock64();
-  while (ld_acquire_u32(&gb[1]) == gen) {
-    if (clock64() - t0 > kWaitCycles) return false;
-  }
-  __threadfence();
-  return true;
 }
 
 // Scalars of the step that starts from t_k = T[ti]: t_{k+1} without restart and beta as

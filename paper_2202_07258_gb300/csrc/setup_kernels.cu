@@ -1,8 +1,8 @@
 // Kernels run once per matrix by bvls_setup: finiteness check, column norms ||a_j||_2
 // (used by the sphere test of Eq. (safe_rule)), w = A^T t for the dual translation of
 // Section 4.2, the row sums used to build candidate directions t, and a power iteration
-// for the step constant L ~ ||A||_2^2.  These run once, so they favour plainness (float64
-// accumulation, simple mappings) over speed.
+// for the step constant L ~ ||A||_2^2.  These run once per matrix; the power iteration,
+// a hundred passes over A, runs in one cooperative launch when its shape fits.
 #include "common.cuh"
 
 namespace bvls {
@@ -62,17 +62,33 @@ cudaError_t launch_col_dots(const float* A, int lda, int m, int n, const double*
   return cudaGetLastError();
 }
 
-// out_i = sum_j a_ij, deterministic: thread per row, columns in order.
-__global__ void k_row_sums(const float* __restrict__ A, int lda, int m, int n, double* out) {
+// out_i = sum_j a_ij, deterministic: column chunks of 64 give per-chunk partials (threads
+// over rows, columns in order), then the partials are summed in chunk order.
+constexpr int kRowSumCols = 64;
+
+__global__ void k_row_sums_part(const float* __restrict__ A, int lda, int m, int n, double* part) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const int j0 = blockIdx.y * kRowSumCols, j1 = min(n, j0 + kRowSumCols);
+  double s = 0.0;
+  for (int j = j0; j < j1; ++j) s += (double)A[(size_t)j * lda + i];
+  part[(size_t)blockIdx.y * m + i] = s;
+}
+
+__global__ void k_row_sums_reduce(const double* part, int m, int nchunks, double* out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
   double s = 0.0;
-  for (int j = 0; j < n; ++j) s += (double)A[(size_t)j * lda + i];
+  for (int c = 0; c < nchunks; ++c) s += part[(size_t)c * m + i];
   out[i] = s;
 }
 
-cudaError_t launch_row_sums(const float* A, int lda, int m, int n, double* out, cudaStream_t s) {
-  k_row_sums<<<(m + 127) / 128, 128, 0, s>>>(A, lda, m, n, out);
+size_t row_sums_scratch(int m, int n) { return (size_t)m * ((n + kRowSumCols - 1) / kRowSumCols); }
+
+cudaError_t launch_row_sums(const float* A, int lda, int m, int n, double* part, double* out, cudaStream_t s) {
+  const int nchunks = (n + kRowSumCols - 1) / kRowSumCols;
+  k_row_sums_part<<<dim3((m + 127) / 128, nchunks), 128, 0, s>>>(A, lda, m, n, part);
+  k_row_sums_reduce<<<(m + 127) / 128, 128, 0, s>>>(part, m, nchunks, out);
   return cudaGetLastError();
 }
 
@@ -160,6 +176,174 @@ cudaError_t launch_power_step(const float* A, int lda, int m, int n, float* v, f
   k_power_norms<<<1, 1024, 0, s>>>(q, m, v2, n, scal);
   k_power_scale<<<256, 256, 0, s>>>(v, v2, n, scal);
   return cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------- power iteration, one launch
+// One CTA per SM owns a contiguous range of columns and keeps their v_j in shared memory.
+// Each step: (1) the CTA's partial of q = A v over its columns (threads over rows);
+// grid barrier; (2) q from the partials in 32-row slices spread over the CTAs, with the slice
+// partials of ||q||^2; grid barrier; (3) q into shared memory, w_j = a_j^T q for the CTA's
+// columns (warp per column) and the CTA's partial of ||w||^2; grid barrier; every CTA sums
+// the ||w||^2 partials in the same order and sets v = w / ||w||.  ||A v||^2 = ||q||^2 is the
+// Rayleigh quotient of the unit v.  float32 products, float64 norms.
+constexpr int kPowThreads = 512;
+constexpr int kPowChunks = 4;   // float4 row chunks per thread: lda <= 4 * 4 * 512 = 8192
+
+__global__ void __launch_bounds__(kPowThreads, 1)
+    k_power_coop(const float* __restrict__ A, int lda, int m, int n, float* v, float* part, float* q, double* wn2,
+                 double* qn2, double* scal, unsigned* gb, int steps) {
+  extern __shared__ __align__(16) float psm[];
+  const int lda4 = lda >> 2;
+  const int per = (n + gridDim.x - 1) / gridDim.x;
+  const int j0 = min(n, (int)blockIdx.x * per), j1 = min(n, j0 + per);
+  float* sq = psm;             // q (lda)
+  float* sv = psm + lda;       // v of the CTA's columns (per)
+  __shared__ double s_red[kPowThreads / 32];
+  __shared__ float2 s_part[kPowThreads / 32][32];
+  __shared__ int s_ok;
+  __shared__ float s_scale;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = kPowThreads / 32;
+  const int nslices = lda / 32;
+  unsigned gen = 0;
+  if (tid == 0) {
+    gen = ld_acquire_u32(&gb[1]);
+    s_ok = 1;
+  }
+  for (int j = j0 + tid; j < j1; j += kPowThreads) sv[j - j0] = v[j];
+  __syncthreads();
+  double lam = 0.0;
+  auto barrier = [&]() -> bool {
+    __syncthreads();
+    if (tid == 0 && !grid_arrive_wait(gb, gridDim.x, gen++)) s_ok = 0;
+    __syncthreads();
+    return s_ok != 0;
+  };
+  for (int it = 0; it < steps; ++it) {
+    // (1) the CTA's partial of A v
+    float4 acc[kPowChunks];
+#pragma unroll
+    for (int k = 0; k < kPowChunks; ++k) acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4* A4 = reinterpret_cast<const float4*>(A);
+    for (int j = j0; j < j1; ++j) {
+      const float vj = sv[j - j0];
+#pragma unroll
+      for (int k = 0; k < kPowChunks; ++k) {
+        const int c = tid + k * kPowThreads;
+        if (c < lda4) {
+          const float4 a = A4[(size_t)j * lda4 + c];
+          acc[k].x = fmaf(a.x, vj, acc[k].x);
+          acc[k].y = fmaf(a.y, vj, acc[k].y);
+          acc[k].z = fmaf(a.z, vj, acc[k].z);
+          acc[k].w = fmaf(a.w, vj, acc[k].w);
+        }
+      }
+    }
+    float4* p4 = reinterpret_cast<float4*>(part + (size_t)blockIdx.x * lda);
+#pragma unroll
+    for (int k = 0; k < kPowChunks; ++k) {
+      const int c = tid + k * kPowThreads;
+      if (c < lda4) p4[c] = acc[k];
+    }
+    if (!barrier()) break;
+    // (2) q in 32-row slices, slice partials of ||q||^2
+    for (int sl = blockIdx.x; sl < nslices; sl += gridDim.x) {
+      const int row = sl * 32 + lane;
+      float sum = 0.f;
+      for (int t = warp; t < (int)gridDim.x; t += NW) sum += __ldcg(part + (size_t)t * lda + row);
+      s_part[warp][lane] = make_float2(sum, 0.f);
+      __syncthreads();
+      if (warp == 0) {
+        float qi = 0.f;
+        for (int w = 0; w < NW; ++w) qi += s_part[w][lane].x;
+        q[row] = qi;
+        double q2 = (double)qi * (double)qi;
+        q2 = warp_sum_d(q2);
+        if (lane == 0) qn2[sl] = q2;
+      }
+      __syncthreads();
+    }
+    if (!barrier()) break;
+    // (3) w = A^T q on the CTA's columns, partial of ||w||^2
+    for (int i = tid; i < lda; i += kPowThreads) sq[i] = __ldcg(q + i);
+    if (it > 0 && blockIdx.x == 0 && warp == 0) {
+      double q2 = 0.0;
+      for (int t = lane; t < nslices; t += 32) q2 += __ldcg(qn2 + t);
+      q2 = warp_sum_d(q2);
+      lam = fmax(lam, q2);
+    }
+    __syncthreads();
+    double w2 = 0.0;
+    const float4* sq4 = reinterpret_cast<const float4*>(sq);
+    for (int j = j0 + warp; j < j1; j += NW) {
+      const float4* a = A4 + (size_t)j * lda4;
+      float s0 = 0.f, s1 = 0.f;
+      for (int c = lane; c < lda4; c += 32) {
+        const float4 av = a[c], qv = sq4[c];
+        s0 = fmaf(av.x, qv.x, s0);
+        s1 = fmaf(av.y, qv.y, s1);
+        s0 = fmaf(av.z, qv.z, s0);
+        s1 = fmaf(av.w, qv.w, s1);
+      }
+      float s = s0 + s1;
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) {
+        sv[j - j0] = s;
+        w2 += (double)s * (double)s;
+      }
+    }
+    if (lane == 0) s_red[warp] = w2;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < NW; ++w) t += s_red[w];
+      wn2[blockIdx.x] = t;
+    }
+    if (!barrier()) break;
+    // every CTA: the same sum of the ||w||^2 partials, then v = w / ||w||
+    if (warp == 0) {
+      double t = 0.0;
+      for (int c = lane; c < (int)gridDim.x; c += 32) t += __ldcg(wn2 + c);
+      t = warp_sum_d(t);
+      if (lane == 0) s_scale = t > 0.0 ? (float)(1.0 / sqrt(t)) : 0.f;
+    }
+    __syncthreads();
+    for (int j = j0 + tid; j < j1; j += kPowThreads) sv[j - j0] *= s_scale;
+    __syncthreads();
+  }
+  for (int j = j0 + tid; j < j1; j += kPowThreads) v[j] = sv[j - j0];
+  if (blockIdx.x == 0 && tid == 0) {
+    scal[0] = lam;
+    if (!s_ok) scal[1] = -1.0;   // a barrier wait gave up: the caller falls back
+  }
+}
+
+cudaError_t launch_power_coop(const float* A, int lda, int m, int n, float* v, float* part, float* q,
+                              double* wn2, double* qn2, double* scal, unsigned* gb, int steps, int grid,
+                              cudaStream_t s) {
+  if (lda > 4 * kPowChunks * kPowThreads || lda % 32 != 0 || grid < 1) return cudaErrorNotSupported;
+  const int per = (n + grid - 1) / grid;
+  const size_t sm = sizeof(float) * ((size_t)lda + per);
+  cudaError_t e = cudaFuncSetAttribute(k_power_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0, dev = 0, sms = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_power_coop, kPowThreads, sm);
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1 || grid > per_sm * sms) return cudaErrorNotSupported;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kPowThreads);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_power_coop, A, lda, m, n, v, part, q, wn2, qn2, scal, gb, steps);
 }
 
 }  // namespace bvls
