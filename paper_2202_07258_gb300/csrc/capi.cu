@@ -130,6 +130,26 @@ void free_handle(bvls_handle* h) {
   delete h;
 }
 
+// The momentum table of the persistent pass (T[0] = 1, T[i+1] = (1 + sqrt(1 + 4 T[i]^2)) / 2),
+// computed once per process in float64.
+const std::vector<MomEntry>& momentum_table() {
+  static const std::vector<MomEntry> tab = [] {
+    std::vector<MomEntry> v(kMomTable);
+    double t = 1.0;
+    for (int i = 0; i < kMomTable; ++i) {
+      const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
+      const double beta = (t - 1.0) / tn;
+      v[i].t = t;
+      v[i].tn = tn;
+      v[i].beta2 = df2_from_double(beta);
+      v[i].onepb2 = df2_from_double(1.0 + beta);
+      t = tn;
+    }
+    return v;
+  }();
+  return tab;
+}
+
 // w = A^T t for a host direction t; returns whether a_j^T t < 0 (with its rounding bound)
 // on every nonzero column with u_j = +inf.
 bvls_status try_direction(bvls_handle* h, const std::vector<double>& t,
@@ -593,18 +613,8 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
   TRY(dalloc(h, &b.gbar, kMaxGridFlags));
   TRY(dalloc(h, &h->mom, kMomTable));
   {
-    std::vector<MomEntry> tab(kMomTable);
-    double t = 1.0;
-    for (int i = 0; i < kMomTable; ++i) {
-      const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
-      const double beta = (t - 1.0) / tn;
-      tab[i].t = t;
-      tab[i].tn = tn;
-      tab[i].beta2 = df2_from_double(beta);
-      tab[i].onepb2 = df2_from_double(1.0 + beta);
-      t = tn;
-    }
-    CK(cudaMemcpy(h->mom, tab.data(), sizeof(MomEntry) * kMomTable, cudaMemcpyHostToDevice));
+    const std::vector<MomEntry>& tab = momentum_table();
+    CK(cudaMemcpyAsync(h->mom, tab.data(), sizeof(MomEntry) * kMomTable, cudaMemcpyHostToDevice, h->s));
   }
   TRY(dalloc(h, &b.xout, n));
   TRY(dalloc(h, &h->y_dev, h->m4));

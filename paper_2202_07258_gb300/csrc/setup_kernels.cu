@@ -226,18 +226,32 @@ __global__ void __launch_bounds__(kPowThreads, 1)
 #pragma unroll
     for (int k = 0; k < kPowChunks; ++k) acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     const float4* A4 = reinterpret_cast<const float4*>(A);
-    for (int j = j0; j < j1; ++j) {
-      const float vj = sv[j - j0];
 #pragma unroll
-      for (int k = 0; k < kPowChunks; ++k) {
-        const int c = tid + k * kPowThreads;
-        if (c < lda4) {
-          const float4 a = A4[(size_t)j * lda4 + c];
-          acc[k].x = fmaf(a.x, vj, acc[k].x);
-          acc[k].y = fmaf(a.y, vj, acc[k].y);
-          acc[k].z = fmaf(a.z, vj, acc[k].z);
-          acc[k].w = fmaf(a.w, vj, acc[k].w);
+    for (int k = 0; k < kPowChunks; ++k) {
+      const int c = tid + k * kPowThreads;
+      if (c >= lda4) continue;
+      // eight columns' loads in flight per round (the loads, not the FMAs, set the pace)
+      int j = j0;
+      for (; j + 8 <= j1; j += 8) {
+        float4 a[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a[u] = A4[(size_t)(j + u) * lda4 + c];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const float vj = sv[j + u - j0];
+          acc[k].x = fmaf(a[u].x, vj, acc[k].x);
+          acc[k].y = fmaf(a[u].y, vj, acc[k].y);
+          acc[k].z = fmaf(a[u].z, vj, acc[k].z);
+          acc[k].w = fmaf(a[u].w, vj, acc[k].w);
         }
+      }
+      for (; j < j1; ++j) {
+        const float4 a = A4[(size_t)j * lda4 + c];
+        const float vj = sv[j - j0];
+        acc[k].x = fmaf(a.x, vj, acc[k].x);
+        acc[k].y = fmaf(a.y, vj, acc[k].y);
+        acc[k].z = fmaf(a.z, vj, acc[k].z);
+        acc[k].w = fmaf(a.w, vj, acc[k].w);
       }
     }
     float4* p4 = reinterpret_cast<float4*>(part + (size_t)blockIdx.x * lda);
