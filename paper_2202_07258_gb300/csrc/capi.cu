@@ -59,7 +59,7 @@ struct GraphKey {
 struct bvls_handle {
   int m = 0, n = 0, lda = 0, m4 = 0, num_sms = 0;
   cudaStream_t user = nullptr, s = nullptr;
-  cudaEvent_t ev_in = nullptr, poll[2] = {nullptr, nullptr};
+  cudaEvent_t ev_in = nullptr;
   float* A = nullptr;
   double *l = nullptr, *u = nullptr, *nrm = nullptr, *w = nullptr, *t = nullptr;
   float2 *l2 = nullptr, *u2 = nullptr;
@@ -71,7 +71,6 @@ struct bvls_handle {
   float* y_dev = nullptr;
   double* x0_dev = nullptr;
   double *theta_dev = nullptr, *wstar_dev = nullptr;  // fixed dual point and A^T theta
-  int* pinned = nullptr;
   int fwd_tiles = 0, fwd_chunks = 0, tr_blocks = 0, red_blocks = 0;
   int pass_stages = 0, pass_qw = 0, pass_cps = 1;  // fused single-pass iteration when pass_stages > 0
   bool pass_coop = false;
@@ -122,10 +121,7 @@ void free_handle(bvls_handle* h) {
   for (void* p : h->b_allocs) cudaFree(p);
   for (auto e : h->prof) cudaEventDestroy(e);
   for (void* p : h->allocs) cudaFree(p);
-  if (h->pinned) cudaFreeHost(h->pinned);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
-  for (auto e : h->poll)
-    if (e) cudaEventDestroy(e);
   if (h->s && h->own_stream) cudaStreamDestroy(h->s);
   delete h;
 }
@@ -415,9 +411,6 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
     h->own_stream = true;
   }
   CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
-  CK(cudaEventCreateWithFlags(&h->poll[0], cudaEventDisableTiming));
-  CK(cudaEventCreateWithFlags(&h->poll[1], cudaEventDisableTiming));
-  CK(cudaHostAlloc(reinterpret_cast<void**>(&h->pinned), 4 * sizeof(int), cudaHostAllocDefault));
   if (h->own_stream) {
     CK(cudaEventRecord(h->ev_in, h->user));
     CK(cudaStreamWaitEvent(h->s, h->ev_in, 0));

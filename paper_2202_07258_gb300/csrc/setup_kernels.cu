@@ -181,12 +181,16 @@ cudaError_t launch_power_step(const float* A, int lda, int m, int n, float* v, f
 
 // ---------------------------------------------------------------- power iteration, one launch
 // One CTA per SM owns a contiguous range of columns and keeps their v_j in shared memory.
-// Each step: (1) the CTA's partial of q = A v over its columns (threads over rows);
-// grid barrier; (2) q from the partials in 32-row slices spread over the CTAs, with the slice
-// partials of ||q||^2; grid barrier; (3) q into shared memory, w_j = a_j^T q for the CTA's
-// columns (warp per column) and the CTA's partial of ||w||^2; grid barrier; every CTA sums
-// the ||w||^2 partials in the same order and sets v = w / ||w||.  ||A v||^2 = ||q||^2 is the
-// Rayleigh quotient of the unit v.  float32 products, float64 norms.
+// A step has two phases, each ended by a grid barrier:
+//   columns  w_j = a_j^T q for the CTA's columns (warp per column, q in shared memory) and
+//            the CTA's partial of ||w||^2; then the CTA's partial of A w over the same
+//            columns (threads over rows, eight column loads in flight);
+//   rows     every CTA sums the ||w||^2 partials in the same order (s = 1 / ||w||), so
+//            v = s w and q = A v = s (sum of the partials), formed in 32-row slices over the
+//            CTAs with the slice partials of ||q||^2 = ||A v||^2, the Rayleigh quotient of
+//            the unit v.
+// The first step starts from v (not normalised) instead of a w, and its quotient is not
+// counted.  float32 products, float64 norms.
 constexpr int kPowThreads = 512;
 constexpr int kPowChunks = 4;   // float4 row chunks per thread: lda <= 4 * 4 * 512 = 8192
 
@@ -198,14 +202,15 @@ __global__ void __launch_bounds__(kPowThreads, 1)
   const int per = (n + gridDim.x - 1) / gridDim.x;
   const int j0 = min(n, (int)blockIdx.x * per), j1 = min(n, j0 + per);
   float* sq = psm;             // q (lda)
-  float* sv = psm + lda;       // v of the CTA's columns (per)
+  float* sv = psm + lda;       // v (or w) of the CTA's columns (per)
   __shared__ double s_red[kPowThreads / 32];
-  __shared__ float2 s_part[kPowThreads / 32][32];
+  __shared__ float s_part[kPowThreads / 32][32];
   __shared__ int s_ok;
   __shared__ float s_scale;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NW = kPowThreads / 32;
   const int nslices = lda / 32;
+  const float4* A4 = reinterpret_cast<const float4*>(A);
   unsigned gen = 0;
   if (tid == 0) {
     gen = ld_acquire_u32(&gb[1]);
@@ -221,16 +226,44 @@ __global__ void __launch_bounds__(kPowThreads, 1)
     return s_ok != 0;
   };
   for (int it = 0; it < steps; ++it) {
-    // (1) the CTA's partial of A v
+    // ---- columns: w = A^T q (from the second step on), then the partial of A w
+    if (it > 0) {
+      for (int i = tid; i < lda; i += kPowThreads) sq[i] = __ldcg(q + i);
+      __syncthreads();
+      double w2 = 0.0;
+      const float4* sq4 = reinterpret_cast<const float4*>(sq);
+      for (int j = j0 + warp; j < j1; j += NW) {
+        const float4* a = A4 + (size_t)j * lda4;
+        float s0 = 0.f, s1 = 0.f;
+        for (int c = lane; c < lda4; c += 32) {
+          const float4 av = a[c], qv = sq4[c];
+          s0 = fmaf(av.x, qv.x, s0);
+          s1 = fmaf(av.y, qv.y, s1);
+          s0 = fmaf(av.z, qv.z, s0);
+          s1 = fmaf(av.w, qv.w, s1);
+        }
+        float s = s0 + s1;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+          sv[j - j0] = s;
+          w2 += (double)s * (double)s;
+        }
+      }
+      if (lane == 0) s_red[warp] = w2;
+      __syncthreads();
+      if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < NW; ++w) t += s_red[w];
+        wn2[blockIdx.x] = t;
+      }
+    }
     float4 acc[kPowChunks];
 #pragma unroll
     for (int k = 0; k < kPowChunks; ++k) acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4* A4 = reinterpret_cast<const float4*>(A);
 #pragma unroll
     for (int k = 0; k < kPowChunks; ++k) {
       const int c = tid + k * kPowThreads;
       if (c >= lda4) continue;
-      // eight columns' loads in flight per round (the loads, not the FMAs, set the pace)
       int j = j0;
       for (; j + 8 <= j1; j += 8) {
         float4 a[8];
@@ -261,16 +294,29 @@ __global__ void __launch_bounds__(kPowThreads, 1)
       if (c < lda4) p4[c] = acc[k];
     }
     if (!barrier()) break;
-    // (2) q in 32-row slices, slice partials of ||q||^2
+    // ---- rows: s = 1 / ||w|| (1 at the first step), v = s w, q = s (sum of the partials)
+    if (warp == 0) {
+      double t = 1.0;
+      if (it > 0) {
+        t = 0.0;
+        for (int c = lane; c < (int)gridDim.x; c += 32) t += __ldcg(wn2 + c);
+        t = warp_sum_d(t);
+      }
+      if (lane == 0) s_scale = t > 0.0 ? (float)(1.0 / sqrt(t)) : 0.f;
+    }
+    __syncthreads();
+    const float sc = s_scale;
+    for (int j = j0 + tid; j < j1; j += kPowThreads) sv[j - j0] *= sc;
     for (int sl = blockIdx.x; sl < nslices; sl += gridDim.x) {
       const int row = sl * 32 + lane;
       float sum = 0.f;
       for (int t = warp; t < (int)gridDim.x; t += NW) sum += __ldcg(part + (size_t)t * lda + row);
-      s_part[warp][lane] = make_float2(sum, 0.f);
+      s_part[warp][lane] = sum;
       __syncthreads();
       if (warp == 0) {
         float qi = 0.f;
-        for (int w = 0; w < NW; ++w) qi += s_part[w][lane].x;
+        for (int w = 0; w < NW; ++w) qi += s_part[w][lane];
+        qi *= sc;
         q[row] = qi;
         double q2 = (double)qi * (double)qi;
         q2 = warp_sum_d(q2);
@@ -279,57 +325,18 @@ __global__ void __launch_bounds__(kPowThreads, 1)
       __syncthreads();
     }
     if (!barrier()) break;
-    // (3) w = A^T q on the CTA's columns, partial of ||w||^2
-    for (int i = tid; i < lda; i += kPowThreads) sq[i] = __ldcg(q + i);
     if (it > 0 && blockIdx.x == 0 && warp == 0) {
       double q2 = 0.0;
       for (int t = lane; t < nslices; t += 32) q2 += __ldcg(qn2 + t);
       q2 = warp_sum_d(q2);
       lam = fmax(lam, q2);
     }
-    __syncthreads();
-    double w2 = 0.0;
-    const float4* sq4 = reinterpret_cast<const float4*>(sq);
-    for (int j = j0 + warp; j < j1; j += NW) {
-      const float4* a = A4 + (size_t)j * lda4;
-      float s0 = 0.f, s1 = 0.f;
-      for (int c = lane; c < lda4; c += 32) {
-        const float4 av = a[c], qv = sq4[c];
-        s0 = fmaf(av.x, qv.x, s0);
-        s1 = fmaf(av.y, qv.y, s1);
-        s0 = fmaf(av.z, qv.z, s0);
-        s1 = fmaf(av.w, qv.w, s1);
-      }
-      float s = s0 + s1;
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) {
-        sv[j - j0] = s;
-        w2 += (double)s * (double)s;
-      }
-    }
-    if (lane == 0) s_red[warp] = w2;
-    __syncthreads();
-    if (tid == 0) {
-      double t = 0.0;
-      for (int w = 0; w < NW; ++w) t += s_red[w];
-      wn2[blockIdx.x] = t;
-    }
-    if (!barrier()) break;
-    // every CTA: the same sum of the ||w||^2 partials, then v = w / ||w||
-    if (warp == 0) {
-      double t = 0.0;
-      for (int c = lane; c < (int)gridDim.x; c += 32) t += __ldcg(wn2 + c);
-      t = warp_sum_d(t);
-      if (lane == 0) s_scale = t > 0.0 ? (float)(1.0 / sqrt(t)) : 0.f;
-    }
-    __syncthreads();
-    for (int j = j0 + tid; j < j1; j += kPowThreads) sv[j - j0] *= s_scale;
-    __syncthreads();
   }
+  __syncthreads();
   for (int j = j0 + tid; j < j1; j += kPowThreads) v[j] = sv[j - j0];
   if (blockIdx.x == 0 && tid == 0) {
     scal[0] = lam;
-    if (!s_ok) scal[1] = -1.0;   // a barrier wait gave up: the caller falls back
+    if (!s_ok) scal[1] = -1.0;   // a barrier wait gave up: the caller reports it
   }
 }
 
