@@ -41,6 +41,10 @@ WORKLOAD_DESC = ("NNLS, A 2000x10000 iid N(0,1) unit columns, x0 5% nonzeros U[0
 VARIANT = "nnls_abs_gaussian_2000x10000"
 TOL = 1e-6
 K_SCREEN = 10
+# Products of the timed single-instance solve: float32 correlations A^T r with the forward
+# product A x and the residual in double-float, gap / radius / test in float64 (the workload's
+# dual point is theta = 0, whose certificate uses only the residual).
+HEAD_PRECISION = "mixed"
 FLUSH_BYTES = 256 << 20
 
 
@@ -157,28 +161,37 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- GPU leg
-def timed_solves(solver, y_dev, flush, stream, steps, warmup, dual_point=None, **kw):
+def timed_solves(solver, y_dev, flush, stream, steps, warmup, variants, dual_point=None):
+    """Time `steps` solves of each variant (name -> make_opts keywords; a variant with
+    dual=True uses dual_point).  The variants alternate step by step on the same handle, so a
+    slow drift of the clocks affects them alike.  Returns name -> (times_ms, infos)."""
     import torch
     from paper_2202_07258_gb300 import make_opts
-    opts = make_opts(tol=TOL, screen_every=K_SCREEN, **kw)
-    if dual_point is not None:
-        opts.dual_point = dual_point.data_ptr()
-    infos = []
+    opts = {}
+    for name, kw in variants.items():
+        kw = dict(kw)
+        use_dual = kw.pop("dual", False)
+        o = make_opts(tol=TOL, screen_every=K_SCREEN, **kw)
+        if use_dual:
+            o.dual_point = dual_point.data_ptr()
+        opts[name] = o
     for _ in range(warmup):
-        solver.solve(y_dev, opts=opts)
-    times = []
+        for o in opts.values():
+            solver.solve(y_dev, opts=o)
+    out = {name: ([], []) for name in opts}
     with torch.cuda.stream(stream):
         for _ in range(steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            x, s, info, st = solver.solve(y_dev, opts=opts)
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-            infos.append(info)
-    return times, infos, x, s
+            for name, o in opts.items():
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                x, s, info, st = solver.solve(y_dev, opts=o)
+                e1.record(stream)
+                e1.synchronize()
+                out[name][0].append(e0.elapsed_time(e1))
+                out[name][1].append(info)
+    return out
 
 
 def kernel_hash():
@@ -193,7 +206,8 @@ def kernel_hash():
 def roofline(solver, y_dev, m):
     """Profile-mode solve: CUDA events around every product launch on the launching stream."""
     from paper_2202_07258_gb300 import make_opts
-    x, s, info, st = solver.solve(y_dev, opts=make_opts(tol=TOL, screen_every=K_SCREEN, profile=True))
+    x, s, info, st = solver.solve(y_dev, opts=make_opts(tol=TOL, screen_every=K_SCREEN, profile=True,
+                                                        precision=HEAD_PRECISION))
     nl = max(1, info["tr_launches"])
     if info["single_pass"] == 2:
         # persistent form: each launch runs K iterations (one read of A_S each) and their
@@ -297,9 +311,11 @@ def table2_leg(dev, stream, flush, steps):
     out = {"workload": "bvls_table2_1000x2000 (A |N(0,1)| unit columns, x0 5% U(0,1), noise N(0,1), box [0,1])"}
     for alg in ("fista", "cp"):
         res = {}
-        for scr in (True, False):
-            times, infos, x, s = timed_solves(solver, y, flush, stream, steps, 1, screening=scr, algorithm=alg)
-            res["screened" if scr else "unscreened"] = {
+        runs = timed_solves(solver, y, flush, stream, steps, 1,
+                            {"screened": dict(screening=True, algorithm=alg),
+                             "unscreened": dict(screening=False, algorithm=alg)})
+        for name, (times, infos) in runs.items():
+            res[name] = {
                 "instances_per_s": 1000.0 * len(times) / sum(times), "iters": infos[-1]["iters"],
                 "gap": infos[-1]["gap"],
                 "avg_preserved_fraction": infos[-1]["sum_preserved"] / max(1, infos[-1]["iters"]) / 2000}
@@ -377,7 +393,7 @@ def e2e_leg(p, steps, stream):
     u_h = np.full(n, np.inf)
     x_h = torch.empty(n, dtype=torch.float64).pin_memory()
     s_h = torch.empty(n, dtype=torch.uint8).pin_memory()
-    opts = make_opts(tol=TOL, screen_every=K_SCREEN)
+    opts = make_opts(tol=TOL, screen_every=K_SCREEN, precision=HEAD_PRECISION)
     times = []
     for i in range(steps + 1):
         torch.cuda.synchronize()
@@ -412,7 +428,7 @@ def ncu_region(args):
         p = make_problem(WORKLOAD, 0)
         s = Solver(torch.from_numpy(p.A).to(dev), p.l, p.u)
         y = torch.from_numpy(p.y).to(dev)
-        opts = make_opts(tol=TOL, screen_every=K_SCREEN, profile=True)
+        opts = make_opts(tol=TOL, screen_every=K_SCREEN, profile=True, precision=HEAD_PRECISION)
         run = lambda: s.solve(y, opts=opts)
     else:
         c = BATCH
@@ -450,7 +466,7 @@ def run_ours(args):
         if world > 1:
             torch.distributed.barrier()
 
-    def leg(name, screening, steps, warmup, keep=False, oracle_dual=False, precision="fp32x2"):
+    def leg(name, variants, steps, warmup, keep=False, oracle_dual=False):
         p = make_problem(name, rank)
         A = torch.from_numpy(p.A).to(dev)
         y = torch.from_numpy(p.y).to(dev)
@@ -466,11 +482,12 @@ def run_ours(args):
             theta = (y.double() - A.double() @ xs).contiguous()
         del A
         barrier()
-        times, infos, x, s = timed_solves(solver, y, flush, stream, steps, warmup, dual_point=theta,
-                                          screening=screening, precision=precision)
+        res = timed_solves(solver, y, flush, stream, steps, warmup, variants, dual_point=theta)
         barrier()
-        out = {"times_ms": times, "info": infos[-1], "setup_s": setup_s,
-               "launches": sum(i["kernel_launches"] for i in infos)}
+        out = {}
+        for vname, (times, infos) in res.items():
+            out[vname] = {"times_ms": times, "info": infos[-1], "setup_s": setup_s,
+                          "launches": sum(i["kernel_launches"] for i in infos)}
         if keep:
             out["solver"], out["y"], out["p"] = solver, y, p
         else:
@@ -478,12 +495,15 @@ def run_ours(args):
         return out
 
     with ClockSampler(local) as clk:
-        scr = leg(WORKLOAD, True, args.steps, args.warmup, keep=True)
-    uns = leg(WORKLOAD, False, args.steps, args.warmup)
-    var_s = leg(VARIANT, True, max(2, args.steps // 2), 1)
-    var_u = leg(VARIANT, False, max(2, args.steps // 2), 1)
-    var_o = leg(VARIANT, True, max(2, args.steps // 2), 1, oracle_dual=True)
-    mix = leg(WORKLOAD, True, args.steps, args.warmup, precision="mixed")
+        head = leg(WORKLOAD, {"screened": dict(screening=True, precision=HEAD_PRECISION),
+                              "unscreened": dict(screening=False, precision=HEAD_PRECISION),
+                              "fp32x2": dict(screening=True, precision="fp32x2")},
+                   args.steps, args.warmup, keep=True)
+    scr, uns, x2 = head["screened"], head["unscreened"], head["fp32x2"]
+    var = leg(VARIANT, {"screened": dict(screening=True), "unscreened": dict(screening=False),
+                        "oracle_dual": dict(screening=True, dual=True)},
+              max(2, args.steps // 2), 1, oracle_dual=True)
+    var_s, var_u, var_o = var["screened"], var["unscreened"], var["oracle_dual"]
 
     total_ms = sum(scr["times_ms"])
     if world > 1:
@@ -492,13 +512,13 @@ def run_ours(args):
         total_ms = float(t.item())
     value = world * args.steps / (total_ms / 1000.0)
 
-    roof = roofline(scr["solver"], scr["y"], 2000) if rank == 0 else None
+    roof = roofline(head["solver"], head["y"], 2000) if rank == 0 else None
     batched = batched_leg(dev, stream, flush, max(2, min(args.steps, 5))) if (rank == 0 and not args.no_batched) else None
     table2 = table2_leg(dev, stream, flush, max(2, min(args.steps, 3))) if rank == 0 else None
     ragged = ragged_leg(dev, stream) if (rank == 0 and not args.no_batched) else None
-    e2e = e2e_leg(scr["p"], max(2, min(args.steps, 5)), stream) if rank == 0 else None
-    cpu = oracle_sample(scr["p"]) if (rank == 0 and world == 1) else None
-    scr["solver"].close()
+    e2e = e2e_leg(head["p"], max(2, min(args.steps, 5)), stream) if rank == 0 else None
+    cpu = oracle_sample(head["p"]) if (rank == 0 and world == 1) else None
+    head["solver"].close()
 
 
     if rank == 0:
@@ -509,7 +529,8 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "desc": WORKLOAD_DESC, "tol": TOL, "screen_every": K_SCREEN,
-                       "precision": "f32 data, double-float (f32x2) products, f64 gap/screening",
+                       "precision": "f32 data; A^T r in f32; A x and r = y - A x in double-float (f32 pairs); "
+                                    "dual point, gap, radius and test in f64 (mode mixed)",
                        "iteration": "persistent: one cooperative launch per screen_every iterations",
                        "l2": "flushed before every step (256 MiB write, untimed)",
                        "parallelism": f"replicas x{world}"},
@@ -535,12 +556,11 @@ def run_ours(args):
                     (sum(var_o["times_ms"]) / len(var_o["times_ms"])),
                     "iters": var_o["info"]["iters"],
                     "avg_preserved_fraction": var_o["info"]["sum_preserved"] / max(1, var_o["info"]["iters"]) / 10000}},
-            "mixed_precision": {
-                "note": "same workload and certified tol; float32 correlations a_j^T r, double-float "
-                        "forward product A x (the zero dual point's certificate needs only the residual)",
-                "instances_per_s": world * len(mix["times_ms"]) / (sum(mix["times_ms"]) / 1000.0),
-                "ms_per_step": sum(mix["times_ms"]) / len(mix["times_ms"]), "iters": mix["info"]["iters"],
-                "gap": mix["info"]["gap"]},
+            "fp32x2_precision": {
+                "note": "same workload and certified tol, both products in double-float (the library default)",
+                "instances_per_s": world * len(x2["times_ms"]) / (sum(x2["times_ms"]) / 1000.0),
+                "ms_per_step": sum(x2["times_ms"]) / len(x2["times_ms"]), "iters": x2["info"]["iters"],
+                "gap": x2["info"]["gap"]},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "batched_shared_A": batched,
             "table2_bvls": table2, "ragged_uneven": ragged,
             "gpu_launches": int(scr["launches"]), "clocks": clk.summary(),
