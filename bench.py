@@ -208,6 +208,13 @@ def roofline(solver, y_dev, m):
     from paper_2202_07258_gb300 import make_opts
     x, s, info, st = solver.solve(y_dev, opts=make_opts(tol=TOL, screen_every=K_SCREEN, profile=True,
                                                         precision=HEAD_PRECISION))
+    return roofline_from_info(info, m)
+
+
+def roofline_from_info(info, m, traffic_key=None):
+    """Algorithmic bytes of the single-instance kernels from a profile-mode solve's counters;
+    the DRAM traffic from profiles/ncu_traffic.json (record `traffic_key`, else the kernel's
+    name) while its source hash matches."""
     nl = max(1, info["tr_launches"])
     if info["single_pass"] == 2:
         # persistent form: each launch runs K iterations (one read of A_S each) and their
@@ -247,7 +254,7 @@ def roofline(solver, y_dev, m):
     tp = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if os.path.exists(tp):
         t = json.load(open(tp))
-        rec = t.get(name.split()[0])
+        rec = t.get(traffic_key or name.split()[0])
         if rec and rec.get("kernel_hash") == kernel_hash():
             traffic = rec.get("dram_bytes_per_launch")
     other = {k: {"ms_total": v[0], "launches": v[2], "gb_per_launch": v[1] / max(1, v[2]) / 1e9,
@@ -321,6 +328,36 @@ def table2_leg(dev, stream, flush, steps):
                 "avg_preserved_fraction": infos[-1]["sum_preserved"] / max(1, infos[-1]["iters"]) / 2000}
         res["speedup"] = res["screened"]["instances_per_s"] / res["unscreened"]["instances_per_s"]
         out[alg] = res
+    solver.close()
+    return out
+
+
+def hbm_leg(dev, stream, flush, steps, iters=1500):
+    """The L2-busting matvec case: |N(0,1)| NNLS 4000 x 20000 (A = 320 MB > 129 MB of L2),
+    x0 5% |N(0,1)|, noise N(0,1), seed 0.  A fixed count of iterations (the solve is cut at
+    `iters`; screening every 10), screened and unscreened alternating, and the roofline of the
+    persistent pass on it (every read of A_S comes from HBM)."""
+    import torch
+    from paper_2202_07258_gb300 import Solver
+    p = W.nnls_abs_gaussian(4000, 20000, 0.05, 1.0, 0)
+    with torch.cuda.stream(stream):
+        solver = Solver(torch.from_numpy(p.A).to(dev), p.l, p.u, stream=stream.cuda_stream)
+    y = torch.from_numpy(p.y).to(dev)
+    runs = timed_solves(solver, y, flush, stream, steps, 1,
+                        {"screened": dict(screening=True, max_iter=iters),
+                         "unscreened": dict(screening=False, max_iter=iters)})
+    out = {"workload": "nnls_abs_gaussian_4000x20000 (A 320 MB, |N(0,1)| unit columns, x0 5% |N(0,1)|, "
+                       "noise N(0,1); %d iterations per solve)" % iters}
+    for name, (times, infos) in runs.items():
+        inf = infos[-1]
+        out[name] = {"ms_per_solve": sum(times) / len(times), "iters": inf["iters"],
+                     "us_per_iteration": 1000.0 * sum(times) / len(times) / max(1, inf["iters"]),
+                     "gap": inf["gap"], "avg_preserved_fraction": inf["sum_preserved"] / max(1, inf["iters"]) / 20000}
+    out["speedup"] = out["unscreened"]["ms_per_solve"] / out["screened"]["ms_per_solve"]
+    from paper_2202_07258_gb300 import make_opts
+    x, sc, info, st = solver.solve(y, opts=make_opts(tol=TOL, screen_every=K_SCREEN, max_iter=iters, profile=True,
+                                                     screening=False))
+    out["roofline_unscreened"] = roofline_from_info(info, 4000, traffic_key="k_iters@nnls_abs_4000x20000")
     solver.close()
     return out
 
@@ -515,6 +552,7 @@ def run_ours(args):
     roof = roofline(head["solver"], head["y"], 2000) if rank == 0 else None
     batched = batched_leg(dev, stream, flush, max(2, min(args.steps, 5))) if (rank == 0 and not args.no_batched) else None
     table2 = table2_leg(dev, stream, flush, max(2, min(args.steps, 3))) if rank == 0 else None
+    hbm = hbm_leg(dev, stream, flush, 2) if (rank == 0 and not args.no_batched) else None
     ragged = ragged_leg(dev, stream) if (rank == 0 and not args.no_batched) else None
     e2e = e2e_leg(head["p"], max(2, min(args.steps, 5)), stream) if rank == 0 else None
     cpu = oracle_sample(head["p"]) if (rank == 0 and world == 1) else None
@@ -562,7 +600,7 @@ def run_ours(args):
                 "ms_per_step": sum(x2["times_ms"]) / len(x2["times_ms"]), "iters": x2["info"]["iters"],
                 "gap": x2["info"]["gap"]},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "batched_shared_A": batched,
-            "table2_bvls": table2, "ragged_uneven": ragged,
+            "table2_bvls": table2, "ragged_uneven": ragged, "hbm_bound_4000x20000": hbm,
             "gpu_launches": int(scr["launches"]), "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)
