@@ -301,9 +301,14 @@ typedef struct {
   int n_translation;    /* instances screened with the dual translation (t = -1) */
   int n_zero;           /* instances with u_j = +inf and no interior t = -1: theta = 0 */
   int chunks;           /* chunks of iterations the device loop ran */
-  int tiles_max;        /* work-list capacity (sum over instances of ceil(n / 16)) */
-  double setup_ms;      /* copies, column norms, dual modes and 40 power iterations */
+  int tiles_max;        /* work-list capacity (sum over instances of ceil(n / 8)) */
+  double setup_ms;      /* copies, column norms, dual modes, 40 power iterations, autotuner */
   double solve_ms;      /* the solve graph (host wall clock around one graph launch) */
+  int tile_cols;        /* columns per tile of the work list (8, 16 or 32), picked by timing */
+  int screen_every;     /* the screening period used (the autotuner's when opts->screen_every = 0) */
+  int tuned;            /* 1 when this call ran the autotuner (the choice is kept for later calls
+                           on a batch of the same shape) */
+  double tune_ms;       /* autotuner time (part of setup_ms) */
 } bvls_ragged_info;
 
 /*
@@ -314,7 +319,12 @@ typedef struct {
  * (every u_j finite), the translation with t = -1 when it is interior (Proposition 2), else
  * theta = 0.  Products are float32 data with double-float accumulation.
  *   probs         host; B problem descriptors (1 <= m_k <= 1024, n_k >= 1).
- *   opts          host or NULL: tol, screen_every, max_iter, screening, restart are used.
+ *   opts          host or NULL: tol, screen_every, max_iter, screening, restart are used;
+ *                 screen_every = 0 lets the autotuner pick it from {5, 10, 20} by timing 40
+ *                 iterations of each from the start point.  The tile width of the work list
+ *                 is always picked by timing eight iterations with 8, 16 and 32 columns (the
+ *                 iterates do not depend on it).  Choices are kept per batch shape for the
+ *                 life of the process.
  *   stream        a cudaStream_t (0 allowed); the call returns when its outputs are written.
  *   x_out         host; B pointers (any memory) to n_k doubles each.
  *   screened_out  host; B pointers (any memory) to n_k bytes, or NULL.

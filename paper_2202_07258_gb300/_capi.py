@@ -131,6 +131,10 @@ class bvls_ragged_info(ctypes.Structure):
         ("tiles_max", ctypes.c_int),
         ("setup_ms", ctypes.c_double),
         ("solve_ms", ctypes.c_double),
+        ("tile_cols", ctypes.c_int),
+        ("screen_every", ctypes.c_int),
+        ("tuned", ctypes.c_int),
+        ("tune_ms", ctypes.c_double),
     ]
 
     def as_dict(self):

@@ -1,5 +1,8 @@
 // C ABI: handle management, setup and the solve loop (CUDA-graph chunks of iterations).
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -1262,6 +1265,35 @@ extern "C" bvls_status bvls_backward(bvls_handle* h, int B, const double* X, con
 }
 
 // ------------------------------------------------------------------ ragged batch
+// Autotuner choices of the ragged solve, per batch shape (process-wide, thread-safe).
+struct RaggedTuneKey {
+  long long B, cols, rows, elems;
+  int screening, restart, auto_k;
+  bool operator<(const RaggedTuneKey& o) const {
+    return std::tie(B, cols, rows, elems, screening, restart, auto_k) <
+           std::tie(o.B, o.cols, o.rows, o.elems, o.screening, o.restart, o.auto_k);
+  }
+};
+struct RaggedTune {
+  int tw, K;
+};
+std::mutex g_tune_mu;
+std::map<RaggedTuneKey, RaggedTune>& tune_cache() {
+  static std::map<RaggedTuneKey, RaggedTune> c;
+  return c;
+}
+bool ragged_tune_lookup(const RaggedTuneKey& k, RaggedTune* t) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  auto it = tune_cache().find(k);
+  if (it == tune_cache().end()) return false;
+  *t = it->second;
+  return true;
+}
+void ragged_tune_store(const RaggedTuneKey& k, const RaggedTune& t) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  tune_cache()[k] = t;
+}
+
 extern "C" bvls_status bvls_solve_ragged(int B, const bvls_problem* probs, const bvls_opts* opts, void* stream,
                                          double* const* x_out, uint8_t* const* screened_out, double* gaps_out,
                                          int* iters_out, int* status_out, bvls_ragged_info* info) {
@@ -1271,6 +1303,8 @@ extern "C" bvls_status bvls_solve_ragged(int B, const bvls_problem* probs, const
   bvls_opts o;
   bvls_default_opts(&o);
   if (opts) o = *opts;
+  const bool auto_k = o.screen_every == 0;   // the autotuner picks the screening period
+  if (auto_k) o.screen_every = 10;
   TRY(validate_opts(o));
   // ---- layout
   std::vector<RInst> in(B);
@@ -1285,7 +1319,7 @@ extern "C" bvls_status bvls_solve_ragged(int B, const bvls_problem* probs, const
     r.m = q.m;
     r.n = q.n;
     r.lda = (q.m + 3) / 4 * 4;
-    r.tiles_max = (q.n + kRTile - 1) / kRTile;
+    r.tiles_max = (q.n + kRTileMin - 1) / kRTileMin;   // room for the narrowest tiles
     r.a_off = a_tot;
     r.c_off = c_tot;
     r.r_off = r_tot;
@@ -1393,10 +1427,11 @@ extern "C" bvls_status bvls_solve_ragged(int B, const bvls_problem* probs, const
   b.u = d_u;
   b.jinf = d_jinf;
   b.B = B;
+  b.tw = 16;
   b.screening = o.screening;
   b.restart = o.restart;
   b.tol = o.tol;
-  const int K = o.screen_every;
+  int K = o.screen_every;
   b.K = K;
   b.max_iter = (int)std::min<long long>((long long)(o.max_iter + K - 1) / K * K, 0x3fffffff);
   // ---- copies
@@ -1446,7 +1481,7 @@ extern "C" bvls_status bvls_solve_ragged(int B, const bvls_problem* probs, const
     n_zero += r.dual_mode == kZero;
     const double dg = ((r.m + 3) / 4 + 31) / 32 + 7;
     r.Cg = 2.0 * (dg + 2.0) * (dg + 2.0) * kU * kU + 4.0 * kU * kU + 2.0 * kU64;
-    const double df = kRTile + r.tiles_max + 2;
+    const double df = kRTileMax + r.tiles_max + 2;   // any tile width: <= 32 columns, <= tiles_max tiles
     r.Cf = 2.0 * (df + 2.0) * (df + 2.0) * kU * kU + 2.0 * kU * kU;
     r.Csub = 8.0 * kU * kU;
     r.invL = 1.0;
@@ -1467,6 +1502,110 @@ extern "C" bvls_status bvls_solve_ragged(int B, const bvls_problem* probs, const
   RCK(cudaStreamSynchronize(s));
   for (int k = 0; k < B; ++k) in[k].invL = hs[k].pw_lambda > 0.0 ? 1.0 / (1.05 * hs[k].pw_lambda) : 1.0;
   RCK(cudaMemcpyAsync(d_in, in.data(), sizeof(RInst) * B, cudaMemcpyHostToDevice, s));
+  // ---- autotuner
+  const auto t_tune0 = clk::now();
+  b.power = 0;
+  bool tuned_now = false;
+  {
+    RaggedTuneKey key{B, c_tot, r_tot, a_tot, o.screening, o.restart, auto_k ? 1 : 0};
+    RaggedTune t{};
+    if (ragged_tune_lookup(key, &t)) {
+      b.tw = t.tw;
+      if (auto_k) K = t.K;
+    } else {
+      tuned_now = true;
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      RCK(cudaEventCreate(&e0));
+      RCK(cudaEventCreate(&e1));
+      auto timed = [&](auto&& body) -> float {
+        float ms = -1.f;
+        if (cudaEventRecord(e0, s) != cudaSuccess) return ms;
+        if (body() != cudaSuccess) return ms;
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return ms;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms;
+      };
+      // tile width: eight plain iterations from the start point per width (the iterates do
+      // not depend on it, only the tile kernel's speed does)
+      float best = 0.f;
+      for (int cand : {8, 16, 32}) {
+        b.tw = cand;
+        RCK(launch_rinit(b, c_tot, 0, s));
+        RCK(launch_rfwd(b, s));
+        RCK(launch_rtiles(b, s));
+        RCK(launch_rpass(b, max_tiles, 0, 0, s));
+        RCK(launch_rresid(b, 0, s));
+        const float ms = timed([&]() {
+          cudaError_t e = cudaSuccess;
+          for (int it = 1; it <= 8 && e == cudaSuccess; ++it) {
+            e = launch_rpass(b, max_tiles, it & 1, 0, s);
+            if (e == cudaSuccess) e = launch_rresid(b, it & 1, s);
+          }
+          return e;
+        });
+        if (ms < 0.f) {
+          const cudaError_t e = cudaGetLastError();
+          RCK(e != cudaSuccess ? e : cudaErrorUnknown);
+        }
+        if (cand == 8 || ms < best) {
+          best = ms;
+          t.tw = cand;
+        }
+      }
+      b.tw = t.tw;
+      t.K = K;
+      if (auto_k) {
+        // screening period: 40 iterations (gap, test, compaction, folds included) from the
+        // start point per candidate, each as one plain graph; the folds change y', which is
+        // restored afterwards
+        float* y0 = nullptr;
+        RCK(alloc(&y0, (size_t)r_tot));
+        RCK(cudaMemcpyAsync(y0, b.yh, sizeof(float) * r_tot, cudaMemcpyDeviceToDevice, s));
+        for (int cand : {5, 10, 20}) {
+          RCK(cudaMemcpyAsync(b.yh, y0, sizeof(float) * r_tot, cudaMemcpyDeviceToDevice, s));
+          RCK(cudaMemsetAsync(b.yl, 0, sizeof(float) * r_tot, s));
+          RCK(launch_rinit(b, c_tot, 0, s));
+          RCK(launch_rfwd(b, s));
+          RCK(launch_rtiles(b, s));
+          cudaGraph_t g = nullptr;
+          cudaGraphExec_t px = nullptr;
+          RCK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+          cudaError_t e1 = cudaSuccess;
+          for (int j = 0; j < 40 && e1 == cudaSuccess; ++j) {
+            const bool gap_iter = ((j + 1) % cand) == 0;
+            e1 = launch_rpass(b, max_tiles, j & 1, gap_iter ? 1 : 0, s);
+            if (e1 == cudaSuccess) e1 = launch_rresid(b, j & 1, s);
+            if (e1 == cudaSuccess && gap_iter) e1 = launch_rgap(b, j & 1, s);
+            if (e1 == cudaSuccess && gap_iter) e1 = launch_rtiles(b, s);
+          }
+          const cudaError_t e2 = cudaStreamEndCapture(s, &g);
+          RCK(e1);
+          RCK(e2);
+          const cudaError_t e3 = cudaGraphInstantiate(&px, g, 0);
+          cudaGraphDestroy(g);
+          RCK(e3);
+          const float ms = timed([&]() { return cudaGraphLaunch(px, s); });
+          cudaGraphExecDestroy(px);
+          if (ms < 0.f) {
+            const cudaError_t e = cudaGetLastError();
+            RCK(e != cudaSuccess ? e : cudaErrorUnknown);
+          }
+          if (cand == 5 || ms < best) {
+            best = ms;
+            t.K = cand;
+          }
+        }
+        RCK(cudaMemcpyAsync(b.yh, y0, sizeof(float) * r_tot, cudaMemcpyDeviceToDevice, s));
+        RCK(cudaMemsetAsync(b.yl, 0, sizeof(float) * r_tot, s));
+        K = t.K;
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      ragged_tune_store(key, t);
+    }
+    b.K = K;
+    b.max_iter = (int)std::min<long long>((long long)(o.max_iter + K - 1) / K * K, 0x3fffffff);
+  }
   const auto t_setup = clk::now();
   // ---- solve: one graph, a while node around one chunk
   b.power = 0;
@@ -1546,6 +1685,10 @@ extern "C" bvls_status bvls_solve_ragged(int B, const bvls_problem* probs, const
     info->n_zero = n_zero;
     info->chunks = hchunks;
     info->tiles_max = max_tiles;
+    info->tile_cols = b.tw;
+    info->screen_every = K;
+    info->tuned = tuned_now ? 1 : 0;
+    info->tune_ms = std::chrono::duration<double, std::milli>(t_setup - t_tune0).count();
     info->setup_ms = std::chrono::duration<double, std::milli>(t_setup - t_start).count();
     info->solve_ms = std::chrono::duration<double, std::milli>(t_solve - t_setup).count();
   }

@@ -159,7 +159,7 @@ cudaError_t launch_rinit(const RBuf& b, long long total_cols, int power, cudaStr
   return cudaGetLastError();
 }
 
-// Work list over the active instances: ceil(n_active / kRTile) tiles each.  One block.
+// Work list over the active instances: ceil(n_active / tw) tiles each.  One block.
 __global__ void __launch_bounds__(kRThreads) k_rtiles(RBuf b) {
   __shared__ int sh[kRThreads / 32];
   __shared__ int s_base, s_ibase;
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(kRThreads) k_rtiles(RBuf b) {
   for (int k0 = 0; k0 < b.B; k0 += kRThreads) {
     const int k = k0 + threadIdx.x;
     const bool live = k < b.B && !b.st[k].done;
-    const int nt = live ? (b.st[k].n_active + kRTile - 1) / kRTile : 0;
+    const int nt = live ? (b.st[k].n_active + b.tw - 1) / b.tw : 0;
     int tot = 0;
     // tiles: exclusive scan of nt (counts up to kRThreads * tiles_max fit an int)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -256,9 +256,9 @@ cudaError_t launch_rfwd(const RBuf& b, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------- one iteration
-// Tile = (instance k, tile t): preserved columns q in [t kRTile, min((t+1) kRTile, n_active)).
-size_t rpass_smem_bytes() {
-  return (size_t)kRMaxRows * 2 * sizeof(float) + (size_t)kRTile * kRMaxRows * sizeof(float);
+// Tile = (instance k, tile t): preserved columns q in [t tw, min((t+1) tw, n_active)).
+size_t rpass_smem_bytes(int tw) {
+  return (size_t)kRMaxRows * 2 * sizeof(float) + (size_t)tw * kRMaxRows * sizeof(float);
 }
 
 __global__ void __launch_bounds__(kRThreads) k_rpass(RBuf b, int slot, int gap_iter) {
@@ -271,14 +271,14 @@ __global__ void __launch_bounds__(kRThreads) k_rpass(RBuf b, int slot, int gap_i
   float* srh = rsm;                      // r (hi), m4 floats
   float* srl = rsm + kRMaxRows;          // r (lo)
   float* sa = rsm + 2 * kRMaxRows;       // tile columns: [c][m4]
-  __shared__ int s_col[kRTile];
-  __shared__ float2 s_xn[kRTile];
-  __shared__ double s_dot[kRTile], s_eps[kRTile], s_v2[kRTile];
+  __shared__ int s_col[kRTileMax];
+  __shared__ float2 s_xn[kRTileMax];
+  __shared__ double s_dot[kRTileMax], s_eps[kRTileMax], s_v2[kRTileMax];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m4 = (in.m + 3) & ~3;
-  const int q0 = tr.tile * kRTile;
-  const int nc = min(kRTile, st.n_active - q0);
-  if (tid < kRTile) {
+  const int q0 = tr.tile * b.tw;
+  const int nc = min(b.tw, st.n_active - q0);
+  if (tid < kRTileMax) {
     s_col[tid] = tid < nc ? b.idx[in.c_off + q0 + tid] : -1;
     s_dot[tid] = 0.0;
     s_eps[tid] = 0.0;
@@ -386,11 +386,13 @@ __global__ void __launch_bounds__(kRThreads) k_rpass(RBuf b, int slot, int gap_i
 }
 
 cudaError_t ragged_configure() {
-  return cudaFuncSetAttribute(k_rpass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rpass_smem_bytes());
+  return cudaFuncSetAttribute(k_rpass, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)rpass_smem_bytes(kRTileMax));
 }
 
 cudaError_t launch_rpass(const RBuf& b, int max_tiles, int slot, int gap_iter, cudaStream_t s) {
-  k_rpass<<<max_tiles, kRThreads, rpass_smem_bytes(), s>>>(b, slot, gap_iter);
+  if (b.tw < kRTileMin || b.tw > kRTileMax) return cudaErrorInvalidValue;
+  k_rpass<<<max_tiles, kRThreads, rpass_smem_bytes(b.tw), s>>>(b, slot, gap_iter);
   return cudaGetLastError();
 }
 
@@ -402,7 +404,7 @@ __global__ void __launch_bounds__(kRThreads) k_rresid(RBuf b, int slot) {
   RState& st = b.st[k];
   if (st.done) return;
   const RInst in = b.inst[k];
-  const int nt = (st.n_active + kRTile - 1) / kRTile;
+  const int nt = (st.n_active + b.tw - 1) / b.tw;
   const float2* part = b.part + in.p_off;
   double p2 = 0.0;
   for (int i = threadIdx.x; i < in.m; i += kRThreads) {

@@ -4,7 +4,7 @@
 // Every instance runs the single-instance iteration (FISTA + restart with the screening of
 // Algorithm 1 / 2 every K iterations, dual scaling or translation with t = -1), in lockstep
 // with the others.  One iteration is two launches over all active instances:
-//   k_rpass   a work list of tiles (instance, up to kRTile preserved columns): the tile's
+//   k_rpass   a work list of tiles (instance, up to tw preserved columns): the tile's
 //             columns are staged in shared memory, then a_j^T r_k in double-float, the FISTA
 //             step, and the tile's partial of A x_{k+1} (double-float, per row);
 //   k_rresid  per instance: r_{k+1} = y' - sum of its tiles' partials, P_{k+1}, and the
@@ -19,7 +19,8 @@
 
 namespace bvls {
 
-constexpr int kRTile = 16;          // columns per tile
+constexpr int kRTileMin = 8;        // columns per tile: tw in {8, 16, 32}, picked by the autotuner
+constexpr int kRTileMax = 32;
 constexpr int kRThreads = 256;
 constexpr int kRMaxRows = 1024;     // m_k limit (r_k in shared memory)
 
@@ -29,7 +30,7 @@ struct RInst {                      // per instance, fixed at setup
   long long r_off;                  // offset of the instance's rows in per-row arrays
   long long p_off;                  // offset of the instance's tile partials (tiles_max x m)
   long long t_off;                  // offset of the instance's per-tile scalars
-  int m, n, lda, tiles_max;         // tiles_max = ceil(n / kRTile)
+  int m, n, lda, tiles_max;         // tiles_max = ceil(n / kRTileMin)
   int dual_mode;                    // kScaling, kTranslation (t = -1) or kZero
   int pad;
   double invL;
@@ -91,6 +92,7 @@ struct RBuf {
   int power;                        // 1: the pass runs power iterations (x <- A^T A x / scale)
   unsigned int* err;                // bit 0: NaN or Inf in A or y
   int* chunks;                      // chunks run by the device-side loop of the solve graph
+  int tw;                           // columns per tile of the work list (kRTileMin..kRTileMax)
 };
 
 cudaError_t launch_rnorms(const RBuf& b, long long total_cols, cudaStream_t s);
@@ -101,8 +103,8 @@ cudaError_t launch_rpass(const RBuf& b, int max_tiles, int slot, int gap_iter, c
 cudaError_t launch_rresid(const RBuf& b, int slot, cudaStream_t s);
 cudaError_t launch_rgap(const RBuf& b, int slot, cudaStream_t s);
 cudaError_t launch_rexport(const RBuf& b, cudaStream_t s);
-size_t rpass_smem_bytes();
-cudaError_t ragged_configure();  // shared-memory attribute of the tile kernel (before any launch)
+size_t rpass_smem_bytes(int tw);
+cudaError_t ragged_configure();  // shared-memory attribute of the tile kernel (before any launch; widest tile)
 // Last node of a chunk in the ragged solve graph's while loop: ends the loop once no instance
 // is active or max_chunks chunks have run.
 cudaError_t launch_rloop_ctl(const RBuf& b, cudaGraphConditionalHandle h, int max_chunks, cudaStream_t s);

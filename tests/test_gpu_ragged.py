@@ -102,3 +102,25 @@ def test_ragged_nonfinite_and_max_iter(P):
     with pytest.raises(P.BVLSError) as e:
         run(P, [probs[1], bad], tol=1e-6)
     assert e.value.status == P.BVLS_ENONFINITE
+
+
+def test_autotuner_picks_tile_and_period_and_keeps_them(P):
+    """screen_every = 0: the autotuner times the tile widths (8, 16, 32 columns) and the
+    screening periods (5, 10, 20) and keeps its choice for batches of the same shape; the
+    tuned solve reaches the same certified results as a fixed-period solve."""
+    probs = W.mixed_uneven(12, 4, m_lo=40, m_hi=200, abs_matrix=True, noise=1.0)
+    a = run(P, probs, tol=1e-7, screen_every=0)
+    info = a[5]
+    assert a[6] == P.BVLS_OK and info["n_converged"] == 12
+    assert info["tile_cols"] in (8, 16, 32) and info["screen_every"] in (5, 10, 20)
+    assert info["tuned"] == 1 and info["tune_ms"] > 0
+    again = run(P, probs, tol=1e-7, screen_every=0)
+    assert again[5]["tuned"] == 0 and again[5]["tile_cols"] == info["tile_cols"]
+    assert again[5]["screen_every"] == info["screen_every"]
+    fixed = run(P, probs, tol=1e-7, screen_every=10)
+    assert fixed[5]["screen_every"] == 10 and fixed[5]["tile_cols"] in (8, 16, 32)
+    for k, p in enumerate(probs):
+        check(p, a[0][k], a[1][k], a[2][k], a[4][k], 1e-7)
+        A, y = p.A.astype(np.float64), p.y.astype(np.float64)
+        Pa, Pf = O.primal_objective(A, y, a[0][k]), O.primal_objective(A, y, fixed[0][k])
+        assert abs(Pa - Pf) <= a[2][k] + fixed[2][k] + 1e-12
