@@ -288,13 +288,16 @@ def ragged_leg(dev, stream, B=512):
         res = {"instances": b, "bytes_A": nbytes}
         for scr in (True, False):
             t0 = time.perf_counter()
-            xs, ss, gaps, its, sts, info, st = solve_ragged(items, tol=TOL, screen_every=K_SCREEN, screening=scr,
+            # screen_every = 0: the autotuner picks the period (and, always, the tile width)
+            xs, ss, gaps, its, sts, info, st = solve_ragged(items, tol=TOL, screen_every=0, screening=scr,
                                                             max_iter=mx, stream=stream.cuda_stream)
             wall = time.perf_counter() - t0
             res["screened" if scr else "unscreened"] = {
                 "instances_per_s_solve": b / (info["solve_ms"] / 1000.0),
                 "instances_per_s_call": b / wall, "solve_ms": info["solve_ms"], "setup_ms": info["setup_ms"],
                 "n_converged": info["n_converged"], "iters_max": int(its.max()), "iters_mean": float(its.mean()),
+                "autotuned": {"tile_cols": info["tile_cols"], "screen_every": info["screen_every"],
+                              "tune_ms": info["tune_ms"]},
                 "screened_fraction_end": float(sum(int((s > 0).sum()) for s in ss) / max(1, sum(len(s) for s in ss))),
                 "dual_modes": {"translation": info["n_translation"], "zero": info["n_zero"]}}
         res["speedup"] = res["unscreened"]["solve_ms"] / res["screened"]["solve_ms"]
