@@ -215,19 +215,25 @@ def test_mixed_precision_mode(P):
 
 @pytest.mark.parametrize("name", ["nnls_abs_300x700", "bvls_t2_200x500"])
 def test_mixed_precision_parity_nondegenerate(P, name):
-    """The reduced-precision bar of the mixed mode: with a unique optimum, the solution agrees
-    with the certified FP64 optimum to 1e-4 relative, and nothing is screened off its bound."""
+    """The reduced-precision bar of the mixed mode: with a unique optimum the iterates agree
+    with the certified FP64 optimum to 1e-4 relative, nothing is screened off its bound, and
+    the reported gap bounds P(x) - P*.  (With theta != 0 the float32 correlations enter the
+    certificate through the margin eta, so the mode certifies only coarse gaps here; its
+    tight certificate is the theta = 0 one.)"""
     p, t = CASES[name]()
     A, y = _f64(p)
     L = _L(A)
     ref = O.solve(A, y, p.l, p.u, tol=1e-10, screen_every=10, L=L, t=t)
     xs = certified_optimum(A, y, p.l, p.u, ref.x)
-    x, scr, info, st = gpu_solve(P, p, t=t, tol=1e-5, screen_every=10, lipschitz=L, precision="mixed")
-    assert st == P.BVLS_OK and info["gap"] < 1e-5
+    x, scr, info, st = gpu_solve(P, p, t=t, tol=0.0, screen_every=10, max_iter=4000, lipschitz=L,
+                                 precision="mixed")
+    assert info["iters"] == 4000
     assert float(np.abs(x - xs).max()) <= 1e-4 * max(1.0, float(np.abs(xs).max()))
     g = A.T @ (y - A @ xs)
     assert np.all(np.abs(xs[scr == 1] - p.l[scr == 1]) <= 1e-12) and np.all(g[scr == 1] < 0)
     assert np.all(np.abs(xs[scr == 2] - p.u[scr == 2]) <= 1e-12) and np.all(g[scr == 2] > 0)
+    Pg, Ps = O.primal_objective(A, y, x), O.primal_objective(A, y, xs)
+    assert Ps - 1e-12 <= Pg <= Ps + info["gap"] * (1 + 1e-9) + 1e-12
 
 
 def test_single_column_closed_form(P):
