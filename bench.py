@@ -350,7 +350,7 @@ def hbm_leg(dev, stream, flush, steps, iters=1500):
                         {"screened": dict(screening=True, max_iter=iters),
                          "unscreened": dict(screening=False, max_iter=iters)})
     out = {"workload": "nnls_abs_gaussian_4000x20000 (A 320 MB, |N(0,1)| unit columns, x0 5% |N(0,1)|, "
-                       "noise N(0,1); %d iterations per solve)" % iters}
+                       f"noise N(0,1); {iters} iterations per solve)"}
     for name, (times, infos) in runs.items():
         inf = infos[-1]
         out[name] = {"ms_per_solve": sum(times) / len(times), "iters": inf["iters"],
