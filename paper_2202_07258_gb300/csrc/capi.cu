@@ -44,6 +44,8 @@ bvls_status set_err(bvls_status s, const char* fmt, ...) {
 constexpr double kU = 5.9604644775390625e-08;   // 2^-24, unit roundoff of float32
 constexpr double kU64 = 1.1102230246251565e-16; // 2^-53
 
+constexpr int kGraphCache = 4;   // solve graphs kept per handle
+
 struct GraphKey {
   int K, screening, precision, restart, max_iter, single_pass, algorithm;
   double tol, invL, eps_star, eta_star;
@@ -76,13 +78,17 @@ struct bvls_handle {
   double *theta_dev = nullptr, *wstar_dev = nullptr;  // fixed dual point and A^T theta
   int fwd_tiles = 0, fwd_chunks = 0, tr_blocks = 0, red_blocks = 0;
   int pass_stages = 0, pass_qw = 0, pass_cps = 1;  // fused single-pass iteration when pass_stages > 0
-  bool pass_coop = false;
-  MomEntry* mom = nullptr;                          // momentum table of the persistent pass                           // its persistent (cooperative) launch fits
+  bool pass_coop = false;                          // its persistent (cooperative) launch fits
+  MomEntry* mom = nullptr;                          // momentum table of the persistent pass
   double Cg[3] = {0, 0, 0}, Cf[3] = {0, 0, 0}, Csub = 0.0;
-  bool have_graph = false;
-  GraphKey key{};
-  cudaGraphExec_t exec = nullptr;
-  int chunk_len = 0;
+  // instantiated solve graphs, one per option set (at most kGraphCache, oldest evicted), so
+  // callers that alternate options do not rebuild a graph on every call
+  struct CachedGraph {
+    GraphKey key;
+    int chunk;
+    cudaGraphExec_t exec;
+  };
+  std::vector<CachedGraph> graphs;
   bool own_stream = false;
   std::vector<cudaEvent_t> prof;
   std::vector<void*> allocs;
@@ -119,7 +125,7 @@ bvls_status dalloc(bvls_handle* h, T** p, size_t count) {
 
 void free_handle(bvls_handle* h) {
   if (!h) return;
-  if (h->exec) cudaGraphExecDestroy(h->exec);
+  for (auto& c : h->graphs) cudaGraphExecDestroy(c.exec);
   if (h->b_exec) cudaGraphExecDestroy(h->b_exec);
   for (void* p : h->b_allocs) cudaFree(p);
   for (auto e : h->prof) cudaEventDestroy(e);
@@ -769,12 +775,14 @@ bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const b
   } else {
     GraphKey key{K, o.screening, o.precision, o.restart, max_iter, o.single_pass, o.algorithm, o.tol, p.invL,
                  p.eps_star, p.eta_star, p.wstar != nullptr};
-    if (!h->have_graph || !(h->key == key) || h->chunk_len != chunk) {
-      if (h->exec) {
-        cudaGraphExecDestroy(h->exec);
-        h->exec = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    for (auto& c : h->graphs)
+      if (c.key == key && c.chunk == chunk) exec = c.exec;
+    if (!exec) {
+      if ((int)h->graphs.size() >= kGraphCache) {
+        cudaGraphExecDestroy(h->graphs.front().exec);
+        h->graphs.erase(h->graphs.begin());
       }
-      h->have_graph = false;
       // One graph for the whole solve: a while node whose body is one chunk of iterations
       // followed by the loop-control kernel, which ends the loop on the device once the stop
       // flag is set (no host polling, no chunk launched after the stop).
@@ -797,14 +805,12 @@ bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const b
         cudaError_t e2 = cudaStreamEndCapture(h->s, &body);
         e = e1 != cudaSuccess ? e1 : e2;
       }
-      if (e == cudaSuccess) e = cudaGraphInstantiate(&h->exec, g, 0);
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
       cudaGraphDestroy(g);
       CK(e);
-      h->have_graph = true;
-      h->key = key;
-      h->chunk_len = chunk;
+      h->graphs.push_back({key, chunk, exec});
     }
-    CK(cudaGraphLaunch(h->exec, h->s));
+    CK(cudaGraphLaunch(exec, h->s));
     chunks_run = -1;  // counted on the device
   }
   CK(cudaStreamSynchronize(h->s));
