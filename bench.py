@@ -470,6 +470,12 @@ def ncu_region(args):
         y = torch.from_numpy(p.y).to(dev)
         opts = make_opts(tol=TOL, screen_every=K_SCREEN, profile=True, precision=HEAD_PRECISION)
         run = lambda: s.solve(y, opts=opts)
+    elif args.ncu_region == "hbm":
+        p = W.nnls_abs_gaussian(4000, 20000, 0.05, 1.0, 0)
+        s = Solver(torch.from_numpy(p.A).to(dev), p.l, p.u)
+        y = torch.from_numpy(p.y).to(dev)
+        opts = make_opts(tol=0.0, screen_every=K_SCREEN, max_iter=20, screening=False, profile=True)
+        run = lambda: s.solve(y, opts=opts)
     else:
         c = BATCH
         p = W.bvls_dirichlet_shared(c["m"], c["n"], c["B"], c["k_support"], c["noise"], c["seed"])
@@ -622,7 +628,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-batched", action="store_true", help="skip the shared-A batched leg")
-    ap.add_argument("--ncu-region", choices=["single", "batched"], default=None,
+    ap.add_argument("--ncu-region", choices=["single", "batched", "hbm"], default=None,
                     help="profiling aid: run one warm solve of that leg between cudaProfilerStart/Stop "
                          "(for ncu --profile-from-start off) and exit without a bench line")
     args = ap.parse_args()

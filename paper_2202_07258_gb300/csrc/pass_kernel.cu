@@ -109,7 +109,8 @@ __device__ __forceinline__ void pmerge(float& s, float& c, float s2, float c2) {
   else s += s2;
 }
 
-// a_j^T r for the two columns of a work unit,
+// a_j^T r for the two columns of a work unit (colB == colA for a lone last column: measured
+// faster than a one-column loop),
 // r staged in shared memory as (hi, lo) float4 rows; double-float (DP == kX2) or float32
 // accumulation.  Every lane returns both sums.
 template <int DP>
@@ -153,51 +154,6 @@ __device__ __forceinline__ void dot_pair(const float4* colA, const float4* colB,
   }
   ga = df2_norm(sa[0], DP == kX2 ? ca[0] : 0.0f);
   gb = df2_norm(sb[0], DP == kX2 ? cb[0] : 0.0f);
-}
-
-// a_j^T r for one column (a unit of a stage with an odd column count): two accumulator sets
-// over alternate row chunks, so the single column keeps the pair's number of chains.
-template <int DP>
-__device__ __forceinline__ float2 dot_single(const float4* colA, const float4* srh, const float4* srl, int m4q,
-                                             int lane) {
-  const ulonglong2* A2 = reinterpret_cast<const ulonglong2*>(colA);
-  const ulonglong2* H2 = reinterpret_cast<const ulonglong2*>(srh);
-  const ulonglong2* L2 = reinterpret_cast<const ulonglong2*>(srl);
-  f32x2 sa2[2] = {0ull, 0ull}, ca2[2] = {0ull, 0ull}, sb2[2] = {0ull, 0ull}, cb2[2] = {0ull, 0ull};
-  int i = lane;
-  for (; i + 32 < m4q; i += 64) {
-    const ulonglong2 h = H2[i], h2 = H2[i + 32];
-    const ulonglong2 l = DP == kX2 ? L2[i] : make_ulonglong2(0ull, 0ull);
-    const ulonglong2 l2 = DP == kX2 ? L2[i + 32] : make_ulonglong2(0ull, 0ull);
-    pacc4x2<DP>(sa2, ca2, A2[i], h.x, h.y, l.x, l.y);
-    pacc4x2<DP>(sb2, cb2, A2[i + 32], h2.x, h2.y, l2.x, l2.y);
-  }
-  if (i < m4q) {
-    const ulonglong2 h = H2[i];
-    const ulonglong2 l = DP == kX2 ? L2[i] : make_ulonglong2(0ull, 0ull);
-    pacc4x2<DP>(sa2, ca2, A2[i], h.x, h.y, l.x, l.y);
-  }
-  float sa[4], ca[4], sb[4], cb[4];
-  x2_unpack(sa2[0], sa[0], sa[1]);
-  x2_unpack(sa2[1], sa[2], sa[3]);
-  x2_unpack(ca2[0], ca[0], ca[1]);
-  x2_unpack(ca2[1], ca[2], ca[3]);
-  x2_unpack(sb2[0], sb[0], sb[1]);
-  x2_unpack(sb2[1], sb[2], sb[3]);
-  x2_unpack(cb2[0], cb[0], cb[1]);
-  x2_unpack(cb2[1], cb[2], cb[3]);
-#pragma unroll
-  for (int q = 0; q < 4; ++q) pmerge<DP>(sa[q], ca[q], sb[q], cb[q]);
-  pmerge<DP>(sa[0], ca[0], sa[1], ca[1]);
-  pmerge<DP>(sa[2], ca[2], sa[3], ca[3]);
-  pmerge<DP>(sa[0], ca[0], sa[2], ca[2]);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float os = __shfl_xor_sync(0xffffffffu, sa[0], o);
-    const float oc = __shfl_xor_sync(0xffffffffu, ca[0], o);
-    pmerge<DP>(sa[0], ca[0], os, oc);
-  }
-  return df2_norm(sa[0], DP == kX2 ? ca[0] : 0.0f);
 }
 
 // q_slice += sum over one stage's columns of a_j x_j on the lane's rows (QT float4 chunks,
@@ -452,12 +408,7 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
       const float4* colA = reinterpret_cast<const float4*>(sbase);
       const float4* colB = reinterpret_cast<const float4*>(sbase + (ncol > 1 ? p.lda : 0));
       float2 ga, gb;
-      if (ncol == 2) {
-        dot_pair<DP>(colA, colB, srh, srl, m4q, lane, ga, gb);
-      } else {
-        ga = dot_single<DP>(colA, srh, srl, m4q, lane);
-        gb = ga;
-      }
+      dot_pair<DP>(colA, colB, srh, srl, m4q, lane, ga, gb);
       __syncwarp();
       if (lane < ncol) {
         const int c = c0 + lane;
@@ -895,12 +846,7 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
         const float4* colA = reinterpret_cast<const float4*>(sbase);
         const float4* colB = reinterpret_cast<const float4*>(sbase + (ncol > 1 ? p.lda : 0));
         float2 ga, gb2;
-        if (ncol == 2) {
-          dot_pair<DP>(colA, colB, srh, srl, m4q, lane, ga, gb2);
-        } else {
-          ga = dot_single<DP>(colA, srh, srl, m4q, lane);
-          gb2 = ga;
-        }
+        dot_pair<DP>(colA, colB, srh, srl, m4q, lane, ga, gb2);
         __syncwarp();
         if (lane < ncol) {
           const int c = c0 + lane;
@@ -1167,7 +1113,10 @@ int pass_configure(int lda, int m4, int idx_cap, int smem_optin, int* qwarps, in
   const int qt = pass_qt(m4);
   if (qt == 0) return 0;
   const int col_bytes = lda * 4;
+  // an even column count splits a stage into column pairs for the dot warps (measured on
+  // 4000-row columns: 2 columns per stage 106 us, 3 columns 130-171 us per iteration)
   for (int cps = std::max(1, std::min(8, 65536 / col_bytes)); cps >= 1; --cps) {
+    if (cps > 1 && cps % 2 != 0) continue;
     int ns = kPassMaxStages;
     // room for the kernels' static shared memory (the persistent form's is about 5 KB)
     while (ns >= 3 && pass_smem_bytes(lda, m4, ns, cps, idx_cap) + 8192 > (size_t)smem_optin) --ns;
