@@ -320,7 +320,7 @@ typedef struct {
  * theta = 0.  Products are float32 data with double-float accumulation.
  *   probs         host; B problem descriptors (1 <= m_k <= 1024, n_k >= 1).
  *   opts          host or NULL: tol, screen_every, max_iter, screening, restart are used;
- *                 screen_every = 0 lets the autotuner pick it from {5, 10, 20} by timing 40
+ *                 screen_every = 0 lets the autotuner pick it from {5, 10, 20} by timing 20
  *                 iterations of each from the start point.  The tile width of the work list
  *                 is always picked by timing eight iterations with 8, 16 and 32 columns (the
  *                 iterates do not depend on it).  Choices are kept per batch shape for the

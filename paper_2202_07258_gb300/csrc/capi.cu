@@ -1561,7 +1561,7 @@ extern "C" bvls_status bvls_solve_ragged(int B, const bvls_problem* probs, const
       b.tw = t.tw;
       t.K = K;
       if (auto_k) {
-        // screening period: 40 iterations (gap, test, compaction, folds included) from the
+        // screening period: 20 iterations (gap, test, compaction, folds included) from the
         // start point per candidate, each as one plain graph; the folds change y', which is
         // restored afterwards
         float* y0 = nullptr;
@@ -1577,7 +1577,7 @@ extern "C" bvls_status bvls_solve_ragged(int B, const bvls_problem* probs, const
           cudaGraphExec_t px = nullptr;
           RCK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
           cudaError_t e1 = cudaSuccess;
-          for (int j = 0; j < 40 && e1 == cudaSuccess; ++j) {
+          for (int j = 0; j < 20 && e1 == cudaSuccess; ++j) {
             const bool gap_iter = ((j + 1) % cand) == 0;
             e1 = launch_rpass(b, max_tiles, j & 1, gap_iter ? 1 : 0, s);
             if (e1 == cudaSuccess) e1 = launch_rresid(b, j & 1, s);
