@@ -415,7 +415,6 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
   __shared__ float s_beta[kBEvalInst];
   __shared__ int s_lj[kBEvalInst][kBEvalList];
   __shared__ float2 s_lx[kBEvalInst][kBEvalList];
-  __shared__ int s_cnt[kBEvalInst];
   __shared__ double s_red[kBEvalThreads / 32][kBEvalInst][5];
   __shared__ int s_ref[kBEvalInst];
   __shared__ float s_qf[kBEvalInst][4];   // eps, eta, eta of refined correlations (rounded up)
@@ -729,7 +728,6 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
     int ref = 0;
     if (inst >= 0) {
       const double P = s_q[tid][0];
-      const double eps = s_q[tid][3];
       const double rnorm = sqrt(2.0 * P) * (1.0 + 1e-6);
       const double E_r = p.Cf * x1 + p.Csub * (rnorm + sqrt(s_q[tid][1]) + x1);
       // the part of the bound that does not depend on the correlations' rounding
