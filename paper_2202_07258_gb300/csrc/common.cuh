@@ -245,6 +245,28 @@ __device__ inline bool grid_arrive_wait(unsigned* gb, unsigned nblocks, unsigned
   return true;
 }
 
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid barrier on a monotonic arrival count: each CTA adds 1 (release) once its threads have
+// synchronised, then waits (bounded) until the count reaches `target` (the number of CTAs
+// times the barriers passed so far).  No last arrival hands anything on, so a barrier costs
+// one reduction and the polls.
+__device__ inline bool grid_count_sync(unsigned long long* cnt, unsigned long long target) {
+  __threadfence();
+  asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(cnt) : "memory");
+  if (ld_acquire_u64(cnt) >= target) return true;
+  const long long t0 = clock64();
+  while (ld_acquire_u64(cnt) < target) {
+    if (clock64() - t0 > kGridWaitCycles) return false;
+  }
+  __threadfence();
+  return true;
+}
+
 // All lanes of a warp agree on the outcome of a bounded wait.
 __device__ __forceinline__ bool warp_all(bool ok) { return __all_sync(0xffffffffu, ok) != 0; }
 
@@ -294,7 +316,7 @@ struct Buffers {
   unsigned int* tile_cnt;
   double* blk;            // per-block partials of the epilogue kernels (4 doubles each)
   float2* qpart;          // fused pass: per-CTA double-float partials of A_S x_S (grid x m4)
-  unsigned int* gbar;     // persistent pass: grid-barrier flags, one per CTA (kMaxGridFlags)
+  unsigned int* gbar;     // persistent pass: grid-barrier words (the first two hold its 64-bit arrival count)
   double* xout;           // float64 copy of the returned iterate (n)
   DevState* st;
   const float* y_in;      // device copy of y

@@ -738,8 +738,11 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
   const int ngroups = (nq + cps - 1) / cps;
   const int nslices = (p.m4 + 31) / 32;
   const int nparts = gridDim.x;
-  unsigned gen = 0;
-  if (threadIdx.x == 32) gen = ld_acquire_u32(&b.gbar[1]);   // before this CTA's first arrival
+  // grid barriers: a monotonic arrival count, zeroed at the start of the solve; every
+  // iteration before this launch passed two barriers, so barrier number nb of the solve
+  // completes when the count reaches gridDim.x * (nb + 1)
+  unsigned long long* gcount = reinterpret_cast<unsigned long long*>(b.gbar);
+  unsigned long long nbar = 2ull * (unsigned long long)k0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < nstages; ++s) {
@@ -964,8 +967,7 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
       *reinterpret_cast<float2*>(&b.blk[4 * blockIdx.x + 0]) = d;   // restart term (double-float)
       b.blk[4 * blockIdx.x + 1] = e;                                 // translation step candidate
       if (s_err) atomicOr(&st->error, 1);
-      bool ok = grid_arrive_wait(b.gbar, gridDim.x, gen);
-      ++gen;
+      bool ok = grid_count_sync(gcount, (unsigned long long)gridDim.x * ++nbar);
       if (ok && *(volatile int*)&st->error) ok = false;
       s_ok = ok ? 1 : 0;
       if (!ok) atomicOr(&st->error, 1);
@@ -977,6 +979,14 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
     // warp meanwhile reduces the restart terms and prepares the next step's scalars
     bool scalars_done = false;
     auto scalars = [&]() {
+      // the two possible next momentum entries (no restart / restart), loaded before the
+      // reduction so their latency overlaps it
+      const int ti_keep = s_ti + 1;
+      MomEntry e_keep{}, e_rst{};
+      if (lane == 0) {
+        if (ti_keep < kMomTable) e_keep = p.mom[ti_keep];
+        e_rst = p.mom[0];
+      }
       // restart test: sign of sum_j g_v,j (x_{k+1,j} - x_{k,j}) over all CTAs, double-float
       float2 d = make_float2(0.f, 0.f);
       double e = 0.0;
@@ -1004,7 +1014,14 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
         const double tnext = restart ? 1.0 : tn;
         s_ti = ti;
         s_tk = tnext;
-        momentum(p.mom, ti, tnext, &s_tn, s_beta2);
+        if (restart || ti_keep < kMomTable) {
+          const MomEntry& me = restart ? e_rst : e_keep;
+          s_tn = me.tn;
+          s_beta2[0] = me.beta2;
+          s_beta2[1] = me.onepb2;
+        } else {
+          momentum(p.mom, ti, tnext, &s_tn, s_beta2);   // past the table's end
+        }
         if (blockIdx.x == 0) {
           st->t = tnext;
           st->ti = ti;
@@ -1091,8 +1108,7 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
     // ---- grid barrier 2: r_{k+1} and the P partials are written
     consumer_sync<NCONS>();
     if (ct == 0) {
-      bool ok = grid_arrive_wait(b.gbar, gridDim.x, gen);
-      ++gen;
+      bool ok = grid_count_sync(gcount, (unsigned long long)gridDim.x * ++nbar);
       if (ok && *(volatile int*)&st->error) ok = false;
       s_ok = ok ? 1 : 0;
       if (!ok) atomicOr(&st->error, 1);
