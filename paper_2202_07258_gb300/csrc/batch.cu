@@ -31,6 +31,25 @@ __device__ __forceinline__ double warp_sum_dd(double v) {
   return v;
 }
 
+__device__ __forceinline__ double warp_max_dd(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
+
+// 4-byte asynchronous copy global -> shared (cp.async.ca)
+__device__ __forceinline__ void cp_async4(void* dst_smem, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst_smem))),
+               "l"(src)
+               : "memory");
+}
+
+// Start of the column chunk of the evaluation's phase 2 in its dynamic shared memory (after
+// the residuals, flags and refinement lists, 16-byte aligned).
+__device__ __forceinline__ float* beval_chunk_smem(float2* sr, int m, int npad) {
+  const size_t base = (size_t)m * kBEvalInst * sizeof(float2) + (size_t)kBEvalInst * npad * (1 + sizeof(uint16_t));
+  return reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(sr) + ((base + 15) & ~(size_t)15));
+}
+
 constexpr float kUf = 6.0e-8f;  // a little above 2^-24, the unit roundoff of float32
 
 __device__ __forceinline__ float warp_sum_f(float v) {
@@ -413,8 +432,10 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
   uint16_t* s_item = reinterpret_cast<uint16_t*>(s_fl + (size_t)kBEvalInst * p.npad);
   __shared__ int s_inst[kBEvalInst];
   __shared__ float s_beta[kBEvalInst];
-  __shared__ int s_lj[kBEvalInst][kBEvalList];
-  __shared__ float2 s_lx[kBEvalInst][kBEvalList];
+  // phase 1's nonzero lists share the dynamic region of phase 2's column chunk (the phases
+  // are separated by a block barrier)
+  int* s_lj = reinterpret_cast<int*>(beval_chunk_smem(sr, p.m, p.npad));            // [inst][list]
+  float2* s_lx = reinterpret_cast<float2*>(s_lj + kBEvalInst * kBEvalList);
   __shared__ double s_red[kBEvalThreads / 32][kBEvalInst][5];
   __shared__ int s_ref[kBEvalInst];
   __shared__ float s_qf[kBEvalInst][4];   // eps, eta, eta of refined correlations (rounded up)
@@ -487,8 +508,8 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
         const unsigned msk = __ballot_sync(kFull, nz);
         if (nz) {
           const int pos = cnt + __popc(msk & ((1u << lane) - 1u));
-          s_lj[bb][pos] = jc + t * 32 + lane;
-          s_lx[bb][pos] = xs[t];
+          s_lj[bb * kBEvalList + pos] = jc + t * 32 + lane;
+          s_lx[bb * kBEvalList + pos] = xs[t];
         }
         cnt += __popc(msk);
       }
@@ -497,7 +518,7 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
         float a[4][kBEvalRows];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const float* col = p.A + (size_t)s_lj[bb][e + u < cnt ? e + u : e] * p.lda;
+          const float* col = p.A + (size_t)s_lj[bb * kBEvalList + (e + u < cnt ? e + u : e)] * p.lda;
 #pragma unroll
           for (int r = 0; r < kBEvalRows; ++r) {
             const int i = r0 + lane + 32 * r;
@@ -506,7 +527,7 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const float2 x = e + u < cnt ? s_lx[bb][e + u] : make_float2(0.f, 0.f);
+          const float2 x = e + u < cnt ? s_lx[bb * kBEvalList + e + u] : make_float2(0.f, 0.f);
 #pragma unroll
           for (int r = 0; r < kBEvalRows; ++r) df_fma(qs[r], qc[r], a[u][r], x.x, x.y);
         }
@@ -542,92 +563,108 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
   }
   __syncthreads();
 
-  // ---- phase 2: correlations of the preserved coordinates, CP columns per warp step (the
-  // residual loads from shared memory serve all of them)
-  double epsm = 0.0;  // lane bb < kBEvalInst: translation step candidate of instance bb
+  // ---- phase 2: correlations of the preserved coordinates g_j = a_j^T r for the CTA's
+  // instances.  Columns stream through shared memory in chunks of 32, by blocks of up to 256
+  // rows (cp.async; the row stride padded to an odd count, so the 32 lanes of a warp, one per
+  // column, read distinct banks).  Warp w sums its 32-row share of each block for all 32
+  // columns and all instances in four interleaved sums per (column, instance), the residuals
+  // broadcast from shared memory; then thread (instance = warp, column = lane) combines the
+  // 8 warps' partials in a fixed three-level tree.  Longest chain of one sum:
+  // ceil(rows per warp / 4) + 2 + 3 (the Cg of make_bparams).
+  double epsm = 0.0;  // warp bb, after the combine: translation step candidate of instance bb
   {
-    constexpr int CP = PREC == kX2 ? 2 : 4;
-    const double eta_g = lane < kBEvalInst ? s_q[lane][2] : 0.0;
-    const int inst_l = lane < kBEvalInst ? s_inst[lane] : -1;
-    constexpr int W = kBEvalThreads / 32;
-    for (int j0 = CP * warp; j0 < p.n; j0 += CP * W) {
-      bool nd[CP];
-      unsigned any = 0;
-      const float* col[CP];
+    static_assert(kBEvalThreads / 32 == kBEvalInst, "one warp per instance in the combine");
+    constexpr int CC = 32, RB = kBEvalRowBlock, RS = RB + 1, RPW = RB / (kBEvalThreads / 32);
+    float* sA = beval_chunk_smem(sr, p.m, p.npad);
+    float* sP = sA + CC * RS;                                 // [warp][instance][column] sums
+    float* sPc = sP + (kBEvalThreads / 32) * kBEvalInst * CC; // their compensations
+    const int inst_w = s_inst[warp];
+    const double eta_w = s_q[warp][2];
+    for (int j0 = 0; j0 < p.n; j0 += CC) {
+      float sa[4][kBEvalInst], ca[4][kBEvalInst];
 #pragma unroll
-      for (int c = 0; c < CP; ++c) {
-        const int j = j0 + c;
-        nd[c] = lane < kBEvalInst && j < p.n && s_fl[lane * p.npad + j] == 0;
-        any |= __ballot_sync(kFull, nd[c]);
-        col[c] = p.A + (size_t)(j < p.n ? j : j0) * p.lda;
-      }
-      if (!any) continue;
-      float sa[CP][kBEvalInst], ca[CP][kBEvalInst];
+      for (int k4 = 0; k4 < 4; ++k4)
 #pragma unroll
-      for (int c = 0; c < CP; ++c)
-#pragma unroll
-        for (int bb = 0; bb < kBEvalInst; ++bb) {
-          sa[c][bb] = 0.f;
-          ca[c][bb] = 0.f;
+        for (int bb = 0; bb < kBEvalInst; ++bb) sa[k4][bb] = ca[k4][bb] = 0.f;
+      for (int rb = 0; rb < p.m; rb += RB) {
+        const int nr = min(RB, p.m - rb);
+        __syncthreads();   // the previous block is consumed
+        for (int e = tid; e < CC * nr; e += kBEvalThreads) {
+          const int c = e / nr, i = e - c * nr;
+          const int j = j0 + c;
+          if (j < p.n) cp_async4(sA + c * RS + i, p.A + (size_t)j * p.lda + rb + i);
+          else sA[c * RS + i] = 0.f;
         }
-#pragma unroll 2
-      for (int i = lane; i < p.m; i += 32) {
-        float a[CP];
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncthreads();
+        const int i0 = warp * RPW, i1 = min(nr, i0 + RPW);
+        const float* acol = sA + lane * RS;
+        for (int i = i0; i < i1; i += 4) {
 #pragma unroll
-        for (int c = 0; c < CP; ++c) a[c] = __ldg(col[c] + i);
-        const float4* rr = reinterpret_cast<const float4*>(sr + (size_t)i * kBEvalInst);
+          for (int k4 = 0; k4 < 4; ++k4) {
+            if (i + k4 < i1) {
+              const float a = acol[i + k4];
+              const float4* rr = reinterpret_cast<const float4*>(sr + (size_t)(rb + i + k4) * kBEvalInst);
 #pragma unroll
-        for (int h = 0; h < kBEvalInst / 2; ++h) {
-          const float4 v = rr[h];
-#pragma unroll
-          for (int c = 0; c < CP; ++c) {
-            if (PREC == kX2) {
-              df_fma(sa[c][2 * h], ca[c][2 * h], a[c], v.x, v.y);
-              df_fma(sa[c][2 * h + 1], ca[c][2 * h + 1], a[c], v.z, v.w);
-            } else {
-              sa[c][2 * h] = fmaf(a[c], v.x, sa[c][2 * h]);
-              sa[c][2 * h + 1] = fmaf(a[c], v.z, sa[c][2 * h + 1]);
+              for (int h = 0; h < kBEvalInst / 2; ++h) {
+                const float4 v = rr[h];
+                if (PREC == kX2) {
+                  df_fma(sa[k4][2 * h], ca[k4][2 * h], a, v.x, v.y);
+                  df_fma(sa[k4][2 * h + 1], ca[k4][2 * h + 1], a, v.z, v.w);
+                } else {
+                  sa[k4][2 * h] = fmaf(a, v.x, sa[k4][2 * h]);
+                  sa[k4][2 * h + 1] = fmaf(a, v.z, sa[k4][2 * h + 1]);
+                }
+              }
             }
           }
         }
       }
+      // the four sums of each (column, instance): (0 + 1) + (2 + 3)
 #pragma unroll
-      for (int c = 0; c < CP; ++c) {
-        float gs = 0.f, gc = 0.f;
-#pragma unroll
-        for (int bb = 0; bb < kBEvalInst; ++bb) {
-          float x = sa[c][bb], cc = ca[c][bb];
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            const float ox = __shfl_xor_sync(kFull, x, o);
-            if (PREC == kX2) {
-              const float oc = __shfl_xor_sync(kFull, cc, o);
-              df_add(x, cc, ox, oc);
-            } else {
-              x += ox;
-            }
-          }
-          if (lane == bb) {
-            gs = x;
-            gc = PREC == kX2 ? cc : 0.f;
-          }
+      for (int bb = 0; bb < kBEvalInst; ++bb) {
+        if (PREC == kX2) {
+          df_add(sa[0][bb], ca[0][bb], sa[1][bb], ca[1][bb]);
+          df_add(sa[2][bb], ca[2][bb], sa[3][bb], ca[3][bb]);
+          df_add(sa[0][bb], ca[0][bb], sa[2][bb], ca[2][bb]);
+        } else {
+          sa[0][bb] = (sa[0][bb] + sa[1][bb]) + (sa[2][bb] + sa[3][bb]);
         }
-        const int j = j0 + c;
-        if (nd[c]) {
-          const float2 g2 = df2_norm(gs, gc);
-          b.Ge[(size_t)inst_l * p.npad + j] = g2;
-          if (trans && p.jinf[j]) {
-            const double nr = p.nrm[j];
-            if (nr > 0.0) {
-              const double den = -p.w[j] - p.gamma_w * nr * p.t_norm;
-              epsm = fmax(epsm, fmax(df2_to_double(g2) + eta_g * nr, 0.0) / den);
-            }
+        sP[(warp * kBEvalInst + bb) * CC + lane] = sa[0][bb];
+        sPc[(warp * kBEvalInst + bb) * CC + lane] = PREC == kX2 ? ca[0][bb] : 0.f;
+      }
+      __syncthreads();
+      // thread (instance warp, column lane): the 8 row groups in a fixed tree
+      float g[8], gcomp[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        g[q] = sP[(q * kBEvalInst + warp) * CC + lane];
+        gcomp[q] = sPc[(q * kBEvalInst + warp) * CC + lane];
+      }
+#pragma unroll
+      for (int w2 = 1; w2 < 8; w2 <<= 1)
+#pragma unroll
+        for (int q = 0; q < 8; q += 2 * w2) {
+          if (PREC == kX2) df_add(g[q], gcomp[q], g[q + w2], gcomp[q + w2]);
+          else g[q] += g[q + w2];
+        }
+      const int j = j0 + lane;
+      if (inst_w >= 0 && j < p.n && s_fl[warp * p.npad + j] == 0) {
+        const float2 g2 = df2_norm(g[0], PREC == kX2 ? gcomp[0] : 0.f);
+        b.Ge[(size_t)inst_w * p.npad + j] = g2;
+        if (trans && p.jinf[j]) {
+          const double nr = p.nrm[j];
+          if (nr > 0.0) {
+            const double den = -p.w[j] - p.gamma_w * nr * p.t_norm;
+            epsm = fmax(epsm, fmax(df2_to_double(g2) + eta_w * nr, 0.0) / den);
           }
         }
       }
     }
+    epsm = warp_max_dd(epsm);
   }
-  if (lane < kBEvalInst) s_red[warp][lane][3] = epsm;
+  if (lane < kBEvalInst) s_red[warp][lane][3] = lane == warp ? epsm : 0.0;
   __syncthreads();
   if (tid < kBEvalInst) {
     double e = 0.0;
@@ -925,7 +962,12 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
 }
 
 size_t beval_smem_bytes(int m, int npad) {
-  return (size_t)m * kBEvalInst * sizeof(float2) + (size_t)kBEvalInst * npad * (1 + sizeof(uint16_t));
+  // residuals, flags, refinement lists, then (16-byte aligned) the column chunk of phase 2
+  // and the partial sums of its combine
+  const size_t base = (size_t)m * kBEvalInst * sizeof(float2) + (size_t)kBEvalInst * npad * (1 + sizeof(uint16_t));
+  const size_t chunk = sizeof(float) * ((size_t)32 * (kBEvalRowBlock + 1) + 2 * (size_t)(kBEvalThreads / 32) * kBEvalInst * 32);
+  const size_t lists = (size_t)kBEvalInst * kBEvalList * (sizeof(int) + sizeof(float2));
+  return ((base + 15) & ~(size_t)15) + (chunk > lists ? chunk : lists);
 }
 
 

@@ -32,6 +32,7 @@ constexpr int kBStages = 4;        // stages in flight
 constexpr int kBStepThreads = 512;  // 16 warps: 4 TMEM lane quarters x 4 column groups
 constexpr int kBEvalInst = 8;      // instances per CTA of the evaluation kernel
 constexpr int kBEvalThreads = 256;
+constexpr int kBEvalRowBlock = 256;  // rows of A per shared-memory block in the evaluation's A^T r
 constexpr int kBMaxRows = 1024;    // m limit: the residuals of a CTA's instances sit in shared memory
 constexpr int kBMaxCols = 4096;    // n limit: the Gram matrix has npad^2 bf16 entries
 constexpr int kBMaxBatch = 1 << 20;

@@ -950,12 +950,17 @@ BParams make_bparams(bvls_handle* h, const bvls_opts& o, int max_iter, int B) {
   p.invL2 = df2_from_double(p.invL);
   p.t_norm = h->t_norm;
   p.gamma_w = h->gamma_w;
-  // Rounding of the evaluation products (see common.cuh for the double-float bound):
-  // a lane sums ceil(m/32) products, then 5 shuffle levels; the residual sums up to n
-  // products per row in double-float.
+  // Rounding of the evaluation products (see common.cuh for the double-float bound).  The
+  // double-float recomputation of selected correlations: a lane sums ceil(m/32) products,
+  // then 5 shuffle levels; the residual sums up to n products per row in double-float.
   const double dg = (h->m + 31) / 32 + 5;
   p.Cg2 = 2.0 * (dg + 2.0) * (dg + 2.0) * kU * kU + 4.0 * kU * kU + 2.0 * kU64;
-  p.Cg = o.precision == BVLS_PREC_FP32X2 ? p.Cg2 : 1.01 * (dg + 2.0) * kU + kU;
+  // the evaluation's phase 2: a warp's share of the rows (32 of every block of 256) in four
+  // interleaved sums, their pairwise merge (2) and the three-level tree over the 8 warps (3)
+  const int rows_w = (h->m + kBEvalRowBlock - 1) / kBEvalRowBlock * (kBEvalRowBlock / (kBEvalThreads / 32));
+  const double de = (rows_w + 3) / 4 + 5;
+  p.Cg = o.precision == BVLS_PREC_FP32X2 ? 2.0 * (de + 2.0) * (de + 2.0) * kU * kU + 4.0 * kU * kU + 2.0 * kU64
+                                         : 1.01 * (de + 2.0) * kU + kU;
   const double df = h->n;
   p.Cf = 2.0 * (df + 2.0) * (df + 2.0) * kU * kU + 2.0 * kU * kU;
   p.Csub = 8.0 * kU * kU;
