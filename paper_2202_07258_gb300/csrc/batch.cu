@@ -566,15 +566,15 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
   // ---- phase 2: correlations of the preserved coordinates g_j = a_j^T r for the CTA's
   // instances.  Columns stream through shared memory in chunks of 32, by blocks of up to 256
   // rows (cp.async; the row stride padded to an odd count, so the 32 lanes of a warp, one per
-  // column, read distinct banks).  Warp w sums its 32-row share of each block for all 32
-  // columns and all instances in four interleaved sums per (column, instance), the residuals
-  // broadcast from shared memory; then thread (instance = warp, column = lane) combines the
-  // 8 warps' partials in a fixed three-level tree.  Longest chain of one sum:
-  // ceil(rows per warp / 4) + 2 + 3 (the Cg of make_bparams).
+  // column, read distinct banks).  Warp w sums its share (an eighth) of each block's rows for
+  // all 32 columns and all instances in four interleaved sums per (column, instance), the
+  // residuals broadcast from shared memory; then thread (instance = warp, column = lane)
+  // combines the 8 warps' partials in a fixed three-level tree.  Longest chain of one sum:
+  // sum over blocks of ceil(ceil(rows / 8) / 4), + 2 + 3 (the Cg of make_bparams).
   double epsm = 0.0;  // warp bb, after the combine: translation step candidate of instance bb
   {
     static_assert(kBEvalThreads / 32 == kBEvalInst, "one warp per instance in the combine");
-    constexpr int CC = 32, RB = kBEvalRowBlock, RS = RB + 1, RPW = RB / (kBEvalThreads / 32);
+    constexpr int CC = 32, RB = kBEvalRowBlock, RS = RB + 1, NW = kBEvalThreads / 32;
     float* sA = beval_chunk_smem(sr, p.m, p.npad);
     float* sP = sA + CC * RS;                                 // [warp][instance][column] sums
     float* sPc = sP + (kBEvalThreads / 32) * kBEvalInst * CC; // their compensations
@@ -598,7 +598,8 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
         cp_async_commit();
         cp_async_wait<0>();
         __syncthreads();
-        const int i0 = warp * RPW, i1 = min(nr, i0 + RPW);
+        const int rpw = (nr + NW - 1) / NW;   // the block's rows spread evenly over the warps
+        const int i0 = min(nr, warp * rpw), i1 = min(nr, i0 + rpw);
         const float* acol = sA + lane * RS;
         for (int i = i0; i < i1; i += 4) {
 #pragma unroll
