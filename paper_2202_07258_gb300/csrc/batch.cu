@@ -37,17 +37,14 @@ __device__ __forceinline__ double warp_max_dd(double v) {
 }
 
 // 4-byte asynchronous copy global -> shared (cp.async.ca)
-__device__ __forceinline__ void cp_async4(void* dst_smem, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst_smem))),
-               "l"(src)
-               : "memory");
-}
-
-// Start of the column chunk of the evaluation's phase 2 in its dynamic shared memory (after
-// the residuals, flags and refinement lists, 16-byte aligned).
-__device__ __forceinline__ float* beval_chunk_smem(float2* sr, int m, int npad) {
-  const size_t base = (size_t)m * kBEvalInst * sizeof(float2) + (size_t)kBEvalInst * npad * (1 + sizeof(uint16_t));
-  return reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(sr) + ((base + 15) & ~(size_t)15));
+// Dynamic shared memory of the evaluation, rows rounded up to 8 (mr), zero past m:
+//   sr   [mr][kBEvalInst] residual (hi, lo)      srh  [mr][kBEvalInst] its float32 part
+//   s_fl [kBEvalInst][npad] flags                s_item [kBEvalInst][npad] coordinate lists
+//   then, 16-byte aligned, phase 1's nonzero lists.
+__host__ __device__ __forceinline__ size_t beval_lists_offset(int m, int npad) {
+  const size_t mr = (size_t)((m + 7) & ~7);
+  const size_t base = mr * kBEvalInst * (sizeof(float2) + sizeof(float)) + (size_t)kBEvalInst * npad * (1 + sizeof(uint16_t));
+  return (base + 15) & ~(size_t)15;
 }
 
 constexpr float kUf = 6.0e-8f;  // a little above 2^-24, the unit roundoff of float32
@@ -424,17 +421,18 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
   const int n_act = st->n_act;
   const int i0 = blockIdx.x * kBEvalInst;
   if (i0 >= n_act) return;
-  // dynamic shared memory: the residuals [m][kBEvalInst] (hi, lo), the screened flags
-  // [kBEvalInst][npad] (bit 2 marks a correlation recomputed in double-float) and the
-  // per-instance lists of coordinates to recompute [kBEvalInst][npad]
+  // dynamic shared memory (beval_lists_offset): the residuals, the screened flags (bit 2
+  // marks a correlation recomputed in double-float), the coordinate lists of phases 2 and 2b,
+  // and phase 1's nonzero lists
+  const int mr = (p.m + 7) & ~7;
   extern __shared__ float2 sr[];
-  uint8_t* s_fl = reinterpret_cast<uint8_t*>(sr + (size_t)p.m * kBEvalInst);
+  float* srh = reinterpret_cast<float*>(sr + (size_t)mr * kBEvalInst);
+  uint8_t* s_fl = reinterpret_cast<uint8_t*>(srh + (size_t)mr * kBEvalInst);
   uint16_t* s_item = reinterpret_cast<uint16_t*>(s_fl + (size_t)kBEvalInst * p.npad);
   __shared__ int s_inst[kBEvalInst];
   __shared__ float s_beta[kBEvalInst];
-  // phase 1's nonzero lists share the dynamic region of phase 2's column chunk (the phases
-  // are separated by a block barrier)
-  int* s_lj = reinterpret_cast<int*>(beval_chunk_smem(sr, p.m, p.npad));            // [inst][list]
+  __shared__ int s_goff[kBMaxCols / 32 + 1];
+  int* s_lj = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(sr) + beval_lists_offset(p.m, p.npad));
   float2* s_lx = reinterpret_cast<float2*>(s_lj + kBEvalInst * kBEvalList);
   __shared__ double s_red[kBEvalThreads / 32][kBEvalInst][5];
   __shared__ int s_ref[kBEvalInst];
@@ -537,9 +535,9 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
 #pragma unroll
     for (int r = 0; r < kBEvalRows; ++r) {
       const int i = r0 + lane + 32 * r;
-      if (i < p.m) {
+      if (i < mr) {
         float rh = 0.f, rl = 0.f;
-        if (inst >= 0) {
+        if (inst >= 0 && i < p.m) {
           const float y = b.Y[(size_t)inst * p.lda + i];
           float dh, de;
           two_sum(y, -qs[r], dh, de);
@@ -550,6 +548,7 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
           yv += (double)y * (double)y;
         }
         sr[(size_t)i * kBEvalInst + bb] = make_float2(rh, rl);
+        srh[(size_t)i * kBEvalInst + bb] = rh;
       }
     }
     }
@@ -563,109 +562,187 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
   }
   __syncthreads();
 
-  // ---- phase 2: correlations of the preserved coordinates g_j = a_j^T r for the CTA's
-  // instances.  Columns stream through shared memory in chunks of 32, by blocks of up to 256
-  // rows (cp.async; the row stride padded to an odd count, so the 32 lanes of a warp, one per
-  // column, read distinct banks).  Warp w sums its share (an eighth) of each block's rows for
-  // all 32 columns and all instances in four interleaved sums per (column, instance), the
-  // residuals broadcast from shared memory; then thread (instance = warp, column = lane)
-  // combines the 8 warps' partials in a fixed three-level tree.  Longest chain of one sum:
-  // sum over blocks of ceil(ceil(rows / 8) / 4), + 2 + 3 (the Cg of make_bparams).
-  double epsm = 0.0;  // warp bb, after the combine: translation step candidate of instance bb
+  // ---- phase 2: correlations g_j = a_j^T r for the CTA's instances over the columns that
+  // some instance preserves.  Those columns are listed in order; thread (warp w, lane c)
+  // owns list entries 32 (BC w + u) + c (u < BC, then strides of 256 BC) and walks all
+  // rows of its columns for the 8 instances: A in 32-byte pieces straight from L2 (the next
+  // piece in flight while the current one is used), the residuals broadcast from shared
+  // memory.  Summation order: beval_chain (the Cg of make_bparams).
   {
-    static_assert(kBEvalThreads / 32 == kBEvalInst, "one warp per instance in the combine");
-    constexpr int CC = 32, RB = kBEvalRowBlock, RS = RB + 1, NW = kBEvalThreads / 32;
-    float* sA = beval_chunk_smem(sr, p.m, p.npad);
-    float* sP = sA + CC * RS;                                 // [warp][instance][column] sums
-    float* sPc = sP + (kBEvalThreads / 32) * kBEvalInst * CC; // their compensations
-    const int inst_w = s_inst[warp];
-    const double eta_w = s_q[warp][2];
-    for (int j0 = 0; j0 < p.n; j0 += CC) {
-      float sa[4][kBEvalInst], ca[4][kBEvalInst];
+    constexpr int NW = kBEvalThreads / 32;
+    constexpr int NI = kBEvalInst;
+    constexpr int BC = PREC == kX2 ? 1 : 2;                 // columns per thread
+    constexpr int ILV = PREC == kX2 ? kBEvalIlvX2 : kBEvalIlvF32;
+    constexpr bool PF = PREC != kX2;                        // prefetch the next rows
+    const int NG = p.npad / 32;
+    // the list: group counts, an exclusive scan by warp 0, then the entries
+    for (int g = warp; g < NG; g += NW) {
+      const int j = g * 32 + lane;
+      bool need = false;
+      if (j < p.n)
 #pragma unroll
-      for (int k4 = 0; k4 < 4; ++k4)
-#pragma unroll
-        for (int bb = 0; bb < kBEvalInst; ++bb) sa[k4][bb] = ca[k4][bb] = 0.f;
-      for (int rb = 0; rb < p.m; rb += RB) {
-        const int nr = min(RB, p.m - rb);
-        __syncthreads();   // the previous block is consumed
-        for (int e = tid; e < CC * nr; e += kBEvalThreads) {
-          const int c = e / nr, i = e - c * nr;
-          const int j = j0 + c;
-          if (j < p.n) cp_async4(sA + c * RS + i, p.A + (size_t)j * p.lda + rb + i);
-          else sA[c * RS + i] = 0.f;
+        for (int bb = 0; bb < NI; ++bb) need |= (s_fl[bb * p.npad + j] & 3) == 0;
+      const unsigned msk = __ballot_sync(kFull, need);
+      if (lane == 0) s_goff[g] = __popc(msk);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      const int per = (NG + 31) / 32;
+      int loc = 0;
+      for (int q = 0; q < per; ++q) {
+        const int g = lane * per + q;
+        if (g < NG) loc += s_goff[g];
+      }
+      int inc = loc;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += v;
+      }
+      int run = inc - loc;
+      for (int q = 0; q < per; ++q) {
+        const int g = lane * per + q;
+        if (g < NG) {
+          const int c = s_goff[g];
+          s_goff[g] = run;
+          run += c;
         }
-        cp_async_commit();
-        cp_async_wait<0>();
-        __syncthreads();
-        const int rpw = (nr + NW - 1) / NW;   // the block's rows spread evenly over the warps
-        const int i0 = min(nr, warp * rpw), i1 = min(nr, i0 + rpw);
-        const float* acol = sA + lane * RS;
-        for (int i = i0; i < i1; i += 4) {
+      }
+      if (lane == 31) s_goff[NG] = inc;
+    }
+    __syncthreads();
+    for (int g = warp; g < NG; g += NW) {
+      const int j = g * 32 + lane;
+      bool need = false;
+      if (j < p.n)
 #pragma unroll
-          for (int k4 = 0; k4 < 4; ++k4) {
-            if (i + k4 < i1) {
-              const float a = acol[i + k4];
-              const float4* rr = reinterpret_cast<const float4*>(sr + (size_t)(rb + i + k4) * kBEvalInst);
+        for (int bb = 0; bb < NI; ++bb) need |= (s_fl[bb * p.npad + j] & 3) == 0;
+      const unsigned msk = __ballot_sync(kFull, need);
+      if (need) s_item[s_goff[g] + __popc(msk & ((1u << lane) - 1u))] = (uint16_t)j;
+    }
+    __syncthreads();
+    const int ncol = s_goff[NG];
+    const int R = p.erb;
+    // s_red[w][bb][3]: warp w's running max of the translation step candidates of instance bb
+    if (lane < NI) s_red[warp][lane][3] = 0.0;
+    __syncwarp();
+    for (int t0 = warp * 32 * BC; t0 < ncol; t0 += kBEvalThreads * BC) {
+      int jc[BC];
+      bool cv[BC];
+      const float* colp[BC];
 #pragma unroll
-              for (int h = 0; h < kBEvalInst / 2; ++h) {
-                const float4 v = rr[h];
-                if (PREC == kX2) {
-                  df_fma(sa[k4][2 * h], ca[k4][2 * h], a, v.x, v.y);
-                  df_fma(sa[k4][2 * h + 1], ca[k4][2 * h + 1], a, v.z, v.w);
-                } else {
-                  sa[k4][2 * h] = fmaf(a, v.x, sa[k4][2 * h]);
-                  sa[k4][2 * h + 1] = fmaf(a, v.z, sa[k4][2 * h + 1]);
-                }
+      for (int u = 0; u < BC; ++u) {
+        const int t = t0 + u * 32 + lane;
+        cv[u] = t < ncol;
+        jc[u] = s_item[cv[u] ? t : t0];
+        colp[u] = p.A + (size_t)jc[u] * p.lda;
+      }
+      float tot[BC][NI], totc[BC][NI], acc[BC][NI][ILV], accc[BC][NI][ILV];
+#pragma unroll
+      for (int u = 0; u < BC; ++u)
+#pragma unroll
+        for (int bb = 0; bb < NI; ++bb) {
+          tot[u][bb] = totc[u][bb] = 0.f;
+#pragma unroll
+          for (int q = 0; q < ILV; ++q) acc[u][bb][q] = accc[u][bb][q] = 0.f;
+        }
+      float a[BC][8], an[BC][8];
+      auto load_rows = [&](float (&dst)[BC][8], int i) {
+#pragma unroll
+        for (int u = 0; u < BC; ++u) {
+          const float4 v0 = __ldg(reinterpret_cast<const float4*>(colp[u] + i));
+          const float4 v1 = __ldg(reinterpret_cast<const float4*>(colp[u] + i + 4));
+          dst[u][0] = v0.x; dst[u][1] = v0.y; dst[u][2] = v0.z; dst[u][3] = v0.w;
+          dst[u][4] = v1.x; dst[u][5] = v1.y; dst[u][6] = v1.z; dst[u][7] = v1.w;
+        }
+      };
+      if (PF) load_rows(a, 0);
+      int rin = 0;  // rows of the running block done
+      for (int i = 0; i < mr; i += 8) {
+        if (PF) {
+          if (i + 8 < mr) load_rows(an, i + 8);
+        } else {
+          load_rows(a, i);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (PREC == kX2) {
+            const float4* rr = reinterpret_cast<const float4*>(sr + (size_t)(i + q) * NI);
+#pragma unroll
+            for (int h = 0; h < NI / 2; ++h) {
+              const float4 v = rr[h];
+#pragma unroll
+              for (int u = 0; u < BC; ++u) {
+                df_fma(acc[u][2 * h][q % ILV], accc[u][2 * h][q % ILV], a[u][q], v.x, v.y);
+                df_fma(acc[u][2 * h + 1][q % ILV], accc[u][2 * h + 1][q % ILV], a[u][q], v.z, v.w);
+              }
+            }
+          } else {
+            const float4* rr = reinterpret_cast<const float4*>(srh + (size_t)(i + q) * NI);
+#pragma unroll
+            for (int h = 0; h < NI / 4; ++h) {
+              const float4 v = rr[h];
+#pragma unroll
+              for (int u = 0; u < BC; ++u) {
+                acc[u][4 * h][q % ILV] = fmaf(a[u][q], v.x, acc[u][4 * h][q % ILV]);
+                acc[u][4 * h + 1][q % ILV] = fmaf(a[u][q], v.y, acc[u][4 * h + 1][q % ILV]);
+                acc[u][4 * h + 2][q % ILV] = fmaf(a[u][q], v.z, acc[u][4 * h + 2][q % ILV]);
+                acc[u][4 * h + 3][q % ILV] = fmaf(a[u][q], v.w, acc[u][4 * h + 3][q % ILV]);
               }
             }
           }
         }
-      }
-      // the four sums of each (column, instance): (0 + 1) + (2 + 3)
+        rin += 8;
+        if (rin == R || i + 8 >= mr) {  // end of a block: merge its sums into the total
 #pragma unroll
-      for (int bb = 0; bb < kBEvalInst; ++bb) {
-        if (PREC == kX2) {
-          df_add(sa[0][bb], ca[0][bb], sa[1][bb], ca[1][bb]);
-          df_add(sa[2][bb], ca[2][bb], sa[3][bb], ca[3][bb]);
-          df_add(sa[0][bb], ca[0][bb], sa[2][bb], ca[2][bb]);
-        } else {
-          sa[0][bb] = (sa[0][bb] + sa[1][bb]) + (sa[2][bb] + sa[3][bb]);
+          for (int u = 0; u < BC; ++u)
+#pragma unroll
+            for (int bb = 0; bb < NI; ++bb) {
+#pragma unroll
+              for (int w2 = 1; w2 < ILV; w2 <<= 1)
+#pragma unroll
+                for (int q = 0; q < ILV; q += 2 * w2) {
+                  if (PREC == kX2) df_add(acc[u][bb][q], accc[u][bb][q], acc[u][bb][q + w2], accc[u][bb][q + w2]);
+                  else acc[u][bb][q] += acc[u][bb][q + w2];
+                }
+              if (PREC == kX2) df_add(tot[u][bb], totc[u][bb], acc[u][bb][0], accc[u][bb][0]);
+              else tot[u][bb] += acc[u][bb][0];
+#pragma unroll
+              for (int q = 0; q < ILV; ++q) acc[u][bb][q] = accc[u][bb][q] = 0.f;
+            }
+          rin = 0;
         }
-        sP[(warp * kBEvalInst + bb) * CC + lane] = sa[0][bb];
-        sPc[(warp * kBEvalInst + bb) * CC + lane] = PREC == kX2 ? ca[0][bb] : 0.f;
-      }
-      __syncthreads();
-      // thread (instance warp, column lane): the 8 row groups in a fixed tree
-      float g[8], gcomp[8];
+        if (PF) {
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        g[q] = sP[(q * kBEvalInst + warp) * CC + lane];
-        gcomp[q] = sPc[(q * kBEvalInst + warp) * CC + lane];
-      }
+          for (int u = 0; u < BC; ++u)
 #pragma unroll
-      for (int w2 = 1; w2 < 8; w2 <<= 1)
-#pragma unroll
-        for (int q = 0; q < 8; q += 2 * w2) {
-          if (PREC == kX2) df_add(g[q], gcomp[q], g[q + w2], gcomp[q + w2]);
-          else g[q] += g[q + w2];
+            for (int q = 0; q < 8; ++q) a[u][q] = an[u][q];
         }
-      const int j = j0 + lane;
-      if (inst_w >= 0 && j < p.n && s_fl[warp * p.npad + j] == 0) {
-        const float2 g2 = df2_norm(g[0], PREC == kX2 ? gcomp[0] : 0.f);
-        b.Ge[(size_t)inst_w * p.npad + j] = g2;
-        if (trans && p.jinf[j]) {
-          const double nr = p.nrm[j];
-          if (nr > 0.0) {
-            const double den = -p.w[j] - p.gamma_w * nr * p.t_norm;
-            epsm = fmax(epsm, fmax(df2_to_double(g2) + eta_w * nr, 0.0) / den);
+      }
+#pragma unroll
+      for (int bb = 0; bb < NI; ++bb) {
+        const int inst = s_inst[bb];
+        double em = 0.0;
+#pragma unroll
+        for (int u = 0; u < BC; ++u) {
+          const int j = jc[u];
+          if (!cv[u] || inst < 0 || s_fl[bb * p.npad + j] != 0) continue;
+          const float2 g2 = df2_norm(tot[u][bb], PREC == kX2 ? totc[u][bb] : 0.f);
+          b.Ge[(size_t)inst * p.npad + j] = g2;
+          if (trans && p.jinf[j]) {
+            const double nr = p.nrm[j];
+            if (nr > 0.0) {
+              const double den = -p.w[j] - p.gamma_w * nr * p.t_norm;
+              em = fmax(em, fmax(df2_to_double(g2) + s_q[bb][2] * nr, 0.0) / den);
+            }
           }
+        }
+        if (trans) {
+          em = warp_max_dd(em);
+          if (lane == 0) s_red[warp][bb][3] = fmax(s_red[warp][bb][3], em);
         }
       }
     }
-    epsm = warp_max_dd(epsm);
   }
-  if (lane < kBEvalInst) s_red[warp][lane][3] = lane == warp ? epsm : 0.0;
   __syncthreads();
   if (tid < kBEvalInst) {
     double e = 0.0;
@@ -963,12 +1040,7 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
 }
 
 size_t beval_smem_bytes(int m, int npad) {
-  // residuals, flags, refinement lists, then (16-byte aligned) the column chunk of phase 2
-  // and the partial sums of its combine
-  const size_t base = (size_t)m * kBEvalInst * sizeof(float2) + (size_t)kBEvalInst * npad * (1 + sizeof(uint16_t));
-  const size_t chunk = sizeof(float) * ((size_t)32 * (kBEvalRowBlock + 1) + 2 * (size_t)(kBEvalThreads / 32) * kBEvalInst * 32);
-  const size_t lists = (size_t)kBEvalInst * kBEvalList * (sizeof(int) + sizeof(float2));
-  return ((base + 15) & ~(size_t)15) + (chunk > lists ? chunk : lists);
+  return beval_lists_offset(m, npad) + (size_t)kBEvalInst * kBEvalList * (sizeof(int) + sizeof(float2));
 }
 
 

@@ -32,7 +32,8 @@ constexpr int kBStages = 4;        // stages in flight
 constexpr int kBStepThreads = 512;  // 16 warps: 4 TMEM lane quarters x 4 column groups
 constexpr int kBEvalInst = 8;      // instances per CTA of the evaluation kernel
 constexpr int kBEvalThreads = 256;
-constexpr int kBEvalRowBlock = 256;  // rows of A per shared-memory block in the evaluation's A^T r
+constexpr int kBEvalIlvF32 = 2;    // interleaved sums per correlation in the evaluation's A^T r
+constexpr int kBEvalIlvX2 = 2;
 constexpr int kBMaxRows = 1024;    // m limit: the residuals of a CTA's instances sit in shared memory
 constexpr int kBMaxCols = 4096;    // n limit: the Gram matrix has npad^2 bf16 entries
 constexpr int kBMaxBatch = 1 << 20;
@@ -74,6 +75,7 @@ struct BParams {
   double Cf;               // residual rounding: <= Cf sum_j |x_j| ||a_j|| (2-norm)
   double Csub;
   double tol;
+  int erb;                 // rows per block of the evaluation's correlation sums (beval_chain)
   int max_iter;
   int dual_mode;
   int screening;
@@ -102,6 +104,24 @@ struct BBuffers {
   int* npres;              // B: preserved coordinates at the finish
   BState* st;
 };
+
+// Summation order of the evaluation's correlations a_j^T r: one thread owns (column, instance)
+// and walks the rows in blocks of `rows` (a multiple of 8) with `ilv` interleaved sums (row i
+// into sum i mod ilv), merged pairwise at the end of each block and added to a running total.
+// `depth` bounds the roundings any product passes through: rows / ilv + log2(ilv) + blocks.
+struct BEvalChain {
+  int rows;
+  int depth;
+};
+__host__ __device__ inline BEvalChain beval_chain(int m, int ilv) {
+  const int lg = ilv >= 4 ? 2 : ilv >= 2 ? 1 : 0;
+  BEvalChain best{8, 1 << 30};
+  for (int r = 8; r <= 1024; r += 8) {
+    const int d = r / ilv + lg + (m + r - 1) / r;
+    if (d < best.depth) best = BEvalChain{r, d};
+  }
+  return best;
+}
 
 cudaError_t launch_bgram(const float* A, int lda, int m, int n, int npad, __nv_bfloat16* H, cudaStream_t s);
 cudaError_t launch_binit(const BParams& p, const BBuffers& b, cudaStream_t s);

@@ -955,16 +955,10 @@ BParams make_bparams(bvls_handle* h, const bvls_opts& o, int max_iter, int B) {
   // then 5 shuffle levels; the residual sums up to n products per row in double-float.
   const double dg = (h->m + 31) / 32 + 5;
   p.Cg2 = 2.0 * (dg + 2.0) * (dg + 2.0) * kU * kU + 4.0 * kU * kU + 2.0 * kU64;
-  // the evaluation's phase 2: a warp's share of the rows (an eighth of every block of up to
-  // 256) in four interleaved sums, their pairwise merge (2) and the three-level tree over
-  // the 8 warps (3)
-  int chain = 0;
-  for (int rb = 0; rb < h->m; rb += kBEvalRowBlock) {
-    const int nr = std::min(kBEvalRowBlock, h->m - rb);
-    const int rpw = (nr + kBEvalThreads / 32 - 1) / (kBEvalThreads / 32);
-    chain += (rpw + 3) / 4;
-  }
-  const double de = chain + 5;
+  // the evaluation's correlations: blocked, interleaved sums (beval_chain)
+  const BEvalChain ch = beval_chain(h->m, o.precision == BVLS_PREC_FP32X2 ? kBEvalIlvX2 : kBEvalIlvF32);
+  p.erb = ch.rows;
+  const double de = ch.depth;
   p.Cg = o.precision == BVLS_PREC_FP32X2 ? 2.0 * (de + 2.0) * (de + 2.0) * kU * kU + 4.0 * kU * kU + 2.0 * kU64
                                          : 1.01 * (de + 2.0) * kU + kU;
   const double df = h->n;
