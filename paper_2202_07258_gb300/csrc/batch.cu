@@ -14,6 +14,7 @@
 
 #include "batch.cuh"
 #include "common.cuh"
+#include "f32x2.cuh"
 #include "umma.cuh"
 
 namespace bvls {
@@ -38,12 +39,12 @@ __device__ __forceinline__ double warp_max_dd(double v) {
 
 // 4-byte asynchronous copy global -> shared (cp.async.ca)
 // Dynamic shared memory of the evaluation, rows rounded up to 8 (mr), zero past m:
-//   sr   [mr][kBEvalInst] residual (hi, lo)      srh  [mr][kBEvalInst] its float32 part
+//   srh  [mr][kBEvalInst] residual, high parts   srl  [mr][kBEvalInst] low parts
 //   s_fl [kBEvalInst][npad] flags                s_item [kBEvalInst][npad] coordinate lists
-//   then, 16-byte aligned, phase 1's nonzero lists.
+//   then, 16-byte aligned, phase 1's nonzero lists, which phase 2's copy ring reuses.
 __host__ __device__ __forceinline__ size_t beval_lists_offset(int m, int npad) {
   const size_t mr = (size_t)((m + 7) & ~7);
-  const size_t base = mr * kBEvalInst * (sizeof(float2) + sizeof(float)) + (size_t)kBEvalInst * npad * (1 + sizeof(uint16_t));
+  const size_t base = mr * kBEvalInst * 2 * sizeof(float) + (size_t)kBEvalInst * npad * (1 + sizeof(uint16_t));
   return (base + 15) & ~(size_t)15;
 }
 
@@ -414,7 +415,12 @@ cudaError_t launch_bstep(const BParams& p, const BBuffers& b, int j, cudaStream_
 //   phase 2  g_j = a_j^T r for preserved j (warp = column, lanes over rows), PREC products;
 //   phase 3  gap sums and the step (thread = coordinate);
 //   phase 4  sphere test; phase 5  outputs of the instances that stop.
-template <int PREC>
+// Bytes of phase 2's copy ring: per warp RING steps of 8 rows of its 32 BC columns.
+__host__ __device__ constexpr size_t beval_ring_bytes(int prec, int ring) {
+  return (size_t)ring * (kBEvalThreads / 32) * (prec == kX2 ? 1 : 2) * 2 * 32 * 16;
+}
+
+template <int PREC, int RING>
 __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers b, int jrel) {
   BState* st = b.st;
   if (st->done) return;
@@ -425,14 +431,15 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
   // marks a correlation recomputed in double-float), the coordinate lists of phases 2 and 2b,
   // and phase 1's nonzero lists
   const int mr = (p.m + 7) & ~7;
-  extern __shared__ float2 sr[];
-  float* srh = reinterpret_cast<float*>(sr + (size_t)mr * kBEvalInst);
-  uint8_t* s_fl = reinterpret_cast<uint8_t*>(srh + (size_t)mr * kBEvalInst);
+  extern __shared__ float4 smem_ev[];
+  float* srh = reinterpret_cast<float*>(smem_ev);
+  float* srl = srh + (size_t)mr * kBEvalInst;
+  uint8_t* s_fl = reinterpret_cast<uint8_t*>(srl + (size_t)mr * kBEvalInst);
   uint16_t* s_item = reinterpret_cast<uint16_t*>(s_fl + (size_t)kBEvalInst * p.npad);
   __shared__ int s_inst[kBEvalInst];
   __shared__ float s_beta[kBEvalInst];
   __shared__ int s_goff[kBMaxCols / 32 + 1];
-  int* s_lj = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(sr) + beval_lists_offset(p.m, p.npad));
+  int* s_lj = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(smem_ev) + beval_lists_offset(p.m, p.npad));
   float2* s_lx = reinterpret_cast<float2*>(s_lj + kBEvalInst * kBEvalList);
   __shared__ double s_red[kBEvalThreads / 32][kBEvalInst][5];
   __shared__ int s_ref[kBEvalInst];
@@ -469,29 +476,33 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
     s_pins[tid] = 0;
   }
   __syncthreads();
-  // the screened flags of the CTA's instances, one coalesced pass (1 = fixed, or no instance)
-  for (int q = tid; q < kBEvalInst * p.npad; q += kBEvalThreads) {
-    const int bb = q / p.npad, j = q - bb * p.npad;
-    const int inst = s_inst[bb];
-    s_fl[q] = inst >= 0 ? b.flags[(size_t)inst * p.npad + j] : (uint8_t)1;
+  // the screened flags of the CTA's instances, one coalesced pass in 4-byte words (1 = fixed,
+  // or no instance)
+  {
+    const int w4 = p.npad / 4;
+#pragma unroll 4
+    for (int q = tid; q < kBEvalInst * w4; q += kBEvalThreads) {
+      const int bb = q / w4, j4 = q - bb * w4;
+      const int inst = s_inst[bb];
+      reinterpret_cast<uint32_t*>(s_fl)[q] =
+          inst >= 0 ? reinterpret_cast<const uint32_t*>(b.flags + (size_t)inst * p.npad)[j4] : 0x01010101u;
+    }
   }
 
   // ---- phase 1: r = y - A x_k.  Warp bb owns instance bb: for each block of 256 rows it
-  // lists the nonzero x_j of a chunk of kBEvalList columns, then its lanes (rows lane,
-  // lane + 32, ...) accumulate the listed columns four at a time, so each lane keeps 32
-  // loads in flight.
+  // lists the nonzero x_j of a chunk of kBEvalList columns, then its lanes (row pairs
+  // 2 lane + 64 t, t < 4) accumulate the listed columns four at a time in packed
+  // double-float pairs, so each lane keeps 16 loads of 8 bytes in flight.
   const float2* __restrict__ Xc = b.X[s];
   {
+    constexpr int NP = kBEvalRows / 2;  // row pairs per lane and block
     const int bb = warp;  // kBEvalThreads / 32 == kBEvalInst
     const int inst = s_inst[bb];
     double pv = 0.0, yv = 0.0;
     for (int r0 = 0; r0 < p.m; r0 += 32 * kBEvalRows) {
-    float qs[kBEvalRows], qc[kBEvalRows];
+    f32x2 qs[NP], qc[NP];
 #pragma unroll
-    for (int r = 0; r < kBEvalRows; ++r) {
-      qs[r] = 0.f;
-      qc[r] = 0.f;
-    }
+    for (int r = 0; r < NP; ++r) qs[r] = qc[r] = 0ull;
     for (int jc = 0; jc < p.n && inst >= 0; jc += kBEvalList) {
       int cnt = 0;
       float2 xs[kBEvalList / 32];
@@ -513,42 +524,50 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
       }
       __syncwarp();
       for (int e = 0; e < cnt; e += 4) {
-        float a[4][kBEvalRows];
+        f32x2 a[4][NP];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const float* col = p.A + (size_t)s_lj[bb * kBEvalList + (e + u < cnt ? e + u : e)] * p.lda;
 #pragma unroll
-          for (int r = 0; r < kBEvalRows; ++r) {
-            const int i = r0 + lane + 32 * r;
-            a[u][r] = (e + u < cnt && i < p.m) ? __ldg(col + i) : 0.f;
+          for (int r = 0; r < NP; ++r) {
+            // rows i, i + 1 (i even, i < m <= lda, so i + 1 < lda: in the column)
+            const int i = r0 + 2 * lane + 64 * r;
+            a[u][r] = (e + u < cnt && i < p.m) ? __ldg(reinterpret_cast<const unsigned long long*>(col + i)) : 0ull;
           }
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const float2 x = e + u < cnt ? s_lx[bb * kBEvalList + e + u] : make_float2(0.f, 0.f);
+          const f32x2 xh = x2_pack(x.x, x.x), xl = x2_pack(x.y, x.y);
 #pragma unroll
-          for (int r = 0; r < kBEvalRows; ++r) df_fma(qs[r], qc[r], a[u][r], x.x, x.y);
+          for (int r = 0; r < NP; ++r) df_fma_x2(qs[r], qc[r], a[u][r], xh, xl);
         }
       }
       __syncwarp();
     }
 #pragma unroll
-    for (int r = 0; r < kBEvalRows; ++r) {
-      const int i = r0 + lane + 32 * r;
-      if (i < mr) {
-        float rh = 0.f, rl = 0.f;
-        if (inst >= 0 && i < p.m) {
-          const float y = b.Y[(size_t)inst * p.lda + i];
-          float dh, de;
-          two_sum(y, -qs[r], dh, de);
-          de -= qc[r];
-          two_sum(dh, de, rh, rl);
-          const double rv = (double)rh + (double)rl;
-          pv += 0.5 * rv * rv;
-          yv += (double)y * (double)y;
+    for (int r = 0; r < NP; ++r) {
+      float q2s[2], q2c[2];
+      x2_unpack(qs[r], q2s[0], q2s[1]);
+      x2_unpack(qc[r], q2c[0], q2c[1]);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int i = r0 + 2 * lane + 64 * r + h;
+        if (i < mr) {
+          float rh = 0.f, rl = 0.f;
+          if (inst >= 0 && i < p.m) {
+            const float y = b.Y[(size_t)inst * p.lda + i];
+            float dh, de;
+            two_sum(y, -q2s[h], dh, de);
+            de -= q2c[h];
+            two_sum(dh, de, rh, rl);
+            const double rv = (double)rh + (double)rl;
+            pv += 0.5 * rv * rv;
+            yv += (double)y * (double)y;
+          }
+          srh[(size_t)i * kBEvalInst + bb] = rh;
+          srl[(size_t)i * kBEvalInst + bb] = rl;
         }
-        sr[(size_t)i * kBEvalInst + bb] = make_float2(rh, rl);
-        srh[(size_t)i * kBEvalInst + bb] = rh;
       }
     }
     }
@@ -565,15 +584,15 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
   // ---- phase 2: correlations g_j = a_j^T r for the CTA's instances over the columns that
   // some instance preserves.  Those columns are listed in order; thread (warp w, lane c)
   // owns list entries 32 (BC w + u) + c (u < BC, then strides of 256 BC) and walks all
-  // rows of its columns for the 8 instances: A in 32-byte pieces straight from L2 (the next
-  // piece in flight while the current one is used), the residuals broadcast from shared
-  // memory.  Summation order: beval_chain (the Cg of make_bparams).
+  // rows of its columns for the 8 instances: A in 32-byte pieces (8 rows) that the thread
+  // copies from L2 into its own slots of a RING-step shared-memory ring (16-byte cp.async,
+  // RING - 1 steps in flight), the residuals broadcast from shared memory.  Summation
+  // order: beval_chain (the Cg of make_bparams).
   {
     constexpr int NW = kBEvalThreads / 32;
     constexpr int NI = kBEvalInst;
     constexpr int BC = PREC == kX2 ? 1 : 2;                 // columns per thread
     constexpr int ILV = PREC == kX2 ? kBEvalIlvX2 : kBEvalIlvF32;
-    constexpr bool PF = PREC != kX2;                        // prefetch the next rows
     const int NG = p.npad / 32;
     // the list: group counts, an exclusive scan by warp 0, then the entries
     for (int g = warp; g < NG; g += NW) {
@@ -622,6 +641,7 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
     __syncthreads();
     const int ncol = s_goff[NG];
     const int R = p.erb;
+    float4* ring = reinterpret_cast<float4*>(s_lj);  // phase 1's lists are dead
     // s_red[w][bb][3]: warp w's running max of the translation step candidates of instance bb
     if (lane < NI) s_red[warp][lane][3] = 0.0;
     __syncwarp();
@@ -636,57 +656,69 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
         jc[u] = s_item[cv[u] ? t : t0];
         colp[u] = p.A + (size_t)jc[u] * p.lda;
       }
-      float tot[BC][NI], totc[BC][NI], acc[BC][NI][ILV], accc[BC][NI][ILV];
+      // instance pairs (2 h, 2 h + 1) in packed registers
+      constexpr int NH = NI / 2;
+      f32x2 tot[BC][NH], totc[BC][NH], acc[BC][NH][ILV], accc[BC][NH][ILV];
 #pragma unroll
       for (int u = 0; u < BC; ++u)
 #pragma unroll
-        for (int bb = 0; bb < NI; ++bb) {
-          tot[u][bb] = totc[u][bb] = 0.f;
+        for (int h = 0; h < NH; ++h) {
+          tot[u][h] = totc[u][h] = 0ull;
 #pragma unroll
-          for (int q = 0; q < ILV; ++q) acc[u][bb][q] = accc[u][bb][q] = 0.f;
+          for (int q = 0; q < ILV; ++q) acc[u][h][q] = accc[u][h][q] = 0ull;
         }
-      float a[BC][8], an[BC][8];
-      auto load_rows = [&](float (&dst)[BC][8], int i) {
+      // ring slot (step t, column u, half h) of this thread: ring + ((t % RING) * 2 BC + 2 u + h) * 32 + lane
+      float4* ringw = ring + (size_t)warp * RING * 2 * BC * 32 + lane;
+      auto issue = [&](int i) {  // rows i..i+7 of the thread's columns
+        float4* d = ringw + (size_t)((i >> 3) % RING) * 2 * BC * 32;
 #pragma unroll
         for (int u = 0; u < BC; ++u) {
-          const float4 v0 = __ldg(reinterpret_cast<const float4*>(colp[u] + i));
-          const float4 v1 = __ldg(reinterpret_cast<const float4*>(colp[u] + i + 4));
-          dst[u][0] = v0.x; dst[u][1] = v0.y; dst[u][2] = v0.z; dst[u][3] = v0.w;
-          dst[u][4] = v1.x; dst[u][5] = v1.y; dst[u][6] = v1.z; dst[u][7] = v1.w;
+          cp_async16(d + (2 * u) * 32, colp[u] + i);
+          cp_async16(d + (2 * u + 1) * 32, colp[u] + i + 4);
         }
       };
-      if (PF) load_rows(a, 0);
+#pragma unroll
+      for (int t = 0; t < RING - 1; ++t) {
+        if (8 * t < mr) issue(8 * t);
+        cp_async_commit();
+      }
+      float a[BC][8];
       int rin = 0;  // rows of the running block done
       for (int i = 0; i < mr; i += 8) {
-        if (PF) {
-          if (i + 8 < mr) load_rows(an, i + 8);
-        } else {
-          load_rows(a, i);
+        if (i + 8 * (RING - 1) < mr) issue(i + 8 * (RING - 1));
+        cp_async_commit();
+        cp_async_wait<RING - 1>();  // this thread's copy of rows i..i+7 has landed
+        {
+          const float4* sl = ringw + (size_t)((i >> 3) % RING) * 2 * BC * 32;
+#pragma unroll
+          for (int u = 0; u < BC; ++u) {
+            const float4 v0 = sl[(2 * u) * 32], v1 = sl[(2 * u + 1) * 32];
+            a[u][0] = v0.x; a[u][1] = v0.y; a[u][2] = v0.z; a[u][3] = v0.w;
+            a[u][4] = v1.x; a[u][5] = v1.y; a[u][6] = v1.z; a[u][7] = v1.w;
+          }
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          if (PREC == kX2) {
-            const float4* rr = reinterpret_cast<const float4*>(sr + (size_t)(i + q) * NI);
+          f32x2 ad[BC];
 #pragma unroll
-            for (int h = 0; h < NI / 2; ++h) {
-              const float4 v = rr[h];
+          for (int u = 0; u < BC; ++u) ad[u] = x2_pack(a[u][q], a[u][q]);
+          const ulonglong2* rh = reinterpret_cast<const ulonglong2*>(srh + (size_t)(i + q) * NI);
+          const ulonglong2* rl = reinterpret_cast<const ulonglong2*>(srl + (size_t)(i + q) * NI);
+#pragma unroll
+          for (int h2 = 0; h2 < NI / 4; ++h2) {
+            const ulonglong2 vh = rh[h2];
+            if (PREC == kX2) {
+              const ulonglong2 vl = rl[h2];
 #pragma unroll
               for (int u = 0; u < BC; ++u) {
-                df_fma(acc[u][2 * h][q % ILV], accc[u][2 * h][q % ILV], a[u][q], v.x, v.y);
-                df_fma(acc[u][2 * h + 1][q % ILV], accc[u][2 * h + 1][q % ILV], a[u][q], v.z, v.w);
+                df_fma_x2(acc[u][2 * h2][q % ILV], accc[u][2 * h2][q % ILV], ad[u], vh.x, vl.x);
+                df_fma_x2(acc[u][2 * h2 + 1][q % ILV], accc[u][2 * h2 + 1][q % ILV], ad[u], vh.y, vl.y);
               }
-            }
-          } else {
-            const float4* rr = reinterpret_cast<const float4*>(srh + (size_t)(i + q) * NI);
-#pragma unroll
-            for (int h = 0; h < NI / 4; ++h) {
-              const float4 v = rr[h];
+            } else {
 #pragma unroll
               for (int u = 0; u < BC; ++u) {
-                acc[u][4 * h][q % ILV] = fmaf(a[u][q], v.x, acc[u][4 * h][q % ILV]);
-                acc[u][4 * h + 1][q % ILV] = fmaf(a[u][q], v.y, acc[u][4 * h + 1][q % ILV]);
-                acc[u][4 * h + 2][q % ILV] = fmaf(a[u][q], v.z, acc[u][4 * h + 2][q % ILV]);
-                acc[u][4 * h + 3][q % ILV] = fmaf(a[u][q], v.w, acc[u][4 * h + 3][q % ILV]);
+                acc[u][2 * h2][q % ILV] = x2_fma(ad[u], vh.x, acc[u][2 * h2][q % ILV]);
+                acc[u][2 * h2 + 1][q % ILV] = x2_fma(ad[u], vh.y, acc[u][2 * h2 + 1][q % ILV]);
               }
             }
           }
@@ -696,28 +728,31 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
 #pragma unroll
           for (int u = 0; u < BC; ++u)
 #pragma unroll
-            for (int bb = 0; bb < NI; ++bb) {
+            for (int h = 0; h < NH; ++h) {
 #pragma unroll
               for (int w2 = 1; w2 < ILV; w2 <<= 1)
 #pragma unroll
                 for (int q = 0; q < ILV; q += 2 * w2) {
-                  if (PREC == kX2) df_add(acc[u][bb][q], accc[u][bb][q], acc[u][bb][q + w2], accc[u][bb][q + w2]);
-                  else acc[u][bb][q] += acc[u][bb][q + w2];
+                  if (PREC == kX2) df_add_x2(acc[u][h][q], accc[u][h][q], acc[u][h][q + w2], accc[u][h][q + w2]);
+                  else acc[u][h][q] = x2_add(acc[u][h][q], acc[u][h][q + w2]);
                 }
-              if (PREC == kX2) df_add(tot[u][bb], totc[u][bb], acc[u][bb][0], accc[u][bb][0]);
-              else tot[u][bb] += acc[u][bb][0];
+              if (PREC == kX2) df_add_x2(tot[u][h], totc[u][h], acc[u][h][0], accc[u][h][0]);
+              else tot[u][h] = x2_add(tot[u][h], acc[u][h][0]);
 #pragma unroll
-              for (int q = 0; q < ILV; ++q) acc[u][bb][q] = accc[u][bb][q] = 0.f;
+              for (int q = 0; q < ILV; ++q) acc[u][h][q] = accc[u][h][q] = 0ull;
             }
           rin = 0;
         }
-        if (PF) {
-#pragma unroll
-          for (int u = 0; u < BC; ++u)
-#pragma unroll
-            for (int q = 0; q < 8; ++q) a[u][q] = an[u][q];
-        }
       }
+      cp_async_wait<0>();
+      float ts[BC][NI], tcs[BC][NI];
+#pragma unroll
+      for (int u = 0; u < BC; ++u)
+#pragma unroll
+        for (int h = 0; h < NH; ++h) {
+          x2_unpack(tot[u][h], ts[u][2 * h], ts[u][2 * h + 1]);
+          x2_unpack(totc[u][h], tcs[u][2 * h], tcs[u][2 * h + 1]);
+        }
 #pragma unroll
       for (int bb = 0; bb < NI; ++bb) {
         const int inst = s_inst[bb];
@@ -726,7 +761,7 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
         for (int u = 0; u < BC; ++u) {
           const int j = jc[u];
           if (!cv[u] || inst < 0 || s_fl[bb * p.npad + j] != 0) continue;
-          const float2 g2 = df2_norm(tot[u][bb], PREC == kX2 ? totc[u][bb] : 0.f);
+          const float2 g2 = df2_norm(ts[u][bb], PREC == kX2 ? tcs[u][bb] : 0.f);
           b.Ge[(size_t)inst * p.npad + j] = g2;
           if (trans && p.jinf[j]) {
             const double nr = p.nrm[j];
@@ -757,7 +792,7 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
     s_qf[tid][1] = f32_up(s_q[tid][5]);
     s_qf[tid][2] = f32_up(s_q[tid][8]);
     if (tid == 0) {
-      const int T = (p.n + kBEvalThreads - 1) / kBEvalThreads;
+      const int T = (p.n + 31) / 32;  // terms per lane in phase 3
       s_sum_infl = 1.0 + 2.0 * (T + 8) * 6.0e-8;
     }
   }
@@ -773,15 +808,15 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
     float2* Xn = b.X[s ^ 1];
     __nv_bfloat16* Dn = b.D[s ^ 1];
     const float2 invL2 = p.invL2;
-    for (int bb = 0; bb < kBEvalInst; ++bb) {
+    {
+      const int bb = warp;  // warp bb owns instance bb, lanes over coordinates
       const int inst = s_inst[bb];
-      if (inst < 0) break;  // active instances are packed at the front
       const float be = s_beta[bb];
       const float eps = s_qf[bb][0], eta = s_qf[bb][1], eta_ref = s_qf[bb][2];
       float va = 0.f, vx = 0.f, vd = 0.f, vs = 0.f;
       int vp = 0;
-#pragma unroll 2
-      for (int j = tid; j < p.n; j += kBEvalThreads) {
+#pragma unroll 4
+      for (int j = lane; j < p.n && inst >= 0; j += 32) {
         const size_t o = (size_t)inst * p.npad + j;
         const float2 xk = Xc[o];
         const float2 xp = Xn[o];
@@ -819,25 +854,19 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
       vs = warp_sum_f(vs);
       for (int o2 = 16; o2 > 0; o2 >>= 1) vp += __shfl_xor_sync(kFull, vp, o2);
       if (lane == 0) {
-        s_red[warp][bb][0] = va;
-        s_red[warp][bb][1] = vx;
-        s_red[warp][bb][2] = vd;
-        s_red[warp][bb][3] = vp;
-        s_red[warp][bb][4] = vs;
+        s_red[bb][bb][0] = va;
+        s_red[bb][bb][1] = vx;
+        s_red[bb][bb][2] = vd;
+        s_red[bb][bb][3] = vp;
+        s_red[bb][bb][4] = vs;
       }
     }
   }
   __syncthreads();
   if (tid < kBEvalInst) {
-    double a = 0.0, x1 = 0.0, d = 0.0, np = 0.0, sl = 0.0;
-    for (int w = 0; w < kBEvalThreads / 32; ++w) {
-      a += s_red[w][tid][0];
-      x1 += s_red[w][tid][1];
-      d += s_red[w][tid][2];
-      np += s_red[w][tid][3];
-      sl += s_red[w][tid][4];
-    }
-    a *= s_sum_infl;   // float32 sums of nonnegative terms: per-thread runs and 5 shuffle levels
+    double a = s_red[tid][tid][0], x1 = s_red[tid][tid][1], d = s_red[tid][tid][2], np = s_red[tid][tid][3],
+           sl = s_red[tid][tid][4];
+    a *= s_sum_infl;   // float32 sums of nonnegative terms: per-lane runs and 5 shuffle levels
     x1 *= s_sum_infl;
     const int inst = s_inst[tid];
     int ref = 0;
@@ -904,9 +933,9 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
         float sh[4] = {0.f, 0.f, 0.f, 0.f}, sc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 2
         for (int i = lane; i < p.m; i += 32) {
-          const float2 r = sr[(size_t)i * kBEvalInst + bb];
+          const float rh = srh[(size_t)i * kBEvalInst + bb], rl = srl[(size_t)i * kBEvalInst + bb];
 #pragma unroll
-          for (int c = 0; c < 4; ++c) df_fma(sh[c], sc[c], __ldg(col[c] + i), r.x, r.y);
+          for (int c = 0; c < 4; ++c) df_fma(sh[c], sc[c], __ldg(col[c] + i), rh, rl);
         }
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
@@ -932,14 +961,14 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
       }
     }
     __syncthreads();
-    // ---- phase 3b: the gap terms of the refined instances again
-    for (int bb2 = 0; bb2 < kBEvalInst; ++bb2) {
-      const int inst2 = s_inst[bb2];
-      if (inst2 < 0) break;
-      if (!s_ref[bb2]) continue;
+    // ---- phase 3b: the gap terms of the refined instances again (warp = instance)
+    {
+      const int bb2 = warp;
+      const int inst2 = s_ref[bb2] ? s_inst[bb2] : -1;
       const float eps = s_qf[bb2][0], eta = s_qf[bb2][1], eta_ref = s_qf[bb2][2];
       float va = 0.f;
-      for (int j = tid; j < p.n; j += kBEvalThreads) {
+#pragma unroll 4
+      for (int j = lane; j < p.n && inst2 >= 0; j += 32) {
         const uint8_t fl = s_fl[bb2 * p.npad + j];
         if (fl & 3) continue;
         const size_t o = (size_t)inst2 * p.npad + j;
@@ -948,12 +977,11 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
         va += gap_term_up(du, dl, gt, E);
       }
       va = warp_sum_f(va);
-      if (lane == 0) s_red[warp][bb2][0] = va;
+      if (lane == 0) s_red[bb2][bb2][0] = va;
     }
     __syncthreads();
     if (tid < kBEvalInst && s_ref[tid]) {
-      double a = 0.0;
-      for (int w = 0; w < kBEvalThreads / 32; ++w) a += s_red[w][tid][0];
+      const double a = s_red[tid][tid][0];
       s_q[tid][6] = fmin(s_q[tid][6], (a * s_sum_infl + s_q[tid][9]) * (1.0 + 1e-12));
     }
     __syncthreads();
@@ -975,13 +1003,14 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
   // x_k and x_{k+1} both sit at the bound the test gives.
   if (p.screening && p.dual_mode != kZero) {
     const float2* __restrict__ Xn = b.X[s ^ 1];
-    for (int bb = 0; bb < kBEvalInst; ++bb) {
+    {
+      const int bb = warp;  // warp = instance
       const int inst = s_inst[bb];
-      if (inst < 0) break;
       const float eps = s_qf[bb][0];
       const float rr = f32_up(s_q[bb][4]);
       int pins = 0;
-      for (int j = tid; j < p.n; j += kBEvalThreads) {
+#pragma unroll 4
+      for (int j = lane; j < p.n && inst >= 0; j += 32) {
         if (s_fl[bb * p.npad + j] & 3) continue;
         const float nr = p.nrmf[j];
         if (!(nr > 0.f)) continue;
@@ -1007,17 +1036,17 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
         }
       }
       for (int o2 = 16; o2 > 0; o2 >>= 1) pins += __shfl_xor_sync(kFull, pins, o2);
-      if (lane == 0 && pins) atomicAdd(&s_pins[bb], pins);
+      if (lane == 0) s_pins[bb] = pins;
     }
     __syncthreads();
   }
 
   // ---- phase 5: outputs of the instances that stop at this evaluation
-  for (int bb = 0; bb < kBEvalInst; ++bb) {
-    const int inst = s_inst[bb];
-    if (inst < 0) break;
-    if (!s_stop[bb]) continue;
-    for (int j = tid; j < p.n; j += kBEvalThreads) {
+  {
+    const int bb = warp;  // warp = instance
+    const int inst = s_stop[bb] ? s_inst[bb] : -1;
+#pragma unroll 4
+    for (int j = lane; j < p.n && inst >= 0; j += 32) {
       const uint8_t f = s_fl[bb * p.npad + j] & 3;
       const size_t o = (size_t)inst * p.npad + j;
       const double x = f == 1 ? p.l[j] : f == 2 ? p.u[j] : fmin(fmax(df2_to_double(Xc[o]), p.l[j]), p.u[j]);
@@ -1039,17 +1068,49 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
   if (blockIdx.x == 0 && tid == 0) st->sum_eval += (double)n_act;
 }
 
-size_t beval_smem_bytes(int m, int npad) {
-  return beval_lists_offset(m, npad) + (size_t)kBEvalInst * kBEvalList * (sizeof(int) + sizeof(float2));
+size_t beval_smem_bytes(int m, int npad, int prec, int ring) {
+  const size_t lists = (size_t)kBEvalInst * kBEvalList * (sizeof(int) + sizeof(float2));
+  const size_t rb = beval_ring_bytes(prec, ring);
+  return beval_lists_offset(m, npad) + (lists > rb ? lists : rb);
 }
+
+namespace {
+// The deep ring when the kernel's shared memory fits the opt-in limit, else a single slot.
+template <int PREC>
+int beval_ring(int m, int npad) {
+  static const int optin = [] {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
+    return v;
+  }();
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, k_beval<PREC, kBEvalRing>) != cudaSuccess) return 1;
+  return beval_smem_bytes(m, npad, PREC, kBEvalRing) + fa.sharedSizeBytes <= (size_t)optin ? kBEvalRing : 1;
+}
+
+template <int PREC>
+cudaError_t beval_configure(int m, int npad) {
+  if (beval_ring<PREC>(m, npad) == kBEvalRing)
+    return cudaFuncSetAttribute(k_beval<PREC, kBEvalRing>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)beval_smem_bytes(m, npad, PREC, kBEvalRing));
+  return cudaFuncSetAttribute(k_beval<PREC, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)beval_smem_bytes(m, npad, PREC, 1));
+}
+
+template <int PREC>
+cudaError_t beval_launch(const BParams& p, const BBuffers& b, int j, cudaStream_t s) {
+  const int grid = (p.B + kBEvalInst - 1) / kBEvalInst;
+  if (beval_ring<PREC>(p.m, p.npad) == kBEvalRing)
+    k_beval<PREC, kBEvalRing><<<grid, kBEvalThreads, beval_smem_bytes(p.m, p.npad, PREC, kBEvalRing), s>>>(p, b, j);
+  else
+    k_beval<PREC, 1><<<grid, kBEvalThreads, beval_smem_bytes(p.m, p.npad, PREC, 1), s>>>(p, b, j);
+  return cudaGetLastError();
+}
+}  // namespace
 
 
 cudaError_t launch_beval(const BParams& p, const BBuffers& b, int j, int precision, cudaStream_t s) {
-  const int grid = (p.B + kBEvalInst - 1) / kBEvalInst;
-  const size_t sm = beval_smem_bytes(p.m, p.npad);
-  if (precision == kX2) k_beval<kX2><<<grid, kBEvalThreads, sm, s>>>(p, b, j);
-  else k_beval<kF32><<<grid, kBEvalThreads, sm, s>>>(p, b, j);
-  return cudaGetLastError();
+  return precision == kX2 ? beval_launch<kX2>(p, b, j, s) : beval_launch<kF32>(p, b, j, s);
 }
 
 // ------------------------------------------------------------------ retirement
@@ -1101,10 +1162,9 @@ __global__ void __launch_bounds__(1024) k_bcompact(BParams p, BBuffers b) {
 cudaError_t batch_configure(int m, int npad) {
   cudaError_t e = cudaFuncSetAttribute(k_bstep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bstep_smem_bytes());
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_beval<kX2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)beval_smem_bytes(m, npad));
+  e = beval_configure<kX2>(m, npad);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_beval<kF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)beval_smem_bytes(m, npad));
+  return beval_configure<kF32>(m, npad);
 }
 
 cudaError_t launch_bcompact(const BParams& p, const BBuffers& b, cudaStream_t s) {

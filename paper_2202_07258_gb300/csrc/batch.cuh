@@ -34,6 +34,7 @@ constexpr int kBEvalInst = 8;      // instances per CTA of the evaluation kernel
 constexpr int kBEvalThreads = 256;
 constexpr int kBEvalIlvF32 = 2;    // interleaved sums per correlation in the evaluation's A^T r
 constexpr int kBEvalIlvX2 = 2;
+constexpr int kBEvalRing = 4;      // steps of 8 rows in the evaluation's copy ring (RING - 1 in flight)
 constexpr int kBMaxRows = 1024;    // m limit: the residuals of a CTA's instances sit in shared memory
 constexpr int kBMaxCols = 4096;    // n limit: the Gram matrix has npad^2 bf16 entries
 constexpr int kBMaxBatch = 1 << 20;
@@ -133,6 +134,6 @@ cudaError_t launch_bchunk_end(const BBuffers& b, int chunk_len, cudaStream_t s);
 cudaError_t launch_bloop_ctl(const BBuffers& b, cudaGraphConditionalHandle h, int max_chunks, cudaStream_t s);
 size_t bstep_smem_bytes();
 cudaError_t batch_configure(int m, int npad);  // shared-memory attributes of the step and evaluation kernels
-size_t beval_smem_bytes(int m, int npad);
+size_t beval_smem_bytes(int m, int npad, int prec, int ring);
 
 }  // namespace bvls
