@@ -210,9 +210,13 @@ cudaError_t launch_binit(const BParams& p, const BBuffers& b, cudaStream_t s) {
 // ------------------------------------------------------------------ tensor-core step
 // Grid (npad / 128 coordinate tiles, ceil(B / 128) instance tiles), 512 threads, one CTA per
 // SM (128 KB of stages).  Operand K chunks of 64 stream through kBStages shared-memory
-// stages with 16-byte asynchronous copies; thread 0 issues four 128x128x16 MMAs per chunk and
-// commits them to the stage's mbarrier, which releases the stage for the chunk kBStages
-// later.  The epilogue warps read the accumulator rows of their 32 coordinates from TMEM.
+// stages, synchronised by mbarriers only: warps 0-3 copy a chunk with 16-byte asynchronous
+// copies into a free stage, wait for their own copies, fence them to the async proxy and
+// arrive on the stage's full barrier; one thread of warp 4 waits for it, issues four
+// 128x128x16 MMAs and commits them to the stage's empty barrier, which frees the stage for
+// the chunk kBStages later, and after the last chunk to the done barrier.  Meanwhile the
+// other warps load their first epilogue operands; then all 16 read the accumulator rows of
+// their 32 coordinates from TMEM.
 __global__ void __launch_bounds__(kBStepThreads, 1) k_bstep(BParams p, BBuffers b, int jrel) {
   BState* st = b.st;
   if (st->done) return;
@@ -220,7 +224,7 @@ __global__ void __launch_bounds__(kBStepThreads, 1) k_bstep(BParams p, BBuffers 
   const int mt = blockIdx.x, nt = blockIdx.y;
   if (nt * kBTile >= n_act) return;
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t mbar[kBStages];
+  __shared__ __align__(8) uint64_t full[kBStages], empty[kBStages], done;
   __shared__ uint32_t s_tmem;
   __shared__ int s_inst[kBTile];
   __shared__ float s_beta[kBTile];
@@ -254,7 +258,11 @@ __global__ void __launch_bounds__(kBStepThreads, 1) k_bstep(BParams p, BBuffers 
   }
   if (warp == 0) tmem_alloc(&s_tmem, kBTile);
   if (tid == 0) {
-    for (int q = 0; q < kBStages; ++q) mbar_init(&mbar[q], 1);
+    for (int q = 0; q < kBStages; ++q) {
+      mbar_init(&full[q], kBProducerWarps * 32);
+      mbar_init(&empty[q], 1);
+    }
+    mbar_init(&done, 1);
     fence_barrier_init();
   }
   tc_fence_before();
@@ -263,56 +271,66 @@ __global__ void __launch_bounds__(kBStepThreads, 1) k_bstep(BParams p, BBuffers 
   const uint32_t tmem = s_tmem;
 
   const int nch = p.npad / kBChunk;
-  const __nv_bfloat16* Hrow = p.H + (size_t)mt * kBTile * p.npad;
-  const __nv_bfloat16* Dsrc = b.D[s];
-  auto load_chunk = [&](int c) {
-    unsigned char* sa = smem + (size_t)(c % kBStages) * kStageBytes;
-    unsigned char* sb = sa + kStageBytes / 2;
-    const int kofs = c * kBChunk;
-#pragma unroll
-    for (int t = 0; t < (kBTile * 8) / kBStepThreads; ++t) {
-      const int q = tid + t * kBStepThreads;
-      const int r = ((q >> 6) << 3) | (q & 7);
-      const int kc = (q >> 3) & 7;
-      const uint32_t off = core_offset(r, kc);
-      cp_async16(sa + off, Hrow + (size_t)r * p.npad + kofs + kc * 8);
-      const int inst = s_inst[r];
-      const int row = inst >= 0 ? inst : p.B;  // row B of D is zero
-      cp_async16(sb + off, Dsrc + (size_t)row * p.npad + kofs + kc * 8);
-    }
-    cp_async_commit();
-  };
-  const int npro = nch < kBStages ? nch : kBStages;
-  for (int c = 0; c < npro; ++c) load_chunk(c);
-  const uint32_t idesc = umma_idesc_bf16(kBTile, kBTile);
   bool ok = true;
-  for (int c = 0; c < nch; ++c) {
-    const int ahead = min(kBStages - 1, nch - 1 - c);
-    if (ahead >= 3) cp_async_wait<3>();
-    else if (ahead == 2) cp_async_wait<2>();
-    else if (ahead == 1) cp_async_wait<1>();
-    else cp_async_wait<0>();
-    fence_proxy_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-      const uint32_t sa = smem_u32(smem + (size_t)(c % kBStages) * kStageBytes);
-      const uint32_t sb = sa + kStageBytes / 2;
+  if (warp < kBProducerWarps) {
+    // producers: chunk c into stage c % kBStages once the MMAs of chunk c - kBStages are done
+    const __nv_bfloat16* Hrow = p.H + (size_t)mt * kBTile * p.npad;
+    const __nv_bfloat16* Dsrc = b.D[s];
+    constexpr int NPT = kBProducerWarps * 32;
+    auto load_chunk = [&](int c) {
+      unsigned char* sa = smem + (size_t)(c % kBStages) * kStageBytes;
+      unsigned char* sb = sa + kStageBytes / 2;
+      const int kofs = c * kBChunk;
 #pragma unroll
-      for (int kk = 0; kk < kBChunk / 16; ++kk)
-        umma_bf16(tmem, umma_smem_desc(sa + kk * 256), umma_smem_desc(sb + kk * 256), idesc, c > 0 || kk > 0);
-      umma_commit(&mbar[c % kBStages]);
+      for (int t = 0; t < (kBTile * 8) / NPT; ++t) {
+        const int q = tid + t * NPT;
+        const int r = ((q >> 6) << 3) | (q & 7);
+        const int kc = (q >> 3) & 7;
+        const uint32_t off = core_offset(r, kc);
+        cp_async16(sa + off, Hrow + (size_t)r * p.npad + kofs + kc * 8);
+        const int inst = s_inst[r];
+        const int row = inst >= 0 ? inst : p.B;  // row B of D is zero
+        cp_async16(sb + off, Dsrc + (size_t)row * p.npad + kofs + kc * 8);
+      }
+      cp_async_commit();
+    };
+    static_assert(kBStages == 4, "the drain below waits on up to kBStages - 2 newer groups");
+    for (int c = 0; c < nch; ++c) {
+      if (c >= kBStages && !mbar_wait(&empty[c % kBStages], ((c / kBStages) - 1) & 1)) ok = false;
+      load_chunk(c);
+      if (c >= kBStages - 1) {  // chunk c - kBStages + 1 has landed: announce it
+        cp_async_wait<kBStages - 1>();
+        fence_proxy_async_smem();
+        mbar_arrive(&full[(c - kBStages + 1) % kBStages]);
+      }
     }
-    if (c + kBStages < nch) {
-      if (!mbar_wait(&mbar[c % kBStages], (c / kBStages) & 1)) ok = false;
-      load_chunk(c + kBStages);
+    for (int c = nch - kBStages + 1 > 0 ? nch - kBStages + 1 : 0; c < nch; ++c) {
+      const int newer = nch - 1 - c;
+      if (newer >= 2) cp_async_wait<2>();
+      else if (newer == 1) cp_async_wait<1>();
+      else cp_async_wait<0>();
+      fence_proxy_async_smem();
+      mbar_arrive(&full[c % kBStages]);
     }
+  } else if (warp == kBProducerWarps) {
+    // MMA issuer: the warp waits for each stage, lane 0 issues and commits
+    const uint32_t idesc = umma_idesc_bf16(kBTile, kBTile);
+    for (int c = 0; c < nch; ++c) {
+      if (!mbar_wait(&full[c % kBStages], (c / kBStages) & 1)) ok = false;
+      tc_fence_after();
+      if (lane == 0) {
+        const uint32_t sa = smem_u32(smem + (size_t)(c % kBStages) * kStageBytes);
+        const uint32_t sb = sa + kStageBytes / 2;
+#pragma unroll
+        for (int kk = 0; kk < kBChunk / 16; ++kk)
+          umma_bf16(tmem, umma_smem_desc(sa + kk * 256), umma_smem_desc(sb + kk * 256), idesc, c > 0 || kk > 0);
+        umma_commit(&empty[c % kBStages]);
+      }
+      __syncwarp();
+    }
+    if (lane == 0) umma_commit(&done);
+    __syncwarp();
   }
-  {
-    const int cl = nch - 1;
-    if (!mbar_wait(&mbar[cl % kBStages], (cl / kBStages) & 1)) ok = false;
-  }
-  tc_fence_after();
 
   // epilogue: warp w reads TMEM lane quarter w % 4 (coordinates) and instance columns
   // [32 (w / 4), 32 (w / 4) + 32); thread = coordinate jg
@@ -327,32 +345,40 @@ __global__ void __launch_bounds__(kBStepThreads, 1) k_bstep(BParams p, BBuffers 
   const float2* __restrict__ Xc = b.X[s];
   float2* Xn = b.X[s ^ 1];
   __nv_bfloat16* Dn = b.D[s ^ 1];
-  const int cbeg = (warp >> 2) * (kBTile / (kBStepThreads / 128));
-  for (int c0 = cbeg; c0 < cbeg + kBTile / (kBStepThreads / 128); c0 += 32) {
-    if (s_inst[c0] < 0) break;  // active instances are packed at the front of the tile
+  static_assert(kBTile / (kBStepThreads / 128) == 32, "one 32-column group of instances per warp");
+  const int c0 = (warp >> 2) * 32;
+  const bool have = s_inst[c0] >= 0;  // active instances are packed at the front of the tile
+  float gp[8];
+  float2 xk[8], xp[8];
+  uint8_t fl[8];
+  auto load8 = [&](int c8) {  // eight instances' operands in flight
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc) {
+      const int inst = s_inst[c0 + c8 + cc];
+      gp[cc] = 0.f;
+      xk[cc] = make_float2(0.f, 0.f);
+      xp[cc] = xk[cc];
+      fl[cc] = 1;
+      if (inst >= 0 && jv) {
+        const size_t o = (size_t)inst * p.npad + jg;
+        gp[cc] = Gp[o];
+        xk[cc] = Xc[o];
+        xp[cc] = Xn[o];
+        fl[cc] = b.flags[o];
+      }
+    }
+  };
+  if (have) load8(0);  // while the MMAs run
+  if (!mbar_wait(&done, 0)) ok = false;
+  __syncwarp();
+  tc_fence_after();
+  if (have) {
     float acc[32];
     tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, acc);
     float dv[32];
 #pragma unroll
     for (int c8 = 0; c8 < 32; c8 += 8) {
-      float gp[8];
-      float2 xk[8], xp[8];
-      uint8_t fl[8];
-#pragma unroll
-      for (int cc = 0; cc < 8; ++cc) {  // loads first: eight instances in flight
-        const int inst = s_inst[c0 + c8 + cc];
-        gp[cc] = 0.f;
-        xk[cc] = make_float2(0.f, 0.f);
-        xp[cc] = xk[cc];
-        fl[cc] = 1;
-        if (inst >= 0 && jv) {
-          const size_t o = (size_t)inst * p.npad + jg;
-          gp[cc] = Gp[o];
-          xk[cc] = Xc[o];
-          xp[cc] = Xn[o];
-          fl[cc] = b.flags[o];
-        }
-      }
+      if (c8 > 0) load8(c8);
 #pragma unroll
       for (int cc = 0; cc < 8; ++cc) {
         const int inst = s_inst[c0 + c8 + cc];
@@ -397,7 +423,7 @@ __global__ void __launch_bounds__(kBStepThreads, 1) k_bstep(BParams p, BBuffers 
     if (inst >= 0) b.dotp[s][(size_t)mt * p.B + inst] = s_dot[0][tid] + s_dot[1][tid] + s_dot[2][tid] + s_dot[3][tid];
   }
   if (warp == 0) tmem_dealloc(tmem, kBTile);
-  if (!ok && tid == 0) atomicOr(&st->error, 1);
+  if (!ok) atomicOr(&st->error, 1);
   if (tid == 0 && mt == 0 && nt == 0) st->sum_step += (double)n_act;
 }
 
@@ -412,9 +438,10 @@ cudaError_t launch_bstep(const BParams& p, const BBuffers& b, int j, cudaStream_
 // ------------------------------------------------------------------ evaluation
 // kBEvalInst instances per CTA (A is read once for all of them), 256 threads.
 //   phase 1  r = y - A x_k (warp = instance, lanes over rows), double-float, nonzero x_j only;
-//   phase 2  g_j = a_j^T r for preserved j (warp = column, lanes over rows), PREC products;
-//   phase 3  gap sums and the step (thread = coordinate);
-//   phase 4  sphere test; phase 5  outputs of the instances that stop.
+//   phase 2  g_j = a_j^T r for the columns some instance preserves (thread = two columns,
+//            all rows), PREC products;
+//   phase 3  gap sums and the step (warp = instance, lanes over coordinates);
+//   phase 4  sphere test; phase 5  outputs of the instances that stop (warp = instance).
 // Bytes of phase 2's copy ring: per warp RING steps of 8 rows of its 32 BC columns.
 __host__ __device__ constexpr size_t beval_ring_bytes(int prec, int ring) {
   return (size_t)ring * (kBEvalThreads / 32) * (prec == kX2 ? 1 : 2) * 2 * 32 * 16;

@@ -30,6 +30,7 @@ constexpr int kBTile = 128;        // coordinates per M tile = instances per N t
 constexpr int kBChunk = 64;        // K elements per shared-memory stage (128 bytes of bf16)
 constexpr int kBStages = 4;        // stages in flight
 constexpr int kBStepThreads = 512;  // 16 warps: 4 TMEM lane quarters x 4 column groups
+constexpr int kBProducerWarps = 4; // warps of the step that copy the operand chunks
 constexpr int kBEvalInst = 8;      // instances per CTA of the evaluation kernel
 constexpr int kBEvalThreads = 256;
 constexpr int kBEvalIlvF32 = 2;    // interleaved sums per correlation in the evaluation's A^T r
