@@ -649,12 +649,12 @@ __device__ __forceinline__ void momentum(const MomEntry* mom, int ti, double tk,
 }  // namespace
 
 
-template <int PREC, int QW, int QT>
-__global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
+template <int PREC, int DW, int QW, int QT>
+__global__ void __launch_bounds__(32 * (1 + DW + QW), 1)
     k_iters(Params p, Buffers b, int slot0, int niter, int gap_last, int nstages, int cps, int idx_cap) {
   constexpr int DP = PREC == kX2 ? kX2 : kF32;
   constexpr int QP = PREC == kF32 ? kF32 : kX2;
-  constexpr int NW = kPassDot + QW;          // consumer warps
+  constexpr int NW = DW + QW;          // consumer warps
   constexpr int NCONS = 32 * NW;
   DevState* st = b.st;
   if (st->done) return;                      // fixed for the whole launch
@@ -678,8 +678,8 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
   float2* sG1 = sv + 3 * idx_cap;
   float2* sL = sv + 4 * idx_cap;
   float2* sU = sv + 5 * idx_cap;
-  __shared__ float2 s_dot[kPassDot];
-  __shared__ double s_eps[kPassDot];
+  __shared__ float2 s_dot[DW];
+  __shared__ double s_eps[DW];
   __shared__ double s_tn, s_tk, s_etag;   // t_{k+1} without restart, t_k, margin eta_g
   __shared__ float2 s_beta2[2];
   __shared__ int s_ti, s_err, s_ok;
@@ -804,7 +804,7 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
     consumer_sync<NCONS>();
     const double tn = s_tn;
 
-    if (warp <= kPassDot) {
+    if (warp <= DW) {
       // ------------------------------------------------------------ dot warps
       const int dw = warp - 1;
       const double eta_g = gap_iter ? s_etag : 0.0;
@@ -817,7 +817,7 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
       float2 dot = make_float2(0.f, 0.f);
       double epsm = 0.0;
       const int U = (cps % 2 == 0) ? 2 : 1;
-      for (int w = dw; w * U < nq; w += kPassDot) {
+      for (int w = dw; w * U < nq; w += DW) {
         const int q0 = w * U;
         const int ncol = min(U, nq - q0);
         const int g = q0 / cps;
@@ -885,7 +885,7 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
       }
     } else {
       // ------------------------------------------------------------ q warps
-      const int qw = warp - 1 - kPassDot;
+      const int qw = warp - 1 - DW;
       f32x2 qs[QT][2], qc[QT][2];
 #pragma unroll
       for (int t = 0; t < QT; ++t)
@@ -917,7 +917,7 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
     if (ct == 0) {
       float2 d = make_float2(0.f, 0.f);
       double e = 0.0;
-      for (int w = 0; w < kPassDot; ++w) {
+      for (int w = 0; w < DW; ++w) {
         d = df2_add(d, s_dot[w]);
         if (gap_iter) e = fmax(e, s_eps[w]);
       }
@@ -1183,12 +1183,77 @@ cudaError_t launch_pass(const Params& p, const Buffers& b, int slot, int precisi
   return cudaGetLastError();
 }
 
-template <int PREC, int QT>
-static cudaError_t iters_launch_t(const Params& p, const Buffers& b, int slot0, int niter, int gap_last, int grid,
-                                  int nstages, int cps, size_t sm, cudaStream_t s) {
+// Warp split of the persistent pass: DW dot warps (column pairs) and QW q warps (row
+// slices of the forward product, QT float4 chunks per lane).
+struct ItersShape {
+  int dw, qw, qt;
+};
+
+static int iters_qt(int m4, int qw) {
+  const int m4q = m4 / 4;
+  for (int qt = 1; qt <= kPassTmax; qt *= 2)
+    if (m4q <= 32 * qw * qt) return qt;
+  return 0;
+}
+
+// In mode MIXED the double-float forward product is the slower half of a column group, so
+// 16 q warps (one or two row chunks per lane) take it with 4 dot warps (measured, solve with
+// 300 iterations on 4000 x 20000: 76 against 86 us per iteration; 2000 x 10000: 0.917
+// against 0.924 ms per solve).  Where both products are double-float the dot warps are the
+// slower half and the even split stays (1.06 against 1.36 ms on 2000 x 10000).
+static ItersShape iters_shape(int precision, int m4) {
+  ItersShape sh{4, 16, 0};
+  sh.qt = iters_qt(m4, sh.qw);
+  if (precision == kMix && sh.qt >= 1 && sh.qt <= 2) return sh;
+  sh = ItersShape{8, 8, 0};
+  sh.qt = iters_qt(m4, sh.qw);
+  return sh;
+}
+
+template <int PREC, int DW, int QW, int QT>
+static const void* iters_fn() {
+  return reinterpret_cast<const void*>(k_iters<PREC, DW, QW, QT>);
+}
+
+// The kernel of a shape, or null for a shape without an instantiation.
+template <int PREC>
+static const void* iters_kernel(const ItersShape& sh) {
+  if (sh.dw == 8 && sh.qw == 8) {
+    switch (sh.qt) {
+      case 1: return iters_fn<PREC, 8, 8, 1>();
+      case 2: return iters_fn<PREC, 8, 8, 2>();
+      case 4: return iters_fn<PREC, 8, 8, 4>();
+      case 8: return iters_fn<PREC, 8, 8, 8>();
+    }
+  } else if (PREC == kMix && sh.dw == 4 && sh.qw == 16) {
+    switch (sh.qt) {
+      case 1: return iters_fn<kMix, 4, 16, 1>();
+      case 2: return iters_fn<kMix, 4, 16, 2>();
+    }
+  }
+  return nullptr;
+}
+
+static const void* iters_kernel_p(int precision, const ItersShape& sh) {
+  switch (precision) {
+    case kX2: return iters_kernel<kX2>(sh);
+    case kF32: return iters_kernel<kF32>(sh);
+    case kMix: return iters_kernel<kMix>(sh);
+    default: return nullptr;
+  }
+}
+
+cudaError_t launch_iters(const Params& p, const Buffers& b, int slot0, int niter, bool gap_last, int precision,
+                         int grid, int nstages, int cps, int qwarps, cudaStream_t s) {
+  const int idx_cap = (p.n + grid - 1) / grid;
+  const size_t sm = iters_smem_bytes(p.lda, p.m4, nstages, cps, idx_cap);
+  const ItersShape sh = iters_shape(precision, p.m4);
+  const void* fn = iters_kernel_p(precision, sh);
+  if (qwarps != 8 || !fn || niter < 1 || b.gbar == nullptr || grid > kMaxGridFlags) return cudaErrorInvalidValue;
+  int g = gap_last ? 1 : 0;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(32 * (1 + kPassDot + 8));
+  cfg.blockDim = dim3(32 * (1 + sh.dw + sh.qw));
   cfg.dynamicSmemBytes = sm;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -1196,62 +1261,29 @@ static cudaError_t iters_launch_t(const Params& p, const Buffers& b, int slot0, 
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_iters<PREC, 8, QT>, p, b, slot0, niter, gap_last, nstages, cps,
-                            (p.n + grid - 1) / grid);
+  Params pp = p;
+  Buffers bb = b;
+  void* args[] = {&pp, &bb, &slot0, &niter, &g, &nstages, &cps, const_cast<int*>(&idx_cap)};
+  return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
-template <int PREC>
-static cudaError_t iters_launch_p(int qt, const Params& p, const Buffers& b, int slot0, int niter, int gap_last,
-                                  int grid, int nstages, int cps, size_t sm, cudaStream_t s) {
-  switch (qt) {
-    case 1: return iters_launch_t<PREC, 1>(p, b, slot0, niter, gap_last, grid, nstages, cps, sm, s);
-    case 2: return iters_launch_t<PREC, 2>(p, b, slot0, niter, gap_last, grid, nstages, cps, sm, s);
-    case 4: return iters_launch_t<PREC, 4>(p, b, slot0, niter, gap_last, grid, nstages, cps, sm, s);
-    default: return iters_launch_t<PREC, 8>(p, b, slot0, niter, gap_last, grid, nstages, cps, sm, s);
-  }
-}
-
-cudaError_t launch_iters(const Params& p, const Buffers& b, int slot0, int niter, bool gap_last, int precision,
-                         int grid, int nstages, int cps, int qwarps, cudaStream_t s) {
-  const size_t sm = iters_smem_bytes(p.lda, p.m4, nstages, cps, (p.n + grid - 1) / grid);
-  const int qt = pass_qt(p.m4);
-  if (qwarps != 8 || qt == 0 || niter < 1 || b.gbar == nullptr || grid > kMaxGridFlags) return cudaErrorInvalidValue;
-  const int g = gap_last ? 1 : 0;
-  switch (precision) {
-    case kX2: return iters_launch_p<kX2>(qt, p, b, slot0, niter, g, grid, nstages, cps, sm, s);
-    case kF32: return iters_launch_p<kF32>(qt, p, b, slot0, niter, g, grid, nstages, cps, sm, s);
-    case kMix: return iters_launch_p<kMix>(qt, p, b, slot0, niter, g, grid, nstages, cps, sm, s);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-template <int PREC, int QT>
-static bool iters_fits(int bytes, int grid) {
-  const void* fn = reinterpret_cast<const void*>(k_iters<PREC, 8, QT>);
+static bool iters_fits(int precision, int bytes, int grid, int m4) {
+  const ItersShape sh = iters_shape(precision, m4);
+  const void* fn = iters_kernel_p(precision, sh);
+  if (!fn) return false;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) return false;
   int per_sm = 0, dev = 0, sms = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * (1 + kPassDot + 8), bytes) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * (1 + sh.dw + sh.qw), bytes) != cudaSuccess)
     return false;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
   return per_sm >= 1 && grid <= per_sm * sms;
 }
 
-template <int QT>
-static bool iters_fits_all(int bytes, int grid) {
-  return iters_fits<kX2, QT>(bytes, grid) && iters_fits<kF32, QT>(bytes, grid) && iters_fits<kMix, QT>(bytes, grid);
-}
-
 bool iters_configure(int lda, int m4, int nstages, int cps, int idx_cap, int grid) {
   if (nstages < 3 || grid > kMaxGridFlags) return false;
   const int bytes = (int)iters_smem_bytes(lda, m4, nstages, cps, idx_cap);
-  switch (pass_qt(m4)) {
-    case 1: return iters_fits_all<1>(bytes, grid);
-    case 2: return iters_fits_all<2>(bytes, grid);
-    case 4: return iters_fits_all<4>(bytes, grid);
-    case 8: return iters_fits_all<8>(bytes, grid);
-    default: return false;
-  }
+  return iters_fits(kX2, bytes, grid, m4) && iters_fits(kF32, bytes, grid, m4) && iters_fits(kMix, bytes, grid, m4);
 }
 
 cudaError_t launch_resid(const Params& p, const Buffers& b, int slot, int nparts, cudaStream_t s) {
