@@ -339,7 +339,7 @@ def hbm_leg(dev, stream, flush, steps, iters=1500):
     """The L2-busting matvec case: |N(0,1)| NNLS 4000 x 20000 (A = 320 MB > 129 MB of L2),
     x0 5% |N(0,1)|, noise N(0,1), seed 0.  A fixed count of iterations (the solve is cut at
     `iters`; screening every 10), screened and unscreened alternating, and the roofline of the
-    persistent pass on it (every read of A_S comes from HBM)."""
+    persistent pass on it (every read of A_S comes from HBM), in the headline's precision mode."""
     import torch
     from paper_2202_07258_gb300 import Solver
     p = W.nnls_abs_gaussian(4000, 20000, 0.05, 1.0, 0)
@@ -347,10 +347,10 @@ def hbm_leg(dev, stream, flush, steps, iters=1500):
         solver = Solver(torch.from_numpy(p.A).to(dev), p.l, p.u, stream=stream.cuda_stream)
     y = torch.from_numpy(p.y).to(dev)
     runs = timed_solves(solver, y, flush, stream, steps, 1,
-                        {"screened": dict(screening=True, max_iter=iters),
-                         "unscreened": dict(screening=False, max_iter=iters)})
+                        {"screened": dict(screening=True, max_iter=iters, precision=HEAD_PRECISION),
+                         "unscreened": dict(screening=False, max_iter=iters, precision=HEAD_PRECISION)})
     out = {"workload": "nnls_abs_gaussian_4000x20000 (A 320 MB, |N(0,1)| unit columns, x0 5% |N(0,1)|, "
-                       f"noise N(0,1); {iters} iterations per solve)"}
+                       f"noise N(0,1); {iters} iterations per solve)", "precision": HEAD_PRECISION}
     for name, (times, infos) in runs.items():
         inf = infos[-1]
         out[name] = {"ms_per_solve": sum(times) / len(times), "iters": inf["iters"],
@@ -359,7 +359,7 @@ def hbm_leg(dev, stream, flush, steps, iters=1500):
     out["speedup"] = out["unscreened"]["ms_per_solve"] / out["screened"]["ms_per_solve"]
     from paper_2202_07258_gb300 import make_opts
     x, sc, info, st = solver.solve(y, opts=make_opts(tol=TOL, screen_every=K_SCREEN, max_iter=iters, profile=True,
-                                                     screening=False))
+                                                     screening=False, precision=HEAD_PRECISION))
     out["roofline_unscreened"] = roofline_from_info(info, 4000, traffic_key="k_iters@nnls_abs_4000x20000")
     solver.close()
     return out
@@ -474,7 +474,8 @@ def ncu_region(args):
         p = W.nnls_abs_gaussian(4000, 20000, 0.05, 1.0, 0)
         s = Solver(torch.from_numpy(p.A).to(dev), p.l, p.u)
         y = torch.from_numpy(p.y).to(dev)
-        opts = make_opts(tol=0.0, screen_every=K_SCREEN, max_iter=20, screening=False, profile=True)
+        opts = make_opts(tol=0.0, screen_every=K_SCREEN, max_iter=20, screening=False, profile=True,
+                         precision=HEAD_PRECISION)
         run = lambda: s.solve(y, opts=opts)
     else:
         c = BATCH
