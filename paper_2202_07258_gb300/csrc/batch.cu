@@ -91,10 +91,12 @@ __device__ __forceinline__ float gap_term_up(float du, float dl, float gt, float
   return fmaxf(h_hi, h_lo) * (1.f + 4.f * kUf) + 1e-30f;
 }
 
-// x_{k+1} = clip(x_k + b (x_k - x_{k-1}) + g_v / L, l, u) with double-float iterates.
-__device__ __forceinline__ float2 fista_step(float2 xk, float2 xp, float gv, float be, float2 invL2, float2 l2,
+// x_{k+1} = clip(x_k + b dk + g_v / L, l, u) with double-float iterates, dk = x_k - x_{k-1}
+// (the evaluation passes it exactly; the tensor-core step passes bf16(x_k - x_{k-1}), the
+// operand its Gram product already used).
+__device__ __forceinline__ float2 fista_step(float2 xk, float2 dk, float gv, float be, float2 invL2, float2 l2,
                                              float2 u2) {
-  const float2 v = df2_add(xk, df2_mul(df2_sub(xk, xp), make_float2(be, 0.f)));
+  const float2 v = df2_add(xk, df2_mul(dk, make_float2(be, 0.f)));
   float2 xn = df2_add(v, df2_mul(make_float2(gv, 0.f), invL2));
   if (df2_lt(xn, l2)) xn = l2;
   if (df2_lt(u2, xn)) xn = u2;
@@ -210,20 +212,26 @@ cudaError_t launch_binit(const BParams& p, const BBuffers& b, cudaStream_t s) {
 // ------------------------------------------------------------------ tensor-core step
 // Grid (npad / 128 coordinate tiles, ceil(B / 128) instance tiles), 512 threads, one CTA per
 // SM (128 KB of stages).  Operand K chunks of 64 stream through kBStages shared-memory
-// stages, synchronised by mbarriers only: warps 0-3 copy a chunk with 16-byte asynchronous
-// copies into a free stage, wait for their own copies, fence them to the async proxy and
-// arrive on the stage's full barrier; one thread of warp 4 waits for it, issues four
-// 128x128x16 MMAs and commits them to the stage's empty barrier, which frees the stage for
-// the chunk kBStages later, and after the last chunk to the done barrier.  Meanwhile the
-// other warps load their first epilogue operands; then all 16 read the accumulator rows of
-// their 32 coordinates from TMEM.
-__global__ void __launch_bounds__(kBStepThreads, 1) k_bstep(BParams p, BBuffers b, int jrel) {
+// stages in the 128-byte swizzled K-major layout, synchronised by mbarriers only.  Into a
+// free stage thread 0 issues one tensor copy of the 64 x 128 box of H~ (16 KB of
+// transaction bytes on the stage's full barrier) and warps 0-3 copy the D rows of the tile's
+// 128 instances (gathered by the active list) with 16-byte cp.async into their swizzled
+// places, wait for their own copies, fence them to the async proxy and arrive on the full
+// barrier; lane 0 of warp 4 waits for it, issues four 128x128x16 MMAs and commits them to
+// the stage's empty barrier, which frees the stage for the chunk kBStages later, and after
+// the last chunk to the done barrier.  Meanwhile the other warps load their first epilogue
+// operands; then all 16 read the accumulator rows of their 32 coordinates from TMEM.
+// (Measured on the 4096 x (224 x 512) batch: cp.async moved each operand at ~17 bytes per
+// clock per SM; D as 32 four-row tensor gathers per chunk from one thread was slower still.)
+__global__ void __launch_bounds__(kBStepThreads, 1) k_bstep(const __grid_constant__ BParams p, BBuffers b, int jrel) {
   BState* st = b.st;
   if (st->done) return;
   const int n_act = st->n_act;
   const int mt = blockIdx.x, nt = blockIdx.y;
   if (nt * kBTile >= n_act) return;
-  extern __shared__ __align__(1024) unsigned char smem[];
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // the swizzle atoms must start on 1024-byte boundaries (the launch adds 1 KB of slack)
+  unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   __shared__ __align__(8) uint64_t full[kBStages], empty[kBStages], done;
   __shared__ uint32_t s_tmem;
   __shared__ int s_inst[kBTile];
@@ -259,7 +267,7 @@ __global__ void __launch_bounds__(kBStepThreads, 1) k_bstep(BParams p, BBuffers 
   if (warp == 0) tmem_alloc(&s_tmem, kBTile);
   if (tid == 0) {
     for (int q = 0; q < kBStages; ++q) {
-      mbar_init(&full[q], kBProducerWarps * 32);
+      mbar_init(&full[q], kBCopyWarps * 32 + 1);  // the copy threads and the tensor copy's expect-tx
       mbar_init(&empty[q], 1);
     }
     mbar_init(&done, 1);
@@ -272,25 +280,26 @@ __global__ void __launch_bounds__(kBStepThreads, 1) k_bstep(BParams p, BBuffers 
 
   const int nch = p.npad / kBChunk;
   bool ok = true;
-  if (warp < kBProducerWarps) {
+  if (warp < kBCopyWarps) {
     // producers: chunk c into stage c % kBStages once the MMAs of chunk c - kBStages are done
-    const __nv_bfloat16* Hrow = p.H + (size_t)mt * kBTile * p.npad;
     const __nv_bfloat16* Dsrc = b.D[s];
-    constexpr int NPT = kBProducerWarps * 32;
+    constexpr int NPT = kBCopyWarps * 32;
     auto load_chunk = [&](int c) {
-      unsigned char* sa = smem + (size_t)(c % kBStages) * kStageBytes;
+      const int st_ = c % kBStages;
+      unsigned char* sa = smem + (size_t)st_ * kStageBytes;
       unsigned char* sb = sa + kStageBytes / 2;
       const int kofs = c * kBChunk;
+      if (tid == 0) {
+        mbar_arrive_expect_tx(&full[st_], (uint32_t)(kStageBytes / 2));
+        tma_load_2d(sa, &p.tmH, kofs, mt * kBTile, &full[st_]);
+      }
 #pragma unroll
       for (int t = 0; t < (kBTile * 8) / NPT; ++t) {
         const int q = tid + t * NPT;
-        const int r = ((q >> 6) << 3) | (q & 7);
-        const int kc = (q >> 3) & 7;
-        const uint32_t off = core_offset(r, kc);
-        cp_async16(sa + off, Hrow + (size_t)r * p.npad + kofs + kc * 8);
+        const int r = q >> 3, kc = q & 7;   // row r, 16-byte chunk kc of its 128-byte K segment
         const int inst = s_inst[r];
         const int row = inst >= 0 ? inst : p.B;  // row B of D is zero
-        cp_async16(sb + off, Dsrc + (size_t)row * p.npad + kofs + kc * 8);
+        cp_async16(sb + r * 128 + ((kc ^ (r & 7)) << 4), Dsrc + (size_t)row * p.npad + kofs + kc * 8);
       }
       cp_async_commit();
     };
@@ -312,7 +321,7 @@ __global__ void __launch_bounds__(kBStepThreads, 1) k_bstep(BParams p, BBuffers 
       fence_proxy_async_smem();
       mbar_arrive(&full[c % kBStages]);
     }
-  } else if (warp == kBProducerWarps) {
+  } else if (warp == kBCopyWarps) {
     // MMA issuer: the warp waits for each stage, lane 0 issues and commits
     const uint32_t idesc = umma_idesc_bf16(kBTile, kBTile);
     for (int c = 0; c < nch; ++c) {
@@ -323,7 +332,8 @@ __global__ void __launch_bounds__(kBStepThreads, 1) k_bstep(BParams p, BBuffers 
         const uint32_t sb = sa + kStageBytes / 2;
 #pragma unroll
         for (int kk = 0; kk < kBChunk / 16; ++kk)
-          umma_bf16(tmem, umma_smem_desc(sa + kk * 256), umma_smem_desc(sb + kk * 256), idesc, c > 0 || kk > 0);
+          umma_bf16(tmem, umma_smem_desc_sw128(sa + kk * 32), umma_smem_desc_sw128(sb + kk * 32), idesc,
+                    c > 0 || kk > 0);
         umma_commit(&empty[c % kBStages]);
       }
       __syncwarp();
@@ -343,13 +353,15 @@ __global__ void __launch_bounds__(kBStepThreads, 1) k_bstep(BParams p, BBuffers 
   const float* __restrict__ Gp = b.G[s ^ 1];
   float* Gc = b.G[s];
   const float2* __restrict__ Xc = b.X[s];
-  float2* Xn = b.X[s ^ 1];
+  const __nv_bfloat16* __restrict__ Dk = b.D[s];   // bf16(x_k - x_{k-1}): the momentum's difference
+  float2* Xn = b.X[s ^ 1];                         // x_{k+1} replaces x_{k-1}, which is not read
   __nv_bfloat16* Dn = b.D[s ^ 1];
   static_assert(kBTile / (kBStepThreads / 128) == 32, "one 32-column group of instances per warp");
   const int c0 = (warp >> 2) * 32;
   const bool have = s_inst[c0] >= 0;  // active instances are packed at the front of the tile
   float gp[8];
-  float2 xk[8], xp[8];
+  float2 xk[8];
+  __nv_bfloat16 dk[8];
   uint8_t fl[8];
   auto load8 = [&](int c8) {  // eight instances' operands in flight
 #pragma unroll
@@ -357,13 +369,13 @@ __global__ void __launch_bounds__(kBStepThreads, 1) k_bstep(BParams p, BBuffers 
       const int inst = s_inst[c0 + c8 + cc];
       gp[cc] = 0.f;
       xk[cc] = make_float2(0.f, 0.f);
-      xp[cc] = xk[cc];
+      dk[cc] = __float2bfloat16_rn(0.f);
       fl[cc] = 1;
       if (inst >= 0 && jv) {
         const size_t o = (size_t)inst * p.npad + jg;
         gp[cc] = Gp[o];
         xk[cc] = Xc[o];
-        xp[cc] = Xn[o];
+        dk[cc] = Dk[o];
         fl[cc] = b.flags[o];
       }
     }
@@ -391,7 +403,7 @@ __global__ void __launch_bounds__(kBStepThreads, 1) k_bstep(BParams p, BBuffers 
           if (!fl[cc]) {
             const float be = s_beta[c0 + c8 + cc];
             const float gv = fmaf(be, gk - gp[cc], gk);  // (1 + b) g_k - b g_{k-1}
-            xn = fista_step(xk[cc], xp[cc], gv, be, invL2, lj, uj);
+            xn = fista_step(xk[cc], make_float2(__bfloat162float(dk[cc]), 0.f), gv, be, invL2, lj, uj);
             const float2 d = df2_sub(xn, xk[cc]);
             dx = d.x + d.y;
             dv[c8 + cc] = gv * dx;
@@ -427,7 +439,7 @@ __global__ void __launch_bounds__(kBStepThreads, 1) k_bstep(BParams p, BBuffers 
   if (tid == 0 && mt == 0 && nt == 0) st->sum_step += (double)n_act;
 }
 
-size_t bstep_smem_bytes() { return (size_t)kBStages * kStageBytes; }
+size_t bstep_smem_bytes() { return (size_t)kBStages * kStageBytes + 1024; }
 
 cudaError_t launch_bstep(const BParams& p, const BBuffers& b, int j, cudaStream_t s) {
   dim3 grid(p.npad / kBTile, (p.B + kBTile - 1) / kBTile);
@@ -867,7 +879,7 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
         }
         const float gk = g2.x;
         const float gv = fmaf(be, gk - gp, gk);
-        const float2 xn = fista_step(xk, xp, gv, be, invL2, p.l2[j], p.u2[j]);
+        const float2 xn = fista_step(xk, df2_sub(xk, xp), gv, be, invL2, p.l2[j], p.u2[j]);
         const float2 d = df2_sub(xn, xk);
         const float dx = d.x + d.y;
         Gc[o] = gk;

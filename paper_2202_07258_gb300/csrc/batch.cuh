@@ -20,6 +20,7 @@
 // correlation.  The certificates (gap, radius, test) only ever use evaluation quantities.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -30,7 +31,7 @@ constexpr int kBTile = 128;        // coordinates per M tile = instances per N t
 constexpr int kBChunk = 64;        // K elements per shared-memory stage (128 bytes of bf16)
 constexpr int kBStages = 4;        // stages in flight
 constexpr int kBStepThreads = 512;  // 16 warps: 4 TMEM lane quarters x 4 column groups
-constexpr int kBProducerWarps = 4; // warps of the step that copy the operand chunks
+constexpr int kBCopyWarps = 4;     // warps of the step that copy the D rows of a chunk
 constexpr int kBEvalInst = 8;      // instances per CTA of the evaluation kernel
 constexpr int kBEvalThreads = 256;
 constexpr int kBEvalIlvF32 = 2;    // interleaved sums per correlation in the evaluation's A^T r
@@ -83,6 +84,8 @@ struct BParams {
   int screening;
   int restart;
   int K;
+  // tensor map of the step's operand H~ (bf16, 128-byte swizzle, 64 x 128 box)
+  CUtensorMap tmH;
 };
 
 struct BBuffers {

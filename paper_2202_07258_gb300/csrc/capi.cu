@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "backward.cuh"
 #include "batch.cuh"
 #include "ragged.cuh"
@@ -98,6 +100,7 @@ struct bvls_handle {
   int b_cap = 0;
   float *b_nrmf = nullptr, *b_wf = nullptr;
   BBuffers bb{};
+  CUtensorMap b_tmH{};  // tensor map of the step's operand H~
   float* bY = nullptr;
   double* bX0 = nullptr;
   std::vector<void*> b_allocs;
@@ -864,6 +867,28 @@ bvls_status balloc(bvls_handle* h, T** p, size_t count) {
   return BVLS_OK;
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point: a 2D bf16 tensor of `rows`
+// rows of `cols` contiguous elements, 128-byte swizzle, box_cols x box_rows.
+bool encode_bf16_2d(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint32_t box_cols,
+                    uint32_t box_rows) {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return static_cast<PFN_cuTensorMapEncodeTiled_v12000>(nullptr);
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {cols, rows};
+  const cuuint64_t strides[1] = {cols * 2};
+  const cuuint32_t box[2] = {box_cols, box_rows};
+  const cuuint32_t es[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Gram matrix and the workspace for B instances.
 bvls_status batch_prepare(bvls_handle* h, int B) {
   const int n = h->n;
@@ -872,6 +897,8 @@ bvls_status batch_prepare(bvls_handle* h, int B) {
     CK(batch_configure(h->m, h->b_npad));
     TRY(dalloc(h, &h->bH, (size_t)h->b_npad * h->b_npad));
     CK(launch_bgram(h->A, h->lda, h->m, n, h->b_npad, h->bH, h->s));
+    if (!encode_bf16_2d(&h->b_tmH, h->bH, (uint64_t)h->b_npad, (uint64_t)h->b_npad, kBChunk, kBTile))
+      return set_err(BVLS_ECUDA, "tensor map of the Gram matrix could not be encoded");
     std::vector<double> nrm(n), w(n);
     CK(cudaMemcpyAsync(nrm.data(), h->nrm, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
     CK(cudaMemcpyAsync(w.data(), h->w, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
@@ -970,6 +997,7 @@ BParams make_bparams(bvls_handle* h, const bvls_opts& o, int max_iter, int B) {
   p.screening = o.screening;
   p.restart = o.restart;
   p.K = o.screen_every;
+  p.tmH = h->b_tmH;
   return p;
 }
 

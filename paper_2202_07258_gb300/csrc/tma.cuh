@@ -78,4 +78,15 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
+// 2D tiled tensor copy (box of the tensor map at (c0, c1): c0 along the contiguous dimension,
+// whose byte offset must be a multiple of 16) into this CTA's shared memory; completion as
+// transaction bytes on `bar`.  `map` is the address of a __grid_constant__ parameter.
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* map, int c0, int c1, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      : "memory");
+}
+
 }  // namespace bvls

@@ -34,6 +34,21 @@ __device__ __forceinline__ uint64_t umma_smem_desc(uint32_t saddr) {
   return d;
 }
 
+// Descriptor of a K-major operand in the 128-byte swizzled layout written by a tensor copy
+// with CU_TENSOR_MAP_SWIZZLE_128B: rows of 64 bf16 (128 bytes), 8-row atoms of 1024 bytes
+// (the stride byte offset), 16-byte chunks XOR-permuted by the row within the atom; the atom
+// must start on a 1024-byte boundary.  The K steps of 16 elements inside the row advance the
+// start address by 32 bytes (the swizzle applies to the computed addresses).
+__device__ __forceinline__ uint64_t umma_smem_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;                 // leading byte offset: unused for swizzled K-major
+  d |= (uint64_t)(1024u >> 4) << 32;      // stride byte offset: 8 rows x 128 bytes
+  d |= (uint64_t)1 << 46;                 // descriptor version 1
+  d |= (uint64_t)2 << 61;                 // layout: 128-byte swizzle
+  return d;
+}
+
 // Instruction descriptor of kind::f16 with bf16 A and B, f32 accumulator, both K-major.
 __host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
