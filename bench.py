@@ -418,6 +418,18 @@ def batched_leg(dev, stream, flush, steps, warmup=1):
                        "avg_launch_us": 1e6 * step_s / max(1, info["step_launches"]),
                        "eval_avg_launch_us": 1e3 * info["eval_ms"] / max(1, info["eval_launches"]),
                        "step_share": info["step_ms"] / max(1e-9, info["step_ms"] + info["eval_ms"])}
+    # the same kernel against HBM: per coordinate and instance it reads g, x (double-float),
+    # bf16(x_k - x_{k-1}) and the flag and writes g, x, bf16(x_{k+1} - x_k) (29 bytes); H~ once
+    npad = (c["n"] + 127) // 128 * 128
+    state_bytes = 29.0 * c["n"] * info["sum_step"] + 2.0 * npad * npad * info["step_launches"]
+    hbm_peak, hbm_src = 6800.0, "fallback"
+    if os.path.exists(peaks_path):
+        hbm_peak, hbm_src = float(json.load(open(peaks_path))["hbm_gbs"]), "measured"
+    ach = state_bytes / step_s / 1e9 if step_s > 0 else None
+    out["roofline_hbm"] = {"bound": "hbm", "kernel": "k_bstep (iterate state of the fused step)", "achieved": ach,
+                           "peak": hbm_peak, "peak_source": hbm_src, "unit": "GB/s",
+                           "frac": ach / hbm_peak if ach else None,
+                           "algorithmic_bytes_per_launch": state_bytes / max(1, info["step_launches"])}
     return out
 
 

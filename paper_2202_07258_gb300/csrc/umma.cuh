@@ -1,13 +1,13 @@
 // Inline-PTX helpers for the 5th-generation tensor cores (tcgen05) of sm_100-class parts:
 // tensor-memory (TMEM) allocation, shared-memory matrix descriptors, the BF16 MMA with an
 // FP32 accumulator in TMEM, commit to an mbarrier, and TMEM -> register loads; plus the
-// 16-byte asynchronous global -> shared copies that stage the operands.
+// 16-byte asynchronous global -> shared copies that stage operand rows.
 //
-// Operand layout (both operands K-major, no swizzle): a tile of R rows x 64 bf16 is a grid of
-// 8 x 8 "core matrices" (8 rows x 16 bytes, 128 contiguous bytes each).  Core matrices that
-// are adjacent along K are 128 bytes apart (the leading byte offset), groups of 8 rows are
-// 1024 bytes apart (the stride byte offset):
-//     byte offset of element (r, k) = (r / 8) * 1024 + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2.
+// Operand layout (both operands K-major, 128-byte swizzle): a tile of R rows x 64 bf16 holds
+// each row in 128 contiguous bytes; 8-row atoms of 1024 bytes start on 1024-byte boundaries,
+// and inside an atom the 16-byte chunk kc of row r sits at chunk position kc ^ (r % 8):
+//     byte offset of element (r, k) = r * 128 + (((k / 8) ^ (r % 8)) * 16) + (k % 8) * 2.
+// A 2D tensor copy with CU_TENSOR_MAP_SWIZZLE_128B writes exactly this layout.
 #pragma once
 
 #include <stdint.h>
@@ -15,24 +15,6 @@
 #include "tma.cuh"
 
 namespace bvls {
-
-constexpr uint32_t kCoreLBO = 128;    // K-adjacent core matrices
-constexpr uint32_t kCoreSBO = 1024;   // 8-row groups (64 bf16 of K per row group)
-
-__device__ __forceinline__ uint32_t core_offset(int r, int kc) {  // kc: 16-byte chunk along K
-  return (uint32_t)(r >> 3) * kCoreSBO + (uint32_t)kc * kCoreLBO + (uint32_t)(r & 7) * 16u;
-}
-
-// Shared-memory matrix descriptor: start address, leading and stride byte offsets (all in
-// units of 16 bytes), descriptor version 1, base offset 0, no swizzle.
-__device__ __forceinline__ uint64_t umma_smem_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((kCoreLBO >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((kCoreSBO >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;
-  return d;
-}
 
 // Descriptor of a K-major operand in the 128-byte swizzled layout written by a tensor copy
 // with CU_TENSOR_MAP_SWIZZLE_128B: rows of 64 bf16 (128 bytes), 8-row atoms of 1024 bytes
