@@ -463,7 +463,7 @@ def e2e_leg(p, steps, stream):
     d2h = 8 * n + n
     return {"value": 1.0 / statistics.median(times), "unit": "instances/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "includes": "bvls_setup from host A (copy, column norms, dual "
-            "direction search, power iteration) + bvls_solve from host y to host x"}
+            "direction search, Lanczos step constant) + bvls_solve from host y to host x"}
 
 
 def ncu_region(args):

@@ -168,7 +168,8 @@ BVLS_API void bvls_default_opts(bvls_opts* opts);
  *   stream  a cudaStream_t (0 = legacy default stream).
  *   out     receives the handle.
  * Setup computes the column norms ||a_j||_2 (used by Eq. (safe_rule)), w = A^T t and the
- * step constant L (1.05 x a 100-step power-iteration estimate of ||A||_2^2).
+ * step constant L (1.05 x the largest Ritz value of 32 Lanczos steps on A^T A, an estimate of
+ * ||A||_2^2 from below; 100 power steps where the one-launch form does not fit).
  * Limits: 1 <= m <= 24576 (the residual is staged in shared memory), 1 <= n < 2^31,
  * lda*n*4 bytes addressable.  Errors: EINVAL, ENOTSUP, ENOMEM, ECUDA, ENONFINITE (A).
  */
@@ -359,7 +360,7 @@ BVLS_API bvls_status bvls_solve_ragged(int B, const bvls_problem* probs, const b
  * problems get BVLS_ENOTSUP with the size in bvls_last_error() (use bvls_setup then).
  * The translation direction for columns with u_j = +inf is t = -1 when it is interior,
  * else theta = 0 (bvls_setup also tries further candidates).  The step constant comes from
- * opts->lipschitz when > 0, else from the same power iteration as bvls_setup.
+ * opts->lipschitz when > 0, else from 1.05 x a 100-step power-iteration estimate of ||A||_2^2.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
  * with that device current; make that first call before any stream capture.  Every call
  * reuses the same array, which keeps the previous call's contents (each call clears what

@@ -396,6 +396,37 @@ const char* bvls_last_error(void) { return g_err.c_str(); }
 
 void bvls_destroy(bvls_handle* h) { free_handle(h); }
 
+// Largest eigenvalue of the symmetric tridiagonal matrix with diagonal alpha and off-diagonal
+// beta, by bisection on the Sturm count (the number of eigenvalues below x is the number of
+// negative pivots of the LDL^T factorisation of T - x I; Golub & Van Loan, Section 8.4.1).
+double tridiag_max_eig(const std::vector<double>& alpha, const std::vector<double>& beta) {
+  const int K = (int)alpha.size();
+  if (K == 0) return 0.0;
+  double lo = 0.0, hi = 0.0;  // Gershgorin bounds
+  for (int i = 0; i < K; ++i) {
+    const double r = (i > 0 ? std::fabs(beta[i - 1]) : 0.0) + (i + 1 < K ? std::fabs(beta[i]) : 0.0);
+    lo = std::min(lo, alpha[i] - r);
+    hi = std::max(hi, alpha[i] + r);
+  }
+  auto below = [&](double x) {  // eigenvalues < x
+    int cnt = 0;
+    double d = 1.0;
+    for (int i = 0; i < K; ++i) {
+      const double b2 = i > 0 ? beta[i - 1] * beta[i - 1] : 0.0;
+      d = alpha[i] - x - (i > 0 ? b2 / d : 0.0);
+      if (d == 0.0) d = -1e-300;
+      if (d < 0.0) ++cnt;
+    }
+    return cnt;
+  };
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(1.0, std::fabs(hi)); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (below(mid) >= K) hi = mid;   // every eigenvalue is below mid
+    else lo = mid;
+  }
+  return hi;
+}
+
 static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const double* l,
                               const double* u, const double* t) {
   const int m = h->m, n = h->n;
@@ -517,7 +548,9 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
     }
   }
 
-  // Step constant: power iteration on A^T A (one unnormalised warm-up step is discarded).
+  // Step constant: L = 1.05 x the largest eigenvalue of A^T A, estimated by K Lanczos steps
+  // (one cooperative launch) or, where that launch does not fit, by 100 power steps (one
+  // unnormalised warm-up step discarded).
   {
     float *v = nullptr, *q = nullptr, *v2 = nullptr;
     double* scal = nullptr;
@@ -527,29 +560,37 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
     TRY(dalloc(h, &scal, 2));
     CK(cudaMemsetAsync(scal, 0, 2 * sizeof(double), h->s));
     CK(launch_power_init(v, n, h->s));
-    // one cooperative launch for all 101 steps when it fits, else one launch per product
     bool done = false;
     {
+      const int K = std::min(kLanczosSteps, n);
       float *part = nullptr, *qc = nullptr;
-      double *wn2 = nullptr, *qn2 = nullptr;
+      double *wn2 = nullptr, *qn2 = nullptr, *ab = nullptr;
       unsigned* gb = nullptr;
       TRY(dalloc(h, &part, (size_t)h->num_sms * h->lda));
       TRY(dalloc(h, &qc, h->lda));
       TRY(dalloc(h, &wn2, h->num_sms));
       TRY(dalloc(h, &qn2, h->lda / 32));
+      TRY(dalloc(h, &ab, 2 * (size_t)K + 2));
       TRY(dalloc(h, &gb, 2));
       CK(cudaMemsetAsync(gb, 0, 2 * sizeof(unsigned), h->s));
-      const cudaError_t e = launch_power_coop(h->A, h->lda, m, n, v, part, qc, wn2, qn2, scal, gb, 101,
-                                              h->num_sms, h->s);
+      CK(cudaMemsetAsync(ab, 0, sizeof(double) * (2 * (size_t)K + 2), h->s));
+      const cudaError_t e = launch_lanczos_coop(h->A, h->lda, m, n, v, part, qc, wn2, qn2, ab, scal, gb, K,
+                                                h->num_sms, h->s);
       if (e == cudaSuccess) {
         double sc[2] = {0.0, 0.0};
+        std::vector<double> hab(2 * (size_t)K + 2);
         CK(cudaMemcpyAsync(sc, scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+        CK(cudaMemcpyAsync(hab.data(), ab, sizeof(double) * hab.size(), cudaMemcpyDeviceToHost, h->s));
         CK(cudaStreamSynchronize(h->s));
         if (sc[1] >= 0.0) {
-          h->L = sc[0] > 0.0 ? 1.05 * sc[0] : 1.0;
+          std::vector<double> alpha(K), beta(K > 1 ? K - 1 : 0);
+          for (int i = 0; i < K; ++i) alpha[i] = hab[2 * (i + 1)];
+          for (int i = 0; i + 1 < K; ++i) beta[i] = hab[2 * (i + 1) + 1];
+          const double lam = tridiag_max_eig(alpha, beta);
+          h->L = lam > 0.0 ? 1.05 * lam : 1.0;
           done = true;
         } else {
-          return set_err(BVLS_ETIMEOUT, "a device-side wait of the power iteration exceeded its bound");
+          return set_err(BVLS_ETIMEOUT, "a device-side wait of the Lanczos steps exceeded its bound");
         }
       } else if (e != cudaErrorNotSupported) {
         CK(e);

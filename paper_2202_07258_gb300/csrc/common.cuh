@@ -26,6 +26,7 @@ constexpr int kRedThreads = 256;  // blocks of the O(|A|) epilogue kernels
 constexpr int kCompactThreads = 1024;
 constexpr int kMaxRows = 24576;   // r is staged in shared memory: 8 bytes per row
 constexpr int kPassDot = 8;       // dot warps of the fused pass
+constexpr int kLanczosSteps = 32; // Lanczos steps of the setup's step-constant estimate
 constexpr int kPassTmax = 8;      // float4 row chunks owned by one lane of a q warp
 constexpr int kPassMaxStages = 32;
 constexpr int kMaxGridFlags = 1024;  // grid barrier words of the persistent pass
@@ -367,13 +368,13 @@ cudaError_t launch_row_sums(const float* A, int lda, int m, int n, double* part,
 cudaError_t launch_power_step(const float* A, int lda, int m, int n, float* v, float* q, float* v2,
                               double* scal, cudaStream_t s);
 cudaError_t launch_power_init(float* v, int n, cudaStream_t s);
-// All power steps in one cooperative launch (one CTA per SM, lda <= 8192): `steps` steps
-// v <- A^T A v / ||A^T A v|| from v (unit or not); scal[0] = the largest ||A v||^2 over the
-// steps after the first.  gb: two zeroed words (grid barrier); part: grid x lda floats;
-// q: lda floats; wn2: grid doubles; qn2: lda / 32 doubles.  Returns cudaErrorNotSupported
-// when the launch shape does not fit.
-cudaError_t launch_power_coop(const float* A, int lda, int m, int n, float* v, float* part, float* q,
-                              double* wn2, double* qn2, double* scal, unsigned* gb, int steps, int grid,
-                              cudaStream_t s);
+// K Lanczos steps on A^T A from v0 (any nonzero vector) in one cooperative launch (one CTA
+// per SM, lda <= 8192): ab[2 i] = alpha_i and ab[2 i + 1] = beta_i for i = 1..K (2 K + 2
+// doubles); scal[1] = -1 if a grid-barrier wait gave up.  gb: two zeroed words (grid
+// barrier); part: grid x lda floats; q: lda floats; wn2: grid doubles; qn2: lda / 32
+// doubles.  Returns cudaErrorNotSupported when the launch shape does not fit.
+cudaError_t launch_lanczos_coop(const float* A, int lda, int m, int n, const float* v0, float* part, float* q,
+                                double* wn2, double* qn2, double* ab, double* scal, unsigned* gb, int K, int grid,
+                                cudaStream_t s);
 
 }  // namespace bvls

@@ -179,34 +179,42 @@ cudaError_t launch_power_step(const float* A, int lda, int m, int n, float* v, f
 }
 
 
-// ---------------------------------------------------------------- power iteration, one launch
-// One CTA per SM owns a contiguous range of columns and keeps their v_j in shared memory.
-// A step has two phases, each ended by a grid barrier:
-//   columns  w_j = a_j^T q for the CTA's columns (warp per column, q in shared memory) and
-//            the CTA's partial of ||w||^2; then the CTA's partial of A w over the same
-//            columns (threads over rows, eight column loads in flight);
-//   rows     every CTA sums the ||w||^2 partials in the same order (s = 1 / ||w||), so
-//            v = s w and q = A v = s (sum of the partials), formed in 32-row slices over the
-//            CTAs with the slice partials of ||q||^2 = ||A v||^2, the Rayleigh quotient of
-//            the unit v.
-// The first step starts from v (not normalised) instead of a w, and its quotient is not
-// counted.  float32 products, float64 norms.
+// ---------------------------------------------------------------- Lanczos on A^T A, one launch
+// The step constant needs the largest eigenvalue of M = A^T A.  Lanczos (Golub & Van Loan,
+// Matrix Computations, Algorithm 10.1.1) builds the tridiagonal T_K = tridiag(beta; alpha;
+// beta) of M on the Krylov space of the start vector; the largest eigenvalue of T_K is a
+// Rayleigh quotient of M, so it never exceeds lambda_max(M), and it converges much faster
+// in K than the power method's quotient.  One CTA per SM owns a contiguous range of
+// columns and keeps its parts of v_k, v_{k-1} and w in shared memory.  Iteration it has two
+// phases, each ended by a grid barrier:
+//   columns  for it > 0: u = A^T q_it (q_it = A v_it in shared memory; warp per column),
+//            alpha_it = ||q_it||^2 = v_it^T M v_it, w = u - alpha_it v_it - beta_{it-1} v_{it-1};
+//            at it = 0 w is the start vector.  Then the CTA's partial of ||w||^2 and of A w
+//            over its columns (threads over rows, eight column loads in flight);
+//   rows     every CTA sums the ||w||^2 partials in the same order: beta_it = ||w||,
+//            v_{it+1} = w / beta_it, q_{it+1} = A v_{it+1} = (sum of the partials) / beta_it,
+//            formed in 32-row slices over the CTAs with the slice partials of ||q||^2.
+// float32 vectors and products, float64 reductions; ab[2 i] = alpha_i and ab[2 i + 1] =
+// beta_i (i = 1..K) are written for the host, which bounds the largest eigenvalue of T_K.
+// No reorthogonalisation: the lost orthogonality only adds copies of converged Ritz values.
 constexpr int kPowThreads = 512;
 constexpr int kPowChunks = 4;   // float4 row chunks per thread: lda <= 4 * 4 * 512 = 8192
 
 __global__ void __launch_bounds__(kPowThreads, 1)
-    k_power_coop(const float* __restrict__ A, int lda, int m, int n, float* v, float* part, float* q, double* wn2,
-                 double* qn2, double* scal, unsigned* gb, int steps) {
+    k_lanczos_coop(const float* __restrict__ A, int lda, int m, int n, const float* v0, float* part, float* q,
+                   double* wn2, double* qn2, double* ab, double* scal, unsigned* gb, int K) {
   extern __shared__ __align__(16) float psm[];
   const int lda4 = lda >> 2;
   const int per = (n + gridDim.x - 1) / gridDim.x;
   const int j0 = min(n, (int)blockIdx.x * per), j1 = min(n, j0 + per);
-  float* sq = psm;             // q (lda)
-  float* sv = psm + lda;       // v (or w) of the CTA's columns (per)
+  float* sq = psm;               // q (lda)
+  float* sv = psm + lda;         // v_it of the CTA's columns (per)
+  float* svp = sv + per;         // v_{it-1}
+  float* sw = svp + per;         // w
   __shared__ double s_red[kPowThreads / 32];
   __shared__ float s_part[kPowThreads / 32][32];
   __shared__ int s_ok;
-  __shared__ float s_scale;
+  __shared__ double s_alpha, s_beta;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NW = kPowThreads / 32;
   const int nslices = lda / 32;
@@ -215,22 +223,34 @@ __global__ void __launch_bounds__(kPowThreads, 1)
   if (tid == 0) {
     gen = ld_acquire_u32(&gb[1]);
     s_ok = 1;
+    s_beta = 0.0;
   }
-  for (int j = j0 + tid; j < j1; j += kPowThreads) sv[j - j0] = v[j];
+  for (int j = j0 + tid; j < j1; j += kPowThreads) {
+    sw[j - j0] = v0[j];
+    sv[j - j0] = 0.f;
+    svp[j - j0] = 0.f;
+  }
   __syncthreads();
-  double lam = 0.0;
   auto barrier = [&]() -> bool {
     __syncthreads();
     if (tid == 0 && !grid_arrive_wait(gb, gridDim.x, gen++)) s_ok = 0;
     __syncthreads();
     return s_ok != 0;
   };
-  for (int it = 0; it < steps; ++it) {
-    // ---- columns: w = A^T q (from the second step on), then the partial of A w
+  for (int it = 0; it <= K; ++it) {
+    // ---- columns
     if (it > 0) {
+      if (warp == 0) {   // alpha_it = ||q_it||^2 from the slice partials, same order in every CTA
+        double t = 0.0;
+        for (int c = lane; c < nslices; c += 32) t += __ldcg(qn2 + c);
+        t = warp_sum_d(t);
+        if (lane == 0) s_alpha = t;
+      }
       for (int i = tid; i < lda; i += kPowThreads) sq[i] = __ldcg(q + i);
       __syncthreads();
-      double w2 = 0.0;
+      const float alpha = (float)s_alpha, beta = (float)s_beta;
+      if (blockIdx.x == 0 && tid == 0) ab[2 * it] = s_alpha;
+      if (it == K) break;   // alpha_K is the last coefficient
       const float4* sq4 = reinterpret_cast<const float4*>(sq);
       for (int j = j0 + warp; j < j1; j += NW) {
         const float4* a = A4 + (size_t)j * lda4;
@@ -244,11 +264,14 @@ __global__ void __launch_bounds__(kPowThreads, 1)
         }
         float s = s0 + s1;
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) {
-          sv[j - j0] = s;
-          w2 += (double)s * (double)s;
-        }
+        if (lane == 0) sw[j - j0] = s - alpha * sv[j - j0] - beta * svp[j - j0];
       }
+      __syncthreads();
+    }
+    {
+      double w2 = 0.0;
+      for (int j = j0 + tid; j < j1; j += kPowThreads) w2 += (double)sw[j - j0] * (double)sw[j - j0];
+      w2 = warp_sum_d(w2);
       if (lane == 0) s_red[warp] = w2;
       __syncthreads();
       if (tid == 0) {
@@ -271,7 +294,7 @@ __global__ void __launch_bounds__(kPowThreads, 1)
         for (int u = 0; u < 8; ++u) a[u] = A4[(size_t)(j + u) * lda4 + c];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-          const float vj = sv[j + u - j0];
+          const float vj = sw[j + u - j0];
           acc[k].x = fmaf(a[u].x, vj, acc[k].x);
           acc[k].y = fmaf(a[u].y, vj, acc[k].y);
           acc[k].z = fmaf(a[u].z, vj, acc[k].z);
@@ -280,7 +303,7 @@ __global__ void __launch_bounds__(kPowThreads, 1)
       }
       for (; j < j1; ++j) {
         const float4 a = A4[(size_t)j * lda4 + c];
-        const float vj = sv[j - j0];
+        const float vj = sw[j - j0];
         acc[k].x = fmaf(a.x, vj, acc[k].x);
         acc[k].y = fmaf(a.y, vj, acc[k].y);
         acc[k].z = fmaf(a.z, vj, acc[k].z);
@@ -294,19 +317,24 @@ __global__ void __launch_bounds__(kPowThreads, 1)
       if (c < lda4) p4[c] = acc[k];
     }
     if (!barrier()) break;
-    // ---- rows: s = 1 / ||w|| (1 at the first step), v = s w, q = s (sum of the partials)
+    // ---- rows: beta_it = ||w||, v_{it+1} = w / beta_it, q_{it+1} = A v_{it+1}
     if (warp == 0) {
-      double t = 1.0;
-      if (it > 0) {
-        t = 0.0;
-        for (int c = lane; c < (int)gridDim.x; c += 32) t += __ldcg(wn2 + c);
-        t = warp_sum_d(t);
+      double t = 0.0;
+      for (int c = lane; c < (int)gridDim.x; c += 32) t += __ldcg(wn2 + c);
+      t = warp_sum_d(t);
+      if (lane == 0) {
+        const double bt = sqrt(t);
+        if (it > 0) s_beta = bt;
+        if (it > 0 && blockIdx.x == 0) ab[2 * it + 1] = bt;
+        s_red[0] = bt > 0.0 ? 1.0 / bt : 0.0;   // an invariant subspace: v and q become zero
       }
-      if (lane == 0) s_scale = t > 0.0 ? (float)(1.0 / sqrt(t)) : 0.f;
     }
     __syncthreads();
-    const float sc = s_scale;
-    for (int j = j0 + tid; j < j1; j += kPowThreads) sv[j - j0] *= sc;
+    const float sc = (float)s_red[0];
+    for (int j = j0 + tid; j < j1; j += kPowThreads) {
+      svp[j - j0] = sv[j - j0];
+      sv[j - j0] = sc * sw[j - j0];
+    }
     for (int sl = blockIdx.x; sl < nslices; sl += gridDim.x) {
       const int row = sl * 32 + lane;
       float sum = 0.f;
@@ -325,31 +353,20 @@ __global__ void __launch_bounds__(kPowThreads, 1)
       __syncthreads();
     }
     if (!barrier()) break;
-    if (it > 0 && blockIdx.x == 0 && warp == 0) {
-      double q2 = 0.0;
-      for (int t = lane; t < nslices; t += 32) q2 += __ldcg(qn2 + t);
-      q2 = warp_sum_d(q2);
-      lam = fmax(lam, q2);
-    }
   }
-  __syncthreads();
-  for (int j = j0 + tid; j < j1; j += kPowThreads) v[j] = sv[j - j0];
-  if (blockIdx.x == 0 && tid == 0) {
-    scal[0] = lam;
-    if (!s_ok) scal[1] = -1.0;   // a barrier wait gave up: the caller reports it
-  }
+  if (blockIdx.x == 0 && tid == 0 && !s_ok) scal[1] = -1.0;   // a barrier wait gave up: the caller reports it
 }
 
-cudaError_t launch_power_coop(const float* A, int lda, int m, int n, float* v, float* part, float* q,
-                              double* wn2, double* qn2, double* scal, unsigned* gb, int steps, int grid,
-                              cudaStream_t s) {
-  if (lda > 4 * kPowChunks * kPowThreads || lda % 32 != 0 || grid < 1) return cudaErrorNotSupported;
+cudaError_t launch_lanczos_coop(const float* A, int lda, int m, int n, const float* v0, float* part, float* q,
+                                double* wn2, double* qn2, double* ab, double* scal, unsigned* gb, int K, int grid,
+                                cudaStream_t s) {
+  if (lda > 4 * kPowChunks * kPowThreads || lda % 32 != 0 || grid < 1 || K < 1) return cudaErrorNotSupported;
   const int per = (n + grid - 1) / grid;
-  const size_t sm = sizeof(float) * ((size_t)lda + per);
-  cudaError_t e = cudaFuncSetAttribute(k_power_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const size_t sm = sizeof(float) * ((size_t)lda + 3 * (size_t)per);
+  cudaError_t e = cudaFuncSetAttribute(k_lanczos_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int per_sm = 0, dev = 0, sms = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_power_coop, kPowThreads, sm);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lanczos_coop, kPowThreads, sm);
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
@@ -364,7 +381,7 @@ cudaError_t launch_power_coop(const float* A, int lda, int m, int n, float* v, f
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_power_coop, A, lda, m, n, v, part, q, wn2, qn2, scal, gb, steps);
+  return cudaLaunchKernelEx(&cfg, k_lanczos_coop, A, lda, m, n, v0, part, q, wn2, qn2, ab, scal, gb, K);
 }
 
 }  // namespace bvls
