@@ -13,7 +13,7 @@ BVLS has every u_j finite.
 Everything here is float64 NumPy written for readability, not speed.  A library primitive
 (matrix-vector product, lstsq, SVD norm) may serve as a step; no blocking or fusion.
 
-Readings of points the paper leaves open (each also listed in the design doc):
+Readings of points the paper leaves open:
   * Primal solver: FISTA with step 1/L and the gradient-based adaptive restart of
     O'Donoghue and Candes; the paper's experiments use plain projected gradient.
   * The screening step of Algorithm 1 is evaluated every ``screen_every`` iterations at the
