@@ -61,6 +61,20 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def replica_rate(local_ms, steps, world, device=None):
+    """Whole-job rate of `world` replicas that each timed `steps` solves in `local_ms`: the
+    units of all ranks over the slowest rank's time (a max all-reduce when world > 1, on the
+    process group already initialised).  Returns (instances/s, slowest rank's ms)."""
+    total_ms = float(local_ms)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return world * steps / (total_ms / 1000.0), total_ms
+
+
 # ----------------------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
@@ -564,12 +578,7 @@ def run_ours(args):
               max(2, args.steps // 2), 1, oracle_dual=True)
     var_s, var_u, var_o = var["screened"], var["unscreened"], var["oracle_dual"]
 
-    total_ms = sum(scr["times_ms"])
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1000.0)
+    value, total_ms = replica_rate(sum(scr["times_ms"]), args.steps, world, dev)
 
     roof = roofline(head["solver"], head["y"], 2000) if rank == 0 else None
     batched = batched_leg(dev, stream, flush, max(2, min(args.steps, 5))) if (rank == 0 and not args.no_batched) else None
@@ -628,10 +637,6 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
-
-
-def args_world_rate(times_ms, world):
-    return world * len(times_ms) / (sum(times_ms) / 1000.0)
 
 
 def main():
