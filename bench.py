@@ -208,11 +208,12 @@ def timed_solves(solver, y_dev, flush, stream, steps, warmup, variants, dual_poi
     return out
 
 
-def kernel_hash():
-    """Hash of every CUDA source: stored ncu counters apply only to the kernels they measured."""
+def kernel_hash(files=None):
+    """Hash of the CUDA sources a kernel is built and configured from (the listed files in
+    order, else every source): stored ncu counters apply only to the kernels they measured."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2202_07258_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in (files if files else sorted(os.listdir(csrc))):
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -269,7 +270,7 @@ def roofline_from_info(info, m, traffic_key=None):
     if os.path.exists(tp):
         t = json.load(open(tp))
         rec = t.get(traffic_key or name.split()[0])
-        if rec and rec.get("kernel_hash") == kernel_hash():
+        if rec and rec.get("kernel_hash") == kernel_hash(rec.get("sources")):
             traffic = rec.get("dram_bytes_per_launch")
     other = {k: {"ms_total": v[0], "launches": v[2], "gb_per_launch": v[1] / max(1, v[2]) / 1e9,
                  "achieved_gbs": (v[1] / max(1, v[2])) / (v[0] / 1000.0 / max(1, v[2])) / 1e9 if v[0] else None}
