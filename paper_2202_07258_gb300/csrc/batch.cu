@@ -66,18 +66,24 @@ __device__ __forceinline__ float f32_up(double x) {
 // u_j = +inf) and dl = x_j - l_j rounded up, gt = a_j^T theta = g_j + eps w_j, and the
 // half-width E of an interval around gt that holds the exact value: the correlation's own
 // error bound e plus the rounding of forming gt.
-__device__ __forceinline__ void term_inputs(float2 xk, float2 g2, int j, const BParams& p, float eps, float e,
-                                            float& du, float& dl, float& gt, float& E) {
-  const float2 a = df2_sub(xk, p.l2[j]);
+__device__ __forceinline__ void term_inputs_v(float2 xk, float2 g2, float2 l2, float2 u2, bool jinf, float wf,
+                                              int dual_mode, float eps, float e, float& du, float& dl, float& gt,
+                                              float& E) {
+  const float2 a = df2_sub(xk, l2);
   dl = fmaxf(a.x + a.y, 0.f) * (1.f + 2.f * kUf);
   du = 0.f;
-  if (!p.jinf[j]) {
-    const float2 c = df2_sub(p.u2[j], xk);
+  if (!jinf) {
+    const float2 c = df2_sub(u2, xk);
     du = fmaxf(c.x + c.y, 0.f) * (1.f + 2.f * kUf);
   }
-  const float ew = p.dual_mode == kTranslation ? eps * p.wf[j] : 0.f;
+  const float ew = dual_mode == kTranslation ? eps * wf : 0.f;
   gt = (g2.x + ew) + g2.y;
   E = e * (1.f + 2.f * kUf) + 8.f * kUf * (fabsf(g2.x) + fabsf(ew)) + fabsf(g2.y);
+}
+
+__device__ __forceinline__ void term_inputs(float2 xk, float2 g2, int j, const BParams& p, float eps, float e,
+                                            float& du, float& dl, float& gt, float& E) {
+  term_inputs_v(xk, g2, p.l2[j], p.u2[j], p.jinf[j] != 0, p.wf[j], p.dual_mode, eps, e, du, dl, gt, E);
 }
 
 // Upper bound of h(g') = du (g')^+ + dl (-g')^+ over |g' - gt| <= E, computed in float32:
@@ -854,38 +860,60 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
       const float eps = s_qf[bb][0], eta = s_qf[bb][1], eta_ref = s_qf[bb][2];
       float va = 0.f, vx = 0.f, vd = 0.f, vs = 0.f;
       int vp = 0;
-#pragma unroll 4
-      for (int j = lane; j < p.n && inst >= 0; j += 32) {
-        const size_t o = (size_t)inst * p.npad + j;
-        const float2 xk = Xc[o];
-        const float2 xp = Xn[o];
-        const float2 g2 = b.Ge[o];
-        const float gp = Gp[o];
-        const float nr = p.nrmf[j];
-        vx += fabsf(xk.x) * nr;
-        const uint8_t fl = s_fl[bb * p.npad + j];
-        if (fl & 3) {
-          Xn[o] = xk;
-          Dn[o] = __float2bfloat16_rn(0.f);
-          continue;
+      // four coordinates per lane and round, every load of the round issued before its stores
+      // (the stores into x_{k+1} could alias the loads of a later coordinate otherwise)
+      constexpr int NB = 4;
+      for (int jb = lane; jb < p.n && inst >= 0; jb += 32 * NB) {
+        float2 xk[NB], xp[NB], g2[NB], l2[NB], u2[NB];
+        float gp[NB], nr[NB], wf[NB];
+        uint8_t fl[NB], jf[NB];
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+          const int j = jb + 32 * u;
+          if (j < p.n) {
+            const size_t o = (size_t)inst * p.npad + j;
+            xk[u] = Xc[o];
+            xp[u] = Xn[o];
+            g2[u] = b.Ge[o];
+            gp[u] = Gp[o];
+            nr[u] = p.nrmf[j];
+            l2[u] = p.l2[j];
+            u2[u] = p.u2[j];
+            jf[u] = p.jinf[j];
+            wf[u] = p.wf[j];
+            fl[u] = s_fl[bb * p.npad + j];
+          }
         }
-        ++vp;
-        if (p.dual_mode != kZero) {
-          float du, dl, gt, E;
-          term_inputs(xk, g2, j, p, eps, ((fl & 4) ? eta_ref : eta) * nr, du, dl, gt, E);
-          const float hup = gap_term_up(du, dl, gt, E);
-          va += hup;
-          vs += hup - (du * fmaxf(gt, 0.f) + dl * fmaxf(-gt, 0.f));  // what exact correlations could remove
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+          const int j = jb + 32 * u;
+          if (j >= p.n) break;
+          const size_t o = (size_t)inst * p.npad + j;
+          vx += fabsf(xk[u].x) * nr[u];
+          if (fl[u] & 3) {
+            Xn[o] = xk[u];
+            Dn[o] = __float2bfloat16_rn(0.f);
+            continue;
+          }
+          ++vp;
+          if (p.dual_mode != kZero) {
+            float du, dl, gt, E;
+            term_inputs_v(xk[u], g2[u], l2[u], u2[u], jf[u] != 0, wf[u], p.dual_mode, eps,
+                          ((fl[u] & 4) ? eta_ref : eta) * nr[u], du, dl, gt, E);
+            const float hup = gap_term_up(du, dl, gt, E);
+            va += hup;
+            vs += hup - (du * fmaxf(gt, 0.f) + dl * fmaxf(-gt, 0.f));  // what exact correlations could remove
+          }
+          const float gk = g2[u].x;
+          const float gv = fmaf(be, gk - gp[u], gk);
+          const float2 xn = fista_step(xk[u], df2_sub(xk[u], xp[u]), gv, be, invL2, l2[u], u2[u]);
+          const float2 d = df2_sub(xn, xk[u]);
+          const float dx = d.x + d.y;
+          Gc[o] = gk;
+          Xn[o] = xn;
+          Dn[o] = __float2bfloat16_rn(dx);
+          vd = fmaf(gv, dx, vd);
         }
-        const float gk = g2.x;
-        const float gv = fmaf(be, gk - gp, gk);
-        const float2 xn = fista_step(xk, df2_sub(xk, xp), gv, be, invL2, p.l2[j], p.u2[j]);
-        const float2 d = df2_sub(xn, xk);
-        const float dx = d.x + d.y;
-        Gc[o] = gk;
-        Xn[o] = xn;
-        Dn[o] = __float2bfloat16_rn(dx);
-        vd = fmaf(gv, dx, vd);
       }
       va = warp_sum_f(va);
       vx = warp_sum_f(vx);
@@ -1048,30 +1076,49 @@ __global__ void __launch_bounds__(kBEvalThreads, 2) k_beval(BParams p, BBuffers 
       const float eps = s_qf[bb][0];
       const float rr = f32_up(s_q[bb][4]);
       int pins = 0;
-#pragma unroll 4
-      for (int j = lane; j < p.n && inst >= 0; j += 32) {
-        if (s_fl[bb * p.npad + j] & 3) continue;
-        const float nr = p.nrmf[j];
-        if (!(nr > 0.f)) continue;
-        const size_t o = (size_t)inst * p.npad + j;
-        const float2 g2 = b.Ge[o];
-        const float ew = trans ? eps * p.wf[j] : 0.f;
-        const float gt = (g2.x + ew) + g2.y;
-        const float dl = 8.f * kUf * (fabsf(g2.x) + fabsf(ew)) + fabsf(g2.y);
-        const float thr = rr * nr * (1.f + 4.f * kUf);
-        int pin = 0;
-        float2 bnd = make_float2(0.f, 0.f);
-        if (gt + dl < -thr) {
-          pin = 1;
-          bnd = p.l2[j];
-        } else if (!p.jinf[j] && gt - dl > thr) {
-          pin = 2;
-          bnd = p.u2[j];
+      // four coordinates per lane and round, their loads issued before any flag store
+      constexpr int NB = 4;
+      for (int jb = lane; jb < p.n && inst >= 0; jb += 32 * NB) {
+        float2 g2[NB], l2[NB], u2[NB];
+        float nr[NB], wf[NB];
+        uint8_t fl[NB], jf[NB];
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+          const int j = jb + 32 * u;
+          fl[u] = 1;
+          if (j < p.n) {
+            fl[u] = s_fl[bb * p.npad + j];
+            nr[u] = p.nrmf[j];
+            g2[u] = b.Ge[(size_t)inst * p.npad + j];
+            wf[u] = p.wf[j];
+            jf[u] = p.jinf[j];
+            l2[u] = p.l2[j];
+            u2[u] = p.u2[j];
+          }
         }
-        if (pin && df2_eq(Xc[o], bnd) && df2_eq(Xn[o], bnd)) {
-          b.flags[o] = (uint8_t)pin;
-          s_fl[bb * p.npad + j] = (uint8_t)pin;
-          ++pins;
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+          const int j = jb + 32 * u;
+          if ((fl[u] & 3) || !(nr[u] > 0.f)) continue;
+          const size_t o = (size_t)inst * p.npad + j;
+          const float ew = trans ? eps * wf[u] : 0.f;
+          const float gt = (g2[u].x + ew) + g2[u].y;
+          const float dl = 8.f * kUf * (fabsf(g2[u].x) + fabsf(ew)) + fabsf(g2[u].y);
+          const float thr = rr * nr[u] * (1.f + 4.f * kUf);
+          int pin = 0;
+          float2 bnd = make_float2(0.f, 0.f);
+          if (gt + dl < -thr) {
+            pin = 1;
+            bnd = l2[u];
+          } else if (!jf[u] && gt - dl > thr) {
+            pin = 2;
+            bnd = u2[u];
+          }
+          if (pin && df2_eq(Xc[o], bnd) && df2_eq(Xn[o], bnd)) {
+            b.flags[o] = (uint8_t)pin;
+            s_fl[bb * p.npad + j] = (uint8_t)pin;
+            ++pins;
+          }
         }
       }
       for (int o2 = 16; o2 > 0; o2 >>= 1) pins += __shfl_xor_sync(kFull, pins, o2);
