@@ -219,8 +219,9 @@ typedef struct {
  *                 (BVLS_PREC_FP32) or double-float (BVLS_PREC_FP32X2) products, the gap,
  *                 the sphere test and the stop test.  The other iterations are tensor-core
  *                 steps: g_k = g_{k-1} - bf16(A^T A) bf16(x_k - x_{k-1}) for all active
- *                 instances in one tcgen05 GEMM with float32 accumulation.  max_iter is
- *                 rounded up to a multiple of K; single_pass is ignored.
+ *                 instances in one tcgen05 GEMM with float32 accumulation, whose momentum
+ *                 term also takes bf16(x_k - x_{k-1}).  max_iter is rounded up to a
+ *                 multiple of K; single_pass is ignored.
  *   X_out         any; B x n doubles: per instance, the iterate of its last evaluation with
  *                 screened coordinates at their bounds.
  *   screened_out  any; B x n bytes or NULL (0 preserved, 1 at l_j, 2 at u_j).
@@ -228,12 +229,13 @@ typedef struct {
  *   iters_out     any; B ints or NULL: the iteration index of that evaluation.
  *   status_out    any; B ints or NULL: BVLS_OK or BVLS_EMAXITER per instance.
  *   info          host or NULL.
- * The iterates are float32 (the bounds are rounded inward to float32 for them); the gap,
- * the radius and the test are float64 with the rounding of every evaluation product
- * bounded, so no coordinate is fixed unless the safe rule holds for the exact problem.
- * Limits: m <= 1024, n <= 4096, 1 <= B <= 2^20.  The first call computes and keeps
- * bf16(A^T A) (n rounded up to 128, squared, 2 bytes each) and a workspace of about
- * 30 * B * n bytes, reused by later calls with the same or smaller B.
+ * The iterates are double-float pairs of float32 (about 48 significant bits), clipped to
+ * the bounds in the same form; the gap, the radius and the test bound the rounding of
+ * every evaluation product, so no coordinate is fixed unless the safe rule holds for the
+ * exact problem.  Limits: m <= 1024, n <= 4096, 1 <= B <= 2^20.  The first call computes
+ * and keeps bf16(A^T A) (n rounded up to 128 = npad, squared, 2 bytes each) and a
+ * workspace of about 37 * B * npad + 8 * B * n bytes, reused by later calls with the same
+ * or smaller B.
  * Returns BVLS_OK when every instance converged, BVLS_EMAXITER otherwise (all outputs
  * valid), or an error (outputs untouched).
  */
