@@ -1,9 +1,12 @@
 // bvls_solve_static: the single-instance solve for callers that cannot allocate device
-// memory (for example code running inside a memory pool it does not own, under a
-// CUDA-graph-capturing framework that forbids cudaMalloc, or in a process whose allocator
-// is fixed by its host application).  It runs the same kernels as bvls_setup + bvls_solve,
-// but every scratch buffer lives in one file-scope device array of fixed size, so the call
-// allocates nothing: no cudaMalloc, cudaFree, pinned host memory, CUDA graphs or events.
+// memory (for example code running inside a memory pool it does not own, or in a process
+// whose allocator is fixed by its host application at start-up).  It uses the same
+// per-iteration kernels as bvls_setup + bvls_solve (the single pass and its residual, or the
+// two passes for large m, then the gap, test and compaction kernels), launched one by one:
+// the step constant comes from power steps instead of the Lanczos launch, and neither the
+// persistent form nor CUDA graphs are used.  Every scratch buffer lives in one file-scope
+// device array of fixed size, so the call allocates nothing: no cudaMalloc, cudaFree,
+// pinned host memory, CUDA graphs or events.
 //
 // The array (kStaticBytes) is part of the library image: every GPU that loads the library
 // holds it until the process exits.  All calls share it and it keeps the last call's
@@ -13,6 +16,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "bvls_gb300.h"
 #include "common.cuh"
@@ -28,8 +32,12 @@ constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_scratch[kStaticBytes];
 
-// Device address of g_scratch per device, taken once per device with that device current.
+// Device address of g_scratch per device, looked up once per device with that device
+// current.  The lookup is serialised by a mutex, so two host threads making their first call
+// on one device do not race.  A cached address belongs to the device's current context:
+// after cudaDeviceReset the process must not call this entry point again on that device.
 void* g_scratch_dev[kMaxDevices] = {nullptr};
+std::mutex g_scratch_mu;
 
 constexpr double kU = 5.9604644775390625e-08;
 constexpr double kU64 = 1.1102230246251565e-16;
@@ -161,8 +169,10 @@ bvls_status bvls_solve_static(const float* A, int m, int n, int lda, const doubl
   if (!(o.tol >= 0.0) || o.screen_every < 1 || o.max_iter < 1 ||
       (o.precision != BVLS_PREC_FP32X2 && o.precision != BVLS_PREC_FP32 && o.precision != BVLS_PREC_MIXED) ||
       !(o.lipschitz >= 0.0) ||
-      !std::isfinite(o.lipschitz))
+      !std::isfinite(o.lipschitz) || o.single_pass < 0 || o.single_pass > 2)
     return fail(BVLS_EINVAL, "invalid options");
+  if (o.algorithm != BVLS_ALG_FISTA)
+    return fail(BVLS_ENOTSUP, "bvls_solve_static runs FISTA only (opts->algorithm = BVLS_ALG_FISTA)");
   bool any_inf = false;
   for (int j = 0; j < n; ++j) {
     const double lj = l ? l[j] : 0.0, uj = u ? u[j] : INFINITY;
@@ -180,11 +190,16 @@ bvls_status bvls_solve_static(const float* A, int m, int n, int lda, const doubl
   SCK(cudaGetDevice(&dev));
   if (dev >= kMaxDevices) return fail(BVLS_ENOTSUP, "device index too large");
   // Once per device, with that device current: the device address of the static array.
-  if (!g_scratch_dev[dev]) {
-    void* ptr = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&ptr, g_scratch);
-    if (e != cudaSuccess || !ptr) return fail(BVLS_ECUDA, "cudaGetSymbolAddress(g_scratch)", e);
-    g_scratch_dev[dev] = ptr;
+  void* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_dev[dev]) {
+      void* ptr = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&ptr, g_scratch);
+      if (e != cudaSuccess || !ptr) return fail(BVLS_ECUDA, "cudaGetSymbolAddress(g_scratch)", e);
+      g_scratch_dev[dev] = ptr;
+    }
+    scratch = g_scratch_dev[dev];
   }
   SCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   SCK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -209,7 +224,7 @@ bvls_status bvls_solve_static(const float* A, int m, int n, int lda, const doubl
              kStaticBytes);
     return fail(BVLS_ENOTSUP, msg);
   }
-  Layout W = carve(static_cast<unsigned char*>(g_scratch_dev[dev]), m, n, m4, lda, fwd_tiles, fwd_chunks,
+  Layout W = carve(static_cast<unsigned char*>(scratch), m, n, m4, lda, fwd_tiles, fwd_chunks,
                    max_blocks, sms);
   Buffers& b = W.b;
 
