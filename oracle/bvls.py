@@ -248,7 +248,7 @@ class SolveResult:
     dual_mode: str                # "scaling", "translation" or "zero"
     L: float
     t: np.ndarray | None
-    history: list = field(default_factory=list)   # (iteration, gap, |preserved|) per evaluation
+    history: list = field(default_factory=list)   # (iteration, gap, |preserved|, deferred) per evaluation
 
 
 def _dual_point(A, y, x, l, u, mode, t, w, cols):
@@ -278,7 +278,7 @@ def _fixed_dual_point(A, y, x, theta0, mode, t, w, cols):
 
 def solve(A, y, l=None, u=None, *, tol=1e-6, screen_every=10, screening=True,
           max_iter=100_000, x0=None, L=None, t=None, eps_scope="preserved",
-          restart=True, record=False, dual_point=None):
+          restart=True, record=False, dual_point=None, pin="at_bound"):
     """Algorithm 1 (Algorithm 2 for NNLS) with a FISTA primal update.
 
     Each iteration k computes, on the preserved set A:
@@ -295,12 +295,18 @@ def solve(A, y, l=None, u=None, *, tol=1e-6, screen_every=10, screening=True,
     ``dual_point`` (length m) replaces Theta(x_k) in every screening step by a fixed dual
     point (translated into F_D when needed) -- the oracle-dual-point experiment of Section 5,
     where theta* itself informs the test; any feasible point keeps the sphere safe.
+    ``pin="immediate"`` is Algorithm 1 read literally: every coordinate that passes the
+    test is set to its bound at once (x_S <- bounds), also when x_k or x_{k+1} is not there
+    yet; ``pin="at_bound"`` (default) fixes it only once both sit at that bound and records,
+    per evaluation, how many passing coordinates it deferred (the fourth history entry).
     """
     A, y, l, u = as_problem(A, y, l, u)
     m, n = A.shape
     K = int(screen_every)
     if K < 1 or max_iter < 1:
         raise ValueError("screen_every and max_iter must be >= 1")
+    if pin not in ("at_bound", "immediate"):
+        raise ValueError("pin must be 'at_bound' or 'immediate'")
     fin = np.isfinite(u)
     if fin.all():
         mode = "scaling"
@@ -351,7 +357,7 @@ def solve(A, y, l=None, u=None, *, tol=1e-6, screen_every=10, screening=True,
                 theta = _dual_point(A_P, y_red, xP, lP, uP, mode, t_dir, w_P, cols_P) if dual_point is None \
                     else _fixed_dual_point(A_P, y_red, xP, dual_point, mode, t_dir, w_P, cols_P)
                 gap = duality_gap(A_P, y_red, xP, theta, lP, uP)
-            history.append((k, gap, int(P.size)))
+            deferred = 0
             if screening and mode != "zero":
                 if eps_scope == "all":
                     tau, pad = rounding_pads(A, y, x, theta)
@@ -359,11 +365,15 @@ def solve(A, y, l=None, u=None, *, tol=1e-6, screen_every=10, screening=True,
                     tau, pad = rounding_pads(A_P, y_red, xP, theta)
                 radius = safe_radius(gap + pad)
                 S_l, S_u = safe_rule(A_P, theta, radius + tau, uP)
-                # A coordinate is fixed once x_k and x_{k+1} both sit at the bound the rule
-                # names (the assignment x_S <- bounds of Algorithm 1 is then exact and the
-                # momentum stays consistent); until then it stays in the preserved set.
-                S_l &= (xP == lP) & (x_new[P] == lP)
-                S_u &= ~S_l & (xP == uP) & (x_new[P] == uP)
+                S_u &= ~S_l
+                if pin == "at_bound":
+                    # A coordinate is fixed once x_k and x_{k+1} both sit at the bound the rule
+                    # names (the assignment x_S <- bounds of Algorithm 1 is then exact and the
+                    # momentum stays consistent); until then it stays in the preserved set.
+                    passing = int(S_l.sum() + S_u.sum())
+                    S_l &= (xP == lP) & (x_new[P] == lP)
+                    S_u &= (xP == uP) & (x_new[P] == uP)
+                    deferred = passing - int(S_l.sum() + S_u.sum())
                 low, upp = P[S_l], P[S_u]
                 pinned = np.concatenate([low, upp])
                 if pinned.size:
@@ -374,6 +384,7 @@ def solve(A, y, l=None, u=None, *, tol=1e-6, screen_every=10, screening=True,
                     active[pinned] = False
                     screened[low] = 1
                     screened[upp] = 2
+            history.append((k, gap, int(P.size), deferred))
             if gap < tol or k == max_iter - 1:
                 # x_k is the iterate the gap certifies (also when max_iter ends the loop)
                 return SolveResult(x, gap, primal_objective(A, y, x), k + 1, screened,

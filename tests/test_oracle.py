@@ -374,3 +374,57 @@ def test_chambolle_pock_matches_brute_force_and_fista():
     assert np.all(xs[b.screened == 2] == 1.0) and np.all(g[b.screened == 2] > 0)
     with pytest.raises(ValueError):
         O.solve_cp(A, y, p.l, np.full(A.shape[1], np.inf))
+
+
+@pytest.mark.parametrize("make", [lambda: W.nnls_abs_gaussian(300, 700, 0.05, 1.0, 1),
+                                  lambda: W.bvls_table2(200, 500, 2),
+                                  lambda: W.bvls_dirichlet_shared(224, 512, 1, 8, 0.005, 0),
+                                  lambda: W.nnls_abs_gaussian(120, 400, 0.1, 1.0, 5)])
+def test_fixing_at_bound_defers_nothing_on_the_test_families(make):
+    """Algorithm 1 sets a coordinate that passes the test to its bound at once; the default
+    reading fixes it once x_k and x_{k+1} already sit there.  On the test families every
+    coordinate that passes the test already sits at its bound, so the two readings run the
+    same iterates bit for bit."""
+    p = make()
+    A, y = _f64(p)
+    L = 1.05 * O.lipschitz(A)
+    a = O.solve(A, y, p.l, p.u, tol=1e-9, L=L, record=True)
+    b = O.solve(A, y, p.l, p.u, tol=1e-9, L=L, record=True, pin="immediate")
+    assert sum(h[3] for h in a.history) == 0
+    assert a.iters == b.iters and np.array_equal(a.x, b.x) and np.array_equal(a.screened, b.screened)
+    assert (a.screened > 0).sum() > 0
+
+
+def test_literal_and_at_bound_fixing_reach_the_same_optimum():
+    """A case where the readings differ: start at the certified optimum with a few
+    coordinates that belong at 0 lifted to 1e-3, screen every iteration with the optimal dual
+    point theta*.  The first evaluation (k = 0) sees a tiny sphere while those coordinates
+    are still off their bound: the literal reading pins them at once, the default defers
+    them.  At that evaluation the literal pins are the default's pins plus the deferred ones;
+    both readings fix only coordinates that sit at that bound in the optimum and both reach
+    it."""
+    p = W.nnls_abs_gaussian(120, 400, 0.05, 1.0, 2)
+    A, y = _f64(p)
+    ref = O.solve(A, y, p.l, p.u, tol=1e-11)
+    xs = O.polish(A, y, ref.x, p.l, p.u, tau=1e-7)
+    assert O.kkt_residual(A, y, xs, p.l, p.u) < 1e-10
+    th = y - A @ xs
+    g = A.T @ th
+    lifted = np.argsort(g)[:5]                      # the most negative a_j^T theta*
+    assert np.all(xs[lifted] == 0.0)
+    x0 = xs.copy()
+    x0[lifted] = 1e-3
+    a = O.solve(A, y, p.l, p.u, tol=1e-9, screen_every=1, x0=x0, dual_point=th, record=True)
+    b = O.solve(A, y, p.l, p.u, tol=1e-9, screen_every=1, x0=x0, dual_point=th, record=True, pin="immediate")
+    assert a.converged and b.converged
+    assert a.history[0][3] >= 5                     # the lifted coordinates were deferred
+    fixed_a0 = a.history[0][2] - a.history[1][2]
+    fixed_b0 = b.history[0][2] - b.history[1][2]
+    assert fixed_b0 == fixed_a0 + a.history[0][3]
+    for r in (a, b):
+        low = r.screened == 1
+        assert np.all(xs[low] == 0.0) and np.all(g[low] < 0)
+        xp = O.polish(A, y, r.x, p.l, p.u, tau=1e-7)
+        assert np.abs(xp - xs).max() <= 1e-9 * max(1.0, np.abs(xs).max())
+    with pytest.raises(ValueError):
+        O.solve(A, y, p.l, p.u, pin="later")
