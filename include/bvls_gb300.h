@@ -104,8 +104,10 @@ typedef struct {
   int precision;      /* BVLS_PREC_* */
   int restart;        /* 1: gradient-based adaptive restart of the momentum */
   double lipschitz;   /* > 0: use this step constant L instead of the one from bvls_setup */
-  int profile;        /* 1: launch without CUDA graphs and time every product kernel with
-                         CUDA events (fills the *_ms fields of bvls_info) */
+  int profile;        /* 1: time every product kernel with CUDA events (one chunk of
+                         iterations captured into a plain graph with event nodes; fills the
+                         *_ms fields of bvls_info); 2 (bvls_solve): launch every kernel directly
+                         from the host, a chunk at a time, with no CUDA graph and no events */
   int single_pass;    /* 1 (default): when m <= 8192, one streaming read of the preserved
                          columns per iteration yields both products, and the K iterations
                          between two gap evaluations run in one persistent (cooperative)
@@ -120,6 +122,21 @@ typedef struct {
                          single-pass form and a dual mode other than BVLS_DUAL_ZERO
                          (else BVLS_ENOTSUP / BVLS_EINVAL).  Ignored by the other entry points. */
   int algorithm;      /* BVLS_ALG_*; bvls_solve only (the other entry points use FISTA) */
+  int refine;         /* 1: after the solve, refine the returned x on its free set (the
+                         optimality conditions of Section 3.2, Eq. (optimality2)): the
+                         coordinates strictly inside the box solve the restricted normal
+                         equations A_F^T A_F x_F = A_F^T (y - A_B x_B), by rounds of float64
+                         residuals and float32 conjugate-gradient corrections; a coordinate
+                         that leaves the box stops on its bound, a coordinate at a bound whose
+                         a_j^T (y - A x) has the wrong sign joins F.  The refined x is returned
+                         only when every preserved coordinate passes its optimality test within
+                         the rounding bound of that test (eta_j = ||a_j|| (gamma ||r|| + ||e_r||),
+                         plus 1e-12 ||a_j|| ||r|| of stationarity on F); otherwise the solver's
+                         iterate is returned unchanged.  Coordinates fixed by the safe rule stay
+                         at their bounds.  Declined when m > 8192, when |F| > min(m, 2048) (A_F
+                         cannot have full column rank: the optimum is not unique) or after 10
+                         rounds.  bvls_solve, bvls_solve_batched, bvls_solve_ragged; 0 (default):
+                         off.  The gap fields keep the solver's certificate. */
 } bvls_opts;
 
 typedef struct {
@@ -147,11 +164,23 @@ typedef struct {
                              already stopped and returned at entry) */
   int single_pass;        /* form of the iterations (see bvls_opts): 0 two passes, 1 single pass
                              with two launches per iteration, 2 single pass, persistent */
+  int refined;            /* opts.refine: 1 when the refined x was returned */
+  int refine_rounds;      /* refinement rounds run (each: float64 residual and correlations,
+                             then a float32 correction on F) */
+  int n_free;             /* |F| of the last refinement round */
+  int refine_cg_iters;    /* conjugate-gradient iterations over all rounds */
+  double kkt;             /* refinement: max over the preserved j of
+                             |x_j - clip(x_j + a_j^T (y - A x), l_j, u_j)| at the returned x
+                             (0 at an optimum; float64 evaluation) */
+  double refine_ms;       /* refinement kernel time (CUDA events) */
+  int refine_reason;      /* 0 refined or off, 1 declined after the last round, 2 declined
+                             because |F| > min(m, 2048), 3 declined because m > 8192 */
+  int pad_;
 } bvls_info;
 
 /* Fill *opts with the defaults: tol 1e-6, screen_every 10, max_iter 100000, screening 1,
    precision BVLS_PREC_FP32X2, restart 1, lipschitz 0 (use setup's), profile 0,
-   single_pass 1. */
+   single_pass 1, dual_point NULL, algorithm BVLS_ALG_FISTA, refine 0. */
 BVLS_API void bvls_default_opts(bvls_opts* opts);
 
 /*
@@ -205,6 +234,12 @@ typedef struct {
   int step_launches, eval_launches;
   double kernel_launches; /* kernels this call launched (including ones that returned at
                              entry because every instance had finished) */
+  int n_refined;          /* opts.refine: instances whose refined x was returned */
+  int refine_free_max;    /* largest |F| of a refined instance */
+  double kkt_max;         /* largest kkt (see bvls_info) over the refined instances */
+  double refine_ms;       /* refinement kernel time (CUDA events) */
+  int refine_out_of_rounds; /* instances declined after the last round */
+  int refine_not_unique;    /* instances declined because |F| > min(m, 2048) */
 } bvls_batch_info;
 
 /*
@@ -312,6 +347,12 @@ typedef struct {
   int tuned;            /* 1 when this call ran the autotuner (the choice is kept for later calls
                            on a batch of the same shape) */
   double tune_ms;       /* autotuner time (part of setup_ms) */
+  int n_refined;        /* opts.refine: instances whose refined x was returned */
+  int refine_free_max;  /* largest |F| of a refined instance */
+  double kkt_max;       /* largest kkt (see bvls_info) over the refined instances */
+  double refine_ms;     /* refinement kernel time (CUDA events) */
+  int refine_out_of_rounds; /* instances declined after the last round */
+  int refine_not_unique;    /* instances declined because |F| > min(m, 2048) */
 } bvls_ragged_info;
 
 /*
@@ -345,26 +386,29 @@ BVLS_API bvls_status bvls_solve_ragged(int B, const bvls_problem* probs, const b
 /*
  * One-call solve that allocates nothing.  The paper has no counterpart: this is a service
  * for callers that cannot allocate device memory -- code that runs inside a memory pool or
- * allocator it does not own, code inside a framework's CUDA stream capture (where
- * cudaMalloc is not permitted), or a plug-in whose host application forbids allocations
- * after start-up.  It runs the same kernels as bvls_setup + bvls_solve, but all scratch
- * lives in one static device array of 8 MiB that every GPU loading this library holds
- * until the process exits; no cudaMalloc, cudaFree, pinned host memory, CUDA graph or
- * event is created.
+ * allocator it does not own, or a plug-in whose host application forbids allocations after
+ * start-up.  It uses the same per-iteration kernels as bvls_setup + bvls_solve, launched one
+ * by one (the single pass and its residual, or the two passes, then the gap, test and
+ * compaction kernels); the step constant comes from power steps, and neither the persistent
+ * form nor CUDA graphs are used.  All scratch lives in one static device array of 8 MiB that
+ * every GPU loading this library holds until the process exits; no cudaMalloc, cudaFree,
+ * pinned host memory, CUDA graph or event is created.
  *   A             device memory, column-major float32, read in place; lda a multiple of 32;
  *                 rows m..lda-1 of each column are read and must be finite (zero them).
  *   l, u          host; n doubles or NULL (0 / +inf), as in bvls_setup.
  *   y             any; m float32.  x0: any; n doubles or NULL.
- *   opts          host or NULL (defaults).  opts->profile is ignored.
+ *   opts          host or NULL (defaults).  opts->profile, opts->dual_point and opts->refine
+ *                 are ignored; only FISTA runs here (another opts->algorithm gets
+ *                 BVLS_ENOTSUP).
  *   stream        a cudaStream_t (0 allowed); the call returns when its outputs are written.
  *   x_out, screened_out, info: as in bvls_solve.
  * Limits: m <= 4096, n <= 16384 and a scratch layout that fits the 8 MiB array; larger
  * problems get BVLS_ENOTSUP with the size in bvls_last_error() (use bvls_setup then).
  * The translation direction for columns with u_j = +inf is t = -1 when it is interior,
  * else theta = 0 (bvls_setup also tries further candidates).  The step constant comes from
- * opts->lipschitz when > 0, else from 1.05 x a 100-step power-iteration estimate of ||A||_2^2.
+ * opts->lipschitz when > 0, else from 1.05 x a 101-step power-iteration estimate of ||A||_2^2.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.  Every call
+ * with that device current and keeps it for later calls on that device.  Every call
  * reuses the same array, which keeps the previous call's contents (each call clears what
  * must start at zero); calls whose GPU work overlaps -- from two threads or on two streams
  * -- race on it and must be serialised by the caller.

@@ -50,7 +50,8 @@ def _host_f64(v, n):
 
 
 def make_opts(tol=1e-6, screen_every=10, max_iter=100000, screening=True, precision="fp32x2",
-              restart=True, lipschitz=0.0, profile=False, single_pass=True, algorithm="fista") -> bvls_opts:
+              restart=True, lipschitz=0.0, profile=False, single_pass=True, algorithm="fista",
+              refine=False) -> bvls_opts:
     o = bvls_default_opts()
     o.tol = float(tol)
     o.screen_every = int(screen_every)
@@ -59,10 +60,11 @@ def make_opts(tol=1e-6, screen_every=10, max_iter=100000, screening=True, precis
     o.precision = {"fp32x2": BVLS_PREC_FP32X2, "fp32": BVLS_PREC_FP32, "mixed": BVLS_PREC_MIXED}[precision]
     o.restart = 1 if restart else 0
     o.lipschitz = float(lipschitz)
-    o.profile = 1 if profile else 0
+    o.profile = int(profile)            # 0 graphs, 1 event-timed chunk graph, 2 direct launches
     o.single_pass = int(single_pass)   # 0 two passes, 1 single pass (persistent), 2 single pass, two launches
     o.algorithm = {"fista": _capi.BVLS_ALG_FISTA, "cp": _capi.BVLS_ALG_CHAMBOLLE_POCK,
                    "chambolle_pock": _capi.BVLS_ALG_CHAMBOLLE_POCK}[algorithm]
+    o.refine = 1 if refine else 0
     return o
 
 

@@ -39,6 +39,7 @@ class bvls_opts(ctypes.Structure):
         ("single_pass", ctypes.c_int),
         ("dual_point", ctypes.c_void_p),
         ("algorithm", ctypes.c_int),
+        ("refine", ctypes.c_int),
     ]
 
 
@@ -61,6 +62,14 @@ class bvls_info(ctypes.Structure):
         ("tr_launches", ctypes.c_int),
         ("kernel_launches", ctypes.c_double),
         ("single_pass", ctypes.c_int),
+        ("refined", ctypes.c_int),
+        ("refine_rounds", ctypes.c_int),
+        ("n_free", ctypes.c_int),
+        ("refine_cg_iters", ctypes.c_int),
+        ("kkt", ctypes.c_double),
+        ("refine_ms", ctypes.c_double),
+        ("refine_reason", ctypes.c_int),
+        ("pad_", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -82,6 +91,12 @@ class bvls_batch_info(ctypes.Structure):
         ("step_launches", ctypes.c_int),
         ("eval_launches", ctypes.c_int),
         ("kernel_launches", ctypes.c_double),
+        ("n_refined", ctypes.c_int),
+        ("refine_free_max", ctypes.c_int),
+        ("kkt_max", ctypes.c_double),
+        ("refine_ms", ctypes.c_double),
+        ("refine_out_of_rounds", ctypes.c_int),
+        ("refine_not_unique", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -135,6 +150,12 @@ class bvls_ragged_info(ctypes.Structure):
         ("screen_every", ctypes.c_int),
         ("tuned", ctypes.c_int),
         ("tune_ms", ctypes.c_double),
+        ("n_refined", ctypes.c_int),
+        ("refine_free_max", ctypes.c_int),
+        ("kkt_max", ctypes.c_double),
+        ("refine_ms", ctypes.c_double),
+        ("refine_out_of_rounds", ctypes.c_int),
+        ("refine_not_unique", ctypes.c_int),
     ]
 
     def as_dict(self):

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libbvls_gb300.so")
-SOURCES = ["iter_kernels.cu", "pass_kernel.cu", "setup_kernels.cu", "batch.cu", "backward.cu", "ragged.cu", "capi.cu", "noalloc.cu"]
+SOURCES = ["iter_kernels.cu", "pass_kernel.cu", "setup_kernels.cu", "batch.cu", "backward.cu", "ragged.cu", "refine.cu", "capi.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]

@@ -16,6 +16,7 @@
 #include "backward.cuh"
 #include "batch.cuh"
 #include "ragged.cuh"
+#include "refine.cuh"
 #include "bvls_gb300.h"
 #include "common.cuh"
 
@@ -107,6 +108,13 @@ struct bvls_handle {
   bool b_have_graph = false;
   double b_key[10] = {0};
   cudaGraphExec_t b_exec = nullptr;
+  // refinement (opts.refine): scratch for ref_cap instances (correlations, saved iterate),
+  // their descriptors and results, and two events around the kernel
+  int ref_cap = 0;
+  double *ref_g = nullptr, *ref_xs = nullptr;
+  RefDesc* ref_desc = nullptr;
+  RefOut* ref_out = nullptr;
+  cudaEvent_t ref_ev[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -133,6 +141,10 @@ void free_handle(bvls_handle* h) {
   for (void* p : h->b_allocs) cudaFree(p);
   for (auto e : h->prof) cudaEventDestroy(e);
   for (void* p : h->allocs) cudaFree(p);
+  for (void* p : {(void*)h->ref_g, (void*)h->ref_xs, (void*)h->ref_desc, (void*)h->ref_out})
+    if (p) cudaFree(p);
+  for (cudaEvent_t e : h->ref_ev)
+    if (e) cudaEventDestroy(e);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->s && h->own_stream) cudaStreamDestroy(h->s);
   delete h;
@@ -235,6 +247,59 @@ bool persistent_form(const bvls_handle* h, const bvls_opts& o) {
   return h->pass_stages > 0 && h->pass_coop && o.single_pass == 1;
 }
 
+// Refinement parameters shared by the entry points (opts.refine).
+RefParams ref_params(const RefDesc* desc, RefOut* out, int B) {
+  RefParams rp{};
+  rp.desc = desc;
+  rp.out = out;
+  rp.B = B;
+  rp.max_rounds = 10;
+  rp.cg_max_iter = 4000;
+  rp.cg_tol = 1e-5f;
+  rp.tau = 1e-9;
+  rp.zeta = 1e-12;
+  return rp;
+}
+
+// Scratch of the refinement for B instances of n coordinates (kept by the handle, grown on
+// demand) and its two timing events.
+bvls_status ref_reserve(bvls_handle* h, int B) {
+  if (!h->ref_ev[0]) {
+    CK(cudaEventCreate(&h->ref_ev[0]));
+    CK(cudaEventCreate(&h->ref_ev[1]));
+  }
+  if (B <= h->ref_cap) return BVLS_OK;
+  for (void** p : {(void**)&h->ref_g, (void**)&h->ref_xs, (void**)&h->ref_desc, (void**)&h->ref_out}) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+  }
+  h->ref_cap = 0;
+  CK(cudaMalloc(&h->ref_g, sizeof(double) * (size_t)B * h->n));
+  CK(cudaMalloc(&h->ref_xs, sizeof(double) * (size_t)B * h->n));
+  CK(cudaMalloc(&h->ref_desc, sizeof(RefDesc) * (size_t)B));
+  CK(cudaMalloc(&h->ref_out, sizeof(RefOut) * (size_t)B));
+  h->ref_cap = B;
+  return BVLS_OK;
+}
+
+// Refine B instances sharing the handle's A and box: Y (pitch ldy floats), X (pitch ldx
+// doubles, in place), flags (pitch ldf bytes, or null).  Results land in out (host, B).
+bvls_status refine_shared(bvls_handle* h, int B, const float* Y, int ldy, double* X, int ldx, const uint8_t* flags,
+                          int ldf, double step, std::vector<RefOut>* out, float* ms) {
+  TRY(ref_reserve(h, B));
+  CK(launch_ref_desc_strided(h->ref_desc, B, h->A, h->m, h->n, h->lda, Y, ldy, h->l, h->u, X, ldx, flags, ldf,
+                             h->ref_g, h->ref_xs, step, h->s));
+  CK(cudaEventRecord(h->ref_ev[0], h->s));
+  CK(launch_refine(ref_params(h->ref_desc, h->ref_out, B), h->m, std::min(std::min(h->n, h->m), kRefMaxFree),
+                   h->s));
+  CK(cudaEventRecord(h->ref_ev[1], h->s));
+  out->resize(B);
+  CK(cudaMemcpyAsync(out->data(), h->ref_out, sizeof(RefOut) * B, cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  CK(cudaEventElapsedTime(ms, h->ref_ev[0], h->ref_ev[1]));
+  return BVLS_OK;
+}
+
 // Enqueue chunk_len iterations (the chunk starts at an even k, so slot = j & 1).
 // With ev != nullptr, records ev[3j], ev[3j+1], ev[3j+2] around the two products.
 cudaError_t enqueue_chunk(bvls_handle* h, const Params& p, const bvls_opts& o, int chunk_len,
@@ -310,6 +375,8 @@ bvls_status validate_opts(const bvls_opts& o) {
     return set_err(BVLS_EINVAL, "invalid options (tol >= 0, screen_every >= 1, max_iter >= 1, "
                                 "precision 0/1/2, lipschitz >= 0 finite)");
   if (o.single_pass < 0 || o.single_pass > 2) return set_err(BVLS_EINVAL, "single_pass must be 0, 1 or 2");
+  if (o.refine < 0 || o.refine > 1) return set_err(BVLS_EINVAL, "refine must be 0 or 1");
+  if (o.profile < 0 || o.profile > 2) return set_err(BVLS_EINVAL, "profile must be 0, 1 or 2");
   return BVLS_OK;
 }
 
@@ -390,6 +457,7 @@ void bvls_default_opts(bvls_opts* o) {
   o->single_pass = 1;
   o->dual_point = nullptr;
   o->algorithm = BVLS_ALG_FISTA;
+  o->refine = 0;
 }
 
 const char* bvls_last_error(void) { return g_err.c_str(); }
@@ -762,7 +830,17 @@ bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const b
   long long chunks_run = 0;
   double fwd_ms = 0.0, tr_ms = 0.0;
   int fwd_launches = 0, tr_launches = 0;
-  if (o.profile) {
+  if (o.profile == 2) {
+    // Every kernel launched directly from the host, a chunk at a time, until the stop flag.
+    for (long long c = 0; c < max_chunks; ++c) {
+      CK(enqueue_chunk(h, p, o, chunk, nullptr));
+      ++chunks_run;
+      DevState hs;
+      CK(cudaMemcpyAsync(&hs, h->b.st, sizeof(DevState), cudaMemcpyDeviceToHost, h->s));
+      CK(cudaStreamSynchronize(h->s));
+      if (hs.done || hs.error) break;
+    }
+  } else if (o.profile) {
     // The chunk, with event-record nodes around the product kernels, is captured into a
     // graph so the events time the kernels without host launch gaps in between.
     while ((int)h->prof.size() < 3 * chunk) {
@@ -863,6 +941,9 @@ bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const b
   if (hs.nonfinite) return set_err(BVLS_ENONFINITE, "y or x0 contains NaN or Inf");
   if (hs.error) return set_err(BVLS_ETIMEOUT, "a device-side wait exceeded its bound; results discarded");
   CK(launch_export(p, h->b, hs.out_slot, h->s));
+  std::vector<RefOut> rout;
+  float ref_ms = 0.f;
+  if (o.refine) TRY(refine_shared(h, 1, h->y_dev, h->m, h->b.xout, h->n, h->b.flags, h->n, p.invL, &rout, &ref_ms));
   CK(cudaMemcpyAsync(x_out, h->b.xout, sizeof(double) * h->n, cudaMemcpyDefault, h->s));
   if (screened_out)
     CK(cudaMemcpyAsync(screened_out, h->b.flags, h->n, cudaMemcpyDefault, h->s));
@@ -887,6 +968,16 @@ bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const b
     const double chunks_done = chunks_run >= 0 ? (double)chunks_run : (double)hs.chunks;
     info->kernel_launches = (fused ? 3.0 : 2.0) + chunks_done * (double)(per_chunk + (chunks_run >= 0 ? 0 : 1));
     info->single_pass = fused ? (pers ? 2 : 1) : 0;
+    if (!rout.empty()) {
+      info->refined = rout[0].refined;
+      info->refine_rounds = rout[0].rounds;
+      info->n_free = rout[0].nfree;
+      info->refine_cg_iters = rout[0].cg_iters;
+      info->kkt = rout[0].kkt;
+      info->refine_ms = ref_ms;
+      info->refine_reason = rout[0].refined ? 0 : rout[0].reason;
+      info->kernel_launches += 2.0;
+    }
   }
   if (!hs.done) return set_err(BVLS_EMAXITER, "stopped after %lld chunks without the stop flag", max_chunks);
   if (!hs.converged) return set_err(BVLS_EMAXITER, "gap %.3e >= tol after %d iterations", hs.gap, hs.k);
@@ -1197,6 +1288,10 @@ extern "C" bvls_status bvls_solve_batched(bvls_handle* h, int B, const float* Y,
   if (hs.error) return set_err(BVLS_ETIMEOUT, "a device-side wait exceeded its bound; results discarded");
   if (!hs.done) return set_err(BVLS_ECUDA, "batched solve stopped after %d chunks without finishing", hs.chunks);
   std::vector<int> st_h(B), it_h(B);
+  std::vector<RefOut> rout;
+  float ref_ms = 0.f;
+  if (o.refine)
+    TRY(refine_shared(h, B, h->bY, h->lda, bb.xout, h->n, bb.flags, h->b_npad, p.invL, &rout, &ref_ms));
   CK(cudaMemcpyAsync(X_out, bb.xout, sizeof(double) * (size_t)B * h->n, cudaMemcpyDefault, h->s));
   if (screened_out)
     CK(cudaMemcpy2DAsync(screened_out, h->n, bb.flags, h->b_npad, h->n, B, cudaMemcpyDefault, h->s));
@@ -1227,6 +1322,18 @@ extern "C" bvls_status bvls_solve_batched(bvls_handle* h, int B, const float* Y,
     info->eval_launches = eval_launches;
     info->kernel_launches =
         1.0 + (chunks_run >= 0 ? (double)chunks_run * (double)per_chunk : (double)hs.chunks * (double)(per_chunk + 1));
+    if (!rout.empty()) {
+      for (const RefOut& r : rout) {
+        info->refine_out_of_rounds += r.reason == 1;
+        info->refine_not_unique += r.reason == 2;
+        if (!r.refined) continue;
+        ++info->n_refined;
+        info->refine_free_max = std::max(info->refine_free_max, r.nfree);
+        info->kkt_max = std::max(info->kkt_max, r.kkt);
+      }
+      info->refine_ms = ref_ms;
+      info->kernel_launches += 2.0;
+    }
   }
   if (nconv < B) return set_err(BVLS_EMAXITER, "%d of %d instances reached max_iter with gap >= tol", B - nconv, B);
   g_err.clear();
@@ -1499,6 +1606,18 @@ extern "C" bvls_status bvls_solve_ragged(int B, const bvls_problem* probs, const
   RCK(alloc(&b.chunks, 1));
   RCK(alloc(&b.act, (size_t)B));
   RCK(alloc(&b.err, 1));
+  // refinement: the original y_k (y' is folded during the solve), scratch, descriptors
+  float* y_orig = nullptr;
+  double *ref_g = nullptr, *ref_xs = nullptr;
+  RefDesc* ref_desc = nullptr;
+  RefOut* ref_out = nullptr;
+  if (o.refine) {
+    RCK(alloc(&y_orig, (size_t)r_tot));
+    RCK(alloc(&ref_g, (size_t)c_tot));
+    RCK(alloc(&ref_xs, (size_t)c_tot));
+    RCK(alloc(&ref_desc, (size_t)B));
+    RCK(alloc(&ref_out, (size_t)B));
+  }
   b.A = A;
   b.inst = d_in;
   b.l2 = d_l2;
@@ -1524,6 +1643,7 @@ extern "C" bvls_status bvls_solve_ragged(int B, const bvls_problem* probs, const
     RCK(cudaMemcpy2DAsync(A + in[k].a_off, sizeof(float) * in[k].lda, q.A, sizeof(float) * q.lda,
                           sizeof(float) * q.m, q.n, cudaMemcpyDefault, s));
     RCK(cudaMemcpyAsync(b.yh + in[k].r_off, q.y, sizeof(float) * q.m, cudaMemcpyDefault, s));
+    if (y_orig) RCK(cudaMemcpyAsync(y_orig + in[k].r_off, q.y, sizeof(float) * q.m, cudaMemcpyDefault, s));
   }
   RCK(cudaMemcpyAsync(d_l, l.data(), sizeof(double) * c_tot, cudaMemcpyHostToDevice, s));
   RCK(cudaMemcpyAsync(d_u, u.data(), sizeof(double) * c_tot, cudaMemcpyHostToDevice, s));
@@ -1746,6 +1866,43 @@ extern "C" bvls_status bvls_solve_ragged(int B, const bvls_problem* probs, const
     nconv += hs[k].converged;
     itmax = std::max(itmax, hs[k].k);
   }
+  std::vector<RefOut> rout;
+  float ref_ms = 0.f;
+  if (o.refine) {
+    std::vector<RefDesc> dh(B);
+    int m_max = 1, f_max = 1;
+    for (int k = 0; k < B; ++k) {
+      RefDesc& d = dh[k];
+      d.A = A + in[k].a_off;
+      d.y = y_orig + in[k].r_off;
+      d.l = d_l + in[k].c_off;
+      d.u = d_u + in[k].c_off;
+      d.x = b.xout + in[k].c_off;
+      d.flags = b.flags + in[k].c_off;
+      d.g = ref_g + in[k].c_off;
+      d.xsave = ref_xs + in[k].c_off;
+      d.step = in[k].invL;
+      d.m = in[k].m;
+      d.n = in[k].n;
+      d.lda = in[k].lda;
+      m_max = std::max(m_max, in[k].m);
+      f_max = std::max(f_max, std::min(in[k].m, in[k].n));
+    }
+    RCK(cudaMemcpyAsync(ref_desc, dh.data(), sizeof(RefDesc) * B, cudaMemcpyHostToDevice, s));
+    cudaEvent_t r0 = nullptr, r1 = nullptr;
+    RCK(cudaEventCreate(&r0));
+    RCK(cudaEventCreate(&r1));
+    cudaError_t e = cudaEventRecord(r0, s);
+    if (e == cudaSuccess) e = launch_refine(ref_params(ref_desc, ref_out, B), m_max, std::min(f_max, kRefMaxFree), s);
+    if (e == cudaSuccess) e = cudaEventRecord(r1, s);
+    rout.resize(B);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rout.data(), ref_out, sizeof(RefOut) * B, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ref_ms, r0, r1);
+    cudaEventDestroy(r0);
+    cudaEventDestroy(r1);
+    RCK(e);
+  }
   for (int k = 0; k < B; ++k) {
     RCK(cudaMemcpyAsync(x_out[k], b.xout + in[k].c_off, sizeof(double) * in[k].n, cudaMemcpyDefault, s));
     if (screened_out && screened_out[k])
@@ -1771,6 +1928,15 @@ extern "C" bvls_status bvls_solve_ragged(int B, const bvls_problem* probs, const
     info->tune_ms = std::chrono::duration<double, std::milli>(t_setup - t_tune0).count();
     info->setup_ms = std::chrono::duration<double, std::milli>(t_setup - t_start).count();
     info->solve_ms = std::chrono::duration<double, std::milli>(t_solve - t_setup).count();
+    for (const RefOut& r : rout) {
+      info->refine_out_of_rounds += r.reason == 1;
+      info->refine_not_unique += r.reason == 2;
+      if (!r.refined) continue;
+      ++info->n_refined;
+      info->refine_free_max = std::max(info->refine_free_max, r.nfree);
+      info->kkt_max = std::max(info->kkt_max, r.kkt);
+    }
+    info->refine_ms = ref_ms;
   }
   if (nconv < B) return set_err(BVLS_EMAXITER, "%d of %d instances reached max_iter with gap >= tol", B - nconv, B);
   g_err.clear();

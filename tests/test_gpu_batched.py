@@ -6,7 +6,8 @@ Each instance of a batch is compared with the oracle's own solve of that instanc
   * zero false screens: every coordinate the GPU fixed sits at that bound in x*, and
     a_j^T theta* has the sign Eq. (screen_cond) requires;
   * the solution agrees with x* to 1e-4 relative (the bar of the reduced-precision forms:
-    the iterates are float32 and the non-evaluation steps use bf16 tensor-core products).
+    the non-evaluation steps use bf16 tensor-core products), and after the free-set
+    refinement (opts.refine) to 1e-7 relative.
 """
 import numpy as np
 import pytest
@@ -48,7 +49,7 @@ def certified_optimum(A, y, l, u, tol):
     return xs
 
 
-def check_instance(A, y, l, u, x, scr, gap, status, xs, tol, name):
+def check_instance(A, y, l, u, x, scr, gap, status, xs, tol, name, xtol=1e-4):
     assert status == 0 and gap < tol, (name, status, gap)
     assert np.all(x >= l) and np.all(x <= u), name
     Pg, Ps = O.primal_objective(A, y, x), O.primal_objective(A, y, xs)
@@ -59,7 +60,7 @@ def check_instance(A, y, l, u, x, scr, gap, status, xs, tol, name):
     assert np.all(np.abs(xs[upp] - u[upp]) <= 1e-12) and np.all(g[upp] > 0), name
     assert np.all(x[low] == l[low]) and np.all(x[upp] == u[upp]), name
     err = float(np.abs(x - xs).max())
-    assert err <= 1e-4 * max(1.0, float(np.abs(xs).max())), (name, err)
+    assert err <= xtol * max(1.0, float(np.abs(xs).max())), (name, err)
 
 
 @pytest.mark.parametrize("precision,tol", [("fp32", 1e-6), ("fp32x2", 1e-8)])
@@ -70,10 +71,13 @@ def test_dirichlet_shared_matches_oracle(P, precision, tol):
     X, S, gaps, its, sts, info, st = batched(P, p, tol=tol, precision=precision)
     assert st == P.BVLS_OK and info["n_converged"] == 12
     assert info["dual"] == "scaling"
+    XR, SR, gR, iR, sR, infoR, stR = batched(P, p, tol=tol, precision=precision, refine=True)
+    assert infoR["n_refined"] == 12 and np.array_equal(iR, its) and np.array_equal(SR, S)
     for b in range(12):
         y = p.y[b].astype(np.float64)
         xs = certified_optimum(A, y, p.l, p.u, 1e-10)
         check_instance(A, y, p.l, p.u, X[b], S[b], gaps[b], sts[b], xs, tol, f"inst{b}")
+        check_instance(A, y, p.l, p.u, XR[b], SR[b], gR[b], sR[b], xs, tol, f"inst{b}", xtol=1e-7)
     assert (S > 0).sum() > 0.5 * S.size   # most coordinates are fixed at 0 by the end
 
 
@@ -82,26 +86,28 @@ def test_nnls_translation_ragged_tiles(P):
     the last ragged) and B = 150 instances (two instance tiles, the last ragged)."""
     p = W.nnls_shared(96, 300, 150, 0.06, 1.0, 2)
     A = p.A.astype(np.float64)
-    X, S, gaps, its, sts, info, st = batched(P, p, tol=1e-7, precision="fp32x2")
+    X, S, gaps, its, sts, info, st = batched(P, p, tol=1e-7, precision="fp32x2", refine=True)
     assert st == P.BVLS_OK and info["dual"] == "translation"
     assert len(set(its.tolist())) > 1          # uneven convergence: instances retire apart
+    assert info["n_refined"] == 150, info
     for b in list(range(0, 150, 13)) + [149]:
         y = p.y[b].astype(np.float64)
         xs = certified_optimum(A, y, p.l, p.u, 1e-9)
-        check_instance(A, y, p.l, p.u, X[b], S[b], gaps[b], sts[b], xs, 1e-7, f"inst{b}")
+        check_instance(A, y, p.l, p.u, X[b], S[b], gaps[b], sts[b], xs, 1e-7, f"inst{b}", xtol=1e-7)
 
 
 def test_gaussian_box_both_bounds(P):
     """BVLS with both bounds active (N(0,1) data, box [-0.05, 0.05]): fixes at l and at u."""
     p = W.bvls_box_shared(80, 150, 40, 0.05, 3)
     A = p.A.astype(np.float64)
-    X, S, gaps, its, sts, info, st = batched(P, p, tol=1e-8, precision="fp32x2")
+    X, S, gaps, its, sts, info, st = batched(P, p, tol=1e-8, precision="fp32x2", refine=True)
     assert st == P.BVLS_OK
     assert (S == 1).sum() > 0 and (S == 2).sum() > 0
+    assert info["n_refined"] == 40, info
     for b in range(0, 40, 5):
         y = p.y[b].astype(np.float64)
         xs = certified_optimum(A, y, p.l, p.u, 1e-11)
-        check_instance(A, y, p.l, p.u, X[b], S[b], gaps[b], sts[b], xs, 1e-8, f"inst{b}")
+        check_instance(A, y, p.l, p.u, X[b], S[b], gaps[b], sts[b], xs, 1e-8, f"inst{b}", xtol=1e-7)
 
 
 def test_screening_off_reaches_the_same_optimum(P):
@@ -175,3 +181,17 @@ def test_repeat_calls_are_identical_and_nonfinite_is_rejected(P):
     c = s.solve_batched(Y, tol=1e-8)   # the handle stays usable
     assert torch.equal(a[0], c[0])
     s.close()
+
+
+def test_full_size_batch_refined_against_certified_optima(P):
+    """The full 4096-instance batch of the 224 x 512 BVLS workload with refinement: sampled
+    instances element by element against FP64 optima certified by the optimality conditions."""
+    p = W.bvls_dirichlet_shared(224, 512, 4096, 8, 0.005, 0)
+    A = p.A.astype(np.float64)
+    X, S, gaps, its, sts, info, st = batched(P, p, tol=1e-6, precision="fp32x2", refine=True)
+    assert st == P.BVLS_OK and info["n_converged"] == 4096
+    assert info["n_refined"] >= 4090, info
+    for b in [0, 1, 777, 2048, 4095]:
+        y = p.y[b].astype(np.float64)
+        xs = certified_optimum(A, y, p.l, p.u, 1e-10)
+        check_instance(A, y, p.l, p.u, X[b], S[b], gaps[b], sts[b], xs, 1e-6, f"inst{b}", xtol=1e-7)

@@ -109,9 +109,10 @@ def test_result_matches_oracle_and_screens_safely(P, name):
     tol = 1e-6 if name.startswith("mixed") else 1e-8
     ref = O.solve(A, y, p.l, p.u, tol=tol, screen_every=10, L=L, t=t)
     assert ref.converged
-    x, scr, info, st = gpu_solve(P, p, t=t, tol=tol, screen_every=10, lipschitz=L)
+    x, scr, info, st = gpu_solve(P, p, t=t, tol=tol, screen_every=10, lipschitz=L, refine=True)
     assert st == P.BVLS_OK and info["converged"] and info["gap"] < tol
     assert abs(info["iters"] - ref.iters) <= 20, (info["iters"], ref.iters)
+    assert info["refined"] == 1, info
     xs = certified_optimum(A, y, p.l, p.u, ref.x)
     th = y - A @ xs
     g = A.T @ th
@@ -124,7 +125,28 @@ def test_result_matches_oracle_and_screens_safely(P, name):
     Pg = O.primal_objective(A, y, x)
     Ps = O.primal_objective(A, y, xs)
     assert Ps - 1e-12 <= Pg <= Ps + tol * 1.0001 + 1e-12
-    assert float(np.abs(x - xs).max()) <= 1e-5 * max(1.0, float(np.abs(xs).max()))
+    # the refined solution against the certified optimum: the FP64-checked bar
+    assert float(np.abs(x - xs).max()) <= 1e-7 * max(1.0, float(np.abs(xs).max())), float(np.abs(x - xs).max())
+    assert info["kkt"] <= 1e-9 * (1 + np.abs(A.T @ y).max())
+
+
+@pytest.mark.parametrize("name", ["nnls_abs_300x700", "bvls_t2_200x500", "mixed_180x140", "bvls_dir_224x512"])
+def test_refinement_from_a_coarse_gap(P, name):
+    """Refinement started from a coarse iterate (gap 1e-3): the active-set rounds must still
+    land on the certified optimum, or decline and return the solver's iterate unchanged."""
+    p, t = CASES[name]()
+    A, y = _f64(p)
+    L = _L(A)
+    ref = O.solve(A, y, p.l, p.u, tol=1e-9 if not name.startswith("mixed") else 1e-6, screen_every=10, L=L, t=t)
+    xs = certified_optimum(A, y, p.l, p.u, ref.x)
+    x0, s0, i0, st0 = gpu_solve(P, p, t=t, tol=1e-3, lipschitz=L)
+    x1, s1, i1, st1 = gpu_solve(P, p, t=t, tol=1e-3, lipschitz=L, refine=True)
+    assert i1["iters"] == i0["iters"] and np.array_equal(s0, s1)
+    if i1["refined"]:
+        assert float(np.abs(x1 - xs).max()) <= 1e-7 * max(1.0, float(np.abs(xs).max()))
+    else:
+        assert np.array_equal(x0, x1)
+    assert i1["refine_rounds"] >= 1 and i1["refine_ms"] > 0
 
 
 @pytest.mark.parametrize("name", ["nnls_abs_300x700", "bvls_t2_200x500", "mixed_180x140"])
@@ -157,6 +179,9 @@ def test_persistent_launch_matches_per_iteration_launches(P, name, K):
     c = gpu_solve(P, p, t=t, tol=0.0, max_iter=120, screen_every=K, lipschitz=L, profile=True)
     assert c[2]["tr_launches"] == 120 // K and c[2]["tr_ms"] > 0 and c[2]["fwd_launches"] == 0
     assert float(np.abs(c[0] - a[0]).max()) <= 1e-10 * max(1.0, float(np.abs(b[0]).max()))
+    # every kernel launched directly from the host (no graph): the same iterates bit for bit
+    d = gpu_solve(P, p, t=t, tol=0.0, max_iter=120, screen_every=K, lipschitz=L, profile=2)
+    assert d[2]["iters"] == 120 and np.array_equal(d[0], a[0]) and np.array_equal(d[1], a[1])
 
 
 def test_screened_and_unscreened_follow_the_same_iterates(P):
@@ -295,11 +320,40 @@ def test_degenerate_single_instance_full_size(P):
     assert b[2]["iters"] == info["iters"]
 
 
+def test_degenerate_refinement_never_worsens(P):
+    """Where the optimum is not unique (Gaussian n >> m, theta* = 0) the free set may exceed
+    m: the refinement either declines and returns the solver's iterate, or returns a point
+    that satisfies the optimality conditions."""
+    p = W.nnls_gaussian(100, 200, 0.1, 0.01, 0)
+    A, y = _f64(p)
+    a = gpu_solve(P, p, tol=1e-9)
+    b = gpu_solve(P, p, tol=1e-9, refine=True)
+    if b[2]["refined"]:
+        assert np.all(b[0] >= 0)
+        assert O.kkt_residual(A, y, b[0], p.l, p.u) <= 1e-8 * (1 + np.abs(A.T @ y).max())
+        assert O.primal_objective(A, y, b[0]) <= O.primal_objective(A, y, a[0]) + 1e-12
+    else:
+        assert np.array_equal(a[0], b[0])
+
+
 def test_screenable_single_instance_full_size(P):
-    """2000 x 10000 |N(0,1)| NNLS (Table 1 family): certified gap and safe screens at full size."""
+    """2000 x 10000 |N(0,1)| NNLS (Table 1 family): certified gap and safe screens at full size,
+    and the refined solution element by element against an FP64 optimum certified by the
+    optimality conditions.  The FP64 oracle's own solve at this size takes tens of minutes, so
+    its polish step (an FP64 least-squares solve on the free set) takes the free set of the
+    GPU's result; the CPU check of the optimality conditions then certifies that the polished
+    point is the optimum whatever its free set came from."""
     p = W.nnls_abs_gaussian(2000, 10000, 0.05, 1.0, 0)
     A, y = _f64(p)
-    x, scr, info, st = gpu_solve(P, p, tol=1e-6)
+    x0, scr0, info0, st0 = gpu_solve(P, p, tol=1e-6)
+    x, scr, info, st = gpu_solve(P, p, tol=1e-6, refine=True)
+    assert info["refined"] == 1 and info["iters"] == info0["iters"]
+    xs = O.polish(A, y, x, p.l, p.u, tau=1e-7)
+    assert np.all(xs >= 0)
+    assert O.kkt_residual(A, y, xs, p.l, p.u) < 1e-9 * (1 + np.abs(A.T @ y).max())
+    assert float(np.abs(x - xs).max()) <= 1e-7 * max(1.0, float(np.abs(xs).max()))
+    g_s = A.T @ (y - A @ xs)
+    assert np.all(g_s[scr == 1] < 0) and np.all(xs[scr == 1] == 0)
     assert st == P.BVLS_OK and info["dual"] == "translation"
     assert np.all(x >= 0) and np.all(x[scr == 1] == 0)
     t = -np.ones(p.m)

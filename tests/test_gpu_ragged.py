@@ -31,7 +31,7 @@ def run(P, probs, device=True, **kw):
     return P.solve_ragged(items, **kw)
 
 
-def check(p, x, scr, gap, status, tol):
+def check(p, x, scr, gap, status, tol, xtol=None):
     A, y = p.A.astype(np.float64), p.y.astype(np.float64)
     assert status == 0 and gap < tol, (p.name, status, gap)
     ref = O.solve(A, y, p.l, p.u, tol=min(tol, 1e-9) * 1e-1)
@@ -39,6 +39,11 @@ def check(p, x, scr, gap, status, tol):
     Pg = O.primal_objective(A, y, x)
     assert np.all(x >= p.l) and np.all(x <= p.u)
     assert Pg <= Ps + gap * (1 + 1e-9) + ref.gap + 1e-12, (p.name, Pg - Ps, gap)
+    if xtol is not None:
+        xs = O.polish(A, y, ref.x, p.l, p.u, tau=1e-7)
+        assert O.kkt_residual(A, y, xs, p.l, p.u) < 1e-9 * (1 + np.abs(A.T @ y).max())
+        err = float(np.abs(x - xs).max())
+        assert err <= xtol * max(1.0, float(np.abs(xs).max())), (p.name, err)
     if scr.any():
         xs = O.polish(A, y, ref.x, p.l, p.u, tau=1e-7)
         assert O.kkt_residual(A, y, xs, p.l, p.u) < 1e-8 * (1 + np.abs(A.T @ y).max())
@@ -49,16 +54,31 @@ def check(p, x, scr, gap, status, tol):
         assert np.all(x[low] == p.l[low]) and np.all(x[upp] == p.u[upp])
 
 
+def unique_optimum(p):
+    """Whether the FP64 optimum is unique: its free set has fewer than m coordinates and
+    independent columns (else theta* = y - A x* is unique but x* is not)."""
+    A, y = p.A.astype(np.float64), p.y.astype(np.float64)
+    ref = O.solve(A, y, p.l, p.u, tol=1e-10)
+    F = O.free_set(ref.x, p.l, p.u, 1e-7)
+    return F.size < p.m and np.linalg.matrix_rank(A[:, F]) == F.size
+
+
 def test_mixed_uneven_nondegenerate_matches_oracle(P):
-    """|N| matrices with unit noise (unique optima, screenable): NNLS on even k (dual
-    translation with t = -1), BVLS on [-1, 1] on odd k (dual scaling)."""
+    """|N| matrices with unit noise (screenable): NNLS on even k (dual translation with
+    t = -1, unique optima), BVLS on [-1, 1] on odd k (dual scaling; several of these have
+    P* = 0 and a free set larger than m, so x* is not unique).  The refinement returns the
+    optimum to 1e-7 where it is unique and declines elsewhere."""
     probs = W.mixed_uneven(10, 1, m_lo=40, m_hi=160, abs_matrix=True, noise=1.0)
-    xs, ss, gaps, its, sts, info, st = run(P, probs, tol=1e-7)
+    xs, ss, gaps, its, sts, info, st = run(P, probs, tol=1e-7, refine=True)
     assert st == P.BVLS_OK and info["n_converged"] == 10
     assert info["n_translation"] == 5 and info["n_zero"] == 0
+    uniq = [unique_optimum(p) for p in probs]
+    assert all(uniq[0::2]) and not all(uniq)
+    assert info["n_refined"] == sum(uniq), (info["n_refined"], info["refine_out_of_rounds"], info["refine_not_unique"])
+    assert info["refine_not_unique"] == 10 - sum(uniq)
     assert len(set(its.tolist())) > 1
     for k, p in enumerate(probs):
-        check(p, xs[k], ss[k], gaps[k], sts[k], 1e-7)
+        check(p, xs[k], ss[k], gaps[k], sts[k], 1e-7, xtol=1e-7 if uniq[k] else None)
     assert sum(int((s > 0).sum()) for s in ss) > 0
 
 
@@ -124,3 +144,33 @@ def test_autotuner_picks_tile_and_period_and_keeps_them(P):
         A, y = p.A.astype(np.float64), p.y.astype(np.float64)
         Pa, Pf = O.primal_objective(A, y, a[0][k]), O.primal_objective(A, y, fixed[0][k])
         assert abs(Pa - Pf) <= a[2][k] + fixed[2][k] + 1e-12
+
+
+def test_full_range_uneven_batch_sampled(P):
+    """The full size range of the uneven workload (m_k up to 1024, n_k up to 8 m_k) on the
+    screenable |N| family: every instance certified, then the refined solutions of sampled
+    NNLS instances (the largest and two others) element by element against FP64 optima certified
+    by the optimality conditions.  The oracle's own solve at these sizes is too slow for a
+    test, so its polish step (an FP64 least-squares solve on the free set) takes the free set
+    of the GPU's result; the CPU check of the optimality conditions then certifies that the
+    polished point is the optimum whatever its free set came from."""
+    probs = W.mixed_uneven(24, 5, m_lo=64, m_hi=1024, abs_matrix=True, noise=1.0)
+    a = run(P, probs, tol=1e-6)
+    b = run(P, probs, tol=1e-6, refine=True)
+    assert a[6] == P.BVLS_OK and b[6] == P.BVLS_OK
+    assert max(p.m for p in probs) > 900
+    # the NNLS half has unique optima; the BVLS half on [-1, 1] is mostly degenerate (P* = 0)
+    assert b[5]["n_refined"] >= 12, (b[5]["n_refined"], b[5]["refine_out_of_rounds"], b[5]["refine_not_unique"])
+    assert b[5]["n_refined"] + b[5]["refine_not_unique"] == 24
+    big = int(np.argmax([p.m * p.n if k % 2 == 0 else 0 for k, p in enumerate(probs)]))
+    for k in sorted({big, 0, 2}):
+        p = probs[k]
+        A, y = p.A.astype(np.float64), p.y.astype(np.float64)
+        xs = O.polish(A, y, b[0][k], p.l, p.u, tau=1e-7)
+        assert O.kkt_residual(A, y, xs, p.l, p.u) < 1e-9 * (1 + np.abs(A.T @ y).max()), p.name
+        assert np.all(xs >= p.l - 1e-12) and np.all(xs <= p.u + 1e-12)
+        err = float(np.abs(b[0][k] - xs).max())
+        assert err <= 1e-7 * max(1.0, float(np.abs(xs).max())), (p.name, err)
+        g = A.T @ (y - A @ xs)
+        low, upp = b[1][k] == 1, b[1][k] == 2
+        assert np.all(g[low] < 0) and np.all(g[upp] > 0)
