@@ -208,6 +208,53 @@ def timed_solves(solver, y_dev, flush, stream, steps, warmup, variants, dual_poi
     return out
 
 
+OPTIMA = os.path.join(ROOT, "tests", "golden", "bench_optima.json")
+
+
+def stored_optimum(workload, key="single"):
+    """The FP64 oracle's optimum of a workload (instance `key` of a batch), written by
+    tests/golden/make_bench_optima.py: unique optima as sparse x*, else only P*."""
+    if not os.path.exists(OPTIMA):
+        return None
+    return json.load(open(OPTIMA)).get(workload, {}).get(str(key))
+
+
+def error_vs_optimum(A64, y64, x, rec, x_ref=None):
+    """Error of a GPU result against the stored FP64 optimum rec (plain numpy arithmetic).
+
+    Unique optimum: ||x - x*||_inf / max(1, ||x*||_inf) for the solver's result and for its
+    refined one, and P(x) - P*.  Otherwise (P* = 0, theta* = 0 on the degenerate workloads)
+    P(x), which bounds P(x) - P*, and ||y - A x|| = ||theta - theta*||."""
+    r = y64 - A64 @ x
+    out = {"P": 0.5 * float(r @ r)}
+    if rec is not None and rec.get("unique"):
+        xs = np.zeros(A64.shape[1])
+        xs[np.asarray(rec["x_star_idx"], dtype=np.int64)] = rec["x_star_val"]
+        scale = max(1.0, float(np.abs(xs).max()))
+        out["P_minus_Pstar"] = out["P"] - rec["P_star"]
+        out["x_err_inf_rel"] = float(np.abs(x - xs).max()) / scale
+        if x_ref is not None:
+            out["x_err_inf_rel_refined"] = float(np.abs(x_ref - xs).max()) / scale
+    else:
+        out["note"] = "optimum not unique (P* = 0): P(x) bounds P(x) - P*, ||y - A x|| = ||theta - theta*||"
+        out["theta_err_norm"] = float(np.linalg.norm(r))
+    return out
+
+
+def solve_errors(solver, y_dev, p, opts_kw, rec):
+    """Untimed re-run of a timed solve (same options: the same iterates) and of the same solve
+    with the free-set refinement, then the errors of both against the stored FP64 optimum."""
+    from paper_2202_07258_gb300 import make_opts
+    x, s, info, st = solver.solve(y_dev, opts=make_opts(tol=TOL, screen_every=K_SCREEN, **opts_kw))
+    xr, sr, infor, str_ = solver.solve(y_dev, opts=make_opts(tol=TOL, screen_every=K_SCREEN, refine=True, **opts_kw))
+    A64, y64 = p.A.astype(np.float64), p.y.astype(np.float64).reshape(-1)
+    err = error_vs_optimum(A64, y64, x.cpu().numpy(), rec, xr.cpu().numpy() if infor["refined"] else None)
+    err.update({"gap_certified": info["gap"], "refined": int(infor["refined"]), "refine_ms": infor["refine_ms"],
+                "refine_rounds": infor["refine_rounds"], "refine_reason": infor["refine_reason"],
+                "kkt_refined": infor["kkt"]})
+    return err
+
+
 def kernel_hash(files=None):
     """Hash of the CUDA sources a kernel is built and configured from (the listed files in
     order, else every source): stored ncu counters apply only to the kernels they measured."""
@@ -284,6 +331,16 @@ def roofline_from_info(info, m, traffic_key=None):
 BATCH = dict(m=224, n=512, B=4096, k_support=8, noise=0.005, seed=0)
 
 
+def _hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return float(json.load(open(path))["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+HBM_PEAK = _hbm_peak()
+
+
 def ragged_leg(dev, stream, B=512):
     """Mixed NNLS/BVLS batch of uneven sizes (each instance its own A_k iid N(0,1), m_k ~
     U{64..1024}, n_k ~ U{2m_k..8m_k}, x0 10% nonzeros, even k NNLS, odd k BVLS [-1,1] with
@@ -314,8 +371,38 @@ def ragged_leg(dev, stream, B=512):
                 "autotuned": {"tile_cols": info["tile_cols"], "screen_every": info["screen_every"],
                               "tune_ms": info["tune_ms"]},
                 "screened_fraction_end": float(sum(int((s > 0).sum()) for s in ss) / max(1, sum(len(s) for s in ss))),
+                "_rows_cols": info["sum_rows_cols"],
                 "dual_modes": {"translation": info["n_translation"], "zero": info["n_zero"]}}
         res["speedup"] = res["unscreened"]["solve_ms"] / res["screened"]["solve_ms"]
+        # the whole solve against HBM: the A_k elements its iterations read (counted on the
+        # device: sum over iterations and active instances of m_k |S_k|, 4 bytes each) over
+        # the solve time (all of its kernels: tiles, residuals, gaps, work lists)
+        for key in ("screened", "unscreened"):
+            rr = res[key]
+            a_bytes = 4.0 * rr.pop("_rows_cols")
+            ach = a_bytes / (rr["solve_ms"] / 1000.0) / 1e9
+            rr["roofline_whole_solve"] = {"bound": "hbm", "kernel": "whole solve (k_rpass, k_rresid, k_rgap, k_rtiles)",
+                                          "achieved": ach, "peak": HBM_PEAK[0], "peak_source": HBM_PEAK[1],
+                                          "unit": "GB/s", "frac": ach / HBM_PEAK[0], "A_bytes_read": a_bytes}
+        # error against FP64 optima on sampled instances (refined solve; untimed)
+        xr, sr, gr, itr, str_, infr, _ = solve_ragged(items, tol=TOL, screen_every=0, max_iter=mx, refine=True,
+                                                      stream=stream.cuda_stream)
+        probs = W.mixed_uneven(b, 0, abs_matrix=absm, noise=noise)
+        sample = sorted({0, 1, 2, 3, b - 2, b - 1})
+        errs = {}
+        for k in sample:
+            q = probs[k]
+            rec = stored_optimum("mixed_uneven_abs_B64", k) if absm else None
+            errs[k] = error_vs_optimum(q.A.astype(np.float64), q.y.astype(np.float64), xs[k], rec, xr[k])
+        del probs
+        cert = [e for e in errs.values() if "x_err_inf_rel" in e]
+        res["err_vs_oracle"] = {
+            "sample": sample, "certified": len(cert),
+            "x_err_inf_rel_max": max((e["x_err_inf_rel"] for e in cert), default=None),
+            "x_err_inf_rel_refined_max": max((e.get("x_err_inf_rel_refined", np.inf) for e in cert), default=None),
+            "P_max_not_unique": max((e["P"] for e in errs.values() if "x_err_inf_rel" not in e), default=None),
+            "refine": {"n_refined": infr["n_refined"], "not_unique": infr["refine_not_unique"],
+                       "out_of_rounds": infr["refine_out_of_rounds"], "refine_ms": infr["refine_ms"]}}
         out[name] = res
         del items
         torch.cuda.empty_cache()
@@ -345,6 +432,8 @@ def table2_leg(dev, stream, flush, steps):
                 "gap": infos[-1]["gap"],
                 "avg_preserved_fraction": infos[-1]["sum_preserved"] / max(1, infos[-1]["iters"]) / 2000}
         res["speedup"] = res["screened"]["instances_per_s"] / res["unscreened"]["instances_per_s"]
+        res["err_vs_oracle"] = solve_errors(solver, y, p, dict(screening=True, algorithm=alg),
+                                            stored_optimum("bvls_table2_1000x2000"))
         out[alg] = res
     solver.close()
     return out
@@ -416,6 +505,24 @@ def batched_leg(dev, stream, flush, steps, warmup=1):
                     "iters_max": info["iters_max"], "iters_mean": float(its.double().mean()),
                     "gap_max": float(gaps.max()), "preserved_fraction": info["sum_preserved"] /
                     max(1.0, info["sum_eval"] * c["n"]), "kernel_launches": info["kernel_launches"]}
+    # error against FP64 optima on sampled instances: the timed solve re-run untimed, and the
+    # same solve with the free-set refinement (its kernel time reported)
+    Xu, *_ = solver.solve_batched(Y, opts=make_opts(tol=TOL, screen_every=K_SCREEN, precision="fp32"))
+    Xr, Sr, gr, itr, str_, infr, _ = solver.solve_batched(Y, opts=make_opts(tol=TOL, screen_every=K_SCREEN,
+                                                                            precision="fp32", refine=True))
+    Xu, Xr = Xu.cpu().numpy(), Xr.cpu().numpy()
+    A64 = p.A.astype(np.float64)
+    sample = [0, 1, 2, 3, 1024, 2047, 3071, 4095]
+    errs = [error_vs_optimum(A64, p.y[b].astype(np.float64), Xu[b],
+                             stored_optimum("bvls_dirichlet_224x512_B4096", b), Xr[b]) for b in sample]
+    cert = [e for e in errs if "x_err_inf_rel" in e]
+    out["err_vs_oracle"] = {
+        "sample": sample, "certified": len(cert),
+        "x_err_inf_rel_max": max((e["x_err_inf_rel"] for e in cert), default=None),
+        "x_err_inf_rel_refined_max": max((e.get("x_err_inf_rel_refined", np.inf) for e in cert), default=None),
+        "P_minus_Pstar_max": max((e["P_minus_Pstar"] for e in cert), default=None),
+        "refine": {"n_refined": infr["n_refined"], "of": c["B"], "refine_ms": infr["refine_ms"],
+                   "kkt_max": infr["kkt_max"], "free_set_max": infr["refine_free_max"]}}
     opts = make_opts(tol=TOL, screen_every=K_SCREEN, precision="fp32", profile=True)
     X, S, gaps, its, sts, info, st = solver.solve_batched(Y, opts=opts)
     solver.close()
@@ -504,6 +611,13 @@ def ncu_region(args):
         opts = make_opts(tol=0.0, screen_every=K_SCREEN, max_iter=20, screening=False, profile=True,
                          precision=HEAD_PRECISION)
         run = lambda: s.solve(y, opts=opts)
+    elif args.ncu_region == "ragged":
+        from paper_2202_07258_gb300 import solve_ragged
+        probs = W.mixed_uneven(512, 0, abs_matrix=False, noise=0.01)
+        items = [(torch.from_numpy(q.A).to(dev), torch.from_numpy(q.y).to(dev), q.l, q.u) for q in probs]
+        del probs
+        s = None
+        run = lambda: solve_ragged(items, tol=TOL, screen_every=K_SCREEN, profile=2)
     else:
         c = BATCH
         p = W.bvls_dirichlet_shared(c["m"], c["n"], c["B"], c["k_support"], c["noise"], c["seed"])
@@ -518,7 +632,8 @@ def ncu_region(args):
     run()
     torch.cuda.synchronize()
     torch.cuda.cudart().cudaProfilerStop()
-    s.close()
+    if s is not None:
+        s.close()
 
 
 def run_ours(args):
@@ -580,6 +695,16 @@ def run_ours(args):
     var_s, var_u, var_o = var["screened"], var["unscreened"], var["oracle_dual"]
 
     value, total_ms = replica_rate(sum(scr["times_ms"]), args.steps, world, dev)
+    err_head = solve_errors(head["solver"], head["y"], head["p"], dict(precision=HEAD_PRECISION), None) \
+        if rank == 0 else None
+    err_var = None
+    if rank == 0:
+        pv = make_problem(VARIANT, 0)
+        with torch.cuda.stream(stream):
+            sv = Solver(torch.from_numpy(pv.A).to(dev), pv.l, pv.u, stream=stream.cuda_stream)
+        err_var = solve_errors(sv, torch.from_numpy(pv.y).to(dev), pv, {}, stored_optimum(VARIANT))
+        sv.close()
+        del pv
 
     roof = roofline(head["solver"], head["y"], 2000) if rank == 0 else None
     batched = batched_leg(dev, stream, flush, max(2, min(args.steps, 5))) if (rank == 0 and not args.no_batched) else None
@@ -607,7 +732,7 @@ def run_ours(args):
             "screened": {"iters": info["iters"], "gap": info["gap"], "dual": info["dual"],
                          "n_preserved_end": info["n_preserved"],
                          "avg_preserved_fraction": info["sum_preserved"] / max(1, info["iters"]) / 10000,
-                         "setup_s": scr["setup_s"]},
+                         "setup_s": scr["setup_s"], "err_vs_oracle": err_head},
             "unscreened": {"value": world * args.steps / (sum(uns["times_ms"]) / 1000.0),
                            "ms_per_step": sum(uns["times_ms"]) / args.steps, "iters": uns["info"]["iters"],
                            "gap": uns["info"]["gap"]},
@@ -618,7 +743,7 @@ def run_ours(args):
                 "speedup": sum(var_u["times_ms"]) / len(var_u["times_ms"]) / (sum(var_s["times_ms"]) / len(var_s["times_ms"])),
                 "iters_screened": var_s["info"]["iters"], "iters_unscreened": var_u["info"]["iters"],
                 "avg_preserved_fraction": var_s["info"]["sum_preserved"] / max(1, var_s["info"]["iters"]) / 10000,
-                "gap": var_s["info"]["gap"],
+                "gap": var_s["info"]["gap"], "err_vs_oracle": err_var,
                 "oracle_dual_point": {
                     "note": "screening informed with theta* = y - A x* (Section 5's oracle-dual-point experiment)",
                     "instances_per_s": 1000.0 * len(var_o["times_ms"]) / sum(var_o["times_ms"]),
@@ -647,7 +772,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-batched", action="store_true", help="skip the shared-A batched leg")
-    ap.add_argument("--ncu-region", choices=["single", "batched", "hbm"], default=None,
+    ap.add_argument("--ncu-region", choices=["single", "batched", "hbm", "ragged"], default=None,
                     help="profiling aid: run one warm solve of that leg between cudaProfilerStart/Stop "
                          "(for ncu --profile-from-start off) and exit without a bench line")
     args = ap.parse_args()

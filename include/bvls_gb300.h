@@ -353,6 +353,8 @@ typedef struct {
   double refine_ms;     /* refinement kernel time (CUDA events) */
   int refine_out_of_rounds; /* instances declined after the last round */
   int refine_not_unique;    /* instances declined because |F| > min(m, 2048) */
+  double sum_rows_cols;     /* sum over the solve's iterations and active instances of
+                               m_k |S_k|: the elements of A_k read (4 bytes each) */
 } bvls_ragged_info;
 
 /*
@@ -363,7 +365,8 @@ typedef struct {
  * (every u_j finite), the translation with t = -1 when it is interior (Proposition 2), else
  * theta = 0.  Products are float32 data with double-float accumulation.
  *   probs         host; B problem descriptors (1 <= m_k <= 1024, n_k >= 1).
- *   opts          host or NULL: tol, screen_every, max_iter, screening, restart are used;
+ *   opts          host or NULL: tol, screen_every, max_iter, screening, restart, refine and
+ *                 profile (2: every kernel launched directly, no CUDA graph) are used;
  *                 screen_every = 0 lets the autotuner pick it from {5, 10, 20} by timing 20
  *                 iterations of each from the start point.  The tile width of the work list
  *                 is always picked by timing eight iterations with 8, 16 and 32 columns (the
@@ -417,6 +420,18 @@ BVLS_API bvls_status bvls_solve_static(const float* A, int m, int n, int lda, co
                                        const double* u, const float* y, const double* x0,
                                        const bvls_opts* opts, void* stream, double* x_out,
                                        uint8_t* screened_out, bvls_info* info);
+
+/*
+ * Testing hook of the failure path; the paper has no counterpart.  Sets the bound, in SM
+ * clock cycles, of the grid-barrier waits of bvls_solve's persistent pass on this handle
+ * (cycles <= 0 restores the default of 4e9 cycles, about 2 s).  A wait that runs out records
+ * an error instead of waiting on: every CTA leaves its iteration loop at its next barrier,
+ * after the bulk copies it has issued have landed, and bvls_solve returns BVLS_ETIMEOUT with
+ * the outputs untouched; the handle stays usable.  A bound far below the time of one
+ * iteration makes every solve in the persistent form time out: the hook exists so that tests
+ * can drive that path without a GPU fault.  Discards the handle's cached solve graphs.
+ */
+BVLS_API bvls_status bvls_set_grid_wait(bvls_handle* h, long long cycles);
 
 /* Release the handle and its device memory (NULL is ignored). */
 BVLS_API void bvls_destroy(bvls_handle* h);

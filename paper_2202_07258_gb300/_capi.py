@@ -23,7 +23,7 @@ DUAL_NAMES = {0: "scaling", 1: "translation", 2: "zero"}
 # Every symbol the header declares; tests check that the library exports all of them.
 EXPORTED = ("bvls_default_opts", "bvls_setup", "bvls_solve", "bvls_destroy", "bvls_last_error",
             "bvls_solve_static", "bvls_solve_batched", "bvls_backward_default_opts", "bvls_backward",
-            "bvls_solve_ragged")
+            "bvls_solve_ragged", "bvls_set_grid_wait")
 
 
 class bvls_opts(ctypes.Structure):
@@ -156,6 +156,7 @@ class bvls_ragged_info(ctypes.Structure):
         ("refine_ms", ctypes.c_double),
         ("refine_out_of_rounds", ctypes.c_int),
         ("refine_not_unique", ctypes.c_int),
+        ("sum_rows_cols", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -200,8 +201,14 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                       ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), vp, vp, vp,
                                       ctypes.POINTER(bvls_ragged_info)]
     lib.bvls_solve_ragged.restype = ci
+    lib.bvls_set_grid_wait.argtypes = [vp, ctypes.c_longlong]
+    lib.bvls_set_grid_wait.restype = ci
     _lib = lib
     return lib
+
+
+def bvls_set_grid_wait(h: int, cycles: int) -> int:
+    return load().bvls_set_grid_wait(h, int(cycles))
 
 
 def bvls_default_opts() -> bvls_opts:

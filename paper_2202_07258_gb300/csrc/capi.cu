@@ -115,6 +115,7 @@ struct bvls_handle {
   RefDesc* ref_desc = nullptr;
   RefOut* ref_out = nullptr;
   cudaEvent_t ref_ev[2] = {nullptr, nullptr};
+  long long grid_wait = kGridWaitCycles;  // bound of the persistent pass's grid-barrier waits
 };
 
 namespace {
@@ -239,6 +240,7 @@ Params make_params(const bvls_handle* h, const bvls_opts& o, int max_iter) {
   p.fwd_chunks = h->fwd_chunks;
   p.fwd_tiles = h->fwd_tiles;
   p.mom = h->mom;
+  p.grid_wait = h->grid_wait;
   return p;
 }
 
@@ -463,6 +465,16 @@ void bvls_default_opts(bvls_opts* o) {
 const char* bvls_last_error(void) { return g_err.c_str(); }
 
 void bvls_destroy(bvls_handle* h) { free_handle(h); }
+
+bvls_status bvls_set_grid_wait(bvls_handle* h, long long cycles) {
+  if (!h) return set_err(BVLS_EINVAL, "handle is required");
+  h->grid_wait = cycles > 0 ? cycles : kGridWaitCycles;
+  // the bound is a kernel argument baked into the instantiated solve graphs
+  CK(cudaStreamSynchronize(h->s));
+  for (auto& c : h->graphs) cudaGraphExecDestroy(c.exec);
+  h->graphs.clear();
+  return BVLS_OK;
+}
 
 // Largest eigenvalue of the symmetric tridiagonal matrix with diagonal alpha and off-diagonal
 // beta, by bisection on the Sturm count (the number of eigenvalues below x is the number of
@@ -689,10 +701,10 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
   {
     int optin = 0;
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    h->pass_stages = pass_configure(h->lda, h->m4, (n + h->num_sms - 1) / h->num_sms, optin, &h->pass_qw,
+    h->pass_stages = pass_configure(h->lda, h->m4, iters_idx_cap(n, h->num_sms), optin, &h->pass_qw,
                                     &h->pass_cps);
     h->pass_coop = h->pass_stages > 0 &&
-                   iters_configure(h->lda, h->m4, h->pass_stages, h->pass_cps, (n + h->num_sms - 1) / h->num_sms,
+                   iters_configure(h->lda, h->m4, h->pass_stages, h->pass_cps, iters_idx_cap(n, h->num_sms),
                                    h->num_sms);
     cudaGetLastError();
   }
@@ -749,8 +761,9 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
     h->Cg[kF32] = 1.01 * (d_g + 2.0) * kU + kU;
     const int per = (n + h->fwd_chunks - 1) / h->fwd_chunks;
     const int d_f = ((per + kFwdWarps - 1) / kFwdWarps + 1) / 2 + 4 + h->fwd_chunks + 1;
-    // the fused pass: a q-warp lane sums its CTA's columns, then 8 warps x nparts/8 partials
-    const int d_p = (n + h->num_sms - 1) / h->num_sms + (h->num_sms + 7) / 8 + 8;
+    // the fused pass: a q-warp lane sums its CTA's columns (at most iters_idx_cap of them when
+    // the persistent pass shrinks its grid), then 8 warps x nparts/8 partials
+    const int d_p = iters_idx_cap(n, h->num_sms) + (h->num_sms + 7) / 8 + 8;
     const int d = std::max(d_f, d_p);
     h->Cf[kX2] = 2.0 * (d + 2.0) * (d + 2.0) * kU * kU + 2.0 * kU * kU;
     h->Cf[kF32] = 1.01 * (d + 2.0) * kU + kU;
@@ -1606,6 +1619,7 @@ extern "C" bvls_status bvls_solve_ragged(int B, const bvls_problem* probs, const
   RCK(alloc(&b.chunks, 1));
   RCK(alloc(&b.act, (size_t)B));
   RCK(alloc(&b.err, 1));
+  RCK(alloc(&b.work, 1));
   // refinement: the original y_k (y' is folded during the solve), scratch, descriptors
   float* y_orig = nullptr;
   double *ref_g = nullptr, *ref_xs = nullptr;
@@ -1809,12 +1823,36 @@ extern "C" bvls_status bvls_solve_ragged(int B, const bvls_problem* probs, const
   const auto t_setup = clk::now();
   // ---- solve: one graph, a while node around one chunk
   b.power = 0;
+  RCK(cudaMemsetAsync(b.work, 0, sizeof(double), s));
   RCK(launch_rinit(b, c_tot, 0, s));
   RCK(launch_rfwd(b, s));
   RCK(launch_rtiles(b, s));
   const int chunk = chunk_length(K);
   const long long max_chunks = (b.max_iter + chunk - 1) / chunk + 2;
-  {
+  auto enqueue_rchunk = [&]() -> cudaError_t {
+    cudaError_t e1 = cudaSuccess;
+    for (int j = 0; j < chunk && e1 == cudaSuccess; ++j) {
+      const bool gap_iter = ((j + 1) % K) == 0;
+      e1 = launch_rpass(b, max_tiles, j & 1, gap_iter ? 1 : 0, s);
+      if (e1 == cudaSuccess) e1 = launch_rresid(b, j & 1, s);
+      if (e1 == cudaSuccess && gap_iter) e1 = launch_rgap(b, j & 1, s);
+      if (e1 == cudaSuccess && gap_iter) e1 = launch_rtiles(b, s);
+    }
+    return e1;
+  };
+  if (o.profile == 2) {
+    // every kernel launched directly from the host, a chunk at a time, until no instance is
+    // active (no CUDA graph, so a profiler sees each launch)
+    for (long long c = 0; c < max_chunks; ++c) {
+      RCK(enqueue_rchunk());
+      int act = 0;
+      unsigned e = 0;
+      RCK(cudaMemcpyAsync(&act, b.n_act_inst, sizeof(int), cudaMemcpyDeviceToHost, s));
+      RCK(cudaMemcpyAsync(&e, b.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+      RCK(cudaStreamSynchronize(s));
+      if (act == 0 || e) break;
+    }
+  } else {
     cudaGraph_t g = nullptr;
     RCK(cudaGraphCreate(&g, 0));
     cudaGraphConditionalHandle hc;
@@ -1829,14 +1867,7 @@ extern "C" bvls_status bvls_solve_ragged(int B, const bvls_problem* probs, const
     cudaGraph_t body = e == cudaSuccess ? np.conditional.phGraph_out[0] : nullptr;
     if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      cudaError_t e1 = cudaSuccess;
-      for (int j = 0; j < chunk && e1 == cudaSuccess; ++j) {
-        const bool gap_iter = ((j + 1) % K) == 0;
-        e1 = launch_rpass(b, max_tiles, j & 1, gap_iter ? 1 : 0, s);
-        if (e1 == cudaSuccess) e1 = launch_rresid(b, j & 1, s);
-        if (e1 == cudaSuccess && gap_iter) e1 = launch_rgap(b, j & 1, s);
-        if (e1 == cudaSuccess && gap_iter) e1 = launch_rtiles(b, s);
-      }
+      cudaError_t e1 = enqueue_rchunk();
       if (e1 == cudaSuccess) e1 = launch_rloop_ctl(b, hc, (int)std::min<long long>(max_chunks, 0x7fffffff), s);
       cudaError_t e2 = cudaStreamEndCapture(s, &body);
       e = e1 != cudaSuccess ? e1 : e2;
@@ -1844,12 +1875,14 @@ extern "C" bvls_status bvls_solve_ragged(int B, const bvls_problem* probs, const
     if (e == cudaSuccess) e = cudaGraphInstantiate(&gx, g, 0);
     cudaGraphDestroy(g);
     RCK(e);
+    RCK(cudaGraphLaunch(gx, s));
   }
-  RCK(cudaGraphLaunch(gx, s));
   RCK(launch_rexport(b, s));
   RCK(cudaMemcpyAsync(hs.data(), b.st, sizeof(RState) * B, cudaMemcpyDeviceToHost, s));
   int hchunks = 0;
+  double hwork = 0.0;
   RCK(cudaMemcpyAsync(&hchunks, b.chunks, sizeof(int), cudaMemcpyDeviceToHost, s));
+  RCK(cudaMemcpyAsync(&hwork, b.work, sizeof(double), cudaMemcpyDeviceToHost, s));
   RCK(cudaMemcpyAsync(&herr, b.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   RCK(cudaStreamSynchronize(s));
   const auto t_solve = clk::now();
@@ -1937,6 +1970,7 @@ extern "C" bvls_status bvls_solve_ragged(int B, const bvls_problem* probs, const
       info->kkt_max = std::max(info->kkt_max, r.kkt);
     }
     info->refine_ms = ref_ms;
+    info->sum_rows_cols = hwork;
   }
   if (nconv < B) return set_err(BVLS_EMAXITER, "%d of %d instances reached max_iter with gap >= tol", B - nconv, B);
   g_err.clear();

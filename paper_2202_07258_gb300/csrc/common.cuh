@@ -31,6 +31,25 @@ constexpr int kPassTmax = 8;      // float4 row chunks owned by one lane of a q 
 constexpr int kPassMaxStages = 32;
 constexpr int kMaxGridFlags = 1024;  // grid barrier words of the persistent pass
 constexpr long long kGridWaitCycles = 4000000000LL;  // bounded grid-barrier wait (about 2 s)
+// The persistent pass gives each CTA at least this many preserved columns: when screening
+// has left fewer than kItersColsMin x (launched CTAs) columns, only ceil(|S| / kItersColsMin)
+// CTAs take part (the others return at entry).  Measured on the Table-2 BVLS shape
+// (1000 x 2000, about a fifth of the columns preserved on average): 16 columns per CTA made
+// the screened solve 1.3x slower than one column (its iteration time is a per-CTA latency
+// chain, not the barriers), so only CTAs that would own no column stay out.
+constexpr int kItersColsMin = 1;
+
+// CTAs of the persistent pass that take part for n_act preserved columns and `grid` launched.
+__host__ __device__ inline int iters_active_ctas(int n_act, int grid) {
+  const int want = (n_act + kItersColsMin - 1) / kItersColsMin;
+  return want < 1 ? 1 : (want < grid ? want : grid);
+}
+// Columns one CTA of the persistent pass may own for n columns and `grid` CTAs.
+__host__ __device__ inline int iters_idx_cap(int n, int grid) {
+  const int per = (n + grid - 1) / grid;
+  const int cap = per > kItersColsMin ? per : kItersColsMin;
+  return cap < n ? cap : n;
+}
 
 enum DualMode { kScaling = 0, kTranslation = 1, kZero = 2 };
 // kMix: float32 correlations a_j^T r, double-float forward product A_S x (the values of the
@@ -67,6 +86,7 @@ struct DevState {
   double sum_active;  // sum of |preserved set| over the A_S^T r passes
   double sum_nnz;     // sum of nonzero preserved x_j over the A_S x_S passes
   double theta_r2;    // ||theta - r_k||^2 for a fixed dual point (computed by the pass at gap iterations)
+  unsigned long long gbase;  // the persistent pass's grid-barrier count at the start of its next launch
   unsigned int cnt_tr, cnt_gap, cnt_fwd, cnt_resid;
 };
 
@@ -116,6 +136,7 @@ struct Params {
   float2 inv1ps2;          // 1 / (1 + sigma)
   double E_cp;             // |r (stored) - r (exact)| from the recurrence r_{k+1} = (r_k + y' - A xbar) / 2
   const MomEntry* mom;     // momentum table (kMomTable entries)
+  long long grid_wait;     // bound of the persistent pass's grid-barrier waits, in SM cycles
   int fwd_chunks;          // grid.y of the A_S x_S kernel
   int fwd_tiles;           // grid.x of the A_S x_S kernel
 };
@@ -246,6 +267,12 @@ __device__ inline bool grid_arrive_wait(unsigned* gb, unsigned nblocks, unsigned
   return true;
 }
 
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
   unsigned long long v;
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -256,15 +283,17 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
 // synchronised, then waits (bounded) until the count reaches `target` (the number of CTAs
 // times the barriers passed so far).  No last arrival hands anything on, so a barrier costs
 // one reduction and the polls.
-__device__ inline bool grid_count_sync(unsigned long long* cnt, unsigned long long target) {
-  __threadfence();
+// The release reduction orders the CTA's earlier writes (the caller synchronised the CTA's
+// threads first, as for a fence by one thread); the polls are relaxed loads, and one acquire
+// load after the count is reached orders the CTA's later reads.
+__device__ inline bool grid_count_sync(unsigned long long* cnt, unsigned long long target, long long limit) {
   asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(cnt) : "memory");
   if (ld_acquire_u64(cnt) >= target) return true;
   const long long t0 = clock64();
-  while (ld_acquire_u64(cnt) < target) {
-    if (clock64() - t0 > kGridWaitCycles) return false;
+  while (ld_relaxed_u64(cnt) < target) {
+    if (clock64() - t0 > limit) return false;
   }
-  __threadfence();
+  (void)ld_acquire_u64(cnt);
   return true;
 }
 

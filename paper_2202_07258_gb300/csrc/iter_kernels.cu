@@ -139,6 +139,7 @@ __global__ void k_init_state(Params p, Buffers b) {
     st->sum_active = 0.0;
     st->sum_nnz = 0.0;
     st->cnt_tr = st->cnt_gap = st->cnt_fwd = st->cnt_resid = 0u;
+    st->gbase = 0ull;
   }
   if (b.gbar)   // the persistent pass counts its grid barriers from 0 in every solve
     for (int i = threadIdx.x; i < kMaxGridFlags; i += blockDim.x) b.gbar[i] = 0u;

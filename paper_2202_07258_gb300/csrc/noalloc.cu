@@ -291,6 +291,7 @@ bvls_status bvls_solve_static(const float* A, int m, int n, int lda, const doubl
   p.u2 = W.u2;
   p.invL = 1.0 / Lc;
   p.invL2 = df2_from_double(p.invL);
+  p.grid_wait = kGridWaitCycles;
   p.t_norm = t_norm;
   p.gamma_w = gamma_w;
   {

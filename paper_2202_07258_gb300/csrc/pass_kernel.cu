@@ -657,7 +657,7 @@ __global__ void __launch_bounds__(32 * (1 + DW + QW), 1)
   constexpr int NW = DW + QW;          // consumer warps
   constexpr int NCONS = 32 * NW;
   DevState* st = b.st;
-  if (st->done) return;                      // fixed for the whole launch
+  if (st->done || st->error) return;         // fixed for the whole launch
   extern __shared__ __align__(128) unsigned char smem[];
   const int m4q = p.m4 >> 2;
   const uint32_t col_bytes = (uint32_t)p.lda * 4u;
@@ -683,23 +683,29 @@ __global__ void __launch_bounds__(32 * (1 + DW + QW), 1)
   __shared__ double s_tn, s_tk, s_etag;   // t_{k+1} without restart, t_k, margin eta_g
   __shared__ float2 s_beta2[2];
   __shared__ int s_ti, s_err, s_ok;
+  __shared__ volatile int s_stop;      // the consumers left the iteration loop early
   __shared__ double s_th[NW];
   __shared__ float2 s_red[NW][32];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_act = st->n_active;
   const int k0 = st->k;
-  const int per = (n_act + gridDim.x - 1) / gridDim.x;
+  // the CTAs that take part: at least kItersColsMin preserved columns each (the preserved set
+  // is fixed for the launch, so every CTA computes the same count)
+  const int G = iters_active_ctas(n_act, gridDim.x);
+  if ((int)blockIdx.x >= G) return;
+  const int per = (n_act + G - 1) / G;
   const int p0 = min(n_act, (int)blockIdx.x * per);
   const int nq = min(n_act, p0 + per) - p0;
   const int ngroups = (nq + cps - 1) / cps;
   const int nslices = (p.m4 + 31) / 32;
-  const int nparts = gridDim.x;
-  // grid barriers: a monotonic arrival count, zeroed at the start of the solve; every
-  // iteration before this launch passed two barriers, so barrier number nb of the solve
-  // completes when the count reaches gridDim.x * (nb + 1)
+  const int nparts = G;
+  // grid barriers: a monotonic arrival count, zeroed at the start of the solve; this launch
+  // starts from the count st->gbase that earlier launches left, and its barrier number nb
+  // (from 1) completes when the count reaches gbase + G * nb
   unsigned long long* gcount = reinterpret_cast<unsigned long long*>(b.gbar);
-  unsigned long long nbar = 2ull * (unsigned long long)k0;
+  const unsigned long long gbase = st->gbase;
+  unsigned long long nbar = 0ull;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < nstages; ++s) {
@@ -711,6 +717,7 @@ __global__ void __launch_bounds__(32 * (1 + DW + QW), 1)
     fence_barrier_init();
     s_err = 0;
     s_ok = 1;
+    s_stop = 0;
     s_ti = st->ti;
     s_tk = st->t;
     momentum(p.mom, s_ti, s_tk, &s_tn, s_beta2);
@@ -737,7 +744,7 @@ __global__ void __launch_bounds__(32 * (1 + DW + QW), 1)
         const int g = gg - (gg / ngroups) * ngroups;
         const int s = gg % nstages;
         const int u = gg / nstages;
-        if (u > 0 && !mbar_wait(&empty[s], (u - 1) & 1)) {
+        if (u > 0 && !mbar_wait_unless(&empty[s], (u - 1) & 1, &s_stop)) {
           s_err = 1;
           break;
         }
@@ -924,7 +931,7 @@ __global__ void __launch_bounds__(32 * (1 + DW + QW), 1)
       *reinterpret_cast<float2*>(&b.blk[4 * blockIdx.x + 0]) = d;   // restart term (double-float)
       b.blk[4 * blockIdx.x + 1] = e;                                 // translation step candidate
       if (s_err) atomicOr(&st->error, 1);
-      bool ok = grid_count_sync(gcount, (unsigned long long)gridDim.x * ++nbar);
+      bool ok = grid_count_sync(gcount, gbase + (unsigned long long)G * ++nbar, p.grid_wait);
       if (ok && *(volatile int*)&st->error) ok = false;
       s_ok = ok ? 1 : 0;
       if (!ok) atomicOr(&st->error, 1);
@@ -989,7 +996,7 @@ __global__ void __launch_bounds__(32 * (1 + DW + QW), 1)
       }
       scalars_done = true;
     };
-    for (int sl = blockIdx.x; sl < nslices; sl += gridDim.x) {
+    for (int sl = blockIdx.x; sl < nslices; sl += G) {
       const int row = sl * 32 + lane;
       float s = 0.f, c = 0.f;
       if (row < p.m4) {
@@ -1065,7 +1072,7 @@ __global__ void __launch_bounds__(32 * (1 + DW + QW), 1)
     // ---- grid barrier 2: r_{k+1} and the P partials are written
     consumer_sync<NCONS>();
     if (ct == 0) {
-      bool ok = grid_count_sync(gcount, (unsigned long long)gridDim.x * ++nbar);
+      bool ok = grid_count_sync(gcount, gbase + (unsigned long long)G * ++nbar, p.grid_wait);
       if (ok && *(volatile int*)&st->error) ok = false;
       s_ok = ok ? 1 : 0;
       if (!ok) atomicOr(&st->error, 1);
@@ -1073,6 +1080,11 @@ __global__ void __launch_bounds__(32 * (1 + DW + QW), 1)
     consumer_sync<NCONS>();
     if (!s_ok) break;
   }
+  // on an early exit the producer may be waiting for a stage no consumer will free: it stops
+  // issuing and waits (bounded) for the copies it already issued before the CTA ends
+  if (ct == 0 && !s_ok) s_stop = 1;
+  // the count the next launch starts from (every CTA has read gbase before its first barrier)
+  if (blockIdx.x == 0 && ct == 0 && s_ok) st->gbase = gbase + (unsigned long long)G * nbar;
 
   // the CTA's columns back to global memory (both slots of x and g)
   for (int q = ct; q < nq; q += NCONS) {
@@ -1245,7 +1257,7 @@ static const void* iters_kernel_p(int precision, const ItersShape& sh) {
 
 cudaError_t launch_iters(const Params& p, const Buffers& b, int slot0, int niter, bool gap_last, int precision,
                          int grid, int nstages, int cps, int qwarps, cudaStream_t s) {
-  const int idx_cap = (p.n + grid - 1) / grid;
+  const int idx_cap = iters_idx_cap(p.n, grid);
   const size_t sm = iters_smem_bytes(p.lda, p.m4, nstages, cps, idx_cap);
   const ItersShape sh = iters_shape(precision, p.m4);
   const void* fn = iters_kernel_p(precision, sh);

@@ -162,16 +162,19 @@ cudaError_t launch_rinit(const RBuf& b, long long total_cols, int power, cudaStr
 // Work list over the active instances: ceil(n_active / tw) tiles each.  One block.
 __global__ void __launch_bounds__(kRThreads) k_rtiles(RBuf b) {
   __shared__ int sh[kRThreads / 32];
+  __shared__ double shd[kRThreads / 32];
   __shared__ int s_base, s_ibase;
   if (threadIdx.x == 0) {
     s_base = 0;
     s_ibase = 0;
   }
   __syncthreads();
+  double work = 0.0;   // sum over the live instances of m_k |S_k|: A elements one iteration reads
   for (int k0 = 0; k0 < b.B; k0 += kRThreads) {
     const int k = k0 + threadIdx.x;
     const bool live = k < b.B && !b.st[k].done;
     const int nt = live ? (b.st[k].n_active + b.tw - 1) / b.tw : 0;
+    if (live) work += (double)b.inst[k].m * (double)b.st[k].n_active;
     int tot = 0;
     // tiles: exclusive scan of nt (counts up to kRThreads * tiles_max fit an int)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -200,9 +203,12 @@ __global__ void __launch_bounds__(kRThreads) k_rtiles(RBuf b) {
     }
     __syncthreads();
   }
+  work = bsum(work, shd);
   if (threadIdx.x == 0) {
     *b.n_tiles = s_base;
     *b.n_act_inst = s_ibase;
+    // the work list stays until the next gap iteration: the next K iterations read this much
+    if (b.work && !b.power) *b.work += work * (double)b.K;
   }
 }
 

@@ -93,6 +93,7 @@ struct RBuf {
   unsigned int* err;                // bit 0: NaN or Inf in A or y
   int* chunks;                      // chunks run by the device-side loop of the solve graph
   int tw;                           // columns per tile of the work list (kRTileMin..kRTileMax)
+  double* work;                     // sum over iterations of sum_k m_k |S_k| (A elements read), or null
 };
 
 cudaError_t launch_rnorms(const RBuf& b, long long total_cols, cudaStream_t s);

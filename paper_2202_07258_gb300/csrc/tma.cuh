@@ -55,6 +55,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return true;
 }
 
+// As mbar_wait, but also gives up (false) as soon as *stop becomes nonzero: the other warps
+// of the CTA have left the loop whose stages this wait would free.
+__device__ __forceinline__ bool mbar_wait_unless(uint64_t* bar, uint32_t parity, const volatile int* stop) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*stop) return false;
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+  return true;
+}
+
 // Wait (bounded) until *flag >= target; flag lives in shared memory and is written by
 // another warp of the CTA.  The poll backs off, so a waiting warp leaves the issue slots
 // and shared-memory bandwidth to the warps that are computing.
