@@ -72,11 +72,13 @@ enum {
                            accumulation; default */
   BVLS_PREC_FP32 = 1,   /* float32 data and plain float32 accumulation; faster, and the
                            rounding margins of the test are about 2^24 times wider */
-  BVLS_PREC_MIXED = 2   /* float32 correlations a_j^T r, double-float forward product A x
+  BVLS_PREC_MIXED = 2   /* float32 correlations a_j^T r; forward product A x with float32
+                           sums over groups of at most 8 columns merged in double-float
                            (bvls_solve, bvls_solve_static): the residual, P(x) and the
-                           certificate of the zero dual point keep the FP32X2 accuracy; the
-                           correlations and the screening margins are those of FP32.
-                           bvls_solve_batched treats it as FP32 */
+                           certificate of the zero dual point are good to about 9 u relative
+                           to sum_j |a_ij x_j| (FP32: about u per column); the correlations and
+                           the screening margins are those of FP32.  bvls_solve_batched treats
+                           it as FP32 */
 };
 
 /* Primal solver of bvls_solve. */

@@ -768,7 +768,10 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
     h->Cf[kX2] = 2.0 * (d + 2.0) * (d + 2.0) * kU * kU + 2.0 * kU * kU;
     h->Cf[kF32] = 1.01 * (d + 2.0) * kU + kU;
     h->Cg[kMix] = h->Cg[kF32];
-    h->Cf[kMix] = h->Cf[kX2];
+    // mode MIXED: the fused pass sums each stage's (at most pass_cps) columns in float32 with
+    // the high part of x_j before one double-float merge: gamma_cps + u for the stage sums
+    // (the dropped low parts), then the double-float bound of the merges
+    h->Cf[kMix] = 1.01 * (std::max(1, h->pass_cps) + 1.0) * kU + 1.01 * h->Cf[kX2];
     h->Csub = 8.0 * kU * kU;
   }
   CK(cudaStreamSynchronize(h->s));

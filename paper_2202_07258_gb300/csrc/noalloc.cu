@@ -303,6 +303,8 @@ bvls_status bvls_solve_static(const float* A, int m, int n, int lda, const doubl
                                            : 1.01 * (d_g + 2.0) * kU + kU;
     p.Cf = o.precision != BVLS_PREC_FP32 ? 2.0 * (d_f + 2.0) * (d_f + 2.0) * kU * kU + 2.0 * kU * kU
                                          : 1.01 * (d_f + 2.0) * kU + kU;
+    // mode MIXED: the pass sums each stage's columns in float32 before a double-float merge
+    if (o.precision == BVLS_PREC_MIXED) p.Cf = 1.01 * (std::max(1, pass_cps) + 1.0) * kU + 1.01 * p.Cf;
     p.Csub = 8.0 * kU * kU;
   }
   const int K = o.screen_every;

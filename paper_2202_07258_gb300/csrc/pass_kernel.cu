@@ -120,12 +120,46 @@ __device__ __forceinline__ void dot_pair(const float4* colA, const float4* colB,
 // the stage's nonzero columns two at a time, both columns' loads issued first (measured on
 // 4000-row columns: 104 against 114 us per iteration; no gain at QT = 2, and at QT = 8 the
 // two columns' registers spill).
+//
+// QP == kMix (mode MIXED): the stage's columns are summed in float32 with the high part of
+// x_j (one packed FMA per element), and that stage sum enters the double-float accumulator
+// with one TwoSum.  The stage sum is off by at most gamma_cps sum |a_ij xh_j| plus the dropped
+// sum |a_ij xl_j| <= u sum |a_ij x_j|, so the forward product is good to about (cps + 1) u
+// relative to sum_j |a_ij x_j| instead of the full double-float accuracy, at a sixth of its
+// arithmetic (the double-float forward product was the pass's bottleneck).
 template <int QP, int QT, int QW>
 __device__ __forceinline__ void q_stage(f32x2 (&qs)[QT][2], f32x2 (&qc)[QT][2], const float* sbase,
                                         const float2* sxs, int nc, int lda, int qw, int lane, int m4q) {
   float2 xs[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) xs[c] = c < nc ? sxs[c] : make_float2(0.f, 0.f);
+  if (QP == kMix) {
+    f32x2 gs[QT][2];
+#pragma unroll
+    for (int t = 0; t < QT; ++t) gs[t][0] = gs[t][1] = 0ull;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      if (xs[c].x != 0.0f) {
+        const ulonglong2* col = reinterpret_cast<const ulonglong2*>(sbase + (size_t)c * lda);
+        const f32x2 xh = x2_pack(xs[c].x, xs[c].x);
+#pragma unroll
+        for (int t = 0; t < QT; ++t) {
+          const int c4 = qw * 32 + lane + t * 32 * QW;
+          if (c4 < m4q) {
+            const ulonglong2 a = col[c4];
+            gs[t][0] = x2_fma(a.x, xh, gs[t][0]);
+            gs[t][1] = x2_fma(a.y, xh, gs[t][1]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < QT; ++t) {
+      df_add_x2(qs[t][0], qc[t][0], gs[t][0], 0ull);
+      df_add_x2(qs[t][1], qc[t][1], gs[t][1], 0ull);
+    }
+    return;
+  }
   if (QT != 4) {
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
@@ -189,7 +223,7 @@ __device__ __forceinline__ void q_store(float2* part, int c4, const f32x2 (&s)[2
   float s0, s1, s2, s3, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
   x2_unpack(s[0], s0, s1);
   x2_unpack(s[1], s2, s3);
-  if (QP == kX2) {
+  if (QP != kF32) {
     x2_unpack(c[0], c0, c1);
     x2_unpack(c[1], c2, c3);
   }
@@ -233,7 +267,7 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
     k_pass(Params p, Buffers b, int slot, int gap_iter, int nstages, int cps) {
   // arithmetic of the two products: correlations a_j^T r_k (DP) and A_S x_{k+1} (QP)
   constexpr int DP = PREC == kX2 ? kX2 : kF32;
-  constexpr int QP = PREC == kF32 ? kF32 : kX2;
+  constexpr int QP = PREC;   // kMix: float32 stage sums merged in double-float
   DevState* st = b.st;
   if (st->done) return;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -419,7 +453,7 @@ __global__ void __launch_bounds__(32 * (1 + kPassDot + QW), 1)
         const float2 g2 = lane == 0 ? ga : gb;
         float2 xf, dc;
         const float2 xnew = coord_step(p, g2, xk, xp, gpv, lj, uj, bb, onepb, xf, dc);
-        sx[(size_t)s * cps + c] = QP == kX2 ? xf : make_float2(xf.x, 0.0f);
+        sx[(size_t)s * cps + c] = QP != kF32 ? xf : make_float2(xf.x, 0.0f);
         mbar_arrive(&xready[s]);
         xn[j] = xnew;
         gc[j] = g2;
@@ -653,7 +687,7 @@ template <int PREC, int DW, int QW, int QT>
 __global__ void __launch_bounds__(32 * (1 + DW + QW), 1)
     k_iters(Params p, Buffers b, int slot0, int niter, int gap_last, int nstages, int cps, int idx_cap) {
   constexpr int DP = PREC == kX2 ? kX2 : kF32;
-  constexpr int QP = PREC == kF32 ? kF32 : kX2;
+  constexpr int QP = PREC;   // kMix: float32 stage sums merged in double-float
   constexpr int NW = DW + QW;          // consumer warps
   constexpr int NCONS = 32 * NW;
   DevState* st = b.st;
@@ -866,7 +900,7 @@ __global__ void __launch_bounds__(32 * (1 + DW + QW), 1)
           const float2 g2 = lane == 0 ? ga : gb2;
           float2 xf, dc;
           const float2 xnew = coord_step(p, g2, xk, xp, gpv, lj, uj, bb, onepb, xf, dc);
-          sx[(size_t)s * cps + c] = QP == kX2 ? xf : make_float2(xf.x, 0.0f);
+          sx[(size_t)s * cps + c] = QP != kF32 ? xf : make_float2(xf.x, 0.0f);
           mbar_arrive(&xready[s]);
           xn[qj] = xnew;
           gc[qj] = g2;
@@ -1208,16 +1242,14 @@ static int iters_qt(int m4, int qw) {
   return 0;
 }
 
-// In mode MIXED the double-float forward product is the slower half of a column group, so
-// 16 q warps (one or two row chunks per lane) take it with 4 dot warps (measured, solve with
-// 300 iterations on 4000 x 20000: 76 against 86 us per iteration; 2000 x 10000: 0.917
-// against 0.924 ms per solve).  Where both products are double-float the dot warps are the
-// slower half and the even split stays (1.06 against 1.36 ms on 2000 x 10000).
+// 8 dot warps and 8 q warps in every mode.  (Mode MIXED used 4 + 16 while its forward
+// product was double-float; with the float32 stage sums of q_stage the dot warps are the
+// slower half, and 8 + 8 measured faster than 4 + 16, 8 + 16 and 12 + 8: 0.703 against
+// 0.824 ms per solve of the 2000 x 10000 workload, 19.4 against 24.5 us per iteration of the
+// 2000 x 10000 |N| one, 67.7 against 69.6 us on 4000 x 20000.)
 static ItersShape iters_shape(int precision, int m4) {
-  ItersShape sh{4, 16, 0};
-  sh.qt = iters_qt(m4, sh.qw);
-  if (precision == kMix && sh.qt >= 1 && sh.qt <= 2) return sh;
-  sh = ItersShape{8, 8, 0};
+  (void)precision;
+  ItersShape sh{8, 8, 0};
   sh.qt = iters_qt(m4, sh.qw);
   return sh;
 }
@@ -1236,11 +1268,6 @@ static const void* iters_kernel(const ItersShape& sh) {
       case 2: return iters_fn<PREC, 8, 8, 2>();
       case 4: return iters_fn<PREC, 8, 8, 4>();
       case 8: return iters_fn<PREC, 8, 8, 8>();
-    }
-  } else if (PREC == kMix && sh.dw == 4 && sh.qw == 16) {
-    switch (sh.qt) {
-      case 1: return iters_fn<kMix, 4, 16, 1>();
-      case 2: return iters_fn<kMix, 4, 16, 2>();
     }
   }
   return nullptr;
