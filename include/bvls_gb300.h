@@ -177,7 +177,11 @@ typedef struct {
   double refine_ms;       /* refinement kernel time (CUDA events) */
   int refine_reason;      /* 0 refined or off, 1 declined after the last round, 2 declined
                              because |F| > min(m, 2048), 3 declined because m > 8192 */
-  int pad_;
+  int t_choice;           /* translation direction t of the handle (Section 4.2): 0 the
+                             caller's, 1 t = -1 (Proposition 2, case 3), 2 minus the mean column,
+                             3 minus the column most correlated with all others, 4 the
+                             least-squares solution of A^T t = -1 (Proposition 2, case 1);
+                             -1 none (BVLS_DUAL_SCALING or BVLS_DUAL_ZERO) */
 } bvls_info;
 
 /* Fill *opts with the defaults: tol 1e-6, screen_every 10, max_iter 100000, screening 1,
@@ -194,8 +198,10 @@ BVLS_API void bvls_default_opts(bvls_opts* opts);
  *   t       host; m doubles: the translation direction of Section 4.2 for the columns
  *           with u_j = +inf, or NULL to choose one (t = -1, then minus the mean column,
  *           then minus the column most correlated with all others, per Proposition 2 and
- *           the choices of Section 5).  A given t must satisfy a_j^T t < 0 on every
- *           nonzero column with u_j = +inf, else BVLS_EINVAL.
+ *           the choices of Section 5, then, when n <= m and n <= 1024, the least-squares
+ *           solution of A^T t = -1 of Proposition 2, case 1, by float64 conjugate gradients
+ *           on A^T A).  A given t must satisfy a_j^T t < 0 on every nonzero column with
+ *           u_j = +inf, else BVLS_EINVAL.
  *   stream  a cudaStream_t (0 = legacy default stream).
  *   out     receives the handle.
  * Setup computes the column norms ||a_j||_2 (used by Eq. (safe_rule)), w = A^T t and the

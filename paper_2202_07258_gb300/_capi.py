@@ -69,7 +69,7 @@ class bvls_info(ctypes.Structure):
         ("kkt", ctypes.c_double),
         ("refine_ms", ctypes.c_double),
         ("refine_reason", ctypes.c_int),
-        ("pad_", ctypes.c_int),
+        ("t_choice", ctypes.c_int),
     ]
 
     def as_dict(self):

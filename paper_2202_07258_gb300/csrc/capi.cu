@@ -75,6 +75,7 @@ struct bvls_handle {
   double t_norm = 0.0, gamma_w = 0.0, L = 0.0;
   double xbox = -1.0;  // sum_j max(|l_j|, |u_j|) ||a_j|| (primal-dual error bound), once computed
   int dual_mode = kScaling;
+  int t_choice = -1;   // translation direction: 0 caller's, 1 -1, 2 minus the mean column, 3 -a_+, 4 case 1
   Buffers b{};
   float* y_dev = nullptr;
   double* x0_dev = nullptr;
@@ -197,6 +198,57 @@ bvls_status try_direction(bvls_handle* h, const std::vector<double>& t,
     h->t_norm = tn;
     h->gamma_w = gamma;
   }
+  return BVLS_OK;
+}
+
+// t = A (A^T A)^{-1} (-1) for n <= min(m, kBwdMaxFree) (Proposition 2, case 1), through the
+// backward pass's free-set solver with every coordinate free.  Scratch is freed on return.
+bvls_status case1_direction(bvls_handle* h, std::vector<double>* t) {
+  const int m = h->m, n = h->n;
+  std::vector<double> half(n, 0.5), zero(n, 0.0), one(n, 1.0), minus(n, -1.0);
+  double *dx = nullptr, *dl = nullptr, *du = nullptr, *dv = nullptr, *dt = nullptr;
+  int* di = nullptr;
+  auto release = [&]() {
+    for (void* p : {(void*)dx, (void*)dl, (void*)du, (void*)dv, (void*)dt, (void*)di})
+      if (p) cudaFree(p);
+  };
+  cudaError_t e = cudaMalloc(&dx, sizeof(double) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&dl, sizeof(double) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&du, sizeof(double) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&dv, sizeof(double) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&dt, sizeof(double) * m);
+  if (e == cudaSuccess) e = cudaMalloc(&di, sizeof(int) * 3);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dx, half.data(), sizeof(double) * n, cudaMemcpyHostToDevice, h->s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dl, zero.data(), sizeof(double) * n, cudaMemcpyHostToDevice, h->s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(du, one.data(), sizeof(double) * n, cudaMemcpyHostToDevice, h->s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dv, minus.data(), sizeof(double) * n, cudaMemcpyHostToDevice, h->s);
+  if (e == cudaSuccess) {
+    BwdParams bp{};
+    bp.A = h->A;
+    bp.m = m;
+    bp.n = n;
+    bp.lda = h->lda;
+    bp.B = 1;
+    bp.l = dl;
+    bp.u = du;
+    bp.X = dx;
+    bp.Y = nullptr;   // read only for r = y - A x, which this call does not request
+    bp.ldy = m;
+    bp.dLdX = dv;
+    bp.dLdY = dt;
+    bp.status = di;
+    bp.iters = di + 1;
+    bp.nfree = di + 2;
+    bp.free_tol = 1e-9;
+    bp.cg_tol = 1e-13;
+    bp.cg_max_iter = 20000;
+    e = launch_bwd(bp, h->s);
+  }
+  t->assign(m, 0.0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(t->data(), dt, sizeof(double) * m, cudaMemcpyDeviceToHost, h->s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
+  release();
+  if (e != cudaSuccess) return set_err(BVLS_ECUDA, "case-1 direction: %s", cudaGetErrorString(e));
   return BVLS_OK;
 }
 
@@ -590,10 +642,12 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
     TRY(try_direction(h, tv, jinf, nrm, &ok));
     if (!ok) return set_err(BVLS_EINVAL, "the given t is not an interior direction (a_j^T t < 0)");
     h->dual_mode = kTranslation;
+    h->t_choice = 0;
   } else {
     bool ok = false;
     std::vector<double> tv(m, -1.0);  // Proposition 2, case 3
     TRY(try_direction(h, tv, jinf, nrm, &ok));
+    if (ok) h->t_choice = 1;
     if (!ok) {
       double *rs = nullptr, *rs_part = nullptr;
       TRY(dalloc(h, &rs, m));
@@ -604,6 +658,7 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
       CK(cudaStreamSynchronize(h->s));
       for (int i = 0; i < m; ++i) tv[i] = -s[i] / n;  // minus the mean column
       TRY(try_direction(h, tv, jinf, nrm, &ok));
+      if (ok) h->t_choice = 2;
       if (!ok) {
         // minus the column most correlated with all others: argmax_j a_j^T sum_k a_k
         TRY(try_direction(h, s, std::vector<uint8_t>(n, 0), nrm, &ok));  // w = A^T s
@@ -619,6 +674,16 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
         CK(cudaStreamSynchronize(h->s));
         for (int i = 0; i < m; ++i) tv[i] = -(double)col[i];
         TRY(try_direction(h, tv, jinf, nrm, &ok));
+        if (ok) h->t_choice = 3;
+      }
+      if (!ok && n <= m && n <= kBwdMaxFree && bwd_smem_bytes(m) <= 227u * 1024u) {
+        // Proposition 2, case 1: with rank(A) = n <= m, A^T t = -1 has the least-squares
+        // (minimum-norm) solution t = A (A^T A)^{-1} (-1).  The backward pass's solver
+        // computes exactly that shape, A_F (A_F^T A_F)^{-1} v, by conjugate gradients in
+        // float64: here with every coordinate free (x = 1/2 in the box [0, 1]) and v = -1.
+        TRY(case1_direction(h, &tv));
+        TRY(try_direction(h, tv, jinf, nrm, &ok));
+        if (ok) h->t_choice = 4;
       }
     }
     h->dual_mode = ok ? kTranslation : kZero;
@@ -984,6 +1049,7 @@ bvls_status bvls_solve(bvls_handle* h, const float* y, const double* x0, const b
     const double chunks_done = chunks_run >= 0 ? (double)chunks_run : (double)hs.chunks;
     info->kernel_launches = (fused ? 3.0 : 2.0) + chunks_done * (double)(per_chunk + (chunks_run >= 0 ? 0 : 1));
     info->single_pass = fused ? (pers ? 2 : 1) : 0;
+    info->t_choice = h->t_choice;
     if (!rout.empty()) {
       info->refined = rout[0].refined;
       info->refine_rounds = rout[0].rounds;
