@@ -265,6 +265,18 @@ def kernel_hash(files=None):
     return h.hexdigest()[:16]
 
 
+def stored_traffic(key):
+    """DRAM bytes per launch of an ncu record in profiles/ncu_traffic.json, or None when the
+    record is missing or the sources its kernel is built from have changed since."""
+    tp = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(tp):
+        return None
+    rec = json.load(open(tp)).get(key)
+    if rec and rec.get("kernel_hash") == kernel_hash(rec.get("sources")):
+        return rec.get("dram_bytes_per_launch")
+    return None
+
+
 def roofline(solver, y_dev, m):
     """Profile-mode solve: CUDA events around every product launch on the launching stream."""
     from paper_2202_07258_gb300 import make_opts
@@ -312,13 +324,7 @@ def roofline_from_info(info, m, traffic_key=None):
         src = "measured"
     else:
         peak, src = 6800.0, "fallback"
-    traffic = None
-    tp = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-    if os.path.exists(tp):
-        t = json.load(open(tp))
-        rec = t.get(traffic_key or name.split()[0])
-        if rec and rec.get("kernel_hash") == kernel_hash(rec.get("sources")):
-            traffic = rec.get("dram_bytes_per_launch")
+    traffic = stored_traffic(traffic_key or name.split()[0])
     other = {k: {"ms_total": v[0], "launches": v[2], "gb_per_launch": v[1] / max(1, v[2]) / 1e9,
                  "achieved_gbs": (v[1] / max(1, v[2])) / (v[0] / 1000.0 / max(1, v[2])) / 1e9 if v[0] else None}
              for k, v in kern.items()}
@@ -383,7 +389,9 @@ def ragged_leg(dev, stream, B=512):
             ach = a_bytes / (rr["solve_ms"] / 1000.0) / 1e9
             rr["roofline_whole_solve"] = {"bound": "hbm", "kernel": "whole solve (k_rpass, k_rresid, k_rgap, k_rtiles)",
                                           "achieved": ach, "peak": HBM_PEAK[0], "peak_source": HBM_PEAK[1],
-                                          "unit": "GB/s", "frac": ach / HBM_PEAK[0], "A_bytes_read": a_bytes}
+                                          "unit": "GB/s", "frac": ach / HBM_PEAK[0], "A_bytes_read": a_bytes,
+                                          "k_rpass_traffic_per_launch": stored_traffic(
+                                              "k_rpass@mixed_uneven_gaussian_B512") if not absm else None}
         # error against FP64 optima on sampled instances (refined solve; untimed)
         xr, sr, gr, itr, str_, infr, _ = solve_ragged(items, tol=TOL, screen_every=0, max_iter=mx, refine=True,
                                                       stream=stream.cuda_stream)
@@ -539,6 +547,7 @@ def batched_leg(dev, stream, flush, steps, warmup=1):
                        "flops_per_launch": flops / max(1, info["step_launches"]),
                        "avg_launch_us": 1e6 * step_s / max(1, info["step_launches"]),
                        "eval_avg_launch_us": 1e3 * info["eval_ms"] / max(1, info["eval_launches"]),
+                       "eval_traffic_per_launch": stored_traffic("k_beval@bvls_dirichlet_224x512_B4096"),
                        "step_share": info["step_ms"] / max(1e-9, info["step_ms"] + info["eval_ms"])}
     # the same kernel against HBM: per coordinate and instance it reads g, x (double-float),
     # bf16(x_k - x_{k-1}) and the flag and writes g, x, bf16(x_{k+1} - x_k) (29 bytes); H~ once
