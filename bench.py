@@ -592,9 +592,41 @@ def e2e_leg(p, steps, stream):
             times.append(t1 - t0)
     h2d = 4 * m * n + 4 * m + 16 * n
     d2h = 8 * n + n
+    # breakdown (separate runs of the same calls): the copy of A alone, setup from a
+    # device-resident A, and the solve from host y to host x
+    A_d = A_h.cuda()
+    buf = torch.empty_like(A_d)
+
+    def med_ms(fn, k=4):
+        ts = []
+        for _ in range(k + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        return 1000.0 * statistics.median(ts[1:])
+
+    handles = []
+
+    def setup_dev():
+        st, hh = _capi.bvls_setup(A_d.data_ptr(), m, n, m, l_h.ctypes.data, u_h.ctypes.data, None,
+                                  stream.cuda_stream)
+        assert st == 0, _capi.bvls_last_error()
+        handles.append(hh)
+
+    h2d_ms = med_ms(lambda: buf.copy_(A_h, non_blocking=True))
+    setup_ms = med_ms(setup_dev)
+    hh = handles[-1]
+    solve_ms = med_ms(lambda: _capi.bvls_solve(hh, y_h.data_ptr(), None, opts, x_h.data_ptr(), s_h.data_ptr()))
+    for hh in handles:
+        _capi.bvls_destroy(hh)
     return {"value": 1.0 / statistics.median(times), "unit": "instances/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "includes": "bvls_setup from host A (copy, column norms, dual "
-            "direction search, Lanczos step constant) + bvls_solve from host y to host x"}
+            "direction search, Lanczos step constant) + bvls_solve from host y to host x",
+            "breakdown_ms": {"h2d_A": h2d_ms, "setup_from_device_A": setup_ms, "solve_host_y_to_host_x": solve_ms,
+                             "note": "setup = padded copy + finiteness check, bounds, column norms, translation "
+                                     "direction search (float64 passes), Lanczos step constant, workspace"}}
 
 
 def ncu_region(args):

@@ -1689,6 +1689,8 @@ extern "C" bvls_status bvls_solve_ragged(int B, const bvls_problem* probs, const
   RCK(alloc(&b.act, (size_t)B));
   RCK(alloc(&b.err, 1));
   RCK(alloc(&b.work, 1));
+  RCK(alloc(&b.rblkP, (size_t)B * kRRowBlocks));
+  RCK(alloc(&b.rcnt, (size_t)B));
   // refinement: the original y_k (y' is folded during the solve), scratch, descriptors
   float* y_orig = nullptr;
   double *ref_g = nullptr, *ref_xs = nullptr;
@@ -1721,6 +1723,7 @@ extern "C" bvls_status bvls_solve_ragged(int B, const bvls_problem* probs, const
   RCK(cudaMemsetAsync(b.yl, 0, sizeof(float) * (size_t)r_tot, s));
   RCK(cudaMemsetAsync(b.err, 0, sizeof(unsigned), s));
   RCK(cudaMemsetAsync(b.chunks, 0, sizeof(int), s));
+  RCK(cudaMemsetAsync(b.rcnt, 0, sizeof(unsigned) * B, s));
   for (int k = 0; k < B; ++k) {
     const bvls_problem& q = probs[k];
     RCK(cudaMemcpy2DAsync(A + in[k].a_off, sizeof(float) * in[k].lda, q.A, sizeof(float) * q.lda,

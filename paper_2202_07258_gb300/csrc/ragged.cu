@@ -2,6 +2,8 @@
 #include "common.cuh"
 #include "ragged.cuh"
 
+#include <algorithm>
+
 namespace bvls {
 
 namespace {
@@ -267,12 +269,10 @@ size_t rpass_smem_bytes(int tw) {
   return (size_t)kRMaxRows * 2 * sizeof(float) + (size_t)tw * kRMaxRows * sizeof(float);
 }
 
+// The grid walks the work list (a CTA takes tiles blockIdx.x, blockIdx.x + gridDim.x, ...), so
+// a launch over few live tiles costs a few CTAs per SM, not one CTA per possible tile.
 __global__ void __launch_bounds__(kRThreads) k_rpass(RBuf b, int slot, int gap_iter) {
-  if (blockIdx.x >= *b.n_tiles) return;
-  const RTileRef tr = b.tiles[blockIdx.x];
-  const int k = tr.inst;
-  const RInst in = b.inst[k];
-  const RState& st = b.st[k];
+  const int ntiles = *b.n_tiles;
   extern __shared__ __align__(16) float rsm[];
   float* srh = rsm;                      // r (hi), m4 floats
   float* srl = rsm + kRMaxRows;          // r (lo)
@@ -281,6 +281,11 @@ __global__ void __launch_bounds__(kRThreads) k_rpass(RBuf b, int slot, int gap_i
   __shared__ float2 s_xn[kRTileMax];
   __shared__ double s_dot[kRTileMax], s_eps[kRTileMax], s_v2[kRTileMax];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int wt = blockIdx.x; wt < ntiles; wt += gridDim.x) {
+  const RTileRef tr = b.tiles[wt];
+  const int k = tr.inst;
+  const RInst in = b.inst[k];
+  const RState& st = b.st[k];
   const int m4 = (in.m + 3) & ~3;
   const int q0 = tr.tile * b.tw;
   const int nc = min(b.tw, st.n_active - q0);
@@ -389,6 +394,8 @@ __global__ void __launch_bounds__(kRThreads) k_rpass(RBuf b, int slot, int gap_i
     b.tdot[ti] = b.power ? v2 : d;
     b.teps[ti] = ep;
   }
+  __syncthreads();   // the next tile reuses the shared staging
+  }
 }
 
 cudaError_t ragged_configure() {
@@ -398,41 +405,97 @@ cudaError_t ragged_configure() {
 
 cudaError_t launch_rpass(const RBuf& b, int max_tiles, int slot, int gap_iter, cudaStream_t s) {
   if (b.tw < kRTileMin || b.tw > kRTileMax) return cudaErrorInvalidValue;
-  k_rpass<<<max_tiles, kRThreads, rpass_smem_bytes(b.tw), s>>>(b, slot, gap_iter);
+  // resident CTAs per SM for this tile width, once per width (the work list is walked by a
+  // grid of that many CTAs per SM)
+  static int per_sm[kRTileMax + 1] = {0};
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+  }
+  if (!per_sm[b.tw]) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[b.tw], k_rpass, kRThreads,
+                                                                  rpass_smem_bytes(b.tw));
+    if (e != cudaSuccess) return e;
+    if (per_sm[b.tw] < 1) per_sm[b.tw] = 1;
+  }
+  const int grid = std::max(1, std::min(max_tiles, per_sm[b.tw] * sms));
+  k_rpass<<<grid, kRThreads, rpass_smem_bytes(b.tw), s>>>(b, slot, gap_iter);
   return cudaGetLastError();
 }
 
 // Per instance: r_{k+1} = y' - sum of the tile partials (power mode: A v_{i+1}), P_{k+1}, and
-// the scalars of the iteration.  Block per instance.
+// the scalars of the iteration.  Grid (row block, instance): a block takes 32 rows, a lane
+// one row, and its 8 warps split the tiles (each sums every 8th tile, loads batched), then
+// the warps' sums are merged in warp order.  The instance's last block to finish (a counter
+// per instance) adds the blocks' P partials in block order and the tiles' restart terms,
+// and updates the instance's scalars.
 __global__ void __launch_bounds__(kRThreads) k_rresid(RBuf b, int slot) {
   __shared__ double sh[kRThreads / 32];
-  const int k = blockIdx.x;
+  __shared__ float2 s_part[kRThreads / 32][32];
+  __shared__ int s_last;
+  const int k = blockIdx.y;
   RState& st = b.st[k];
   if (st.done) return;
   const RInst in = b.inst[k];
+  const int rb = blockIdx.x;
+  const int nrb = (in.m + 31) / 32;
+  if (rb >= nrb) return;
   const int nt = (st.n_active + b.tw - 1) / b.tw;
   const float2* part = b.part + in.p_off;
-  double p2 = 0.0;
-  for (int i = threadIdx.x; i < in.m; i += kRThreads) {
-    float s = 0.f, c = 0.f;
-    for (int t = 0; t < nt; ++t) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = rb * 32 + lane;
+  float s = 0.f, c = 0.f;
+  if (i < in.m) {
+    int t = warp;
+    for (; t + 3 * (kRThreads / 32) < nt; t += 4 * (kRThreads / 32)) {
+      float2 v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[q] = __ldcg(part + (long long)(t + q * (kRThreads / 32)) * in.m + i);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) df_add(s, c, v[q].x, v[q].y);
+    }
+    for (; t < nt; t += kRThreads / 32) {
       const float2 v = __ldcg(part + (long long)t * in.m + i);
       df_add(s, c, v.x, v.y);
     }
-    float rh, rl;
-    if (b.power) {
-      two_sum(s, c, rh, rl);
-    } else {
-      float dh, de;
-      two_sum(b.yh[in.r_off + i], -s, dh, de);
-      de += b.yl[in.r_off + i] - c;
-      two_sum(dh, de, rh, rl);
-    }
-    b.rh[in.r_off + i] = rh;
-    b.rl[in.r_off + i] = rl;
-    const double r = (double)rh + (double)rl;
-    p2 += 0.5 * r * r;
   }
+  s_part[warp][lane] = make_float2(s, c);
+  __syncthreads();
+  if (warp == 0) {
+    for (int w = 1; w < kRThreads / 32; ++w) df_add(s, c, s_part[w][lane].x, s_part[w][lane].y);
+    double p2 = 0.0;
+    if (i < in.m) {
+      float rh, rl;
+      if (b.power) {
+        two_sum(s, c, rh, rl);
+      } else {
+        float dh, de;
+        two_sum(b.yh[in.r_off + i], -s, dh, de);
+        de += b.yl[in.r_off + i] - c;
+        two_sum(dh, de, rh, rl);
+      }
+      b.rh[in.r_off + i] = rh;
+      b.rl[in.r_off + i] = rl;
+      const double r = (double)rh + (double)rl;
+      p2 = 0.5 * r * r;
+    }
+    p2 = wsum(p2);
+    if (lane == 0) {
+      b.rblkP[(long long)k * kRRowBlocks + rb] = p2;
+      __threadfence();
+      const unsigned prev = atomicAdd(&b.rcnt[k], 1u);
+      s_last = prev == (unsigned)nrb - 1u;
+    }
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // the instance's last block: P in block order, the restart terms and translation steps
+  double p2 = 0.0;
+  for (int q = threadIdx.x; q < nrb; q += kRThreads) p2 += __ldcg(b.rblkP + (long long)k * kRRowBlocks + q);
   p2 = bsum(p2, sh);
   const long long t0 = in.t_off;
   double d = 0.0, ep = 0.0;
@@ -443,6 +506,7 @@ __global__ void __launch_bounds__(kRThreads) k_rresid(RBuf b, int slot) {
   d = bsum(d, sh);
   ep = bmax(ep, sh);
   if (threadIdx.x == 0) {
+    b.rcnt[k] = 0u;
     st.eps = ep;
     st.dot = d;
     if (b.power) {
@@ -462,7 +526,7 @@ __global__ void __launch_bounds__(kRThreads) k_rresid(RBuf b, int slot) {
 }
 
 cudaError_t launch_rresid(const RBuf& b, int slot, cudaStream_t s) {
-  k_rresid<<<b.B, kRThreads, 0, s>>>(b, slot);
+  k_rresid<<<dim3(kRRowBlocks, b.B), kRThreads, 0, s>>>(b, slot);
   return cudaGetLastError();
 }
 

@@ -23,6 +23,7 @@ constexpr int kRTileMin = 8;        // columns per tile: tw in {8, 16, 32}, pick
 constexpr int kRTileMax = 32;
 constexpr int kRThreads = 256;
 constexpr int kRMaxRows = 1024;     // m_k limit (r_k in shared memory)
+constexpr int kRRowBlocks = kRMaxRows / 32;   // row blocks of the residual kernel per instance
 
 struct RInst {                      // per instance, fixed at setup
   long long a_off;                  // offset of A_k in the float arena (column-major, lda)
@@ -94,6 +95,8 @@ struct RBuf {
   int* chunks;                      // chunks run by the device-side loop of the solve graph
   int tw;                           // columns per tile of the work list (kRTileMin..kRTileMax)
   double* work;                     // sum over iterations of sum_k m_k |S_k| (A elements read), or null
+  double* rblkP;                    // per (instance, row block): partial of P of the residual kernel
+  unsigned int* rcnt;               // per instance: row blocks of the residual kernel done (zeroed)
 };
 
 cudaError_t launch_rnorms(const RBuf& b, long long total_cols, cudaStream_t s);
