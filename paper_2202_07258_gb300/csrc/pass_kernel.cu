@@ -113,6 +113,48 @@ __device__ __forceinline__ void dot_pair(const float4* colA, const float4* colB,
   gb = df2_norm(sb[0], DP == kX2 ? cb[0] : 0.0f);
 }
 
+// As dot_pair<kF32> over at most RTOT float4 chunks per lane, with the lane's first RT chunks
+// of r (rows lane + 32 t) held in registers for the whole iteration instead of read from
+// shared memory for every pair; the same accumulation order, so the same sums bit for bit.
+template <int RT, int RTOT>
+__device__ __forceinline__ void dot_pair_reg(const float4* colA, const float4* colB, const float4 (&rr)[RT],
+                                             const float4* srh, int m4q, int lane, float2& ga, float2& gb) {
+  const ulonglong2* A2 = reinterpret_cast<const ulonglong2*>(colA);
+  const ulonglong2* B2 = reinterpret_cast<const ulonglong2*>(colB);
+  f32x2 sa2[2] = {0ull, 0ull}, sb2[2] = {0ull, 0ull};
+#pragma unroll
+  for (int t = 0; t < RTOT; ++t) {
+    const int i = lane + 32 * t;
+    if (i < m4q) {
+      const ulonglong2 a = A2[i], b = B2[i];
+      const float4 r4 = t < RT ? rr[t < RT ? t : 0] : srh[i];
+      const f32x2 h0 = x2_pack(r4.x, r4.y), h1 = x2_pack(r4.z, r4.w);
+      sa2[0] = x2_fma(a.x, h0, sa2[0]);
+      sa2[1] = x2_fma(a.y, h1, sa2[1]);
+      sb2[0] = x2_fma(b.x, h0, sb2[0]);
+      sb2[1] = x2_fma(b.y, h1, sb2[1]);
+    }
+  }
+  float sa[4], sb[4];
+  x2_unpack(sa2[0], sa[0], sa[1]);
+  x2_unpack(sa2[1], sa[2], sa[3]);
+  x2_unpack(sb2[0], sb[0], sb[1]);
+  x2_unpack(sb2[1], sb[2], sb[3]);
+  sa[0] += sa[1];
+  sa[2] += sa[3];
+  sa[0] += sa[2];
+  sb[0] += sb[1];
+  sb[2] += sb[3];
+  sb[0] += sb[2];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sa[0] += __shfl_xor_sync(0xffffffffu, sa[0], o);
+    sb[0] += __shfl_xor_sync(0xffffffffu, sb[0], o);
+  }
+  ga = df2_norm(sa[0], 0.0f);
+  gb = df2_norm(sb[0], 0.0f);
+}
+
 // q_slice += sum over one stage's columns of a_j x_j on the lane's rows (QT float4 chunks,
 // as packed pairs), columns with x_j = 0 skipped (the test is uniform across the warp).  A
 // stage holds at most 8 columns and their x values are read together.  With few row chunks
@@ -825,7 +867,7 @@ __global__ void __launch_bounds__(32 * (1 + DW + QW), 1)
     }
     for (int i = ct; i < m4q; i += NCONS) {
       srh[i] = __ldcg(reinterpret_cast<const float4*>(b.rh) + i);
-      srl[i] = __ldcg(reinterpret_cast<const float4*>(b.rl) + i);
+      if (DP == kX2) srl[i] = __ldcg(reinterpret_cast<const float4*>(b.rl) + i);   // float32 dots use r's high part
     }
     if (gap_iter && p.wstar && blockIdx.x == 0) {
       double acc = 0.0;
@@ -848,6 +890,15 @@ __global__ void __launch_bounds__(32 * (1 + DW + QW), 1)
     if (warp <= DW) {
       // ------------------------------------------------------------ dot warps
       const int dw = warp - 1;
+      // mode MIXED with at most 16 float4 row chunks per lane: r_k (high part) in registers
+      constexpr bool kRReg = PREC == kMix && QT <= 2;
+      constexpr int RT = kRReg ? 8 : 1;   // 16 chunks in registers spilled at 120 registers
+      float4 rr[RT];
+#pragma unroll
+      for (int t = 0; t < RT; ++t) {
+        const int i = lane + 32 * t;
+        rr[t] = (kRReg && i < m4q) ? srh[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
       const double eta_g = gap_iter ? s_etag : 0.0;
       const float2 bb = s_beta2[0], onepb = s_beta2[1];
       const bool want_eps = gap_iter && p.dual_mode == kTranslation && !p.wstar;
@@ -892,7 +943,8 @@ __global__ void __launch_bounds__(32 * (1 + DW + QW), 1)
         const float4* colA = reinterpret_cast<const float4*>(sbase);
         const float4* colB = reinterpret_cast<const float4*>(sbase + (ncol > 1 ? p.lda : 0));
         float2 ga, gb2;
-        dot_pair<DP>(colA, colB, srh, srl, m4q, lane, ga, gb2);
+        if constexpr (kRReg) dot_pair_reg<RT, 16>(colA, colB, rr, srh, m4q, lane, ga, gb2);
+        else dot_pair<DP>(colA, colB, srh, srl, m4q, lane, ga, gb2);
         __syncwarp();
         if (lane < ncol) {
           const int c = c0 + lane;
