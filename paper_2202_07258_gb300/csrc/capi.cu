@@ -117,16 +117,35 @@ struct bvls_handle {
   RefOut* ref_out = nullptr;
   cudaEvent_t ref_ev[2] = {nullptr, nullptr};
   long long grid_wait = kGridWaitCycles;  // bound of the persistent pass's grid-barrier waits
+  unsigned char* pool_cur = nullptr;       // device pool of dalloc
+  size_t pool_left = 0;
 };
 
 namespace {
 
+// Handle-owned device buffers: carved (256-byte aligned, 16 bytes of slack each) from pool
+// chunks of kPoolChunk bytes, a request larger than that in a chunk of its own; setup makes
+// a few dozen small buffers, and one cudaMalloc per buffer cost a few tenths of a ms.
+constexpr size_t kPoolChunk = size_t(4) << 20;
+
 template <typename T>
 bvls_status dalloc(bvls_handle* h, T** p, size_t count) {
-  void* q = nullptr;
-  CK(cudaMalloc(&q, count * sizeof(T) + 16));
-  h->allocs.push_back(q);
-  *p = static_cast<T*>(q);
+  const size_t bytes = (count * sizeof(T) + 16 + 255) & ~size_t(255);
+  if (bytes > h->pool_left) {
+    const size_t chunk = std::max(bytes, kPoolChunk);
+    void* q = nullptr;
+    CK(cudaMalloc(&q, chunk));
+    h->allocs.push_back(q);
+    if (bytes >= kPoolChunk) {   // a large buffer keeps its chunk; the current pool stays
+      *p = static_cast<T*>(q);
+      return BVLS_OK;
+    }
+    h->pool_cur = static_cast<unsigned char*>(q);
+    h->pool_left = chunk;
+  }
+  *p = reinterpret_cast<T*>(h->pool_cur);
+  h->pool_cur += bytes;
+  h->pool_left -= bytes;
   return BVLS_OK;
 }
 
@@ -172,13 +191,13 @@ const std::vector<MomEntry>& momentum_table() {
   return tab;
 }
 
-// w = A^T t for a host direction t; returns whether a_j^T t < 0 (with its rounding bound)
-// on every nonzero column with u_j = +inf.
+// w = A^T t for a host direction t (or, with w_ready, the w already in h->w); returns whether
+// a_j^T t < 0 (with its rounding bound) on every nonzero column with u_j = +inf.
 bvls_status try_direction(bvls_handle* h, const std::vector<double>& t,
                           const std::vector<uint8_t>& jinf, const std::vector<double>& nrm,
-                          bool* ok) {
+                          bool* ok, bool w_ready = false) {
   CK(cudaMemcpyAsync(h->t, t.data(), sizeof(double) * h->m, cudaMemcpyHostToDevice, h->s));
-  CK(launch_col_dots(h->A, h->lda, h->m, h->n, h->t, h->w, h->s));
+  if (!w_ready) CK(launch_col_dots(h->A, h->lda, h->m, h->n, h->t, h->w, h->s));
   std::vector<double> w(h->n);
   CK(cudaMemcpyAsync(w.data(), h->w, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->s));
   CK(cudaStreamSynchronize(h->s));
@@ -626,7 +645,8 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
   }
   CK(cudaMemcpyAsync(h->jinf, jinf.data(), n, cudaMemcpyHostToDevice, h->s));
   CK(cudaMemsetAsync(h->w, 0, sizeof(double) * n, h->s));
-  CK(launch_col_norms(h->A, h->lda, m, n, h->nrm, h->s));
+  // with no caller t, the first candidate t = -1 gets its products w = A^T t in this pass
+  CK(launch_col_norms(h->A, h->lda, m, n, h->nrm, h->s, (any_inf && !t) ? h->w : nullptr));
   std::vector<double> nrm(n);
   CK(cudaMemcpyAsync(nrm.data(), h->nrm, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
   CK(cudaStreamSynchronize(h->s));
@@ -645,26 +665,28 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
     h->t_choice = 0;
   } else {
     bool ok = false;
-    std::vector<double> tv(m, -1.0);  // Proposition 2, case 3
-    TRY(try_direction(h, tv, jinf, nrm, &ok));
+    std::vector<double> tv(m, -1.0);  // Proposition 2, case 3 (w from the column-norm pass)
+    TRY(try_direction(h, tv, jinf, nrm, &ok, true));
     if (ok) h->t_choice = 1;
     if (!ok) {
-      double *rs = nullptr, *rs_part = nullptr;
+      // s = sum_k a_k and c = A^T s serve the next two candidates: minus the mean column has
+      // w = -c / n, and the column most correlated with all others is argmax_j c_j
+      double *rs = nullptr, *rs_part = nullptr, *corr_d = nullptr;
       TRY(dalloc(h, &rs, m));
       TRY(dalloc(h, &rs_part, row_sums_scratch(m, n)));
+      TRY(dalloc(h, &corr_d, n));
       CK(launch_row_sums(h->A, h->lda, m, n, rs_part, rs, h->s));
-      std::vector<double> s(m);
+      CK(launch_col_dots(h->A, h->lda, m, n, rs, corr_d, h->s));
+      CK(launch_scale_neg(corr_d, n, 1.0 / n, h->w, h->s));
+      std::vector<double> s(m), corr(n);
       CK(cudaMemcpyAsync(s.data(), rs, sizeof(double) * m, cudaMemcpyDeviceToHost, h->s));
+      CK(cudaMemcpyAsync(corr.data(), corr_d, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
       CK(cudaStreamSynchronize(h->s));
       for (int i = 0; i < m; ++i) tv[i] = -s[i] / n;  // minus the mean column
-      TRY(try_direction(h, tv, jinf, nrm, &ok));
+      TRY(try_direction(h, tv, jinf, nrm, &ok, true));
       if (ok) h->t_choice = 2;
       if (!ok) {
         // minus the column most correlated with all others: argmax_j a_j^T sum_k a_k
-        TRY(try_direction(h, s, std::vector<uint8_t>(n, 0), nrm, &ok));  // w = A^T s
-        std::vector<double> corr(n);
-        CK(cudaMemcpyAsync(corr.data(), h->w, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
-        CK(cudaStreamSynchronize(h->s));
         int jb = 0;
         for (int j = 1; j < n; ++j)
           if (corr[j] > corr[jb]) jb = j;

@@ -245,28 +245,6 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   return v;
 }
 
-// One arrival of this CTA at the grid barrier (gb[0] arrivals, gb[1] generation) and a
-// bounded wait for the others; called by one thread once the CTA's participating threads
-// have synchronised.
-// The last arrival resets the count and then publishes the next generation.
-__device__ inline bool grid_arrive_wait(unsigned* gb, unsigned nblocks, unsigned gen) {
-  __threadfence();
-  const unsigned prev = atomicAdd(&gb[0], 1u);
-  if (prev == nblocks - 1) {
-    atomicExch(&gb[0], 0u);
-    __threadfence();
-    atomicAdd(&gb[1], 1u);
-    return true;
-  }
-  if (ld_acquire_u32(&gb[1]) != gen) return true;
-  const long long t0 = clock64();
-  while (ld_acquire_u32(&gb[1]) == gen) {
-    if (clock64() - t0 > kGridWaitCycles) return false;
-  }
-  __threadfence();
-  return true;
-}
-
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
   unsigned long long v;
   asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -388,7 +366,11 @@ void record_error(const char* msg);
 
 // Setup kernels (setup_kernels.cu).
 cudaError_t launch_check_finite(const float* A, int lda, int m, int n, int* flag, cudaStream_t s);
-cudaError_t launch_col_norms(const float* A, int lda, int m, int n, double* nrm, cudaStream_t s);
+// ||a_j||; with wneg1, also a_j^T (-1) (the direction t = -1) in the same pass.
+cudaError_t launch_col_norms(const float* A, int lda, int m, int n, double* nrm, cudaStream_t s,
+                             double* wneg1 = nullptr);
+// w_j = -c_j * inv
+cudaError_t launch_scale_neg(const double* c, int n, double inv, double* w, cudaStream_t s);
 cudaError_t launch_col_dots(const float* A, int lda, int m, int n, const double* t, double* w,
                             cudaStream_t s);
 // out_i = sum_j a_ij (deterministic); part: row_sums_scratch(m, n) doubles.

@@ -24,21 +24,42 @@ cudaError_t launch_check_finite(const float* A, int lda, int m, int n, int* flag
 }
 
 // one warp per column, float64 accumulation
-__global__ void k_col_norms(const float* __restrict__ A, int lda, int m, int n, double* nrm) {
+// ||a_j||_2 and, when wneg1 is given, a_j^T (-1) = -sum_i a_ij in the same pass (the
+// summation order of k_col_dots with t = -1, so the same values bit for bit).
+__global__ void k_col_norms(const float* __restrict__ A, int lda, int m, int n, double* nrm, double* wneg1) {
   const int lane = threadIdx.x & 31;
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int j = w; j < n; j += nw) {
     const float* a = A + (size_t)j * lda;
-    double s = 0.0;
-    for (int i = lane; i < m; i += 32) s = fma((double)a[i], (double)a[i], s);
+    double s = 0.0, c = 0.0;
+    for (int i = lane; i < m; i += 32) {
+      const double v = (double)a[i];
+      s = fma(v, v, s);
+      c = fma(v, -1.0, c);
+    }
     s = warp_sum_d(s);
-    if (lane == 0) nrm[j] = sqrt(s);
+    c = warp_sum_d(c);
+    if (lane == 0) {
+      nrm[j] = sqrt(s);
+      if (wneg1) wneg1[j] = c;
+    }
   }
 }
 
-cudaError_t launch_col_norms(const float* A, int lda, int m, int n, double* nrm, cudaStream_t s) {
-  k_col_norms<<<1024, 256, 0, s>>>(A, lda, m, n, nrm);
+cudaError_t launch_col_norms(const float* A, int lda, int m, int n, double* nrm, cudaStream_t s,
+                             double* wneg1) {
+  k_col_norms<<<1024, 256, 0, s>>>(A, lda, m, n, nrm, wneg1);
+  return cudaGetLastError();
+}
+
+// w_j = -c_j / n (the minus-mean-column direction from c = A^T (sum_k a_k)).
+__global__ void k_scale_neg(const double* c, int n, double inv, double* w) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) w[j] = -c[j] * inv;
+}
+
+cudaError_t launch_scale_neg(const double* c, int n, double inv, double* w, cudaStream_t s) {
+  k_scale_neg<<<(n + 255) / 256, 256, 0, s>>>(c, n, inv, w);
   return cudaGetLastError();
 }
 
@@ -219,9 +240,11 @@ __global__ void __launch_bounds__(kPowThreads, 1)
   constexpr int NW = kPowThreads / 32;
   const int nslices = lda / 32;
   const float4* A4 = reinterpret_cast<const float4*>(A);
-  unsigned gen = 0;
+  // grid barriers on a monotonic 64-bit arrival count (gb[0..1], zeroed before the launch):
+  // barrier number nb completes when the count reaches gridDim.x * nb
+  unsigned long long* gcount = reinterpret_cast<unsigned long long*>(gb);
+  unsigned long long nbar = 0ull;
   if (tid == 0) {
-    gen = ld_acquire_u32(&gb[1]);
     s_ok = 1;
     s_beta = 0.0;
   }
@@ -233,7 +256,7 @@ __global__ void __launch_bounds__(kPowThreads, 1)
   __syncthreads();
   auto barrier = [&]() -> bool {
     __syncthreads();
-    if (tid == 0 && !grid_arrive_wait(gb, gridDim.x, gen++)) s_ok = 0;
+    if (tid == 0 && !grid_count_sync(gcount, (unsigned long long)gridDim.x * ++nbar, kGridWaitCycles)) s_ok = 0;
     __syncthreads();
     return s_ok != 0;
   };
