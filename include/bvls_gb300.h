@@ -205,7 +205,7 @@ BVLS_API void bvls_default_opts(bvls_opts* opts);
  *   stream  a cudaStream_t (0 = legacy default stream).
  *   out     receives the handle.
  * Setup computes the column norms ||a_j||_2 (used by Eq. (safe_rule)), w = A^T t and the
- * step constant L (1.05 x the largest Ritz value of 32 Lanczos steps on A^T A, an estimate of
+ * step constant L (1.05 x the largest Ritz value of 20 Lanczos steps on A^T A, an estimate of
  * ||A||_2^2 from below; 100 power steps where the one-launch form does not fit).
  * Limits: 1 <= m <= 24576 (the residual is staged in shared memory), 1 <= n < 2^31,
  * lda*n*4 bytes addressable.  Errors: EINVAL, ENOTSUP, ENOMEM, ECUDA, ENONFINITE (A).

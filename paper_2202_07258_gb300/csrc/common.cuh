@@ -26,7 +26,7 @@ constexpr int kRedThreads = 256;  // blocks of the O(|A|) epilogue kernels
 constexpr int kCompactThreads = 1024;
 constexpr int kMaxRows = 24576;   // r is staged in shared memory: 8 bytes per row
 constexpr int kPassDot = 8;       // dot warps of the fused pass
-constexpr int kLanczosSteps = 32; // Lanczos steps of the setup's step-constant estimate
+constexpr int kLanczosSteps = 20; // Lanczos steps of the setup's step-constant estimate
 constexpr int kPassTmax = 8;      // float4 row chunks owned by one lane of a q warp
 constexpr int kPassMaxStages = 32;
 constexpr int kMaxGridFlags = 1024;  // grid barrier words of the persistent pass

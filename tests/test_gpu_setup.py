@@ -26,7 +26,9 @@ def P():
 
 
 CASES = [
-    ("gaussian_2000x10000", lambda: W.nnls_gaussian(2000, 10000, 0.05, 0.01, 0), 2e-3),
+    # no spectral gap at the top of a Gaussian matrix's spectrum: 20 Lanczos steps land within
+    # about 1e-3 of ||A||^2 (float64 replay), far inside the factor 1.05
+    ("gaussian_2000x10000", lambda: W.nnls_gaussian(2000, 10000, 0.05, 0.01, 0), 5e-3),
     ("abs_1000x2000", lambda: W.nnls_abs_gaussian(1000, 2000, 0.05, 1.0, 0), 1e-5),
     ("bvls_224x512", lambda: W.bvls_dirichlet_shared(224, 512, 1, 8, 0.005, 0), 1e-5),
     ("abs_30x50", lambda: W.nnls_abs_gaussian(30, 50, 0.2, 1.0, 3), 1e-5),
@@ -47,4 +49,4 @@ def test_step_constant_brackets_the_spectral_norm(P, name, make, low):
     s.close()
     ratio = info["L"] / (1.05 * lam)
     assert ratio <= 1.0 + 1e-5, (name, ratio)        # a Rayleigh quotient: never above
-    assert ratio >= 1.0 - low, (name, ratio)         # and close after 32 steps
+    assert ratio >= 1.0 - low, (name, ratio)         # and close after 20 steps
