@@ -45,7 +45,7 @@ def ragged_sample():
 
 
 WORKLOADS = {
-    "nnls_abs_gaussian_2000x10000": single(lambda: W.nnls_abs_gaussian(2000, 10000, 0.05, 1.0, 0), 1e-9),
+    "nnls_abs_gaussian_2000x10000": single(lambda: W.nnls_abs_gaussian(2000, 10000, 0.05, 1.0, 0), 1e-8),
     "bvls_table2_1000x2000": single(lambda: W.bvls_table2(1000, 2000, 0), 1e-10),
     "bvls_dirichlet_224x512_B4096": batch_sample,
     "mixed_uneven_abs_B64": ragged_sample,
@@ -57,12 +57,18 @@ def optimum(A, y, l, u, tol):
     y = y.astype(np.float64)
     t0 = time.perf_counter()
     r = O.solve(A, y, l, u, tol=tol, screen_every=10, max_iter=400000)
-    xs = O.polish(A, y, r.x, l, u, tau=1e-7)
-    kkt = O.kkt_residual(A, y, xs, l, u)
+    # the free set of the polish step is read off the solve's iterate with a margin tau; the
+    # first margin whose polished point passes the optimality conditions is kept
+    bound = 1e-9 * (1 + float(np.abs(A.T @ y).max()))
+    for tau in (1e-7, 1e-9, 1e-6, 1e-5):
+        xs = O.polish(A, y, r.x, l, u, tau=tau)
+        kkt = O.kkt_residual(A, y, xs, l, u)
+        if kkt < bound:
+            break
     F = O.free_set(xs, l, u, 1e-7)
     inside = bool(np.all(xs >= l - 1e-12) and np.all(xs <= u + 1e-12))
     unique = inside and F.size < A.shape[0] and np.linalg.matrix_rank(A[:, F]) == F.size
-    ok = unique and kkt < 1e-9 * (1 + float(np.abs(A.T @ y).max()))
+    ok = unique and kkt < bound
     rec = {"m": int(A.shape[0]), "n": int(A.shape[1]), "oracle_iters": int(r.iters), "oracle_gap": float(r.gap),
            "oracle_P": float(r.primal), "seconds": time.perf_counter() - t0}
     if ok:
