@@ -248,6 +248,9 @@ typedef struct {
   double refine_ms;       /* refinement kernel time (CUDA events) */
   int refine_out_of_rounds; /* instances declined after the last round */
   int refine_not_unique;    /* instances declined because |F| > min(m, 2048) */
+  int steps_persistent;     /* 1: the K - 1 tensor-core steps between two evaluations ran as
+                               one cluster launch with the iteration state on chip */
+  int pad0;
 } bvls_batch_info;
 
 /*
@@ -264,7 +267,10 @@ typedef struct {
  *                 steps: g_k = g_{k-1} - bf16(A^T A) bf16(x_k - x_{k-1}) for all active
  *                 instances in one tcgen05 GEMM with float32 accumulation, whose momentum
  *                 term also takes bf16(x_k - x_{k-1}).  max_iter is rounded up to a
- *                 multiple of K; single_pass is ignored.
+ *                 multiple of K.  single_pass 1 (default) runs the K - 1 steps between two
+ *                 evaluations as one launch of clusters of npad / 128 CTAs that keep x, g
+ *                 and bf16(x_k - x_{k-1}) in tensor and shared memory (when npad <= 512);
+ *                 0 or 2: one launch per step.  Both give the same iterates.
  *   X_out         any; B x n doubles: per instance, the iterate of its last evaluation with
  *                 screened coordinates at their bounds.
  *   screened_out  any; B x n bytes or NULL (0 preserved, 1 at l_j, 2 at u_j).

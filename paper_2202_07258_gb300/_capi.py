@@ -97,6 +97,8 @@ class bvls_batch_info(ctypes.Structure):
         ("refine_ms", ctypes.c_double),
         ("refine_out_of_rounds", ctypes.c_int),
         ("refine_not_unique", ctypes.c_int),
+        ("steps_persistent", ctypes.c_int),
+        ("pad0", ctypes.c_int),
     ]
 
     def as_dict(self):

@@ -9,6 +9,8 @@
 //               coordinates, the dual point (Eq. (BVLR_dual_up) / (BVLR_dual_up2)), the gap in
 //               its nonnegative-sum form, the Gap safe radius (Eq. (GAP_Safe_sph)), the sphere
 //               test (Eq. (safe_rule)), the stop test, and the step to x_{k+1} from the exact g.
+//   k_bsteps    the K - 1 tensor-core steps between two evaluations in one launch of
+//               clusters that keep x, g and the GEMM operand d on chip (npad <= 512).
 //   k_bcompact  retires finished instances from the active list (stable).
 #include <cuda_bf16.h>
 
@@ -107,6 +109,109 @@ __device__ __forceinline__ float2 fista_step(float2 xk, float2 dk, float gv, flo
   if (df2_lt(xn, l2)) xn = l2;
   if (df2_lt(u2, xn)) xn = u2;
   return xn;
+}
+
+// Momentum of iteration k for one instance (Section 5, FISTA with gradient restart): T = t_k
+// from tp = t_{k-1} and the restart-test sum of iteration k - 1; returns b = (t_k - 1) / t_{k+1}.
+__device__ __forceinline__ float bstep_momentum(float tp, float dsum, int restart, float& T) {
+  T = (restart && dsum < 0.f) ? 1.f : 0.5f * (1.f + sqrtf(1.f + 4.f * tp * tp));
+  const float tn = 0.5f * (1.f + sqrtf(1.f + 4.f * T * T));
+  return (T - 1.f) / tn;
+}
+
+// One (coordinate, instance) element of the tensor-core step: g_k = g_{k-1} - acc; for a
+// preserved coordinate x_{k+1} = clip(x_k + delta, l, u) with g_v = (1 + b) g_k - b g_{k-1}
+// and the increment delta = b d_k + g_v / L formed in float32 (its rounding error is
+// relative to the increment, so it vanishes with it) and added to the double-float iterate
+// by two TwoSums; d = x_{k+1} - x_k in float32 (delta, or the distance to the bound that
+// clipped it).  A fixed coordinate keeps x_{k+1} = x_k, d = 0.  Returns the restart-test
+// term g_v d.
+__device__ __forceinline__ float bstep_elem(float gp, float acc, float2 xk, float dk, bool fixed, float be,
+                                            float invLf, float2 lj, float2 uj, float& gk, float2& xn, float& dx) {
+  gk = gp - acc;
+  xn = xk;
+  dx = 0.f;
+  if (fixed) return 0.f;
+  const float gv = fmaf(be, gk - gp, gk);
+  const float delta = fmaf(gv, invLf, be * dk);
+  float s, e, h, l;
+  two_sum(xk.x, delta, s, e);
+  two_sum(s, e + xk.y, h, l);
+  xn = make_float2(h, l);
+  dx = delta;
+  if (df2_lt(xn, lj)) {
+    xn = lj;
+    dx = (lj.x - xk.x) + (lj.y - xk.y);
+  } else if (df2_lt(uj, xn)) {
+    xn = uj;
+    dx = (uj.x - xk.x) + (uj.y - xk.y);
+  }
+  return gv * dx;
+}
+
+// bstep_elem for two instance columns of one coordinate, the float32 operations of both on
+// packed f32x2 instructions (each lane rounds as the scalar instruction; the products are
+// formed as fma(a, b, -0), which rounds as a*b and keeps its sign) and the clip per lane.
+// Inputs are bit patterns (TMEM words): g_{k-1}, acc, x high and x low of columns 0 and 1.
+// The fixed and inactive cases are left to the caller.
+__device__ __forceinline__ void bstep_pair(uint32_t gp0, uint32_t gp1, uint32_t ac0, uint32_t ac1, uint32_t xh0,
+                                           uint32_t xh1, uint32_t xl0, uint32_t xl1, float dk0, float dk1,
+                                           float be0, float be1, float invLf, float2 lj, float2 uj, float (&gk)[2],
+                                           float2 (&xn)[2], float (&dx)[2], float (&dv)[2]) {
+  constexpr f32x2 kNegZero = 0x8000000080000000ull;
+  const f32x2 gp = x2_pack(__uint_as_float(gp0), __uint_as_float(gp1));
+  const f32x2 ac = x2_pack(__uint_as_float(ac0), __uint_as_float(ac1));
+  const f32x2 xh = x2_pack(__uint_as_float(xh0), __uint_as_float(xh1));
+  const f32x2 xl = x2_pack(__uint_as_float(xl0), __uint_as_float(xl1));
+  const f32x2 be = x2_pack(be0, be1);
+  const f32x2 gk2 = x2_sub(gp, ac);
+  const f32x2 gv = x2_fma(be, x2_sub(gk2, gp), gk2);
+  const f32x2 delta = x2_fma(gv, x2_pack(invLf, invLf), x2_fma(be, x2_pack(dk0, dk1), kNegZero));
+  // two TwoSums: (s, e) = xh + delta, (h, l) = s + (e + xl)
+  const f32x2 s = x2_add(xh, delta);
+  f32x2 bb = x2_sub(s, xh);
+  const f32x2 e = x2_add(x2_sub(xh, x2_sub(s, bb)), x2_sub(delta, bb));
+  const f32x2 e2 = x2_add(e, xl);
+  const f32x2 h = x2_add(s, e2);
+  bb = x2_sub(h, s);
+  const f32x2 l = x2_add(x2_sub(s, x2_sub(h, bb)), x2_sub(e2, bb));
+  float hv[2], lv[2], dl[2];
+  x2_unpack(h, hv[0], hv[1]);
+  x2_unpack(l, lv[0], lv[1]);
+  x2_unpack(delta, dl[0], dl[1]);
+  x2_unpack(gk2, gk[0], gk[1]);
+  const float2 xk[2] = {make_float2(__uint_as_float(xh0), __uint_as_float(xl0)),
+                        make_float2(__uint_as_float(xh1), __uint_as_float(xl1))};
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    xn[t] = make_float2(hv[t], lv[t]);
+    dx[t] = dl[t];
+    if (df2_lt(xn[t], lj)) {
+      xn[t] = lj;
+      dx[t] = (lj.x - xk[t].x) + (lj.y - xk[t].y);
+    } else if (df2_lt(uj, xn[t])) {
+      xn[t] = uj;
+      dx[t] = (uj.x - xk[t].x) + (uj.y - xk[t].y);
+    }
+  }
+  const f32x2 d = x2_fma(gv, x2_pack(dx[0], dx[1]), kNegZero);
+  x2_unpack(d, dv[0], dv[1]);
+}
+
+// Column sums over the 32 lanes of v[0..15] (v is overwritten): lanes c and c + 16 return the
+// sum of column c (a transposed butterfly, 16 shuffles).
+__device__ __forceinline__ float lane_sums16(float (&v)[16], int lane) {
+#pragma unroll
+  for (int o = 8; o >= 1; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int t = 0; t < o; ++t) {
+      const float send = up ? v[t] : v[t + o];
+      const float keep = up ? v[t + o] : v[t];
+      v[t] = keep + __shfl_xor_sync(kFull, send, o);
+    }
+  }
+  return v[0] + __shfl_xor_sync(kFull, v[0], 16);
 }
 
 }  // namespace
@@ -260,9 +365,8 @@ __global__ void __launch_bounds__(kBStepThreads, 1) k_bstep(const __grid_constan
       const float tp = b.tval[s ^ 1][inst];
       float dsum = 0.f;
       for (int t = 0; t < MT; ++t) dsum += b.dotp[s ^ 1][(size_t)t * p.B + inst];
-      const float T = (p.restart && dsum < 0.f) ? 1.f : 0.5f * (1.f + sqrtf(1.f + 4.f * tp * tp));
-      const float tn = 0.5f * (1.f + sqrtf(1.f + 4.f * T * T));
-      beta = (T - 1.f) / tn;
+      float T;
+      beta = bstep_momentum(tp, dsum, p.restart, T);
       if (mt == 0) b.tval[s][inst] = T;
     }
     s_beta[tid] = beta;
@@ -355,7 +459,7 @@ __global__ void __launch_bounds__(kBStepThreads, 1) k_bstep(const __grid_constan
   const int jg = mt * kBTile + i;
   const bool jv = jg < p.n;
   const float2 lj = s_l[i], uj = s_u[i];
-  const float2 invL2 = p.invL2;
+  const float invLf = p.invL2.x;
   const float* __restrict__ Gp = b.G[s ^ 1];
   float* Gc = b.G[s];
   const float2* __restrict__ Xc = b.X[s];
@@ -393,46 +497,32 @@ __global__ void __launch_bounds__(kBStepThreads, 1) k_bstep(const __grid_constan
   if (have) {
     float acc[32];
     tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, acc);
-    float dv[32];
 #pragma unroll
-    for (int c8 = 0; c8 < 32; c8 += 8) {
-      if (c8 > 0) load8(c8);
+    for (int h = 0; h < 32; h += 16) {
+      float dv[16];
 #pragma unroll
-      for (int cc = 0; cc < 8; ++cc) {
-        const int inst = s_inst[c0 + c8 + cc];
-        dv[c8 + cc] = 0.f;
-        if (inst >= 0 && jv) {
-          const size_t o = (size_t)inst * p.npad + jg;
-          const float gk = gp[cc] - acc[c8 + cc];
-          float2 xn = xk[cc];
-          float dx = 0.f;
-          if (!fl[cc]) {
-            const float be = s_beta[c0 + c8 + cc];
-            const float gv = fmaf(be, gk - gp[cc], gk);  // (1 + b) g_k - b g_{k-1}
-            xn = fista_step(xk[cc], make_float2(__bfloat162float(dk[cc]), 0.f), gv, be, invL2, lj, uj);
-            const float2 d = df2_sub(xn, xk[cc]);
-            dx = d.x + d.y;
-            dv[c8 + cc] = gv * dx;
+      for (int c8 = 0; c8 < 16; c8 += 8) {
+        if (h + c8 > 0) load8(h + c8);
+#pragma unroll
+        for (int cc = 0; cc < 8; ++cc) {
+          const int inst = s_inst[c0 + h + c8 + cc];
+          dv[c8 + cc] = 0.f;
+          if (inst >= 0 && jv) {
+            const size_t o = (size_t)inst * p.npad + jg;
+            float gk, dx;
+            float2 xn;
+            dv[c8 + cc] = bstep_elem(gp[cc], acc[h + c8 + cc], xk[cc], __bfloat162float(dk[cc]), fl[cc] != 0,
+                                     s_beta[c0 + h + c8 + cc], invLf, lj, uj, gk, xn, dx);
+            Gc[o] = gk;
+            Xn[o] = xn;
+            Dn[o] = __float2bfloat16_rn(dx);
           }
-          Gc[o] = gk;
-          Xn[o] = xn;
-          Dn[o] = __float2bfloat16_rn(dx);
         }
       }
+      // restart-test partials of the warp's 32 coordinates for instance columns c0 + h + (0..15)
+      const float sum = lane_sums16(dv, lane);
+      if (lane < 16) s_dot[quarter][c0 + h + lane] = sum;
     }
-    // restart-test partials: transpose-reduce 32 values over the 32 lanes; lane L ends with
-    // the warp's sum for instance column c0 + L
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-      const bool up = (lane & o) != 0;
-#pragma unroll
-      for (int t = 0; t < o; ++t) {
-        const float send = up ? dv[t] : dv[t + o];
-        const float keep = up ? dv[t + o] : dv[t];
-        dv[t] = keep + __shfl_xor_sync(kFull, send, o);
-      }
-    }
-    s_dot[quarter][c0 + lane] = dv[0];
   }
   tc_fence_before();
   __syncthreads();
@@ -451,6 +541,365 @@ cudaError_t launch_bstep(const BParams& p, const BBuffers& b, int j, cudaStream_
   dim3 grid(p.npad / kBTile, (p.B + kBTile - 1) / kBTile);
   k_bstep<<<grid, kBStepThreads, bstep_smem_bytes(), s>>>(p, b, j);
   return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ persistent tensor-core steps
+// The run of tensor-core steps between two evaluations in one launch, with the iteration
+// state on chip.  A cluster of MT = npad / 128 CTAs (MT <= 4) covers one tile of 128
+// instances: CTA mt owns coordinates [128 mt, 128 mt + 128) of them.  Per CTA:
+//   TMEM    512 columns: the accumulator [0, 128), x_k as high and low float32 parts
+//           [128, 384), g_{k-1} [384, 512); lane = coordinate, column = instance.
+//   shared  the whole B operand d_k = bf16(x_k - x_{k-1}) of the tile's instances (npad / 64
+//           swizzled K chunks of 16 KB) and a ring of kBPStages 16 KB chunks of H~ (tensor
+//           copies, as in k_bstep).
+// A step k: the MMA lane waits for the peers' slices of d_k (one dfull phase per step),
+// issues the products over all K chunks in k_bstep's order and commits; the 16 warps run
+// k_bstep's element arithmetic on TMEM (bstep_pair: the same operations, two instance
+// columns per packed instruction), park the new d in the accumulator's columns and send
+// their restart-test partials into every CTA's shared memory; a cluster barrier (every
+// CTA has finished the products that read d_k, so also every copy of d_k, and the partials
+// have landed); each CTA writes d_{k+1} into its own slice of the B operand, sums the
+// partials into the next momentum and pushes the 32 KB slice into each peer with one bulk
+// copy, completing on the peer's dfull barrier.  Every copy is issued unconditionally and
+// awaited by its receiver before the receiver's next cluster barrier, so no CTA leaves while
+// a peer may still write to it; every wait is bounded.  The last step leaves g, x, dotp and
+// tval in global memory and the one before it x: everything the evaluation that follows
+// reads (it rewrites d itself).
+constexpr int kBPStages = 4;
+constexpr int kBPMaxTiles = 4;
+constexpr int kChunkBytes = kBTile * 128;        // one K chunk of 64 bf16 for 128 rows
+constexpr int kSliceBytes = 2 * kChunkBytes;     // a CTA's 128 coordinates of d: two K chunks
+constexpr uint32_t kTmX = 128, kTmXl = 256, kTmG = 384;
+
+__global__ void __launch_bounds__(kBStepThreads, 1)
+    k_bsteps(const __grid_constant__ BParams p, BBuffers b, int j0, int nsteps) {
+  BState* st = b.st;
+  if (st->done) return;
+  const int n_act = st->n_act;
+  const int mt = blockIdx.x, nt = blockIdx.y;  // the cluster spans blockIdx.x
+  if (nt * kBTile >= n_act) return;            // uniform over the cluster
+  const int MT = p.npad / kBTile;
+  const int nch = p.npad / kBChunk;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  unsigned char* sD = smem;                                // nch chunks: the B operand
+  unsigned char* sH = smem + (size_t)nch * kChunkBytes;    // kBPStages chunks of H~
+  __shared__ __align__(8) uint64_t full[kBPStages], empty[kBPStages], done, dfull;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_inst[kBTile];
+  __shared__ __align__(16) float s_beta[kBTile];
+  __shared__ float s_tval[kBTile];
+  __shared__ float2 s_l[kBTile], s_u[kBTile];
+  __shared__ float s_dot[4][kBTile];
+  __shared__ float s_part[2][kBPMaxTiles][kBTile];     // [step parity][coordinate tile][instance column]
+  __shared__ __align__(16) uint32_t s_fix[4][kBTile];  // bit `lane` of [quarter][column]: fixed coordinate
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int kb = st->kbase + j0;  // iteration of the first step
+  if (tid < kBTile) {
+    const int q = nt * kBTile + tid;
+    const int inst = q < n_act ? b.act[q] : -1;
+    s_inst[tid] = inst;
+    float beta = 0.f, T = 1.f;
+    if (inst >= 0) {
+      const int s = kb & 1;
+      const float tp = b.tval[s ^ 1][inst];
+      float dsum = 0.f;
+      for (int t = 0; t < MT; ++t) dsum += b.dotp[s ^ 1][(size_t)t * p.B + inst];
+      beta = bstep_momentum(tp, dsum, p.restart, T);
+      if (mt == 0 && nsteps == 1) b.tval[s][inst] = T;
+    }
+    s_beta[tid] = beta;
+    s_tval[tid] = T;
+    const int jj = mt * kBTile + tid;
+    s_l[tid] = jj < p.n ? p.l2[jj] : make_float2(0.f, 0.f);
+    s_u[tid] = jj < p.n ? p.u2[jj] : make_float2(0.f, 0.f);
+  }
+  if (warp == 0) tmem_alloc(&s_tmem, 512);
+  if (tid == 0) {
+    for (int q = 0; q < kBPStages; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], 1);
+    }
+    mbar_init(&done, 1);
+    mbar_init(&dfull, 1);
+    fence_barrier_init();
+  }
+  __syncthreads();  // s_inst
+  {
+    // d_k of the tile's instances (row B of D is zero) into the swizzled B operand
+    const __nv_bfloat16* Dsrc = b.D[kb & 1];
+    const int units = kBTile * 8 * nch;
+    for (int q = tid; q < units; q += kBStepThreads) {
+      const int c = q >> 10, rem = q & 1023;
+      const int r = rem >> 3, kc = rem & 7;
+      const int inst = s_inst[r];
+      const int row = inst >= 0 ? inst : p.B;
+      cp_async16(sD + (size_t)c * kChunkBytes + r * 128 + ((kc ^ (r & 7)) << 4),
+                 Dsrc + (size_t)row * p.npad + c * kBChunk + kc * 8);
+    }
+    cp_async_commit();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  const int quarter = warp & 3;
+  const int i = quarter * 32 + lane;
+  const int jg = mt * kBTile + i;
+  const bool jv = jg < p.n;
+  const int c0 = (warp >> 2) * 32;
+  const bool have = s_inst[c0] >= 0;  // active instances are packed at the front of the tile
+  const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
+  // this thread's coordinate in row c0 + cc of the B operand (c0 is a multiple of 8, so the
+  // swizzle term depends on cc only)
+  const int kin = i & 63;
+  unsigned char* const drow = sD + (size_t)(2 * mt + (i >> 6)) * kChunkBytes + (size_t)c0 * 128 + (kin & 7) * 2;
+  auto dptr = [&](int cc) {
+    return reinterpret_cast<__nv_bfloat16*>(drow + cc * 128 + ((((kin >> 3) ^ (cc & 7))) << 4));
+  };
+  const int nat = min(kBTile, n_act - nt * kBTile);  // active instance columns of the tile
+  if (have) {
+    // x_k and g_{k-1} into TMEM, fixed flags into bits
+    const float2* __restrict__ X0 = b.X[kb & 1];
+    const float* __restrict__ G0 = b.G[(kb & 1) ^ 1];
+#pragma unroll
+    for (int h = 0; h < 32; h += 16) {
+      float xh[16], xl[16], gg[16];
+#pragma unroll
+      for (int cc = 0; cc < 16; ++cc) {
+        const int inst = s_inst[c0 + h + cc];
+        float2 x = make_float2(0.f, 0.f);
+        float g = 0.f;
+        uint8_t f = 1;
+        if (inst >= 0 && jv) {
+          const size_t o = (size_t)inst * p.npad + jg;
+          x = X0[o];
+          g = G0[o];
+          f = b.flags[o];
+        }
+        xh[cc] = x.x;
+        xl[cc] = x.y;
+        gg[cc] = g;
+        const uint32_t w = __ballot_sync(kFull, f != 0);
+        if (lane == 0) s_fix[quarter][c0 + h + cc] = w;
+      }
+      tmem_st16(tl + kTmX + (uint32_t)(c0 + h), xh);
+      tmem_st16(tl + kTmXl + (uint32_t)(c0 + h), xl);
+      tmem_st16(tl + kTmG + (uint32_t)(c0 + h), gg);
+    }
+    tmem_wait_st();
+  }
+  cp_async_wait<0>();
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();  // every CTA of the cluster runs and has initialised its barriers
+  tc_fence_after();
+
+  const float2 lj = s_l[i], uj = s_u[i];
+  const float invLf = p.invL2.x;
+  const int total = nsteps * nch;  // H~ chunks over the launch
+  int issued = 0;
+  bool ok = true;
+  auto produce = [&](int lim) {  // thread 0: H~ chunks into the ring up to chunk lim - 1
+    for (; issued < lim; ++issued) {
+      const int stg = issued % kBPStages;
+      if (issued >= kBPStages && !mbar_wait(&empty[stg], ((issued / kBPStages) - 1) & 1)) ok = false;
+      mbar_arrive_expect_tx(&full[stg], (uint32_t)kChunkBytes);
+      tma_load_2d(sH + (size_t)stg * kChunkBytes, &p.tmH, (issued % nch) * kBChunk, mt * kBTile, &full[stg]);
+    }
+  };
+  if (tid == 0) produce(total < kBPStages ? total : kBPStages);
+  const uint32_t idesc = umma_idesc_bf16(kBTile, kBTile);
+  const size_t own = (size_t)mt * kSliceBytes;
+
+  for (int q = 0; q < nsteps; ++q) {
+    const int k = kb + q, s = k & 1;
+    const bool wr = q >= nsteps - 2;
+    const bool last = q == nsteps - 1;
+    if (warp == kBCopyWarps) {
+      if (lane == 0) {
+        if (q > 0 && MT > 1) {
+          // the peers' slices of d_k
+          mbar_arrive_expect_tx(&dfull, (uint32_t)((MT - 1) * kSliceBytes));
+          if (!mbar_wait_cluster(&dfull, (q - 1) & 1)) ok = false;
+        }
+        for (int c = 0; c < nch; ++c) {
+          const int g = q * nch + c, stg = g % kBPStages;
+          if (!mbar_wait(&full[stg], (g / kBPStages) & 1)) ok = false;
+          tc_fence_after();
+          const uint32_t sa = smem_u32(sH + (size_t)stg * kChunkBytes);
+          const uint32_t sb = smem_u32(sD + (size_t)c * kChunkBytes);
+#pragma unroll
+          for (int kk = 0; kk < kBChunk / 16; ++kk)
+            umma_bf16(tmem, umma_smem_desc_sw128(sa + kk * 32), umma_smem_desc_sw128(sb + kk * 32), idesc,
+                      c > 0 || kk > 0);
+          umma_commit(&empty[stg]);
+        }
+        umma_commit(&done);
+      }
+      __syncwarp();
+    } else if (warp == 0) {
+      if (lane == 0) {
+        const int lim = (q + 1) * nch + kBPStages;
+        produce(lim < total ? lim : total);
+      }
+      __syncwarp();
+    }
+
+    // epilogue (bstep_elem's arithmetic, two instance columns per packed instruction):
+    // thread = coordinate jg, instance columns c0 .. c0 + 31 in four groups of eight; the TMEM
+    // loads of group g + 1 are in flight while group g is computed
+    if (!mbar_wait(&done, q & 1)) ok = false;
+    __syncwarp();
+    tc_fence_after();
+    if (have) {
+      float* __restrict__ Gc = b.G[s];
+      float2* __restrict__ Xn = b.X[s ^ 1];
+      uint32_t R[2][4][8];  // [group parity][accumulator, g, x high, x low][column]
+      auto load_group = [&](int g, uint32_t (&r)[4][8]) {
+        const uint32_t cb = (uint32_t)(c0 + 8 * g);
+        tmem_ld8_nw(tl + cb, r[0]);
+        tmem_ld8_nw(tl + kTmG + cb, r[1]);
+        tmem_ld8_nw(tl + kTmX + cb, r[2]);
+        tmem_ld8_nw(tl + kTmXl + cb, r[3]);
+      };
+      load_group(0, R[0]);
+      float dv[16];
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        uint32_t (&r)[4][8] = R[g & 1];
+        tmem_wait_ld8(r[0]);
+        tmem_wait_ld8(r[1]);
+        tmem_wait_ld8(r[2]);
+        tmem_wait_ld8(r[3]);
+        if (g < 3) load_group(g + 1, R[(g + 1) & 1]);
+        const int cb = c0 + 8 * g;
+#pragma unroll
+        for (int c4 = 0; c4 < 8; c4 += 4) {
+          const float4 b4 = *reinterpret_cast<const float4*>(&s_beta[cb + c4]);
+          const uint4 f4 = *reinterpret_cast<const uint4*>(&s_fix[quarter][cb + c4]);
+          const float bev[4] = {b4.x, b4.y, b4.z, b4.w};
+          const uint32_t fw[4] = {f4.x, f4.y, f4.z, f4.w};
+#pragma unroll
+          for (int u = 0; u < 4; u += 2) {
+            const int cc = c4 + u;  // columns cb + cc, cb + cc + 1
+            const __nv_bfloat162 d2 = __halves2bfloat162(*dptr(8 * g + cc), *dptr(8 * g + cc + 1));
+            float gk[2], dx[2], dvp[2];
+            float2 xn[2];
+            bstep_pair(r[1][cc], r[1][cc + 1], r[0][cc], r[0][cc + 1], r[2][cc], r[2][cc + 1], r[3][cc],
+                       r[3][cc + 1], __low2float(d2), __high2float(d2), bev[u], bev[u + 1], invLf, lj, uj, gk, xn,
+                       dx, dvp);
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+              const int c = cb + cc + e;
+              const bool act = c < nat && jv;
+              const bool fixed = ((fw[u + e] >> lane) & 1u) != 0;
+              if (fixed || !act) {
+                xn[e] = make_float2(__uint_as_float(r[2][cc + e]), __uint_as_float(r[3][cc + e]));
+                dx[e] = 0.f;
+                dvp[e] = 0.f;
+              }
+              dv[(8 * g + cc + e) & 15] = dvp[e];
+              if (wr && act) {
+                const size_t o = (size_t)s_inst[c] * p.npad + jg;
+                Xn[o] = xn[e];
+                if (last) Gc[o] = gk[e];
+              }
+              r[1][cc + e] = __float_as_uint(gk[e]);
+              r[2][cc + e] = __float_as_uint(xn[e].x);
+              r[3][cc + e] = __float_as_uint(xn[e].y);
+              r[0][cc + e] = __float_as_uint(dx[e]);  // the new d waits in the accumulator's own columns
+            }
+          }
+        }
+        const uint32_t cbu = (uint32_t)cb;
+        tmem_st8(tl + kTmG + cbu, r[1]);
+        tmem_st8(tl + kTmX + cbu, r[2]);
+        tmem_st8(tl + kTmXl + cbu, r[3]);
+        tmem_st8(tl + cbu, r[0]);
+        if (g & 1) {
+          // restart-test partials of the warp's 32 coordinates for columns c0 + 16 (g / 2) + (0..15)
+          const float sum = lane_sums16(dv, lane);
+          if (lane < 16) s_dot[quarter][c0 + 16 * (g >> 1) + lane] = sum;
+        }
+      }
+      tmem_wait_st();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (tid < kBTile) {
+      const float part = s_dot[0][tid] + s_dot[1][tid] + s_dot[2][tid] + s_dot[3][tid];
+      const int inst = s_inst[tid];
+      if (last && inst >= 0) b.dotp[s][(size_t)mt * p.B + inst] = part;
+      const uint32_t a = smem_u32(&s_part[q & 1][mt][tid]);
+      for (int r = 0; r < MT; ++r) st_cluster_f32(map_to_rank(a, (uint32_t)r), part);
+    }
+    // every CTA of the cluster has finished the products that read d_k and sent its partials
+    cluster_sync_all();
+    tc_fence_after();
+    if (!last) {
+      if (have) {
+        float dn[32];
+        tmem_ld32(tl + (uint32_t)c0, dn);
+#pragma unroll
+        for (int cc = 0; cc < 32; ++cc) *dptr(cc) = __float2bfloat16_rn(dn[cc]);
+        fence_proxy_async_smem();
+      }
+      if (tid < kBTile) {
+        const int inst = s_inst[tid];
+        if (inst >= 0) {
+          float dsum = 0.f;
+          for (int t = 0; t < MT; ++t) dsum += s_part[q & 1][t][tid];
+          float T;
+          s_beta[tid] = bstep_momentum(s_tval[tid], dsum, p.restart, T);
+          s_tval[tid] = T;
+          if (mt == 0 && q + 1 == nsteps - 1) b.tval[(k + 1) & 1][inst] = T;
+        }
+      }
+      tc_fence_before();
+      __syncthreads();
+      if (tid == 0) {
+        for (int d = 1; d < MT; ++d) {
+          const uint32_t r = (uint32_t)((mt + d) % MT);
+          bulk_s2s(map_to_rank(smem_u32(sD + own), r), sD + own, (uint32_t)kSliceBytes,
+                   map_to_rank(smem_u32(&dfull), r));
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 512);
+  if (!ok) atomicOr(&st->error, 1);
+  if (tid == 0 && mt == 0 && nt == 0) st->sum_step += (double)n_act * nsteps;
+}
+
+size_t bsteps_smem_bytes(int npad) {
+  return (size_t)(npad / kBChunk) * kChunkBytes + (size_t)kBPStages * kChunkBytes + 1024;
+}
+
+// dynamic shared memory within the 227 KB a CTA may hold, the kernel's 12 KB of static
+// shared memory aside
+bool bsteps_supported(int npad) { return npad / kBTile <= kBPMaxTiles && bsteps_smem_bytes(npad) <= 215 * 1024; }
+
+cudaError_t launch_bsteps(const BParams& p, const BBuffers& b, int j0, int nsteps, cudaStream_t s) {
+  const int MT = p.npad / kBTile;
+  if (!bsteps_supported(p.npad) || nsteps < 1) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(MT, (p.B + kBTile - 1) / kBTile);
+  cfg.blockDim = dim3(kBStepThreads);
+  cfg.dynamicSmemBytes = bsteps_smem_bytes(p.npad);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = MT;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_bsteps, p, b, j0, nsteps);
 }
 
 // ------------------------------------------------------------------ evaluation
@@ -1247,6 +1696,8 @@ __global__ void __launch_bounds__(1024) k_bcompact(BParams p, BBuffers b) {
 
 cudaError_t batch_configure(int m, int npad) {
   cudaError_t e = cudaFuncSetAttribute(k_bstep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bstep_smem_bytes());
+  if (e == cudaSuccess && bsteps_supported(npad))
+    e = cudaFuncSetAttribute(k_bsteps, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsteps_smem_bytes(npad));
   if (e != cudaSuccess) return e;
   e = beval_configure<kX2>(m, npad);
   if (e != cudaSuccess) return e;

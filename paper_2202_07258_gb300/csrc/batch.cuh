@@ -131,6 +131,12 @@ __host__ __device__ inline BEvalChain beval_chain(int m, int ilv) {
 cudaError_t launch_bgram(const float* A, int lda, int m, int n, int npad, __nv_bfloat16* H, cudaStream_t s);
 cudaError_t launch_binit(const BParams& p, const BBuffers& b, cudaStream_t s);
 cudaError_t launch_bstep(const BParams& p, const BBuffers& b, int j, cudaStream_t s);
+// The steps j0 .. j0 + nsteps - 1 of a chunk (all tensor-core steps) in one cluster launch
+// with the iteration state on chip; only when bsteps_supported(npad) (npad <= 512).  Same
+// arithmetic in the same order as launch_bstep per step.
+bool bsteps_supported(int npad);
+size_t bsteps_smem_bytes(int npad);
+cudaError_t launch_bsteps(const BParams& p, const BBuffers& b, int j0, int nsteps, cudaStream_t s);
 cudaError_t launch_beval(const BParams& p, const BBuffers& b, int j, int precision, cudaStream_t s);
 cudaError_t launch_bcompact(const BParams& p, const BBuffers& b, cudaStream_t s);
 cudaError_t launch_bchunk_end(const BBuffers& b, int chunk_len, cudaStream_t s);

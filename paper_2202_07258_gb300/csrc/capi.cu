@@ -1237,17 +1237,30 @@ BParams make_bparams(bvls_handle* h, const bvls_opts& o, int max_iter, int B) {
   return p;
 }
 
+// Whether the batched solve runs the tensor-core steps between two evaluations as one
+// persistent cluster launch (single_pass 1, npad <= 512) or one launch per step.
+bool bsteps_persistent(const bvls_handle* h, const bvls_opts& o) {
+  return o.single_pass == 1 && bsteps_supported(h->b_npad);
+}
+
 // One chunk of iterations k = kbase + j (kbase a multiple of K and even): evaluations at
-// j % K == 0 (followed by the retirement of finished instances), tensor-core steps otherwise.
+// j % K == 0 (followed by the retirement of finished instances), tensor-core steps otherwise:
+// the K - 1 steps after an evaluation in one launch when bsteps_persistent, else one launch
+// each.  With events (profile), a persistent launch is timed as a whole and its later steps
+// get empty intervals.
 cudaError_t enqueue_bchunk(bvls_handle* h, const BParams& p, const bvls_opts& o, int chunk, cudaEvent_t* ev) {
   cudaError_t e = cudaSuccess;
+  const int K = o.screen_every;
+  const bool persist = bsteps_persistent(h, o);
   for (int j = 0; j < chunk && e == cudaSuccess; ++j) {
     if (ev) cudaEventRecordWithFlags(ev[2 * j], h->s, cudaEventRecordExternal);
-    if (j % o.screen_every == 0) {
+    if (j % K == 0) {
       e = launch_beval(p, h->bb, j, o.precision, h->s);
       if (e == cudaSuccess) e = launch_bcompact(p, h->bb, h->s);
-    } else {
+    } else if (!persist) {
       e = launch_bstep(p, h->bb, j, h->s);
+    } else if (j % K == 1) {
+      e = launch_bsteps(p, h->bb, j, std::min(K - 1, chunk - j), h->s);
     }
     if (ev) cudaEventRecordWithFlags(ev[2 * j + 1], h->s, cudaEventRecordExternal);
   }
@@ -1294,7 +1307,10 @@ extern "C" bvls_status bvls_solve_batched(bvls_handle* h, int B, const float* Y,
   CK(launch_binit(p, bb, h->s));
 
   const long long max_chunks = (max_iter + chunk - 1) / chunk + 2;
-  const long long per_chunk = (long long)chunk + chunk / K + 1;
+  // per chunk: chunk / K evaluations with their compaction, the steps (one launch per run of
+  // K - 1 when persistent), the chunk-end kernel
+  const long long per_chunk =
+      (long long)(chunk / K) * (bsteps_persistent(h, o) ? (K > 1 ? 3 : 2) : K + 1) + 1;
   long long chunks_run = 0;
   double step_ms = 0.0, eval_ms = 0.0;
   int step_launches = 0, eval_launches = 0;
@@ -1347,8 +1363,9 @@ extern "C" bvls_status bvls_solve_batched(bvls_handle* h, int B, const float* Y,
     cudaGraphExecDestroy(gx);
     if (pst != BVLS_OK) return pst;
   } else {
-    const double key[10] = {(double)K,  (double)chunk, (double)o.precision, (double)o.screening, (double)o.restart,
-                            o.tol,      (double)max_iter, p.invL,          (double)B,           2.0};
+    const double key[10] = {(double)K,  (double)chunk,    (double)o.precision, (double)o.screening,
+                            (double)o.restart, o.tol, (double)max_iter, p.invL, (double)B,
+                            bsteps_persistent(h, o) ? 3.0 : 2.0};
     if (!h->b_have_graph || std::memcmp(key, h->b_key, sizeof(key)) != 0) {
       if (h->b_exec) {
         cudaGraphExecDestroy(h->b_exec);
@@ -1426,6 +1443,7 @@ extern "C" bvls_status bvls_solve_batched(bvls_handle* h, int B, const float* Y,
     info->eval_launches = eval_launches;
     info->kernel_launches =
         1.0 + (chunks_run >= 0 ? (double)chunks_run * (double)per_chunk : (double)hs.chunks * (double)(per_chunk + 1));
+    info->steps_persistent = bsteps_persistent(h, o) ? 1 : 0;
     if (!rout.empty()) {
       for (const RefOut& r : rout) {
         info->refine_out_of_rounds += r.reason == 1;

@@ -195,3 +195,29 @@ def test_full_size_batch_refined_against_certified_optima(P):
         y = p.y[b].astype(np.float64)
         xs = certified_optimum(A, y, p.l, p.u, 1e-10)
         check_instance(A, y, p.l, p.u, X[b], S[b], gaps[b], sts[b], xs, 1e-6, f"inst{b}", xtol=1e-7)
+
+
+@pytest.mark.parametrize("make,K", [
+    (lambda: W.bvls_dirichlet_shared(224, 512, 300, 8, 0.005, 2), 10),   # 4 coordinate tiles, ragged last instance tile
+    (lambda: W.bvls_dirichlet_shared(224, 512, 4096, 8, 0.005, 0), 10),  # the benchmark's batch
+    (lambda: W.bvls_box_shared(96, 384, 130, 0.5, 3), 3),                # 3 tiles, runs of 2 steps
+    (lambda: W.nnls_shared(120, 200, 129, 0.05, 1.0, 4), 10),            # 2 tiles, translation dual point
+    (lambda: W.bvls_box_shared(60, 100, 40, 1.0, 5), 2),                 # 1 tile, runs of 1 step
+])
+def test_persistent_steps_match_per_step_launches(P, make, K):
+    """single_pass 1 runs the K - 1 tensor-core steps between two evaluations as one launch of
+    clusters that keep x, g and d on chip; single_pass 0 launches every step.  Both take the
+    same operations in the same order, so every output agrees bit for bit."""
+    p = make()
+    runs = [batched(P, p, tol=1e-7, screen_every=K, max_iter=20000, single_pass=sp) for sp in (1, 0)]
+    (X1, S1, g1, i1, s1, info1, st1), (X0, S0, g0, i0, s0, info0, st0) = runs
+    assert info1["steps_persistent"] == 1 and info0["steps_persistent"] == 0
+    assert st1 == st0 and st1 in (P.BVLS_OK, P.BVLS_EMAXITER)
+    assert info1["n_converged"] == info0["n_converged"] > 0
+    assert np.array_equal(i1, i0) and np.array_equal(s1, s0)
+    assert np.array_equal(S1, S0)
+    assert np.array_equal(g1, g0)
+    assert np.array_equal(X1, X0)
+    assert info1["sum_step"] == info0["sum_step"]
+    # one launch per run of K - 1 steps instead of K - 1 launches
+    assert info1["kernel_launches"] < info0["kernel_launches"] or K == 2
