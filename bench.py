@@ -223,8 +223,9 @@ def error_vs_optimum(A64, y64, x, rec, x_ref=None):
     """Error of a GPU result against the stored FP64 optimum rec (plain numpy arithmetic).
 
     Unique optimum: ||x - x*||_inf / max(1, ||x*||_inf) for the solver's result and for its
-    refined one, and P(x) - P*.  Otherwise (P* = 0, theta* = 0 on the degenerate workloads)
-    P(x), which bounds P(x) - P*, and ||y - A x|| = ||theta - theta*||."""
+    refined one, and P(x) - P*.  Not unique (P* = 0, theta* = 0 on the degenerate workloads):
+    P(x), which bounds P(x) - P*, and ||y - A x|| = ||theta - theta*||.  No record: P(x) and
+    ||y - A x|| alone."""
     r = y64 - A64 @ x
     out = {"P": 0.5 * float(r @ r)}
     if rec is not None and rec.get("unique"):
@@ -235,6 +236,9 @@ def error_vs_optimum(A64, y64, x, rec, x_ref=None):
         out["x_err_inf_rel"] = float(np.abs(x - xs).max()) / scale
         if x_ref is not None:
             out["x_err_inf_rel_refined"] = float(np.abs(x_ref - xs).max()) / scale
+    elif rec is None:
+        out["note"] = "no stored FP64 optimum for this workload: P(x) and ||y - A x|| only"
+        out["residual_norm"] = float(np.linalg.norm(r))
     else:
         out["note"] = "optimum not unique (P* = 0): P(x) bounds P(x) - P*, ||y - A x|| = ||theta - theta*||"
         out["theta_err_norm"] = float(np.linalg.norm(r))
