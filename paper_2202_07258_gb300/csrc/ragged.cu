@@ -405,23 +405,15 @@ cudaError_t ragged_configure() {
 
 cudaError_t launch_rpass(const RBuf& b, int max_tiles, int slot, int gap_iter, cudaStream_t s) {
   if (b.tw < kRTileMin || b.tw > kRTileMax) return cudaErrorInvalidValue;
-  // resident CTAs per SM for this tile width, once per width (the work list is walked by a
-  // grid of that many CTAs per SM)
-  static int per_sm[kRTileMax + 1] = {0};
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-  }
-  if (!per_sm[b.tw]) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[b.tw], k_rpass, kRThreads,
-                                                                  rpass_smem_bytes(b.tw));
-    if (e != cudaSuccess) return e;
-    if (per_sm[b.tw] < 1) per_sm[b.tw] = 1;
-  }
-  const int grid = std::max(1, std::min(max_tiles, per_sm[b.tw] * sms));
+  // resident CTAs per SM for this tile width on the current device (the work list is walked
+  // by a grid of that many CTAs per SM); the occupancy query is cheap next to the solve
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rpass, kRThreads, rpass_smem_bytes(b.tw));
+  if (e != cudaSuccess) return e;
+  const int grid = std::max(1, std::min(max_tiles, std::max(1, per_sm) * sms));
   k_rpass<<<grid, kRThreads, rpass_smem_bytes(b.tw), s>>>(b, slot, gap_iter);
   return cudaGetLastError();
 }

@@ -221,3 +221,17 @@ def test_persistent_steps_match_per_step_launches(P, make, K):
     assert info1["sum_step"] == info0["sum_step"]
     # one launch per run of K - 1 steps instead of K - 1 launches
     assert info1["kernel_launches"] < info0["kernel_launches"] or K == 2
+
+
+def test_wide_batch_takes_per_step_launches(P):
+    """npad = 640 needs five coordinate tiles, more than the persistent step's clusters hold:
+    the solve falls back to one step launch per iteration and still matches the oracle."""
+    p = W.bvls_dirichlet_shared(150, 600, 6, 8, 0.005, 7)
+    A = p.A.astype(np.float64)
+    X, S, gaps, its, sts, info, st = batched(P, p, tol=1e-7, precision="fp32x2")
+    assert st == P.BVLS_OK and info["n_converged"] == 6
+    assert info["steps_persistent"] == 0
+    for b in range(6):
+        y = p.y[b].astype(np.float64)
+        xs = certified_optimum(A, y, p.l, p.u, 1e-10)
+        check_instance(A, y, p.l, p.u, X[b], S[b], gaps[b], sts[b], xs, 1e-7, f"inst{b}")
