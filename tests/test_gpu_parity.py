@@ -100,6 +100,43 @@ def test_trajectory_matches_oracle(P, name):
     assert gpu_fixed.sum() >= 0.97 * ref_fixed.sum() - 2, (gpu_fixed.sum(), ref_fixed.sum())
 
 
+@pytest.mark.parametrize("make", [lambda: W.nnls_abs_gaussian(1500, 400, 0.05, 1.0, 4),   # 2 row chunks per q lane
+                                  lambda: W.bvls_table2(3000, 500, 5),                    # 4
+                                  lambda: W.nnls_abs_gaussian(6000, 300, 0.05, 1.0, 6)])  # 8
+def test_trajectory_row_templates(P, make):
+    """The persistent pass picks its q-warp template by m (1, 2, 4 or 8 float4 row chunks per
+    lane, for m up to 1024, 2048, 4096 and 8192); the trajectory cases above all take the first.
+    200 iterations from the same point and step constant agree with the FP64 oracle to 1e-9."""
+    p = make()
+    A, y = _f64(p)
+    L = _L(A)
+    N = 200
+    ref = O.solve(A, y, p.l, p.u, tol=0.0, screen_every=10, max_iter=N, L=L)
+    x, scr, info, st = gpu_solve(P, p, tol=0.0, screen_every=10, max_iter=N, lipschitz=L)
+    assert st == P.BVLS_EMAXITER and info["iters"] == N == ref.iters
+    assert info["single_pass"] == 2          # the persistent form ran
+    scale = max(1.0, float(np.abs(ref.x).max()))
+    err = float(np.abs(x - ref.x).max())
+    assert err <= 1e-9 * scale, (p.m, err)
+
+
+def test_mixed_trajectory_headline_template(P):
+    """Mode MIXED on the headline's template (2 row chunks per q lane, half of r in the dot
+    warps' registers) against the FP64 trajectory, at the reduced-precision bar of the mode
+    (1e-4 relative, as test_mixed_precision_parity_nondegenerate): its forward product is
+    good to about (cps + 1) u = 9 x 2^-24 relative to sum_j |a_ij x_j| per iteration, its
+    correlations to float32 accuracy."""
+    p = W.nnls_abs_gaussian(1800, 500, 0.05, 1.0, 8)
+    A, y = _f64(p)
+    L = _L(A)
+    N = 200
+    ref = O.solve(A, y, p.l, p.u, tol=0.0, screen_every=10, max_iter=N, L=L)
+    x, scr, info, st = gpu_solve(P, p, tol=0.0, screen_every=10, max_iter=N, lipschitz=L, precision="mixed")
+    assert info["iters"] == N and info["single_pass"] == 2
+    scale = max(1.0, float(np.abs(ref.x).max()))
+    assert float(np.abs(x - ref.x).max()) <= 1e-4 * scale
+
+
 @pytest.mark.parametrize("name", ["nnls_abs_300x700", "bvls_t2_200x500", "mixed_180x140", "bvls_dir_224x512"])
 def test_result_matches_oracle_and_screens_safely(P, name):
     p, t = CASES[name]()
