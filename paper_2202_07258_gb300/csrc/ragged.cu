@@ -280,6 +280,8 @@ __global__ void __launch_bounds__(kRThreads) k_rpass(RBuf b, int slot, int gap_i
   __shared__ int s_col[kRTileMax];
   __shared__ float2 s_xn[kRTileMax];
   __shared__ double s_dot[kRTileMax], s_eps[kRTileMax], s_v2[kRTileMax];
+  __shared__ float2 s_bb, s_onepb, s_invL2;
+  __shared__ double s_etag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int wt = blockIdx.x; wt < ntiles; wt += gridDim.x) {
   const RTileRef tr = b.tiles[wt];
@@ -295,6 +297,18 @@ __global__ void __launch_bounds__(kRThreads) k_rpass(RBuf b, int slot, int gap_i
     s_eps[tid] = 0.0;
     s_v2[tid] = 0.0;
   }
+  if (tid == 0) {
+    // FISTA parameters of the instance (t_k stored), once per tile: float64 runs at a small
+    // fraction of the float32 rate on this part, so one thread computes them while the
+    // others stage the tile
+    const double tk = st.t;
+    const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk * tk));
+    const double beta = (tk - 1.0) / tn;
+    s_bb = df2_from_double(beta);
+    s_onepb = df2_from_double(1.0 + beta);
+    s_invL2 = df2_from_double(in.invL);
+    s_etag = in.Cg * sqrt(2.0 * st.P) * (1.0 + 1e-6);
+  }
   for (int i = tid; i < m4; i += kRThreads) {
     srh[i] = i < in.m ? b.rh[in.r_off + i] : 0.f;
     srl[i] = i < in.m ? b.rl[in.r_off + i] : 0.f;
@@ -309,13 +323,10 @@ __global__ void __launch_bounds__(kRThreads) k_rpass(RBuf b, int slot, int gap_i
   }
   __syncthreads();
 
-  // FISTA parameters of the instance (t_k stored), or the power iteration's scale
-  const double tk = st.t;
-  const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk * tk));
-  const double beta = (tk - 1.0) / tn;
-  const float2 bb = df2_from_double(beta), onepb = df2_from_double(1.0 + beta);
-  const float2 invL2 = df2_from_double(in.invL);
-  const double eta_g = in.Cg * sqrt(2.0 * st.P) * (1.0 + 1e-6);
+  // FISTA parameters of the instance (from thread 0), or the power iteration's scale
+  const float2 bb = s_bb, onepb = s_onepb;
+  const float2 invL2 = s_invL2;
+  const double eta_g = s_etag;
   const bool want_eps = gap_iter && in.dual_mode == kTranslation && !b.power;
   const float2* __restrict__ xc = b.x[slot];
   float2* xn = b.x[slot ^ 1];
