@@ -235,3 +235,26 @@ def test_wide_batch_takes_per_step_launches(P):
         y = p.y[b].astype(np.float64)
         xs = certified_optimum(A, y, p.l, p.u, 1e-10)
         check_instance(A, y, p.l, p.u, X[b], S[b], gaps[b], sts[b], xs, 1e-7, f"inst{b}")
+
+
+@pytest.mark.parametrize("kw", [dict(profile=True), dict(screening=False), dict(restart=False), dict(refine=True),
+                                dict(warm=True), dict(precision="fp32")])
+def test_persistent_steps_match_under_options(P, kw):
+    """The persistent and per-step forms agree bit for bit under the other options too: the
+    event-timed chunk graph (profile), no screening, no restart, the refinement that follows
+    the solve, a warm start and float32 evaluations."""
+    kw = dict(kw)
+    p = W.bvls_box_shared(120, 320, 140, 0.5, 9)
+    X0 = None
+    if kw.pop("warm", False):
+        X0 = np.random.default_rng(9).uniform(-0.5, 0.5, (140, 320))
+    runs = [batched(P, p, X0=X0, tol=1e-7, screen_every=10, max_iter=20000, single_pass=sp, **kw) for sp in (1, 0)]
+    (X1, S1, g1, i1, s1, info1, st1), (X0r, S0, g0, i0, s0, info0, st0) = runs
+    assert info1["steps_persistent"] == 1 and info0["steps_persistent"] == 0
+    assert st1 == st0 and info1["n_converged"] == info0["n_converged"] > 0
+    assert np.array_equal(i1, i0) and np.array_equal(s1, s0) and np.array_equal(S1, S0)
+    assert np.array_equal(g1, g0) and np.array_equal(X1, X0r)
+    if kw.get("profile"):
+        # every step is timed (a persistent launch as a whole, its later steps as empty intervals)
+        assert info1["step_launches"] == info0["step_launches"] > 0
+        assert info1["step_ms"] > 0 and info0["step_ms"] > 0
