@@ -590,6 +590,57 @@ def batched_leg(dev, stream, flush, steps, warmup=1):
     return out
 
 
+def backward_leg(dev, stream, steps=3):
+    """Differentiable NNLS batch: 1024 instances sharing A 256 x 1024 (N(0,1), columns
+    normalised as in the other shared families), x_b 8% nonzeros ~U[0.1, 1], y_b = A x_b +
+    N(0, 0.01^2); the batched forward to gap 1e-8 (double-float evaluations), then the
+    backward of L = 1/2 ||x - x_t||^2 (x_t ~ U[0, 1]) to y and A through the free-set normal
+    equations (float64 conjugate gradients per instance).  With Gaussian A and n = 4m the
+    optimum is not unique and a free set can exceed m (those instances report their CG
+    status); the |N(0,1)| / unit-noise variant has unique optima."""
+    import torch
+    from paper_2202_07258_gb300 import Solver, make_opts
+    out = {}
+    fp64_peak = 1250.0   # GFLOP/s: the part's nominal float64 rate (no measured figure in the pool's peaks)
+    for name, absm, noise in (("gauss_B1024", False, 0.01), ("abs_B1024", True, 1.0)):
+        p = W.nnls_shared(256, 1024, 1024, 0.08, noise, 5, abs_matrix=absm, x_low=0.1)
+        B = p.y.shape[0]
+        with torch.cuda.stream(stream):
+            solver = Solver(torch.from_numpy(p.A).to(dev), p.l, p.u, stream=stream.cuda_stream)
+            Y = torch.from_numpy(p.y).to(dev)
+            Xt = torch.from_numpy(np.random.default_rng(5).uniform(0.0, 1.0, (B, p.A.shape[1]))).to(dev)
+        opts = make_opts(tol=1e-8, screen_every=K_SCREEN, precision="fp32x2")
+        fw, bw = [], []
+        with torch.cuda.stream(stream):
+            for it in range(steps + 1):    # the first round warms up
+                e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                e0.record(stream)
+                X, S, gaps, its, sts, info, st = solver.solve_batched(Y, opts=opts)
+                e1.record(stream)
+                dY, dA, bsts, binfo = solver.backward(X, Y, X - Xt)
+                e2.record(stream)
+                e2.synchronize()
+                if it > 0:
+                    fw.append(e0.elapsed_time(e1))
+                    bw.append(e1.elapsed_time(e2))
+        solver.close()
+        f_ms, b_ms = sum(fw) / len(fw), sum(bw) / len(bw)
+        flops = 4.0 * p.A.shape[0] * binfo["cg_work"]
+        ach = flops / (binfo["kernel_ms"] / 1e3) / 1e9 if binfo["kernel_ms"] > 0 else None
+        out[name] = {
+            "forward": {"ms": f_ms, "instances_per_s": B / (f_ms / 1e3), "n_converged": info["n_converged"],
+                        "gap_max": float(gaps.max()), "iters_max": info["iters_max"]},
+            "backward": {"ms": b_ms, "instances_per_s": B / (b_ms / 1e3), "kernel_ms": binfo["kernel_ms"],
+                         "cg": {k: binfo[k] for k in ("n_converged", "n_iter_limit", "n_too_large", "n_not_unique",
+                                                      "max_free", "max_cg_iters")},
+                         "roofline": {"bound": "alu (float64)", "kernel": "k_bwd (per-instance CG) + k_bwd_da",
+                                      "achieved": ach, "peak": fp64_peak,
+                                      "peak_source": "nominal float64 rate of the part", "unit": "GFLOP/s",
+                                      "frac": ach / fp64_peak if ach else None, "flops": flops}},
+            "forward_plus_backward_instances_per_s": B / ((f_ms + b_ms) / 1e3)}
+    return out
+
+
 def e2e_leg(p, steps, stream):
     """Whole job through the C ABI from pinned host buffers: setup(A) + solve(y) + read x."""
     import ctypes
@@ -778,6 +829,7 @@ def run_ours(args):
     table2 = table2_leg(dev, stream, flush, max(2, min(args.steps, 3))) if rank == 0 else None
     hbm = hbm_leg(dev, stream, flush, 2) if (rank == 0 and not args.no_batched) else None
     ragged = ragged_leg(dev, stream) if (rank == 0 and not args.no_batched) else None
+    backward = backward_leg(dev, stream) if (rank == 0 and not args.no_batched) else None
     e2e = e2e_leg(head["p"], max(2, min(args.steps, 5)), stream) if rank == 0 else None
     cpu = oracle_sample(head["p"]) if (rank == 0 and world == 1) else None
     head["solver"].close()
@@ -825,6 +877,7 @@ def run_ours(args):
                 "gap": x2["info"]["gap"]},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "batched_shared_A": batched,
             "table2_bvls": table2, "ragged_uneven": ragged, "hbm_bound_4000x20000": hbm,
+            "differentiable_B1024": backward,
             "gpu_launches": int(scr["launches"]), "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)

@@ -304,8 +304,12 @@ typedef struct {
   int n_converged;      /* instances whose CG met cg_tol */
   int n_iter_limit;     /* instances that stopped at cg_max_iter (gradients approximate) */
   int n_too_large;      /* instances whose free set exceeds 1024 (zero gradients returned) */
+  int n_not_unique;     /* instances whose free set exceeds m (zero gradients returned) */
   int max_free;         /* largest free set */
   int max_cg_iters;     /* most CG iterations of an instance */
+  double cg_work;       /* sum over instances of CG iterations x |F| (each iteration applies
+                           A_F^T A_F: 4 m |F| float64 flops) */
+  double kernel_ms;     /* device time of the backward kernels (CUDA events) */
 } bvls_backward_info;
 
 /* Fill *opts with the defaults above. */
@@ -329,7 +333,9 @@ BVLS_API void bvls_backward_default_opts(bvls_backward_opts* opts);
  *   dLdA     any; m x n doubles, column-major (leading dimension m), summed over the batch,
  *            or NULL.
  *   status_out  any; B ints or NULL: 0 CG converged, 1 CG iteration limit, 2 free set
- *            larger than 1024 (that instance contributes zero gradients).
+ *            larger than 1024, 3 free set larger than m (A_F cannot have full column rank:
+ *            the optimum is not unique and has no derivative); with 2 and 3 that instance
+ *            contributes zero gradients and runs no CG.
  *   info     host or NULL.
  * Limits: m <= 24576 (the handle's limit); free sets up to 1024 coordinates.  Returns
  * BVLS_OK, or an error (EINVAL, ENOMEM, ECUDA; outputs untouched).

@@ -118,8 +118,11 @@ class bvls_backward_info(ctypes.Structure):
         ("n_converged", ctypes.c_int),
         ("n_iter_limit", ctypes.c_int),
         ("n_too_large", ctypes.c_int),
+        ("n_not_unique", ctypes.c_int),
         ("max_free", ctypes.c_int),
         ("max_cg_iters", ctypes.c_int),
+        ("cg_work", ctypes.c_double),
+        ("kernel_ms", ctypes.c_double),
     ]
 
     def as_dict(self):

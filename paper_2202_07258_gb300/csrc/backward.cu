@@ -78,9 +78,12 @@ __global__ void __launch_bounds__(kBwdThreads) k_bwd(BwdParams p) {
     __syncthreads();
   }
   const bool too_big = nf > kBwdMaxFree;
-  if (too_big) {
+  // |F| > m: A_F (m x |F|) cannot have full column rank, so A_F^T A_F is singular, the
+  // optimum is not unique and the solution map has no derivative to follow
+  const bool no_rank = !too_big && nf > p.m;
+  if (too_big || no_rank) {
     if (tid == 0) {
-      p.status[b] = 2;   // free set larger than supported
+      p.status[b] = too_big ? 2 : 3;
       p.iters[b] = 0;
       p.nfree[b] = nf;
     }
@@ -162,7 +165,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_bwd(BwdParams p) {
       p.R[(size_t)b * p.m + i] = acc;
     }
   }
-  if (tid == 0 && !too_big) {
+  if (tid == 0 && !too_big && !no_rank) {
     p.status[b] = conv ? 0 : 1;
     p.iters[b] = it;
     p.nfree[b] = nf;

@@ -22,7 +22,7 @@ struct BwdParams {
   double* W;             // B x n scratch: w (zero off the free set), or null
   double* Q;             // B x m scratch: A_F w, or null
   double* R;             // B x m scratch: y - A x, or null
-  int* status;           // B: 0 converged, 1 CG iteration limit, 2 free set too large
+  int* status;           // B: 0 converged, 1 CG iteration limit, 2 free set too large, 3 |F| > m
   int* iters;            // B: CG iterations
   int* nfree;            // B: |F|
   double free_tol;

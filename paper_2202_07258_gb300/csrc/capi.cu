@@ -1547,8 +1547,21 @@ extern "C" bvls_status bvls_backward(bvls_handle* h, int B, const double* X, con
   p.status = dSt;
   p.iters = dIt;
   p.nfree = dNf;
+  struct EventPair {   // destroyed on every return
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~EventPair() {
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+    }
+  } ev;
+  if (info) {
+    BCK(cudaEventCreate(&ev.a));
+    BCK(cudaEventCreate(&ev.b));
+    BCK(cudaEventRecord(ev.a, h->s));
+  }
   BCK(launch_bwd(p, h->s));
   if (dLdA) BCK(launch_bwd_da(p, dDA, h->s));
+  if (info) BCK(cudaEventRecord(ev.b, h->s));
   std::vector<int> st(B), it(B), nf(B);
   BCK(cudaMemcpyAsync(st.data(), dSt, sizeof(int) * B, cudaMemcpyDeviceToHost, h->s));
   BCK(cudaMemcpyAsync(it.data(), dIt, sizeof(int) * B, cudaMemcpyDeviceToHost, h->s));
@@ -1557,6 +1570,8 @@ extern "C" bvls_status bvls_backward(bvls_handle* h, int B, const double* X, con
   if (dLdA) BCK(cudaMemcpyAsync(dLdA, dDA, sizeof(double) * (size_t)m * n, cudaMemcpyDefault, h->s));
   if (status_out) BCK(cudaMemcpyAsync(status_out, dSt, sizeof(int) * B, cudaMemcpyDefault, h->s));
   BCK(cudaStreamSynchronize(h->s));
+  float kms = 0.f;
+  if (info) BCK(cudaEventElapsedTime(&kms, ev.a, ev.b));
   release();
 #undef BCK
   if (info) {
@@ -1565,9 +1580,12 @@ extern "C" bvls_status bvls_backward(bvls_handle* h, int B, const double* X, con
       info->n_converged += st[b] == 0;
       info->n_iter_limit += st[b] == 1;
       info->n_too_large += st[b] == 2;
+      info->n_not_unique += st[b] == 3;
       info->max_free = std::max(info->max_free, nf[b]);
       info->max_cg_iters = std::max(info->max_cg_iters, it[b]);
+      info->cg_work += (double)it[b] * (double)nf[b];
     }
+    info->kernel_ms = kms;
   }
   g_err.clear();
   return BVLS_OK;

@@ -51,6 +51,12 @@ def test_backward_matches_oracle_at_the_same_point(P):
         assert np.allclose(dY[b], dy, rtol=1e-7, atol=1e-9 * np.abs(dy).max()), b
         dA_ref += da
     assert np.allclose(dA, dA_ref, rtol=1e-7, atol=1e-9 * np.abs(dA_ref).max())
+    # the work counters: every instance's CG ran on its free set (oracle's |F|), within the maxima
+    nF = [O.backward(A, p.y[b].astype(np.float64), XS[b], V[b], p.l, p.u)[2].size for b in range(6)]
+    assert binfo["max_free"] == max(nF)
+    assert 0 < binfo["cg_work"] <= 6 * binfo["max_cg_iters"] * binfo["max_free"]
+    assert binfo["cg_work"] >= binfo["max_cg_iters"] * min(nF)
+    assert binfo["kernel_ms"] > 0
     s.close()
 
 
@@ -126,3 +132,25 @@ def test_free_set_over_the_limit_gives_status_2(P):
     assert torch.all(bst == 2) and info["n_too_large"] == 2 and info["max_free"] == n
     assert torch.all(dY == 0)
     s.close()
+
+
+def test_free_set_larger_than_m_is_declined(P):
+    """Gaussian A with n = 4m (the degenerate differentiable-NNLS shape): an optimum with more
+    than m positive coordinates cannot have A_F of full column rank, so it is not unique and
+    has no derivative.  Those instances get status 3, zero gradients and no CG iterations; the
+    others are solved as usual."""
+    p = W.nnls_shared(40, 160, 8, 0.08, 0.01, 21, abs_matrix=False, x_low=0.1)
+    dev = torch.device("cuda:0")
+    s = P.Solver(torch.from_numpy(p.A).to(dev), p.l, p.u)
+    X, S, gaps, its, sts, info, st = s.solve_batched(torch.from_numpy(p.y).to(dev), tol=1e-8, precision="fp32x2")
+    assert st == P.BVLS_OK
+    X = X.cpu().numpy()
+    V = np.random.default_rng(2).standard_normal(X.shape)
+    dY, dA, bst, binfo = s.backward(X, p.y, V)
+    s.close()
+    nfree = (X > 1e-9).sum(axis=1)        # l = 0, u = +inf: free means x_j > free_tol (1 + |l_j|)
+    assert np.array_equal(bst == 3, nfree > p.m), (bst, nfree)
+    assert np.any(bst == 3)
+    assert binfo["n_not_unique"] == int((bst == 3).sum())
+    assert np.all(dY[bst == 3] == 0.0)
+    assert binfo["cg_work"] <= binfo["max_cg_iters"] * int(nfree[bst != 3].sum())
