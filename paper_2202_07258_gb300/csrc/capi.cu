@@ -70,7 +70,7 @@ struct bvls_handle {
   cudaEvent_t ev_in = nullptr;
   float* A = nullptr;
   double *l = nullptr, *u = nullptr, *nrm = nullptr, *w = nullptr, *t = nullptr;
-  float2 *l2 = nullptr, *u2 = nullptr;
+  float2 *l2 = nullptr, *u2 = nullptr, *t2 = nullptr;   // t2: t as double-float pairs
   uint8_t* jinf = nullptr;
   double t_norm = 0.0, gamma_w = 0.0, L = 0.0;
   double xbox = -1.0;  // sum_j max(|l_j|, |u_j|) ||a_j|| (primal-dual error bound), once computed
@@ -80,6 +80,7 @@ struct bvls_handle {
   float* y_dev = nullptr;
   double* x0_dev = nullptr;
   double *theta_dev = nullptr, *wstar_dev = nullptr;  // fixed dual point and A^T theta
+  float2* theta2_dev = nullptr;                        // theta as double-float pairs
   int fwd_tiles = 0, fwd_chunks = 0, tr_blocks = 0, red_blocks = 0;
   int pass_stages = 0, pass_qw = 0, pass_cps = 1;  // fused single-pass iteration when pass_stages > 0
   bool pass_coop = false;                          // its persistent (cooperative) launch fits
@@ -172,10 +173,22 @@ void free_handle(bvls_handle* h) {
 }
 
 // The momentum table of the persistent pass (T[0] = 1, T[i+1] = (1 + sqrt(1 + 4 T[i]^2)) / 2),
-// computed once per process in float64.
-const std::vector<MomEntry>& momentum_table() {
-  static const std::vector<MomEntry> tab = [] {
-    std::vector<MomEntry> v(kMomTable);
+// computed once per process in float64, in page-locked host memory where that can be had
+// (its 2 MB then reach each new handle by an asynchronous copy instead of a staged one).
+struct MomTable {
+  const MomEntry* data;
+  bool pinned;
+};
+
+const MomTable& momentum_table() {
+  static const MomTable tab = [] {
+    MomEntry* v = nullptr;
+    bool pinned = cudaHostAlloc(reinterpret_cast<void**>(&v), sizeof(MomEntry) * kMomTable, cudaHostAllocDefault) ==
+                  cudaSuccess;
+    if (!pinned) {
+      cudaGetLastError();
+      v = new MomEntry[kMomTable];
+    }
     double t = 1.0;
     for (int i = 0; i < kMomTable; ++i) {
       const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
@@ -186,7 +199,7 @@ const std::vector<MomEntry>& momentum_table() {
       v[i].onepb2 = df2_from_double(1.0 + beta);
       t = tn;
     }
-    return v;
+    return MomTable{v, pinned};
   }();
   return tab;
 }
@@ -197,14 +210,15 @@ bvls_status try_direction(bvls_handle* h, const std::vector<double>& t,
                           const std::vector<uint8_t>& jinf, const std::vector<double>& nrm,
                           bool* ok, bool w_ready = false) {
   CK(cudaMemcpyAsync(h->t, t.data(), sizeof(double) * h->m, cudaMemcpyHostToDevice, h->s));
-  if (!w_ready) CK(launch_col_dots(h->A, h->lda, h->m, h->n, h->t, h->w, h->s));
+  CK(launch_split_pairs(h->t, h->t2, h->m, h->s));
+  if (!w_ready) CK(launch_col_dots(h->A, h->lda, h->m, h->n, h->t2, h->w, h->s));
   std::vector<double> w(h->n);
   CK(cudaMemcpyAsync(w.data(), h->w, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->s));
   CK(cudaStreamSynchronize(h->s));
   double tn = 0.0;
   for (double v : t) tn += v * v;
   tn = std::sqrt(tn);
-  const double gamma = 1.01 * (h->m + 8) * kU64;
+  const double gamma = setup_dot_gamma(h->m);
   *ok = true;
   for (int j = 0; j < h->n; ++j) {
     if (!jinf[j] || !(nrm[j] > 0.0)) continue;
@@ -475,12 +489,14 @@ bvls_status prepare_fixed_dual(bvls_handle* h, const double* theta, Params* p) {
   const int m = h->m, n = h->n;
   if (!h->theta_dev) {
     TRY(dalloc(h, &h->theta_dev, m));
+    TRY(dalloc(h, &h->theta2_dev, m));
     TRY(dalloc(h, &h->wstar_dev, n));
   }
   std::vector<double> th(m), ws(n), nr(n), w(n);
   CK(cudaMemcpyAsync(h->theta_dev, theta, sizeof(double) * m, cudaMemcpyDefault, h->s));
   CK(cudaMemcpyAsync(th.data(), h->theta_dev, sizeof(double) * m, cudaMemcpyDeviceToHost, h->s));
-  CK(launch_col_dots(h->A, h->lda, m, n, h->theta_dev, h->wstar_dev, h->s));
+  CK(launch_split_pairs(h->theta_dev, h->theta2_dev, m, h->s));
+  CK(launch_col_dots(h->A, h->lda, m, n, h->theta2_dev, h->wstar_dev, h->s));
   CK(cudaMemcpyAsync(ws.data(), h->wstar_dev, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
   CK(cudaMemcpyAsync(nr.data(), h->nrm, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
   CK(cudaMemcpyAsync(w.data(), h->w, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
@@ -493,7 +509,7 @@ bvls_status prepare_fixed_dual(bvls_handle* h, const double* theta, Params* p) {
     tn += v * v;
   }
   tn = std::sqrt(tn);
-  const double eta0 = 1.01 * (m + 8) * kU64 * tn;  // float64 dot a_j^T theta, per unit ||a_j||
+  const double eta0 = setup_dot_gamma(m) * tn;  // the product a_j^T theta, per unit ||a_j||
   double eps = 0.0;
   if (h->dual_mode == kTranslation) {
     for (int j = 0; j < n; ++j) {
@@ -611,45 +627,45 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
   }
 
   TRY(dalloc(h, &h->A, (size_t)h->lda * n));
-  CK(cudaMemsetAsync(h->A, 0, sizeof(float) * (size_t)h->lda * n, h->s));
+  if (h->lda > m)   // the padding rows m..lda-1 of every column are zero
+    CK(cudaMemset2DAsync(h->A + m, sizeof(float) * h->lda, 0, sizeof(float) * (h->lda - m), n, h->s));
   CK(cudaMemcpy2DAsync(h->A, sizeof(float) * h->lda, A, sizeof(float) * lda, sizeof(float) * m, n,
                        cudaMemcpyDefault, h->s));
   int* flag = nullptr;
   TRY(dalloc(h, &flag, 4));
   CK(cudaMemsetAsync(flag, 0, sizeof(int), h->s));
-  CK(launch_check_finite(h->A, h->lda, m, n, flag, h->s));
-  int bad = 0;
-  CK(cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, h->s));
-  CK(cudaStreamSynchronize(h->s));
-  if (bad) return set_err(BVLS_ENONFINITE, "A contains NaN or Inf");
+  // every stored row (the padding rows are zero), read back with the column norms
+  CK(launch_check_finite(h->A, h->lda, h->lda, n, flag, h->s));
 
-  TRY(dalloc(h, &h->l, n));
-  TRY(dalloc(h, &h->u, n));
+  // l and u in one buffer and one copy; their double-float pairs and J_inf formed on the device
+  double* lu = nullptr;
+  TRY(dalloc(h, &lu, 2 * (size_t)n));
+  h->l = lu;
+  h->u = lu + n;
   TRY(dalloc(h, &h->nrm, n));
   TRY(dalloc(h, &h->w, n));
   TRY(dalloc(h, &h->jinf, n));
   TRY(dalloc(h, &h->t, m));
-  CK(cudaMemcpyAsync(h->l, lv.data(), sizeof(double) * n, cudaMemcpyHostToDevice, h->s));
-  CK(cudaMemcpyAsync(h->u, uv.data(), sizeof(double) * n, cudaMemcpyHostToDevice, h->s));
+  TRY(dalloc(h, &h->t2, m));
   {
-    std::vector<float2> l2(n), u2(n);
-    for (int j = 0; j < n; ++j) {
-      l2[j] = df2_from_double(lv[j]);
-      u2[j] = df2_from_double(uv[j]);
-    }
-    TRY(dalloc(h, &h->l2, n));
-    TRY(dalloc(h, &h->u2, n));
-    CK(cudaMemcpyAsync(h->l2, l2.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, h->s));
-    CK(cudaMemcpyAsync(h->u2, u2.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, h->s));
-    CK(cudaStreamSynchronize(h->s));
+    std::vector<double> luv(2 * (size_t)n);
+    std::memcpy(luv.data(), lv.data(), sizeof(double) * n);
+    std::memcpy(luv.data() + n, uv.data(), sizeof(double) * n);
+    // a pageable copy: the call returns once the source is staged, so luv may go
+    CK(cudaMemcpyAsync(lu, luv.data(), sizeof(double) * 2 * (size_t)n, cudaMemcpyHostToDevice, h->s));
   }
-  CK(cudaMemcpyAsync(h->jinf, jinf.data(), n, cudaMemcpyHostToDevice, h->s));
+  TRY(dalloc(h, &h->l2, n));
+  TRY(dalloc(h, &h->u2, n));
+  CK(launch_bound_pairs(h->l, h->u, h->l2, h->u2, h->jinf, n, h->s));
   CK(cudaMemsetAsync(h->w, 0, sizeof(double) * n, h->s));
   // with no caller t, the first candidate t = -1 gets its products w = A^T t in this pass
   CK(launch_col_norms(h->A, h->lda, m, n, h->nrm, h->s, (any_inf && !t) ? h->w : nullptr));
   std::vector<double> nrm(n);
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, h->s));
   CK(cudaMemcpyAsync(nrm.data(), h->nrm, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
   CK(cudaStreamSynchronize(h->s));
+  if (bad) return set_err(BVLS_ENONFINITE, "A contains NaN or Inf");
 
   // Dual point of Section 4.
   if (!any_inf) {
@@ -672,11 +688,14 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
       // s = sum_k a_k and c = A^T s serve the next two candidates: minus the mean column has
       // w = -c / n, and the column most correlated with all others is argmax_j c_j
       double *rs = nullptr, *rs_part = nullptr, *corr_d = nullptr;
+      float2* rs2 = nullptr;
       TRY(dalloc(h, &rs, m));
+      TRY(dalloc(h, &rs2, m));
       TRY(dalloc(h, &rs_part, row_sums_scratch(m, n)));
       TRY(dalloc(h, &corr_d, n));
       CK(launch_row_sums(h->A, h->lda, m, n, rs_part, rs, h->s));
-      CK(launch_col_dots(h->A, h->lda, m, n, rs, corr_d, h->s));
+      CK(launch_split_pairs(rs, rs2, m, h->s));
+      CK(launch_col_dots(h->A, h->lda, m, n, rs2, corr_d, h->s));
       CK(launch_scale_neg(corr_d, n, 1.0 / n, h->w, h->s));
       std::vector<double> s(m), corr(n);
       CK(cudaMemcpyAsync(s.data(), rs, sizeof(double) * m, cudaMemcpyDeviceToHost, h->s));
@@ -825,10 +844,7 @@ static bvls_status setup_impl(bvls_handle* h, const float* A, int lda, const dou
   TRY(dalloc(h, &b.qpart, (size_t)h->num_sms * h->m4));
   TRY(dalloc(h, &b.gbar, kMaxGridFlags));
   TRY(dalloc(h, &h->mom, kMomTable));
-  {
-    const std::vector<MomEntry>& tab = momentum_table();
-    CK(cudaMemcpyAsync(h->mom, tab.data(), sizeof(MomEntry) * kMomTable, cudaMemcpyHostToDevice, h->s));
-  }
+  CK(cudaMemcpyAsync(h->mom, momentum_table().data, sizeof(MomEntry) * kMomTable, cudaMemcpyHostToDevice, h->s));
   TRY(dalloc(h, &b.xout, n));
   TRY(dalloc(h, &h->y_dev, h->m4));
   TRY(dalloc(h, &h->x0_dev, n));

@@ -366,13 +366,28 @@ void record_error(const char* msg);
 
 // Setup kernels (setup_kernels.cu).
 cudaError_t launch_check_finite(const float* A, int lda, int m, int n, int* flag, cudaStream_t s);
-// ||a_j||; with wneg1, also a_j^T (-1) (the direction t = -1) in the same pass.
+// l2, u2 as double-float pairs and jinf[j] = (u_j == +inf) from the device bounds l, u
+cudaError_t launch_bound_pairs(const double* l, const double* u, float2* l2, float2* u2, uint8_t* jinf, int n,
+                               cudaStream_t s);
+// ||a_j|| rounded up (never below the exact norm); with wneg1, also a_j^T (-1) (the
+// direction t = -1) in the same pass, bounded as launch_col_dots.
 cudaError_t launch_col_norms(const float* A, int lda, int m, int n, double* nrm, cudaStream_t s,
                              double* wneg1 = nullptr);
 // w_j = -c_j * inv
 cudaError_t launch_scale_neg(const double* c, int n, double inv, double* w, cudaStream_t s);
-cudaError_t launch_col_dots(const float* A, int lda, int m, int n, const double* t, double* w,
+// t (float64, m) as double-float pairs t2 = (float(t), float(t - float(t)))
+cudaError_t launch_split_pairs(const double* t, float2* t2, int m, cudaStream_t s);
+// w_j = a_j^T t for t given by launch_split_pairs, double-float accumulation
+cudaError_t launch_col_dots(const float* A, int lda, int m, int n, const float2* t2, double* w,
                             cudaStream_t s);
+// Bound of those products relative to ||a_j|| ||t||: a lane chain of d = ceil(m / 32) + 5
+// TwoSum steps (2 (d+2)^2 u^2), the pair split of t and the rounded low products (4 u^2),
+// the float64 lane tree, a scaling of w and the float64 norm of t (12 float64 units), with
+// 1% for second-order terms.
+inline double setup_dot_gamma(int m) {
+  const double d = (double)((m + 31) / 32 + 5);
+  return 1.01 * (2.0 * (d + 2.0) * (d + 2.0) * 0x1p-48 + 4.0 * 0x1p-48 + 12.0 * 0x1p-53);
+}
 // out_i = sum_j a_ij (deterministic); part: row_sums_scratch(m, n) doubles.
 size_t row_sums_scratch(int m, int n);
 cudaError_t launch_row_sums(const float* A, int lda, int m, int n, double* part, double* out, cudaStream_t s);

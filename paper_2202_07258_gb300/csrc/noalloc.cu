@@ -66,10 +66,6 @@ __global__ void k_fill_bounds(double* l, double* u, float2* l2, float2* u2, uint
   }
 }
 
-__global__ void k_fill(double* v, int n, double val) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = val;
-}
-
 // bad = 1 unless a_j^T t < 0 (with its rounding bound) on every nonzero column of J_inf.
 __global__ void k_dir_check(const double* w, const double* nrm, const uint8_t* jinf, int n,
                             double gamma_tn, int* bad) {
@@ -81,7 +77,7 @@ __global__ void k_dir_check(const double* w, const double* nrm, const uint8_t* j
 
 struct Layout {
   Buffers b;
-  double *l, *u, *nrm, *w, *t, *scal;
+  double *l, *u, *nrm, *w, *scal;
   float2 *l2, *u2;
   uint8_t* jinf;
   float *y, *v, *v2, *q;
@@ -121,7 +117,6 @@ Layout carve(unsigned char* base, int m, int n, int m4, int lda, int fwd_tiles, 
   L.nrm = a.take<double>(n);
   L.w = a.take<double>(n);
   L.jinf = a.take<uint8_t>(n);
-  L.t = a.take<double>(m);
   L.scal = a.take<double>(2);
   L.y = a.take<float>(m4);
   L.x0 = a.take<double>(n);
@@ -241,16 +236,14 @@ bvls_status bvls_solve_static(const float* A, int m, int n, int lda, const doubl
   if (u) SCK(cudaMemcpyAsync(W.u, u, sizeof(double) * n, cudaMemcpyHostToDevice, s));
   k_fill_bounds<<<64, 256, 0, s>>>(W.l, W.u, W.l2, W.u2, W.jinf, n, l != nullptr, u != nullptr);
   SCK(cudaGetLastError());
-  SCK(launch_col_norms(A, lda, m, n, W.nrm, s));
+  // with an infinite upper bound, the same pass gives w = A^T t for t = -1 (Proposition 2,
+  // case 3), as bvls_setup tries first; otherwise theta = 0
+  SCK(launch_col_norms(A, lda, m, n, W.nrm, s, any_inf ? W.w : nullptr));
   int dual_mode = kScaling;
   double t_norm = 0.0, gamma_w = 0.0;
   if (any_inf) {
-    // t = -1 (Proposition 2, case 3), as bvls_setup tries first; otherwise theta = 0.
-    k_fill<<<16, 256, 0, s>>>(W.t, m, -1.0);
-    SCK(cudaGetLastError());
-    SCK(launch_col_dots(A, lda, m, n, W.t, W.w, s));
     t_norm = std::sqrt((double)m);
-    gamma_w = 1.01 * (m + 8) * kU64;
+    gamma_w = setup_dot_gamma(m);
     k_dir_check<<<64, 256, 0, s>>>(W.w, W.nrm, W.jinf, n, gamma_w * t_norm, W.flag + 1);
     SCK(cudaGetLastError());
   }

@@ -33,6 +33,9 @@ CASES = [
     ("bvls_224x512", lambda: W.bvls_dirichlet_shared(224, 512, 1, 8, 0.005, 0), 1e-5),
     ("abs_30x50", lambda: W.nnls_abs_gaussian(30, 50, 0.2, 1.0, 3), 1e-5),
     ("gaussian_40x8", lambda: W.nnls_gaussian(40, 8, 0.5, 0.01, 1), 1e-5),   # n below the step count
+    # two and four float4 row chunks per thread in the Lanczos kernel (lda > 2048, > 4096)
+    ("abs_3000x900", lambda: W.nnls_abs_gaussian(3000, 900, 0.05, 1.0, 2), 1e-5),
+    ("abs_5000x700", lambda: W.nnls_abs_gaussian(5000, 700, 0.05, 1.0, 4), 1e-5),
 ]
 
 
