@@ -563,23 +563,227 @@ __global__ void __launch_bounds__(kPowThreads, 1)
   if (blockIdx.x == 0 && tid == 0 && !s_ok) scal[1] = -1.0;   // a barrier wait gave up: the caller reports it
 }
 
-template <int KC>
-static cudaError_t lanczos_launch_kc(const float* A, int lda, int m, int n, const float* v0, float* part, float* q,
-                                     double* wn2, double* qn2, double* ab, double* scal, unsigned* gb, int K, int grid,
-                                     cudaStream_t s) {
-  const int per = (n + grid - 1) / grid;
-  const size_t sm = sizeof(float) * ((size_t)lda + 3 * (size_t)per);
-  cudaError_t e = cudaFuncSetAttribute(k_lanczos_coop<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+// The same iteration for lda <= 2048 with a warp per column: a lane holds rows lane + 32 k
+// (float4 chunks, k < 16) of one column in registers, sums its products with q over the warp,
+// forms w_j and adds a_j w_j into its own rows of the warp's partial of A w; the next column
+// of the warp loads meanwhile.  No block barrier per column: the eight warps' partials meet
+// in shared memory once per iteration.  256 threads, up to 255 registers each.
+constexpr int kWcThreads = 256;
+constexpr int kWcChunks = 16;   // float4 row chunks per lane: lda <= 4 * 32 * 16 = 2048
+
+__global__ void __launch_bounds__(kWcThreads, 1)
+    k_lanczos_wc(const float* __restrict__ A, int lda, int m, int n, const float* v0, float* part, float* q,
+                 double* wn2, double* qn2, double* ab, double* scal, unsigned* gb, int K) {
+  constexpr int NW = kWcThreads / 32;
+  constexpr int RC = kWcChunks;
+  extern __shared__ __align__(16) float psm[];
+  const int lda4 = lda >> 2;
+  const int per = (n + gridDim.x - 1) / gridDim.x;
+  const int j0 = min(n, (int)blockIdx.x * per), j1 = min(n, j0 + per);
+  float* sq = psm;                                              // q (lda)
+  float4* sacc = reinterpret_cast<float4*>(psm + lda);          // the warps' partials of A w (NW x lda4)
+  float* sv = psm + (size_t)(NW + 1) * lda;                     // v_it of the CTA's columns (per)
+  float* svp = sv + per;                                        // v_{it-1}
+  float* sw = svp + per;                                        // w
+  __shared__ double s_red[NW];
+  __shared__ float s_part[NW][32];
+  __shared__ int s_ok;
+  __shared__ double s_alpha, s_beta;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nslices = lda / 32;
+  const float4* A4 = reinterpret_cast<const float4*>(A);
+  unsigned long long* gcount = reinterpret_cast<unsigned long long*>(gb);
+  unsigned long long nbar = 0ull;
+  if (tid == 0) {
+    s_ok = 1;
+    s_beta = 0.0;
+    s_alpha = 0.0;
+  }
+  for (int j = j0 + tid; j < j1; j += kWcThreads) {
+    sw[j - j0] = v0[j];
+    sv[j - j0] = 0.f;
+    svp[j - j0] = 0.f;
+  }
+  __syncthreads();
+  auto barrier = [&]() -> bool {
+    __syncthreads();
+    if (tid == 0 && !grid_count_sync(gcount, (unsigned long long)gridDim.x * ++nbar, kGridWaitCycles)) s_ok = 0;
+    __syncthreads();
+    return s_ok != 0;
+  };
+  for (int it = 0; it <= K; ++it) {
+    // ---- columns
+    if (it > 0) {
+      if (warp == 0) {   // alpha_it = ||q_it||^2 from the slice partials, same order in every CTA
+        const double t = warp_load_sum(qn2, nslices);
+        if (lane == 0) s_alpha = t;
+      }
+      {
+        float4 qv[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int c = tid + k * kWcThreads;
+          qv[k] = c < lda4 ? __ldcg(reinterpret_cast<const float4*>(q) + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int c = tid + k * kWcThreads;
+          if (c < lda4) reinterpret_cast<float4*>(sq)[c] = qv[k];
+        }
+      }
+      __syncthreads();
+      if (blockIdx.x == 0 && tid == 0) ab[2 * it] = s_alpha;
+      if (it == K) break;   // alpha_K is the last coefficient
+    }
+    const float alpha = (float)s_alpha, beta = (float)s_beta;
+    const float4* sq4 = reinterpret_cast<const float4*>(sq);
+    float4 acc[RC];
+#pragma unroll
+    for (int k = 0; k < RC; ++k) acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto load_col = [&](int j, float4 (&r)[RC]) {
+#pragma unroll
+      for (int k = 0; k < RC; ++k) {
+        const int c = lane + 32 * k;
+        r[k] = c < lda4 ? A4[(size_t)j * lda4 + c] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    };
+    auto body = [&](int j, const float4 (&r)[RC]) {
+      float wj;
+      if (it > 0) {
+        float d0 = 0.f, d1 = 0.f;
+#pragma unroll
+        for (int k = 0; k < RC; ++k) {
+          const int c = lane + 32 * k;
+          if (c < lda4) {
+            const float4 qk = sq4[c];
+            d0 = fmaf(r[k].x, qk.x, d0);
+            d1 = fmaf(r[k].y, qk.y, d1);
+            d0 = fmaf(r[k].z, qk.z, d0);
+            d1 = fmaf(r[k].w, qk.w, d1);
+          }
+        }
+        float u = d0 + d1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+        wj = u - alpha * sv[j - j0] - beta * svp[j - j0];
+        if (lane == 0) sw[j - j0] = wj;
+      } else {
+        wj = sw[j - j0];   // w = v0
+      }
+#pragma unroll
+      for (int k = 0; k < RC; ++k) {
+        acc[k].x = fmaf(r[k].x, wj, acc[k].x);
+        acc[k].y = fmaf(r[k].y, wj, acc[k].y);
+        acc[k].z = fmaf(r[k].z, wj, acc[k].z);
+        acc[k].w = fmaf(r[k].w, wj, acc[k].w);
+      }
+    };
+    {
+      float4 ca[RC], cb[RC];
+      int j = j0 + warp;
+      if (j < j1) load_col(j, ca);
+      for (; j < j1; j += 2 * NW) {
+        if (j + NW < j1) load_col(j + NW, cb);
+        body(j, ca);
+        if (j + NW >= j1) break;
+        if (j + 2 * NW < j1) load_col(j + 2 * NW, ca);
+        body(j + NW, cb);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < RC; ++k) {
+      const int c = lane + 32 * k;
+      if (c < lda4) sacc[(size_t)warp * lda4 + c] = acc[k];
+    }
+    __syncthreads();
+    {
+      double w2 = 0.0;
+      for (int j = j0 + tid; j < j1; j += kWcThreads) w2 += (double)sw[j - j0] * (double)sw[j - j0];
+      w2 = warp_sum_d(w2);
+      if (lane == 0) s_red[warp] = w2;
+    }
+    float4* p4 = reinterpret_cast<float4*>(part + (size_t)blockIdx.x * lda);
+    for (int c = tid; c < lda4; c += kWcThreads) {   // the warps' partials, in warp order
+      float4 t = sacc[c];
+#pragma unroll
+      for (int w = 1; w < NW; ++w) {
+        const float4 o = sacc[(size_t)w * lda4 + c];
+        t.x += o.x;
+        t.y += o.y;
+        t.z += o.z;
+        t.w += o.w;
+      }
+      p4[c] = t;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < NW; ++w) t += s_red[w];
+      wn2[blockIdx.x] = t;
+    }
+    if (!barrier()) break;
+    // ---- rows: beta_it = ||w||, v_{it+1} = w / beta_it, q_{it+1} = A v_{it+1}
+    if (warp == 0) {
+      const double t = warp_load_sum(wn2, gridDim.x);
+      if (lane == 0) {
+        const double bt = sqrt(t);
+        if (it > 0) s_beta = bt;
+        if (it > 0 && blockIdx.x == 0) ab[2 * it + 1] = bt;
+        s_red[0] = bt > 0.0 ? 1.0 / bt : 0.0;   // an invariant subspace: v and q become zero
+      }
+    }
+    __syncthreads();
+    const float sc = (float)s_red[0];
+    for (int j = j0 + tid; j < j1; j += kWcThreads) {
+      svp[j - j0] = sv[j - j0];
+      sv[j - j0] = sc * sw[j - j0];
+    }
+    for (int sl = blockIdx.x; sl < nslices; sl += gridDim.x) {
+      const int row = sl * 32 + lane;
+      float sum = 0.f;
+      for (int t0 = warp; t0 < (int)gridDim.x; t0 += NW * 10) {   // ten loads in flight per lane
+        float v[10];
+#pragma unroll
+        for (int k = 0; k < 10; ++k) {
+          const int t = t0 + NW * k;
+          v[k] = t < (int)gridDim.x ? __ldcg(part + (size_t)t * lda + row) : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < 10; ++k) sum += v[k];
+      }
+      s_part[warp][lane] = sum;
+      __syncthreads();
+      if (warp == 0) {
+        float qi = 0.f;
+        for (int w = 0; w < NW; ++w) qi += s_part[w][lane];
+        qi *= sc;
+        q[row] = qi;
+        double q2 = (double)qi * (double)qi;
+        q2 = warp_sum_d(q2);
+        if (lane == 0) qn2[sl] = q2;
+      }
+      __syncthreads();
+    }
+    if (!barrier()) break;
+  }
+  if (blockIdx.x == 0 && tid == 0 && !s_ok) scal[1] = -1.0;   // a barrier wait gave up: the caller reports it
+}
+
+// Cooperative launch of a Lanczos kernel: one CTA per SM at most (grid <= what fits).
+static cudaError_t lanczos_launch(const void* fn, int threads, size_t sm, const float* A, int lda, int m, int n,
+                                  const float* v0, float* part, float* q, double* wn2, double* qn2, double* ab,
+                                  double* scal, unsigned* gb, int K, int grid, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int per_sm = 0, dev = 0, sms = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lanczos_coop<KC>, kPowThreads, sm);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, sm);
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   if (per_sm < 1 || grid > per_sm * sms) return cudaErrorNotSupported;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(kPowThreads);
+  cfg.blockDim = dim3(threads);
   cfg.dynamicSmemBytes = sm;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -587,7 +791,8 @@ static cudaError_t lanczos_launch_kc(const float* A, int lda, int m, int n, cons
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_lanczos_coop<KC>, A, lda, m, n, v0, part, q, wn2, qn2, ab, scal, gb, K);
+  void* args[] = {&A, &lda, &m, &n, &v0, &part, &q, &wn2, &qn2, &ab, &scal, &gb, &K};
+  return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 cudaError_t launch_lanczos_coop(const float* A, int lda, int m, int n, const float* v0, float* part, float* q,
@@ -595,10 +800,16 @@ cudaError_t launch_lanczos_coop(const float* A, int lda, int m, int n, const flo
                                 cudaStream_t s) {
   if (lda > 4 * kPowChunks * kPowThreads || lda % 32 != 0 || grid < 1 || K < 1) return cudaErrorNotSupported;
   const int lda4 = lda / 4;
-  if (lda4 <= kPowThreads) return lanczos_launch_kc<1>(A, lda, m, n, v0, part, q, wn2, qn2, ab, scal, gb, K, grid, s);
-  if (lda4 <= 2 * kPowThreads)
-    return lanczos_launch_kc<2>(A, lda, m, n, v0, part, q, wn2, qn2, ab, scal, gb, K, grid, s);
-  return lanczos_launch_kc<4>(A, lda, m, n, v0, part, q, wn2, qn2, ab, scal, gb, K, grid, s);
+  const int per = (n + grid - 1) / grid;
+  if (lda4 <= 32 * kWcChunks) {
+    const size_t sm = sizeof(float) * ((size_t)(kWcThreads / 32 + 1) * lda + 3 * (size_t)per);
+    return lanczos_launch(reinterpret_cast<const void*>(k_lanczos_wc), kWcThreads, sm, A, lda, m, n, v0, part, q,
+                          wn2, qn2, ab, scal, gb, K, grid, s);
+  }
+  const size_t sm = sizeof(float) * ((size_t)lda + 3 * (size_t)per);
+  const void* fn = lda4 <= 2 * kPowThreads ? reinterpret_cast<const void*>(k_lanczos_coop<2>)
+                                           : reinterpret_cast<const void*>(k_lanczos_coop<4>);
+  return lanczos_launch(fn, kPowThreads, sm, A, lda, m, n, v0, part, q, wn2, qn2, ab, scal, gb, K, grid, s);
 }
 
 }  // namespace bvls
