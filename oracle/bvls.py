@@ -61,6 +61,8 @@ __all__ = [
     "free_set",
     "backward",
     "solve_cp",
+    "round_bf16",
+    "gram_fista_batch",
 ]
 
 
@@ -569,3 +571,76 @@ def solve_cp(A, y, l, u, *, tol=1e-6, screen_every=10, screening=True, max_iter=
         x = x_new
     raise AssertionError("unreachable: the last iteration always evaluates the gap")
 
+
+
+def round_bf16(v):
+    """Round float64 values to bfloat16 (8 significant bits, round to nearest, ties to even),
+    returned as float64: the value is first rounded to float32 (the precision the operands
+    have before conversion), then its float32 bit pattern is rounded at bit 16."""
+    f = np.asarray(v, dtype=np.float64).astype(np.float32)
+    bits = f.view(np.uint32).astype(np.uint64)
+    lsb = (bits >> 16) & 1
+    rounded = ((bits + 0x7FFF + lsb) >> 16) << 16
+    out = (rounded & 0xFFFFFFFF).astype(np.uint32).view(np.float32).astype(np.float64)
+    finite = np.isfinite(f)
+    return np.where(finite, out, f.astype(np.float64))
+
+
+def gram_fista_batch(A, Y, l, u, L, *, screen_every=10, max_iter=30, restart=False, x0=None,
+                     bf16=True):
+    """The batched iteration for B right-hand sides sharing A, without screening: FISTA (as
+    ``solve``) whose correlations g_k = A^T (y - A x_k) are formed exactly every
+    ``screen_every`` iterations (k = 0, K, 2K, ...) and in between by the Gram recurrence
+
+        g_k = g_{k-1} - H d_k,   d_k = x_k - x_{k-1},   H = A^T A,
+
+    exact in exact arithmetic because A x is affine in x.  With ``bf16`` the recurrence uses
+    H~ = bf16(A^T A) and d~_k = bf16(d_k) (the tensor-core operands), and the step's
+    momentum term uses d~_k as well; the evaluation steps use the exact d_k.  Every step:
+
+        t_k = 1 at k = 0 (or after a restart), else (1 + sqrt(1 + 4 t_{k-1}^2)) / 2,
+        beta_k = (t_k - 1) / t_{k+1},   g_v = (1 + beta_k) g_k - beta_k g_{k-1},
+        x_{k+1} = clip(x_k + beta_k d_k + g_v / L, l, u),
+
+    and with ``restart`` t_k = 1 when g_v^T (x_k - x_{k-1}) < 0 at step k - 1.  Y is B x m;
+    returns X (B x n) after ``max_iter`` steps.  With bf16=False this is the exact-gradient
+    FISTA of ``solve(..., screening=False)``, step for step."""
+    A = np.asarray(A, dtype=np.float64)
+    Y = np.atleast_2d(np.asarray(Y, dtype=np.float64))
+    m, n = A.shape
+    l = np.zeros(n) if l is None else np.asarray(l, dtype=np.float64)
+    u = np.full(n, np.inf) if u is None else np.asarray(u, dtype=np.float64)
+    K = int(screen_every)
+    H = A.T @ A
+    if bf16:
+        H = round_bf16(H)
+    out = np.empty((Y.shape[0], n))
+    for b in range(Y.shape[0]):
+        y = Y[b]
+        x = np.clip(np.zeros(n) if x0 is None else np.asarray(x0[b], dtype=np.float64), l, u)
+        x_prev = x.copy()
+        g_prev = np.zeros(n)
+        d_op = np.zeros(n)          # the recurrence's operand for the next step
+        t_prev, dsum_prev = 1.0, 0.0
+        for k in range(max_iter):
+            if k == 0 or (restart and dsum_prev < 0.0):
+                t = 1.0
+            else:
+                t = 0.5 * (1.0 + np.sqrt(1.0 + 4.0 * t_prev * t_prev))
+            t_next = 0.5 * (1.0 + np.sqrt(1.0 + 4.0 * t * t))
+            beta = (t - 1.0) / t_next
+            if k % K == 0:
+                g = A.T @ (y - A @ x)
+                d_mom = x - x_prev
+            else:
+                g = g_prev - H @ d_op
+                d_mom = d_op
+            gv = (1.0 + beta) * g - beta * g_prev
+            x_next = np.clip(x + beta * d_mom + gv / L, l, u)
+            d = x_next - x
+            dsum_prev = float(gv @ d)
+            d_op = round_bf16(d) if bf16 else d
+            x_prev, x = x, x_next
+            g_prev, t_prev = g, t
+        out[b] = x
+    return out

@@ -258,3 +258,33 @@ def test_persistent_steps_match_under_options(P, kw):
         # every step is timed (a persistent launch as a whole, its later steps as empty intervals)
         assert info1["step_launches"] == info0["step_launches"] > 0
         assert info1["step_ms"] > 0 and info0["step_ms"] > 0
+
+
+@pytest.mark.parametrize("single_pass", [1, 0])
+def test_tensor_core_iterates_follow_the_bf16_gram_oracle(P, single_pass):
+    """Iterate-level parity of the tensor-core path.  Between two evaluations the GPU forms the
+    correlations by the Gram recurrence g_k = g_{k-1} - bf16(A^T A) bf16(x_k - x_{k-1})
+    (float32 accumulation); oracle.gram_fista_batch runs the same iteration in float64 with
+    the same two bf16 roundings.  Exact agreement is out of reach: a change of a few float32
+    units in x_k - x_{k-1} moves some entries across a bf16 rounding boundary (2^-8 relative),
+    so float32 arithmetic alone puts a float64 copy of the iteration about 1.5e-5 away from
+    the oracle after 30 iterations, against about 1e-4 between the bf16 iteration and the
+    exact-gradient FISTA.  After 30 iterations (evaluations at 0, 10, 20, 30; no screening,
+    no restart, the same L) the GPU must sit within 1e-4 of the bf16 oracle and at most half
+    as far from it as from the exact-gradient FISTA: the deviation the bf16 operands cause is
+    the oracle's, what is left is float32 arithmetic."""
+    p = W.bvls_dirichlet_shared(224, 512, 16, 8, 0.005, 3)
+    A, Y = p.A.astype(np.float64), p.y.astype(np.float64)
+    L = 1.05 * float(np.linalg.norm(A, 2) ** 2)
+    N = 30
+    X, S, gaps, its, sts, info, st = batched(P, p, tol=0.0, screen_every=10, max_iter=N, screening=False,
+                                             restart=False, lipschitz=L, precision="fp32",
+                                             single_pass=single_pass, check=False)
+    assert np.all(its == N) and not np.any(S)
+    Xb = O.gram_fista_batch(A, Y, p.l, p.u, L, screen_every=10, max_iter=N, bf16=True)
+    Xe = O.gram_fista_batch(A, Y, p.l, p.u, L, screen_every=10, max_iter=N, bf16=False)
+    scale = max(1.0, float(np.abs(Xb).max()))
+    err_b = float(np.abs(X - Xb).max())
+    err_e = float(np.abs(X - Xe).max())
+    assert err_b <= 1e-4 * scale, (err_b, err_e)
+    assert err_b <= 0.5 * err_e, (err_b, err_e)

@@ -428,3 +428,46 @@ def test_literal_and_at_bound_fixing_reach_the_same_optimum():
         assert np.abs(xp - xs).max() <= 1e-9 * max(1.0, np.abs(xs).max())
     with pytest.raises(ValueError):
         O.solve(A, y, p.l, p.u, pin="later")
+
+
+# ---------------------------------------------------------------- batched Gram recurrence
+def test_round_bf16_matches_the_library_conversion():
+    """round_bf16 against torch's float32 -> bfloat16 conversion (round to nearest even), on
+    ties, subnormal-range, large and random values."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(11)
+    v = np.concatenate([
+        [0.0, -0.0, 1.0, 1 + 2.0 ** -8, 1 + 3 * 2.0 ** -9, 1 - 2.0 ** -9, -2.5, 1e-30, 3.0e38, 65504.0],
+        rng.standard_normal(2000) * 10.0 ** rng.integers(-6, 6, 2000)])
+    ref = torch.tensor(v, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(O.round_bf16(v), ref)
+
+
+@pytest.mark.parametrize("restart", [False, True])
+def test_gram_recurrence_with_exact_operands_is_fista(restart):
+    """Without the bf16 roundings the Gram-form iteration (exact correlations every K steps,
+    g_k = g_{k-1} - A^T A (x_k - x_{k-1}) in between) is the exact-gradient FISTA of solve()
+    step for step: the recurrence is exact because A x is affine in x.  solve() returns the
+    iterate its last evaluation certifies, x_N after N + 1 iterations."""
+    p = W.bvls_dirichlet_shared(64, 128, 5, 8, 0.005, 2)
+    A, Y = p.A.astype(np.float64), p.y.astype(np.float64)
+    L = 1.05 * np.linalg.norm(A, 2) ** 2
+    for N in (1, 9, 10, 11, 30):
+        G = O.gram_fista_batch(A, Y, p.l, p.u, L, screen_every=10, max_iter=N, restart=restart, bf16=False)
+        for b in range(Y.shape[0]):
+            r = O.solve(A, Y[b], p.l, p.u, tol=0.0, screen_every=10, screening=False, max_iter=N + 1,
+                        L=L, restart=restart)
+            assert np.abs(G[b] - r.x).max() <= 1e-13 * max(1.0, np.abs(r.x).max()), (N, b)
+
+
+def test_gram_recurrence_bf16_operands_perturb_the_iterates():
+    """The bf16 operands change the iterates between evaluations (so a comparison against
+    the bf16 form tests the rounding, not only FISTA), by far less than the iterate."""
+    p = W.bvls_dirichlet_shared(64, 128, 5, 8, 0.005, 2)
+    A, Y = p.A.astype(np.float64), p.y.astype(np.float64)
+    L = 1.05 * np.linalg.norm(A, 2) ** 2
+    Gb = O.gram_fista_batch(A, Y, p.l, p.u, L, screen_every=10, max_iter=30, bf16=True)
+    Ge = O.gram_fista_batch(A, Y, p.l, p.u, L, screen_every=10, max_iter=30, bf16=False)
+    d = np.abs(Gb - Ge).max()
+    assert 1e-7 < d < 1e-2 * np.abs(Ge).max()
+    assert np.all(Gb >= p.l) and np.all(Gb <= p.u)
