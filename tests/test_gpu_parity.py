@@ -7,6 +7,9 @@ Two kinds of comparison:
     objective, its solution and its screened set are checked against the oracle and
     against an FP64 optimum certified by the optimality conditions of Section 3.2.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -391,6 +394,17 @@ def test_screenable_single_instance_full_size(P):
     assert float(np.abs(x - xs).max()) <= 1e-7 * max(1.0, float(np.abs(xs).max()))
     g_s = A.T @ (y - A @ xs)
     assert np.all(g_s[scr == 1] < 0) and np.all(xs[scr == 1] == 0)
+    # the FP64 optimum of the oracle's own run (tests/golden/make_bench_optima.py: oracle solve,
+    # polish, optimality conditions), independent of the GPU's free set
+    rec = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "bench_optima.json")))
+    rec = rec["nnls_abs_gaussian_2000x10000"]["single"]
+    assert rec["unique"]
+    x_star = np.zeros(p.n)
+    x_star[np.asarray(rec["x_star_idx"], dtype=int)] = rec["x_star_val"]
+    scale = max(1.0, float(np.abs(x_star).max()))
+    assert float(np.abs(x - x_star).max()) <= 1e-7 * scale
+    assert float(np.abs(x0 - x_star).max()) <= 1e-6 * scale
+    assert O.primal_objective(A, y, x0) <= rec["P_star"] + info0["gap"] * (1 + 1e-9) + 1e-9
     assert st == P.BVLS_OK and info["dual"] == "translation"
     assert np.all(x >= 0) and np.all(x[scr == 1] == 0)
     t = -np.ones(p.m)
