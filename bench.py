@@ -729,6 +729,20 @@ def ncu_region(args):
         opts = make_opts(tol=0.0, screen_every=K_SCREEN, max_iter=20, screening=False, profile=True,
                          precision=HEAD_PRECISION)
         run = lambda: s.solve(y, opts=opts)
+    elif args.ncu_region == "setup":
+        # bvls_setup of the headline matrix from device memory (norms, direction search,
+        # Lanczos step constant, workspace); each call makes and destroys a handle
+        from paper_2202_07258_gb300 import _capi
+        p = make_problem(WORKLOAD, 0)
+        A_d = torch.from_numpy(np.ascontiguousarray(p.A.T)).to(dev)   # column-major A
+        l_h, u_h = np.ascontiguousarray(p.l), np.ascontiguousarray(p.u)
+        s = None
+
+        def run():
+            st, h = _capi.bvls_setup(A_d.data_ptr(), p.m, p.n, p.m, l_h.ctypes.data, u_h.ctypes.data, None, 0)
+            assert st == 0, _capi.bvls_last_error()
+            torch.cuda.synchronize()
+            _capi.bvls_destroy(h)
     elif args.ncu_region == "ragged":
         from paper_2202_07258_gb300 import solve_ragged
         probs = W.mixed_uneven(512, 0, abs_matrix=False, noise=0.01)
@@ -892,7 +906,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-batched", action="store_true", help="skip the shared-A batched leg")
-    ap.add_argument("--ncu-region", choices=["single", "batched", "hbm", "ragged"], default=None,
+    ap.add_argument("--ncu-region", choices=["single", "batched", "hbm", "ragged", "setup"], default=None,
                     help="profiling aid: run one warm solve of that leg between cudaProfilerStart/Stop "
                          "(for ncu --profile-from-start off) and exit without a bench line")
     args = ap.parse_args()
