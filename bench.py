@@ -729,6 +729,13 @@ def ncu_region(args):
         opts = make_opts(tol=0.0, screen_every=K_SCREEN, max_iter=20, screening=False, profile=True,
                          precision=HEAD_PRECISION)
         run = lambda: s.solve(y, opts=opts)
+    elif args.ncu_region == "table2":
+        # the Table-2 BVLS shape, FISTA with screening, to gap 1e-6
+        p = W.bvls_table2(1000, 2000, 0)
+        s = Solver(torch.from_numpy(p.A).to(dev), p.l, p.u)
+        y = torch.from_numpy(p.y).to(dev)
+        opts = make_opts(tol=TOL, screen_every=K_SCREEN, profile=True)
+        run = lambda: s.solve(y, opts=opts)
     elif args.ncu_region == "setup":
         # bvls_setup of the headline matrix from device memory (norms, direction search,
         # Lanczos step constant, workspace); each call makes and destroys a handle
@@ -906,7 +913,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-batched", action="store_true", help="skip the shared-A batched leg")
-    ap.add_argument("--ncu-region", choices=["single", "batched", "hbm", "ragged", "setup"], default=None,
+    ap.add_argument("--ncu-region", choices=["single", "batched", "hbm", "ragged", "setup", "table2"], default=None,
                     help="profiling aid: run one warm solve of that leg between cudaProfilerStart/Stop "
                          "(for ncu --profile-from-start off) and exit without a bench line")
     args = ap.parse_args()
